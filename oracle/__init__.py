@@ -1,0 +1,213 @@
+"""Plain CPU oracle for the compressed key sort hot path (arXiv 2009.11543).
+
+TEST INFRASTRUCTURE ONLY: only ``tests/``, ``__graft_entry__.smoke()`` and the
+``cpu_baseline`` / ``--impl reference`` legs of ``bench.py`` may import this
+package.  It shares no code with the CUDA path and never imports it.
+
+The arithmetic lives in ``ck_oracle.c`` (plain C, single thread); this module
+only builds it with gcc and marshals numpy arrays.  Each wrapper names the
+passage of the paper it follows:
+
+* ``dbit``            -- Sec. 3.1, definition of the distinction bit position
+* ``sort_rows``       -- Sec. 3.1, sorted (lexicographic) order; ties by row id
+* ``dmask``           -- Theorem 1, D = {D_1..D_n} over adjacent sorted keys
+* ``variant_mask``    -- Sec. 4.2 variant bitmap, computed as in Sec. 4.3
+* ``compress``        -- Sec. 3.2, Compress(key), bit by bit
+* ``sort_compressed`` -- Sec. 3.2, compressed key sort
+* ``refine``          -- Sec. 4.3 rebuild step 1 with D-offset (Sec. 5.3)
+* ``btree``           -- Sec. 4.2 / 5.3, bottom-up bulk load
+* ``mlp``             -- (``oracle.mlp``) the learned CDF model, fp64
+
+Layout conventions are stated in the header of ``ck_oracle.c``: bitmaps are
+uint64 words most-significant-first (position p = bit 63 - p%64 of word p/64),
+compressed keys are row-major ``[n, K]`` uint32 words, least significant first.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "ck_oracle.c")
+_LIB = os.path.join(_HERE, "libck_oracle.so")
+NO_DBIT = 0xFFFF
+MAX_LEVELS = 64
+
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile ck_oracle.c with gcc into oracle/libck_oracle.so."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + ".tmp%d" % os.getpid()
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-shared", "-fPIC", "-o", tmp, _SRC])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        build()
+        lib = ctypes.CDLL(_LIB)
+        P = ctypes.c_void_p
+        U64, U32, I64 = ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int64
+        lib.cko_uint_to_bytes.argtypes = [P, U64, U32, P]
+        lib.cko_dbit.argtypes = [P, P, U32]
+        lib.cko_dbit.restype = I64
+        lib.cko_sort_rows.argtypes = [P, U64, U32, U32, P]
+        lib.cko_dmask.argtypes = [P, U64, U32, U32, P, P]
+        lib.cko_variant_mask.argtypes = [P, U64, U32, U32, P, P]
+        lib.cko_compress.argtypes = [P, U64, U32, U32, P, U32, P]
+        lib.cko_compress.restype = I64
+        lib.cko_sort_compressed.argtypes = [P, U64, U32, P]
+        lib.cko_refine.argtypes = [P, P, U64, U32, P, U32, P]
+        lib.cko_btree_shape.argtypes = [U64, U32, P, U32]
+        lib.cko_btree_shape.restype = U32
+        lib.cko_btree_leaf_dbits.argtypes = [P, U64, U32, U32, P, P]
+        lib.cko_btree_inner.argtypes = [P, U64, U32, U32, P, U32, U32, P, P, P, P]
+        _lib = lib
+    return _lib
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def as_key_bytes(keys: np.ndarray) -> np.ndarray:
+    """Sec. 4.1: uint32/uint64 columns become big-endian byte strings; a 2-D
+    uint8 array of rows is used as given.  Returns a C-contiguous [n, W] uint8."""
+    keys = np.asarray(keys)
+    if keys.dtype == np.uint8 and keys.ndim == 2:
+        return np.ascontiguousarray(keys)
+    if keys.dtype in (np.uint32, np.uint64) and keys.ndim == 1:
+        k = np.ascontiguousarray(keys)
+        w = k.dtype.itemsize
+        out = np.empty((k.shape[0], w), np.uint8)
+        _load().cko_uint_to_bytes(_ptr(k), k.shape[0], 1 if w == 4 else 2, _ptr(out))
+        return out
+    raise TypeError("keys must be [n, W] uint8 rows or a 1-D uint32/uint64 column")
+
+
+def mask_words(key_bits: int) -> int:
+    return (key_bits + 63) // 64
+
+
+def dbit(a: bytes, b: bytes) -> int:
+    """Sec. 3.1: most significant differing bit position; -1 if equal."""
+    assert len(a) == len(b)
+    aa = np.frombuffer(bytes(a), np.uint8).copy()
+    bb = np.frombuffer(bytes(b), np.uint8).copy()
+    return int(_load().cko_dbit(_ptr(aa), _ptr(bb), len(a)))
+
+
+def sort_rows(keys) -> np.ndarray:
+    """Sorted order of the rows (lexicographic on the key bytes, ties by row id)."""
+    kb = as_key_bytes(keys)
+    n, W = kb.shape
+    perm = np.empty(n, np.uint32)
+    _load().cko_sort_rows(_ptr(kb), n, W, W, _ptr(perm))
+    return perm
+
+
+def dmask(keys, perm=None) -> np.ndarray:
+    """Theorem 1: the D-bitmap of the keys from adjacent pairs in sorted order."""
+    kb = as_key_bytes(keys)
+    n, W = kb.shape
+    if perm is None:
+        perm = sort_rows(kb)
+    perm = np.ascontiguousarray(perm, np.uint32)
+    out = np.zeros(mask_words(8 * W), np.uint64)
+    _load().cko_dmask(_ptr(kb), n, W, W, _ptr(perm), _ptr(out))
+    return out
+
+
+def variant_mask(keys, ref_row: int = 0) -> np.ndarray:
+    """Sec. 4.2/4.3: OR over all keys of (key xor reference key)."""
+    kb = as_key_bytes(keys)
+    n, W = kb.shape
+    out = np.zeros(mask_words(8 * W), np.uint64)
+    if n == 0:
+        return out
+    ref = np.ascontiguousarray(kb[ref_row])
+    _load().cko_variant_mask(_ptr(kb), n, W, W, _ptr(ref), _ptr(out))
+    return out
+
+
+def popcount(mask: np.ndarray) -> int:
+    return int(sum(bin(int(w)).count("1") for w in np.asarray(mask, np.uint64)))
+
+
+def compress(keys, mask: np.ndarray, K: int | None = None) -> np.ndarray:
+    """Sec. 3.2: Compress(key) for every row -> [n, K] uint32, least significant word first."""
+    kb = as_key_bytes(keys)
+    n, W = kb.shape
+    m = np.ascontiguousarray(mask, np.uint64)
+    assert m.shape[0] == mask_words(8 * W)
+    nbits = popcount(m)
+    if K is None:
+        K = max(1, (nbits + 31) // 32)
+    out = np.zeros((n, K), np.uint32)
+    r = _load().cko_compress(_ptr(kb), n, W, W, _ptr(m), K, _ptr(out))
+    if r < 0:
+        raise ValueError("mask has more set positions than %d words hold" % K)
+    return out
+
+
+def sort_compressed(ck: np.ndarray) -> np.ndarray:
+    """Sec. 3.2: sort the rows by their compressed value (ties by row id)."""
+    ck = np.ascontiguousarray(ck, np.uint32)
+    n, K = ck.shape
+    perm = np.empty(n, np.uint32)
+    _load().cko_sort_compressed(_ptr(ck), n, K, _ptr(perm))
+    return perm
+
+
+def refine(ck: np.ndarray, perm: np.ndarray, old_mask: np.ndarray, key_bits: int) -> np.ndarray:
+    """Sec. 4.3 step 1 + D-offset (Sec. 5.3): new D-bitmap from sorted compressed keys."""
+    ck = np.ascontiguousarray(ck, np.uint32)
+    n, K = ck.shape
+    perm = np.ascontiguousarray(perm, np.uint32)
+    om = np.ascontiguousarray(old_mask, np.uint64)
+    out = np.zeros(mask_words(key_bits), np.uint64)
+    _load().cko_refine(_ptr(ck), _ptr(perm), n, K, _ptr(om), key_bits, _ptr(out))
+    return out
+
+
+def btree_shape(n: int, f: int) -> list[int]:
+    """Entries per level (level 0 = leaves) of the canonical bulk-loaded tree."""
+    le = np.zeros(MAX_LEVELS, np.uint64)
+    levels = _load().cko_btree_shape(n, f, _ptr(le), MAX_LEVELS)
+    return [int(x) for x in le[:levels]]
+
+
+def entries_per_node(fanout: int, fill: float) -> int:
+    """Sec. 5.3: nodes are filled up to max fanout x fill factor."""
+    return max(1, int(fanout * fill))
+
+
+def btree(keys, perm: np.ndarray, f: int) -> dict:
+    """Sec. 4.2 / 5.3 bottom-up bulk load over the sorted permutation.
+
+    Returns ``levels`` (entries per level), ``leaf_dbit`` [n] and, for the inner
+    levels concatenated (level 1 first), ``child``, ``high`` (sorted index of the
+    highest key) and ``dbit`` (vs the previous entry's highest key)."""
+    kb = as_key_bytes(keys)
+    n, W = kb.shape
+    perm = np.ascontiguousarray(perm, np.uint32)
+    shape = btree_shape(n, f)
+    le = np.array(shape + [0], np.uint64)
+    lib = _load()
+    leaf = np.empty(n, np.uint16)
+    lib.cko_btree_leaf_dbits(_ptr(kb), n, W, W, _ptr(perm), _ptr(leaf))
+    ninner = int(sum(shape[1:]))
+    child = np.empty(max(ninner, 1), np.uint32)
+    high = np.empty(max(ninner, 1), np.uint64)
+    idbit = np.empty(max(ninner, 1), np.uint16)
+    lib.cko_btree_inner(_ptr(kb), n, W, W, _ptr(perm), f, len(shape), _ptr(le),
+                        _ptr(child), _ptr(high), _ptr(idbit))
+    return {"levels": shape, "leaf_dbit": leaf, "child": child[:ninner],
+            "high": high[:ninner], "dbit": idbit[:ninner]}

@@ -1,0 +1,409 @@
+"""Pins for the CPU oracle: each test checks an oracle function against something
+other than itself -- a fact the paper states for a worked example, a closed
+form, a brute-force enumeration, or an independently written procedure -- so
+that a dropped term, a wrong sign or index, or a transposed operand in the
+oracle fails at least one of them.  CPU only."""
+import itertools
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# ---------------------------------------------------------------- helpers
+def ints_to_rows(vals, nbits):
+    """Big-integer keys of nbits bits -> [n, W] big-endian uint8 rows (zero-padded)."""
+    W = (nbits + 7) // 8
+    pad = 8 * W - nbits
+    return np.array([list((v << pad).to_bytes(W, "big")) for v in vals], np.uint8).reshape(len(vals), W)
+
+
+def positions_of(mask, key_bits):
+    return [p for p in range(key_bits) if (int(mask[p // 64]) >> (63 - p % 64)) & 1]
+
+
+def mask_of(positions, key_bits):
+    m = np.zeros((key_bits + 63) // 64, np.uint64)
+    for p in positions:
+        m[p // 64] |= np.uint64(1 << (63 - p % 64))
+    return m
+
+
+def row_int(row):
+    return int.from_bytes(bytes(row), "big")
+
+
+def dbit_py(a: int, b: int, nbits: int) -> int:
+    """Closed form on integers: nbits - bit_length(a xor b); -1 if equal."""
+    x = a ^ b
+    return -1 if x == 0 else nbits - x.bit_length()
+
+
+def ck_ints(ck):
+    return [sum(int(w) << (32 * k) for k, w in enumerate(row)) for row in ck]
+
+
+def random_structured_keys(rng, n, W, nvary):
+    """Keys sharing a random pattern except at nvary random positions."""
+    base = rng.integers(0, 256, W, dtype=np.uint8)
+    pos = rng.choice(8 * W, size=nvary, replace=False)
+    keys = np.repeat(base[None, :], n, axis=0)
+    bits = np.unpackbits(keys, axis=1)
+    bits[:, pos] = rng.integers(0, 2, (n, nvary), dtype=np.uint8)
+    return np.packbits(bits, axis=1)
+
+
+# ------------------------------------------------ Sec. 3.1 worked example
+def load_fig2():
+    with open(os.path.join(GOLD, "fig2_worked_example.json")) as f:
+        g = json.load(f)
+    vals = [int(h, 16) for h in g["keys_sorted_hex"]]
+    return g, vals
+
+
+def test_fig2_stated_facts():
+    g, vals = load_fig2()
+    st, nb = g["stated"], g["key_bits"]
+    rows = ints_to_rows(vals, nb)
+    perm = oracle.sort_rows(rows)
+    assert list(perm) == list(range(len(vals)))            # the carrier keys are sorted
+    D = positions_of(oracle.dmask(rows), 8 * rows.shape[1])
+    assert D == st["distinction_positions"]
+    V = positions_of(oracle.variant_mask(rows), 8 * rows.shape[1])
+    assert V == st["variant_positions"]
+    inv = [p for p in range(nb) if p not in V]
+    assert inv == st["invariant_positions"]
+    adj = [oracle.dbit(bytes(rows[i - 1]), bytes(rows[i])) for i in range(1, len(vals))]
+    assert adj[:4] == [st["D_1"], st["D_2"], st["D_3"], st["D_4"]]
+    assert oracle.dbit(bytes(rows[1]), bytes(rows[3])) == st["dbit_key1_key3"]
+    assert oracle.dbit(bytes(rows[0]), bytes(rows[2])) == st["dbit_key0_key2"]
+    assert sorted(set(V) - set(D)) == st["variant_not_distinction"]
+    # deletion example (Sec. 3.2): delete key3, then key0
+    r3 = np.delete(rows, 3, axis=0)
+    D3 = positions_of(oracle.dmask(r3), 16)
+    assert (7 in D3) == st["after_deleting_key3"]["7_in_D"]
+    assert (7 in positions_of(oracle.variant_mask(r3), 16)) == st["after_deleting_key3"]["7_variant"]
+    r30 = np.delete(r3, 0, axis=0)
+    assert positions_of(oracle.dmask(r30), 16) == D3
+    assert (7 in positions_of(oracle.variant_mask(r30), 16)) == st["after_deleting_key3_and_key0"]["7_variant"]
+    # partial key (Sec. 4.2): the pk = 4 bits following D_1 of key_1
+    d1 = st["D_1"]
+    pk = "".join(str((vals[1] >> (nb - 1 - p)) & 1) for p in range(d1 + 1, d1 + 5))
+    assert pk == st["partial_key_of_key1_pk4"]
+
+
+def test_remark1_not_minimal():
+    with open(os.path.join(GOLD, "remark1_example.json")) as f:
+        g = json.load(f)
+    vals = [int(b, 2) for b in g["keys_sorted_bin"]]
+    rows = ints_to_rows(vals, g["key_bits"])
+    D = positions_of(oracle.dmask(rows), 8)
+    assert D == g["stated"]["distinction_positions"]
+    # brute force the smallest position subset whose slice orders the keys strictly
+    best = None
+    for size in range(1, 5):
+        for sub in itertools.combinations(range(4), size):
+            sl = [tuple((v >> (3 - p)) & 1 for p in sub) for v in vals]
+            if all(sl[i] < sl[i + 1] for i in range(len(sl) - 1)):
+                best = (size, list(sub))
+                break
+        if best:
+            break
+    assert best == (g["stated"]["minimum_size"], g["stated"]["minimal_slice"])
+    assert len(D) > best[0]          # the method does not claim minimality
+
+
+# --------------------------------------------------- Sec. 3.1 definitions
+def test_dbit_closed_form_uint64():
+    rng = np.random.default_rng(1)
+    a = rng.integers(0, 2**63, 2000, dtype=np.uint64) * np.uint64(2) + rng.integers(0, 2, 2000, dtype=np.uint64)
+    b = a ^ (np.uint64(1) << rng.integers(0, 64, 2000, dtype=np.uint64))   # one flipped bit
+    b[::3] = rng.integers(0, 2**63, len(b[::3]), dtype=np.uint64)
+    b[5] = a[5]
+    ab, bb = oracle.as_key_bytes(a), oracle.as_key_bytes(b)
+    for i in range(len(a)):
+        assert oracle.dbit(bytes(ab[i]), bytes(bb[i])) == dbit_py(int(a[i]), int(b[i]), 64)
+
+
+def test_uint_keys_are_big_endian():
+    v = np.array([0x0102030405060708], np.uint64)
+    assert bytes(oracle.as_key_bytes(v)[0]) == bytes([1, 2, 3, 4, 5, 6, 7, 8])
+    v32 = np.array([0xA1B2C3D4], np.uint32)
+    assert bytes(oracle.as_key_bytes(v32)[0]) == bytes([0xA1, 0xB2, 0xC3, 0xD4])
+
+
+def test_sort_rows_against_python_sorted():
+    rng = np.random.default_rng(2)
+    for W in (1, 3, 8, 13):
+        keys = rng.integers(0, 4, (500, W), dtype=np.uint8)     # many duplicates
+        perm = oracle.sort_rows(keys)
+        ref = sorted(range(500), key=lambda i: (bytes(keys[i]), i))
+        assert list(perm) == ref
+
+
+def test_sort_u64_matches_numeric_stable_argsort():
+    rng = np.random.default_rng(3)
+    v = rng.integers(0, 1000, 3000, dtype=np.uint64) << np.uint64(40)
+    assert list(oracle.sort_rows(v)) == list(np.argsort(v, kind="stable"))
+
+
+def test_varchar_nul_rule():
+    # Sec. 4.1 C: "AB" + NUL < "ABA" + NUL, and the D-bit falls in the NUL byte.
+    rows = np.array([list(b"ABA\0"), list(b"AB\0\0")], np.uint8)
+    assert list(oracle.sort_rows(rows)) == [1, 0]
+    p = oracle.dbit(bytes(rows[1]), bytes(rows[0]))
+    assert p // 8 == 2 and p == 16 + (8 - (ord("A")).bit_length())
+
+
+# ----------------------------------------------------- Lemma 1, Theorem 1
+def brute_dall(vals, nbits):
+    s = set()
+    for i in range(len(vals)):
+        for j in range(i + 1, len(vals)):
+            d = dbit_py(vals[i], vals[j], nbits)
+            if d >= 0:
+                s.add(d)
+    return sorted(s)
+
+
+def test_theorem1_exhaustive_tiny():
+    """D_all == D_adj over every multiset of up to 5 keys of 4 bits."""
+    nb = 4
+    count = 0
+    for size in range(1, 6):
+        for combo in itertools.combinations_with_replacement(range(16), size):
+            rows = ints_to_rows(list(combo), nb)
+            D = positions_of(oracle.dmask(rows), 8)
+            assert D == brute_dall(list(combo), nb)
+            count += 1
+    assert count > 6000
+
+
+@pytest.mark.parametrize("seed", range(8))
+def test_theorem1_random(seed):
+    rng = np.random.default_rng(10 + seed)
+    W = int(rng.integers(1, 6))
+    keys = random_structured_keys(rng, int(rng.integers(2, 60)), W, int(rng.integers(1, 8 * W)))
+    keys = keys[rng.permutation(len(keys))]
+    vals = [row_int(r) for r in keys]
+    D = positions_of(oracle.dmask(keys), 8 * W)
+    assert D == brute_dall(vals, 8 * W)
+
+
+def test_lemma1_min_over_adjacent():
+    rng = np.random.default_rng(4)
+    vals = sorted(set(int(x) for x in rng.integers(0, 2**20, 200)))
+    nb = 24
+    Dk = [None] + [dbit_py(vals[k - 1], vals[k], nb) for k in range(1, len(vals))]
+    for _ in range(2000):
+        i, j = sorted(rng.choice(len(vals), 2, replace=False))
+        rows = ints_to_rows([vals[i], vals[j]], nb)
+        assert oracle.dbit(bytes(rows[0]), bytes(rows[1])) == min(Dk[i + 1:j + 1])
+
+
+# ------------------------------------------------------ variant bitmap
+def test_variant_mask_brute_force():
+    rng = np.random.default_rng(5)
+    for W in (1, 4, 7):
+        keys = random_structured_keys(rng, 40, W, 5)
+        bits = np.unpackbits(keys, axis=1)
+        expect = [p for p in range(8 * W) if len(set(bits[:, p])) > 1]
+        for ref in (0, 17, 39):
+            assert positions_of(oracle.variant_mask(keys, ref), 8 * W) == expect
+
+
+# ------------------------------------------------------ Sec. 3.2 Compress
+def test_compress_all_positions_is_identity():
+    rng = np.random.default_rng(6)
+    for W in (4, 8, 12, 5):
+        keys = rng.integers(0, 256, (50, W), dtype=np.uint8)
+        ck = oracle.compress(keys, mask_of(range(8 * W), 8 * W))
+        assert ck_ints(ck) == [row_int(r) for r in keys]
+
+
+def test_compress_single_position_and_order():
+    rng = np.random.default_rng(7)
+    keys = rng.integers(0, 256, (64, 6), dtype=np.uint8)
+    for p in (0, 7, 8, 31, 47):
+        ck = oracle.compress(keys, mask_of([p], 48))
+        assert [int(r[0]) for r in ck] == [(row_int(k) >> (47 - p)) & 1 for k in keys]
+    # first set position lands in the most significant bit
+    ck = oracle.compress(keys, mask_of([3, 40], 48))
+    for k, c in zip(keys, ck):
+        v = row_int(k)
+        assert int(c[0]) == (((v >> 44) & 1) << 1) | ((v >> 7) & 1)
+
+
+def pext(x: int, m: int) -> int:
+    """Parallel bit extract (BMI2 PEXT semantics) on Python integers."""
+    out, k = 0, 0
+    while m:
+        low = m & -m
+        if x & low:
+            out |= 1 << k
+        k += 1
+        m ^= low
+    return out
+
+
+def paper_extract(key: bytes, mask_bytes: bytes) -> tuple[int, int]:
+    """Sec. 5.1 procedure: 8-byte masks starting at the byte of the next 1,
+    PEXT per mask, shift-and-OR concatenation.  Written independently of the
+    oracle's bit-by-bit definition."""
+    W = len(mask_bytes)
+    out, nb, start, masks = 0, 0, 0, 0
+    while True:
+        while start < W and mask_bytes[start] == 0:
+            start += 1
+        if start >= W:
+            break
+        mseg = mask_bytes[start:start + 8].ljust(8, b"\0")
+        kseg = key[start:start + 8].ljust(8, b"\0")
+        m, x = int.from_bytes(mseg, "big"), int.from_bytes(kseg, "big")
+        c = bin(m).count("1")
+        out = (out << c) | pext(x, m)
+        nb += c
+        masks += 1
+        start += 8
+    return out, masks
+
+
+def load_table3():
+    with open(os.path.join(GOLD, "table3_indbtab_dbitmap.txt")) as f:
+        bits = "".join(l.strip().replace(" ", "") for l in f if not l.startswith("#"))
+    assert len(bits) == 35 * 8
+    return bytes(int(bits[i:i + 8], 2) for i in range(0, len(bits), 8))
+
+
+def test_table3_mask_facts_and_paper_extraction():
+    mb = load_table3()
+    m = np.zeros(5, np.uint64)
+    big = int.from_bytes(mb, "big") << (320 - 280)
+    for w in range(5):
+        m[w] = np.uint64((big >> (64 * (4 - w))) & (2**64 - 1))
+    pos = positions_of(m, 280)
+    assert len(pos) == 56                                   # Table 2: 56 D-bits
+    assert max(pos) // 8 + 1 == 22                          # last D-bit in byte 22
+    assert (len(pos) + 7) // 8 == 7                         # fits in 7 bytes
+    assert (pos[0], pos[-1]) == (23, 174)
+    rng = np.random.default_rng(8)
+    keys = rng.integers(0, 256, (300, 35), dtype=np.uint8)
+    ck = oracle.compress(keys, m)
+    assert ck.shape == (300, 2)
+    masks = None
+    for k, c in zip(keys, ck_ints(ck)):
+        v, masks = paper_extract(bytes(k), mb)
+        assert c == v
+    assert masks == 3                                       # three 8-byte masks
+    allones = oracle.compress(np.frombuffer(mb, np.uint8)[None, :], m)
+    assert ck_ints(allones) == [2**56 - 1]
+
+
+# ------------------------------------------------------ Theorem 2
+@pytest.mark.parametrize("seed", range(6))
+def test_theorem2_compressed_order_equals_full_order(seed):
+    rng = np.random.default_rng(20 + seed)
+    W = int(rng.integers(1, 9))
+    keys = random_structured_keys(rng, 400, W, int(rng.integers(1, min(8 * W, 30))))
+    keys[rng.integers(0, 400, 50)] = keys[rng.integers(0, 400, 50)]     # duplicates
+    keys = keys[rng.permutation(400)]
+    perm_full = oracle.sort_rows(keys)
+    D = oracle.dmask(keys, perm_full)
+    for mask in (D, oracle.variant_mask(keys),
+                 D | mask_of(rng.choice(8 * W, 5), 8 * W)):
+        ck = oracle.compress(keys, mask)
+        assert list(oracle.sort_compressed(ck)) == list(perm_full)
+
+
+def test_theorem2_needs_every_dbit():
+    """Dropping any position of D breaks the order for some row arrangement."""
+    g, vals = load_fig2()
+    rows = ints_to_rows(vals, 12)
+    D = positions_of(oracle.dmask(rows), 16)
+    for drop in D:
+        m = mask_of([p for p in D if p != drop], 16)
+        broken = False
+        for order in itertools.permutations(range(len(vals))):
+            r = rows[list(order)]
+            if list(oracle.sort_compressed(oracle.compress(r, m))) != list(oracle.sort_rows(r)):
+                broken = True
+                break
+        assert broken
+
+
+# --------------------------------------- Sec. 4.3 rebuild step 1 / D-offset
+@pytest.mark.parametrize("seed", range(5))
+def test_refine_from_superset_equals_full_key_D(seed):
+    rng = np.random.default_rng(40 + seed)
+    W = int(rng.integers(2, 10))
+    keys = random_structured_keys(rng, 300, W, int(rng.integers(2, min(40, 8 * W))))
+    keys = keys[rng.permutation(300)]
+    perm = oracle.sort_rows(keys)
+    D = oracle.dmask(keys, perm)
+    for sup in (oracle.variant_mask(keys), D | mask_of(rng.choice(8 * W, 7), 8 * W), D):
+        ck = oracle.compress(keys, sup)
+        p2 = oracle.sort_compressed(ck)
+        assert list(oracle.refine(ck, p2, sup, 8 * W)) == list(D)
+
+
+# ------------------------------------------------------ Sec. 5.3 bulk load
+def test_btree_shape_closed_form():
+    for n in (1, 2, 63, 64, 65, 4096, 4097, 1_000_000, 10**7 + 3):
+        for f in (2, 3, 14, 64, 256):
+            lv = oracle.btree_shape(n, f)
+            m, expect = n, [n]
+            while m > f:
+                m = math.ceil(m / f)
+                expect.append(m)
+            assert lv == expect
+            if n > f:
+                assert len(lv) == math.ceil(math.log(math.ceil(n / f), f) - 1e-12) + 1
+    assert oracle.btree_shape(0, 64) == []
+    assert oracle.btree_shape(10**6, 64) == [10**6, 15625, 245, 4]
+
+
+@pytest.mark.parametrize("n,f", [(1, 4), (5, 4), (1000, 8), (4097, 64), (3000, 3)])
+def test_btree_entries(n, f):
+    rng = np.random.default_rng(n + f)
+    v = (rng.integers(0, 2**20, n, dtype=np.uint64) << np.uint64(30)) | np.uint64(7)
+    perm = oracle.sort_rows(v)
+    t = oracle.btree(v, perm, f)
+    sv = [int(v[i]) for i in perm]
+    # leaves: D-bit against the previous key, closed form on integers
+    assert [int(x) for x in t["leaf_dbit"]] == [0xFFFF] + [
+        (lambda d: 0xFFFF if d < 0 else d)(dbit_py(sv[i - 1], sv[i], 64)) for i in range(1, n)]
+    off = 0
+    for l, m in enumerate(t["levels"][1:], start=1):
+        hi = t["high"][off:off + m]
+        assert list(t["child"][off:off + m]) == list(range(m))
+        assert [int(h) for h in hi] == [min((e + 1) * f ** l, n) - 1 for e in range(m)]
+        for e in range(m):
+            d = int(t["dbit"][off + e])
+            if e == 0:
+                assert d == 0xFFFF
+            else:   # Lemma 1: min of the leaf D-bits over the covered range
+                rng_d = [int(x) for x in t["leaf_dbit"][int(hi[e - 1]) + 1:int(hi[e]) + 1]]
+                assert d == min(rng_d)
+        off += m
+
+
+# ------------------------------------------------------ generators sanity
+def test_generator_shapes():
+    keys, pos = synth.varying_bits_u64(20000, 7)
+    assert len(set(pos)) == 24
+    D = positions_of(oracle.dmask(keys), 64)
+    assert set(D) <= set(pos) and len(D) >= 20
+    u = synth.urls(2000, 3)
+    assert all(bytes(r).startswith(b"http://www.") for r in u)
+    d = synth.dna(2000, 4)
+    assert set(np.unique(d)) <= set(b"ACGT")
+    # 0x41,0x43,0x47,0x54: only bit positions 3, 5, 6 of each byte can distinguish
+    Dd = positions_of(oracle.dmask(d), 256)
+    assert set(p % 8 for p in Dd) <= {3, 5, 6}
