@@ -1,0 +1,380 @@
+"""Benchmark: keys/s sorted + indexed on one GB300, compressed key sort vs a
+full-key sort on the same kernels, with the HBM roofline fraction of the
+dominant kernel (the onesweep radix pass).
+
+A step is one index rebuild from stored DS-metadata (Sec. 5 of the paper):
+extract the compressed keys with the stored D-bitmap, radix-sort the
+(compressed key, row id) pairs, bulk-load the tree and recompute the D-bitmap.
+Inputs are resident in HBM when the timed region starts and are larger than
+L2 (no flush needed).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload urls64m|int1m|dna200m]
+
+Under torchrun (N > 1) every rank rebuilds its own replica of the workload
+(the path has no exchange step); value is the keys of all ranks over the
+slowest rank's time.  ``--impl reference`` times the CPU oracle on a bounded
+sample of the same workload (rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "keys/sec sorted+indexed (1 GB300) and % of HBM roofline, compressed vs full-key sort"
+FALLBACK_HBM_GBS = 6800.0
+SORT_SRC = os.path.join(ROOT, "paper_2009_11543_gb300", "csrc", "ck_sort.cu")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "onesweep_pass_traffic.json")
+
+WORKLOADS = {
+    # name: (description, n, generator, fanout, cpu sample rows)
+    "urls64m": ("64M 32-byte URL keys ('http://www.' + Zipf(1.1) name over 100k + '.com/' + 0-16 path chars), "
+                "fanout 64, compressed keys packed to 128 bits", 64 * 2**20, "urls", 64, 8_000_000),
+    "urls8m": ("8M 32-byte URL keys (the 64M workload's generator, first 8M rows), fanout 64; profiling size",
+               8 * 2**20, "urls", 64, 2_000_000),
+    "int1m": ("1M uint64 keys with 24 seeded varying bit positions, fanout 64", 1_000_000, "int", 64, 1_000_000),
+    "dna200m": ("200M 32-byte {A,C,G,T} keys, 20% with one of 65536 shared 24-char prefixes, fanout 256",
+                200_000_000, "dna", 256, 4_000_000),
+}
+
+
+def gen_keys(kind: str, n: int):
+    import synth
+    if kind == "urls":
+        return synth.urls(n, synth.BASE_SEED + 2)
+    if kind == "int":
+        return synth.varying_bits_u64(n, synth.BASE_SEED + 1)[0]
+    if kind == "dna":
+        return synth.dna(n, synth.BASE_SEED + 5)
+    raise ValueError(kind)
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def file_sha(path: str) -> str:
+    with open(path, "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
+def ncu_traffic(n: int):
+    """DRAM bytes per pass launch from the committed ncu summary, scaled to n
+    keys, if the pass kernel's source is unchanged since the capture."""
+    try:
+        with open(TRAFFIC_FILE) as f:
+            t = json.load(f)
+        if t.get("kernel_src_sha") != file_sha(SORT_SRC):
+            return None
+        return t["dram_bytes_per_launch"] * n / t["n"]
+    except Exception:
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples while the GPU is busy."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
+                                         stdout=self.file, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.file.flush()
+        self.file.seek(0)
+        rows = [l.strip().split(", ") for l in self.file.read().splitlines() if l.strip()]
+        os.unlink(self.file.name)
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            if len(r) < 9:
+                continue
+            try:
+                sm.append(float(r[1]))
+                smax = float(r[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, r[5:9]):
+                if v.strip().lower() == "active":
+                    reasons.add(nm)
+        busy = [s for s in sm if smax and s > 0.3 * smax] or sm
+        return {"sm_mhz": statistics.median(busy) if busy else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# --------------------------------------------------------------------- ours
+def run_ours(args, rank, world, local_rank):
+    import torch
+    from paper_2009_11543_gb300 import build as b
+    b.build()
+    from paper_2009_11543_gb300 import ck, metrics, pipeline
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    desc, n, kind, fanout, cpu_rows = WORKLOADS[args.workload]
+    keys_np = gen_keys(kind, n)
+    keys_host = torch.from_numpy(keys_np.view(np.int64) if keys_np.dtype == np.uint64 else keys_np).pin_memory()
+    keys = keys_host.to(dev)
+    key_bytes = keys_np.shape[1] if keys_np.ndim == 2 else keys_np.dtype.itemsize
+
+    # stored DS-metadata: the D-bitmap of a first build (untimed set-up)
+    dmask = pipeline.first_build_dmask(keys, digit_bits=args.digit_bits)
+    nbits = ck.popcount(dmask)
+    R = pipeline.Rebuild(keys, dmask, fanout=fanout, digit_bits=args.digit_bits)
+    F = pipeline.Rebuild(keys, pipeline.full_key_mask(8 * key_bytes), fanout=fanout, digit_bits=args.digit_bits)
+    passes = metrics.radix_passes(nbits, args.digit_bits)
+    fpasses = metrics.radix_passes(8 * key_bytes, args.digit_bits)
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        torch.cuda.synchronize()
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    def timed(fn, steps, warmup, pass_count):
+        for _ in range(warmup):
+            fn(None)
+        barrier()
+        ev = [[torch.cuda.Event(enable_timing=True) for _ in range(pass_count + 1)] for _ in range(steps)]
+        for row in ev:                   # torch creates an event on its first record
+            for e in row:
+                e.record(stream)
+        ph = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(steps)]
+        l0 = ck.ck_launch_count()
+        start = torch.cuda.Event(enable_timing=True)
+        end = torch.cuda.Event(enable_timing=True)
+        start.record(stream)
+        for s in range(steps):
+            fn((ph[s], ck.event_handles(ev[s])))
+        end.record(stream)
+        barrier()
+        launches = ck.ck_launch_count() - l0
+        total_ms = start.elapsed_time(end)
+        pass_ms = [ev[s][q].elapsed_time(ev[s][q + 1]) for s in range(steps) for q in range(pass_count)]
+        phase = [[ph[s][i].elapsed_time(ph[s][i + 1]) for i in range(3)] for s in range(steps)]
+        return total_ms, pass_ms, phase, launches
+
+    def step_fn(r):
+        def fn(hooks):
+            if hooks is None:
+                r.run()
+                return
+            ph, evh = hooks
+            ph[0].record(stream)
+            r.extract()
+            ph[1].record(stream)
+            ck.ck_sort(r.ck_in, None, r.ck_sorted, r.rid_sorted, r.n, r.K, r.nbits, r.ws, digit_bits=r.digit_bits,
+                       pass_events=evh)
+            ph[2].record(stream)
+            r.build()
+            ph[3].record(stream)
+        return fn
+
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    time.sleep(0.2)
+    total_ms, pass_ms, phase, launches = timed(step_fn(R), args.steps, args.warmup, passes)
+    f_total_ms, f_pass_ms, f_phase, _ = timed(step_fn(F), max(1, args.steps // 2), args.warmup, fpasses)
+
+    # end to end: host keys -> device, rebuild, sorted row ids -> host, every step
+    rid_host = torch.empty(n, dtype=torch.int32, pin_memory=True)
+
+    def e2e_step():
+        R.keys.copy_(keys_host, non_blocking=True)
+        R.run()
+        rid_host.copy_(R.rid_sorted[:n], non_blocking=True)
+
+    for _ in range(args.warmup):
+        e2e_step()
+    barrier()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        e2e_step()
+    e1.record(stream)
+    barrier()
+    e2e_ms = e0.elapsed_time(e1)
+    clk = clocks.stop()
+    status, detail = ck.ck_device_status()
+    if status != ck.CK_OK:
+        raise RuntimeError("device status %s (detail %d)" % (ck.ck_status_string(status), detail))
+
+    # max over ranks
+    times = np.array([total_ms, e2e_ms, f_total_ms], np.float64)
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.from_numpy(times)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        times = t.numpy()
+    total_ms, e2e_ms, f_total_ms = (float(x) for x in times)
+    if rank != 0:
+        return None
+
+    ms_step = total_ms / args.steps
+    f_ms_step = f_total_ms / max(1, args.steps // 2)
+    value = world * n / (ms_step / 1e3)
+    peak, peak_src = peaks()
+    avg_pass_ms = float(np.mean(pass_ms))
+    pb = metrics.pass_bytes(n, R.K)
+    achieved = pb / (avg_pass_ms / 1e3) / 1e9
+    traffic = ncu_traffic(n)
+    ph = np.mean(np.array(phase), axis=0)
+    fph = np.mean(np.array(f_phase), axis=0)
+    alg = metrics.extract_sort_alg_bytes(n, key_bytes, R.K, passes)
+    f_alg = metrics.extract_sort_alg_bytes(n, key_bytes, F.K, fpasses)
+    f_pass_gbs = metrics.pass_bytes(n, F.K) / (float(np.mean(f_pass_ms)) / 1e3) / 1e9
+    line = {
+        "metric": METRIC,
+        "value": value,
+        "unit": "keys/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": ms_step,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "u32",
+        "data": "synthetic (seeded generator standing in for the paper's URL tables)",
+        "config": {"workload": desc, "n": n, "key_bytes": key_bytes, "distinction_bits": nbits,
+                   "ck_words": R.K, "digit_bits": args.digit_bits, "radix_passes": passes, "fanout": fanout,
+                   "tree_levels": int(R.shape.levels), "l2": "inputs larger than L2 (no flush)",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "roofline": {"bound": "hbm", "kernel": "onesweep_pass_kernel<8>", "achieved": achieved, "peak": peak,
+                     "peak_source": peak_src, "unit": "GB/s", "frac": achieved / peak,
+                     "traffic": traffic, "alg_bytes_per_launch": pb, "avg_launch_ms": avg_pass_ms},
+        "phases_ms": {"extract": float(ph[0]), "sort": float(ph[1]), "build": float(ph[2])},
+        "extract_sort_roofline_frac": alg / ((ph[0] + ph[1]) / 1e3) / 1e9 / peak,
+        "full_key": {"value": world * n / (f_ms_step / 1e3), "unit": "keys/s", "ms_per_step": f_ms_step,
+                     "radix_passes": fpasses, "ck_words": F.K,
+                     "phases_ms": {"extract": float(fph[0]), "sort": float(fph[1]), "build": float(fph[2])},
+                     "pass_gbs": f_pass_gbs, "extract_sort_roofline_frac":
+                         f_alg / ((fph[0] + fph[1]) / 1e3) / 1e9 / peak},
+        "compressed_vs_full_speedup": f_ms_step / ms_step,
+        "compression_ratio": metrics.compression_ratio(8 * key_bytes, nbits) if nbits else None,
+        "e2e": {"value": world * n / (e2e_ms / args.steps / 1e3), "unit": "keys/s",
+                "h2d_bytes_per_step": int(keys_np.nbytes), "d2h_bytes_per_step": 4 * n},
+        "gpu_launches": int(launches),
+        "clocks": clk,
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(args.workload, dmask, cpu_rows)
+    return line
+
+
+# -------------------------------------------------------- oracle (CPU) leg
+def oracle_step(keys, dmask, fanout, key_bits):
+    """One rebuild of the sample by the CPU oracle: Compress, compressed key
+    sort, D refinement, bottom-up bulk load."""
+    import oracle
+    K = max(1, (oracle.popcount(dmask) + 31) // 32)
+    c = oracle.compress(keys, dmask, K)
+    perm = oracle.sort_compressed(c)
+    oracle.refine(c, perm, dmask, key_bits)
+    oracle.btree(keys, perm, fanout)
+
+
+def cpu_baseline(workload, dmask, rows):
+    desc, n, kind, fanout, _ = WORKLOADS[workload]
+    keys = gen_keys(kind, rows)          # the first rows of the same seeded column
+    kb = 8 * (keys.shape[1] if keys.ndim == 2 else keys.dtype.itemsize)
+    t = time.perf_counter()
+    oracle_step(keys, dmask, fanout, kb)
+    dt = time.perf_counter() - t
+    return {"value": rows / dt, "unit": "keys/s", "cores": 1, "kind": "oracle",
+            "sample": "first %d rows of the same seeded workload, one rebuild (compress, sort, refine, bulk load), "
+                      "single thread" % rows}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return None
+    import oracle
+    desc, n, kind, fanout, rows = WORKLOADS[args.workload]
+    rows = min(rows, n) if args.workload != "urls64m" else 2_000_000
+    keys = gen_keys(kind, rows)
+    kb = 8 * (keys.shape[1] if keys.ndim == 2 else keys.dtype.itemsize)
+    dmask = oracle.dmask(keys)           # the sample's stored D-bitmap (set-up, untimed)
+    for _ in range(args.warmup):
+        oracle_step(keys, dmask, fanout, kb)
+    t = time.perf_counter()
+    for _ in range(args.steps):
+        oracle_step(keys, dmask, fanout, kb)
+    dt = (time.perf_counter() - t) / args.steps
+    v = rows / dt
+    sample = "first %d rows of the same seeded workload per step, single thread" % rows
+    return {"metric": METRIC, "value": v, "unit": "keys/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "config": {"workload": desc, "n": n, "sample_rows": rows}, "impl": "reference",
+            "cpu_baseline": {"value": v, "unit": "keys/s", "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": v, "unit": "keys/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="urls64m", choices=sorted(WORKLOADS))
+    ap.add_argument("--digit-bits", type=int, default=8)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3) if args.impl == "ours" else args.warmup
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1 and args.impl == "ours":
+        import torch.distributed as dist
+        dist.init_process_group("gloo")
+    if args.impl == "reference":
+        line = run_reference(args, rank, world)
+    else:
+        line = run_ours(args, rank, world, local_rank)
+    if line is not None and rank == 0:
+        print(json.dumps(line))
+    if world > 1 and args.impl == "ours":
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

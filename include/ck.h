@@ -1,0 +1,246 @@
+/*
+ * ck.h -- C ABI of libck, the GB300 (sm_103a) hot path of the compressed key
+ * sort of Kwon et al., "Compressed Key Sort and Fast Index Reconstruction"
+ * (arXiv 2009.11543).
+ *
+ * The library turns a column of index keys into a bulk-loaded index tree:
+ *
+ *   ck_variant_bits      variant bitmap of the keys              (Sec. 4.2, 4.3)
+ *   ck_distinction_bits  D-bitmap of sorted keys                 (Sec. 3.1, Theorem 1)
+ *   ck_extract           Compress(key) for every row             (Sec. 3.2, 5.1)
+ *   ck_sort              stable LSD radix sort of (ck, row id)   (Sec. 3.2, 5.2)
+ *   ck_build_index       bottom-up bulk load + D refinement      (Sec. 4.3, 5.3)
+ *
+ * Conventions shared by every call:
+ *   - Bit position p of a key (0 = most significant bit of byte 0) is bit
+ *     (7 - p % 8) of byte p / 8 (Sec. 3.1).  Unsigned integer columns
+ *     (CK_KIND_U32 / CK_KIND_U64, native little-endian values) compare like
+ *     their big-endian bytes, so position 0 is the value's most significant bit.
+ *   - A bitmap over key positions (D-bitmap, variant bitmap) is an array of
+ *     ceil(key_bits / 64) uint64 words, most significant first: position p is
+ *     bit (63 - p % 64) of word p / 64.
+ *   - A compressed key of nbits bits is the unsigned integer whose most
+ *     significant bit is the key's bit at the first set position (Sec. 3.2),
+ *     right-aligned in ck_words uint32 words.  Compressed key columns are
+ *     word-major ("structure of arrays") with a padded leading dimension:
+ *     word k (k = 0 least significant) of row i is at ck[k * CK_LD(n) + i],
+ *     so a column occupies ck_words * CK_LD(n) uint32 and every word array
+ *     starts 256-byte aligned.  The padding entries are never read as keys.
+ *   - Row ids are uint32; n <= CK_MAX_ROWS.
+ *   - Every call is asynchronous on the given stream (NULL = the legacy default
+ *     stream) and allocates no device memory.  The caller owns every buffer.
+ *     Device pointers must come from cudaMalloc (or torch) on the current
+ *     device; HOST pointers are read before the call returns.
+ *   - Argument errors are returned synchronously.  Device-side failures (a
+ *     bounded wait that ran out) are recorded in a device status word that
+ *     ck_device_status() reads; no call ever traps the GPU.
+ */
+#ifndef CK_H_
+#define CK_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st* ck_stream; /* a cudaStream_t */
+
+typedef enum ck_status {
+    CK_OK = 0,
+    CK_EINVAL = 1,     /* an argument is out of range or a required pointer is NULL */
+    CK_ENOMEM = 2,     /* the caller's workspace is smaller than the size query says */
+    CK_ECUDA = 3,      /* a CUDA runtime call or kernel launch failed */
+    CK_EOVERFLOW = 4,  /* the D-bitmap has more set positions than ck_words words hold */
+    CK_ETIMEOUT = 5,   /* a bounded device-side wait ran out (see ck_device_status) */
+    CK_EVERIFY = 6     /* a verification pass failed; the exact fallback produced the result */
+} ck_status;
+
+enum { CK_KIND_BYTES = 0, CK_KIND_U32 = 1, CK_KIND_U64 = 2 };
+
+#define CK_MAX_ROWS ((1ull << 30) - 1) /* look-back words pack a 30-bit count */
+#define CK_MAX_KEY_BYTES 512u          /* 4096 key positions; D-bits fit uint16 */
+#define CK_NO_DBIT 0xFFFFu             /* "no distinction bit": first key or equal keys */
+#define CK_MAX_LEVELS 32u
+#define CK_LD(n) ((((uint64_t)(n)) + 63u) & ~(uint64_t)63u) /* leading dimension of ck columns */
+
+/* A key column in device memory.  CK_KIND_BYTES: binary-comparable byte
+ * strings (fixed-size strings as they are, varchar with its terminating NUL and
+ * zero padding, Sec. 4.1).  CK_KIND_U32 / CK_KIND_U64: key_bytes must be 4 / 8. */
+typedef struct ck_column {
+    const void* keys;    /* device, n * row_stride readable bytes; row r starts at
+                            (const char*)keys + r * row_stride */
+    uint64_t n;          /* number of rows, <= CK_MAX_ROWS */
+    uint32_t key_bytes;  /* W, 1 .. CK_MAX_KEY_BYTES */
+    uint32_t row_stride; /* bytes between rows, >= key_bytes */
+    uint32_t kind;       /* CK_KIND_* */
+} ck_column;
+
+/* ---------------------------------------------------------------------------
+ * ck_variant_bits -- the variant bitmap of Sec. 4.2: position p is set iff some
+ * row differs from the reference row at p (computed as in Sec. 4.3, DS-metadata
+ * recompute step 3: OR over all keys of key XOR reference key).
+ *   col       key column (device).
+ *   ref_row   row used as the reference key value (any row works, Sec. 4.2).
+ *   mask_out  device, ceil(8 * key_bytes / 64) words; overwritten.
+ * Errors: CK_EINVAL for a bad column or ref_row >= n (n > 0).  n == 0 zeroes
+ * the mask. */
+ck_status ck_variant_bits(const ck_column* col, uint64_t ref_row, uint64_t* mask_out, ck_stream stream);
+
+/* ---------------------------------------------------------------------------
+ * ck_distinction_bits -- the D-bitmap of Sec. 3.1 / Theorem 1:
+ * D = { D-bit(key_{i-1}, key_i) : 1 <= i < n, key_{i-1} != key_i } over the
+ * rows in sorted order, each D-bit the most significant differing position of
+ * an adjacent pair.
+ *   col       key column (device), rows in ascending key order unless order
+ *             is given.
+ *   order     device, n uint32 row ids listing the rows in ascending order, or
+ *             NULL when the rows are already stored in order.
+ *   mask_out  device, ceil(8 * key_bytes / 64) words; overwritten.
+ * The result is exact only for sorted input; on unsorted input it is the set
+ * of adjacent-pair D-bits of the given order.  Errors: CK_EINVAL.  An order
+ * entry >= n is skipped and recorded as CK_EINVAL in the device status word. */
+ck_status ck_distinction_bits(const ck_column* col, const uint32_t* order, uint64_t* mask_out,
+                              ck_stream stream);
+
+/* ---------------------------------------------------------------------------
+ * ck_extract -- Compress(key) of Sec. 3.2 for every row: the concatenation of
+ * the key's bits at the set positions of the (extended) D-bitmap, in position
+ * order (the paper extracts with 8-byte masks and PEXT, Sec. 5.1; any gather
+ * with the same bits is equivalent).
+ *   col       key column (device).
+ *   dmask     HOST, ceil(8 * key_bytes / 64) words: the D-bitmap, or any
+ *             superset of it (Sec. 3.2, extended distinction bit positions).
+ *   ck_words  uint32 words per compressed key, >= ceil(popcount(dmask) / 32).
+ *   ck_out    device, ck_words * n uint32, word-major; fully overwritten.
+ * Errors: CK_EINVAL; CK_EOVERFLOW when popcount(dmask) > 32 * ck_words. */
+ck_status ck_extract(const ck_column* col, const uint64_t* dmask, uint32_t ck_words, uint32_t* ck_out,
+                     ck_stream stream);
+
+/* ---------------------------------------------------------------------------
+ * ck_sort -- stable least-significant-digit radix sort of the pairs
+ * (compressed key, row id) by compressed key (the sort step of Sec. 5, done
+ * here as a radix sort rather than the paper's comparison sort).  Equal keys
+ * keep their input order, so with rid_in = NULL (row ids 0..n-1) ties break by
+ * row id, and by Theorem 2 the output order is the sorted order of the full
+ * keys.  One onesweep pass per digit of the low nbits bits.
+ *   ck_in     device, ck_words * n, word-major; read only.
+ *   rid_in    device, n row ids, or NULL for 0..n-1; read only.
+ *   ck_out    device, ck_words * n; may equal ck_in (an extra copy may run).
+ *   rid_out   device, n; may equal rid_in.
+ *   nbits     significant low bits of the keys, <= 32 * ck_words; higher bits
+ *             must be zero.  nbits == 0 copies the input.
+ *   opts      NULL for defaults.
+ *   ws        device workspace of at least ck_sort_workspace_bytes() bytes,
+ *             256-byte aligned; its contents on entry do not matter.
+ * Errors: CK_EINVAL, CK_ENOMEM (ws too small).  A look-back wait that runs
+ * out records CK_ETIMEOUT in the device status word; the output is then
+ * undefined but every access stays in bounds. */
+typedef struct ck_sort_opts {
+    uint32_t digit_bits; /* radix digit width, 4 .. 11; 0 = 8 */
+    uint32_t spin_limit; /* polls per look-back wait before giving up; 0 = default (~1 s) */
+    uint32_t inject;     /* test-only fault injection (CK_INJECT_*); 0 in production */
+    uint32_t reserved;   /* must be 0 */
+    void* pass_events;   /* optional profiling hook: cudaEvent_t[passes + 1]; event 0 is
+                            recorded on the stream before the first digit pass and event
+                            p + 1 after pass p (passes = ceil(nbits / digit_bits)).  NULL
+                            records nothing. */
+} ck_sort_opts;
+
+/* The first tile of the first pass never publishes its look-back entries, so
+ * the second tile's wait runs out: exercises the CK_ETIMEOUT path without any
+ * GPU fault. */
+#define CK_INJECT_STALL_FIRST_TILE 1u
+
+size_t ck_sort_workspace_bytes(uint64_t n, uint32_t ck_words, uint32_t nbits, const ck_sort_opts* opts);
+
+ck_status ck_sort(const uint32_t* ck_in, const uint32_t* rid_in, uint32_t* ck_out, uint32_t* rid_out,
+                  uint64_t n, uint32_t ck_words, uint32_t nbits, const ck_sort_opts* opts, void* ws,
+                  size_t ws_bytes, ck_stream stream);
+
+/* ---------------------------------------------------------------------------
+ * Index tree (Sec. 4.2 structure, Sec. 5.3 bottom-up build).  Canonical
+ * layout: each node holds f = max(1, floor(fanout * fill)) consecutive entries
+ * (the last node of a level may hold fewer).  Level 0 has one entry per key in
+ * sorted order; level l+1 has one entry per node of level l; the first level
+ * with at most f entries is the root.  Node j of any level holds entries
+ * [j*f, min((j+1)*f, m)), m the level's entry count.
+ *
+ * ck_btree_plan fills the shape (host only) so that the caller can allocate
+ * the arrays of ck_btree.  Errors: CK_EINVAL for fanout * fill < 2 with n > 1,
+ * n > CK_MAX_ROWS, or a height above CK_MAX_LEVELS. */
+typedef struct ck_btree_shape {
+    uint32_t levels;           /* 0 when n == 0 */
+    uint32_t entries_per_node; /* f */
+    uint64_t n;
+    uint64_t level_entries[CK_MAX_LEVELS]; /* entries at level l; [0] = n */
+    uint64_t level_nodes[CK_MAX_LEVELS];   /* ceil(level_entries[l] / f) */
+    uint64_t inner_offset[CK_MAX_LEVELS];  /* start of level l (l >= 1) in the inner arrays */
+    uint64_t inner_entries;                /* sum of level_entries[1 .. levels-1] */
+} ck_btree_shape;
+
+ck_status ck_btree_plan(uint64_t n, uint32_t fanout, float fill, ck_btree_shape* shape);
+
+/* Caller-allocated device arrays (sizes from ck_btree_plan).  Leaf entry i:
+ * the record id and the full-key D-bit against the previous key (Sec. 4.2;
+ * computed through D-offset, Sec. 5.3).  Leaf header j: the sorted index of
+ * the node's highest key.  Inner entry (levels >= 1, concatenated level 1
+ * first): the child node, the sorted index, record id and compressed key of
+ * the highest key under the child, and that key's D-bit against the previous
+ * entry's highest key at the same level (CK_NO_DBIT for the level's first
+ * entry or equal keys). */
+typedef struct ck_btree {
+    ck_btree_shape shape;     /* written by ck_build_index */
+    uint32_t* leaf_rid;       /* [n] */
+    uint16_t* leaf_dbit;      /* [n] */
+    uint32_t* leaf_high;      /* [level_nodes[0]] */
+    uint32_t* inner_child;    /* [inner_entries] */
+    uint32_t* inner_high;     /* [inner_entries] */
+    uint32_t* inner_high_rid; /* [inner_entries] */
+    uint32_t* inner_high_ck;  /* [inner_entries * ck_words], entry-major, least significant word first */
+    uint16_t* inner_dbit;     /* [inner_entries] */
+} ck_btree;
+
+/* ---------------------------------------------------------------------------
+ * ck_build_index -- bulk-loads the tree from the sorted pairs and, in the same
+ * pass over the leaves, recomputes the D-bitmap (Sec. 4.3 rebuild, step 1):
+ * refined = { D-offset[D-bit(Compress(key_{i-1}), Compress(key_i))] }, where
+ * D-offset[q] is the position of the (q+1)-st set bit of dmask (Sec. 5.3).
+ *   sorted_ck, sorted_rid  device, as produced by ck_sort (word-major ck).
+ *   dmask     HOST, ceil(key_bits / 64) words: the bitmap used by ck_extract.
+ *   key_bits  8 * key_bytes of the column.
+ *   tree      its shape is recomputed and written; its arrays are written.
+ *   refined_mask  device, ceil(key_bits / 64) words, or NULL to skip.
+ * Errors: CK_EINVAL, CK_EOVERFLOW (popcount(dmask) > 32 * ck_words). */
+ck_status ck_build_index(const uint32_t* sorted_ck, const uint32_t* sorted_rid, uint64_t n, uint32_t ck_words,
+                         const uint64_t* dmask, uint32_t key_bits, uint32_t fanout, float fill, ck_btree* tree,
+                         uint64_t* refined_mask, ck_stream stream);
+
+/* ---------------------------------------------------------------------------
+ * Device status.  ck_device_status synchronises the device, returns the first
+ * device-side error recorded since the last clear (CK_OK if none) and, if
+ * detail is not NULL, a call-specific detail word (for CK_ETIMEOUT: the pass
+ * in bits 0..15 and the waiting tile in bits 16..47).  The status is one word
+ * per device shared by all streams. */
+ck_status ck_device_status(uint64_t* detail);
+ck_status ck_clear_device_status(void);
+
+/* Static name of a status code. */
+const char* ck_status_string(ck_status status);
+
+/* Number of kernels this library launched in the calling process (all calls,
+ * all devices), for launch accounting in benchmarks. */
+uint64_t ck_launch_count(void);
+
+/* Host-side evaluation of the per-word bit gather that ck_extract runs on the
+ * GPU: the bits of x at the set bits of mask, in order, packed into the low
+ * popcount(mask) bits (the PEXT of Sec. 5.1 on one 32-bit big-endian word).
+ * For host tests of the extraction plan; touches no device. */
+uint32_t ck_compress_word_host(uint32_t x, uint32_t mask);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CK_H_ */

@@ -1,0 +1,287 @@
+"""Thin Python binding of libck (include/ck.h), argument marshalling only.
+
+Every function here has the name of the C entry point it calls and does no
+arithmetic of the method: device buffers are torch CUDA tensors (uint32 data
+is carried in int32 tensors and uint64 bitmaps in int64 tensors, bit for bit),
+host bitmaps are numpy uint64 arrays.  There is no CPU fallback: if libck.so
+is missing the import fails with an error that says how to build it.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libck.so")
+
+CK_OK, CK_EINVAL, CK_ENOMEM, CK_ECUDA, CK_EOVERFLOW, CK_ETIMEOUT, CK_EVERIFY = range(7)
+CK_KIND_BYTES, CK_KIND_U32, CK_KIND_U64 = 0, 1, 2
+CK_MAX_ROWS = (1 << 30) - 1
+CK_MAX_KEY_BYTES = 512
+CK_NO_DBIT = 0xFFFF
+CK_MAX_LEVELS = 32
+CK_INJECT_STALL_FIRST_TILE = 1
+
+EXPORTED = ["ck_variant_bits", "ck_distinction_bits", "ck_extract", "ck_sort_workspace_bytes", "ck_sort",
+            "ck_btree_plan", "ck_build_index", "ck_device_status", "ck_clear_device_status",
+            "ck_status_string", "ck_launch_count", "ck_compress_word_host"]
+
+
+class CkError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        super().__init__("%s failed: %s" % (what, _lib().ck_status_string(status).decode()))
+        self.status = status
+
+
+class ck_column(ctypes.Structure):
+    _fields_ = [("keys", ctypes.c_void_p), ("n", ctypes.c_uint64), ("key_bytes", ctypes.c_uint32),
+                ("row_stride", ctypes.c_uint32), ("kind", ctypes.c_uint32)]
+
+
+class ck_sort_opts(ctypes.Structure):
+    _fields_ = [("digit_bits", ctypes.c_uint32), ("spin_limit", ctypes.c_uint32), ("inject", ctypes.c_uint32),
+                ("reserved", ctypes.c_uint32), ("pass_events", ctypes.c_void_p)]
+
+
+class ck_btree_shape(ctypes.Structure):
+    _fields_ = [("levels", ctypes.c_uint32), ("entries_per_node", ctypes.c_uint32), ("n", ctypes.c_uint64),
+                ("level_entries", ctypes.c_uint64 * CK_MAX_LEVELS), ("level_nodes", ctypes.c_uint64 * CK_MAX_LEVELS),
+                ("inner_offset", ctypes.c_uint64 * CK_MAX_LEVELS), ("inner_entries", ctypes.c_uint64)]
+
+
+class ck_btree(ctypes.Structure):
+    _fields_ = [("shape", ck_btree_shape), ("leaf_rid", ctypes.c_void_p), ("leaf_dbit", ctypes.c_void_p),
+                ("leaf_high", ctypes.c_void_p), ("inner_child", ctypes.c_void_p), ("inner_high", ctypes.c_void_p),
+                ("inner_high_rid", ctypes.c_void_p), ("inner_high_ck", ctypes.c_void_p),
+                ("inner_dbit", ctypes.c_void_p)]
+
+
+_LIB = None
+
+
+def _lib():
+    global _LIB
+    if _LIB is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libck.so is not built (%s); run __graft_entry__.build() or "
+                               "python -m paper_2009_11543_gb300.build" % LIB_PATH)
+        lib = ctypes.CDLL(LIB_PATH)
+        P, U64, U32, I = ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int
+        CP = ctypes.POINTER(ck_column)
+        lib.ck_variant_bits.argtypes = [CP, U64, P, P]
+        lib.ck_distinction_bits.argtypes = [CP, P, P, P]
+        lib.ck_extract.argtypes = [CP, P, U32, P, P]
+        lib.ck_sort_workspace_bytes.argtypes = [U64, U32, U32, ctypes.POINTER(ck_sort_opts)]
+        lib.ck_sort_workspace_bytes.restype = ctypes.c_size_t
+        lib.ck_sort.argtypes = [P, P, P, P, U64, U32, U32, ctypes.POINTER(ck_sort_opts), P, ctypes.c_size_t, P]
+        lib.ck_btree_plan.argtypes = [U64, U32, ctypes.c_float, ctypes.POINTER(ck_btree_shape)]
+        lib.ck_build_index.argtypes = [P, P, U64, U32, P, U32, U32, ctypes.c_float, ctypes.POINTER(ck_btree), P, P]
+        lib.ck_device_status.argtypes = [ctypes.POINTER(U64)]
+        lib.ck_status_string.argtypes = [I]
+        lib.ck_status_string.restype = ctypes.c_char_p
+        lib.ck_launch_count.restype = U64
+        lib.ck_compress_word_host.argtypes = [U32, U32]
+        lib.ck_compress_word_host.restype = U32
+        for name in EXPORTED:
+            if name not in ("ck_sort_workspace_bytes", "ck_status_string", "ck_launch_count",
+                            "ck_compress_word_host"):
+                getattr(lib, name).restype = I
+        _LIB = lib
+    return _LIB
+
+
+def lib_path() -> str:
+    return LIB_PATH
+
+
+def _check(status: int, what: str) -> None:
+    if status != CK_OK:
+        raise CkError(status, what)
+
+
+def _stream(stream):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if isinstance(t, np.ndarray):
+        return ctypes.c_void_p(t.ctypes.data)
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def column(keys: torch.Tensor, kind: int | None = None) -> ck_column:
+    """ck_column over a CUDA tensor: [n, W] uint8 rows (bytes), or a 1-D
+    4-byte (uint32) / 8-byte (uint64) integer column."""
+    if keys.dim() == 2:
+        if keys.element_size() != 1:
+            raise ValueError("2-D key columns must be uint8 rows")
+        n, W = keys.shape
+        stride = keys.stride(0)
+        k = CK_KIND_BYTES if kind is None else kind
+        if keys.stride(1) != 1:
+            raise ValueError("key rows must be contiguous")
+    elif keys.dim() == 1:
+        n = keys.shape[0]
+        W = keys.element_size()
+        stride = W * keys.stride(0)
+        k = kind if kind is not None else {4: CK_KIND_U32, 8: CK_KIND_U64}[W]
+    else:
+        raise ValueError("keys must be 1-D or 2-D")
+    return ck_column(keys.data_ptr(), n, W, stride, k)
+
+
+def mask_words(key_bits: int) -> int:
+    return (key_bits + 63) // 64
+
+
+def CK_LD(n: int) -> int:
+    """Leading dimension of word-major compressed key columns (include/ck.h)."""
+    return (n + 63) & ~63
+
+
+def ck_buffer(ck_words: int, n: int, device) -> torch.Tensor:
+    """Device storage for a word-major compressed key column: [ck_words, CK_LD(n)]."""
+    return torch.empty((ck_words, max(CK_LD(n), 64)), dtype=torch.int32, device=device)
+
+
+def ck_variant_bits(keys: torch.Tensor, ref_row: int = 0, out: torch.Tensor | None = None, kind=None, stream=None):
+    col = column(keys, kind)
+    if out is None:
+        out = torch.empty(mask_words(8 * col.key_bytes), dtype=torch.int64, device=keys.device)
+    _check(_lib().ck_variant_bits(ctypes.byref(col), ref_row, _ptr(out), _stream(stream)), "ck_variant_bits")
+    return out
+
+
+def ck_distinction_bits(keys: torch.Tensor, order: torch.Tensor | None = None, out: torch.Tensor | None = None,
+                        kind=None, stream=None):
+    col = column(keys, kind)
+    if out is None:
+        out = torch.empty(mask_words(8 * col.key_bytes), dtype=torch.int64, device=keys.device)
+    _check(_lib().ck_distinction_bits(ctypes.byref(col), _ptr(order), _ptr(out), _stream(stream)),
+           "ck_distinction_bits")
+    return out
+
+
+def popcount(mask: np.ndarray) -> int:
+    return int(sum(bin(int(w)).count("1") for w in np.asarray(mask, np.uint64)))
+
+
+def words_for(nbits: int) -> int:
+    return max(1, (nbits + 31) // 32)
+
+
+def ck_extract(keys: torch.Tensor, dmask: np.ndarray, ck_words: int | None = None, out: torch.Tensor | None = None,
+               kind=None, stream=None):
+    col = column(keys, kind)
+    m = np.ascontiguousarray(np.asarray(dmask, np.uint64))
+    if ck_words is None:
+        ck_words = words_for(popcount(m))
+    if out is None:
+        out = ck_buffer(ck_words, col.n, keys.device)
+    _check(_lib().ck_extract(ctypes.byref(col), _ptr(m), ck_words, _ptr(out), _stream(stream)), "ck_extract")
+    return out
+
+
+def _opts(digit_bits=0, spin_limit=0, inject=0, pass_events=None):
+    return ck_sort_opts(digit_bits, spin_limit, inject, 0, pass_events)
+
+
+def event_handles(events) -> ctypes.Array:
+    """cudaEvent_t array for the pass_events hook, from torch.cuda.Event objects."""
+    arr = (ctypes.c_void_p * len(events))()
+    for i, e in enumerate(events):
+        arr[i] = e.cuda_event
+    return arr
+
+
+def ck_sort_workspace_bytes(n: int, ck_words: int, nbits: int, digit_bits: int = 0) -> int:
+    o = _opts(digit_bits)
+    return int(_lib().ck_sort_workspace_bytes(n, ck_words, nbits, ctypes.byref(o)))
+
+
+def ck_sort(ck_in: torch.Tensor, rid_in: torch.Tensor | None, ck_out: torch.Tensor, rid_out: torch.Tensor, n: int,
+            ck_words: int, nbits: int, ws: torch.Tensor, digit_bits: int = 0, spin_limit: int = 0, inject: int = 0,
+            pass_events=None, stream=None) -> None:
+    o = _opts(digit_bits, spin_limit, inject,
+              ctypes.cast(pass_events, ctypes.c_void_p) if pass_events is not None else None)
+    _check(_lib().ck_sort(_ptr(ck_in), _ptr(rid_in), _ptr(ck_out), _ptr(rid_out), n, ck_words, nbits,
+                          ctypes.byref(o), _ptr(ws), ws.numel() * ws.element_size(), _stream(stream)), "ck_sort")
+
+
+def ck_btree_plan(n: int, fanout: int, fill: float = 1.0) -> ck_btree_shape:
+    s = ck_btree_shape()
+    _check(_lib().ck_btree_plan(n, fanout, fill, ctypes.byref(s)), "ck_btree_plan")
+    return s
+
+
+def alloc_btree(shape: ck_btree_shape, ck_words: int, device) -> dict:
+    """Device arrays for a tree of the given shape (torch allocations)."""
+    n = int(shape.n)
+    ni = int(shape.inner_entries)
+    nodes0 = int(shape.level_nodes[0]) if shape.levels else 0
+
+    def e(sz, dt):
+        return torch.empty(max(sz, 1), dtype=dt, device=device)
+    return {"leaf_rid": e(n, torch.int32), "leaf_dbit": e(n, torch.int16), "leaf_high": e(nodes0, torch.int32),
+            "inner_child": e(ni, torch.int32), "inner_high": e(ni, torch.int32), "inner_high_rid": e(ni, torch.int32),
+            "inner_high_ck": e(ni * ck_words, torch.int32), "inner_dbit": e(ni, torch.int16)}
+
+
+def ck_build_index(sorted_ck: torch.Tensor, sorted_rid: torch.Tensor, n: int, ck_words: int, dmask: np.ndarray,
+                   key_bits: int, fanout: int, fill: float = 1.0, arrays: dict | None = None,
+                   refined_out: torch.Tensor | None = None, stream=None):
+    """Returns (shape, arrays); arrays are allocated when not given."""
+    shape = ck_btree_plan(n, fanout, fill)
+    if arrays is None:
+        arrays = alloc_btree(shape, ck_words, sorted_rid.device if sorted_rid is not None else "cuda")
+    t = ck_btree()
+    for name, tensor in arrays.items():
+        setattr(t, name, tensor.data_ptr())
+    m = np.ascontiguousarray(np.asarray(dmask, np.uint64))
+    _check(_lib().ck_build_index(_ptr(sorted_ck), _ptr(sorted_rid), n, ck_words, _ptr(m), key_bits, fanout, fill,
+                                 ctypes.byref(t), _ptr(refined_out), _stream(stream)), "ck_build_index")
+    return t.shape, arrays
+
+
+def ck_device_status() -> tuple[int, int]:
+    d = ctypes.c_uint64(0)
+    s = _lib().ck_device_status(ctypes.byref(d))
+    return int(s), int(d.value)
+
+
+def ck_clear_device_status() -> None:
+    _check(_lib().ck_clear_device_status(), "ck_clear_device_status")
+
+
+def ck_status_string(status: int) -> str:
+    return _lib().ck_status_string(status).decode()
+
+
+def ck_launch_count() -> int:
+    return int(_lib().ck_launch_count())
+
+
+def ck_compress_word_host(x: int, mask: int) -> int:
+    return int(_lib().ck_compress_word_host(x & 0xFFFFFFFF, mask & 0xFFFFFFFF))
+
+
+def mask_to_host(mask: torch.Tensor) -> np.ndarray:
+    """Device bitmap (int64 storage) -> numpy uint64 words."""
+    return mask.cpu().numpy().view(np.uint64)
+
+
+def u32(t: torch.Tensor) -> np.ndarray:
+    """Device uint32 data (int32 storage) -> numpy uint32."""
+    return t.cpu().numpy().view(np.uint32)
+
+
+def ck_rows(ck_dev: torch.Tensor, n: int) -> np.ndarray:
+    """Word-major device column [K, CK_LD(n)] -> row-major numpy [n, K] uint32."""
+    return np.ascontiguousarray(u32(ck_dev)[:, :n].T)

@@ -1,0 +1,207 @@
+// ck_internal.cuh -- shared device helpers and host launch declarations of libck.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "ck.h"
+
+namespace ck {
+
+constexpr uint32_t kFull = 0xFFFFFFFFu;
+constexpr uint32_t kMaxKeyWords = CK_MAX_KEY_BYTES / 4;  // 32-bit key words
+constexpr uint32_t kMaxMaskWords = CK_MAX_KEY_BYTES / 8;  // uint64 bitmap words
+constexpr uint32_t kMaxKeyBits = CK_MAX_KEY_BYTES * 8;
+
+// ---------------------------------------------------------------- status word
+// Keeps the first error: code in bits 0..7, detail above.
+__device__ __forceinline__ void report(unsigned long long* status, uint32_t code, uint64_t detail) {
+    atomicCAS(status, 0ull, (unsigned long long)code | ((unsigned long long)detail << 8));
+}
+
+__device__ __forceinline__ uint32_t ld_relaxed(const uint32_t* p) {
+    uint32_t v;
+    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_relaxed(uint32_t* p, uint32_t v) {
+    asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// ------------------------------------------------- TMA bulk copy + mbarrier
+// One-dimensional bulk copies (global -> shared) signal an mbarrier with the
+// bytes they deliver; consumers poll the barrier's phase with a bounded loop.
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async_smem() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// The calling thread arrives once on bar and announces `bytes` more bytes,
+// then starts the copy of `bytes` (a multiple of 16; both addresses 16-byte
+// aligned) that completes them.
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_addr(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_addr(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Waits for the phase with the given parity to complete; gives up after
+// `limit` polls and returns false (the caller records the timeout).
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint32_t limit) {
+    for (uint32_t i = 0;; ++i) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if (i >= limit) return false;
+        if (i > 8) __nanosleep(32);
+    }
+}
+
+// ------------------------------------------------------------- key loading
+// A key is presented as a sequence of 32-bit words in big-endian bit order:
+// word w holds key positions [32w, 32w + 32), position 32w in bit 31.
+//   BYTES: word w = bytes 4w..4w+3 of the row, byte 4w most significant;
+//   U32:   word 0 = the value;
+//   U64:   word 0 = high half, word 1 = low half of the value.
+// Bytes at or past key_bytes read as zero.  VEC is the load width in bytes
+// (16, 8, 4 or 1), chosen by the host so that every vector load stays inside
+// the row's stride.
+struct KeyDesc {
+    const unsigned char* base;
+    uint64_t stride;
+    uint32_t key_bytes;
+    uint32_t kind;
+    uint32_t nwords;      // ceil(key_bytes / 4)
+    uint32_t tail_mask;   // valid bits of the last word (big-endian order)
+};
+
+__device__ __forceinline__ uint32_t bswap32(uint32_t x) { return __byte_perm(x, 0, 0x0123); }
+
+// Loads 16 bytes worth of words starting at word 4c of row r.  Words past the
+// key read 0.  Only the word indices [4c, 4c+4) are produced.
+template <int VEC>
+__device__ __forceinline__ void load_chunk_row(const KeyDesc& k, const unsigned char* row, uint32_t c,
+                                               uint32_t (&w)[4]);
+
+template <int VEC>
+__device__ __forceinline__ void load_chunk(const KeyDesc& k, uint64_t r, uint32_t c, uint32_t (&w)[4]) {
+    load_chunk_row<VEC>(k, k.base + r * k.stride, c, w);
+}
+
+// Same, for a row that starts at `row` (global or shared memory).
+template <int VEC>
+__device__ __forceinline__ void load_chunk_row(const KeyDesc& k, const unsigned char* row, uint32_t c,
+                                               uint32_t (&w)[4]) {
+    if (k.kind == CK_KIND_U64) {            // 8-byte value; chunk 0 only
+        uint2 v = *reinterpret_cast<const uint2*>(row);
+        w[0] = v.y; w[1] = v.x; w[2] = 0; w[3] = 0;
+        return;
+    }
+    if (k.kind == CK_KIND_U32) {
+        w[0] = *reinterpret_cast<const uint32_t*>(row); w[1] = 0; w[2] = 0; w[3] = 0;
+        return;
+    }
+    const uint32_t first = 4 * c;
+    if (VEC == 16) {
+        uint4 v = *reinterpret_cast<const uint4*>(row + 16 * c);
+        w[0] = bswap32(v.x); w[1] = bswap32(v.y); w[2] = bswap32(v.z); w[3] = bswap32(v.w);
+    } else if (VEC == 8) {
+        uint2 a = *reinterpret_cast<const uint2*>(row + 16 * c);
+        uint2 b = (first + 2 < k.nwords) ? *reinterpret_cast<const uint2*>(row + 16 * c + 8) : make_uint2(0, 0);
+        w[0] = bswap32(a.x); w[1] = bswap32(a.y); w[2] = bswap32(b.x); w[3] = bswap32(b.y);
+    } else if (VEC == 4) {
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+            w[i] = (first + i < k.nwords) ? bswap32(*reinterpret_cast<const uint32_t*>(row + 16 * c + 4 * i)) : 0u;
+    } else {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            uint32_t x = 0;
+#pragma unroll
+            for (int b = 0; b < 4; ++b) {
+                uint32_t byte = 16 * c + 4 * i + b;
+                x = (x << 8) | (byte < k.key_bytes ? (uint32_t)row[byte] : 0u);
+            }
+            w[i] = x;
+        }
+    }
+    // zero the bytes past key_bytes inside the last word
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+        if (first + i == k.nwords - 1) w[i] &= k.tail_mask;
+        else if (first + i >= k.nwords) w[i] = 0;
+}
+
+}  // namespace ck
+
+// ------------------------------------------------------------ host helpers
+namespace ck {
+int num_sms();
+unsigned long long* status_ptr();     // device address of the status word (current device)
+void count_launch(uint32_t k = 1);
+bool make_key_desc(const ck_column* col, KeyDesc* d, int* vec);
+
+// launchers (each returns a CUDA error code of the launch)
+cudaError_t launch_variant(const KeyDesc& k, int vec, uint64_t n, uint64_t ref_row, uint64_t* mask_out,
+                           cudaStream_t s);
+cudaError_t launch_dbits(const KeyDesc& k, int vec, uint64_t n, const uint32_t* order, uint64_t* mask_out,
+                         cudaStream_t s);
+
+struct ExtractPlan {
+    uint32_t first_word, last_word;  // words with a non-zero mask
+    uint32_t K;                      // output words
+    uint32_t lead_zero_words;        // whole zero words at the top of the output
+    uint32_t pad_bits;               // zero bits at the top of the first non-zero output word
+    uint32_t mask[kMaxKeyWords];     // per key word, big-endian bit order
+    uint32_t mv[5][kMaxKeyWords];    // move masks of the compress network
+    uint8_t pc[kMaxKeyWords];        // popcount of mask[w]
+};
+cudaError_t launch_extract(const KeyDesc& k, int vec, uint64_t n, uint64_t ld, const ExtractPlan& plan,
+                           uint32_t* ck_out, cudaStream_t s);
+constexpr uint32_t kDefaultSpin = 1u << 22;  // polls before a device wait gives up
+
+struct SortPlan {
+    uint32_t digit_bits, passes, tile, tiles, K;
+    size_t off_hist, off_counter, off_lookback, off_alt_ck, off_alt_rid, total;
+};
+bool make_sort_plan(uint64_t n, uint32_t K, uint32_t nbits, uint32_t digit_bits, SortPlan* p);
+cudaError_t run_sort(const SortPlan& p, const uint32_t* ck_in, const uint32_t* rid_in, uint32_t* ck_out,
+                     uint32_t* rid_out, uint64_t n, uint32_t nbits, uint32_t spin_limit, uint32_t inject,
+                     cudaEvent_t* pass_events, unsigned char* ws, cudaStream_t s);
+
+struct BtreeArgs {
+    const uint32_t* ck;  // word-major, K words, leading dimension ld
+    uint64_t ld;
+    const uint32_t* rid;
+    uint64_t n;
+    uint32_t K, nbits, key_bits, f;
+    uint64_t dmask[kMaxMaskWords];
+};
+cudaError_t launch_btree(const BtreeArgs& a, const ck_btree_shape& shape, ck_btree* t, uint64_t* refined,
+                         cudaStream_t s);
+}  // namespace ck

@@ -1,0 +1,314 @@
+// ck_scan.cu -- kernels that stream the key column once:
+//   variant_kernel  variant bitmap (Sec. 4.2 / 4.3 step 3)
+//   dbits_kernel    D-bitmap of adjacent sorted keys (Sec. 3.1, Theorem 1)
+//   extract_kernel  Compress(key) (Sec. 3.2 / 5.1) by a per-word compress network
+//
+// One thread per row, grid-stride over rows.  Rows are read with the widest
+// vector load the host found safe (16/8/4/1 bytes); a warp's loads of one chunk
+// cover contiguous rows, so every DRAM sector of the column is fetched once.
+// Bitmaps are accumulated in shared memory (one atomicOr per distinct position
+// per warp) and merged into the global bitmap once per block.
+#include "ck_internal.cuh"
+
+namespace ck {
+
+// Block-level merge of a shared bitmap (32-bit words, big-endian bit order)
+// into the global uint64 bitmap (most significant first).
+__device__ __forceinline__ void merge_bitmap(const uint32_t* sm, uint32_t nwords32, uint64_t* out) {
+    for (uint32_t q = threadIdx.x; 2 * q < nwords32; q += blockDim.x) {
+        uint64_t hi = sm[2 * q], lo = (2 * q + 1 < nwords32) ? sm[2 * q + 1] : 0u;
+        uint64_t v = (hi << 32) | lo;
+        if (v) atomicOr(reinterpret_cast<unsigned long long*>(out + q), (unsigned long long)v);
+    }
+}
+
+// Records position p (or nothing for p < 0) in the shared bitmap; the warp's
+// lanes agree on equal positions first so that each distinct position costs
+// one shared atomic.
+__device__ __forceinline__ void warp_mark(uint32_t* sm, int32_t p) {
+    const uint32_t peers = __match_any_sync(kFull, p);
+    const uint32_t lane = threadIdx.x & 31;
+    if (p >= 0 && (__ffs(peers) - 1) == (int)lane) atomicOr(&sm[p >> 5], 0x80000000u >> (p & 31));
+}
+
+// ------------------------------------------------------------------ variant
+template <int VEC>
+__global__ void __launch_bounds__(256) variant_kernel(const KeyDesc k, uint64_t n, uint64_t ref_row,
+                                                      uint64_t* __restrict__ mask_out) {
+    __shared__ uint32_t sm[kMaxKeyWords];
+    for (uint32_t i = threadIdx.x; i < k.nwords; i += blockDim.x) sm[i] = 0;
+    __syncthreads();
+    const uint32_t lane = threadIdx.x & 31;
+    const uint32_t nchunks = (k.nwords + 3) / 4;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    // warp-uniform trip count so that every lane takes part in the reductions
+    for (uint64_t r0 = (uint64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31u); r0 < n; r0 += stride) {
+        const uint64_t r = r0 + lane;
+        const bool valid = r < n;
+        for (uint32_t c = 0; c < nchunks; ++c) {
+            uint32_t w[4] = {0, 0, 0, 0}, ref[4];
+            load_chunk<VEC>(k, ref_row, c, ref);
+            if (valid) load_chunk<VEC>(k, r, c, w);
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const uint32_t x = __reduce_or_sync(kFull, valid ? (w[i] ^ ref[i]) : 0u);
+                if (lane == 0 && x && 4 * c + i < k.nwords) atomicOr(&sm[4 * c + i], x);
+            }
+        }
+    }
+    __syncthreads();
+    merge_bitmap(sm, k.nwords, mask_out);
+}
+
+// ------------------------------------------------------------------ D-bits
+// D-bit of rows a and b: the first differing position, or -1 if equal.
+template <int VEC>
+__device__ __forceinline__ int32_t key_dbit(const KeyDesc& k, uint64_t a, uint64_t b) {
+    const uint32_t nchunks = (k.nwords + 3) / 4;
+    for (uint32_t c = 0; c < nchunks; ++c) {
+        uint32_t wa[4], wb[4];
+        load_chunk<VEC>(k, a, c, wa);
+        load_chunk<VEC>(k, b, c, wb);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const uint32_t x = wa[i] ^ wb[i];
+            if (x) return (int32_t)(32 * (4 * c + i) + __clz(x));
+        }
+    }
+    return -1;
+}
+
+template <int VEC>
+__global__ void __launch_bounds__(256) dbits_kernel(const KeyDesc k, uint64_t n, const uint32_t* __restrict__ order,
+                                                    uint64_t* __restrict__ mask_out, unsigned long long* status) {
+    __shared__ uint32_t sm[kMaxKeyWords];
+    for (uint32_t i = threadIdx.x; i < k.nwords; i += blockDim.x) sm[i] = 0;
+    __syncthreads();
+    const uint32_t lane = threadIdx.x & 31;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t r0 = (uint64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31u); r0 < n; r0 += stride) {
+        const uint64_t i = r0 + lane;
+        int32_t p = -1;
+        if (i >= 1 && i < n) {
+            const uint64_t a = order ? order[i - 1] : i - 1;
+            const uint64_t b = order ? order[i] : i;
+            if (a < n && b < n) p = key_dbit<VEC>(k, a, b);
+            else report(status, CK_EINVAL, i);          // a row id past the column: skip it
+        }
+        warp_mark(sm, p);
+    }
+    __syncthreads();
+    merge_bitmap(sm, k.nwords, mask_out);
+}
+
+// ------------------------------------------------------------------ extract
+// Compress network (H. S. Warren, Hacker's Delight, 2nd ed., Sec. 7-4): with
+// move masks mv[s] precomputed for the word's mask, five rounds of
+//   t = x & mv[s];  x = (x ^ t) | (t >> 2^s)
+// gather the masked bits of x, in order, into its low popcount(mask) bits.
+// The compressed bits of successive key words are appended (most significant
+// key word first) to a bit stream that begins with the output's leading zero
+// padding; every full 32 bits leave as one output word, top word first.
+// The per-word extraction plan, copied once per block into shared memory so
+// that every lookup is a broadcast shared load (indexing the kernel parameter
+// with a runtime word index would serialise on the indexed constant cache).
+struct WordPlan {
+    uint32_t mask, mv[5], pc, pad;
+};
+
+// Compress of R rows at once: row q's chunks come from rows[q] (global or
+// shared memory); each plan word is read once for all R rows.
+template <int VEC, int R>
+__device__ __forceinline__ void extract_rows(const KeyDesc& k, const unsigned char* const (&rows)[R],
+                                             const uint64_t (&r)[R], const bool (&valid)[R], uint64_t ld,
+                                             const ExtractPlan& plan, const WordPlan* wp, uint32_t* __restrict__ out) {
+    uint32_t kout = plan.K;
+    for (uint32_t z = 0; z < plan.lead_zero_words; ++z) {
+        --kout;
+#pragma unroll
+        for (int q = 0; q < R; ++q)
+            if (valid[q]) out[(uint64_t)kout * ld + r[q]] = 0u;
+    }
+    uint64_t acc[R];
+#pragma unroll
+    for (int q = 0; q < R; ++q) acc[q] = 0;
+    uint32_t cnt = plan.pad_bits;
+    const uint32_t c0 = plan.first_word >> 2, c1 = plan.last_word >> 2;
+    for (uint32_t c = c0; c <= c1; ++c) {
+        uint32_t w[R][4];
+#pragma unroll
+        for (int q = 0; q < R; ++q) {
+            if (valid[q]) load_chunk_row<VEC>(k, rows[q], c, w[q]);
+            else w[q][0] = w[q][1] = w[q][2] = w[q][3] = 0;
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const uint32_t wi = 4 * c + i;
+            if (wi < plan.first_word || wi > plan.last_word) continue;
+            const WordPlan p = wp[wi];
+            if (p.mask == 0) continue;
+#pragma unroll
+            for (int q = 0; q < R; ++q) {
+                uint32_t x = w[q][i] & p.mask;
+#pragma unroll
+                for (int s = 0; s < 5; ++s) {
+                    const uint32_t t = x & p.mv[s];
+                    x = (x ^ t) | (t >> (1u << s));
+                }
+                acc[q] = (acc[q] << p.pc) | x;
+            }
+            cnt += p.pc;
+            if (cnt >= 32) {
+                cnt -= 32;
+                --kout;
+#pragma unroll
+                for (int q = 0; q < R; ++q)
+                    if (valid[q]) out[(uint64_t)kout * ld + r[q]] = (uint32_t)(acc[q] >> cnt);
+            }
+        }
+    }
+}
+
+// Persistent extraction with TMA staging: block b takes row tiles b, b + G,
+// b + 2G, ...; each full tile (rows_per_tile rows, contiguous in memory
+// because row_stride * rows_per_tile is a multiple of 16) arrives in a ring of
+// kExtractStages shared buffers by one bulk copy, issued kExtractStages tiles
+// ahead.  The ragged last tile is read straight from global memory.  Each
+// thread extracts kExtractRows rows of a tile together.
+constexpr int kExtractStages = 4;
+constexpr int kExtractThreads = 256;
+constexpr int kExtractRows = 2;
+
+template <int VEC>
+__global__ void __launch_bounds__(kExtractThreads) extract_kernel(const KeyDesc k, uint64_t n, uint64_t ld,
+                                                                  uint32_t rows_per_tile, uint32_t staged,
+                                                                  const __grid_constant__ ExtractPlan plan,
+                                                                  uint32_t* __restrict__ out, uint32_t spin_limit,
+                                                                  unsigned long long* status) {
+    constexpr int R = kExtractRows;
+    extern __shared__ __align__(128) unsigned char sm[];
+    const uint32_t tile_bytes = staged ? rows_per_tile * (uint32_t)k.stride : 0u;
+    uint64_t* bar = reinterpret_cast<uint64_t*>(sm + (size_t)kExtractStages * tile_bytes);
+    WordPlan* wp = reinterpret_cast<WordPlan*>(bar + kExtractStages);
+    const uint64_t tiles = (n + rows_per_tile - 1) / rows_per_tile;
+    const uint64_t full_tiles = staged ? n / rows_per_tile : 0;  // tiles that arrive by bulk copy
+    const uint32_t tid = threadIdx.x;
+    for (uint32_t w = plan.first_word + tid; w <= plan.last_word; w += kExtractThreads) {
+        WordPlan p;
+        p.mask = plan.mask[w];
+        for (int s = 0; s < 5; ++s) p.mv[s] = plan.mv[s][w];
+        p.pc = plan.pc[w];
+        p.pad = 0;
+        wp[w] = p;
+    }
+    if (tid == 0 && staged) {
+        for (int b = 0; b < kExtractStages; ++b) mbar_init(&bar[b], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    auto issue = [&](uint64_t i) {  // thread 0: local tile i into stage i % kExtractStages
+        const uint64_t t = blockIdx.x + i * gridDim.x;
+        if (t < full_tiles)
+            bulk_load(sm + (size_t)(i % kExtractStages) * tile_bytes, k.base + t * rows_per_tile * k.stride,
+                      tile_bytes, &bar[i % kExtractStages]);
+    };
+    if (tid == 0)
+        for (uint64_t i = 0; i < (uint64_t)kExtractStages; ++i) issue(i);
+    for (uint64_t i = 0;; ++i) {
+        const uint64_t t = blockIdx.x + i * gridDim.x;
+        if (t >= tiles) break;
+        const uint64_t r0 = t * rows_per_tile;
+        const unsigned char* base = k.base + r0 * k.stride;
+        if (t < full_tiles) {
+            const uint32_t st = (uint32_t)(i % kExtractStages);
+            if (!mbar_wait(&bar[st], (uint32_t)(i / kExtractStages) & 1u, spin_limit))
+                report(status, CK_ETIMEOUT, t);
+            base = sm + (size_t)st * tile_bytes;
+        }
+        const uint64_t nrows = min((uint64_t)rows_per_tile, n - r0);
+        for (uint32_t j0 = tid; j0 < nrows; j0 += R * kExtractThreads) {
+            const unsigned char* rows[R];
+            uint64_t r[R];
+            bool valid[R];
+#pragma unroll
+            for (int q = 0; q < R; ++q) {
+                const uint64_t j = j0 + (uint64_t)q * kExtractThreads;
+                valid[q] = j < nrows;
+                r[q] = r0 + j;
+                rows[q] = base + (valid[q] ? j : 0) * k.stride;
+            }
+            extract_rows<VEC, R>(k, rows, r, valid, ld, plan, wp, out);
+        }
+        __syncthreads();  // stage i % kExtractStages is free again
+        if (tid == 0) {
+            fence_proxy_async_smem();
+            issue(i + kExtractStages);
+        }
+    }
+}
+
+// ------------------------------------------------------------------ launchers
+static unsigned grid_for(uint64_t n, unsigned threads) {
+    const uint64_t want = (n + threads - 1) / threads;
+    const uint64_t cap = (uint64_t)num_sms() * 8;
+    return (unsigned)(want < cap ? (want ? want : 1) : cap);
+}
+
+#define CK_DISPATCH_VEC(vec, KERNEL, ...)                                      \
+    switch (vec) {                                                             \
+        case 16: KERNEL<16><<<grid, 256, 0, s>>>(__VA_ARGS__); break;          \
+        case 8: KERNEL<8><<<grid, 256, 0, s>>>(__VA_ARGS__); break;            \
+        case 4: KERNEL<4><<<grid, 256, 0, s>>>(__VA_ARGS__); break;            \
+        default: KERNEL<1><<<grid, 256, 0, s>>>(__VA_ARGS__); break;           \
+    }
+
+cudaError_t launch_variant(const KeyDesc& k, int vec, uint64_t n, uint64_t ref_row, uint64_t* mask_out,
+                           cudaStream_t s) {
+    const unsigned grid = grid_for(n, 256);
+    CK_DISPATCH_VEC(vec, variant_kernel, k, n, ref_row, mask_out);
+    count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_dbits(const KeyDesc& k, int vec, uint64_t n, const uint32_t* order, uint64_t* mask_out,
+                         cudaStream_t s) {
+    const unsigned grid = grid_for(n, 256);
+    CK_DISPATCH_VEC(vec, dbits_kernel, k, n, order, mask_out, status_ptr());
+    count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_extract(const KeyDesc& k, int vec, uint64_t n, uint64_t ld, const ExtractPlan& plan,
+                           uint32_t* ck_out, cudaStream_t s) {
+    // rows per tile: a multiple of 16 (so that tiles start 16-byte aligned),
+    // about 16 KB of keys, at most kExtractRows rows per thread.  Staging needs
+    // a 16-byte aligned column and a ring that fits shared memory.
+    uint32_t rows = (uint32_t)(16384 / k.stride) & ~15u;
+    if (rows > (uint32_t)(kExtractRows * kExtractThreads)) rows = kExtractRows * kExtractThreads;
+    if (rows < 16) rows = 16;
+    const bool staged = (reinterpret_cast<uintptr_t>(k.base) & 15) == 0 &&
+                        (uint64_t)kExtractStages * rows * k.stride <= 160 * 1024;
+    if (!staged) rows = kExtractRows * kExtractThreads;
+    const size_t smem = (staged ? (size_t)kExtractStages * rows * k.stride : 0) +
+                        kExtractStages * sizeof(uint64_t) + sizeof(WordPlan) * kMaxKeyWords;
+    const uint64_t tiles = (n + rows - 1) / rows;
+    const uint64_t cap = (uint64_t)num_sms() * 3;
+    const unsigned grid = (unsigned)(tiles < cap ? tiles : cap);
+    cudaError_t e = cudaSuccess;
+#define CK_EXTRACT_LAUNCH(V)                                                                                  \
+    e = cudaFuncSetAttribute(extract_kernel<V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);     \
+    if (e != cudaSuccess) return e;                                                                           \
+    extract_kernel<V><<<grid, kExtractThreads, smem, s>>>(k, n, ld, rows, staged ? 1u : 0u, plan, ck_out,      \
+                                                           kDefaultSpin, status_ptr());
+    switch (vec) {
+        case 16: CK_EXTRACT_LAUNCH(16); break;
+        case 8: CK_EXTRACT_LAUNCH(8); break;
+        case 4: CK_EXTRACT_LAUNCH(4); break;
+        default: CK_EXTRACT_LAUNCH(1); break;
+    }
+#undef CK_EXTRACT_LAUNCH
+    count_launch();
+    return cudaGetLastError();
+}
+
+}  // namespace ck

@@ -1,0 +1,478 @@
+// ck_sort.cu -- stable LSD radix sort of (compressed key, row id) pairs.
+//
+// The paper sorts with a parallel comparison sort (Sec. 5.2, Appendix A);
+// here the sort is a GPU onesweep radix sort (Adinets and Merrill, "Onesweep:
+// a faster least significant digit radix sort for GPUs", 2022), written for
+// word-major multi-word keys:
+//
+//   upsweep  one read of the keys -> the digit histogram of every pass
+//   scan     per pass, exclusive scan of the histogram -> digit bucket bases
+//   pass     per digit, one kernel: each block takes the next tile (dynamic
+//            tile id), ranks its digits stably (warp ballots + per-warp
+//            counters), publishes its per-digit counts, obtains the counts of
+//            all earlier tiles by decoupled look-back, and scatters every key
+//            word and the row id through shared memory so that each digit run
+//            leaves as contiguous stores.
+//
+// Look-back words pack a 2-bit state (1 = tile aggregate, 2 = inclusive
+// prefix) over a 30-bit count, hence n <= 2^30 - 1.  Every wait on a
+// predecessor is bounded by spin_limit polls; when it runs out the block
+// records CK_ETIMEOUT, assumes zero for the missing count (which keeps every
+// store in bounds), and carries on so that later tiles never wait forever.
+#include "ck_internal.cuh"
+
+namespace ck {
+
+constexpr uint32_t kFlagAgg = 1u << 30;
+constexpr uint32_t kFlagPrefix = 2u << 30;
+constexpr uint32_t kValMask = (1u << 30) - 1;
+constexpr int kPassThreads = 512;
+constexpr int kPassItems = 8;
+constexpr int kTile = kPassThreads * kPassItems;  // pairs per tile
+constexpr int kRing = 3;                          // staging buffers per block
+constexpr int kPassBlocksPerSM = 3;
+constexpr int kUpThreads = 256;
+
+// Exclusive scan in place over count entries of arr (shared or global memory)
+// by one block; returns the total.  scratch: THREADS/32 + 1 shared words.
+template <int THREADS>
+__device__ uint32_t block_exclusive_scan(uint32_t* arr, int count, uint32_t* scratch) {
+    constexpr int WARPS = THREADS / 32;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int per = (count + THREADS - 1) / THREADS;
+    const int beg = tid * per;
+    uint32_t sum = 0;
+    for (int i = 0; i < per; ++i)
+        if (beg + i < count) sum += arr[beg + i];
+    uint32_t inc = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t t = __shfl_up_sync(kFull, inc, o);
+        if (lane >= o) inc += t;
+    }
+    if (lane == 31) scratch[warp] = inc;
+    __syncthreads();
+    if (warp == 0) {
+        const uint32_t v = lane < WARPS ? scratch[lane] : 0u;
+        uint32_t vi = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t t = __shfl_up_sync(kFull, vi, o);
+            if (lane >= o) vi += t;
+        }
+        if (lane < WARPS) scratch[lane] = vi - v;
+        if (lane == 31) scratch[WARPS] = vi;
+    }
+    __syncthreads();
+    uint32_t run = scratch[warp] + inc - sum;
+    for (int i = 0; i < per; ++i)
+        if (beg + i < count) {
+            const uint32_t t = arr[beg + i];
+            arr[beg + i] = run;
+            run += t;
+        }
+    const uint32_t total = scratch[WARPS];
+    __syncthreads();
+    return total;
+}
+
+// Digit of pass p (bits [shift, shift + bits) of the right-aligned key).
+__device__ __forceinline__ uint32_t digit_of(const uint32_t* ck, uint64_t ld, uint64_t r, uint32_t shift,
+                                             uint32_t bits) {
+    const uint32_t w = shift >> 5, sh = shift & 31;
+    uint32_t d = ck[(uint64_t)w * ld + r] >> sh;
+    if (sh + bits > 32) d |= ck[(uint64_t)(w + 1) * ld + r] << (32 - sh);
+    return d & ((1u << bits) - 1u);
+}
+
+// ------------------------------------------------------------------ upsweep
+template <int RB>
+__global__ void __launch_bounds__(kUpThreads) upsweep_kernel(const uint32_t* __restrict__ ck, uint64_t n, uint64_t ld,
+                                                             uint32_t nbits, uint32_t p0, uint32_t np,
+                                                             uint32_t* __restrict__ hist) {
+    constexpr int BINS = 1 << RB;
+    extern __shared__ uint32_t sh[];
+    for (uint32_t i = threadIdx.x; i < np * BINS; i += blockDim.x) sh[i] = 0;
+    __syncthreads();
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t r = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += stride) {
+        for (uint32_t p = 0; p < np; ++p) {
+            const uint32_t shift = (p0 + p) * RB;
+            const uint32_t bits = min((uint32_t)RB, nbits - shift);
+            atomicAdd(&sh[p * BINS + digit_of(ck, ld, r, shift, bits)], 1u);
+        }
+    }
+    __syncthreads();
+    for (uint32_t i = threadIdx.x; i < np * BINS; i += blockDim.x)
+        if (sh[i]) atomicAdd(&hist[(uint64_t)p0 * BINS + i], sh[i]);
+}
+
+template <int RB>
+__global__ void __launch_bounds__(256) scan_kernel(uint32_t* hist) {
+    __shared__ uint32_t scratch[256 / 32 + 1];
+    block_exclusive_scan<256>(hist + (uint64_t)blockIdx.x * (1u << RB), 1 << RB, scratch);
+}
+
+__global__ void iota_kernel(uint32_t* out, uint64_t n) {
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x)
+        out[i] = (uint32_t)i;
+}
+
+// ------------------------------------------------------------------ pass
+struct PassArgs {
+    const uint32_t* ck_in;  // word-major, leading dimension ld
+    uint32_t* ck_out;
+    const uint32_t* rid_in;  // NULL: row ids are the input positions
+    uint32_t* rid_out;
+    uint64_t n, ld;
+    uint32_t K, shift, bits, pass;
+    uint32_t bulk;                // 1: every array is 16-byte aligned, full tiles stage by TMA
+    const uint32_t* bucket_base;  // [BINS] of this pass
+    uint32_t* lookback;           // [tiles][BINS] of this pass, zeroed
+    uint32_t* tile_counter;       // zeroed
+    uint32_t spin_limit, inject;
+    unsigned long long* status;
+};
+
+// Shared memory of one pass block: a ring of kRing staging buffers (one word
+// array of the tile each), per-warp digit counters, per-slot source position
+// and digit, per-digit tile counts and destinations, the staging order of the
+// arrays, and the ring's mbarriers.
+template <int RB>
+struct PassSmem {
+    static constexpr int BINS = 1 << RB, WARPS = kPassThreads / 32;
+    uint32_t stage[kRing][kTile];
+    uint16_t whist[WARPS][BINS];  // counts <= kTile fit 16 bits
+    uint16_t src_pos[kTile];
+    uint32_t tile_total[BINS];
+    uint32_t tile_excl[BINS];
+    int32_t dest_base[BINS];
+    uint32_t scratch[WARPS + 2];
+    uint16_t order[kMaxKeyWords + 1];
+    alignas(8) uint64_t bar[kRing];
+};
+
+template <int RB>
+__global__ void __launch_bounds__(kPassThreads, kPassBlocksPerSM) onesweep_pass_kernel(const PassArgs a) {
+    constexpr int BINS = 1 << RB, WARPS = kPassThreads / 32, ITEMS = kPassItems, WITEMS = 32 * ITEMS;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    PassSmem<RB>& S = *reinterpret_cast<PassSmem<RB>*>(smem_raw);
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const uint64_t n = a.n;
+    const uint32_t wlo = a.shift >> 5, sh = a.shift & 31;
+    const bool straddle = sh + a.bits > 32;
+    // staging order: the digit word(s) first, then the other key words, then the
+    // row ids.  Row ids without an input array (0..n-1) are staged by nobody; they
+    // are last in the order, so no later item reuses their ring slot and its
+    // mbarrier phases stay in step.
+    const uint32_t M = a.K + 1;
+    if (tid == 0) {
+        S.scratch[WARPS + 1] = atomicAdd(a.tile_counter, 1u);
+        uint32_t m = 0;
+        S.order[m++] = (uint16_t)wlo;
+        if (straddle) S.order[m++] = (uint16_t)(wlo + 1);
+        for (uint32_t w = 0; w < a.K; ++w)
+            if (w != wlo && !(straddle && w == wlo + 1)) S.order[m++] = (uint16_t)w;
+        S.order[m++] = (uint16_t)a.K;
+        for (int b = 0; b < kRing; ++b) mbar_init(&S.bar[b], 1);
+        fence_mbar_init();
+    }
+    for (int i = tid; i < WARPS * BINS; i += kPassThreads) (&S.whist[0][0])[i] = 0;
+    __syncthreads();
+    const uint32_t tile = S.scratch[WARPS + 1];
+    const uint64_t tile_base = (uint64_t)tile * kTile;
+    const uint32_t count = (uint32_t)min((uint64_t)kTile, n - tile_base);
+    const bool bulk = a.bulk && count == (uint32_t)kTile;
+
+    auto src_of = [&](uint32_t arr) -> const uint32_t* {
+        return arr == a.K ? a.rid_in : a.ck_in + (uint64_t)arr * a.ld;
+    };
+    // stages item m of the order into ring buffer m % kRing
+    auto issue = [&](uint32_t m) {  // thread 0 only, bulk tiles only
+        const uint32_t* src = src_of(S.order[m]);
+        if (src) bulk_load(S.stage[m % kRing], src + tile_base, kTile * sizeof(uint32_t), &S.bar[m % kRing]);
+    };
+    auto stage_plain = [&](uint32_t m) {  // all threads; caller synchronises
+        const uint32_t* src = src_of(S.order[m]);
+        if (src)
+            for (uint32_t e = tid; e < count; e += kPassThreads) S.stage[m % kRing][e] = src[tile_base + e];
+    };
+    auto wait_item = [&](uint32_t m) {
+        const uint32_t* src = src_of(S.order[m]);
+        if (!src) return;
+        if (!mbar_wait(&S.bar[m % kRing], (m / kRing) & 1u, a.spin_limit))
+            report(a.status, CK_ETIMEOUT, (uint64_t)a.pass | ((uint64_t)tile << 16) | (1ull << 47));
+    };
+
+    if (bulk) {
+        if (tid == 0)
+            for (uint32_t m = 0; m < M && m < (uint32_t)kRing; ++m) issue(m);
+        wait_item(0);
+        if (straddle) wait_item(1);
+    } else {
+        stage_plain(0);
+        if (straddle) stage_plain(1);
+        __syncthreads();
+    }
+
+    // 1. digits of this warp's items, warp-striped: item j of lane l is e = warp*WITEMS + 32j + l
+    const uint32_t dmask = (1u << a.bits) - 1u;
+    uint32_t dr[ITEMS];  // digit in bits 0..15, rank within the warp in bits 16..31
+#pragma unroll
+    for (int j = 0; j < ITEMS; ++j) {
+        const uint32_t e = warp * WITEMS + 32 * j + lane;
+        uint32_t d = 0;
+        if (e < count) {
+            d = S.stage[0][e] >> sh;
+            if (straddle) d |= S.stage[1][e] << (32 - sh);
+            d &= dmask;
+        }
+        dr[j] = d;
+    }
+
+    // 2. stable rank within the warp: lanes with equal digits found by RB ballots
+    uint16_t* my = S.whist[warp];
+    const uint32_t lt = (1u << lane) - 1u;
+#pragma unroll
+    for (int j = 0; j < ITEMS; ++j) {
+        const bool valid = warp * WITEMS + 32 * j + lane < count;
+        const uint32_t d = dr[j];
+        uint32_t peers = __ballot_sync(kFull, valid);
+#pragma unroll
+        for (int b = 0; b < RB; ++b) {
+            const bool bit = (d >> b) & 1u;
+            const uint32_t bal = __ballot_sync(kFull, bit);
+            peers &= bit ? bal : ~bal;
+        }
+        const uint32_t base = valid ? my[d] : 0u;
+        __syncwarp();
+        if (valid && (peers & lt) == 0) my[d] = (uint16_t)(base + __popc(peers));
+        __syncwarp();
+        dr[j] = d | ((base + __popc(peers & lt)) << 16);  // < WITEMS, fits 16 bits
+    }
+    __syncthreads();
+
+    // 3. per digit: exclusive prefix over warps, tile total, publish the aggregate
+    const bool stall = (a.inject & CK_INJECT_STALL_FIRST_TILE) && a.pass == 0 && tile == 0;
+    for (int b = tid; b < BINS; b += kPassThreads) {
+        uint32_t sum = 0;
+#pragma unroll
+        for (int w = 0; w < WARPS; ++w) {
+            const uint32_t t = S.whist[w][b];
+            S.whist[w][b] = (uint16_t)sum;
+            sum += t;
+        }
+        S.tile_total[b] = sum;
+        S.tile_excl[b] = sum;
+        if (!stall) st_relaxed(&a.lookback[(uint64_t)tile * BINS + b], (tile == 0 ? kFlagPrefix : kFlagAgg) | sum);
+    }
+    __syncthreads();
+    block_exclusive_scan<kPassThreads>(S.tile_excl, BINS, S.scratch);
+
+    // 4. decoupled look-back: counts of every digit in all earlier tiles
+    for (int b = tid; b < BINS; b += kPassThreads) {
+        uint32_t excl = 0;
+        if (tile > 0) {
+            int64_t p = (int64_t)tile - 1;
+            uint32_t polls = 0;
+            while (p >= 0) {
+                const uint32_t v = ld_relaxed(&a.lookback[(uint64_t)p * BINS + b]);
+                const uint32_t flag = v & ~kValMask;
+                if (flag == 0) {
+                    if (++polls > a.spin_limit) {
+                        report(a.status, CK_ETIMEOUT, (uint64_t)a.pass | ((uint64_t)tile << 16));
+                        break;
+                    }
+                    __nanosleep(64);
+                    continue;
+                }
+                excl += v & kValMask;
+                if (flag == kFlagPrefix) break;
+                --p;
+            }
+            st_relaxed(&a.lookback[(uint64_t)tile * BINS + b], kFlagPrefix | ((excl + S.tile_total[b]) & kValMask));
+        }
+        S.dest_base[b] = (int32_t)(a.bucket_base[b] + excl) - (int32_t)S.tile_excl[b];
+    }
+
+    // 5. local slot of every item in digit order: record where it comes from
+#pragma unroll
+    for (int j = 0; j < ITEMS; ++j) {
+        const uint32_t e = warp * WITEMS + 32 * j + lane;
+        const uint32_t d = dr[j] & 0xFFFFu;
+        if (e < count) S.src_pos[(dr[j] >> 16) + S.tile_excl[d] + my[d]] = (uint16_t)e;
+    }
+    __syncthreads();
+    // this thread's slots tid + i*THREADS: source position and global destination
+    // (the digit is re-read from the staged digit word, still in ring slots 0/1)
+    uint32_t srcp[ITEMS], dst[ITEMS];
+#pragma unroll
+    for (int i = 0; i < ITEMS; ++i) {
+        const uint32_t s = tid + i * kPassThreads;
+        srcp[i] = 0;
+        dst[i] = 0;
+        if (s < count) {
+            const uint32_t e = S.src_pos[s];
+            uint32_t d = S.stage[0][e] >> sh;
+            if (straddle) d |= S.stage[1][e] << (32 - sh);
+            srcp[i] = e;
+            dst[i] = (uint32_t)(S.dest_base[d & dmask] + (int32_t)s);
+        }
+    }
+
+    // 6. every array in staging order: wait for it, scatter it, refill its buffer
+    for (uint32_t m = 0; m < M; ++m) {
+        if (bulk) {
+            if (m > 0 && !(straddle && m == 1)) wait_item(m);
+        } else if (m > 0 && !(straddle && m == 1)) {
+            stage_plain(m);
+            __syncthreads();
+        }
+        const uint32_t arr = S.order[m];
+        const bool iota = arr == a.K && a.rid_in == nullptr;
+        const uint32_t* buf = S.stage[m % kRing];
+        uint32_t* out = arr == a.K ? a.rid_out : a.ck_out + (uint64_t)arr * a.ld;
+#pragma unroll
+        for (int i = 0; i < ITEMS; ++i) {
+            const uint32_t s = tid + i * kPassThreads;
+            if (s < count) out[dst[i]] = iota ? (uint32_t)(tile_base + srcp[i]) : buf[srcp[i]];  // dst < 2^30
+        }
+        __syncthreads();  // buffer m % kRing is free again
+        if (bulk && tid == 0 && m + kRing < M) {
+            fence_proxy_async_smem();
+            issue(m + kRing);
+        }
+    }
+}
+
+// ------------------------------------------------------------------ host
+static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+bool make_sort_plan(uint64_t n, uint32_t K, uint32_t nbits, uint32_t digit_bits, SortPlan* p) {
+    if (digit_bits == 0) digit_bits = 8;
+    if (digit_bits < 4 || digit_bits > 11) return false;
+    p->digit_bits = digit_bits;
+    p->passes = (nbits + digit_bits - 1) / digit_bits;
+    p->tile = kTile;
+    p->tiles = (uint32_t)((n + kTile - 1) / kTile);
+    p->K = K;
+    const size_t bins = (size_t)1 << digit_bits;
+    size_t off = 0;
+    p->off_hist = off;
+    off = align256(off + sizeof(uint32_t) * bins * p->passes);
+    p->off_counter = off;
+    off = align256(off + sizeof(uint32_t) * p->passes);
+    p->off_lookback = off;
+    off = align256(off + sizeof(uint32_t) * bins * (size_t)p->tiles * p->passes);
+    p->off_alt_ck = off;
+    off = align256(off + sizeof(uint32_t) * (size_t)K * CK_LD(n));
+    p->off_alt_rid = off;
+    off = align256(off + sizeof(uint32_t) * n);
+    p->total = off;
+    return true;
+}
+
+template <int RB>
+static cudaError_t run_sort_rb(const SortPlan& p, const uint32_t* ck_in, const uint32_t* rid_in, uint32_t* ck_out,
+                               uint32_t* rid_out, uint64_t n, uint32_t nbits, uint32_t spin_limit, uint32_t inject,
+                               cudaEvent_t* ev, unsigned char* ws, cudaStream_t s) {
+    constexpr int BINS = 1 << RB;
+    uint32_t* hist = reinterpret_cast<uint32_t*>(ws + p.off_hist);
+    uint32_t* counters = reinterpret_cast<uint32_t*>(ws + p.off_counter);
+    uint32_t* lookback = reinterpret_cast<uint32_t*>(ws + p.off_lookback);
+    uint32_t* alt_ck = reinterpret_cast<uint32_t*>(ws + p.off_alt_ck);
+    uint32_t* alt_rid = reinterpret_cast<uint32_t*>(ws + p.off_alt_rid);
+    cudaError_t e = cudaMemsetAsync(ws, 0, p.off_alt_ck, s);
+    if (e != cudaSuccess) return e;
+
+    // upsweep: all pass histograms, in chunks that fit 64 KB of shared memory
+    const uint32_t chunk = (uint32_t)(65536 / (sizeof(uint32_t) * BINS));
+    const int up_grid = num_sms() * 4;
+    e = cudaFuncSetAttribute(upsweep_kernel<RB>, cudaFuncAttributeMaxDynamicSharedMemorySize, 65536);
+    if (e != cudaSuccess) return e;
+    for (uint32_t p0 = 0; p0 < p.passes; p0 += chunk) {
+        const uint32_t np = min(chunk, p.passes - p0);
+        upsweep_kernel<RB><<<up_grid, kUpThreads, sizeof(uint32_t) * np * BINS, s>>>(ck_in, n, CK_LD(n), nbits, p0,
+                                                                                     np, hist);
+        count_launch();
+    }
+    scan_kernel<RB><<<p.passes, 256, 0, s>>>(hist);
+    count_launch();
+
+    constexpr size_t smem = sizeof(PassSmem<RB>);
+    static_assert(sizeof(PassSmem<RB>) <= 227 * 1024, "pass block exceeds shared memory");
+    e = cudaFuncSetAttribute(onesweep_pass_kernel<RB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const bool inplace = (ck_in == ck_out) || (rid_in != nullptr && rid_in == rid_out);
+    auto al16 = [](const void* q) { return (reinterpret_cast<uintptr_t>(q) & 15) == 0; };
+    const uint32_t bulk = al16(ck_in) && al16(ck_out) && al16(rid_out) && (rid_in == nullptr || al16(rid_in)) ? 1u : 0u;
+    if (ev && (e = cudaEventRecord(ev[0], s)) != cudaSuccess) return e;
+    const uint32_t* src_ck = ck_in;
+    const uint32_t* src_rid = rid_in;
+    for (uint32_t q = 0; q < p.passes; ++q) {
+        const bool to_out = inplace ? (q % 2 == 1) : ((p.passes - 1 - q) % 2 == 0);
+        PassArgs a;
+        a.ck_in = src_ck;
+        a.rid_in = src_rid;
+        a.ck_out = to_out ? ck_out : alt_ck;
+        a.rid_out = to_out ? rid_out : alt_rid;
+        a.n = n;
+        a.ld = CK_LD(n);
+        a.bulk = bulk;
+        a.K = p.K;
+        a.shift = q * RB;
+        a.bits = min((uint32_t)RB, nbits - q * RB);
+        a.pass = q;
+        a.bucket_base = hist + (size_t)q * BINS;
+        a.lookback = lookback + (size_t)q * BINS * p.tiles;
+        a.tile_counter = counters + q;
+        a.spin_limit = spin_limit;
+        a.inject = inject;
+        a.status = status_ptr();
+        onesweep_pass_kernel<RB><<<p.tiles, kPassThreads, smem, s>>>(a);
+        count_launch();
+        if (ev && (e = cudaEventRecord(ev[q + 1], s)) != cudaSuccess) return e;
+        src_ck = a.ck_out;
+        src_rid = a.rid_out;
+    }
+    if (src_ck != ck_out) {
+        e = cudaMemcpyAsync(ck_out, src_ck, sizeof(uint32_t) * (size_t)p.K * CK_LD(n), cudaMemcpyDeviceToDevice, s);
+        if (e != cudaSuccess) return e;
+        e = cudaMemcpyAsync(rid_out, src_rid, sizeof(uint32_t) * n, cudaMemcpyDeviceToDevice, s);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t run_sort(const SortPlan& p, const uint32_t* ck_in, const uint32_t* rid_in, uint32_t* ck_out,
+                     uint32_t* rid_out, uint64_t n, uint32_t nbits, uint32_t spin_limit, uint32_t inject,
+                     cudaEvent_t* ev, unsigned char* ws, cudaStream_t s) {
+    if (p.passes == 0) {  // nothing to order: outputs are the inputs
+        cudaError_t e = cudaSuccess;
+        if (ck_out != ck_in)
+            e = cudaMemcpyAsync(ck_out, ck_in, sizeof(uint32_t) * (size_t)p.K * CK_LD(n), cudaMemcpyDeviceToDevice, s);
+        if (e != cudaSuccess) return e;
+        if (rid_in == nullptr) {
+            iota_kernel<<<num_sms() * 4, 256, 0, s>>>(rid_out, n);
+            count_launch();
+        } else if (rid_out != rid_in) {
+            e = cudaMemcpyAsync(rid_out, rid_in, sizeof(uint32_t) * n, cudaMemcpyDeviceToDevice, s);
+        }
+        if (e != cudaSuccess) return e;
+        return cudaGetLastError();
+    }
+    switch (p.digit_bits) {
+        case 4: return run_sort_rb<4>(p, ck_in, rid_in, ck_out, rid_out, n, nbits, spin_limit, inject, ev, ws, s);
+        case 5: return run_sort_rb<5>(p, ck_in, rid_in, ck_out, rid_out, n, nbits, spin_limit, inject, ev, ws, s);
+        case 6: return run_sort_rb<6>(p, ck_in, rid_in, ck_out, rid_out, n, nbits, spin_limit, inject, ev, ws, s);
+        case 7: return run_sort_rb<7>(p, ck_in, rid_in, ck_out, rid_out, n, nbits, spin_limit, inject, ev, ws, s);
+        case 8: return run_sort_rb<8>(p, ck_in, rid_in, ck_out, rid_out, n, nbits, spin_limit, inject, ev, ws, s);
+        case 9: return run_sort_rb<9>(p, ck_in, rid_in, ck_out, rid_out, n, nbits, spin_limit, inject, ev, ws, s);
+        case 10: return run_sort_rb<10>(p, ck_in, rid_in, ck_out, rid_out, n, nbits, spin_limit, inject, ev, ws, s);
+        case 11: return run_sort_rb<11>(p, ck_in, rid_in, ck_out, rid_out, n, nbits, spin_limit, inject, ev, ws, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace ck

@@ -1,0 +1,94 @@
+"""Index reconstruction on the GPU (Sec. 5 of the paper): the four C-ABI calls
+in order, with device buffers allocated once through torch.
+
+``Rebuild`` is the rebuild with stored DS-metadata (the D-bitmap kept from the
+previous build, Sec. 4.2): extract -> sort -> bulk load, the bulk load also
+recomputing the D-bitmap (Sec. 4.3, step 1).  ``first_build_dmask`` derives
+the D-bitmap when there is none yet: the variant bitmap is a superset of D
+(every distinction position is variant), so extracting with it, sorting and
+refining gives the exact D (Sec. 4.3 reads the first D from full keys; the
+refined set is the same by Theorem 2 and the D-offset mapping of Sec. 5.3).
+
+Python only marshals arguments; every step runs in libck's kernels.
+"""
+from __future__ import annotations
+
+import numpy as np
+import torch
+
+from . import ck
+
+
+class Rebuild:
+    """Buffers and launches for one key column and one D-bitmap.
+
+    keys:   CUDA tensor, [n, W] uint8 rows or a 1-D uint32 / uint64 column.
+    dmask:  host numpy uint64 bitmap over the key positions (the D-bitmap).
+    """
+
+    def __init__(self, keys: torch.Tensor, dmask: np.ndarray, fanout: int = 64, fill: float = 1.0,
+                 digit_bits: int = 8, ck_words: int | None = None, kind: int | None = None):
+        self.keys = keys
+        self.kind = kind
+        self.col = ck.column(keys, kind)
+        self.n = int(self.col.n)
+        self.key_bits = 8 * int(self.col.key_bytes)
+        self.dmask = np.ascontiguousarray(np.asarray(dmask, np.uint64))
+        self.nbits = ck.popcount(self.dmask)
+        self.K = ck_words or ck.words_for(self.nbits)
+        self.fanout, self.fill, self.digit_bits = fanout, fill, digit_bits
+        dev = keys.device
+        n = max(self.n, 1)
+        self.ck_in = ck.ck_buffer(self.K, n, dev)
+        self.ck_sorted = ck.ck_buffer(self.K, n, dev)
+        self.rid_sorted = torch.empty(n, dtype=torch.int32, device=dev)
+        wsb = ck.ck_sort_workspace_bytes(self.n, self.K, self.nbits, digit_bits)
+        self.ws = torch.empty(max(wsb, 256), dtype=torch.uint8, device=dev)
+        self.shape = ck.ck_btree_plan(self.n, fanout, fill)
+        self.tree = ck.alloc_btree(self.shape, self.K, dev)
+        self.refined = torch.empty(ck.mask_words(self.key_bits), dtype=torch.int64, device=dev)
+
+    def extract(self, stream=None):
+        ck.ck_extract(self.keys, self.dmask, self.K, out=self.ck_in, kind=self.kind, stream=stream)
+
+    def sort(self, stream=None):
+        ck.ck_sort(self.ck_in, None, self.ck_sorted, self.rid_sorted, self.n, self.K, self.nbits, self.ws,
+                   digit_bits=self.digit_bits, stream=stream)
+
+    def build(self, stream=None):
+        ck.ck_build_index(self.ck_sorted, self.rid_sorted, self.n, self.K, self.dmask, self.key_bits, self.fanout,
+                          self.fill, arrays=self.tree, refined_out=self.refined, stream=stream)
+
+    def run(self, stream=None):
+        """One full rebuild: extract, sort, bulk load (+ refined D-bitmap)."""
+        self.extract(stream)
+        self.sort(stream)
+        self.build(stream)
+
+    def launches_per_run(self) -> int:
+        passes = (self.nbits + self.digit_bits - 1) // self.digit_bits
+        if passes == 0:
+            return 1 + 1 + (2 if self.shape.inner_entries else 1)
+        bins = 1 << self.digit_bits
+        chunk = 65536 // (4 * bins)
+        up = (passes + chunk - 1) // chunk
+        btree = 1 + (1 if self.shape.inner_entries else 0)
+        return 1 + up + 1 + passes + btree
+
+
+def full_key_mask(key_bits: int) -> np.ndarray:
+    """Bitmap with every key position set: Compress is then the key itself,
+    and the same kernels sort the full keys (the full-key baseline)."""
+    m = np.zeros(ck.mask_words(key_bits), np.uint64)
+    for p in range(key_bits):
+        m[p // 64] |= np.uint64(1 << (63 - p % 64))
+    return m
+
+
+def first_build_dmask(keys: torch.Tensor, kind: int | None = None, digit_bits: int = 8) -> np.ndarray:
+    """D-bitmap of a column with no stored DS-metadata: variant bitmap ->
+    extract -> sort -> refine (all on the GPU)."""
+    variant = ck.mask_to_host(ck.ck_variant_bits(keys, 0, kind=kind))
+    r = Rebuild(keys, variant, digit_bits=digit_bits, kind=kind)
+    r.run()
+    return ck.mask_to_host(r.refined)

@@ -1,0 +1,133 @@
+"""Host-side checks that need no GPU: the C ABI library loads and exports every
+function include/ck.h declares, the host planning code agrees with the
+oracle and the closed forms, argument errors come back synchronously, and the
+reported metric formulas reproduce Table 2 of the paper."""
+import json
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def ckmod():
+    from paper_2009_11543_gb300 import build as b
+    b.build()
+    from paper_2009_11543_gb300 import ck
+    return ck
+
+
+def header_functions():
+    src = open(os.path.join(ROOT, "include", "ck.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(ck_[a-z0-9_]+)\s*\(", src)))
+
+
+def test_every_declared_symbol_is_exported(ckmod):
+    lib = ckmod._lib()
+    names = header_functions()
+    assert "ck_sort" in names and "ck_extract" in names
+    for name in names:
+        assert hasattr(lib, name), name
+    assert sorted(ckmod.EXPORTED) == names
+
+
+def pext32(x, m):
+    out, k = 0, 0
+    for b in range(32):
+        if (m >> b) & 1:
+            out |= ((x >> b) & 1) << k
+            k += 1
+    return out
+
+
+def test_compress_network_matches_pext(ckmod):
+    rng = np.random.default_rng(0)
+    masks = [0, 0xFFFFFFFF, 0x80000001, 0x0F0F0F0F, 0x00000001, 0x80000000] + \
+            [int(x) for x in rng.integers(0, 2**32, 300, dtype=np.uint64)]
+    for m in masks:
+        for x in [0, 0xFFFFFFFF] + [int(v) for v in rng.integers(0, 2**32, 20, dtype=np.uint64)]:
+            assert ckmod.ck_compress_word_host(x, m) == pext32(x, m)
+
+
+def test_btree_plan_matches_oracle(ckmod):
+    for n in (0, 1, 2, 14, 15, 1000, 4097, 10**6, 200 * 10**6):
+        for fanout, fill in ((64, 1.0), (256, 1.0), (14, 0.9), (9, 0.9), (10, 0.7)):
+            s = ckmod.ck_btree_plan(n, fanout, fill)
+            f = oracle.entries_per_node(fanout, fill)
+            assert s.entries_per_node == f
+            lv = oracle.btree_shape(n, f)
+            assert s.levels == len(lv)
+            assert [int(s.level_entries[i]) for i in range(s.levels)] == lv
+            off = 0
+            for l in range(1, s.levels):
+                assert s.inner_offset[l] == off
+                off += lv[l]
+            assert s.inner_entries == off
+
+
+def test_argument_errors_are_synchronous(ckmod):
+    import ctypes
+    lib = ckmod._lib()
+    col = ckmod.ck_column(0, 10, 8, 8, ckmod.CK_KIND_BYTES)          # NULL keys with n > 0
+    m = np.zeros(1, np.uint64)
+    assert lib.ck_extract(ctypes.byref(col), m.ctypes.data, 1, None, None) == ckmod.CK_EINVAL
+    col = ckmod.ck_column(4096, 10, 8, 4, ckmod.CK_KIND_BYTES)       # stride < key bytes
+    assert lib.ck_variant_bits(ctypes.byref(col), 0, 4096, None) == ckmod.CK_EINVAL
+    col = ckmod.ck_column(4096, 10, 600, 600, ckmod.CK_KIND_BYTES)   # key too wide
+    assert lib.ck_distinction_bits(ctypes.byref(col), None, 4096, None) == ckmod.CK_EINVAL
+    col = ckmod.ck_column(4096, 10, 8, 8, ckmod.CK_KIND_U32)         # U32 needs 4 bytes
+    assert lib.ck_distinction_bits(ctypes.byref(col), None, 4096, None) == ckmod.CK_EINVAL
+    col = ckmod.ck_column(4096, 10, 4, 4, ckmod.CK_KIND_BYTES)
+    m = np.array([0xFFFFFFFFF0000000], np.uint64)                    # 36 set bits > 32 * 1 word
+    assert lib.ck_extract(ctypes.byref(col), m.ctypes.data, 1, 4096, None) in (ckmod.CK_EINVAL,)
+    m = np.array([0xFFFFFFFF00000000], np.uint64)
+    col = ckmod.ck_column(4096, 10, 8, 8, ckmod.CK_KIND_BYTES)
+    m2 = np.array([0xFFFFFFFF80000000], np.uint64)                   # 33 bits into 1 word
+    assert lib.ck_extract(ctypes.byref(col), m2.ctypes.data, 1, 4096, None) == ckmod.CK_EOVERFLOW
+    o = ckmod.ck_sort_opts(3, 0, 0, 0)                               # digit width out of range
+    assert lib.ck_sort(4096, None, 8192, 12288, 100, 1, 20, ctypes.byref(o), None, 0, None) == ckmod.CK_EINVAL
+    o = ckmod.ck_sort_opts(8, 0, 0, 0)
+    assert lib.ck_sort(4096, None, 8192, 12288, 100, 1, 20, ctypes.byref(o), None, 0, None) == ckmod.CK_ENOMEM
+    assert lib.ck_sort(4096, None, 8192, 12288, 100, 1, 40, ctypes.byref(o), None, 0, None) == ckmod.CK_EINVAL
+    assert lib.ck_sort(4096, None, 8192, 12288, 1 << 30, 1, 20, None, None, 0, None) == ckmod.CK_EINVAL
+    s = ckmod.ck_btree_shape()
+    assert lib.ck_btree_plan(100, 1, ctypes.c_float(1.0), ctypes.byref(s)) == ckmod.CK_EINVAL
+
+
+def test_workspace_size_formula(ckmod):
+    n, K, nbits = 10**6, 4, 120
+    ws = ckmod.ck_sort_workspace_bytes(n, K, nbits, 8)
+    tiles = (n + 4095) // 4096
+    passes = 15
+    ld = ckmod.CK_LD(n)
+    assert ld % 64 == 0 and ld >= n
+    body = 4 * K * ld + 4 * n + 4 * 256 * tiles * passes
+    assert body <= ws < body + 4 * 256 * passes + 4 * passes + 5 * 256
+
+
+def test_table2_metric_formulas():
+    from paper_2009_11543_gb300 import metrics as mt
+    with open(os.path.join(ROOT, "tests", "golden", "table2_dataset_stats.json")) as f:
+        g = json.load(f)
+    crs, skrs = [], []
+    for i in range(6):
+        cr = mt.compression_ratio(g["full_key_bits"][i], g["distinction_bits"][i])
+        assert round(cr, 2) == g["compression_ratio"][i]
+        fb = mt.full_sort_key_bytes(g["max_key_length_bytes"][i], g["record_id_bytes"])
+        cb = mt.compressed_sort_key_bytes(g["distinction_bits"][i], g["record_id_variant_bits"][i])
+        assert fb == g["full_sort_key_bytes"][i]
+        assert cb == g["compressed_sort_key_bytes"][i]
+        skr = mt.sort_key_ratio(fb, cb)
+        assert round(skr, 2) == g["sort_key_ratio"][i]
+        crs.append(cr)
+        skrs.append(skr)
+    assert round(sum(crs) / 6, 2) == g["average_compression_ratio"]
+    assert round(sum(skrs) / 6, 2) == g["average_sort_key_ratio"]
+    frac = sum(d / f for d, f in zip(g["distinction_bits"], g["full_key_bits"])) / 6
+    assert round(100 * frac, 1) == g["average_distinction_fraction_percent"]
