@@ -160,6 +160,31 @@ ck_status ck_sort(const uint32_t* ck_in, const uint32_t* rid_in, uint32_t* ck_ou
                   size_t ws_bytes, ck_stream stream);
 
 /* ---------------------------------------------------------------------------
+ * ck_sort_static -- the same sort as ck_sort, for callers that cannot allocate
+ * device memory: its scratch lives in one fixed device array inside the
+ * library instead of a caller workspace.  The paper has no counterpart; it
+ * exists because some hosts of this library own all device memory through
+ * their own memory manager and forbid their components to call cudaMalloc,
+ * and because cudaMalloc / cudaFree can synchronise the whole device, which a
+ * latency-bound rebuild path cannot afford.
+ *   Arguments, outputs and errors are those of ck_sort without ws / ws_bytes.
+ *   Limit: the call is accepted only if ck_sort_workspace_bytes(n, ck_words,
+ *   nbits, opts) <= CK_SORT_STATIC_SCRATCH_BYTES (32 MiB, about 1.4M pairs of
+ *   128-bit keys); larger sorts return CK_ENOMEM without launching anything
+ *   and should use ck_sort with a workspace.
+ *   The array is allocated once per GPU when the library is loaded and held
+ *   until the process exits.  The first call on each device looks up the
+ *   array's device address (with that device current); make that first call
+ *   before any stream capture.  Every call on a device uses the same array:
+ *   calls whose execution overlaps on the GPU (other streams, other threads)
+ *   race and give wrong results, so serialise them.  Nothing is allocated or
+ *   freed by the call. */
+#define CK_SORT_STATIC_SCRATCH_BYTES (32u << 20)
+
+ck_status ck_sort_static(const uint32_t* ck_in, const uint32_t* rid_in, uint32_t* ck_out, uint32_t* rid_out,
+                         uint64_t n, uint32_t ck_words, uint32_t nbits, const ck_sort_opts* opts, ck_stream stream);
+
+/* ---------------------------------------------------------------------------
  * Index tree (Sec. 4.2 structure, Sec. 5.3 bottom-up build).  Canonical
  * layout: each node holds f = max(1, floor(fanout * fill)) consecutive entries
  * (the last node of a level may hold fewer).  Level 0 has one entry per key in

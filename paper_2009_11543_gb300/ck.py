@@ -27,7 +27,8 @@ CK_INJECT_STALL_FIRST_TILE = 1
 
 EXPORTED = ["ck_variant_bits", "ck_distinction_bits", "ck_extract", "ck_sort_workspace_bytes", "ck_sort",
             "ck_btree_plan", "ck_build_index", "ck_device_status", "ck_clear_device_status",
-            "ck_status_string", "ck_launch_count", "ck_compress_word_host"]
+            "ck_status_string", "ck_launch_count", "ck_compress_word_host", "ck_sort_static"]
+CK_SORT_STATIC_SCRATCH_BYTES = 32 << 20
 
 
 class CkError(RuntimeError):
@@ -77,6 +78,7 @@ def _lib():
         lib.ck_sort_workspace_bytes.argtypes = [U64, U32, U32, ctypes.POINTER(ck_sort_opts)]
         lib.ck_sort_workspace_bytes.restype = ctypes.c_size_t
         lib.ck_sort.argtypes = [P, P, P, P, U64, U32, U32, ctypes.POINTER(ck_sort_opts), P, ctypes.c_size_t, P]
+        lib.ck_sort_static.argtypes = [P, P, P, P, U64, U32, U32, ctypes.POINTER(ck_sort_opts), P]
         lib.ck_btree_plan.argtypes = [U64, U32, ctypes.c_float, ctypes.POINTER(ck_btree_shape)]
         lib.ck_build_index.argtypes = [P, P, U64, U32, P, U32, U32, ctypes.c_float, ctypes.POINTER(ck_btree), P, P]
         lib.ck_device_status.argtypes = [ctypes.POINTER(U64)]
@@ -213,6 +215,15 @@ def ck_sort(ck_in: torch.Tensor, rid_in: torch.Tensor | None, ck_out: torch.Tens
               ctypes.cast(pass_events, ctypes.c_void_p) if pass_events is not None else None)
     _check(_lib().ck_sort(_ptr(ck_in), _ptr(rid_in), _ptr(ck_out), _ptr(rid_out), n, ck_words, nbits,
                           ctypes.byref(o), _ptr(ws), ws.numel() * ws.element_size(), _stream(stream)), "ck_sort")
+
+
+def ck_sort_static(ck_in: torch.Tensor, rid_in: torch.Tensor | None, ck_out: torch.Tensor, rid_out: torch.Tensor,
+                   n: int, ck_words: int, nbits: int, digit_bits: int = 0, stream=None) -> None:
+    """ck_sort without a caller workspace: the library's fixed scratch array is
+    used instead (for callers that cannot allocate device memory; see ck.h)."""
+    o = _opts(digit_bits)
+    _check(_lib().ck_sort_static(_ptr(ck_in), _ptr(rid_in), _ptr(ck_out), _ptr(rid_out), n, ck_words, nbits,
+                                 ctypes.byref(o), _stream(stream)), "ck_sort_static")
 
 
 def ck_btree_plan(n: int, fanout: int, fill: float = 1.0) -> ck_btree_shape:
