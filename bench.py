@@ -74,13 +74,13 @@ def file_sha(path: str) -> str:
         return hashlib.sha256(f.read()).hexdigest()[:16]
 
 
-def ncu_traffic(n: int):
+def ncu_traffic(n: int, ck_words: int):
     """DRAM bytes per pass launch from the committed ncu summary, scaled to n
     keys, if the pass kernel's source is unchanged since the capture."""
     try:
         with open(TRAFFIC_FILE) as f:
             t = json.load(f)
-        if t.get("kernel_src_sha") != file_sha(SORT_SRC):
+        if t.get("kernel_src_sha") != file_sha(SORT_SRC) or t.get("ck_words") != ck_words:
             return None
         return t["dram_bytes_per_launch"] * n / t["n"]
     except Exception:
@@ -186,7 +186,7 @@ def run_ours(args, rank, world, local_rank):
         barrier()
         launches = ck.ck_launch_count() - l0
         total_ms = start.elapsed_time(end)
-        pass_ms = [ev[s][q].elapsed_time(ev[s][q + 1]) for s in range(steps) for q in range(pass_count)]
+        pass_ms = [[ev[s][q].elapsed_time(ev[s][q + 1]) for q in range(pass_count)] for s in range(steps)]
         phase = [[ph[s][i].elapsed_time(ph[s][i + 1]) for i in range(3)] for s in range(steps)]
         return total_ms, pass_ms, phase, launches
 
@@ -199,8 +199,7 @@ def run_ours(args, rank, world, local_rank):
             ph[0].record(stream)
             r.extract()
             ph[1].record(stream)
-            ck.ck_sort(r.ck_in, None, r.ck_sorted, r.rid_sorted, r.n, r.K, r.nbits, r.ws, digit_bits=r.digit_bits,
-                       pass_events=evh)
+            r.sort(pass_events=evh)
             ph[2].record(stream)
             r.build()
             ph[3].record(stream)
@@ -251,15 +250,19 @@ def run_ours(args, rank, world, local_rank):
     f_ms_step = f_total_ms / max(1, args.steps // 2)
     value = world * n / (ms_step / 1e3)
     peak, peak_src = peaks()
-    avg_pass_ms = float(np.mean(pass_ms))
-    pb = metrics.pass_bytes(n, R.K)
-    achieved = pb / (avg_pass_ms / 1e3) / 1e9
-    traffic = ncu_traffic(n)
+    # achieved = all passes' algorithmic bytes / all passes' time
+    sort_bytes = passes * metrics.pass_bytes(n, R.K)
+    pass_total_ms = float(np.mean([sum(p) for p in pass_ms]))
+    avg_pass_ms = pass_total_ms / passes
+    pb = sort_bytes / passes
+    achieved = sort_bytes / (pass_total_ms / 1e3) / 1e9
+    traffic = ncu_traffic(n, R.K)
     ph = np.mean(np.array(phase), axis=0)
     fph = np.mean(np.array(f_phase), axis=0)
-    alg = metrics.extract_sort_alg_bytes(n, key_bytes, R.K, passes)
-    f_alg = metrics.extract_sort_alg_bytes(n, key_bytes, F.K, fpasses)
-    f_pass_gbs = metrics.pass_bytes(n, F.K) / (float(np.mean(f_pass_ms)) / 1e3) / 1e9
+    alg = metrics.extract_bytes(n, key_bytes, R.K) + sort_bytes
+    f_sort_bytes = fpasses * metrics.pass_bytes(n, F.K)
+    f_alg = metrics.extract_bytes(n, key_bytes, F.K) + f_sort_bytes
+    f_pass_gbs = f_sort_bytes / (float(np.mean([sum(p) for p in f_pass_ms])) / 1e3) / 1e9
     line = {
         "metric": METRIC,
         "value": value,
@@ -277,8 +280,8 @@ def run_ours(args, rank, world, local_rank):
                    "ck_words": R.K, "digit_bits": args.digit_bits, "radix_passes": passes, "fanout": fanout,
                    "tree_levels": int(R.shape.levels), "l2": "inputs larger than L2 (no flush)",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
-        "roofline": {"bound": "hbm", "kernel": "onesweep_pass_kernel<8>", "achieved": achieved, "peak": peak,
-                     "peak_source": peak_src, "unit": "GB/s", "frac": achieved / peak,
+        "roofline": {"bound": "hbm", "kernel": "onesweep_pass_kernel<%d>" % args.digit_bits, "achieved": achieved,
+                     "peak": peak, "peak_source": peak_src, "unit": "GB/s", "frac": achieved / peak,
                      "traffic": traffic, "alg_bytes_per_launch": pb, "avg_launch_ms": avg_pass_ms},
         "phases_ms": {"extract": float(ph[0]), "sort": float(ph[1]), "build": float(ph[2])},
         "extract_sort_roofline_frac": alg / ((ph[0] + ph[1]) / 1e3) / 1e9 / peak,

@@ -141,12 +141,19 @@ typedef struct ck_sort_opts {
     uint32_t digit_bits; /* radix digit width, 4 .. 11; 0 = 8 */
     uint32_t spin_limit; /* polls per look-back wait before giving up; 0 = default (~1 s) */
     uint32_t inject;     /* test-only fault injection (CK_INJECT_*); 0 in production */
-    uint32_t reserved;   /* must be 0 */
+    uint32_t flags;      /* CK_SORT_* bits; 0 = default */
     void* pass_events;   /* optional profiling hook: cudaEvent_t[passes + 1]; event 0 is
                             recorded on the stream before the first digit pass and event
                             p + 1 after pass p (passes = ceil(nbits / digit_bits)).  NULL
                             records nothing. */
 } ck_sort_opts;
+
+/* Only the permutation is wanted: ck_out is used as scratch and its contents
+ * are unspecified on return (rid_out is the result).  Each pass then stops
+ * carrying the key words whose digits have all been consumed, which cuts the
+ * bytes moved per key. */
+#define CK_SORT_PERM_ONLY 1u
+#define CK_SORT_FLAGS_ALL 1u
 
 /* The first tile of the first pass never publishes its look-back entries, so
  * the second tile's wait runs out: exercises the CK_ETIMEOUT path without any
@@ -241,6 +248,23 @@ typedef struct ck_btree {
 ck_status ck_build_index(const uint32_t* sorted_ck, const uint32_t* sorted_rid, uint64_t n, uint32_t ck_words,
                          const uint64_t* dmask, uint32_t key_bits, uint32_t fanout, float fill, ck_btree* tree,
                          uint64_t* refined_mask, ck_stream stream);
+
+/* ---------------------------------------------------------------------------
+ * ck_build_index_keys -- the same tree as ck_build_index, built from the key
+ * column and the sorted row ids only (for instance after ck_sort with
+ * CK_SORT_PERM_ONLY).  A leaf's D-bit is computed on the two full keys it
+ * compares (gathered by row id); by Sec. 5.3 this is the value D-offset maps
+ * the compressed D-bit to, so the tree and the refined D-bitmap are
+ * identical.  Inner entries' compressed highest keys are extracted with dmask.
+ *   col         the key column (device) the row ids refer to.
+ *   sorted_rid  device, n row ids in ascending key order (ties by row id).
+ *   dmask       HOST, ceil(8 * key_bytes / 64) words (as given to ck_extract).
+ *   ck_words, fanout, fill, tree, refined_mask: as ck_build_index.
+ * Errors: CK_EINVAL, CK_EOVERFLOW; a row id >= n is skipped and recorded as
+ * CK_EINVAL in the device status word. */
+ck_status ck_build_index_keys(const ck_column* col, const uint32_t* sorted_rid, const uint64_t* dmask,
+                              uint32_t ck_words, uint32_t fanout, float fill, ck_btree* tree, uint64_t* refined_mask,
+                              ck_stream stream);
 
 /* ---------------------------------------------------------------------------
  * Device status.  ck_device_status synchronises the device, returns the first

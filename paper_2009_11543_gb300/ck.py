@@ -24,10 +24,11 @@ CK_MAX_KEY_BYTES = 512
 CK_NO_DBIT = 0xFFFF
 CK_MAX_LEVELS = 32
 CK_INJECT_STALL_FIRST_TILE = 1
+CK_SORT_PERM_ONLY = 1
 
 EXPORTED = ["ck_variant_bits", "ck_distinction_bits", "ck_extract", "ck_sort_workspace_bytes", "ck_sort",
             "ck_btree_plan", "ck_build_index", "ck_device_status", "ck_clear_device_status",
-            "ck_status_string", "ck_launch_count", "ck_compress_word_host", "ck_sort_static"]
+            "ck_status_string", "ck_launch_count", "ck_compress_word_host", "ck_sort_static", "ck_build_index_keys"]
 CK_SORT_STATIC_SCRATCH_BYTES = 32 << 20
 
 
@@ -44,7 +45,7 @@ class ck_column(ctypes.Structure):
 
 class ck_sort_opts(ctypes.Structure):
     _fields_ = [("digit_bits", ctypes.c_uint32), ("spin_limit", ctypes.c_uint32), ("inject", ctypes.c_uint32),
-                ("reserved", ctypes.c_uint32), ("pass_events", ctypes.c_void_p)]
+                ("flags", ctypes.c_uint32), ("pass_events", ctypes.c_void_p)]
 
 
 class ck_btree_shape(ctypes.Structure):
@@ -81,6 +82,7 @@ def _lib():
         lib.ck_sort_static.argtypes = [P, P, P, P, U64, U32, U32, ctypes.POINTER(ck_sort_opts), P]
         lib.ck_btree_plan.argtypes = [U64, U32, ctypes.c_float, ctypes.POINTER(ck_btree_shape)]
         lib.ck_build_index.argtypes = [P, P, U64, U32, P, U32, U32, ctypes.c_float, ctypes.POINTER(ck_btree), P, P]
+        lib.ck_build_index_keys.argtypes = [CP, P, P, U32, U32, ctypes.c_float, ctypes.POINTER(ck_btree), P, P]
         lib.ck_device_status.argtypes = [ctypes.POINTER(U64)]
         lib.ck_status_string.argtypes = [I]
         lib.ck_status_string.restype = ctypes.c_char_p
@@ -191,8 +193,8 @@ def ck_extract(keys: torch.Tensor, dmask: np.ndarray, ck_words: int | None = Non
     return out
 
 
-def _opts(digit_bits=0, spin_limit=0, inject=0, pass_events=None):
-    return ck_sort_opts(digit_bits, spin_limit, inject, 0, pass_events)
+def _opts(digit_bits=0, spin_limit=0, inject=0, pass_events=None, flags=0):
+    return ck_sort_opts(digit_bits, spin_limit, inject, flags, pass_events)
 
 
 def event_handles(events) -> ctypes.Array:
@@ -210,9 +212,10 @@ def ck_sort_workspace_bytes(n: int, ck_words: int, nbits: int, digit_bits: int =
 
 def ck_sort(ck_in: torch.Tensor, rid_in: torch.Tensor | None, ck_out: torch.Tensor, rid_out: torch.Tensor, n: int,
             ck_words: int, nbits: int, ws: torch.Tensor, digit_bits: int = 0, spin_limit: int = 0, inject: int = 0,
-            pass_events=None, stream=None) -> None:
+            pass_events=None, perm_only: bool = False, stream=None) -> None:
     o = _opts(digit_bits, spin_limit, inject,
-              ctypes.cast(pass_events, ctypes.c_void_p) if pass_events is not None else None)
+              ctypes.cast(pass_events, ctypes.c_void_p) if pass_events is not None else None,
+              CK_SORT_PERM_ONLY if perm_only else 0)
     _check(_lib().ck_sort(_ptr(ck_in), _ptr(rid_in), _ptr(ck_out), _ptr(rid_out), n, ck_words, nbits,
                           ctypes.byref(o), _ptr(ws), ws.numel() * ws.element_size(), _stream(stream)), "ck_sort")
 
@@ -258,6 +261,23 @@ def ck_build_index(sorted_ck: torch.Tensor, sorted_rid: torch.Tensor, n: int, ck
     m = np.ascontiguousarray(np.asarray(dmask, np.uint64))
     _check(_lib().ck_build_index(_ptr(sorted_ck), _ptr(sorted_rid), n, ck_words, _ptr(m), key_bits, fanout, fill,
                                  ctypes.byref(t), _ptr(refined_out), _stream(stream)), "ck_build_index")
+    return t.shape, arrays
+
+
+def ck_build_index_keys(keys: torch.Tensor, sorted_rid: torch.Tensor, dmask: np.ndarray, ck_words: int, fanout: int,
+                        fill: float = 1.0, arrays: dict | None = None, refined_out: torch.Tensor | None = None,
+                        kind=None, stream=None):
+    """Returns (shape, arrays); arrays are allocated when not given."""
+    col = column(keys, kind)
+    shape = ck_btree_plan(col.n, fanout, fill)
+    if arrays is None:
+        arrays = alloc_btree(shape, ck_words, keys.device)
+    t = ck_btree()
+    for name, tensor in arrays.items():
+        setattr(t, name, tensor.data_ptr())
+    m = np.ascontiguousarray(np.asarray(dmask, np.uint64))
+    _check(_lib().ck_build_index_keys(ctypes.byref(col), _ptr(sorted_rid), _ptr(m), ck_words, fanout, fill,
+                                      ctypes.byref(t), _ptr(refined_out), _stream(stream)), "ck_build_index_keys")
     return t.shape, arrays
 
 

@@ -126,6 +126,34 @@ static bool mask_fits(const uint64_t* mask, uint32_t key_bits) {
 
 static ck_status cuda_status(cudaError_t e) { return e == cudaSuccess ? CK_OK : CK_ECUDA; }
 
+// Extraction plan of a D-bitmap: per 32-bit key word its mask, the move masks
+// of its compress network and its popcount, plus the output padding.  With no
+// set bit, first_word > last_word and only the leading zero words are written.
+bool make_extract_plan(const KeyDesc& k, const uint64_t* dmask, uint32_t ck_words, ExtractPlan* plan) {
+    memset(plan, 0, sizeof(*plan));
+    const uint32_t nbits = popcount64(dmask, 8 * k.key_bytes);
+    if (nbits > 32u * ck_words) return false;
+    plan->K = ck_words;
+    const uint32_t used = (nbits + 31) / 32;
+    plan->lead_zero_words = ck_words - used;
+    plan->pad_bits = 32 * used - nbits;
+    plan->first_word = 0xFFFFFFFFu;
+    plan->last_word = 0;
+    for (uint32_t w = 0; w < k.nwords; ++w) {
+        const uint64_t mw = dmask[w / 2];
+        const uint32_t m = (w % 2 == 0) ? (uint32_t)(mw >> 32) : (uint32_t)mw;
+        plan->mask[w] = m;
+        if (!m) continue;
+        uint32_t mv[5];
+        compress_network(m, mv);
+        for (int st = 0; st < 5; ++st) plan->mv[st][w] = mv[st];
+        plan->pc[w] = (uint8_t)__builtin_popcount(m);
+        if (plan->first_word == 0xFFFFFFFFu) plan->first_word = w;
+        plan->last_word = w;
+    }
+    return true;
+}
+
 }  // namespace ck
 
 using namespace ck;
@@ -167,25 +195,7 @@ ck_status ck_extract(const ck_column* col, const uint64_t* dmask, uint32_t ck_wo
     if (nbits == 0)
         return cuda_status(cudaMemsetAsync(ck_out, 0, sizeof(uint32_t) * (size_t)ck_words * CK_LD(col->n), s));
     static thread_local ExtractPlan plan;  // ~3 KB; passed to the kernel by value
-    memset(&plan, 0, sizeof(plan));
-    plan.K = ck_words;
-    const uint32_t used = (nbits + 31) / 32;
-    plan.lead_zero_words = ck_words - used;
-    plan.pad_bits = 32 * used - nbits;
-    plan.first_word = 0xFFFFFFFFu;
-    plan.last_word = 0;
-    for (uint32_t w = 0; w < k.nwords; ++w) {
-        const uint64_t mw = dmask[w / 2];
-        const uint32_t m = (w % 2 == 0) ? (uint32_t)(mw >> 32) : (uint32_t)mw;
-        plan.mask[w] = m;
-        if (!m) continue;
-        uint32_t mv[5];
-        compress_network(m, mv);
-        for (int st = 0; st < 5; ++st) plan.mv[st][w] = mv[st];
-        plan.pc[w] = (uint8_t)__builtin_popcount(m);
-        if (plan.first_word == 0xFFFFFFFFu) plan.first_word = w;
-        plan.last_word = w;
-    }
+    make_extract_plan(k, dmask, ck_words, &plan);
     return cuda_status(launch_extract(k, vec, col->n, CK_LD(col->n), plan, ck_out, s));
 }
 
@@ -199,7 +209,8 @@ ck_status ck_sort(const uint32_t* ck_in, const uint32_t* rid_in, uint32_t* ck_ou
                   uint32_t ck_words, uint32_t nbits, const ck_sort_opts* opts, void* ws, size_t ws_bytes,
                   ck_stream stream) {
     if (n > CK_MAX_ROWS || ck_words == 0 || nbits > 32u * ck_words) return CK_EINVAL;
-    if (opts && (opts->reserved != 0 || (opts->digit_bits != 0 && (opts->digit_bits < 4 || opts->digit_bits > 11))))
+    if (opts && ((opts->flags & ~CK_SORT_FLAGS_ALL) != 0 ||
+                 (opts->digit_bits != 0 && (opts->digit_bits < 4 || opts->digit_bits > 11))))
         return CK_EINVAL;
     if (n == 0) return CK_OK;
     if (!ck_in || !ck_out || !rid_out) return CK_EINVAL;
@@ -209,9 +220,10 @@ ck_status ck_sort(const uint32_t* ck_in, const uint32_t* rid_in, uint32_t* ck_ou
     if (p.passes > 0 && (reinterpret_cast<uintptr_t>(ws) & 255)) return CK_EINVAL;
     const uint32_t spin = (opts && opts->spin_limit) ? opts->spin_limit : (1u << 22);
     const uint32_t inject = opts ? opts->inject : 0u;
+    const uint32_t flags = opts ? opts->flags : 0u;
     if (!status_ptr()) return CK_ECUDA;
     cudaEvent_t* ev = opts ? static_cast<cudaEvent_t*>(opts->pass_events) : nullptr;
-    return cuda_status(run_sort(p, ck_in, rid_in, ck_out, rid_out, n, nbits, spin, inject, ev,
+    return cuda_status(run_sort(p, ck_in, rid_in, ck_out, rid_out, n, nbits, spin, inject, flags, ev,
                                 static_cast<unsigned char*>(ws), reinterpret_cast<cudaStream_t>(stream)));
 }
 
@@ -275,6 +287,36 @@ ck_status ck_build_index(const uint32_t* sorted_ck, const uint32_t* sorted_rid, 
     const uint32_t words = (key_bits + 63) / 64;
     for (uint32_t i = 0; i < words; ++i) a.dmask[i] = dmask[i];
     return cuda_status(launch_btree(a, shape, tree, refined_mask, reinterpret_cast<cudaStream_t>(stream)));
+}
+
+ck_status ck_build_index_keys(const ck_column* col, const uint32_t* sorted_rid, const uint64_t* dmask,
+                              uint32_t ck_words, uint32_t fanout, float fill, ck_btree* tree, uint64_t* refined_mask,
+                              ck_stream stream) {
+    KeyDesc k;
+    int vec = 1;
+    if (!make_key_desc(col, &k, &vec) || !dmask || ck_words == 0 || !tree) return CK_EINVAL;
+    const uint32_t key_bits = 8 * k.key_bytes;
+    if (!mask_fits(dmask, key_bits)) return CK_EINVAL;
+    if (popcount64(dmask, key_bits) > 32u * ck_words) return CK_EOVERFLOW;
+    ck_btree_shape shape;
+    ck_status st = ck_btree_plan(col->n, fanout, fill, &shape);
+    if (st != CK_OK) return st;
+    if (col->n > 0 && (!sorted_rid || !tree->leaf_rid || !tree->leaf_dbit || !tree->leaf_high)) return CK_EINVAL;
+    if (shape.inner_entries > 0 && (!tree->inner_child || !tree->inner_high || !tree->inner_high_rid ||
+                                    !tree->inner_high_ck || !tree->inner_dbit))
+        return CK_EINVAL;
+    tree->shape = shape;
+    if (!status_ptr()) return CK_ECUDA;
+    static thread_local ExtractPlan plan;
+    make_extract_plan(k, dmask, ck_words, &plan);
+    InnerLevels lv;
+    memset(&lv, 0, sizeof(lv));
+    lv.levels = shape.levels;
+    lv.inner_entries = shape.inner_entries;
+    for (uint32_t l = 0; l < CK_MAX_LEVELS; ++l) lv.offset[l] = shape.inner_offset[l];
+    return cuda_status(launch_btree_keys(k, vec, col->n, sorted_rid, shape.entries_per_node, lv,
+                                         shape.levels ? shape.level_nodes[0] : 0, plan, tree, refined_mask,
+                                         reinterpret_cast<cudaStream_t>(stream)));
 }
 
 ck_status ck_device_status(uint64_t* detail) {

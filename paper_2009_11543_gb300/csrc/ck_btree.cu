@@ -83,11 +83,7 @@ __global__ void __launch_bounds__(256) leaf_kernel(const __grid_constant__ Btree
     }
 }
 
-struct InnerShape {
-    uint32_t levels;
-    uint64_t inner_entries;
-    uint64_t offset[CK_MAX_LEVELS];  // start of level l in the inner arrays
-};
+using InnerShape = InnerLevels;
 
 __global__ void __launch_bounds__(256) inner_kernel(const __grid_constant__ BtreeArgs a,
                                                     const __grid_constant__ InnerShape sh, uint32_t* __restrict__ child,

@@ -185,6 +185,16 @@ cudaError_t launch_extract(const KeyDesc& k, int vec, uint64_t n, uint64_t ld, c
                            uint32_t* ck_out, cudaStream_t s);
 constexpr uint32_t kDefaultSpin = 1u << 22;  // polls before a device wait gives up
 
+struct InnerLevels {
+    uint32_t levels;
+    uint64_t inner_entries;
+    uint64_t offset[CK_MAX_LEVELS];  // start of level l in the inner arrays
+};
+cudaError_t launch_btree_keys(const KeyDesc& k, int vec, uint64_t n, const uint32_t* rid, uint32_t f,
+                              const InnerLevels& lv, uint64_t nodes0, const ExtractPlan& plan, ck_btree* t,
+                              uint64_t* refined, cudaStream_t s);
+bool make_extract_plan(const KeyDesc& k, const uint64_t* dmask, uint32_t ck_words, ExtractPlan* plan);
+
 struct SortPlan {
     uint32_t digit_bits, passes, tile, tiles, K;
     size_t off_hist, off_counter, off_lookback, off_alt_ck, off_alt_rid, total;
@@ -192,7 +202,7 @@ struct SortPlan {
 bool make_sort_plan(uint64_t n, uint32_t K, uint32_t nbits, uint32_t digit_bits, SortPlan* p);
 cudaError_t run_sort(const SortPlan& p, const uint32_t* ck_in, const uint32_t* rid_in, uint32_t* ck_out,
                      uint32_t* rid_out, uint64_t n, uint32_t nbits, uint32_t spin_limit, uint32_t inject,
-                     cudaEvent_t* pass_events, unsigned char* ws, cudaStream_t s);
+                     uint32_t flags, cudaEvent_t* pass_events, unsigned char* ws, cudaStream_t s);
 
 struct BtreeArgs {
     const uint32_t* ck;  // word-major, K words, leading dimension ld

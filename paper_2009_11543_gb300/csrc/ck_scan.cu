@@ -193,7 +193,8 @@ __global__ void __launch_bounds__(kExtractThreads) extract_kernel(const KeyDesc 
     const uint64_t tiles = (n + rows_per_tile - 1) / rows_per_tile;
     const uint64_t full_tiles = staged ? n / rows_per_tile : 0;  // tiles that arrive by bulk copy
     const uint32_t tid = threadIdx.x;
-    for (uint32_t w = plan.first_word + tid; w <= plan.last_word; w += kExtractThreads) {
+    for (uint32_t w = plan.first_word + tid; plan.first_word <= plan.last_word && w <= plan.last_word;
+         w += kExtractThreads) {
         WordPlan p;
         p.mask = plan.mask[w];
         for (int s = 0; s < 5; ++s) p.mv[s] = plan.mv[s][w];
@@ -247,6 +248,97 @@ __global__ void __launch_bounds__(kExtractThreads) extract_kernel(const KeyDesc 
     }
 }
 
+// ------------------------------------------------- bulk load from full keys
+// The tree of ck_build_index, built from the key column and the sorted row
+// ids alone (no sorted compressed keys): a leaf's D-bit is the D-bit of the
+// two full keys it compares, gathered by row id -- by Sec. 5.3 the same value
+// D-offset maps the compressed D-bit to -- and an inner entry's compressed
+// highest key is extracted from its full key on the spot.
+__device__ __forceinline__ void merge_bitmap_bits(const uint32_t* sm, uint32_t nwords32, uint64_t* out) {
+    merge_bitmap(sm, nwords32, out);
+}
+
+template <int VEC>
+__global__ void __launch_bounds__(256) leaf_keys_kernel(const KeyDesc k, uint64_t n, const uint32_t* __restrict__ rid,
+                                                        uint32_t f, uint32_t* __restrict__ leaf_rid,
+                                                        uint16_t* __restrict__ leaf_dbit,
+                                                        uint32_t* __restrict__ leaf_high, uint64_t nodes0,
+                                                        uint64_t* __restrict__ refined, unsigned long long* status) {
+    __shared__ uint32_t sm[kMaxKeyWords];
+    for (uint32_t i = threadIdx.x; i < k.nwords; i += blockDim.x) sm[i] = 0;
+    __syncthreads();
+    const uint32_t lane = threadIdx.x & 31;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t i0 = (uint64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31u); i0 < n; i0 += stride) {
+        const uint64_t i = i0 + lane;
+        int32_t p = -1;
+        if (i < n) {
+            const uint32_t b = rid[i];
+            leaf_rid[i] = b;
+            if (i > 0) {
+                const uint32_t a = rid[i - 1];
+                if (a < n && b < n) p = key_dbit<VEC>(k, a, b);
+                else report(status, CK_EINVAL, i);
+            }
+            leaf_dbit[i] = p >= 0 ? (uint16_t)p : (uint16_t)CK_NO_DBIT;
+            if (i < nodes0) leaf_high[i] = (uint32_t)(min((i + 1) * (uint64_t)f, n) - 1);
+        }
+        if (refined) warp_mark(sm, p);
+    }
+    if (!refined) return;
+    __syncthreads();
+    merge_bitmap(sm, k.nwords, refined);
+}
+
+template <int VEC>
+__global__ void __launch_bounds__(256) inner_keys_kernel(const KeyDesc k, uint64_t n, const uint32_t* __restrict__ rid,
+                                                         uint32_t f, const __grid_constant__ InnerLevels lv,
+                                                         const __grid_constant__ ExtractPlan plan,
+                                                         uint32_t* __restrict__ child, uint32_t* __restrict__ high,
+                                                         uint32_t* __restrict__ high_rid,
+                                                         uint32_t* __restrict__ high_ck, uint16_t* __restrict__ dbit,
+                                                         unsigned long long* status) {
+    __shared__ WordPlan wp[kMaxKeyWords];
+    for (uint32_t w = plan.first_word + threadIdx.x; plan.first_word <= plan.last_word && w <= plan.last_word;
+         w += blockDim.x) {
+        WordPlan q;
+        q.mask = plan.mask[w];
+        for (int s = 0; s < 5; ++s) q.mv[s] = plan.mv[s][w];
+        q.pc = plan.pc[w];
+        q.pad = 0;
+        wp[w] = q;
+    }
+    __syncthreads();
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t g = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; g < lv.inner_entries; g += stride) {
+        uint32_t l = 1;
+        while (l + 1 < lv.levels && g >= lv.offset[l + 1]) ++l;
+        const uint64_t e = g - lv.offset[l];
+        uint64_t span = 1;  // f^l, capped at n (a capped span only occurs when the level has one entry)
+        for (uint32_t t = 0; t < l; ++t) span = min(span * f, n);
+        const uint64_t hi = min((e + 1) * span, n) - 1;
+        const uint32_t r = rid[hi];
+        child[g] = (uint32_t)e;
+        high[g] = (uint32_t)hi;
+        high_rid[g] = r;
+        int32_t p = -1;
+        if (r < n) {
+            const unsigned char* rows[1] = {k.base + (uint64_t)r * k.stride};
+            const uint64_t rr[1] = {g * plan.K};
+            const bool valid[1] = {true};
+            extract_rows<VEC, 1>(k, rows, rr, valid, 1, plan, wp, high_ck);  // entry-major: ld = 1
+            if (e > 0) {
+                const uint32_t a = rid[e * span - 1];
+                if (a < n) p = key_dbit<VEC>(k, a, r);
+                else report(status, CK_EINVAL, e * span - 1);
+            }
+        } else {
+            report(status, CK_EINVAL, hi);
+        }
+        dbit[g] = p >= 0 ? (uint16_t)p : (uint16_t)CK_NO_DBIT;
+    }
+}
+
 // ------------------------------------------------------------------ launchers
 static unsigned grid_for(uint64_t n, unsigned threads) {
     const uint64_t want = (n + threads - 1) / threads;
@@ -275,6 +367,27 @@ cudaError_t launch_dbits(const KeyDesc& k, int vec, uint64_t n, const uint32_t* 
     const unsigned grid = grid_for(n, 256);
     CK_DISPATCH_VEC(vec, dbits_kernel, k, n, order, mask_out, status_ptr());
     count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_btree_keys(const KeyDesc& k, int vec, uint64_t n, const uint32_t* rid, uint32_t f,
+                              const InnerLevels& lv, uint64_t nodes0, const ExtractPlan& plan, ck_btree* t,
+                              uint64_t* refined, cudaStream_t s) {
+    if (refined) {
+        cudaError_t e = cudaMemsetAsync(refined, 0, sizeof(uint64_t) * ((8ull * k.key_bytes + 63) / 64), s);
+        if (e != cudaSuccess) return e;
+    }
+    if (n == 0) return cudaSuccess;
+    unsigned grid = grid_for(n, 256);
+    CK_DISPATCH_VEC(vec, leaf_keys_kernel, k, n, rid, f, t->leaf_rid, t->leaf_dbit, t->leaf_high, nodes0, refined,
+                    status_ptr());
+    count_launch();
+    if (lv.inner_entries > 0) {
+        grid = grid_for(lv.inner_entries, 256);
+        CK_DISPATCH_VEC(vec, inner_keys_kernel, k, n, rid, f, lv, plan, t->inner_child, t->inner_high,
+                        t->inner_high_rid, t->inner_high_ck, t->inner_dbit, status_ptr());
+        count_launch();
+    }
     return cudaGetLastError();
 }
 

@@ -30,6 +30,7 @@ constexpr int kPassThreads = 512;
 constexpr int kPassItems = 8;
 constexpr int kTile = kPassThreads * kPassItems;  // pairs per tile
 constexpr int kRing = 3;                          // staging buffers per block
+constexpr int kMaxPassArrays = kMaxKeyWords + 2;  // key words, row ids, one extra
 constexpr int kPassBlocksPerSM = 3;
 constexpr int kUpThreads = 256;
 
@@ -119,13 +120,20 @@ __global__ void iota_kernel(uint32_t* out, uint64_t n) {
 }
 
 // ------------------------------------------------------------------ pass
+// The arrays a pass moves, in staging order.  Array 0 (and array 1 when the
+// digit straddles two words) holds the digit.  A NULL source means the values
+// are the input positions (row ids 0..n-1; such an array takes no ring slot);
+// a NULL destination means the array is read for its digit but not carried on.
+struct PassArrays {
+    const uint32_t* src[kMaxPassArrays];
+    uint32_t* dst[kMaxPassArrays];
+};
+
 struct PassArgs {
-    const uint32_t* ck_in;  // word-major, leading dimension ld
-    uint32_t* ck_out;
-    const uint32_t* rid_in;  // NULL: row ids are the input positions
-    uint32_t* rid_out;
-    uint64_t n, ld;
-    uint32_t K, shift, bits, pass;
+    uint64_t n;
+    uint32_t narr;                // arrays in PassArrays
+    uint32_t sh, bits, straddle;  // digit = bits [sh, sh + bits) of array 0 (spilling into array 1)
+    uint32_t pass;
     uint32_t bulk;                // 1: every array is 16-byte aligned, full tiles stage by TMA
     const uint32_t* bucket_base;  // [BINS] of this pass
     uint32_t* lookback;           // [tiles][BINS] of this pass, zeroed
@@ -134,10 +142,9 @@ struct PassArgs {
     unsigned long long* status;
 };
 
-// Shared memory of one pass block: a ring of kRing staging buffers (one word
-// array of the tile each), per-warp digit counters, per-slot source position
-// and digit, per-digit tile counts and destinations, the staging order of the
-// arrays, and the ring's mbarriers.
+// Shared memory of one pass block: a ring of kRing staging buffers (one array
+// of the tile each), per-warp digit counters, per-slot source position,
+// per-digit tile counts and destinations, and the ring's mbarriers.
 template <int RB>
 struct PassSmem {
     static constexpr int BINS = 1 << RB, WARPS = kPassThreads / 32;
@@ -148,33 +155,26 @@ struct PassSmem {
     uint32_t tile_excl[BINS];
     int32_t dest_base[BINS];
     uint32_t scratch[WARPS + 2];
-    uint16_t order[kMaxKeyWords + 1];
+    int16_t use[kMaxPassArrays];  // staging sequence number of each array, -1 if not staged
     alignas(8) uint64_t bar[kRing];
 };
 
 template <int RB>
-__global__ void __launch_bounds__(kPassThreads, kPassBlocksPerSM) onesweep_pass_kernel(const PassArgs a) {
+__global__ void __launch_bounds__(kPassThreads, kPassBlocksPerSM)
+    onesweep_pass_kernel(const PassArgs a, const __grid_constant__ PassArrays arr) {
     constexpr int BINS = 1 << RB, WARPS = kPassThreads / 32, ITEMS = kPassItems, WITEMS = 32 * ITEMS;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     PassSmem<RB>& S = *reinterpret_cast<PassSmem<RB>*>(smem_raw);
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const uint64_t n = a.n;
-    const uint32_t wlo = a.shift >> 5, sh = a.shift & 31;
-    const bool straddle = sh + a.bits > 32;
-    // staging order: the digit word(s) first, then the other key words, then the
-    // row ids.  Row ids without an input array (0..n-1) are staged by nobody; they
-    // are last in the order, so no later item reuses their ring slot and its
-    // mbarrier phases stay in step.
-    const uint32_t M = a.K + 1;
+    const uint32_t sh = a.sh;
+    const bool straddle = a.straddle != 0;
+    const uint32_t M = a.narr;
     if (tid == 0) {
         S.scratch[WARPS + 1] = atomicAdd(a.tile_counter, 1u);
-        uint32_t m = 0;
-        S.order[m++] = (uint16_t)wlo;
-        if (straddle) S.order[m++] = (uint16_t)(wlo + 1);
-        for (uint32_t w = 0; w < a.K; ++w)
-            if (w != wlo && !(straddle && w == wlo + 1)) S.order[m++] = (uint16_t)w;
-        S.order[m++] = (uint16_t)a.K;
+        int16_t u = 0;
+        for (uint32_t m = 0; m < M; ++m) S.use[m] = arr.src[m] ? u++ : (int16_t)-1;
         for (int b = 0; b < kRing; ++b) mbar_init(&S.bar[b], 1);
         fence_mbar_init();
     }
@@ -185,36 +185,43 @@ __global__ void __launch_bounds__(kPassThreads, kPassBlocksPerSM) onesweep_pass_
     const uint32_t count = (uint32_t)min((uint64_t)kTile, n - tile_base);
     const bool bulk = a.bulk && count == (uint32_t)kTile;
 
-    auto src_of = [&](uint32_t arr) -> const uint32_t* {
-        return arr == a.K ? a.rid_in : a.ck_in + (uint64_t)arr * a.ld;
-    };
-    // stages item m of the order into ring buffer m % kRing
+    // array m lives in ring slot use[m] % kRing; its k-th use is phase k of that slot's barrier
+    auto buf_of = [&](uint32_t m) -> uint32_t* { return S.stage[S.use[m] % kRing]; };
     auto issue = [&](uint32_t m) {  // thread 0 only, bulk tiles only
-        const uint32_t* src = src_of(S.order[m]);
-        if (src) bulk_load(S.stage[m % kRing], src + tile_base, kTile * sizeof(uint32_t), &S.bar[m % kRing]);
+        if (arr.src[m])
+            bulk_load(buf_of(m), arr.src[m] + tile_base, kTile * sizeof(uint32_t), &S.bar[S.use[m] % kRing]);
     };
-    auto stage_plain = [&](uint32_t m) {  // all threads; caller synchronises
-        const uint32_t* src = src_of(S.order[m]);
-        if (src)
-            for (uint32_t e = tid; e < count; e += kPassThreads) S.stage[m % kRing][e] = src[tile_base + e];
+    auto stage_plain = [&](uint32_t m) {  // all threads; the caller synchronises
+        if (arr.src[m]) {
+            uint32_t* b = buf_of(m);
+            for (uint32_t e = tid; e < count; e += kPassThreads) b[e] = arr.src[m][tile_base + e];
+        }
     };
-    auto wait_item = [&](uint32_t m) {
-        const uint32_t* src = src_of(S.order[m]);
-        if (!src) return;
-        if (!mbar_wait(&S.bar[m % kRing], (m / kRing) & 1u, a.spin_limit))
+    auto wait_array = [&](uint32_t m) {
+        if (!arr.src[m]) return;
+        if (!mbar_wait(&S.bar[S.use[m] % kRing], (uint32_t)(S.use[m] / kRing) & 1u, a.spin_limit))
             report(a.status, CK_ETIMEOUT, (uint64_t)a.pass | ((uint64_t)tile << 16) | (1ull << 47));
     };
+    // the staged arrays whose use < kRing can all start now
+    const uint32_t staged_total = [&] {
+        uint32_t c = 0;
+        for (uint32_t m = 0; m < M; ++m) c += arr.src[m] ? 1u : 0u;
+        return c;
+    }();
 
     if (bulk) {
         if (tid == 0)
-            for (uint32_t m = 0; m < M && m < (uint32_t)kRing; ++m) issue(m);
-        wait_item(0);
-        if (straddle) wait_item(1);
+            for (uint32_t m = 0; m < M; ++m)
+                if (arr.src[m] && S.use[m] < kRing) issue(m);
+        wait_array(0);
+        if (straddle) wait_array(1);
     } else {
         stage_plain(0);
         if (straddle) stage_plain(1);
         __syncthreads();
     }
+    const uint32_t* dig0 = buf_of(0);
+    const uint32_t* dig1 = straddle ? buf_of(1) : dig0;
 
     // 1. digits of this warp's items, warp-striped: item j of lane l is e = warp*WITEMS + 32j + l
     const uint32_t dmask = (1u << a.bits) - 1u;
@@ -224,8 +231,8 @@ __global__ void __launch_bounds__(kPassThreads, kPassBlocksPerSM) onesweep_pass_
         const uint32_t e = warp * WITEMS + 32 * j + lane;
         uint32_t d = 0;
         if (e < count) {
-            d = S.stage[0][e] >> sh;
-            if (straddle) d |= S.stage[1][e] << (32 - sh);
+            d = dig0[e] >> sh;
+            if (straddle) d |= dig1[e] << (32 - sh);
             d &= dmask;
         }
         dr[j] = d;
@@ -305,7 +312,7 @@ __global__ void __launch_bounds__(kPassThreads, kPassBlocksPerSM) onesweep_pass_
     }
     __syncthreads();
     // this thread's slots tid + i*THREADS: source position and global destination
-    // (the digit is re-read from the staged digit word, still in ring slots 0/1)
+    // (the digit is re-read from the staged digit word(s), not refilled before this)
     uint32_t srcp[ITEMS], dst[ITEMS];
 #pragma unroll
     for (int i = 0; i < ITEMS; ++i) {
@@ -314,36 +321,57 @@ __global__ void __launch_bounds__(kPassThreads, kPassBlocksPerSM) onesweep_pass_
         dst[i] = 0;
         if (s < count) {
             const uint32_t e = S.src_pos[s];
-            uint32_t d = S.stage[0][e] >> sh;
-            if (straddle) d |= S.stage[1][e] << (32 - sh);
+            uint32_t d = dig0[e] >> sh;
+            if (straddle) d |= dig1[e] << (32 - sh);
             srcp[i] = e;
-            dst[i] = (uint32_t)(S.dest_base[d & dmask] + (int32_t)s);
+            dst[i] = (uint32_t)(S.dest_base[d & dmask] + (int32_t)s);  // < 2^30
         }
     }
+    __syncthreads();  // every thread has read the digit words; their slots may be refilled
 
-    // 6. every array in staging order: wait for it, scatter it, refill its buffer
+    // 6. every array in staging order: wait for it, scatter it, refill its ring slot
     for (uint32_t m = 0; m < M; ++m) {
+        const bool digit_array = m == 0 || (straddle && m == 1);
         if (bulk) {
-            if (m > 0 && !(straddle && m == 1)) wait_item(m);
-        } else if (m > 0 && !(straddle && m == 1)) {
+            if (!digit_array) wait_array(m);
+        } else if (!digit_array) {
             stage_plain(m);
             __syncthreads();
         }
-        const uint32_t arr = S.order[m];
-        const bool iota = arr == a.K && a.rid_in == nullptr;
-        const uint32_t* buf = S.stage[m % kRing];
-        uint32_t* out = arr == a.K ? a.rid_out : a.ck_out + (uint64_t)arr * a.ld;
+        uint32_t* out = arr.dst[m];
+        if (out) {
+            const bool iota = arr.src[m] == nullptr;
+            const uint32_t* buf = iota ? nullptr : buf_of(m);
 #pragma unroll
-        for (int i = 0; i < ITEMS; ++i) {
-            const uint32_t s = tid + i * kPassThreads;
-            if (s < count) out[dst[i]] = iota ? (uint32_t)(tile_base + srcp[i]) : buf[srcp[i]];  // dst < 2^30
+            for (int i = 0; i < ITEMS; ++i) {
+                const uint32_t s = tid + i * kPassThreads;
+                if (s < count) out[dst[i]] = iota ? (uint32_t)(tile_base + srcp[i]) : buf[srcp[i]];
+            }
         }
-        __syncthreads();  // buffer m % kRing is free again
-        if (bulk && tid == 0 && m + kRing < M) {
-            fence_proxy_async_smem();
-            issue(m + kRing);
+        if (bulk && arr.src[m] && (uint32_t)S.use[m] + kRing < staged_total) {
+            __syncthreads();  // ring slot of array m is free again
+            if (tid == 0) {
+                fence_proxy_async_smem();
+                for (uint32_t q = m + 1; q < M; ++q)
+                    if (arr.src[q] && S.use[q] == S.use[m] + kRing) issue(q);
+            }
+        } else if (!bulk) {
+            __syncthreads();
         }
     }
+}
+
+// Launches one pass; `arrays` lists the arrays in staging order.
+template <int RB>
+static cudaError_t launch_pass(const PassArgs& a, const PassArrays& arrays, uint32_t tiles, cudaStream_t s) {
+    constexpr size_t smem = sizeof(PassSmem<RB>);
+    static_assert(sizeof(PassSmem<RB>) <= 227 * 1024, "pass block exceeds shared memory");
+    cudaError_t e = cudaFuncSetAttribute(onesweep_pass_kernel<RB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    onesweep_pass_kernel<RB><<<tiles, kPassThreads, smem, s>>>(a, arrays);
+    count_launch();
+    return cudaGetLastError();
 }
 
 // ------------------------------------------------------------------ host
@@ -376,13 +404,14 @@ bool make_sort_plan(uint64_t n, uint32_t K, uint32_t nbits, uint32_t digit_bits,
 template <int RB>
 static cudaError_t run_sort_rb(const SortPlan& p, const uint32_t* ck_in, const uint32_t* rid_in, uint32_t* ck_out,
                                uint32_t* rid_out, uint64_t n, uint32_t nbits, uint32_t spin_limit, uint32_t inject,
-                               cudaEvent_t* ev, unsigned char* ws, cudaStream_t s) {
+                               uint32_t flags, cudaEvent_t* ev, unsigned char* ws, cudaStream_t s) {
     constexpr int BINS = 1 << RB;
     uint32_t* hist = reinterpret_cast<uint32_t*>(ws + p.off_hist);
     uint32_t* counters = reinterpret_cast<uint32_t*>(ws + p.off_counter);
     uint32_t* lookback = reinterpret_cast<uint32_t*>(ws + p.off_lookback);
     uint32_t* alt_ck = reinterpret_cast<uint32_t*>(ws + p.off_alt_ck);
     uint32_t* alt_rid = reinterpret_cast<uint32_t*>(ws + p.off_alt_rid);
+    const uint64_t ld = CK_LD(n);
     cudaError_t e = cudaMemsetAsync(ws, 0, p.off_alt_ck, s);
     if (e != cudaSuccess) return e;
 
@@ -393,53 +422,70 @@ static cudaError_t run_sort_rb(const SortPlan& p, const uint32_t* ck_in, const u
     if (e != cudaSuccess) return e;
     for (uint32_t p0 = 0; p0 < p.passes; p0 += chunk) {
         const uint32_t np = min(chunk, p.passes - p0);
-        upsweep_kernel<RB><<<up_grid, kUpThreads, sizeof(uint32_t) * np * BINS, s>>>(ck_in, n, CK_LD(n), nbits, p0,
-                                                                                     np, hist);
+        upsweep_kernel<RB><<<up_grid, kUpThreads, sizeof(uint32_t) * np * BINS, s>>>(ck_in, n, ld, nbits, p0, np,
+                                                                                     hist);
         count_launch();
     }
     scan_kernel<RB><<<p.passes, 256, 0, s>>>(hist);
     count_launch();
 
-    constexpr size_t smem = sizeof(PassSmem<RB>);
-    static_assert(sizeof(PassSmem<RB>) <= 227 * 1024, "pass block exceeds shared memory");
-    e = cudaFuncSetAttribute(onesweep_pass_kernel<RB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
+    const bool perm_only = (flags & CK_SORT_PERM_ONLY) != 0;
     const bool inplace = (ck_in == ck_out) || (rid_in != nullptr && rid_in == rid_out);
     auto al16 = [](const void* q) { return (reinterpret_cast<uintptr_t>(q) & 15) == 0; };
     const uint32_t bulk = al16(ck_in) && al16(ck_out) && al16(rid_out) && (rid_in == nullptr || al16(rid_in)) ? 1u : 0u;
     if (ev && (e = cudaEventRecord(ev[0], s)) != cudaSuccess) return e;
-    const uint32_t* src_ck = ck_in;
-    const uint32_t* src_rid = rid_in;
+    const uint32_t* cur_ck = ck_in;
+    const uint32_t* cur_rid = rid_in;
+    static thread_local PassArrays arrays;
     for (uint32_t q = 0; q < p.passes; ++q) {
         const bool to_out = inplace ? (q % 2 == 1) : ((p.passes - 1 - q) % 2 == 0);
+        uint32_t* out_ck = to_out ? ck_out : alt_ck;
+        uint32_t* out_rid = to_out ? rid_out : alt_rid;
+        const uint32_t shift = q * RB, wlo = shift >> 5, sh = shift & 31;
+        const uint32_t bits = min((uint32_t)RB, nbits - shift);
+        const bool straddle = sh + bits > 32;
+        // first key word still needed after this pass (all of them unless only
+        // the permutation is wanted)
+        const uint32_t keep = perm_only ? (q + 1 < p.passes ? ((q + 1) * RB) >> 5 : p.K) : 0u;
+        uint32_t m = 0;
+        auto add_word = [&](uint32_t w) {
+            arrays.src[m] = cur_ck + (uint64_t)w * ld;
+            arrays.dst[m] = w >= keep ? out_ck + (uint64_t)w * ld : nullptr;
+            ++m;
+        };
+        add_word(wlo);
+        if (straddle) add_word(wlo + 1);
+        for (uint32_t w = keep; w < p.K; ++w)
+            if (w != wlo && !(straddle && w == wlo + 1)) add_word(w);
+        arrays.src[m] = cur_rid;
+        arrays.dst[m] = out_rid;
+        ++m;
         PassArgs a;
-        a.ck_in = src_ck;
-        a.rid_in = src_rid;
-        a.ck_out = to_out ? ck_out : alt_ck;
-        a.rid_out = to_out ? rid_out : alt_rid;
         a.n = n;
-        a.ld = CK_LD(n);
-        a.bulk = bulk;
-        a.K = p.K;
-        a.shift = q * RB;
-        a.bits = min((uint32_t)RB, nbits - q * RB);
+        a.narr = m;
+        a.sh = sh;
+        a.bits = bits;
+        a.straddle = straddle ? 1u : 0u;
         a.pass = q;
+        a.bulk = bulk;
         a.bucket_base = hist + (size_t)q * BINS;
         a.lookback = lookback + (size_t)q * BINS * p.tiles;
         a.tile_counter = counters + q;
         a.spin_limit = spin_limit;
         a.inject = inject;
         a.status = status_ptr();
-        onesweep_pass_kernel<RB><<<p.tiles, kPassThreads, smem, s>>>(a);
-        count_launch();
-        if (ev && (e = cudaEventRecord(ev[q + 1], s)) != cudaSuccess) return e;
-        src_ck = a.ck_out;
-        src_rid = a.rid_out;
-    }
-    if (src_ck != ck_out) {
-        e = cudaMemcpyAsync(ck_out, src_ck, sizeof(uint32_t) * (size_t)p.K * CK_LD(n), cudaMemcpyDeviceToDevice, s);
+        e = launch_pass<RB>(a, arrays, p.tiles, s);
         if (e != cudaSuccess) return e;
-        e = cudaMemcpyAsync(rid_out, src_rid, sizeof(uint32_t) * n, cudaMemcpyDeviceToDevice, s);
+        if (ev && (e = cudaEventRecord(ev[q + 1], s)) != cudaSuccess) return e;
+        cur_ck = out_ck;
+        cur_rid = out_rid;
+    }
+    if (!perm_only && cur_ck != ck_out) {
+        e = cudaMemcpyAsync(ck_out, cur_ck, sizeof(uint32_t) * (size_t)p.K * ld, cudaMemcpyDeviceToDevice, s);
+        if (e != cudaSuccess) return e;
+    }
+    if (cur_rid != rid_out) {
+        e = cudaMemcpyAsync(rid_out, cur_rid, sizeof(uint32_t) * n, cudaMemcpyDeviceToDevice, s);
         if (e != cudaSuccess) return e;
     }
     return cudaGetLastError();
@@ -447,7 +493,7 @@ static cudaError_t run_sort_rb(const SortPlan& p, const uint32_t* ck_in, const u
 
 cudaError_t run_sort(const SortPlan& p, const uint32_t* ck_in, const uint32_t* rid_in, uint32_t* ck_out,
                      uint32_t* rid_out, uint64_t n, uint32_t nbits, uint32_t spin_limit, uint32_t inject,
-                     cudaEvent_t* ev, unsigned char* ws, cudaStream_t s) {
+                     uint32_t flags, cudaEvent_t* ev, unsigned char* ws, cudaStream_t s) {
     if (p.passes == 0) {  // nothing to order: outputs are the inputs
         cudaError_t e = cudaSuccess;
         if (ck_out != ck_in)
@@ -463,14 +509,14 @@ cudaError_t run_sort(const SortPlan& p, const uint32_t* ck_in, const uint32_t* r
         return cudaGetLastError();
     }
     switch (p.digit_bits) {
-        case 4: return run_sort_rb<4>(p, ck_in, rid_in, ck_out, rid_out, n, nbits, spin_limit, inject, ev, ws, s);
-        case 5: return run_sort_rb<5>(p, ck_in, rid_in, ck_out, rid_out, n, nbits, spin_limit, inject, ev, ws, s);
-        case 6: return run_sort_rb<6>(p, ck_in, rid_in, ck_out, rid_out, n, nbits, spin_limit, inject, ev, ws, s);
-        case 7: return run_sort_rb<7>(p, ck_in, rid_in, ck_out, rid_out, n, nbits, spin_limit, inject, ev, ws, s);
-        case 8: return run_sort_rb<8>(p, ck_in, rid_in, ck_out, rid_out, n, nbits, spin_limit, inject, ev, ws, s);
-        case 9: return run_sort_rb<9>(p, ck_in, rid_in, ck_out, rid_out, n, nbits, spin_limit, inject, ev, ws, s);
-        case 10: return run_sort_rb<10>(p, ck_in, rid_in, ck_out, rid_out, n, nbits, spin_limit, inject, ev, ws, s);
-        case 11: return run_sort_rb<11>(p, ck_in, rid_in, ck_out, rid_out, n, nbits, spin_limit, inject, ev, ws, s);
+        case 4: return run_sort_rb<4>(p, ck_in, rid_in, ck_out, rid_out, n, nbits, spin_limit, inject, flags, ev, ws, s);
+        case 5: return run_sort_rb<5>(p, ck_in, rid_in, ck_out, rid_out, n, nbits, spin_limit, inject, flags, ev, ws, s);
+        case 6: return run_sort_rb<6>(p, ck_in, rid_in, ck_out, rid_out, n, nbits, spin_limit, inject, flags, ev, ws, s);
+        case 7: return run_sort_rb<7>(p, ck_in, rid_in, ck_out, rid_out, n, nbits, spin_limit, inject, flags, ev, ws, s);
+        case 8: return run_sort_rb<8>(p, ck_in, rid_in, ck_out, rid_out, n, nbits, spin_limit, inject, flags, ev, ws, s);
+        case 9: return run_sort_rb<9>(p, ck_in, rid_in, ck_out, rid_out, n, nbits, spin_limit, inject, flags, ev, ws, s);
+        case 10: return run_sort_rb<10>(p, ck_in, rid_in, ck_out, rid_out, n, nbits, spin_limit, inject, flags, ev, ws, s);
+        case 11: return run_sort_rb<11>(p, ck_in, rid_in, ck_out, rid_out, n, nbits, spin_limit, inject, flags, ev, ws, s);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -60,7 +60,8 @@ extern "C" ck_status ck_sort_static(const uint32_t* ck_in, const uint32_t* rid_i
                                     uint32_t* rid_out, uint64_t n, uint32_t ck_words, uint32_t nbits,
                                     const ck_sort_opts* opts, ck_stream stream) {
     if (n > CK_MAX_ROWS || ck_words == 0 || nbits > 32u * ck_words) return CK_EINVAL;
-    if (opts && (opts->reserved != 0 || (opts->digit_bits != 0 && (opts->digit_bits < 4 || opts->digit_bits > 11))))
+    if (opts && ((opts->flags & ~CK_SORT_FLAGS_ALL) != 0 ||
+                 (opts->digit_bits != 0 && (opts->digit_bits < 4 || opts->digit_bits > 11))))
         return CK_EINVAL;
     if (n == 0) return CK_OK;
     if (!ck_in || !ck_out || !rid_out) return CK_EINVAL;
@@ -73,8 +74,9 @@ extern "C" ck_status ck_sort_static(const uint32_t* ck_in, const uint32_t* rid_i
     if (!status_ptr()) return CK_ECUDA;
     const uint32_t spin = (opts && opts->spin_limit) ? opts->spin_limit : kDefaultSpin;
     const uint32_t inject = opts ? opts->inject : 0u;
+    const uint32_t flags = opts ? opts->flags : 0u;
     cudaEvent_t* ev = opts ? static_cast<cudaEvent_t*>(opts->pass_events) : nullptr;
-    const cudaError_t e = run_sort(p, ck_in, rid_in, ck_out, rid_out, n, nbits, spin, inject, ev, ws,
+    const cudaError_t e = run_sort(p, ck_in, rid_in, ck_out, rid_out, n, nbits, spin, inject, flags, ev, ws,
                                    reinterpret_cast<cudaStream_t>(stream));
     return e == cudaSuccess ? CK_OK : CK_ECUDA;
 }

@@ -46,3 +46,24 @@ def extract_sort_alg_bytes(n: int, key_bytes: int, ck_words: int, passes: int) -
 def build_bytes(n: int, ck_words: int) -> int:
     """Leaf pass: reads sorted (ck, rid), writes rid (4 B) and D-bit (2 B)."""
     return n * (4 * ck_words + 4 + 4 + 2)
+
+
+def perm_only_pass_arrays(ck_words: int, nbits: int, digit_bits: int) -> list:
+    """(arrays read, arrays written) per pass of the permutation-only sort: a
+    pass reads its digit word(s), the key words later passes still need and
+    the row ids, and writes the still-needed words and the row ids."""
+    out = []
+    passes = radix_passes(nbits, digit_bits)
+    for q in range(passes):
+        shift = q * digit_bits
+        wlo, bits = shift // 32, min(digit_bits, nbits - shift)
+        straddle = (shift % 32) + bits > 32
+        keep = ((q + 1) * digit_bits) // 32 if q + 1 < passes else ck_words
+        read = {wlo} | ({wlo + 1} if straddle else set()) | set(range(keep, ck_words))
+        out.append((len(read) + 1, len(range(keep, ck_words)) + 1))
+    return out
+
+
+def perm_only_sort_bytes(n: int, ck_words: int, nbits: int, digit_bits: int) -> int:
+    """Algorithmic bytes of all passes of the permutation-only sort."""
+    return sum(4 * n * (r + w) for r, w in perm_only_pass_arrays(ck_words, nbits, digit_bits))

@@ -27,7 +27,7 @@ class Rebuild:
     """
 
     def __init__(self, keys: torch.Tensor, dmask: np.ndarray, fanout: int = 64, fill: float = 1.0,
-                 digit_bits: int = 8, ck_words: int | None = None, kind: int | None = None):
+                 digit_bits: int = 8, ck_words: int | None = None, kind: int | None = None, perm_only: bool = False):
         self.keys = keys
         self.kind = kind
         self.col = ck.column(keys, kind)
@@ -37,6 +37,9 @@ class Rebuild:
         self.nbits = ck.popcount(self.dmask)
         self.K = ck_words or ck.words_for(self.nbits)
         self.fanout, self.fill, self.digit_bits = fanout, fill, digit_bits
+        # perm_only: the sort returns only the permutation (and stops carrying
+        # consumed key words); the tree is then built from the key column
+        self.perm_only = perm_only
         dev = keys.device
         n = max(self.n, 1)
         self.ck_in = ck.ck_buffer(self.K, n, dev)
@@ -51,13 +54,17 @@ class Rebuild:
     def extract(self, stream=None):
         ck.ck_extract(self.keys, self.dmask, self.K, out=self.ck_in, kind=self.kind, stream=stream)
 
-    def sort(self, stream=None):
+    def sort(self, stream=None, pass_events=None):
         ck.ck_sort(self.ck_in, None, self.ck_sorted, self.rid_sorted, self.n, self.K, self.nbits, self.ws,
-                   digit_bits=self.digit_bits, stream=stream)
+                   digit_bits=self.digit_bits, pass_events=pass_events, perm_only=self.perm_only, stream=stream)
 
     def build(self, stream=None):
-        ck.ck_build_index(self.ck_sorted, self.rid_sorted, self.n, self.K, self.dmask, self.key_bits, self.fanout,
-                          self.fill, arrays=self.tree, refined_out=self.refined, stream=stream)
+        if self.perm_only:
+            ck.ck_build_index_keys(self.keys, self.rid_sorted, self.dmask, self.K, self.fanout, self.fill,
+                                   arrays=self.tree, refined_out=self.refined, kind=self.kind, stream=stream)
+        else:
+            ck.ck_build_index(self.ck_sorted, self.rid_sorted, self.n, self.K, self.dmask, self.key_bits,
+                              self.fanout, self.fill, arrays=self.tree, refined_out=self.refined, stream=stream)
 
     def run(self, stream=None):
         """One full rebuild: extract, sort, bulk load (+ refined D-bitmap)."""

@@ -54,7 +54,7 @@ def test_urls_64m_full_size():
     dmask = pipeline.first_build_dmask(kd)
     nbits = ck.popcount(dmask)
     assert 100 <= nbits <= 128, nbits            # packs into 128-bit compressed keys
-    r = pipeline.Rebuild(kd, dmask, fanout=64, digit_bits=8)
+    r = pipeline.Rebuild(kd, dmask, fanout=64, digit_bits=8)    # the bench configuration
     assert r.K == 4
     r.run()
     torch.cuda.synchronize()
@@ -77,3 +77,6 @@ def test_urls_64m_full_size():
     exp = oracle.compress(keys[idx], dmask, 4)
     assert np.array_equal(ck.u32(r.ck_in)[:, idx].T, exp)                 # extraction, input order
     assert np.array_equal(ck.u32(r.ck_sorted)[:, idx].T, oracle.compress(keys[perm[idx]], dmask, 4))
+    hck = ck.u32(r.tree["inner_high_ck"])[:ni * 4].reshape(ni, 4)
+    sel = np.sort(rng.choice(ni, min(ni, 50_000), replace=False))
+    assert np.array_equal(hck[sel], oracle.compress(keys[perm[t["high"][sel]]], dmask, 4))

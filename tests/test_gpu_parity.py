@@ -278,18 +278,19 @@ def test_sort_timeout_is_reported_and_gpu_stays_usable():
 
 
 # --------------------------------------------------------------- B-tree
-def check_tree(keys, fanout, fill=1.0, dmask=None, digit_bits=8):
+def check_tree(keys, fanout, fill=1.0, dmask=None, digit_bits=8, perm_only=False):
     kd = to_dev(keys) if keys.dtype == np.uint8 else u64_keys_dev(keys)
     perm = oracle.sort_rows(keys)
     D = oracle.dmask(keys, perm)
     m = D if dmask is None else dmask
-    r = pipeline.Rebuild(kd, m, fanout=fanout, fill=fill, digit_bits=digit_bits)
+    r = pipeline.Rebuild(kd, m, fanout=fanout, fill=fill, digit_bits=digit_bits, perm_only=perm_only)
     r.run()
     torch.cuda.synchronize()
     n = len(perm)
     assert np.array_equal(ck.u32(r.rid_sorted)[:n], perm)
     kb = oracle.as_key_bytes(keys)
-    assert np.array_equal(ck_rows(r.ck_sorted, n), oracle.compress(kb, m, r.K)[perm])
+    if not perm_only:
+        assert np.array_equal(ck_rows(r.ck_sorted, n), oracle.compress(kb, m, r.K)[perm])
     f = oracle.entries_per_node(fanout, fill)
     t = oracle.btree(kb, perm, f)
     assert [int(r.shape.level_entries[i]) for i in range(r.shape.levels)] == t["levels"]
@@ -312,31 +313,45 @@ def check_tree(keys, fanout, fill=1.0, dmask=None, digit_bits=8):
     return r
 
 
+@pytest.mark.parametrize("perm_only", [False, True])
 @pytest.mark.parametrize("fanout,fill", [(64, 1.0), (14, 0.9), (9, 0.9), (256, 1.0), (2, 1.0)])
-def test_btree_fanouts(fanout, fill):
+def test_btree_fanouts(fanout, fill, perm_only):
     rng = np.random.default_rng(fanout)
     keys = structured(rng, 3 * TILE + 300, 12, 50)
-    check_tree(keys, fanout, fill)
+    check_tree(keys, fanout, fill, perm_only=perm_only)
 
 
-def test_btree_from_superset_mask():
+@pytest.mark.parametrize("perm_only", [False, True])
+def test_btree_from_superset_mask(perm_only):
     """Extraction with the variant bitmap (a superset of D): same permutation,
     same tree, and the refinement recovers D exactly."""
     rng = np.random.default_rng(11)
     keys = structured(rng, 2 * TILE + 9, 16, 60)
-    check_tree(keys, 64, dmask=oracle.variant_mask(keys, 0))
+    check_tree(keys, 64, dmask=oracle.variant_mask(keys, 0), perm_only=perm_only)
 
 
+@pytest.mark.parametrize("perm_only", [False, True])
 @pytest.mark.parametrize("n", [1, 2, 63, 64, 65])
-def test_btree_tiny(n):
+def test_btree_tiny(n, perm_only):
     rng = np.random.default_rng(n)
     keys = structured(rng, n, 8, 10, dup_frac=0.3)
-    check_tree(keys, 8)
+    check_tree(keys, 8, perm_only=perm_only)
 
 
-def test_btree_all_equal_keys():
+@pytest.mark.parametrize("perm_only", [False, True])
+def test_btree_all_equal_keys(perm_only):
     keys = np.full((1000, 8), 42, np.uint8)
-    check_tree(keys, 16)
+    check_tree(keys, 16, perm_only=perm_only)
+
+
+@pytest.mark.parametrize("digit_bits", [4, 7, 8, 11])
+@pytest.mark.parametrize("W,nvary", [(8, 24), (16, 70), (32, 117), (64, 200)])
+def test_perm_only_sort_and_keys_tree(W, nvary, digit_bits):
+    """The permutation-only sort (consumed key words dropped) and the tree
+    built from the key column: identical to the oracle."""
+    rng = np.random.default_rng(W * 100 + digit_bits)
+    keys = structured(rng, 3 * TILE + 41, W, nvary)
+    check_tree(keys, 64, digit_bits=digit_bits, perm_only=True)
 
 
 # ------------------------------------------------------------ workloads
@@ -362,6 +377,7 @@ def test_pipeline_urls_dna_titles():
         perm = oracle.sort_rows(keys)
         assert list(D_gpu) == list(oracle.dmask(keys, perm))
         check_tree(keys, 64)
+        check_tree(keys, 256, perm_only=True)
 
 
 def test_full_key_baseline_same_permutation():

@@ -90,9 +90,9 @@ def test_argument_errors_are_synchronous(ckmod):
     col = ckmod.ck_column(4096, 10, 8, 8, ckmod.CK_KIND_BYTES)
     m2 = np.array([0xFFFFFFFF80000000], np.uint64)                   # 33 bits into 1 word
     assert lib.ck_extract(ctypes.byref(col), m2.ctypes.data, 1, 4096, None) == ckmod.CK_EOVERFLOW
-    o = ckmod.ck_sort_opts(3, 0, 0, 0)                               # digit width out of range
+    o = ckmod.ck_sort_opts(3, 0, 0, 0, None)                             # digit width out of range
     assert lib.ck_sort(4096, None, 8192, 12288, 100, 1, 20, ctypes.byref(o), None, 0, None) == ckmod.CK_EINVAL
-    o = ckmod.ck_sort_opts(8, 0, 0, 0)
+    o = ckmod.ck_sort_opts(8, 0, 0, 0, None)
     assert lib.ck_sort(4096, None, 8192, 12288, 100, 1, 20, ctypes.byref(o), None, 0, None) == ckmod.CK_ENOMEM
     assert lib.ck_sort(4096, None, 8192, 12288, 100, 1, 40, ctypes.byref(o), None, 0, None) == ckmod.CK_EINVAL
     assert lib.ck_sort(4096, None, 8192, 12288, 1 << 30, 1, 20, None, None, 0, None) == ckmod.CK_EINVAL
@@ -131,3 +131,15 @@ def test_table2_metric_formulas():
     assert round(sum(skrs) / 6, 2) == g["average_sort_key_ratio"]
     frac = sum(d / f for d, f in zip(g["distinction_bits"], g["full_key_bits"])) / 6
     assert round(100 * frac, 1) == g["average_distinction_fraction_percent"]
+
+
+def test_perm_only_pass_bytes():
+    """Permutation-only LSD sort of 121-bit keys in 4 words with 8-bit digits:
+    word w is carried until its last digit is consumed."""
+    from paper_2009_11543_gb300 import metrics as mt
+    arrs = mt.perm_only_pass_arrays(4, 121, 8)
+    assert len(arrs) == 16
+    assert arrs[0] == (5, 5) and arrs[3] == (5, 4) and arrs[4] == (4, 4) and arrs[15] == (2, 1)
+    assert sum(r + w for r, w in arrs) == 108            # vs 16 * 10 = 160 when every word is carried
+    assert mt.perm_only_sort_bytes(10, 4, 121, 8) == 4 * 10 * 108
+    assert mt.perm_only_pass_arrays(1, 20, 8) == [(2, 2), (2, 2), (2, 1)]
