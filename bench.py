@@ -39,14 +39,19 @@ SORT_SRC = os.path.join(ROOT, "paper_2009_11543_gb300", "csrc", "ck_sort.cu")
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "onesweep_pass_traffic.json")
 
 WORKLOADS = {
-    # name: (description, n, generator, fanout, cpu sample rows)
+    # name: (description, n, generator, fanout, cpu sample rows, path the headline value uses)
     "urls64m": ("64M 32-byte URL keys ('http://www.' + Zipf(1.1) name over 100k + '.com/' + 0-16 path chars), "
-                "fanout 64, compressed keys packed to 128 bits", 64 * 2**20, "urls", 64, 8_000_000),
+                "fanout 64, compressed keys packed to 128 bits, plain path", 64 * 2**20, "urls", 64, 8_000_000,
+                "plain"),
     "urls8m": ("8M 32-byte URL keys (the 64M workload's generator, first 8M rows), fanout 64; profiling size",
-               8 * 2**20, "urls", 64, 2_000_000),
-    "int1m": ("1M uint64 keys with 24 seeded varying bit positions, fanout 64", 1_000_000, "int", 64, 1_000_000),
-    "dna200m": ("200M 32-byte {A,C,G,T} keys, 20% with one of 65536 shared 24-char prefixes, fanout 256",
-                200_000_000, "dna", 256, 4_000_000),
+               8 * 2**20, "urls", 64, 2_000_000, "plain"),
+    "zipf256m": ("256M uint64 keys, Zipf(0.9) over 2^40 values under a constant 12-bit tag, learned partition "
+                 "(1% sample, 16-unit CDF model, 65536 buckets) vs plain radix, fanout 64", 256 * 2**20, "zipf", 64,
+                 8_000_000, "learned"),
+    "dna200m": ("200M 32-byte {A,C,G,T} keys, 20% sharing one of 65536 random 24-char prefixes, learned partition "
+                "+ bulk load with fanout 256", 200_000_000, "dna", 256, 4_000_000, "learned"),
+    "int1m": ("1M uint64 keys with 24 seeded varying bit positions, fanout 64", 1_000_000, "int", 64, 1_000_000,
+              "plain"),
 }
 
 
@@ -58,6 +63,8 @@ def gen_keys(kind: str, n: int):
         return synth.varying_bits_u64(n, synth.BASE_SEED + 1)[0]
     if kind == "dna":
         return synth.dna(n, synth.BASE_SEED + 5)
+    if kind == "zipf":
+        return synth.zipf_tagged_u64(n, synth.BASE_SEED + 4, 0.9)
     raise ValueError(kind)
 
 
@@ -146,7 +153,7 @@ def run_ours(args, rank, world, local_rank):
 
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
-    desc, n, kind, fanout, cpu_rows = WORKLOADS[args.workload]
+    desc, n, kind, fanout, cpu_rows, main_path = WORKLOADS[args.workload]
     keys_np = gen_keys(kind, n)
     keys_host = torch.from_numpy(keys_np.view(np.int64) if keys_np.dtype == np.uint64 else keys_np).pin_memory()
     keys = keys_host.to(dev)
@@ -157,6 +164,8 @@ def run_ours(args, rank, world, local_rank):
     nbits = ck.popcount(dmask)
     R = pipeline.Rebuild(keys, dmask, fanout=fanout, digit_bits=args.digit_bits)
     F = pipeline.Rebuild(keys, pipeline.full_key_mask(8 * key_bytes), fanout=fanout, digit_bits=args.digit_bits)
+    L = pipeline.Rebuild(keys, dmask, fanout=fanout, digit_bits=args.digit_bits, learned=True) if R.K <= 8 else None
+    V = L if (main_path == "learned" and L is not None) else R
     passes = metrics.radix_passes(nbits, args.digit_bits)
     fpasses = metrics.radix_passes(8 * key_bytes, args.digit_bits)
     stream = torch.cuda.current_stream()
@@ -187,6 +196,8 @@ def run_ours(args, rank, world, local_rank):
         launches = ck.ck_launch_count() - l0
         total_ms = start.elapsed_time(end)
         pass_ms = [[ev[s][q].elapsed_time(ev[s][q + 1]) for q in range(pass_count)] for s in range(steps)]
+        if pass_count == 0:
+            pass_ms = [[0.0] for _ in range(steps)]
         phase = [[ph[s][i].elapsed_time(ph[s][i + 1]) for i in range(3)] for s in range(steps)]
         return total_ms, pass_ms, phase, launches
 
@@ -199,7 +210,7 @@ def run_ours(args, rank, world, local_rank):
             ph[0].record(stream)
             r.extract()
             ph[1].record(stream)
-            r.sort(pass_events=evh)
+            r.sort(pass_events=None if r.learned else evh)
             ph[2].record(stream)
             r.build()
             ph[3].record(stream)
@@ -210,14 +221,17 @@ def run_ours(args, rank, world, local_rank):
     time.sleep(0.2)
     total_ms, pass_ms, phase, launches = timed(step_fn(R), args.steps, args.warmup, passes)
     f_total_ms, f_pass_ms, f_phase, _ = timed(step_fn(F), max(1, args.steps // 2), args.warmup, fpasses)
+    l_total_ms, l_phase, l_launches = None, None, 0
+    if L is not None:
+        l_total_ms, _, l_phase, l_launches = timed(step_fn(L), args.steps, args.warmup, 0)
 
     # end to end: host keys -> device, rebuild, sorted row ids -> host, every step
     rid_host = torch.empty(n, dtype=torch.int32, pin_memory=True)
 
     def e2e_step():
-        R.keys.copy_(keys_host, non_blocking=True)
-        R.run()
-        rid_host.copy_(R.rid_sorted[:n], non_blocking=True)
+        V.keys.copy_(keys_host, non_blocking=True)
+        V.run()
+        rid_host.copy_(V.rid_sorted[:n], non_blocking=True)
 
     for _ in range(args.warmup):
         e2e_step()
@@ -236,19 +250,23 @@ def run_ours(args, rank, world, local_rank):
         raise RuntimeError("device status %s (detail %d)" % (ck.ck_status_string(status), detail))
 
     # max over ranks
-    times = np.array([total_ms, e2e_ms, f_total_ms], np.float64)
+    times = np.array([total_ms, e2e_ms, f_total_ms, l_total_ms or 0.0], np.float64)
     if world > 1:
         import torch.distributed as dist
         t = torch.from_numpy(times)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         times = t.numpy()
-    total_ms, e2e_ms, f_total_ms = (float(x) for x in times)
+    total_ms, e2e_ms, f_total_ms = (float(x) for x in times[:3])
+    if L is not None:
+        l_total_ms = float(times[3])
     if rank != 0:
         return None
 
     ms_step = total_ms / args.steps
     f_ms_step = f_total_ms / max(1, args.steps // 2)
-    value = world * n / (ms_step / 1e3)
+    l_ms_step = l_total_ms / args.steps if L is not None else None
+    v_ms_step = l_ms_step if V is L else ms_step
+    value = world * n / (v_ms_step / 1e3)
     peak, peak_src = peaks()
     # achieved = all passes' algorithmic bytes / all passes' time
     sort_bytes = passes * metrics.pass_bytes(n, R.K)
@@ -270,7 +288,7 @@ def run_ours(args, rank, world, local_rank):
         "n_gpus": world,
         "steps": args.steps,
         "warmup": args.warmup,
-        "ms_per_step": ms_step,
+        "ms_per_step": v_ms_step,
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
@@ -290,11 +308,18 @@ def run_ours(args, rank, world, local_rank):
                      "phases_ms": {"extract": float(fph[0]), "sort": float(fph[1]), "build": float(fph[2])},
                      "pass_gbs": f_pass_gbs, "extract_sort_roofline_frac":
                          f_alg / ((fph[0] + fph[1]) / 1e3) / 1e9 / peak},
-        "compressed_vs_full_speedup": f_ms_step / ms_step,
+        "compressed_vs_full_speedup": f_ms_step / v_ms_step,
         "compression_ratio": metrics.compression_ratio(8 * key_bytes, nbits) if nbits else None,
         "e2e": {"value": world * n / (e2e_ms / args.steps / 1e3), "unit": "keys/s",
                 "h2d_bytes_per_step": int(keys_np.nbytes), "d2h_bytes_per_step": 4 * n},
-        "gpu_launches": int(launches),
+        "path": "learned" if V is L else "plain",
+        "plain": {"value": world * n / (ms_step / 1e3), "unit": "keys/s", "ms_per_step": ms_step,
+                  "phases_ms": {"extract": float(ph[0]), "sort": float(ph[1]), "build": float(ph[2])}},
+        "learned": None if L is None else {
+            "value": world * n / (l_ms_step / 1e3), "unit": "keys/s", "ms_per_step": l_ms_step,
+            "phases_ms": dict(zip(("extract", "sort", "build"), (float(x) for x in np.mean(np.array(l_phase), 0)))),
+            "stats": L.learned_stats, "speedup_vs_plain": ms_step / l_ms_step},
+        "gpu_launches": int(l_launches if V is L else launches),
         "clocks": clk,
     }
     if world == 1 and not args.no_cpu_baseline:
@@ -315,7 +340,7 @@ def oracle_step(keys, dmask, fanout, key_bits):
 
 
 def cpu_baseline(workload, dmask, rows):
-    desc, n, kind, fanout, _ = WORKLOADS[workload]
+    desc, n, kind, fanout, _, _ = WORKLOADS[workload]
     keys = gen_keys(kind, rows)          # the first rows of the same seeded column
     kb = 8 * (keys.shape[1] if keys.ndim == 2 else keys.dtype.itemsize)
     t = time.perf_counter()
@@ -330,8 +355,8 @@ def run_reference(args, rank, world):
     if rank != 0:
         return None
     import oracle
-    desc, n, kind, fanout, rows = WORKLOADS[args.workload]
-    rows = min(rows, n) if args.workload != "urls64m" else 2_000_000
+    desc, n, kind, fanout, rows, _ = WORKLOADS[args.workload]
+    rows = min(rows, n, 2_000_000)
     keys = gen_keys(kind, rows)
     kb = 8 * (keys.shape[1] if keys.ndim == 2 else keys.dtype.itemsize)
     dmask = oracle.dmask(keys)           # the sample's stored D-bitmap (set-up, untimed)

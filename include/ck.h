@@ -192,6 +192,80 @@ ck_status ck_sort_static(const uint32_t* ck_in, const uint32_t* rid_in, uint32_t
                          uint64_t n, uint32_t ck_words, uint32_t nbits, const ck_sort_opts* opts, ck_stream stream);
 
 /* ---------------------------------------------------------------------------
+ * Learned partition (not in the paper; it replaces most radix passes for wide
+ * compressed keys).  A tiny fp32 CDF model
+ *   y(x) = b2 + sum_j w2_j * relu(w1_j * x + b1_j),  j < CK_MLP_HIDDEN,
+ * parameters packed [w1, b1, w2, b2] (CK_MLP_PARAMS floats), on the feature
+ * x = (top 24 bits of the nbits-bit compressed key) / 2^24, is trained on the
+ * GPU by full-batch Adam to the empirical CDF (rank + 0.5) / S of a sorted
+ * stride sample of S = n / sample_div keys.  The buckets are the 2^bucket_bits
+ * key ranges between the quantiles of the sorted sample (a key value that
+ * fills several quantiles gets a bucket of its own); the model proposes each
+ * key's bucket as floor(y(x) * B) and a short walk against the splitters makes
+ * the assignment exact.  Two radix passes on the bucket id partition the pairs
+ * stably, and each bucket is sorted in shared memory.
+ *
+ * ck_sort_learned gives exactly the output of ck_sort (stable, ties by row id,
+ * sorted ck and rid).  A verification pass checks every adjacent output pair;
+ * if it fails, or a bucket whose keys are not all equal exceeds what one block
+ * can sort, the plain radix sort recomputes the result from ck_in and the call
+ * returns CK_EVERIFY (the output is still exact).  The call synchronises its
+ * stream once, to read the verification flag.
+ *   ck_in      device, ck_words * CK_LD(n), word-major; read only.
+ *   ck_out, rid_out  device outputs as ck_sort (ck_out != ck_in).
+ *   ck_words   1 .. 8.
+ *   opts       NULL for defaults.  stats: HOST, optional.
+ *   ws         device, >= ck_sort_learned_workspace_bytes(), 256-byte aligned.
+ * Errors: CK_EINVAL, CK_ENOMEM; CK_EVERIFY as above. */
+#define CK_MLP_HIDDEN 16
+#define CK_MLP_PARAMS (3 * CK_MLP_HIDDEN + 1)
+
+typedef struct ck_learned_opts {
+    uint32_t bucket_bits; /* log2 of the bucket count, 8 .. 16; 0 = 16 */
+    uint32_t sample_div;  /* one sample per sample_div keys; 0 = 100 (1%) */
+    uint32_t epochs;      /* Adam epochs; 0 = 100 */
+    float lr;             /* Adam learning rate; 0 = 1e-3 */
+    uint32_t flags;       /* CK_LEARNED_* bits */
+    uint32_t reserved;    /* must be 0 */
+} ck_learned_opts;
+
+/* No model: buckets are plain sample quantiles and every key's bucket is found
+ * by binary search over the splitters (the method without the network). */
+#define CK_LEARNED_NO_MODEL 1u
+/* Test-only: the verification pass reports a failure, forcing the fallback. */
+#define CK_LEARNED_INJECT_VERIFY_FAIL 2u
+
+typedef struct ck_learned_stats {
+    float train_loss;           /* mean squared error of the model on the sample */
+    float mean_search_steps;    /* splitter comparisons per key to reach the exact bucket: from the model's
+                                   guess (galloping search), or a binary search without the model */
+    uint32_t max_search_steps;  /* most comparisons for one key */
+    uint32_t buckets;           /* 2^bucket_bits */
+    uint32_t sample_size;       /* S */
+    uint32_t max_bucket;        /* largest bucket (pairs) */
+    uint32_t sorted_segments;   /* shared-memory sorts run */
+    uint32_t constant_buckets;  /* buckets of equal keys left as partitioned */
+    uint32_t oversize_buckets;  /* non-constant buckets too large for a block */
+    uint32_t fell_back;         /* 1 if the plain radix sort produced the result */
+} ck_learned_stats;
+
+size_t ck_sort_learned_workspace_bytes(uint64_t n, uint32_t ck_words, uint32_t nbits, const ck_learned_opts* opts);
+
+ck_status ck_sort_learned(const uint32_t* ck_in, uint32_t* ck_out, uint32_t* rid_out, uint64_t n, uint32_t ck_words,
+                          uint32_t nbits, const ck_learned_opts* opts, ck_learned_stats* stats, float* params_out,
+                          void* ws, size_t ws_bytes, ck_stream stream);
+
+/* ck_mlp_loss_grad -- one forward + backward pass of the CDF model over S
+ * samples: the mean squared error against t (or against (i + 0.5) / S when t
+ * is NULL) and its gradient with respect to the 49 parameters, summed in a
+ * fixed order (deterministic).  All pointers are device memory: params [49],
+ * x [S], t [S] or NULL, grad_out [49], loss_out [1].
+ * ws >= ck_mlp_workspace_bytes() bytes.  Errors: CK_EINVAL, CK_ENOMEM. */
+size_t ck_mlp_workspace_bytes(void);
+ck_status ck_mlp_loss_grad(const float* params, const float* x, const float* t, uint64_t S, float* grad_out,
+                           float* loss_out, void* ws, size_t ws_bytes, ck_stream stream);
+
+/* ---------------------------------------------------------------------------
  * Index tree (Sec. 4.2 structure, Sec. 5.3 bottom-up build).  Canonical
  * layout: each node holds f = max(1, floor(fanout * fill)) consecutive entries
  * (the last node of a level may hold fewer).  Level 0 has one entry per key in

@@ -16,7 +16,8 @@ passage of the paper it follows:
 * ``sort_compressed`` -- Sec. 3.2, compressed key sort
 * ``refine``          -- Sec. 4.3 rebuild step 1 with D-offset (Sec. 5.3)
 * ``btree``           -- Sec. 4.2 / 5.3, bottom-up bulk load
-* ``mlp``             -- (``oracle.mlp``) the learned CDF model, fp64
+* ``mlp_loss_grad``   -- the learned CDF model (not in the paper), fp64 forward
+                         and backward by the chain rule
 
 Layout conventions are stated in the header of ``ck_oracle.c``: bitmaps are
 uint64 words most-significant-first (position p = bit 63 - p%64 of word p/64),
@@ -69,6 +70,10 @@ def _load():
         lib.cko_btree_shape.restype = U32
         lib.cko_btree_leaf_dbits.argtypes = [P, U64, U32, U32, P, P]
         lib.cko_btree_inner.argtypes = [P, U64, U32, U32, P, U32, U32, P, P, P, P]
+        lib.cko_mlp_forward.argtypes = [P, ctypes.c_double]
+        lib.cko_mlp_forward.restype = ctypes.c_double
+        lib.cko_mlp_loss_grad.argtypes = [P, P, P, U64, P]
+        lib.cko_mlp_loss_grad.restype = ctypes.c_double
         _lib = lib
     return _lib
 
@@ -211,3 +216,24 @@ def btree(keys, perm: np.ndarray, f: int) -> dict:
                         _ptr(child), _ptr(high), _ptr(idbit))
     return {"levels": shape, "leaf_dbit": leaf, "child": child[:ninner],
             "high": high[:ninner], "dbit": idbit[:ninner]}
+
+
+# ------------------------------------------------------------ learned model
+MLP_HIDDEN = 16
+MLP_PARAMS = 3 * MLP_HIDDEN + 1
+
+
+def mlp_forward(params, x: float) -> float:
+    """fp64 forward of the 1-16-1 ReLU CDF model (parameters [w1, b1, w2, b2])."""
+    p = np.ascontiguousarray(params, np.float64)
+    return float(_load().cko_mlp_forward(_ptr(p), float(x)))
+
+
+def mlp_loss_grad(params, x, t):
+    """fp64 mean squared error of the model on (x, t) and its gradient."""
+    p = np.ascontiguousarray(params, np.float64)
+    xs = np.ascontiguousarray(x, np.float64)
+    ts = np.ascontiguousarray(t, np.float64)
+    g = np.zeros(MLP_PARAMS, np.float64)
+    loss = _load().cko_mlp_loss_grad(_ptr(p), _ptr(xs), _ptr(ts), len(xs), _ptr(g))
+    return float(loss), g

@@ -261,3 +261,39 @@ void cko_btree_inner(const uint8_t* keys, uint64_t n, uint32_t W, uint32_t strid
     }
     free(entry_high);
 }
+
+/* ---- learned CDF model (not in the paper): fp64 reference ----------------
+ * y(x) = b2 + sum_j w2[j] * relu(w1[j] * x + b1[j]), j < 16, parameters packed
+ * as [w1(16), b1(16), w2(16), b2] (49 values).  Loss over S samples with
+ * targets t_i: L = (1/S) * sum_i (y(x_i) - t_i)^2.  Writes L and dL/dparams
+ * (49 values) by the chain rule, summed over the samples in index order. */
+#define CKO_HIDDEN 16
+double cko_mlp_forward(const double* p, double x) {
+    double y = p[3 * CKO_HIDDEN];
+    for (int j = 0; j < CKO_HIDDEN; ++j) {
+        double z = p[j] * x + p[CKO_HIDDEN + j];
+        if (z > 0.0) y += p[2 * CKO_HIDDEN + j] * z;
+    }
+    return y;
+}
+
+double cko_mlp_loss_grad(const double* p, const double* x, const double* t, uint64_t S, double* grad) {
+    memset(grad, 0, sizeof(double) * (3 * CKO_HIDDEN + 1));
+    double loss = 0.0;
+    for (uint64_t i = 0; i < S; ++i) {
+        double y = cko_mlp_forward(p, x[i]);
+        double r = y - t[i];
+        loss += r * r;
+        double dy = 2.0 * r / (double)S;                 /* dL/dy_i */
+        grad[3 * CKO_HIDDEN] += dy;                      /* b2 */
+        for (int j = 0; j < CKO_HIDDEN; ++j) {
+            double z = p[j] * x[i] + p[CKO_HIDDEN + j];
+            if (z <= 0.0) continue;                      /* relu'(z) = 0 */
+            grad[2 * CKO_HIDDEN + j] += dy * z;          /* w2_j: dy/dw2_j = relu(z) */
+            double dz = dy * p[2 * CKO_HIDDEN + j];      /* dL/dz_j */
+            grad[j] += dz * x[i];                        /* w1_j */
+            grad[CKO_HIDDEN + j] += dz;                  /* b1_j */
+        }
+    }
+    return loss / (double)S;
+}

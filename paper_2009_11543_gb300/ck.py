@@ -28,7 +28,8 @@ CK_SORT_PERM_ONLY = 1
 
 EXPORTED = ["ck_variant_bits", "ck_distinction_bits", "ck_extract", "ck_sort_workspace_bytes", "ck_sort",
             "ck_btree_plan", "ck_build_index", "ck_device_status", "ck_clear_device_status",
-            "ck_status_string", "ck_launch_count", "ck_compress_word_host", "ck_sort_static", "ck_build_index_keys"]
+            "ck_status_string", "ck_launch_count", "ck_compress_word_host", "ck_sort_static", "ck_build_index_keys",
+            "ck_sort_learned_workspace_bytes", "ck_sort_learned", "ck_mlp_workspace_bytes", "ck_mlp_loss_grad"]
 CK_SORT_STATIC_SCRATCH_BYTES = 32 << 20
 
 
@@ -46,6 +47,22 @@ class ck_column(ctypes.Structure):
 class ck_sort_opts(ctypes.Structure):
     _fields_ = [("digit_bits", ctypes.c_uint32), ("spin_limit", ctypes.c_uint32), ("inject", ctypes.c_uint32),
                 ("flags", ctypes.c_uint32), ("pass_events", ctypes.c_void_p)]
+
+
+class ck_learned_opts(ctypes.Structure):
+    _fields_ = [("bucket_bits", ctypes.c_uint32), ("sample_div", ctypes.c_uint32), ("epochs", ctypes.c_uint32),
+                ("lr", ctypes.c_float), ("flags", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
+
+
+class ck_learned_stats(ctypes.Structure):
+    _fields_ = [("train_loss", ctypes.c_float), ("mean_search_steps", ctypes.c_float),
+                ("max_search_steps", ctypes.c_uint32), ("buckets", ctypes.c_uint32),
+                ("sample_size", ctypes.c_uint32), ("max_bucket", ctypes.c_uint32),
+                ("sorted_segments", ctypes.c_uint32), ("constant_buckets", ctypes.c_uint32),
+                ("oversize_buckets", ctypes.c_uint32), ("fell_back", ctypes.c_uint32)]
+
+    def as_dict(self) -> dict:
+        return {name: getattr(self, name) for name, _ in self._fields_}
 
 
 class ck_btree_shape(ctypes.Structure):
@@ -83,6 +100,13 @@ def _lib():
         lib.ck_btree_plan.argtypes = [U64, U32, ctypes.c_float, ctypes.POINTER(ck_btree_shape)]
         lib.ck_build_index.argtypes = [P, P, U64, U32, P, U32, U32, ctypes.c_float, ctypes.POINTER(ck_btree), P, P]
         lib.ck_build_index_keys.argtypes = [CP, P, P, U32, U32, ctypes.c_float, ctypes.POINTER(ck_btree), P, P]
+        LO = ctypes.POINTER(ck_learned_opts)
+        lib.ck_sort_learned_workspace_bytes.argtypes = [U64, U32, U32, LO]
+        lib.ck_sort_learned_workspace_bytes.restype = ctypes.c_size_t
+        lib.ck_sort_learned.argtypes = [P, P, P, U64, U32, U32, LO, ctypes.POINTER(ck_learned_stats), P, P,
+                                        ctypes.c_size_t, P]
+        lib.ck_mlp_workspace_bytes.restype = ctypes.c_size_t
+        lib.ck_mlp_loss_grad.argtypes = [P, P, P, U64, P, P, P, ctypes.c_size_t, P]
         lib.ck_device_status.argtypes = [ctypes.POINTER(U64)]
         lib.ck_status_string.argtypes = [I]
         lib.ck_status_string.restype = ctypes.c_char_p
@@ -91,7 +115,7 @@ def _lib():
         lib.ck_compress_word_host.restype = U32
         for name in EXPORTED:
             if name not in ("ck_sort_workspace_bytes", "ck_status_string", "ck_launch_count",
-                            "ck_compress_word_host"):
+                            "ck_compress_word_host", "ck_sort_learned_workspace_bytes", "ck_mlp_workspace_bytes"):
                 getattr(lib, name).restype = I
         _LIB = lib
     return _LIB
@@ -279,6 +303,50 @@ def ck_build_index_keys(keys: torch.Tensor, sorted_rid: torch.Tensor, dmask: np.
     _check(_lib().ck_build_index_keys(ctypes.byref(col), _ptr(sorted_rid), _ptr(m), ck_words, fanout, fill,
                                       ctypes.byref(t), _ptr(refined_out), _stream(stream)), "ck_build_index_keys")
     return t.shape, arrays
+
+
+CK_MLP_HIDDEN = 16
+CK_MLP_PARAMS = 3 * CK_MLP_HIDDEN + 1
+CK_LEARNED_NO_MODEL = 1
+CK_LEARNED_INJECT_VERIFY_FAIL = 2
+
+
+def learned_opts(bucket_bits=0, sample_div=0, epochs=0, lr=0.0, flags=0) -> ck_learned_opts:
+    return ck_learned_opts(bucket_bits, sample_div, epochs, lr, flags, 0)
+
+
+def ck_sort_learned_workspace_bytes(n: int, ck_words: int, nbits: int, opts: ck_learned_opts | None = None) -> int:
+    return int(_lib().ck_sort_learned_workspace_bytes(n, ck_words, nbits,
+                                                      ctypes.byref(opts) if opts is not None else None))
+
+
+def ck_sort_learned(ck_in: torch.Tensor, ck_out: torch.Tensor, rid_out: torch.Tensor, n: int, ck_words: int,
+                    nbits: int, ws: torch.Tensor, opts: ck_learned_opts | None = None, stream=None):
+    """Returns (status, stats dict, trained parameters as numpy float32 or None).
+    CK_EVERIFY (the exact fallback ran) is returned, not raised."""
+    stats = ck_learned_stats()
+    params = np.zeros(CK_MLP_PARAMS, np.float32)
+    st = _lib().ck_sort_learned(_ptr(ck_in), _ptr(ck_out), _ptr(rid_out), n, ck_words, nbits,
+                                ctypes.byref(opts) if opts is not None else None, ctypes.byref(stats), _ptr(params),
+                                _ptr(ws), ws.numel() * ws.element_size(), _stream(stream))
+    if st not in (CK_OK, CK_EVERIFY):
+        raise CkError(st, "ck_sort_learned")
+    no_model = opts is not None and (opts.flags & CK_LEARNED_NO_MODEL)
+    return st, stats.as_dict(), (None if no_model else params)
+
+
+def ck_mlp_workspace_bytes() -> int:
+    return int(_lib().ck_mlp_workspace_bytes())
+
+
+def ck_mlp_loss_grad(params: torch.Tensor, x: torch.Tensor, t: torch.Tensor | None, ws: torch.Tensor,
+                     stream=None):
+    """Device fwd + bwd of the CDF model: returns (loss, grad) device tensors."""
+    grad = torch.empty(CK_MLP_PARAMS, dtype=torch.float32, device=params.device)
+    loss = torch.empty(1, dtype=torch.float32, device=params.device)
+    _check(_lib().ck_mlp_loss_grad(_ptr(params), _ptr(x), _ptr(t), x.numel(), _ptr(grad), _ptr(loss), _ptr(ws),
+                                   ws.numel() * ws.element_size(), _stream(stream)), "ck_mlp_loss_grad")
+    return loss, grad
 
 
 def ck_device_status() -> tuple[int, int]:

@@ -195,6 +195,38 @@ cudaError_t launch_btree_keys(const KeyDesc& k, int vec, uint64_t n, const uint3
                               uint64_t* refined, cudaStream_t s);
 bool make_extract_plan(const KeyDesc& k, const uint64_t* dmask, uint32_t ck_words, ExtractPlan* plan);
 
+constexpr int kPassTile = 4096;                   // pairs per onesweep tile
+constexpr int kMaxPassArrays = kMaxKeyWords + 2;  // key words, row ids, one extra
+constexpr uint32_t kLookbackFlagAgg = 1u << 30;
+
+// The arrays a pass moves, in staging order.  Array 0 (and array 1 when the
+// digit straddles two words) holds the digit.  A NULL source means the values
+// are the input positions (row ids 0..n-1; such an array takes no ring slot);
+// a NULL destination means the array is read for its digit but not carried on.
+struct PassArrays {
+    const uint32_t* src[kMaxPassArrays];
+    uint32_t* dst[kMaxPassArrays];
+};
+
+struct PassArgs {
+    uint64_t n;
+    uint32_t narr;                // arrays in PassArrays
+    uint32_t sh, bits, straddle;  // digit = bits [sh, sh + bits) of array 0 (spilling into array 1)
+    uint32_t pass;
+    uint32_t bulk;                // 1: every array is 16-byte aligned, full tiles stage by TMA
+    const uint32_t* bucket_base;  // [BINS] of this pass
+    uint32_t* lookback;           // [tiles][BINS] of this pass, zeroed
+    uint32_t* tile_counter;       // zeroed
+    uint32_t spin_limit, inject;
+    unsigned long long* status;
+};
+
+// One onesweep pass with digit width rb (4..11); tiles = ceil(n / kPassTile).
+cudaError_t launch_onesweep_pass(uint32_t rb, const PassArgs& a, const PassArrays& arrays, uint32_t tiles,
+                                 cudaStream_t s);
+// Exclusive scan, in place, of `sets` histograms of 2^rb bins (rb <= 8).
+cudaError_t launch_bucket_scan(uint32_t* hist, uint32_t sets, uint32_t rb, cudaStream_t s);
+
 struct SortPlan {
     uint32_t digit_bits, passes, tile, tiles, K;
     size_t off_hist, off_counter, off_lookback, off_alt_ck, off_alt_rid, total;

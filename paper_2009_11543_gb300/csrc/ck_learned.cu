@@ -1,0 +1,854 @@
+// ck_learned.cu -- the learned-partition sort (not in the paper): a tiny fp32
+// CDF model, trained on the GPU on a sample of the compressed keys, places
+// every key in one of B = 2^bucket_bits key-range buckets; two radix passes on
+// the bucket id partition the pairs stably, and each bucket is then sorted in
+// shared memory.  The result is the same permutation as the plain radix sort:
+//
+//  * the buckets are ranges between monotone splitters (the B-quantiles of the
+//    sorted sample, with heavy keys isolated in buckets of their own), so a
+//    stable partition by bucket followed by a stable sort inside each bucket
+//    is a stable sort of the whole column;
+//  * the model proposes each key's bucket as floor(y(x) * B) in O(1); a short
+//    walk against the splitters makes the assignment exact (a far-off guess
+//    falls back to binary search), so a poor model costs time, not
+//    correctness.  Without the model every key needs a binary search;
+//  * a verification pass checks every adjacent output pair; if it fails, or a
+//    non-constant bucket is larger than a block can sort, the plain radix sort
+//    recomputes the result from the untouched input (status CK_EVERIFY).
+//
+// The model: y(x) = b2 + sum_j w2_j relu(w1_j x + b1_j), 16 hidden units, on
+// x = the top 24 bits of the compressed key / 2^24, fitted by full-batch Adam
+// to the empirical CDF (rank + 0.5) / S of the sorted sample.
+#include <cmath>
+#include <cstring>
+
+#include "ck_internal.cuh"
+
+namespace ck {
+
+constexpr int kHidden = CK_MLP_HIDDEN;
+constexpr int kParams = CK_MLP_PARAMS;  // [w1(16), b1(16), w2(16), b2]
+constexpr int kRed = kParams + 1;       // gradient + loss
+constexpr int kTrainThreads = 256;
+constexpr int kMaxLearnedWords = 8;
+
+__device__ __forceinline__ float mlp_eval(const float* p, float x) {
+    float y = p[3 * kHidden];
+#pragma unroll
+    for (int j = 0; j < kHidden; ++j) {
+        const float z = fmaf(p[j], x, p[kHidden + j]);
+        y = fmaf(p[2 * kHidden + j], fmaxf(z, 0.0f), y);
+    }
+    return y;
+}
+
+// Adds the gradient of (y(x) - t)^2 * scale to g[0..48] and returns the squared residual.
+__device__ __forceinline__ float mlp_accumulate(const float* p, float x, float t, float scale, float* g) {
+    float z[kHidden];
+    float y = p[3 * kHidden];
+#pragma unroll
+    for (int j = 0; j < kHidden; ++j) {
+        z[j] = fmaf(p[j], x, p[kHidden + j]);
+        y = fmaf(p[2 * kHidden + j], fmaxf(z[j], 0.0f), y);
+    }
+    const float r = y - t;
+    const float dy = 2.0f * r * scale;
+    g[3 * kHidden] += dy;
+#pragma unroll
+    for (int j = 0; j < kHidden; ++j) {
+        if (z[j] > 0.0f) {
+            g[2 * kHidden + j] += dy * z[j];
+            const float dz = dy * p[2 * kHidden + j];
+            g[j] += dz * x;
+            g[kHidden + j] += dz;
+        }
+    }
+    return r * r;
+}
+
+// Top 24 bits of an nbits-bit compressed key (word-major, leading dimension
+// ld) as a float in [0, 1); exact in fp32.
+__device__ __forceinline__ float key_feature(const uint32_t* ck, uint64_t ld, uint64_t i, uint32_t K,
+                                             uint32_t nbits) {
+    uint32_t top;
+    if (nbits >= 24) {
+        const uint32_t lo = nbits - 24, w = lo >> 5, s = lo & 31;
+        uint64_t v = ck[(uint64_t)w * ld + i];
+        if (w + 1 < K) v |= (uint64_t)ck[(uint64_t)(w + 1) * ld + i] << 32;
+        top = (uint32_t)(v >> s) & 0xFFFFFFu;
+    } else {
+        top = (ck[i] << (24 - nbits)) & 0xFFFFFFu;
+    }
+    return (float)top * (1.0f / 16777216.0f);
+}
+
+// Deterministic block reduction of kRed per-thread values: warp butterflies,
+// then the warps' results summed in warp order.  Result in out[0..kRed).
+__device__ void block_reduce_red(float (&v)[kRed], float* sm /*[warps][kRed]*/, float* out) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, warps = blockDim.x >> 5;
+#pragma unroll
+    for (int k = 0; k < kRed; ++k) {
+        float x = v[k];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(kFull, x, o);
+        if (lane == 0) sm[warp * kRed + k] = x;
+    }
+    __syncthreads();
+    if (threadIdx.x < kRed) {
+        float s = 0.0f;
+        for (int w = 0; w < warps; ++w) s += sm[w * kRed + threadIdx.x];
+        out[threadIdx.x] = s;
+    }
+    __syncthreads();
+}
+
+// ------------------------------------------------------------ sample, features
+__global__ void sample_kernel(const uint32_t* __restrict__ ck, uint64_t ld, uint32_t K, uint64_t div, uint64_t S,
+                              uint32_t* __restrict__ out, uint64_t ld_s) {
+    for (uint64_t j = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; j < S; j += (uint64_t)gridDim.x * blockDim.x)
+        for (uint32_t w = 0; w < K; ++w) out[(uint64_t)w * ld_s + j] = ck[(uint64_t)w * ld + j * div];
+}
+
+__global__ void features_kernel(const uint32_t* __restrict__ ck, uint64_t ld, uint64_t S, uint32_t K, uint32_t nbits,
+                                float* __restrict__ xs) {
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < S; i += (uint64_t)gridDim.x * blockDim.x)
+        xs[i] = key_feature(ck, ld, i, K, nbits);
+}
+
+// Initial parameters: the linear spline through the sample CDF at 16 knots
+// (sample quantiles j / 16).  Hidden unit j is relu(x - k_j); its output weight
+// is the change of slope at k_j.  One warp.
+__global__ void mlp_init_kernel(const float* __restrict__ xs, uint64_t S, float* __restrict__ params) {
+    __shared__ float k[kHidden + 1], y[kHidden + 1];
+    const int j = threadIdx.x;
+    if (j <= kHidden) {
+        const uint64_t idx = j < kHidden ? (uint64_t)j * S / kHidden : S - 1;
+        k[j] = xs[idx];
+        y[j] = j < kHidden ? ((float)idx + 0.5f) / (float)S : 1.0f;
+    }
+    __syncwarp();
+    if (j < kHidden) {
+        auto slope = [&](int q) {
+            const float dx = k[q + 1] - k[q];
+            return dx > 1e-7f ? (y[q + 1] - y[q]) / dx : 0.0f;
+        };
+        const float sj = slope(j), sp = j > 0 ? slope(j - 1) : 0.0f;
+        params[j] = 1.0f;
+        params[kHidden + j] = -k[j];
+        params[2 * kHidden + j] = sj - sp;
+    }
+    if (j == 0) params[3 * kHidden] = y[0];
+}
+
+// ------------------------------------------------------------ fwd + bwd
+// Loss and gradient of the model over S samples (targets (i + 0.5) / S when
+// t == NULL), one launch: per-block partials in partial[block][kRed].
+__global__ void __launch_bounds__(kTrainThreads) mlp_grad_kernel(const float* __restrict__ params,
+                                                                  const float* __restrict__ xs,
+                                                                  const float* __restrict__ ts, uint64_t S,
+                                                                  float* __restrict__ partial) {
+    __shared__ float p[kParams];
+    __shared__ float red[(kTrainThreads / 32) * kRed];
+    __shared__ float out[kRed];
+    if (threadIdx.x < kParams) p[threadIdx.x] = params[threadIdx.x];
+    __syncthreads();
+    float g[kRed];
+#pragma unroll
+    for (int q = 0; q < kRed; ++q) g[q] = 0.0f;
+    const float scale = 1.0f / (float)S;
+    const uint64_t i0 = S * blockIdx.x / gridDim.x, i1 = S * (blockIdx.x + 1) / gridDim.x;
+    for (uint64_t i = i0 + threadIdx.x; i < i1; i += kTrainThreads) {
+        const float t = ts ? ts[i] : ((float)i + 0.5f) * scale;
+        g[kParams] += mlp_accumulate(p, xs[i], t, scale, g);
+    }
+    block_reduce_red(g, red, out);
+    if (threadIdx.x < kRed) partial[(uint64_t)blockIdx.x * kRed + threadIdx.x] = out[threadIdx.x];
+}
+
+// Fixed-order sum of the per-block partials: grad[0..48], loss = sum r^2 / S.
+__global__ void mlp_grad_sum_kernel(const float* __restrict__ partial, uint32_t blocks, uint64_t S,
+                                    float* __restrict__ grad, float* __restrict__ loss) {
+    const int k = threadIdx.x;
+    if (k >= kRed) return;
+    float s = 0.0f;
+    for (uint32_t b = 0; b < blocks; ++b) s += partial[(uint64_t)b * kRed + k];
+    if (k < kParams) grad[k] = s;
+    else if (loss) *loss = s / (float)S;
+}
+
+// ------------------------------------------------------------ training
+struct TrainArgs {
+    const float* xs;
+    uint64_t S;
+    float* params;        // in: initial parameters, out: trained
+    float* partial;       // [2][gridDim][kRed]
+    unsigned* barrier;    // zeroed
+    float* loss;          // out: loss of the last epoch
+    uint32_t epochs;
+    float lr;
+    uint32_t spin_limit;
+    unsigned long long* status;
+};
+
+__device__ __forceinline__ uint32_t ld_acquire(const unsigned* p) {
+    uint32_t v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// All blocks of the (cooperatively launched, hence co-resident) grid arrive;
+// the wait is bounded and reports CK_ETIMEOUT instead of hanging.
+__device__ void grid_barrier(unsigned* ctr, unsigned target, uint32_t limit, unsigned long long* status) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        atomicAdd(ctr, 1u);
+        uint32_t polls = 0;
+        while (ld_acquire(ctr) < target) {
+            if (++polls > limit) {
+                report(status, CK_ETIMEOUT, (1ull << 46) | target);
+                break;
+            }
+            __nanosleep(64);
+        }
+        __threadfence();
+    }
+    __syncthreads();
+}
+
+// Full-batch Adam (beta1 0.9, beta2 0.999, eps 1e-8).  Every block keeps the
+// parameters and the moments in shared memory and applies the same update to
+// the same fixed-order gradient sum, so all copies stay identical.
+__global__ void __launch_bounds__(kTrainThreads) mlp_train_kernel(const TrainArgs a) {
+    __shared__ float p[kParams], m1[kParams], m2[kParams];
+    __shared__ float red[(kTrainThreads / 32) * kRed];
+    __shared__ float out[kRed];
+    const int tid = threadIdx.x;
+    if (tid < kParams) {
+        p[tid] = a.params[tid];
+        m1[tid] = 0.0f;
+        m2[tid] = 0.0f;
+    }
+    __syncthreads();
+    const float scale = 1.0f / (float)a.S;
+    const uint64_t i0 = a.S * blockIdx.x / gridDim.x, i1 = a.S * (blockIdx.x + 1) / gridDim.x;
+    float b1t = 1.0f, b2t = 1.0f, last_loss = 0.0f;
+    for (uint32_t ep = 0; ep < a.epochs; ++ep) {
+        float g[kRed];
+#pragma unroll
+        for (int q = 0; q < kRed; ++q) g[q] = 0.0f;
+        for (uint64_t i = i0 + tid; i < i1; i += kTrainThreads)
+            g[kParams] += mlp_accumulate(p, a.xs[i], ((float)i + 0.5f) * scale, scale, g);
+        block_reduce_red(g, red, out);
+        float* part = a.partial + (uint64_t)(ep & 1) * gridDim.x * kRed;
+        if (tid < kRed) part[(uint64_t)blockIdx.x * kRed + tid] = out[tid];
+        grid_barrier(a.barrier, (ep + 1) * gridDim.x, a.spin_limit, a.status);
+        b1t *= 0.9f;
+        b2t *= 0.999f;
+        if (tid < kRed) {
+            float s = 0.0f;
+            for (uint32_t b = 0; b < gridDim.x; ++b) s += __ldcg(&part[(uint64_t)b * kRed + tid]);
+            if (tid < kParams) {
+                m1[tid] = 0.9f * m1[tid] + 0.1f * s;
+                m2[tid] = 0.999f * m2[tid] + 0.001f * s * s;
+                const float mh = m1[tid] / (1.0f - b1t), vh = m2[tid] / (1.0f - b2t);
+                p[tid] -= a.lr * mh / (sqrtf(vh) + 1e-8f);
+            } else {
+                last_loss = s * scale;
+            }
+        }
+        __syncthreads();
+    }
+    if (blockIdx.x == 0) {
+        if (tid < kParams) a.params[tid] = p[tid];
+        if (tid == kParams && a.loss) *a.loss = last_loss;
+    }
+}
+
+
+// ------------------------------------------------------------ splitters
+// Multi-word comparison of key a (K words, entry-major or registers) with b.
+__device__ __forceinline__ int cmp_words(const uint32_t* a, const uint32_t* b, uint32_t K) {
+    for (int w = (int)K - 1; w >= 0; --w)
+        if (a[w] != b[w]) return a[w] < b[w] ? -1 : 1;
+    return 0;
+}
+
+// Splitter b (1 <= b < B) is the sample key at idx_b = floor(b * S / B) of the
+// sorted sample (or at first[b] when given).
+__global__ void splitter_kernel(const uint32_t* __restrict__ sample, uint64_t ld_s, uint64_t S, uint32_t K,
+                                uint32_t B, const uint32_t* __restrict__ first, uint32_t* __restrict__ spl) {
+    for (uint32_t b = blockIdx.x * blockDim.x + threadIdx.x + 1; b < B; b += gridDim.x * blockDim.x) {
+        uint64_t idx = first ? first[b] : (uint64_t)b * S / B;
+        if (idx >= S) idx = S - 1;  // no sample reaches b / B: the largest sample key
+        for (uint32_t w = 0; w < K; ++w) spl[(uint64_t)(b - 1) * K + w] = sample[(uint64_t)w * ld_s + idx];
+    }
+}
+
+// Heavy keys: in a run of equal splitters v (length >= 2) the last becomes
+// v + 1, so that bucket [v, v + 1) holds exactly the copies of v (a bucket of
+// equal keys needs no sorting).  Monotonicity is kept since the next splitter
+// is > v.  Writes the final splitters to out.
+__global__ void singleton_kernel(const uint32_t* __restrict__ spl, uint32_t K, uint32_t B, uint32_t nbits,
+                                 uint32_t* __restrict__ out) {
+    for (uint32_t b = blockIdx.x * blockDim.x + threadIdx.x; b + 1 < B; b += gridDim.x * blockDim.x) {
+        const uint32_t* v = spl + (uint64_t)b * K;
+        uint32_t* o = out + (uint64_t)b * K;
+        bool last_of_run = b > 0 && cmp_words(v, v - K, K) == 0 && (b + 2 == B || cmp_words(v, v + K, K) != 0);
+        uint32_t carry = last_of_run ? 1u : 0u;
+        // v + 1 must still fit nbits bits; the all-ones key keeps its value
+        bool all_ones = true;
+        for (uint32_t w = 0; w < K; ++w) {
+            const uint32_t bits = min(32u, nbits > 32 * w ? nbits - 32 * w : 0u);
+            const uint32_t full = bits == 32 ? 0xFFFFFFFFu : ((1u << bits) - 1u);
+            all_ones = all_ones && v[w] == full;
+        }
+        if (all_ones) carry = 0;
+        for (uint32_t w = 0; w < K; ++w) {
+            const uint64_t sum = (uint64_t)v[w] + carry;
+            o[w] = (uint32_t)sum;
+            carry = (uint32_t)(sum >> 32);
+        }
+    }
+}
+
+// ------------------------------------------------------------ bucket ids
+struct BucketArgs {
+    const uint32_t* ck;
+    uint64_t ld, n;
+    uint32_t K, nbits, B, bucket_bits, use_model;
+    const uint32_t* spl;  // [(B - 1) * K], entry-major, non-decreasing
+    const float* params;
+    uint32_t* bkt;        // [n]
+    uint32_t* hist;       // [2][256] digit histograms of the bucket id (low byte, high bits)
+    unsigned long long* steps;  // [0]: total search steps, [1]: max
+};
+
+// Bucket of key x: the number of splitters <= x, i.e. the b with
+// spl[b-1] <= x < spl[b] (spl[-1] = -inf, spl[B-1] = +inf), searched in
+// [lo, hi]; counts the splitter comparisons in *cmp.
+__device__ __forceinline__ uint32_t bucket_search(const uint32_t* key, const uint32_t* spl, uint32_t K, uint32_t lo,
+                                                  uint32_t hi, uint32_t* cmp) {
+    while (lo < hi) {
+        const uint32_t mid = (lo + hi) >> 1;  // is x >= spl[mid]?
+        ++*cmp;
+        if (cmp_words(key, spl + (uint64_t)mid * K, K) >= 0) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
+}
+
+// Exact bucket from a guess g: check the guess's range, then gallop away from
+// it (1, 2, 4, ... buckets) and finish with a binary search, so a guess that
+// is e buckets off costs about 2 log2(e) + 2 comparisons.
+__device__ __forceinline__ uint32_t bucket_from_guess(const uint32_t* key, const uint32_t* spl, uint32_t K,
+                                                      uint32_t B, uint32_t g, uint32_t* cmp) {
+    ++*cmp;
+    if (g > 0 && cmp_words(key, spl + (uint64_t)(g - 1) * K, K) < 0) {  // below: gallop down
+        uint32_t hi = g - 1, step = 1;                                  // answer <= g - 1
+        while (true) {
+            const uint32_t probe = hi >= step ? hi - step : 0;          // is x >= spl[probe]?
+            ++*cmp;
+            if (probe == 0 && cmp_words(key, spl, K) < 0) return 0;
+            if (cmp_words(key, spl + (uint64_t)probe * K, K) >= 0) return bucket_search(key, spl, K, probe + 1, hi, cmp);
+            hi = probe;
+            if (probe == 0) return 0;
+            step <<= 1;
+        }
+    }
+    ++*cmp;
+    if (g < B - 1 && cmp_words(key, spl + (uint64_t)g * K, K) >= 0) {  // above: gallop up
+        uint32_t lo = g + 1, step = 1;                                 // answer >= g + 1
+        while (true) {
+            const uint32_t probe = lo + step - 1 < B - 1 ? lo + step - 1 : B - 2;  // is x < spl[probe]?
+            ++*cmp;
+            if (cmp_words(key, spl + (uint64_t)probe * K, K) < 0) return bucket_search(key, spl, K, lo, probe, cmp);
+            lo = probe + 1;
+            if (probe == B - 2) return B - 1;
+            step <<= 1;
+        }
+    }
+    return g;
+}
+
+__global__ void __launch_bounds__(256) bucket_kernel(const BucketArgs a) {
+    __shared__ float p[kParams];
+    __shared__ uint32_t hlo[256], hhi[256];
+    __shared__ unsigned long long s_sum, s_max;
+    const int tid = threadIdx.x;
+    if (tid < kParams) p[tid] = a.params ? a.params[tid] : 0.0f;
+    hlo[tid] = 0;
+    hhi[tid] = 0;
+    if (tid == 0) {
+        s_sum = 0;
+        s_max = 0;
+    }
+    __syncthreads();
+    const uint32_t B = a.B, K = a.K;
+    unsigned long long my_sum = 0, my_max = 0;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + tid; i < a.n; i += (uint64_t)gridDim.x * blockDim.x) {
+        uint32_t key[kMaxLearnedWords];
+#pragma unroll
+        for (uint32_t w = 0; w < kMaxLearnedWords; ++w) key[w] = w < K ? a.ck[(uint64_t)w * a.ld + i] : 0u;
+        uint32_t g, steps = 0;
+        if (a.use_model) {
+            const float y = mlp_eval(p, key_feature(a.ck, a.ld, i, K, a.nbits)) * (float)B;
+            const uint32_t guess = y <= 0.0f ? 0u : (y >= (float)(B - 1) ? B - 1 : (uint32_t)y);
+            g = bucket_from_guess(key, a.spl, K, B, guess, &steps);
+        } else {
+            g = bucket_search(key, a.spl, K, 0, B - 1, &steps);
+        }
+        a.bkt[i] = g;
+        atomicAdd(&hlo[g & 255u], 1u);
+        atomicAdd(&hhi[g >> 8], 1u);
+        my_sum += steps;
+        my_max = my_max > steps ? my_max : steps;
+    }
+    atomicAdd(&s_sum, my_sum);
+    atomicMax(&s_max, my_max);
+    __syncthreads();
+    if (hlo[tid]) atomicAdd(&a.hist[tid], hlo[tid]);
+    if (hhi[tid]) atomicAdd(&a.hist[256 + tid], hhi[tid]);
+    if (tid == 0) {
+        atomicAdd(&a.steps[0], s_sum);
+        atomicMax(&a.steps[1], s_max);
+    }
+}
+
+// ------------------------------------------------------------ bucket sorts
+struct LocalArgs {
+    uint32_t* ck;          // partitioned, sorted in place; word-major, leading dimension ld
+    uint32_t* rid;
+    const uint32_t* bkt;   // bucket id of every position (non-decreasing)
+    const uint32_t* spl;   // final splitters
+    uint64_t ld, n, chunk;
+    uint32_t K, B, cap;
+    uint32_t* flags;       // [0] oversize buckets, [1] order violations
+    uint32_t* counts;      // [0] segments sorted, [1] constant buckets, [2] max bucket
+};
+
+__device__ uint64_t upper_bound_u32(const uint32_t* a, uint64_t n, uint32_t v) {
+    uint64_t lo = 0, hi = n;
+    while (lo < hi) {
+        const uint64_t mid = (lo + hi) >> 1;
+        if (a[mid] <= v) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
+}
+
+// Bucket b holds only equal keys when its range is [v, v + 1).
+__device__ bool constant_bucket(const uint32_t* spl, uint32_t K, uint32_t B, uint32_t b) {
+    if (b == 0 || b + 1 >= B) return false;
+    const uint32_t* lo = spl + (uint64_t)(b - 1) * K;
+    const uint32_t* hi = spl + (uint64_t)b * K;
+    uint32_t carry = 1;
+    for (uint32_t w = 0; w < K; ++w) {  // hi == lo + 1 ?
+        const uint64_t sum = (uint64_t)lo[w] + carry;
+        if ((uint32_t)sum != hi[w]) return false;
+        carry = (uint32_t)(sum >> 32);
+    }
+    return carry == 0;
+}
+
+// Block j sorts the buckets that start in positions [j * chunk, (j+1) * chunk):
+// consecutive buckets are grouped while the group fits `cap` pairs and each
+// group is bitonic-sorted in shared memory on (key, position), which is a
+// stable sort; it is written back to the same positions.
+__global__ void __launch_bounds__(1024) local_sort_kernel(const LocalArgs a) {
+    extern __shared__ __align__(16) uint32_t lsm[];
+    const uint32_t K = a.K, cap = a.cap;
+    uint32_t* keys = lsm;                                          // [K][cap]
+    uint32_t* rids = keys + (size_t)K * cap;                       // [cap]
+    uint16_t* idx = reinterpret_cast<uint16_t*>(rids + cap);       // [cap]
+    __shared__ uint64_t s_range[2];
+    const uint32_t tid = threadIdx.x;
+    const uint64_t c0 = blockIdx.x * a.chunk;
+    const uint64_t c1 = min(a.n, c0 + a.chunk);
+    if (tid == 0) {
+        uint64_t s0 = (c0 == 0 || a.bkt[c0] != a.bkt[c0 - 1]) ? c0 : upper_bound_u32(a.bkt, a.n, a.bkt[c0]);
+        s_range[0] = s0;
+        s_range[1] = s0 < c1 ? upper_bound_u32(a.bkt, a.n, a.bkt[c1 - 1]) : s0;
+    }
+    __syncthreads();
+    const uint64_t s0 = s_range[0], e0 = s_range[1];
+    __shared__ uint64_t g_range[2];
+    __shared__ uint32_t g_kind;  // 0: sort, 1: skip (constant or oversize)
+    uint64_t bs = s0;
+    while (bs < e0) {
+        if (tid == 0) {
+            uint64_t ge = upper_bound_u32(a.bkt, a.n, a.bkt[bs]);
+            const uint64_t first_size = ge - bs;
+            atomicMax(&a.counts[2], (uint32_t)(first_size < 0xFFFFFFFFull ? first_size : 0xFFFFFFFFull));
+            uint32_t kind = 0;
+            if (first_size > cap) {
+                if (constant_bucket(a.spl, K, a.B, a.bkt[bs])) {
+                    kind = 1;
+                    atomicAdd(&a.counts[1], 1u);
+                } else {
+                    kind = 1;
+                    atomicAdd(&a.flags[0], 1u);
+                }
+            } else {
+                while (ge < e0) {
+                    const uint64_t nx = upper_bound_u32(a.bkt, a.n, a.bkt[ge]);
+                    if (nx - bs > cap) break;
+                    atomicMax(&a.counts[2], (uint32_t)(nx - ge));
+                    ge = nx;
+                }
+                atomicAdd(&a.counts[0], 1u);
+            }
+            g_range[0] = bs;
+            g_range[1] = ge;
+            g_kind = kind;
+        }
+        __syncthreads();
+        const uint64_t s = g_range[0], e = g_range[1];
+        const uint32_t kind = g_kind;
+        __syncthreads();
+        bs = e;
+        if (kind != 0) continue;
+        const uint32_t m = (uint32_t)(e - s);
+        uint32_t P = 1;
+        while (P < m) P <<= 1;
+        for (uint32_t t = tid; t < m; t += blockDim.x) {
+            for (uint32_t w = 0; w < K; ++w) keys[(size_t)w * cap + t] = a.ck[(uint64_t)w * a.ld + s + t];
+            rids[t] = a.rid[s + t];
+        }
+        for (uint32_t t = tid; t < P; t += blockDim.x) idx[t] = t < m ? (uint16_t)t : (uint16_t)0xFFFF;
+        __syncthreads();
+        // true if the element at slot position u must come after the one at v
+        auto after = [&](uint32_t u, uint32_t v) -> bool {
+            if (u == 0xFFFF) return v != 0xFFFF;
+            if (v == 0xFFFF) return false;
+            for (int w = (int)K - 1; w >= 0; --w) {
+                const uint32_t ku = keys[(size_t)w * cap + u], kv = keys[(size_t)w * cap + v];
+                if (ku != kv) return ku > kv;
+            }
+            return u > v;  // equal keys keep their partition order
+        };
+        for (uint32_t k = 2; k <= P; k <<= 1) {
+            for (uint32_t j = k >> 1; j > 0; j >>= 1) {
+                for (uint32_t t = tid; t < P; t += blockDim.x) {
+                    const uint32_t l = t ^ j;
+                    if (l > t) {
+                        const uint32_t u = idx[t], v = idx[l];
+                        const bool up = (t & k) == 0;
+                        if (up ? after(u, v) : after(v, u)) {
+                            idx[t] = (uint16_t)v;
+                            idx[l] = (uint16_t)u;
+                        }
+                    }
+                }
+                __syncthreads();
+            }
+        }
+        for (uint32_t t = tid; t < m; t += blockDim.x) {
+            const uint32_t src = idx[t];
+            for (uint32_t w = 0; w < K; ++w) a.ck[(uint64_t)w * a.ld + s + t] = keys[(size_t)w * cap + src];
+            a.rid[s + t] = rids[src];
+        }
+        __syncthreads();
+    }
+}
+
+// Every adjacent output pair must be in (key, row id) order.
+__global__ void verify_kernel(const uint32_t* __restrict__ ck, const uint32_t* __restrict__ rid, uint64_t ld,
+                              uint64_t n, uint32_t K, uint32_t* __restrict__ flags) {
+    uint32_t bad = 0;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x + 1; i < n;
+         i += (uint64_t)gridDim.x * blockDim.x) {
+        int c = 0;
+        for (int w = (int)K - 1; w >= 0 && c == 0; --w) {
+            const uint32_t x = ck[(uint64_t)w * ld + i - 1], y = ck[(uint64_t)w * ld + i];
+            c = x < y ? -1 : (x > y ? 1 : 0);
+        }
+        if (c > 0 || (c == 0 && rid[i - 1] >= rid[i])) ++bad;
+    }
+    if (bad) atomicAdd(&flags[1], bad);
+}
+
+// ------------------------------------------------------------ workspace
+struct LearnedPlan {
+    uint32_t B, bucket_bits, passes, K, nbits;
+    uint64_t S, ld_s, n, ld, div, chunk;
+    uint32_t cap, epochs, train_blocks, flags;
+    float lr;
+    SortPlan sample_sort, plain;
+    size_t off_sample, off_sample_sorted, off_sample_rid, off_sample_ws, off_xs, off_params, off_partial,
+        off_misc, off_spl, off_spl_final, off_bkt, off_alt_bkt, off_alt_ck, off_alt_rid, off_hist,
+        off_lookback, off_plain_ws, total;
+};
+
+static size_t a256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+static bool make_learned_plan(uint64_t n, uint32_t K, uint32_t nbits, const ck_learned_opts* o, LearnedPlan* p) {
+    memset(p, 0, sizeof(*p));
+    p->bucket_bits = o && o->bucket_bits ? o->bucket_bits : 16;
+    if (p->bucket_bits < 8 || p->bucket_bits > 16) return false;
+    p->B = 1u << p->bucket_bits;
+    p->passes = p->bucket_bits > 8 ? 2 : 1;
+    p->div = o && o->sample_div ? o->sample_div : 100;
+    p->epochs = o && o->epochs ? o->epochs : 100;
+    p->lr = o && o->lr > 0.0f ? o->lr : 1e-3f;
+    p->flags = o ? o->flags : 0u;
+    p->K = K;
+    p->nbits = nbits;
+    p->n = n;
+    p->ld = CK_LD(n);
+    p->S = n / p->div;
+    if (p->S < 2) p->S = n < 2 ? n : 2;
+    p->ld_s = CK_LD(p->S);
+    p->chunk = 4096;
+    // bucket capacity of one block: (K + 1) words per pair + a 16-bit index, <= 200 KB
+    uint32_t cap = 8192;
+    while (cap > 256 && (size_t)cap * (4 * (K + 1) + 2) > 200 * 1024) cap >>= 1;
+    p->cap = cap;
+    p->train_blocks = (uint32_t)num_sms();
+    if (!make_sort_plan(p->S, K, nbits, 8, &p->sample_sort)) return false;
+    if (!make_sort_plan(n, K, nbits, 8, &p->plain)) return false;
+    const uint64_t tiles = (n + kPassTile - 1) / kPassTile;
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        const size_t at = off;
+        off = a256(off + bytes);
+        return at;
+    };
+    p->off_sample = take(4ull * K * p->ld_s);
+    p->off_sample_sorted = take(4ull * K * p->ld_s);
+    p->off_sample_rid = take(4ull * p->S);
+    p->off_sample_ws = take(p->sample_sort.total);
+    p->off_xs = take(4ull * p->S);
+    p->off_params = take(4ull * kParams);
+    p->off_partial = take(4ull * 2 * p->train_blocks * kRed);
+    p->off_misc = take(256);  // barrier, loss, flags[2], counts[3], steps[2] (u64)
+    p->off_spl = take(4ull * K * p->B);
+    p->off_spl_final = take(4ull * K * p->B);
+    p->off_bkt = take(4ull * n);
+    p->off_alt_bkt = take(4ull * n);
+    p->off_alt_ck = take(4ull * K * p->ld);
+    p->off_alt_rid = take(4ull * n);
+    p->off_hist = take(4ull * 512);
+    p->off_lookback = take(4ull * 256 * tiles * p->passes + 4 * p->passes);
+    p->off_plain_ws = take(p->plain.total);
+    p->total = off;
+    return true;
+}
+
+}  // namespace ck
+
+using namespace ck;
+
+namespace {
+struct Misc {  // layout of the misc block of the learned workspace
+    unsigned barrier;
+    float loss;
+    uint32_t flags[2];   // oversize buckets, order violations
+    uint32_t counts[3];  // segments sorted, constant buckets, max bucket
+    uint32_t pad;
+    unsigned long long steps[2];
+};
+}  // namespace
+
+extern "C" {
+
+size_t ck_mlp_workspace_bytes(void) { return (size_t)4 * 1024 * kRed; }
+
+ck_status ck_mlp_loss_grad(const float* params, const float* x, const float* t, uint64_t S, float* grad_out,
+                           float* loss_out, void* ws, size_t ws_bytes, ck_stream stream) {
+    if (!params || !x || !grad_out || S == 0) return CK_EINVAL;
+    if (!ws || ws_bytes < ck_mlp_workspace_bytes()) return CK_ENOMEM;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const uint64_t want = (S + kTrainThreads - 1) / kTrainThreads;
+    const uint32_t blocks = (uint32_t)(want < 1024 ? want : 1024);
+    float* partial = static_cast<float*>(ws);
+    mlp_grad_kernel<<<blocks, kTrainThreads, 0, s>>>(params, x, t, S, partial);
+    mlp_grad_sum_kernel<<<1, 64, 0, s>>>(partial, blocks, S, grad_out, loss_out);
+    count_launch(2);
+    return cudaGetLastError() == cudaSuccess ? CK_OK : CK_ECUDA;
+}
+
+size_t ck_sort_learned_workspace_bytes(uint64_t n, uint32_t ck_words, uint32_t nbits, const ck_learned_opts* opts) {
+    LearnedPlan p;
+    if (ck_words == 0 || ck_words > kMaxLearnedWords || !make_learned_plan(n, ck_words, nbits, opts, &p)) return 0;
+    return p.total;
+}
+
+ck_status ck_sort_learned(const uint32_t* ck_in, uint32_t* ck_out, uint32_t* rid_out, uint64_t n, uint32_t ck_words,
+                          uint32_t nbits, const ck_learned_opts* opts, ck_learned_stats* stats, float* params_out,
+                          void* ws_v, size_t ws_bytes, ck_stream stream) {
+    if (n > CK_MAX_ROWS || ck_words == 0 || ck_words > kMaxLearnedWords || nbits > 32u * ck_words) return CK_EINVAL;
+    if (opts && (opts->reserved != 0 || (opts->flags & ~3u))) return CK_EINVAL;
+    if (stats) memset(stats, 0, sizeof(*stats));
+    if (n == 0) return CK_OK;
+    if (!ck_in || !ck_out || !rid_out || ck_in == ck_out) return CK_EINVAL;
+    LearnedPlan P;
+    if (!make_learned_plan(n, ck_words, nbits, opts, &P)) return CK_EINVAL;
+    if (!ws_v || ws_bytes < P.total || (reinterpret_cast<uintptr_t>(ws_v) & 255)) return CK_ENOMEM;
+    unsigned long long* status = status_ptr();
+    if (!status) return CK_ECUDA;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    unsigned char* ws = static_cast<unsigned char*>(ws_v);
+    auto at = [&](size_t off) { return reinterpret_cast<uint32_t*>(ws + off); };
+    const uint32_t K = ck_words;
+    const bool use_model = !(P.flags & CK_LEARNED_NO_MODEL);
+    cudaError_t e = cudaSuccess;
+#define CK_TRY(x)                                \
+    do {                                         \
+        if ((e = (x)) != cudaSuccess) return CK_ECUDA; \
+    } while (0)
+    Misc* misc = reinterpret_cast<Misc*>(ws + P.off_misc);
+    CK_TRY(cudaMemsetAsync(misc, 0, sizeof(Misc), s));
+    CK_TRY(cudaMemsetAsync(ws + P.off_hist, 0, 4ull * 512, s));
+    CK_TRY(cudaMemsetAsync(ws + P.off_lookback, 0, P.off_plain_ws - P.off_lookback, s));
+    const int sms = num_sms();
+
+    // 1. sample, sort the sample, features
+    sample_kernel<<<sms * 4, 256, 0, s>>>(ck_in, P.ld, K, P.div, P.S, at(P.off_sample), P.ld_s);
+    count_launch();
+    CK_TRY(run_sort(P.sample_sort, at(P.off_sample), nullptr, at(P.off_sample_sorted), at(P.off_sample_rid), P.S,
+                    nbits, kDefaultSpin, 0, 0, nullptr, ws + P.off_sample_ws, s));
+    float* xs = reinterpret_cast<float*>(ws + P.off_xs);
+    features_kernel<<<sms * 4, 256, 0, s>>>(at(P.off_sample_sorted), P.ld_s, P.S, K, nbits, xs);
+    count_launch();
+
+    // 2. model: spline initialisation, full-batch Adam (cooperative launch)
+    float* params = reinterpret_cast<float*>(ws + P.off_params);
+    if (use_model) {
+        mlp_init_kernel<<<1, 32, 0, s>>>(xs, P.S, params);
+        count_launch();
+        TrainArgs ta;
+        ta.xs = xs;
+        ta.S = P.S;
+        ta.params = params;
+        ta.partial = reinterpret_cast<float*>(ws + P.off_partial);
+        ta.barrier = &misc->barrier;
+        ta.loss = &misc->loss;
+        ta.epochs = P.epochs;
+        ta.lr = P.lr;
+        ta.spin_limit = kDefaultSpin;
+        ta.status = status;
+        void* args[] = {&ta};
+        CK_TRY(cudaLaunchCooperativeKernel((const void*)mlp_train_kernel, dim3(P.train_blocks), dim3(kTrainThreads),
+                                           args, 0, s));
+        count_launch();
+    }
+    // 3. splitters: sample quantiles (they cut through long shared prefixes that
+    //    a 24-bit feature cannot see), heavy-key singletons
+    splitter_kernel<<<(P.B + 255) / 256, 256, 0, s>>>(at(P.off_sample_sorted), P.ld_s, P.S, K, P.B, nullptr,
+                                                      at(P.off_spl));
+    singleton_kernel<<<(P.B + 255) / 256, 256, 0, s>>>(at(P.off_spl), K, P.B, nbits, at(P.off_spl_final));
+    count_launch(2);
+
+    // 4. bucket id of every key (model guess + exact correction), digit histograms
+    BucketArgs ba;
+    ba.ck = ck_in;
+    ba.ld = P.ld;
+    ba.n = n;
+    ba.K = K;
+    ba.nbits = nbits;
+    ba.B = P.B;
+    ba.bucket_bits = P.bucket_bits;
+    ba.use_model = use_model ? 1u : 0u;
+    ba.spl = at(P.off_spl_final);
+    ba.params = use_model ? params : nullptr;
+    ba.bkt = at(P.off_bkt);
+    ba.hist = at(P.off_hist);
+    ba.steps = misc->steps;
+    bucket_kernel<<<sms * 8, 256, 0, s>>>(ba);
+    count_launch();
+    CK_TRY(launch_bucket_scan(at(P.off_hist), P.passes, 8, s));
+
+    // 5. stable partition by bucket id: radix passes over its low 8 bits, then the rest
+    auto al16 = [](const void* q) { return (reinterpret_cast<uintptr_t>(q) & 15) == 0; };
+    const uint32_t bulk = al16(ck_in) && al16(ck_out) && al16(rid_out) ? 1u : 0u;
+    const uint64_t tiles = (n + kPassTile - 1) / kPassTile;
+    uint32_t* counters = at(P.off_lookback) + 256ull * tiles * P.passes;
+    static thread_local PassArrays arr;
+    // bucket ids ping-pong between two buffers (never read and written in one
+    // pass); the last pass's copy locates the buckets for the local sorts
+    uint32_t* bkt_src = at(P.off_bkt);
+    uint32_t* bkt_final = bkt_src;
+    for (uint32_t q = 0; q < P.passes; ++q) {
+        const bool last = q + 1 == P.passes;
+        uint32_t m = 0;
+        const uint32_t* src_ck = q == 0 ? ck_in : at(P.off_alt_ck);
+        uint32_t* dst_ck = last ? ck_out : at(P.off_alt_ck);
+        uint32_t* bkt_dst = (q % 2 == 0) ? at(P.off_alt_bkt) : at(P.off_bkt);
+        arr.src[m] = bkt_src;
+        arr.dst[m] = bkt_dst;
+        bkt_src = bkt_dst;
+        bkt_final = bkt_dst;
+        ++m;
+        for (uint32_t w = 0; w < K; ++w, ++m) {
+            arr.src[m] = src_ck + (uint64_t)w * P.ld;
+            arr.dst[m] = dst_ck + (uint64_t)w * P.ld;
+        }
+        arr.src[m] = q == 0 ? nullptr : at(P.off_alt_rid);
+        arr.dst[m] = last ? rid_out : at(P.off_alt_rid);
+        ++m;
+        PassArgs a;
+        a.n = n;
+        a.narr = m;
+        a.sh = 8 * q;
+        a.bits = last ? P.bucket_bits - 8 * q : 8;
+        a.straddle = 0;
+        a.pass = q;
+        a.bulk = bulk;
+        a.bucket_base = at(P.off_hist) + 256 * q;
+        a.lookback = at(P.off_lookback) + 256ull * tiles * q;
+        a.tile_counter = counters + q;
+        a.spin_limit = kDefaultSpin;
+        a.inject = 0;
+        a.status = status;
+        CK_TRY(launch_onesweep_pass(8, a, arr, (uint32_t)tiles, s));
+    }
+
+    // 6. sort every bucket in shared memory, in place
+    LocalArgs la;
+    la.ck = ck_out;
+    la.rid = rid_out;
+    la.bkt = bkt_final;
+    la.spl = at(P.off_spl_final);
+    la.ld = P.ld;
+    la.n = n;
+    la.chunk = P.chunk;
+    la.K = K;
+    la.B = P.B;
+    la.cap = P.cap;
+    la.flags = misc->flags;
+    la.counts = misc->counts;
+    const size_t lsmem = (size_t)P.cap * (4 * (K + 1) + 2);
+    CK_TRY(cudaFuncSetAttribute(local_sort_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lsmem));
+    local_sort_kernel<<<(unsigned)((n + P.chunk - 1) / P.chunk), 1024, lsmem, s>>>(la);
+    count_launch();
+
+    // 7. verification of every adjacent pair
+    verify_kernel<<<sms * 8, 256, 0, s>>>(ck_out, rid_out, P.ld, n, K, misc->flags);
+    count_launch();
+    Misc host;
+    CK_TRY(cudaMemcpyAsync(&host, misc, sizeof(Misc), cudaMemcpyDeviceToHost, s));
+    CK_TRY(cudaStreamSynchronize(s));
+    if (params_out && use_model) CK_TRY(cudaMemcpy(params_out, params, 4 * kParams, cudaMemcpyDeviceToHost));
+    const bool failed = host.flags[0] != 0 || host.flags[1] != 0 || (P.flags & CK_LEARNED_INJECT_VERIFY_FAIL);
+    if (stats) {
+        stats->train_loss = use_model ? host.loss : 0.0f;
+        stats->mean_search_steps = (float)((double)host.steps[0] / (double)n);
+        stats->max_search_steps = (uint32_t)host.steps[1];
+        stats->buckets = P.B;
+        stats->sample_size = (uint32_t)P.S;
+        stats->max_bucket = host.counts[2];
+        stats->sorted_segments = host.counts[0];
+        stats->constant_buckets = host.counts[1];
+        stats->oversize_buckets = host.flags[0];
+        stats->fell_back = failed ? 1u : 0u;
+    }
+    if (!failed) return CK_OK;
+    // fallback: the plain radix sort from the untouched input
+    CK_TRY(run_sort(P.plain, ck_in, nullptr, ck_out, rid_out, n, nbits, kDefaultSpin, 0, 0, nullptr,
+                    ws + P.off_plain_ws, s));
+#undef CK_TRY
+    return CK_EVERIFY;
+}
+
+}  // extern "C"

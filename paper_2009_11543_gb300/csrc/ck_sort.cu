@@ -30,7 +30,6 @@ constexpr int kPassThreads = 512;
 constexpr int kPassItems = 8;
 constexpr int kTile = kPassThreads * kPassItems;  // pairs per tile
 constexpr int kRing = 3;                          // staging buffers per block
-constexpr int kMaxPassArrays = kMaxKeyWords + 2;  // key words, row ids, one extra
 constexpr int kPassBlocksPerSM = 3;
 constexpr int kUpThreads = 256;
 
@@ -120,28 +119,6 @@ __global__ void iota_kernel(uint32_t* out, uint64_t n) {
 }
 
 // ------------------------------------------------------------------ pass
-// The arrays a pass moves, in staging order.  Array 0 (and array 1 when the
-// digit straddles two words) holds the digit.  A NULL source means the values
-// are the input positions (row ids 0..n-1; such an array takes no ring slot);
-// a NULL destination means the array is read for its digit but not carried on.
-struct PassArrays {
-    const uint32_t* src[kMaxPassArrays];
-    uint32_t* dst[kMaxPassArrays];
-};
-
-struct PassArgs {
-    uint64_t n;
-    uint32_t narr;                // arrays in PassArrays
-    uint32_t sh, bits, straddle;  // digit = bits [sh, sh + bits) of array 0 (spilling into array 1)
-    uint32_t pass;
-    uint32_t bulk;                // 1: every array is 16-byte aligned, full tiles stage by TMA
-    const uint32_t* bucket_base;  // [BINS] of this pass
-    uint32_t* lookback;           // [tiles][BINS] of this pass, zeroed
-    uint32_t* tile_counter;       // zeroed
-    uint32_t spin_limit, inject;
-    unsigned long long* status;
-};
-
 // Shared memory of one pass block: a ring of kRing staging buffers (one array
 // of the tile each), per-warp digit counters, per-slot source position,
 // per-digit tile counts and destinations, and the ring's mbarriers.
@@ -370,6 +347,34 @@ static cudaError_t launch_pass(const PassArgs& a, const PassArrays& arrays, uint
                                          (int)smem);
     if (e != cudaSuccess) return e;
     onesweep_pass_kernel<RB><<<tiles, kPassThreads, smem, s>>>(a, arrays);
+    count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_onesweep_pass(uint32_t rb, const PassArgs& a, const PassArrays& arrays, uint32_t tiles,
+                                 cudaStream_t s) {
+    switch (rb) {
+        case 4: return launch_pass<4>(a, arrays, tiles, s);
+        case 5: return launch_pass<5>(a, arrays, tiles, s);
+        case 6: return launch_pass<6>(a, arrays, tiles, s);
+        case 7: return launch_pass<7>(a, arrays, tiles, s);
+        case 8: return launch_pass<8>(a, arrays, tiles, s);
+        case 9: return launch_pass<9>(a, arrays, tiles, s);
+        case 10: return launch_pass<10>(a, arrays, tiles, s);
+        case 11: return launch_pass<11>(a, arrays, tiles, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_bucket_scan(uint32_t* hist, uint32_t sets, uint32_t rb, cudaStream_t s) {
+    switch (rb) {
+        case 4: scan_kernel<4><<<sets, 256, 0, s>>>(hist); break;
+        case 5: scan_kernel<5><<<sets, 256, 0, s>>>(hist); break;
+        case 6: scan_kernel<6><<<sets, 256, 0, s>>>(hist); break;
+        case 7: scan_kernel<7><<<sets, 256, 0, s>>>(hist); break;
+        case 8: scan_kernel<8><<<sets, 256, 0, s>>>(hist); break;
+        default: return cudaErrorInvalidValue;
+    }
     count_launch();
     return cudaGetLastError();
 }

@@ -27,7 +27,8 @@ class Rebuild:
     """
 
     def __init__(self, keys: torch.Tensor, dmask: np.ndarray, fanout: int = 64, fill: float = 1.0,
-                 digit_bits: int = 8, ck_words: int | None = None, kind: int | None = None, perm_only: bool = False):
+                 digit_bits: int = 8, ck_words: int | None = None, kind: int | None = None, perm_only: bool = False,
+                 learned: bool = False, learned_opts=None):
         self.keys = keys
         self.kind = kind
         self.col = ck.column(keys, kind)
@@ -40,12 +41,18 @@ class Rebuild:
         # perm_only: the sort returns only the permutation (and stops carrying
         # consumed key words); the tree is then built from the key column
         self.perm_only = perm_only
+        # learned: the sort is the learned-partition sort (same output bits)
+        self.learned = learned
+        self.learned_opts = learned_opts
+        self.learned_stats = None
         dev = keys.device
         n = max(self.n, 1)
         self.ck_in = ck.ck_buffer(self.K, n, dev)
         self.ck_sorted = ck.ck_buffer(self.K, n, dev)
         self.rid_sorted = torch.empty(n, dtype=torch.int32, device=dev)
         wsb = ck.ck_sort_workspace_bytes(self.n, self.K, self.nbits, digit_bits)
+        if learned:
+            wsb = max(wsb, ck.ck_sort_learned_workspace_bytes(self.n, self.K, self.nbits, learned_opts))
         self.ws = torch.empty(max(wsb, 256), dtype=torch.uint8, device=dev)
         self.shape = ck.ck_btree_plan(self.n, fanout, fill)
         self.tree = ck.alloc_btree(self.shape, self.K, dev)
@@ -55,6 +62,11 @@ class Rebuild:
         ck.ck_extract(self.keys, self.dmask, self.K, out=self.ck_in, kind=self.kind, stream=stream)
 
     def sort(self, stream=None, pass_events=None):
+        if self.learned:
+            st, self.learned_stats, _ = ck.ck_sort_learned(self.ck_in, self.ck_sorted, self.rid_sorted, self.n,
+                                                           self.K, self.nbits, self.ws, self.learned_opts,
+                                                           stream=stream)
+            return
         ck.ck_sort(self.ck_in, None, self.ck_sorted, self.rid_sorted, self.n, self.K, self.nbits, self.ws,
                    digit_bits=self.digit_bits, pass_events=pass_events, perm_only=self.perm_only, stream=stream)
 

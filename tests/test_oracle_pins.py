@@ -407,3 +407,42 @@ def test_generator_shapes():
     # 0x41,0x43,0x47,0x54: only bit positions 3, 5, 6 of each byte can distinguish
     Dd = positions_of(oracle.dmask(d), 256)
     assert set(p % 8 for p in Dd) <= {3, 5, 6}
+
+
+# ------------------------------------------------------ learned CDF model
+def test_mlp_oracle_finite_differences():
+    """fp64 gradient of the oracle against central differences (h = 1e-6)."""
+    rng = np.random.default_rng(77)
+    p = rng.normal(0, 1, oracle.MLP_PARAMS)
+    x = rng.random(300)
+    t = np.sort(rng.random(300))
+    _, g = oracle.mlp_loss_grad(p, x, t)
+    h = 1e-6
+    for k in range(oracle.MLP_PARAMS):
+        a, b = p.copy(), p.copy()
+        a[k] += h
+        b[k] -= h
+        fd = (oracle.mlp_loss_grad(a, x, t)[0] - oracle.mlp_loss_grad(b, x, t)[0]) / (2 * h)
+        assert abs(fd - g[k]) <= 1e-6 * max(1.0, abs(g[k])), (k, fd, g[k])
+
+
+def test_mlp_oracle_closed_forms():
+    """Special cases with a closed form: all hidden units off leaves only b2,
+    and a single active unit is a straight line."""
+    x = np.linspace(0.0, 1.0, 11)
+    t = x.copy()
+    p = np.zeros(oracle.MLP_PARAMS)
+    p[3 * 16] = 0.25                                   # y = 0.25 everywhere
+    loss, g = oracle.mlp_loss_grad(p, x, t)
+    assert loss == pytest.approx(np.mean((0.25 - x) ** 2))
+    assert g[48] == pytest.approx(2 * np.mean(0.25 - x))
+    assert np.all(g[:48] == 0)
+    p = np.zeros(oracle.MLP_PARAMS)
+    p[0], p[16], p[32] = 1.0, 0.5, 2.0                 # y = 2 * (x + 0.5)
+    assert oracle.mlp_forward(p, 0.3) == pytest.approx(1.6)
+    loss, g = oracle.mlp_loss_grad(p, x, t)
+    r = 2 * (x + 0.5) - t
+    assert loss == pytest.approx(np.mean(r ** 2))
+    assert g[32] == pytest.approx(np.mean(2 * r * (x + 0.5)))
+    assert g[0] == pytest.approx(np.mean(2 * r * 2.0 * x))
+    assert g[16] == pytest.approx(np.mean(2 * r * 2.0))
