@@ -52,7 +52,11 @@ WORKLOADS = {
                 "+ bulk load with fanout 256", 200_000_000, "dna", 256, 4_000_000, "learned"),
     "int1m": ("1M uint64 keys with 24 seeded varying bit positions, fanout 64", 1_000_000, "int", 64, 1_000_000,
               "plain"),
+    "table16m": ("one table of 16M rows with 6 indexes of key widths 4, 8, 12, 16, 32, 64 bytes (uint32 uniform, "
+                 "uint64 sequential+noise, Zipf-prefixed strings), all rebuilt in one graph-captured batched launch, "
+                 "digit width autotuned per index", 16 * 2**20, "table", 64, 1_000_000, "batched"),
 }
+TABLE_FANOUTS = [64, 64, 64, 64, 256, 256]
 
 
 def gen_keys(kind: str, n: int):
@@ -145,6 +149,137 @@ class ClockSampler:
 
 
 # --------------------------------------------------------------------- ours
+def run_table(args, rank, world, local_rank):
+    """The batched workload: every index of one table per step, one graph launch."""
+    import torch
+    import synth
+    from paper_2009_11543_gb300 import build as b
+    b.build()
+    from paper_2009_11543_gb300 import ck, metrics, pipeline
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    desc, n, kind, fanout, cpu_rows, main_path = WORKLOADS[args.workload]
+    cols_np = synth.table_columns(n, synth.BASE_SEED + 3)
+
+    def as_tensor(c):
+        return torch.from_numpy(c.view(np.int64) if c.dtype == np.uint64 else
+                                (c.view(np.int32) if c.dtype == np.uint32 else c))
+    hosts = [as_tensor(c).pin_memory() for c in cols_np]
+    cols = [h.to(dev) for h in hosts]
+    dmasks = [pipeline.first_build_dmask(c) for c in cols]
+    cache = os.path.join(tempfile.gettempdir(), "ck_autotune_%d.txt" % os.getpid())
+    B = pipeline.BatchedRebuild(cols, dmasks, TABLE_FANOUTS, cache_path=cache, tune_reps=3)
+    seq = [pipeline.Rebuild(c, m, fanout=f, digit_bits=8) for c, m, f in zip(cols, dmasks, TABLE_FANOUTS)]
+    full = [pipeline.Rebuild(c, pipeline.full_key_mask(8 * (c.shape[1] if c.dim() == 2 else c.element_size())),
+                             fanout=f, digit_bits=8) for c, f in zip(cols, TABLE_FANOUTS)]
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        torch.cuda.synchronize()
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    def timed(fn, steps, warmup):
+        for _ in range(warmup):
+            fn()
+        barrier()
+        l0 = ck.ck_launch_count()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            fn()
+        e1.record(stream)
+        barrier()
+        return e0.elapsed_time(e1) / steps, ck.ck_launch_count() - l0
+
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    time.sleep(0.2)
+    B.capture()
+    graph_ms, graph_launches = timed(B.launch, args.steps, args.warmup)
+    streams_ms, stream_launches = timed(B.run, args.steps, args.warmup)
+
+    def seq_run():
+        for r in seq:
+            r.run()
+    seq_ms, _ = timed(seq_run, args.steps, args.warmup)
+
+    def full_run():
+        for r in full:
+            r.run()
+    full_ms, _ = timed(full_run, max(1, args.steps // 2), args.warmup)
+    rid_hosts = [torch.empty(n, dtype=torch.int32, pin_memory=True) for _ in cols]
+
+    def e2e_step():
+        for c, h in zip(cols, hosts):
+            c.copy_(h, non_blocking=True)
+        B.launch()
+        for r, h in zip(B.parts, rid_hosts):
+            h.copy_(r.rid_sorted[:n], non_blocking=True)
+    e2e_ms, _ = timed(e2e_step, args.steps, args.warmup)
+    clk = clocks.stop()
+    status, detail = ck.ck_device_status()
+    if status != ck.CK_OK:
+        raise RuntimeError("device status %s (detail %d)" % (ck.ck_status_string(status), detail))
+    B.close()
+    times = np.array([graph_ms, e2e_ms, seq_ms, full_ms], np.float64)
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.from_numpy(times)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        times = t.numpy()
+    graph_ms, e2e_ms, seq_ms, full_ms = (float(x) for x in times)
+    if rank != 0:
+        return None
+    keys = 6 * n
+    peak, peak_src = peaks()
+    alg = 0
+    for r in B.parts:
+        kb = r.key_bits // 8
+        alg += metrics.extract_bytes(n, kb, r.K) + metrics.radix_passes(r.nbits, r.digit_bits) * \
+            metrics.pass_bytes(n, r.K) + metrics.build_bytes(n, r.K)
+    achieved = alg / (graph_ms / 1e3) / 1e9
+    return {
+        "metric": METRIC, "value": world * keys / (graph_ms / 1e3), "unit": "keys/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": graph_ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+        "data": "synthetic (seeded generators standing in for a table with integer and title columns)",
+        "config": {"workload": desc, "rows": n, "indexes": 6,
+                   "key_bytes": [r.key_bits // 8 for r in B.parts], "distinction_bits": [r.nbits for r in B.parts],
+                   "ck_words": [r.K for r in B.parts], "digit_bits_autotuned": [r.digit_bits for r in B.parts],
+                   "fanouts": TABLE_FANOUTS, "l2": "inputs larger than L2 (no flush)",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "roofline": {"bound": "hbm", "kernel": "whole batched rebuild (all kernels of 6 indexes)",
+                     "achieved": achieved, "peak": peak, "peak_source": peak_src, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": None, "alg_bytes_per_launch": alg, "avg_launch_ms": graph_ms},
+        "path": "batched graph",
+        "batched_streams": {"value": world * keys / (streams_ms / 1e3), "unit": "keys/s", "ms_per_step": streams_ms},
+        "plain_sequential": {"value": world * keys / (seq_ms / 1e3), "unit": "keys/s", "ms_per_step": seq_ms,
+                             "digit_bits": 8},
+        "batched_vs_plain_speedup": seq_ms / graph_ms,
+        "full_key": {"value": world * keys / (full_ms / 1e3), "unit": "keys/s", "ms_per_step": full_ms},
+        "compressed_vs_full_speedup": full_ms / graph_ms,
+        "e2e": {"value": world * keys / (e2e_ms / 1e3), "unit": "keys/s",
+                "h2d_bytes_per_step": int(sum(c.nbytes for c in cols_np)), "d2h_bytes_per_step": 4 * n * 6},
+        "gpu_launches": int(graph_launches), "clocks": clk,
+        "cpu_baseline": None if (world > 1 or args.no_cpu_baseline) else table_cpu_baseline(dmasks, cpu_rows),
+    }
+
+
+def table_cpu_baseline(dmasks, rows):
+    import synth
+    cols = synth.table_columns(rows, synth.BASE_SEED + 3)
+    t = time.perf_counter()
+    for c, m, f in zip(cols, dmasks, TABLE_FANOUTS):
+        kb = 8 * (c.shape[1] if c.ndim == 2 else c.dtype.itemsize)
+        oracle_step(c, m, f, kb)
+    dt = time.perf_counter() - t
+    return {"value": 6 * rows / dt, "unit": "keys/s", "cores": 1, "kind": "oracle",
+            "sample": "first %d rows of the same seeded table, all 6 indexes rebuilt, single thread" % rows}
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
     from paper_2009_11543_gb300 import build as b
@@ -356,6 +491,24 @@ def run_reference(args, rank, world):
         return None
     import oracle
     desc, n, kind, fanout, rows, _ = WORKLOADS[args.workload]
+    if kind == "table":
+        import synth
+        rows = min(rows, 500_000)
+        cols = synth.table_columns(rows, synth.BASE_SEED + 3)
+        dms = [oracle.dmask(c) for c in cols]
+        t = time.perf_counter()
+        for _ in range(args.steps):
+            for c, m, f in zip(cols, dms, TABLE_FANOUTS):
+                oracle_step(c, m, f, 8 * (c.shape[1] if c.ndim == 2 else c.dtype.itemsize))
+        dt = (time.perf_counter() - t) / args.steps
+        v = 6 * rows / dt
+        sample = "first %d rows of the same seeded table (6 indexes) per step, single thread" % rows
+        return {"metric": METRIC, "value": v, "unit": "keys/s", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+                "config": {"workload": desc, "rows": n, "sample_rows": rows}, "impl": "reference",
+                "cpu_baseline": {"value": v, "unit": "keys/s", "cores": 1, "kind": "oracle", "sample": sample},
+                "e2e": {"value": v, "unit": "keys/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     rows = min(rows, n, 2_000_000)
     keys = gen_keys(kind, rows)
     kb = 8 * (keys.shape[1] if keys.ndim == 2 else keys.dtype.itemsize)
@@ -395,6 +548,8 @@ def main():
         dist.init_process_group("gloo")
     if args.impl == "reference":
         line = run_reference(args, rank, world)
+    elif args.workload == "table16m":
+        line = run_table(args, rank, world, local_rank)
     else:
         line = run_ours(args, rank, world, local_rank)
     if line is not None and rank == 0:

@@ -198,7 +198,8 @@ ck_status ck_sort_static(const uint32_t* ck_in, const uint32_t* rid_in, uint32_t
  * parameters packed [w1, b1, w2, b2] (CK_MLP_PARAMS floats), on the feature
  * x = (top 24 bits of the nbits-bit compressed key) / 2^24, is trained on the
  * GPU by full-batch Adam to the empirical CDF (rank + 0.5) / S of a sorted
- * stride sample of S = n / sample_div keys.  The buckets are the 2^bucket_bits
+ * stride sample of S = n / sample_div keys (fitted on at most 65536 of its
+ * points, taken at a fixed stride).  The buckets are the 2^bucket_bits
  * key ranges between the quantiles of the sorted sample (a key value that
  * fills several quantiles gets a bucket of its own); the model proposes each
  * key's bucket as floor(y(x) * B) and a short walk against the splitters makes
@@ -206,11 +207,12 @@ ck_status ck_sort_static(const uint32_t* ck_in, const uint32_t* rid_in, uint32_t
  * stably, and each bucket is sorted in shared memory.
  *
  * ck_sort_learned gives exactly the output of ck_sort (stable, ties by row id,
- * sorted ck and rid).  A verification pass checks every adjacent output pair;
- * if it fails, or a bucket whose keys are not all equal exceeds what one block
- * can sort, the plain radix sort recomputes the result from ck_in and the call
+ * sorted ck and rid).  A bucket whose keys are not all equal and that
+ * exceeds what one block can sort is sorted by the plain radix sort on just
+ * its segment.  A verification pass checks every adjacent output pair; if it
+ * fails, the plain radix sort recomputes the result from ck_in and the call
  * returns CK_EVERIFY (the output is still exact).  The call synchronises its
- * stream once, to read the verification flag.
+ * stream (to read the oversize-bucket list and the verification flag).
  *   ck_in      device, ck_words * CK_LD(n), word-major; read only.
  *   ck_out, rid_out  device outputs as ck_sort (ck_out != ck_in).
  *   ck_words   1 .. 8.
@@ -221,7 +223,8 @@ ck_status ck_sort_static(const uint32_t* ck_in, const uint32_t* rid_in, uint32_t
 #define CK_MLP_PARAMS (3 * CK_MLP_HIDDEN + 1)
 
 typedef struct ck_learned_opts {
-    uint32_t bucket_bits; /* log2 of the bucket count, 8 .. 16; 0 = 16 */
+    uint32_t bucket_bits; /* log2 of the bucket count, 8 .. 16; 0 = chosen from n (about half the
+                             pairs one block sorts in shared memory per bucket) */
     uint32_t sample_div;  /* one sample per sample_div keys; 0 = 100 (1%) */
     uint32_t epochs;      /* Adam epochs; 0 = 100 */
     float lr;             /* Adam learning rate; 0 = 1e-3 */
@@ -243,10 +246,10 @@ typedef struct ck_learned_stats {
     uint32_t buckets;           /* 2^bucket_bits */
     uint32_t sample_size;       /* S */
     uint32_t max_bucket;        /* largest bucket (pairs) */
-    uint32_t sorted_segments;   /* shared-memory sorts run */
-    uint32_t constant_buckets;  /* buckets of equal keys left as partitioned */
-    uint32_t oversize_buckets;  /* non-constant buckets too large for a block */
-    uint32_t fell_back;         /* 1 if the plain radix sort produced the result */
+    uint32_t sorted_segments;   /* buckets sorted in shared memory */
+    uint32_t constant_buckets;  /* large buckets of equal keys left as partitioned */
+    uint32_t oversize_buckets;  /* large non-constant buckets sorted by the plain radix on their segment */
+    uint32_t fell_back;         /* 1 if verification failed and the plain radix sort produced the result */
 } ck_learned_stats;
 
 size_t ck_sort_learned_workspace_bytes(uint64_t n, uint32_t ck_words, uint32_t nbits, const ck_learned_opts* opts);
@@ -339,6 +342,62 @@ ck_status ck_build_index(const uint32_t* sorted_ck, const uint32_t* sorted_rid, 
 ck_status ck_build_index_keys(const ck_column* col, const uint32_t* sorted_rid, const uint64_t* dmask,
                               uint32_t ck_words, uint32_t fanout, float fill, ck_btree* tree, uint64_t* refined_mask,
                               ck_stream stream);
+
+/* ---------------------------------------------------------------------------
+ * Batched rebuild of all the indexes of one table (not in the paper, which
+ * motivates it: a table can carry many indexes, all rebuilt after a restart).
+ * Each job is one index: extract -> sort -> bulk load (+ refined D-bitmap),
+ * exactly the calls above.  ck_build_batched records every job on its own
+ * internal stream, forked from and joined back to `stream` by events, so the
+ * jobs run concurrently and the call is asynchronous; it can be captured into
+ * a CUDA graph (ck_graph_capture_batched does that and instantiates it).
+ * Every buffer of a job is the caller's; jobs must not share buffers.
+ *   digit_bits  radix digit width of the job's sort, 4 .. 11 (0 = 8); see
+ *               ck_autotune_sort.
+ *   ws          the job's sort workspace (ck_sort_workspace_bytes).
+ * Errors: those of the underlying calls; CK_EINVAL for njobs == 0 or
+ * njobs > CK_MAX_JOBS. */
+#define CK_MAX_JOBS 64u
+
+typedef struct ck_index_job {
+    ck_column col;          /* key column (device) */
+    const uint64_t* dmask;  /* HOST, the stored D-bitmap of the column */
+    uint32_t ck_words;      /* words per compressed key */
+    uint32_t digit_bits;    /* 0 = 8 */
+    uint32_t fanout;
+    float fill;
+    uint32_t* ck;           /* device, ck_words * CK_LD(n): extracted keys */
+    uint32_t* ck_sorted;    /* device, ck_words * CK_LD(n) */
+    uint32_t* rid_sorted;   /* device, n */
+    ck_btree* tree;         /* HOST struct with device arrays (shape written) */
+    uint64_t* refined_mask; /* device or NULL */
+    void* ws;
+    size_t ws_bytes;
+} ck_index_job;
+
+ck_status ck_build_batched(const ck_index_job* jobs, uint32_t njobs, ck_stream stream);
+
+/* A captured, instantiated CUDA graph of one ck_build_batched call (opaque). */
+typedef struct ck_graph_st* ck_graph;
+ck_status ck_graph_capture_batched(const ck_index_job* jobs, uint32_t njobs, ck_graph* graph_out);
+ck_status ck_graph_launch(ck_graph graph, ck_stream stream);
+ck_status ck_graph_destroy(ck_graph graph);
+
+/* ---------------------------------------------------------------------------
+ * ck_autotune_sort -- picks the radix digit width (4 .. 11, hence the pass
+ * count) for one index by timing ck_sort on its own extracted keys: every
+ * width whose workspace fits ws runs once untimed and `reps` times timed with
+ * CUDA events on `stream`; the fastest median wins.  The result is kept in a
+ * text cache file (one line per GPU name, n rounded up to a power of two,
+ * ck_words and nbits) when cache_path is not NULL, and read from it when
+ * present, in which case nothing runs.  Synchronises `stream`.
+ *   ck_in, n, ck_words, nbits  as ck_sort (ck_in is read only).
+ *   ck_out, rid_out            scratch outputs of the trial sorts.
+ *   best_digit_bits, best_ms   HOST outputs (best_ms may be NULL; 0 from cache).
+ * Errors: CK_EINVAL, CK_ENOMEM (no width fits ws), CK_ECUDA. */
+ck_status ck_autotune_sort(const uint32_t* ck_in, uint32_t* ck_out, uint32_t* rid_out, uint64_t n, uint32_t ck_words,
+                           uint32_t nbits, void* ws, size_t ws_bytes, uint32_t reps, const char* cache_path,
+                           uint32_t* best_digit_bits, float* best_ms, ck_stream stream);
 
 /* ---------------------------------------------------------------------------
  * Device status.  ck_device_status synchronises the device, returns the first

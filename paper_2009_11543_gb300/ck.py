@@ -29,7 +29,9 @@ CK_SORT_PERM_ONLY = 1
 EXPORTED = ["ck_variant_bits", "ck_distinction_bits", "ck_extract", "ck_sort_workspace_bytes", "ck_sort",
             "ck_btree_plan", "ck_build_index", "ck_device_status", "ck_clear_device_status",
             "ck_status_string", "ck_launch_count", "ck_compress_word_host", "ck_sort_static", "ck_build_index_keys",
-            "ck_sort_learned_workspace_bytes", "ck_sort_learned", "ck_mlp_workspace_bytes", "ck_mlp_loss_grad"]
+            "ck_sort_learned_workspace_bytes", "ck_sort_learned", "ck_mlp_workspace_bytes", "ck_mlp_loss_grad",
+            "ck_build_batched", "ck_graph_capture_batched", "ck_graph_launch", "ck_graph_destroy",
+            "ck_autotune_sort"]
 CK_SORT_STATIC_SCRATCH_BYTES = 32 << 20
 
 
@@ -78,6 +80,14 @@ class ck_btree(ctypes.Structure):
                 ("inner_dbit", ctypes.c_void_p)]
 
 
+class ck_index_job(ctypes.Structure):
+    _fields_ = [("col", ck_column), ("dmask", ctypes.c_void_p), ("ck_words", ctypes.c_uint32),
+                ("digit_bits", ctypes.c_uint32), ("fanout", ctypes.c_uint32), ("fill", ctypes.c_float),
+                ("ck", ctypes.c_void_p), ("ck_sorted", ctypes.c_void_p), ("rid_sorted", ctypes.c_void_p),
+                ("tree", ctypes.POINTER(ck_btree)), ("refined_mask", ctypes.c_void_p), ("ws", ctypes.c_void_p),
+                ("ws_bytes", ctypes.c_size_t)]
+
+
 _LIB = None
 
 
@@ -107,6 +117,13 @@ def _lib():
                                         ctypes.c_size_t, P]
         lib.ck_mlp_workspace_bytes.restype = ctypes.c_size_t
         lib.ck_mlp_loss_grad.argtypes = [P, P, P, U64, P, P, P, ctypes.c_size_t, P]
+        JP = ctypes.POINTER(ck_index_job)
+        lib.ck_build_batched.argtypes = [JP, U32, P]
+        lib.ck_graph_capture_batched.argtypes = [JP, U32, ctypes.POINTER(ctypes.c_void_p)]
+        lib.ck_graph_launch.argtypes = [P, P]
+        lib.ck_graph_destroy.argtypes = [P]
+        lib.ck_autotune_sort.argtypes = [P, P, P, U64, U32, U32, P, ctypes.c_size_t, U32, ctypes.c_char_p,
+                                         ctypes.POINTER(U32), ctypes.POINTER(ctypes.c_float), P]
         lib.ck_device_status.argtypes = [ctypes.POINTER(U64)]
         lib.ck_status_string.argtypes = [I]
         lib.ck_status_string.restype = ctypes.c_char_p
@@ -347,6 +364,37 @@ def ck_mlp_loss_grad(params: torch.Tensor, x: torch.Tensor, t: torch.Tensor | No
     _check(_lib().ck_mlp_loss_grad(_ptr(params), _ptr(x), _ptr(t), x.numel(), _ptr(grad), _ptr(loss), _ptr(ws),
                                    ws.numel() * ws.element_size(), _stream(stream)), "ck_mlp_loss_grad")
     return loss, grad
+
+
+def ck_build_batched(jobs, stream=None) -> None:
+    """jobs: a ctypes array of ck_index_job (see pipeline.BatchedRebuild)."""
+    _check(_lib().ck_build_batched(jobs, len(jobs), _stream(stream)), "ck_build_batched")
+
+
+def ck_graph_capture_batched(jobs):
+    h = ctypes.c_void_p()
+    _check(_lib().ck_graph_capture_batched(jobs, len(jobs), ctypes.byref(h)), "ck_graph_capture_batched")
+    return h
+
+
+def ck_graph_launch(graph, stream=None) -> None:
+    _check(_lib().ck_graph_launch(graph, _stream(stream)), "ck_graph_launch")
+
+
+def ck_graph_destroy(graph) -> None:
+    _check(_lib().ck_graph_destroy(graph), "ck_graph_destroy")
+
+
+def ck_autotune_sort(ck_in: torch.Tensor, ck_out: torch.Tensor, rid_out: torch.Tensor, n: int, ck_words: int,
+                     nbits: int, ws: torch.Tensor, reps: int = 3, cache_path: str | None = None, stream=None):
+    """Returns (best digit width, its median ms; 0.0 when read from the cache)."""
+    d = ctypes.c_uint32(0)
+    ms = ctypes.c_float(0.0)
+    _check(_lib().ck_autotune_sort(_ptr(ck_in), _ptr(ck_out), _ptr(rid_out), n, ck_words, nbits, _ptr(ws),
+                                   ws.numel() * ws.element_size(), reps,
+                                   cache_path.encode() if cache_path else None, ctypes.byref(d), ctypes.byref(ms),
+                                   _stream(stream)), "ck_autotune_sort")
+    return int(d.value), float(ms.value)
 
 
 def ck_device_status() -> tuple[int, int]:

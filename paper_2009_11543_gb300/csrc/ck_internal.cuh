@@ -229,9 +229,11 @@ cudaError_t launch_bucket_scan(uint32_t* hist, uint32_t sets, uint32_t rb, cudaS
 
 struct SortPlan {
     uint32_t digit_bits, passes, tile, tiles, K;
+    uint64_t ld;  // leading dimension of the word arrays (input, output and scratch)
     size_t off_hist, off_counter, off_lookback, off_alt_ck, off_alt_rid, total;
 };
-bool make_sort_plan(uint64_t n, uint32_t K, uint32_t nbits, uint32_t digit_bits, SortPlan* p);
+// ld == 0 selects CK_LD(n); a larger ld sorts a segment of wider arrays in place.
+bool make_sort_plan(uint64_t n, uint32_t K, uint32_t nbits, uint32_t digit_bits, SortPlan* p, uint64_t ld = 0);
 cudaError_t run_sort(const SortPlan& p, const uint32_t* ck_in, const uint32_t* rid_in, uint32_t* ck_out,
                      uint32_t* rid_out, uint64_t n, uint32_t nbits, uint32_t spin_limit, uint32_t inject,
                      uint32_t flags, cudaEvent_t* pass_events, unsigned char* ws, cudaStream_t s);

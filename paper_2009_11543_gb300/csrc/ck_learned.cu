@@ -31,6 +31,7 @@ constexpr int kParams = CK_MLP_PARAMS;  // [w1(16), b1(16), w2(16), b2]
 constexpr int kRed = kParams + 1;       // gradient + loss
 constexpr int kTrainThreads = 256;
 constexpr int kMaxLearnedWords = 8;
+constexpr uint64_t kMaxTrainPoints = 65536;  // training uses a stride subsample of the sorted sample
 
 __device__ __forceinline__ float mlp_eval(const float* p, float x) {
     float y = p[3 * kHidden];
@@ -178,8 +179,9 @@ __global__ void mlp_grad_sum_kernel(const float* __restrict__ partial, uint32_t 
 
 // ------------------------------------------------------------ training
 struct TrainArgs {
-    const float* xs;
-    uint64_t S;
+    const float* xs;      // features of the sorted sample, [S]
+    uint64_t S;           // sample size (targets (i + 0.5) / S)
+    uint64_t T, stride;   // training points: sample indices 0, stride, ..., (T - 1) * stride
     float* params;        // in: initial parameters, out: trained
     float* partial;       // [2][gridDim][kRed]
     unsigned* barrier;    // zeroed
@@ -230,15 +232,17 @@ __global__ void __launch_bounds__(kTrainThreads) mlp_train_kernel(const TrainArg
         m2[tid] = 0.0f;
     }
     __syncthreads();
-    const float scale = 1.0f / (float)a.S;
-    const uint64_t i0 = a.S * blockIdx.x / gridDim.x, i1 = a.S * (blockIdx.x + 1) / gridDim.x;
+    const float scale = 1.0f / (float)a.T, tscale = 1.0f / (float)a.S;
+    const uint64_t i0 = a.T * blockIdx.x / gridDim.x, i1 = a.T * (blockIdx.x + 1) / gridDim.x;
     float b1t = 1.0f, b2t = 1.0f, last_loss = 0.0f;
     for (uint32_t ep = 0; ep < a.epochs; ++ep) {
         float g[kRed];
 #pragma unroll
         for (int q = 0; q < kRed; ++q) g[q] = 0.0f;
-        for (uint64_t i = i0 + tid; i < i1; i += kTrainThreads)
-            g[kParams] += mlp_accumulate(p, a.xs[i], ((float)i + 0.5f) * scale, scale, g);
+        for (uint64_t i = i0 + tid; i < i1; i += kTrainThreads) {
+            const uint64_t si = i * a.stride;
+            g[kParams] += mlp_accumulate(p, a.xs[si], ((float)si + 0.5f) * tscale, scale, g);
+        }
         block_reduce_red(g, red, out);
         float* part = a.partial + (uint64_t)(ep & 1) * gridDim.x * kRed;
         if (tid < kRed) part[(uint64_t)blockIdx.x * kRed + tid] = out[tid];
@@ -324,15 +328,39 @@ struct BucketArgs {
     unsigned long long* steps;  // [0]: total search steps, [1]: max
 };
 
-// Bucket of key x: the number of splitters <= x, i.e. the b with
-// spl[b-1] <= x < spl[b] (spl[-1] = -inf, spl[B-1] = +inf), searched in
-// [lo, hi]; counts the splitter comparisons in *cmp.
-__device__ __forceinline__ uint32_t bucket_search(const uint32_t* key, const uint32_t* spl, uint32_t K, uint32_t lo,
-                                                  uint32_t hi, uint32_t* cmp) {
+// Compile-time-width comparisons for the bucket kernel (key in registers).
+template <int KW>
+__device__ __forceinline__ int cmp_key(const uint32_t (&key)[KW], const uint32_t* s) {
+#pragma unroll
+    for (int w = KW - 1; w >= 0; --w)
+        if (key[w] != s[w]) return key[w] < s[w] ? -1 : 1;
+    return 0;
+}
+
+// Comparison of key x with splitter m: the shared table of splitter top words
+// decides unless the top words are equal, then the full splitter is read.
+template <int KW>
+__device__ __forceinline__ int cmp_split(const uint32_t (&key)[KW], const uint32_t* top, const uint32_t* spl,
+                                         uint32_t m) {
+    const uint32_t t = top[m];
+    if (key[KW - 1] != t) return key[KW - 1] < t ? -1 : 1;
+    return cmp_key<KW>(key, spl + (uint64_t)m * KW);
+}
+
+template <int KW, bool STAGED>
+__device__ __forceinline__ int cmp_at(const uint32_t (&key)[KW], const uint32_t* top, const uint32_t* spl,
+                                      uint32_t m) {
+    return STAGED ? cmp_split<KW>(key, top, spl, m) : cmp_key<KW>(key, spl + (uint64_t)m * KW);
+}
+
+// Number of splitters <= x within [lo, hi] (binary search).
+template <int KW, bool STAGED>
+__device__ __forceinline__ uint32_t search_range(const uint32_t (&key)[KW], const uint32_t* top, const uint32_t* spl,
+                                                 uint32_t lo, uint32_t hi, uint32_t* cmp) {
     while (lo < hi) {
-        const uint32_t mid = (lo + hi) >> 1;  // is x >= spl[mid]?
+        const uint32_t mid = (lo + hi) >> 1;
         ++*cmp;
-        if (cmp_words(key, spl + (uint64_t)mid * K, K) >= 0) lo = mid + 1;
+        if (cmp_at<KW, STAGED>(key, top, spl, mid) >= 0) lo = mid + 1;
         else hi = mid;
     }
     return lo;
@@ -341,28 +369,30 @@ __device__ __forceinline__ uint32_t bucket_search(const uint32_t* key, const uin
 // Exact bucket from a guess g: check the guess's range, then gallop away from
 // it (1, 2, 4, ... buckets) and finish with a binary search, so a guess that
 // is e buckets off costs about 2 log2(e) + 2 comparisons.
-__device__ __forceinline__ uint32_t bucket_from_guess(const uint32_t* key, const uint32_t* spl, uint32_t K,
-                                                      uint32_t B, uint32_t g, uint32_t* cmp) {
+template <int KW, bool STAGED>
+__device__ __forceinline__ uint32_t search_from_guess(const uint32_t (&key)[KW], const uint32_t* top,
+                                                      const uint32_t* spl, uint32_t B, uint32_t g, uint32_t* cmp) {
     ++*cmp;
-    if (g > 0 && cmp_words(key, spl + (uint64_t)(g - 1) * K, K) < 0) {  // below: gallop down
-        uint32_t hi = g - 1, step = 1;                                  // answer <= g - 1
+    if (g > 0 && cmp_at<KW, STAGED>(key, top, spl, g - 1) < 0) {  // below: gallop down
+        uint32_t hi = g - 1, step = 1;
         while (true) {
-            const uint32_t probe = hi >= step ? hi - step : 0;          // is x >= spl[probe]?
+            const uint32_t probe = hi >= step ? hi - step : 0;
             ++*cmp;
-            if (probe == 0 && cmp_words(key, spl, K) < 0) return 0;
-            if (cmp_words(key, spl + (uint64_t)probe * K, K) >= 0) return bucket_search(key, spl, K, probe + 1, hi, cmp);
-            hi = probe;
+            if (cmp_at<KW, STAGED>(key, top, spl, probe) >= 0)
+                return search_range<KW, STAGED>(key, top, spl, probe + 1, hi, cmp);
             if (probe == 0) return 0;
+            hi = probe;
             step <<= 1;
         }
     }
     ++*cmp;
-    if (g < B - 1 && cmp_words(key, spl + (uint64_t)g * K, K) >= 0) {  // above: gallop up
-        uint32_t lo = g + 1, step = 1;                                 // answer >= g + 1
+    if (g < B - 1 && cmp_at<KW, STAGED>(key, top, spl, g) >= 0) {  // above: gallop up
+        uint32_t lo = g + 1, step = 1;
         while (true) {
-            const uint32_t probe = lo + step - 1 < B - 1 ? lo + step - 1 : B - 2;  // is x < spl[probe]?
+            const uint32_t probe = lo + step - 1 < B - 1 ? lo + step - 1 : B - 2;
             ++*cmp;
-            if (cmp_words(key, spl + (uint64_t)probe * K, K) < 0) return bucket_search(key, spl, K, lo, probe, cmp);
+            if (cmp_at<KW, STAGED>(key, top, spl, probe) < 0)
+                return search_range<KW, STAGED>(key, top, spl, lo, probe, cmp);
             lo = probe + 1;
             if (probe == B - 2) return B - 1;
             step <<= 1;
@@ -371,32 +401,65 @@ __device__ __forceinline__ uint32_t bucket_from_guess(const uint32_t* key, const
     return g;
 }
 
-__global__ void __launch_bounds__(256) bucket_kernel(const BucketArgs a) {
+// Bucket id of every key.  With STAGED, the most significant word of every
+// splitter sits in shared memory ((B - 1) words), with a table over its top
+// kPrefixBits bits: pre[p] = first splitter whose top word is >= p << (32 -
+// kPrefixBits).  A key whose top word has prefix p has its bucket in
+// [pre[p], pre[p + 1]]; the model's guess is clamped into that range and the
+// search (galloping from the guess, or binary without the model) runs there.
+constexpr int kPrefixBits = 12;
+
+template <int KW, bool STAGED>
+__global__ void __launch_bounds__(1024) bucket_kernel(const BucketArgs a) {
+    extern __shared__ uint32_t top[];
+    uint32_t* pre = top + (a.B - 1);  // [2^kPrefixBits + 1] when staged
     __shared__ float p[kParams];
     __shared__ uint32_t hlo[256], hhi[256];
     __shared__ unsigned long long s_sum, s_max;
     const int tid = threadIdx.x;
+    const uint32_t B = a.B;
     if (tid < kParams) p[tid] = a.params ? a.params[tid] : 0.0f;
-    hlo[tid] = 0;
-    hhi[tid] = 0;
+    if (tid < 256) {
+        hlo[tid] = 0;
+        hhi[tid] = 0;
+    }
     if (tid == 0) {
         s_sum = 0;
         s_max = 0;
     }
+    if (STAGED) {
+        for (uint32_t m = tid; m + 1 < B; m += blockDim.x) top[m] = a.spl[(uint64_t)m * KW + KW - 1];
+        __syncthreads();
+        for (uint32_t q = tid; q <= (1u << kPrefixBits); q += blockDim.x) {
+            uint32_t lo = 0, hi = B - 1;  // first m with top[m] >= q << (32 - kPrefixBits)
+            const uint64_t bound = (uint64_t)q << (32 - kPrefixBits);
+            while (lo < hi) {
+                const uint32_t mid = (lo + hi) >> 1;
+                if ((uint64_t)top[mid] >= bound) hi = mid;
+                else lo = mid + 1;
+            }
+            pre[q] = lo;
+        }
+    }
     __syncthreads();
-    const uint32_t B = a.B, K = a.K;
     unsigned long long my_sum = 0, my_max = 0;
     for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + tid; i < a.n; i += (uint64_t)gridDim.x * blockDim.x) {
-        uint32_t key[kMaxLearnedWords];
+        uint32_t key[KW];
 #pragma unroll
-        for (uint32_t w = 0; w < kMaxLearnedWords; ++w) key[w] = w < K ? a.ck[(uint64_t)w * a.ld + i] : 0u;
-        uint32_t g, steps = 0;
+        for (int w = 0; w < KW; ++w) key[w] = a.ck[(uint64_t)w * a.ld + i];
+        uint32_t g, steps = 0, lo = 0, hi = B - 1;
+        if (STAGED) {
+            const uint32_t q = key[KW - 1] >> (32 - kPrefixBits);
+            lo = pre[q];
+            hi = pre[q + 1];
+        }
         if (a.use_model) {
-            const float y = mlp_eval(p, key_feature(a.ck, a.ld, i, K, a.nbits)) * (float)B;
-            const uint32_t guess = y <= 0.0f ? 0u : (y >= (float)(B - 1) ? B - 1 : (uint32_t)y);
-            g = bucket_from_guess(key, a.spl, K, B, guess, &steps);
+            const float y = mlp_eval(p, key_feature(a.ck, a.ld, i, KW, a.nbits)) * (float)B;
+            uint32_t guess = y <= 0.0f ? 0u : (y >= (float)(B - 1) ? B - 1 : (uint32_t)y);
+            guess = guess < lo ? lo : (guess > hi ? hi : guess);
+            g = search_from_guess<KW, STAGED>(key, top, a.spl, B, guess, &steps);
         } else {
-            g = bucket_search(key, a.spl, K, 0, B - 1, &steps);
+            g = search_range<KW, STAGED>(key, top, a.spl, lo, hi, &steps);
         }
         a.bkt[i] = g;
         atomicAdd(&hlo[g & 255u], 1u);
@@ -407,34 +470,74 @@ __global__ void __launch_bounds__(256) bucket_kernel(const BucketArgs a) {
     atomicAdd(&s_sum, my_sum);
     atomicMax(&s_max, my_max);
     __syncthreads();
-    if (hlo[tid]) atomicAdd(&a.hist[tid], hlo[tid]);
-    if (hhi[tid]) atomicAdd(&a.hist[256 + tid], hhi[tid]);
+    if (tid < 256) {
+        if (hlo[tid]) atomicAdd(&a.hist[tid], hlo[tid]);
+        if (hhi[tid]) atomicAdd(&a.hist[256 + tid], hhi[tid]);
+    }
     if (tid == 0) {
         atomicAdd(&a.steps[0], s_sum);
         atomicMax(&a.steps[1], s_max);
     }
 }
 
-// ------------------------------------------------------------ bucket sorts
-struct LocalArgs {
-    uint32_t* ck;          // partitioned, sorted in place; word-major, leading dimension ld
-    uint32_t* rid;
-    const uint32_t* bkt;   // bucket id of every position (non-decreasing)
-    const uint32_t* spl;   // final splitters
-    uint64_t ld, n, chunk;
-    uint32_t K, B, cap;
-    uint32_t* flags;       // [0] oversize buckets, [1] order violations
-    uint32_t* counts;      // [0] segments sorted, [1] constant buckets, [2] max bucket
-};
-
-__device__ uint64_t upper_bound_u32(const uint32_t* a, uint64_t n, uint32_t v) {
-    uint64_t lo = 0, hi = n;
-    while (lo < hi) {
-        const uint64_t mid = (lo + hi) >> 1;
-        if (a[mid] <= v) lo = mid + 1;
-        else hi = mid;
+template <int KW>
+static cudaError_t launch_bucket_kw(const BucketArgs& ba, bool staged, size_t smem, int sms, cudaStream_t s) {
+    if (staged) {
+        cudaError_t e = cudaFuncSetAttribute(bucket_kernel<KW, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (e != cudaSuccess) return e;
+        bucket_kernel<KW, true><<<sms, 1024, smem, s>>>(ba);
+    } else {
+        bucket_kernel<KW, false><<<sms, 1024, 0, s>>>(ba);
     }
-    return lo;
+    return cudaGetLastError();
+}
+
+static cudaError_t launch_bucket(const BucketArgs& ba, bool staged, size_t smem, int sms, cudaStream_t s) {
+    switch (ba.K) {
+        case 1: return launch_bucket_kw<1>(ba, staged, smem, sms, s);
+        case 2: return launch_bucket_kw<2>(ba, staged, smem, sms, s);
+        case 3: return launch_bucket_kw<3>(ba, staged, smem, sms, s);
+        case 4: return launch_bucket_kw<4>(ba, staged, smem, sms, s);
+        case 5: return launch_bucket_kw<5>(ba, staged, smem, sms, s);
+        case 6: return launch_bucket_kw<6>(ba, staged, smem, sms, s);
+        case 7: return launch_bucket_kw<7>(ba, staged, smem, sms, s);
+        default: return launch_bucket_kw<8>(ba, staged, smem, sms, s);
+    }
+}
+
+// ------------------------------------------------------------ bucket sorts
+// start[b] = first position of bucket b after the partition (bucket ids are
+// non-decreasing): written by the first position of every non-empty bucket,
+// then empty buckets take the start of the next non-empty one (suffix minimum,
+// start[B] = n).
+__global__ void bucket_start_kernel(const uint32_t* __restrict__ bkt, uint64_t n, uint32_t* __restrict__ start) {
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x)
+        if (i == 0 || bkt[i] != bkt[i - 1]) start[bkt[i]] = (uint32_t)i;
+}
+
+__global__ void suffix_min_kernel(uint32_t* v, uint32_t count) {  // one block; v[count - 1] is the sentinel
+    __shared__ uint32_t part[1024];
+    const uint32_t per = (count + blockDim.x - 1) / blockDim.x;
+    const uint32_t lo = threadIdx.x * per, hi = min(count, lo + per);
+    uint32_t m = 0xFFFFFFFFu;
+    for (uint32_t c = hi; c-- > lo;) m = min(m, v[c]);
+    part[threadIdx.x] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t r = 0xFFFFFFFFu;
+        for (int t = blockDim.x - 1; t >= 0; --t) {
+            const uint32_t x = part[t];
+            part[t] = r;
+            r = min(r, x);
+        }
+    }
+    __syncthreads();
+    uint32_t r = part[threadIdx.x];
+    for (uint32_t c = hi; c-- > lo;) {
+        r = min(r, v[c]);
+        v[c] = r;
+    }
 }
 
 // Bucket b holds only equal keys when its range is [v, v + 1).
@@ -451,103 +554,171 @@ __device__ bool constant_bucket(const uint32_t* spl, uint32_t K, uint32_t B, uin
     return carry == 0;
 }
 
-// Block j sorts the buckets that start in positions [j * chunk, (j+1) * chunk):
-// consecutive buckets are grouped while the group fits `cap` pairs and each
-// group is bitonic-sorted in shared memory on (key, position), which is a
-// stable sort; it is written back to the same positions.
-__global__ void __launch_bounds__(1024) local_sort_kernel(const LocalArgs a) {
+struct LocalArgs {
+    uint32_t* ck;          // partitioned, sorted in place; word-major, leading dimension ld
+    uint32_t* rid;
+    const uint32_t* start; // [B + 1]
+    const uint32_t* spl;   // final splitters
+    uint64_t ld;
+    uint32_t K, B, nbits, cap;
+    uint32_t* next;        // bucket queue
+    uint32_t* flags;       // [0] oversize buckets (also the length of `over`)
+    uint32_t* counts;      // [0] buckets sorted, [1] constant buckets, [2] max bucket
+    uint32_t* over;        // [2 * max_over] start/end of oversize buckets
+    uint32_t max_over;
+};
+
+constexpr int kLocalThreads = 1024;
+constexpr int kLocalWarps = kLocalThreads / 32;
+
+// Persistent blocks take buckets from a queue.  A bucket of m <= cap pairs is
+// loaded into shared memory and sorted by an LSD radix sort with 8-bit digits
+// over only the digits that vary inside the bucket (all others are equal
+// there); each pass ranks the items stably by warp ballots, in the current
+// order, and permutes a 16-bit index.  The keys then leave in sorted order and
+// the row ids are gathered through the permutation.  Constant buckets are left
+// as partitioned (already stable); other oversize buckets are queued for the
+// plain radix sort.
+__global__ void __launch_bounds__(kLocalThreads) local_sort_kernel(const LocalArgs a) {
     extern __shared__ __align__(16) uint32_t lsm[];
     const uint32_t K = a.K, cap = a.cap;
-    uint32_t* keys = lsm;                                          // [K][cap]
-    uint32_t* rids = keys + (size_t)K * cap;                       // [cap]
-    uint16_t* idx = reinterpret_cast<uint16_t*>(rids + cap);       // [cap]
-    __shared__ uint64_t s_range[2];
-    const uint32_t tid = threadIdx.x;
-    const uint64_t c0 = blockIdx.x * a.chunk;
-    const uint64_t c1 = min(a.n, c0 + a.chunk);
-    if (tid == 0) {
-        uint64_t s0 = (c0 == 0 || a.bkt[c0] != a.bkt[c0 - 1]) ? c0 : upper_bound_u32(a.bkt, a.n, a.bkt[c0]);
-        s_range[0] = s0;
-        s_range[1] = s0 < c1 ? upper_bound_u32(a.bkt, a.n, a.bkt[c1 - 1]) : s0;
-    }
-    __syncthreads();
-    const uint64_t s0 = s_range[0], e0 = s_range[1];
-    __shared__ uint64_t g_range[2];
-    __shared__ uint32_t g_kind;  // 0: sort, 1: skip (constant or oversize)
-    uint64_t bs = s0;
-    while (bs < e0) {
-        if (tid == 0) {
-            uint64_t ge = upper_bound_u32(a.bkt, a.n, a.bkt[bs]);
-            const uint64_t first_size = ge - bs;
-            atomicMax(&a.counts[2], (uint32_t)(first_size < 0xFFFFFFFFull ? first_size : 0xFFFFFFFFull));
-            uint32_t kind = 0;
-            if (first_size > cap) {
-                if (constant_bucket(a.spl, K, a.B, a.bkt[bs])) {
-                    kind = 1;
+    uint32_t* keys = lsm;                                              // [K][cap]
+    uint16_t* idx_a = reinterpret_cast<uint16_t*>(keys + (size_t)K * cap);  // [cap]
+    uint16_t* idx_b = idx_a + cap;                                     // [cap]
+    uint16_t* rnk = idx_b + cap;                                       // [cap] rank within the warp
+    uint8_t* dig = reinterpret_cast<uint8_t*>(rnk + cap);              // [cap]
+    __shared__ uint16_t whist[kLocalWarps][256];
+    __shared__ uint32_t dtot[256];
+    __shared__ uint32_t vary[kMaxLearnedWords];
+    __shared__ uint32_t s_bucket;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const uint32_t lt = (1u << lane) - 1u;
+    for (;;) {
+        if (tid == 0) s_bucket = atomicAdd(a.next, 1u);
+        if (tid < kMaxLearnedWords) vary[tid] = 0;
+        __syncthreads();
+        const uint32_t b = s_bucket;
+        if (b >= a.B) break;
+        const uint32_t s = a.start[b], m = a.start[b + 1] - s;
+        if (tid == 0 && m > 0) atomicMax(&a.counts[2], m);
+        if (m <= 1) {
+            __syncthreads();
+            continue;
+        }
+        if (m > cap) {
+            if (tid == 0) {
+                if (constant_bucket(a.spl, K, a.B, b)) {
                     atomicAdd(&a.counts[1], 1u);
                 } else {
-                    kind = 1;
-                    atomicAdd(&a.flags[0], 1u);
-                }
-            } else {
-                while (ge < e0) {
-                    const uint64_t nx = upper_bound_u32(a.bkt, a.n, a.bkt[ge]);
-                    if (nx - bs > cap) break;
-                    atomicMax(&a.counts[2], (uint32_t)(nx - ge));
-                    ge = nx;
-                }
-                atomicAdd(&a.counts[0], 1u);
-            }
-            g_range[0] = bs;
-            g_range[1] = ge;
-            g_kind = kind;
-        }
-        __syncthreads();
-        const uint64_t s = g_range[0], e = g_range[1];
-        const uint32_t kind = g_kind;
-        __syncthreads();
-        bs = e;
-        if (kind != 0) continue;
-        const uint32_t m = (uint32_t)(e - s);
-        uint32_t P = 1;
-        while (P < m) P <<= 1;
-        for (uint32_t t = tid; t < m; t += blockDim.x) {
-            for (uint32_t w = 0; w < K; ++w) keys[(size_t)w * cap + t] = a.ck[(uint64_t)w * a.ld + s + t];
-            rids[t] = a.rid[s + t];
-        }
-        for (uint32_t t = tid; t < P; t += blockDim.x) idx[t] = t < m ? (uint16_t)t : (uint16_t)0xFFFF;
-        __syncthreads();
-        // true if the element at slot position u must come after the one at v
-        auto after = [&](uint32_t u, uint32_t v) -> bool {
-            if (u == 0xFFFF) return v != 0xFFFF;
-            if (v == 0xFFFF) return false;
-            for (int w = (int)K - 1; w >= 0; --w) {
-                const uint32_t ku = keys[(size_t)w * cap + u], kv = keys[(size_t)w * cap + v];
-                if (ku != kv) return ku > kv;
-            }
-            return u > v;  // equal keys keep their partition order
-        };
-        for (uint32_t k = 2; k <= P; k <<= 1) {
-            for (uint32_t j = k >> 1; j > 0; j >>= 1) {
-                for (uint32_t t = tid; t < P; t += blockDim.x) {
-                    const uint32_t l = t ^ j;
-                    if (l > t) {
-                        const uint32_t u = idx[t], v = idx[l];
-                        const bool up = (t & k) == 0;
-                        if (up ? after(u, v) : after(v, u)) {
-                            idx[t] = (uint16_t)v;
-                            idx[l] = (uint16_t)u;
-                        }
+                    const uint32_t slot = atomicAdd(&a.flags[0], 1u);
+                    if (slot < a.max_over) {
+                        a.over[2 * slot] = s;
+                        a.over[2 * slot + 1] = s + m;
                     }
                 }
-                __syncthreads();
             }
+            __syncthreads();
+            continue;
         }
-        for (uint32_t t = tid; t < m; t += blockDim.x) {
-            const uint32_t src = idx[t];
+        // load, and find the bits that vary inside the bucket
+        for (uint32_t w = 0; w < K; ++w) {
+            const uint32_t first = a.ck[(uint64_t)w * a.ld + s];
+            uint32_t diff = 0;
+            for (uint32_t t = tid; t < m; t += kLocalThreads) {
+                const uint32_t v = a.ck[(uint64_t)w * a.ld + s + t];
+                keys[(size_t)w * cap + t] = v;
+                diff |= v ^ first;
+            }
+            diff = __reduce_or_sync(kFull, diff);
+            if (lane == 0 && diff) atomicOr(&vary[w], diff);
+        }
+        for (uint32_t t = tid; t < m; t += kLocalThreads) idx_a[t] = (uint16_t)t;
+        __syncthreads();
+        // warp w ranks positions [w * per, (w + 1) * per), per a multiple of 32
+        const uint32_t per = ((m + kLocalWarps * 32 - 1) / (kLocalWarps * 32)) * 32;
+        const uint32_t pbeg = warp * per, pend = min(m, pbeg + per);
+        const uint32_t digits = (a.nbits + 7) / 8;
+        for (uint32_t q = 0; q < digits; ++q) {
+            const uint32_t shift = 8 * q, w = shift >> 5, sh = shift & 31;
+            if (((vary[w] >> sh) & 0xFFu) == 0) continue;  // digit constant in this bucket
+            for (int d = tid; d < kLocalWarps * 256; d += kLocalThreads) (&whist[0][0])[d] = 0;
+            __syncthreads();
+            const uint32_t* kw = keys + (size_t)w * cap;
+            for (uint32_t p0 = pbeg; p0 < pend; p0 += 32) {  // warp-uniform trip count
+                const uint32_t p = p0 + lane;
+                const bool valid = p < pend;
+                const uint32_t d = valid ? (kw[idx_a[p]] >> sh) & 0xFFu : 0u;
+                uint32_t peers = __ballot_sync(kFull, valid);
+#pragma unroll
+                for (int bit = 0; bit < 8; ++bit) {
+                    const bool x = (d >> bit) & 1u;
+                    const uint32_t bal = __ballot_sync(kFull, x);
+                    peers &= x ? bal : ~bal;
+                }
+                const uint32_t base = valid ? whist[warp][d] : 0u;
+                __syncwarp();
+                if (valid && (peers & lt) == 0) whist[warp][d] = (uint16_t)(base + __popc(peers));
+                __syncwarp();
+                if (valid) {
+                    rnk[p] = (uint16_t)(base + __popc(peers & lt));
+                    dig[p] = (uint8_t)d;
+                }
+            }
+            __syncthreads();
+            // per digit: totals over warps, then exclusive offsets digit-major, warp-minor
+            if (tid < 256) {
+                uint32_t sum = 0;
+                for (int ww = 0; ww < kLocalWarps; ++ww) sum += whist[ww][tid];
+                dtot[tid] = sum;
+            }
+            __syncthreads();
+            if (tid < 32) {  // exclusive scan of 256 totals by one warp, 8 per lane
+                uint32_t v[8], run = 0;
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    v[i] = dtot[lane * 8 + i];
+                    run += v[i];
+                }
+                uint32_t inc = run;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const uint32_t t = __shfl_up_sync(kFull, inc, o);
+                    if (lane >= o) inc += t;
+                }
+                uint32_t ex = inc - run;
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    dtot[lane * 8 + i] = ex;
+                    ex += v[i];
+                }
+            }
+            __syncthreads();
+            if (tid < 256) {
+                uint32_t off = dtot[tid];
+                for (int ww = 0; ww < kLocalWarps; ++ww) {
+                    const uint32_t c = whist[ww][tid];
+                    whist[ww][tid] = (uint16_t)off;
+                    off += c;
+                }
+            }
+            __syncthreads();
+            for (uint32_t p = pbeg + lane; p < pend; p += 32) idx_b[whist[warp][dig[p]] + rnk[p]] = idx_a[p];
+            __syncthreads();
+            uint16_t* t = idx_a;
+            idx_a = idx_b;
+            idx_b = t;
+        }
+        // write the bucket back in sorted order; row ids through the permutation
+        for (uint32_t t = tid; t < m; t += kLocalThreads) {
+            const uint32_t src = idx_a[t];
             for (uint32_t w = 0; w < K; ++w) a.ck[(uint64_t)w * a.ld + s + t] = keys[(size_t)w * cap + src];
-            a.rid[s + t] = rids[src];
         }
+        __syncthreads();
+        uint32_t* rtmp = keys;  // the keys are written out; their space holds the row ids
+        for (uint32_t t = tid; t < m; t += kLocalThreads) rtmp[t] = a.rid[s + t];
+        __syncthreads();
+        for (uint32_t t = tid; t < m; t += kLocalThreads) a.rid[s + t] = rtmp[idx_a[t]];
+        if (tid == 0) atomicAdd(&a.counts[0], 1u);
         __syncthreads();
     }
 }
@@ -572,11 +743,11 @@ __global__ void verify_kernel(const uint32_t* __restrict__ ck, const uint32_t* _
 struct LearnedPlan {
     uint32_t B, bucket_bits, passes, K, nbits;
     uint64_t S, ld_s, n, ld, div, chunk;
-    uint32_t cap, epochs, train_blocks, flags;
+    uint32_t cap, epochs, train_blocks, flags, max_over;
     float lr;
     SortPlan sample_sort, plain;
     size_t off_sample, off_sample_sorted, off_sample_rid, off_sample_ws, off_xs, off_params, off_partial,
-        off_misc, off_spl, off_spl_final, off_bkt, off_alt_bkt, off_alt_ck, off_alt_rid, off_hist,
+        off_misc, off_start, off_over, off_spl, off_spl_final, off_bkt, off_alt_bkt, off_alt_ck, off_alt_rid, off_hist,
         off_lookback, off_plain_ws, total;
 };
 
@@ -584,7 +755,17 @@ static size_t a256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 static bool make_learned_plan(uint64_t n, uint32_t K, uint32_t nbits, const ck_learned_opts* o, LearnedPlan* p) {
     memset(p, 0, sizeof(*p));
-    p->bucket_bits = o && o->bucket_bits ? o->bucket_bits : 16;
+    // bucket capacity of one block: K key words, two 16-bit indices, a 16-bit
+    // rank and an 8-bit digit per pair in <= 200 KB, a multiple of 512
+    uint32_t cap = (uint32_t)((200 * 1024) / (4 * K + 7)) / 512 * 512;
+    if (cap > 16384) cap = 16384;
+    p->cap = cap;
+    // default bucket count: about 0.6 cap pairs per bucket (headroom for the
+    // sampling noise of the quantiles), between 2^8 and 2^16 buckets
+    uint32_t auto_bits = 8;
+    while (auto_bits < 16 && (n >> auto_bits) > cap * 6 / 10) ++auto_bits;
+    if (auto_bits == 16 && (n >> 15) <= cap * 3 / 4) auto_bits = 15;  // keeps the splitter table in shared memory
+    p->bucket_bits = o && o->bucket_bits ? o->bucket_bits : auto_bits;
     if (p->bucket_bits < 8 || p->bucket_bits > 16) return false;
     p->B = 1u << p->bucket_bits;
     p->passes = p->bucket_bits > 8 ? 2 : 1;
@@ -600,11 +781,7 @@ static bool make_learned_plan(uint64_t n, uint32_t K, uint32_t nbits, const ck_l
     if (p->S < 2) p->S = n < 2 ? n : 2;
     p->ld_s = CK_LD(p->S);
     p->chunk = 4096;
-    // bucket capacity of one block: (K + 1) words per pair + a 16-bit index, <= 200 KB
-    uint32_t cap = 8192;
-    while (cap > 256 && (size_t)cap * (4 * (K + 1) + 2) > 200 * 1024) cap >>= 1;
-    p->cap = cap;
-    p->train_blocks = (uint32_t)num_sms();
+    p->train_blocks = (uint32_t)min(num_sms(), 32);
     if (!make_sort_plan(p->S, K, nbits, 8, &p->sample_sort)) return false;
     if (!make_sort_plan(n, K, nbits, 8, &p->plain)) return false;
     const uint64_t tiles = (n + kPassTile - 1) / kPassTile;
@@ -621,7 +798,10 @@ static bool make_learned_plan(uint64_t n, uint32_t K, uint32_t nbits, const ck_l
     p->off_xs = take(4ull * p->S);
     p->off_params = take(4ull * kParams);
     p->off_partial = take(4ull * 2 * p->train_blocks * kRed);
-    p->off_misc = take(256);  // barrier, loss, flags[2], counts[3], steps[2] (u64)
+    p->off_misc = take(256);  // barrier, loss, flags[2], counts[3], queue, steps[2] (u64)
+    p->max_over = 4096;
+    p->off_start = take(4ull * (p->B + 1));
+    p->off_over = take(4ull * 2 * p->max_over);
     p->off_spl = take(4ull * K * p->B);
     p->off_spl_final = take(4ull * K * p->B);
     p->off_bkt = take(4ull * n);
@@ -644,8 +824,8 @@ struct Misc {  // layout of the misc block of the learned workspace
     unsigned barrier;
     float loss;
     uint32_t flags[2];   // oversize buckets, order violations
-    uint32_t counts[3];  // segments sorted, constant buckets, max bucket
-    uint32_t pad;
+    uint32_t counts[3];  // buckets sorted, constant buckets, max bucket
+    uint32_t next;       // bucket queue of the local sorts
     unsigned long long steps[2];
 };
 }  // namespace
@@ -720,6 +900,8 @@ ck_status ck_sort_learned(const uint32_t* ck_in, uint32_t* ck_out, uint32_t* rid
         TrainArgs ta;
         ta.xs = xs;
         ta.S = P.S;
+        ta.stride = (P.S + kMaxTrainPoints - 1) / kMaxTrainPoints;
+        ta.T = (P.S + ta.stride - 1) / ta.stride;
         ta.params = params;
         ta.partial = reinterpret_cast<float*>(ws + P.off_partial);
         ta.barrier = &misc->barrier;
@@ -755,7 +937,9 @@ ck_status ck_sort_learned(const uint32_t* ck_in, uint32_t* ck_out, uint32_t* rid
     ba.bkt = at(P.off_bkt);
     ba.hist = at(P.off_hist);
     ba.steps = misc->steps;
-    bucket_kernel<<<sms * 8, 256, 0, s>>>(ba);
+    const size_t top_bytes = 4ull * (P.B - 1) + 4ull * ((1u << kPrefixBits) + 1);
+    const bool staged = top_bytes <= 160 * 1024;
+    CK_TRY(launch_bucket(ba, staged, top_bytes, sms, s));
     count_launch();
     CK_TRY(launch_bucket_scan(at(P.off_hist), P.passes, 8, s));
 
@@ -804,33 +988,63 @@ ck_status ck_sort_learned(const uint32_t* ck_in, uint32_t* ck_out, uint32_t* rid
         CK_TRY(launch_onesweep_pass(8, a, arr, (uint32_t)tiles, s));
     }
 
-    // 6. sort every bucket in shared memory, in place
+    // 6. bucket starts, then every bucket sorted in shared memory, in place
+    uint32_t* start = at(P.off_start);
+    CK_TRY(cudaMemsetAsync(start, 0xFF, 4ull * P.B, s));
+    const uint32_t n32 = (uint32_t)n;
+    CK_TRY(cudaMemcpyAsync(start + P.B, &n32, 4, cudaMemcpyHostToDevice, s));
+    bucket_start_kernel<<<sms * 8, 256, 0, s>>>(bkt_final, n, start);
+    suffix_min_kernel<<<1, 1024, 0, s>>>(start, P.B + 1);
+    count_launch(2);
     LocalArgs la;
     la.ck = ck_out;
     la.rid = rid_out;
-    la.bkt = bkt_final;
+    la.start = start;
     la.spl = at(P.off_spl_final);
     la.ld = P.ld;
-    la.n = n;
-    la.chunk = P.chunk;
     la.K = K;
     la.B = P.B;
+    la.nbits = nbits;
     la.cap = P.cap;
+    la.next = &misc->next;
     la.flags = misc->flags;
     la.counts = misc->counts;
-    const size_t lsmem = (size_t)P.cap * (4 * (K + 1) + 2);
+    la.over = at(P.off_over);
+    la.max_over = P.max_over;
+    const size_t lsmem = (size_t)P.cap * (4 * K + 7) + 16;
     CK_TRY(cudaFuncSetAttribute(local_sort_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lsmem));
-    local_sort_kernel<<<(unsigned)((n + P.chunk - 1) / P.chunk), 1024, lsmem, s>>>(la);
-    count_launch();
-
-    // 7. verification of every adjacent pair
-    verify_kernel<<<sms * 8, 256, 0, s>>>(ck_out, rid_out, P.ld, n, K, misc->flags);
+    int per_sm = 1;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, local_sort_kernel, kLocalThreads, lsmem);
+    local_sort_kernel<<<sms * (per_sm > 0 ? per_sm : 1), kLocalThreads, lsmem, s>>>(la);
     count_launch();
     Misc host;
     CK_TRY(cudaMemcpyAsync(&host, misc, sizeof(Misc), cudaMemcpyDeviceToHost, s));
     CK_TRY(cudaStreamSynchronize(s));
+    // 7. buckets too large for a block (keys not all equal): the plain radix
+    //    sort on just that segment, in place (the partition order is stable)
+    bool failed = host.flags[0] > P.max_over;
+    if (!failed && host.flags[0] > 0) {
+        static thread_local uint32_t over[2 * 4096];
+        CK_TRY(cudaMemcpy(over, at(P.off_over), 8ull * host.flags[0], cudaMemcpyDeviceToHost));
+        for (uint32_t k = 0; k < host.flags[0] && !failed; ++k) {
+            const uint64_t b0 = over[2 * k], m = over[2 * k + 1] - b0;
+            SortPlan sp;
+            if (!make_sort_plan(m, K, nbits, 8, &sp, P.ld) || sp.total > P.plain.total) {
+                failed = true;
+                break;
+            }
+            CK_TRY(run_sort(sp, ck_out + b0, rid_out + b0, ck_out + b0, rid_out + b0, m, nbits, kDefaultSpin, 0, 0,
+                            nullptr, ws + P.off_plain_ws, s));
+        }
+    }
+
+    // 8. verification of every adjacent pair
+    verify_kernel<<<sms * 8, 256, 0, s>>>(ck_out, rid_out, P.ld, n, K, misc->flags);
+    count_launch();
+    CK_TRY(cudaMemcpyAsync(&host, misc, sizeof(Misc), cudaMemcpyDeviceToHost, s));
+    CK_TRY(cudaStreamSynchronize(s));
     if (params_out && use_model) CK_TRY(cudaMemcpy(params_out, params, 4 * kParams, cudaMemcpyDeviceToHost));
-    const bool failed = host.flags[0] != 0 || host.flags[1] != 0 || (P.flags & CK_LEARNED_INJECT_VERIFY_FAIL);
+    failed = failed || host.flags[1] != 0 || (P.flags & CK_LEARNED_INJECT_VERIFY_FAIL);
     if (stats) {
         stats->train_loss = use_model ? host.loss : 0.0f;
         stats->mean_search_steps = (float)((double)host.steps[0] / (double)n);

@@ -382,8 +382,10 @@ cudaError_t launch_bucket_scan(uint32_t* hist, uint32_t sets, uint32_t rb, cudaS
 // ------------------------------------------------------------------ host
 static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
-bool make_sort_plan(uint64_t n, uint32_t K, uint32_t nbits, uint32_t digit_bits, SortPlan* p) {
+bool make_sort_plan(uint64_t n, uint32_t K, uint32_t nbits, uint32_t digit_bits, SortPlan* p, uint64_t ld) {
     if (digit_bits == 0) digit_bits = 8;
+    p->ld = ld ? ld : CK_LD(n);
+    if (p->ld < n) return false;
     if (digit_bits < 4 || digit_bits > 11) return false;
     p->digit_bits = digit_bits;
     p->passes = (nbits + digit_bits - 1) / digit_bits;
@@ -399,7 +401,7 @@ bool make_sort_plan(uint64_t n, uint32_t K, uint32_t nbits, uint32_t digit_bits,
     p->off_lookback = off;
     off = align256(off + sizeof(uint32_t) * bins * (size_t)p->tiles * p->passes);
     p->off_alt_ck = off;
-    off = align256(off + sizeof(uint32_t) * (size_t)K * CK_LD(n));
+    off = align256(off + sizeof(uint32_t) * (size_t)K * p->ld);
     p->off_alt_rid = off;
     off = align256(off + sizeof(uint32_t) * n);
     p->total = off;
@@ -416,7 +418,7 @@ static cudaError_t run_sort_rb(const SortPlan& p, const uint32_t* ck_in, const u
     uint32_t* lookback = reinterpret_cast<uint32_t*>(ws + p.off_lookback);
     uint32_t* alt_ck = reinterpret_cast<uint32_t*>(ws + p.off_alt_ck);
     uint32_t* alt_rid = reinterpret_cast<uint32_t*>(ws + p.off_alt_rid);
-    const uint64_t ld = CK_LD(n);
+    const uint64_t ld = p.ld;
     cudaError_t e = cudaMemsetAsync(ws, 0, p.off_alt_ck, s);
     if (e != cudaSuccess) return e;
 
@@ -486,7 +488,8 @@ static cudaError_t run_sort_rb(const SortPlan& p, const uint32_t* ck_in, const u
         cur_rid = out_rid;
     }
     if (!perm_only && cur_ck != ck_out) {
-        e = cudaMemcpyAsync(ck_out, cur_ck, sizeof(uint32_t) * (size_t)p.K * ld, cudaMemcpyDeviceToDevice, s);
+        e = cudaMemcpy2DAsync(ck_out, sizeof(uint32_t) * ld, cur_ck, sizeof(uint32_t) * ld, sizeof(uint32_t) * n, p.K,
+                              cudaMemcpyDeviceToDevice, s);
         if (e != cudaSuccess) return e;
     }
     if (cur_rid != rid_out) {
@@ -502,7 +505,8 @@ cudaError_t run_sort(const SortPlan& p, const uint32_t* ck_in, const uint32_t* r
     if (p.passes == 0) {  // nothing to order: outputs are the inputs
         cudaError_t e = cudaSuccess;
         if (ck_out != ck_in)
-            e = cudaMemcpyAsync(ck_out, ck_in, sizeof(uint32_t) * (size_t)p.K * CK_LD(n), cudaMemcpyDeviceToDevice, s);
+            e = cudaMemcpy2DAsync(ck_out, sizeof(uint32_t) * p.ld, ck_in, sizeof(uint32_t) * p.ld, sizeof(uint32_t) * n,
+                                  p.K, cudaMemcpyDeviceToDevice, s);
         if (e != cudaSuccess) return e;
         if (rid_in == nullptr) {
             iota_kernel<<<num_sms() * 4, 256, 0, s>>>(rid_out, n);

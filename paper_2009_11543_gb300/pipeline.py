@@ -111,3 +111,71 @@ def first_build_dmask(keys: torch.Tensor, kind: int | None = None, digit_bits: i
     r = Rebuild(keys, variant, digit_bits=digit_bits, kind=kind)
     r.run()
     return ck.mask_to_host(r.refined)
+
+
+class BatchedRebuild:
+    """All the indexes of one table rebuilt together (one Rebuild per column,
+    concurrently through ck_build_batched, optionally as one CUDA graph).
+
+    columns: list of CUDA key columns (same row count); dmasks: their stored
+    D-bitmaps; digit_bits: per column, or None to run the autotuner on each
+    column's own keys (ck_autotune_sort, cached in cache_path)."""
+
+    def __init__(self, columns, dmasks, fanouts, fill: float = 1.0, digit_bits=None, cache_path: str | None = None,
+                 tune_reps: int = 3):
+        import ctypes
+        self.parts = [Rebuild(c, m, fanout=f, fill=fill, digit_bits=8) for c, m, f in zip(columns, dmasks, fanouts)]
+        self.tuned_ms = []
+        for k, r in enumerate(self.parts):
+            if digit_bits is not None:
+                r.digit_bits = int(digit_bits[k])
+            else:
+                r.extract()
+                wsb = max(ck.ck_sort_workspace_bytes(r.n, r.K, r.nbits, d) for d in range(4, 12))
+                if wsb > r.ws.numel():
+                    r.ws = torch.empty(wsb, dtype=torch.uint8, device=r.keys.device)
+                r.digit_bits, ms = ck.ck_autotune_sort(r.ck_in, r.ck_sorted, r.rid_sorted, r.n, r.K, r.nbits,
+                                                       r.ws, tune_reps, cache_path)
+                self.tuned_ms.append(ms)
+            need = ck.ck_sort_workspace_bytes(r.n, r.K, r.nbits, r.digit_bits)
+            if need > r.ws.numel():
+                r.ws = torch.empty(need, dtype=torch.uint8, device=r.keys.device)
+        self._trees = []
+        self.jobs = (ck.ck_index_job * len(self.parts))()
+        for k, r in enumerate(self.parts):
+            t = ck.ck_btree()
+            for name, tensor in r.tree.items():
+                setattr(t, name, tensor.data_ptr())
+            self._trees.append(t)
+            j = self.jobs[k]
+            j.col = r.col
+            j.dmask = r.dmask.ctypes.data
+            j.ck_words, j.digit_bits, j.fanout, j.fill = r.K, r.digit_bits, r.fanout, r.fill
+            j.ck, j.ck_sorted, j.rid_sorted = r.ck_in.data_ptr(), r.ck_sorted.data_ptr(), r.rid_sorted.data_ptr()
+            j.tree = ctypes.pointer(t)
+            j.refined_mask = r.refined.data_ptr()
+            j.ws, j.ws_bytes = r.ws.data_ptr(), r.ws.numel()
+        self.graph = None
+
+    def run(self, stream=None):
+        """One batched rebuild, the jobs on concurrent internal streams."""
+        ck.ck_build_batched(self.jobs, stream)
+
+    def capture(self):
+        """Captures one batched rebuild as a CUDA graph (replayed by launch())."""
+        if self.graph is None:
+            self.graph = ck.ck_graph_capture_batched(self.jobs)
+        return self.graph
+
+    def launch(self, stream=None):
+        ck.ck_graph_launch(self.capture(), stream)
+
+    def run_sequential(self, stream=None):
+        """The same rebuilds one after another on one stream (the unbatched path)."""
+        for r in self.parts:
+            r.run(stream)
+
+    def close(self):
+        if self.graph is not None:
+            ck.ck_graph_destroy(self.graph)
+            self.graph = None
