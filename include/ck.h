@@ -344,6 +344,22 @@ ck_status ck_build_index_keys(const ck_column* col, const uint32_t* sorted_rid, 
                               ck_stream stream);
 
 /* ---------------------------------------------------------------------------
+ * ck_model_separators -- model-proposed inner separators (not in the paper).
+ * For every inner entry of a built tree the CDF model (parameters as trained
+ * by ck_sort_learned, device [CK_MLP_PARAMS]) proposes the top 24 bits of the
+ * entry's separator -- the key of sorted rank min((e + 1) f^l, n) - 1 -- as the
+ * smallest 24-bit feature value where the model reaches (rank + 0.5) / n.
+ * Each proposal is checked against the tree's canonical separator; the tree
+ * is never changed (a wrong proposal is replaced by the canonical key), so it
+ * stays bit-identical to ck_build_index's.
+ *   proposals  device [inner_entries]: the proposed 24-bit prefixes.
+ *   hits       device [1]: the number of proposals equal to the canonical
+ *              separator's top 24 bits (zeroed by the call).
+ * Errors: CK_EINVAL. */
+ck_status ck_model_separators(const float* params, const ck_btree* tree, uint32_t ck_words, uint32_t nbits,
+                              uint32_t* proposals, uint32_t* hits, ck_stream stream);
+
+/* ---------------------------------------------------------------------------
  * Batched rebuild of all the indexes of one table (not in the paper, which
  * motivates it: a table can carry many indexes, all rebuilt after a restart).
  * Each job is one index: extract -> sort -> bulk load (+ refined D-bitmap),

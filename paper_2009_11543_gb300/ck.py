@@ -31,7 +31,7 @@ EXPORTED = ["ck_variant_bits", "ck_distinction_bits", "ck_extract", "ck_sort_wor
             "ck_status_string", "ck_launch_count", "ck_compress_word_host", "ck_sort_static", "ck_build_index_keys",
             "ck_sort_learned_workspace_bytes", "ck_sort_learned", "ck_mlp_workspace_bytes", "ck_mlp_loss_grad",
             "ck_build_batched", "ck_graph_capture_batched", "ck_graph_launch", "ck_graph_destroy",
-            "ck_autotune_sort"]
+            "ck_autotune_sort", "ck_model_separators"]
 CK_SORT_STATIC_SCRATCH_BYTES = 32 << 20
 
 
@@ -124,6 +124,7 @@ def _lib():
         lib.ck_graph_destroy.argtypes = [P]
         lib.ck_autotune_sort.argtypes = [P, P, P, U64, U32, U32, P, ctypes.c_size_t, U32, ctypes.c_char_p,
                                          ctypes.POINTER(U32), ctypes.POINTER(ctypes.c_float), P]
+        lib.ck_model_separators.argtypes = [P, ctypes.POINTER(ck_btree), U32, U32, P, P, P]
         lib.ck_device_status.argtypes = [ctypes.POINTER(U64)]
         lib.ck_status_string.argtypes = [I]
         lib.ck_status_string.restype = ctypes.c_char_p
@@ -395,6 +396,21 @@ def ck_autotune_sort(ck_in: torch.Tensor, ck_out: torch.Tensor, rid_out: torch.T
                                    cache_path.encode() if cache_path else None, ctypes.byref(d), ctypes.byref(ms),
                                    _stream(stream)), "ck_autotune_sort")
     return int(d.value), float(ms.value)
+
+
+def ck_model_separators(params: torch.Tensor, shape: ck_btree_shape, arrays: dict, ck_words: int, nbits: int,
+                        stream=None):
+    """Returns (proposals, hits) device tensors (see ck.h)."""
+    t = ck_btree()
+    t.shape = shape
+    for name, tensor in arrays.items():
+        setattr(t, name, tensor.data_ptr())
+    ni = int(shape.inner_entries)
+    prop = torch.empty(max(ni, 1), dtype=torch.int32, device=params.device)
+    hits = torch.zeros(1, dtype=torch.int32, device=params.device)
+    _check(_lib().ck_model_separators(_ptr(params), ctypes.byref(t), ck_words, nbits, _ptr(prop), _ptr(hits),
+                                      _stream(stream)), "ck_model_separators")
+    return prop, hits
 
 
 def ck_device_status() -> tuple[int, int]:

@@ -739,6 +739,53 @@ __global__ void verify_kernel(const uint32_t* __restrict__ ck, const uint32_t* _
     if (bad) atomicAdd(&flags[1], bad);
 }
 
+// ------------------------------------------------------------ separators
+// Model-proposed inner separators: for inner entry e of level l the canonical
+// separator is the key of sorted rank hi = min((e + 1) f^l, n) - 1; the model
+// proposes its top 24 compressed bits as the smallest 24-bit feature value x
+// with y(x) >= (hi + 0.5) / n (bisection, 24 steps).  A proposal is a hit when
+// it equals the canonical separator's top 24 bits; the tree always keeps the
+// canonical key, so a miss is simply replaced.
+__global__ void separators_kernel(const float* __restrict__ params, const __grid_constant__ InnerLevels lv, uint64_t n,
+                                  uint32_t f, const uint32_t* __restrict__ high_ck, uint32_t K, uint32_t nbits,
+                                  uint32_t* __restrict__ prop, uint32_t* __restrict__ hits) {
+    __shared__ float p[kParams];
+    if (threadIdx.x < kParams) p[threadIdx.x] = params[threadIdx.x];
+    __syncthreads();
+    uint32_t my_hits = 0;
+    for (uint64_t g = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; g < lv.inner_entries;
+         g += (uint64_t)gridDim.x * blockDim.x) {
+        uint32_t l = 1;
+        while (l + 1 < lv.levels && g >= lv.offset[l + 1]) ++l;
+        const uint64_t e = g - lv.offset[l];
+        uint64_t span = 1;
+        for (uint32_t t = 0; t < l; ++t) span = min(span * f, n);
+        const uint64_t hi = min((e + 1) * span, n) - 1;
+        const float target = ((float)hi + 0.5f) / (float)n;
+        uint32_t lo = 0, up = 1u << 24;
+        while (lo < up) {
+            const uint32_t mid = (lo + up) >> 1;
+            if (mlp_eval(p, (float)mid * (1.0f / 16777216.0f)) >= target) up = mid;
+            else lo = mid + 1;
+        }
+        const uint32_t proposal = lo > 0xFFFFFFu ? 0xFFFFFFu : lo;
+        prop[g] = proposal;
+        // canonical top 24 bits of the entry's compressed key (entry-major, K words)
+        uint32_t canon;
+        const uint32_t* c = high_ck + g * K;
+        if (nbits >= 24) {
+            const uint32_t lob = nbits - 24, w = lob >> 5, sh = lob & 31;
+            uint64_t v = c[w];
+            if (w + 1 < K) v |= (uint64_t)c[w + 1] << 32;
+            canon = (uint32_t)(v >> sh) & 0xFFFFFFu;
+        } else {
+            canon = (c[0] << (24 - nbits)) & 0xFFFFFFu;
+        }
+        my_hits += proposal == canon ? 1u : 0u;
+    }
+    if (my_hits) atomicAdd(hits, my_hits);
+}
+
 // ------------------------------------------------------------ workspace
 struct LearnedPlan {
     uint32_t B, bucket_bits, passes, K, nbits;
@@ -1063,6 +1110,28 @@ ck_status ck_sort_learned(const uint32_t* ck_in, uint32_t* ck_out, uint32_t* rid
                     ws + P.off_plain_ws, s));
 #undef CK_TRY
     return CK_EVERIFY;
+}
+
+ck_status ck_model_separators(const float* params, const ck_btree* tree, uint32_t ck_words, uint32_t nbits,
+                              uint32_t* proposals, uint32_t* hits, ck_stream stream) {
+    if (!params || !tree || ck_words == 0 || ck_words > kMaxLearnedWords || nbits > 32u * ck_words || !hits)
+        return CK_EINVAL;
+    const ck_btree_shape& sh = tree->shape;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    if (cudaMemsetAsync(hits, 0, sizeof(uint32_t), s) != cudaSuccess) return CK_ECUDA;
+    if (sh.inner_entries == 0) return CK_OK;
+    if (!proposals || !tree->inner_high_ck) return CK_EINVAL;
+    InnerLevels lv;
+    memset(&lv, 0, sizeof(lv));
+    lv.levels = sh.levels;
+    lv.inner_entries = sh.inner_entries;
+    for (uint32_t l = 0; l < CK_MAX_LEVELS; ++l) lv.offset[l] = sh.inner_offset[l];
+    const uint64_t want = (sh.inner_entries + 255) / 256, cap = (uint64_t)num_sms() * 8;
+    separators_kernel<<<(unsigned)(want < cap ? want : cap), 256, 0, s>>>(params, lv, sh.n, sh.entries_per_node,
+                                                                        tree->inner_high_ck, ck_words, nbits,
+                                                                        proposals, hits);
+    count_launch();
+    return cudaGetLastError() == cudaSuccess ? CK_OK : CK_ECUDA;
 }
 
 }  // extern "C"

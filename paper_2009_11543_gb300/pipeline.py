@@ -45,6 +45,7 @@ class Rebuild:
         self.learned = learned
         self.learned_opts = learned_opts
         self.learned_stats = None
+        self.learned_params = None
         dev = keys.device
         n = max(self.n, 1)
         self.ck_in = ck.ck_buffer(self.K, n, dev)
@@ -63,9 +64,9 @@ class Rebuild:
 
     def sort(self, stream=None, pass_events=None):
         if self.learned:
-            st, self.learned_stats, _ = ck.ck_sort_learned(self.ck_in, self.ck_sorted, self.rid_sorted, self.n,
-                                                           self.K, self.nbits, self.ws, self.learned_opts,
-                                                           stream=stream)
+            st, self.learned_stats, self.learned_params = ck.ck_sort_learned(
+                self.ck_in, self.ck_sorted, self.rid_sorted, self.n, self.K, self.nbits, self.ws, self.learned_opts,
+                stream=stream)
             return
         ck.ck_sort(self.ck_in, None, self.ck_sorted, self.rid_sorted, self.n, self.K, self.nbits, self.ws,
                    digit_bits=self.digit_bits, pass_events=pass_events, perm_only=self.perm_only, stream=stream)
@@ -77,6 +78,15 @@ class Rebuild:
         else:
             ck.ck_build_index(self.ck_sorted, self.rid_sorted, self.n, self.K, self.dmask, self.key_bits,
                               self.fanout, self.fill, arrays=self.tree, refined_out=self.refined, stream=stream)
+
+    def separators(self, stream=None):
+        """Model-proposed inner separators of the built tree (learned mode):
+        returns (proposals, hit count); the tree itself is not changed."""
+        if self.learned_params is None:
+            raise RuntimeError("no trained model: run a learned sort first")
+        params = torch.from_numpy(self.learned_params).to(self.keys.device)
+        prop, hits = ck.ck_model_separators(params, self.shape, self.tree, self.K, self.nbits, stream=stream)
+        return prop, hits
 
     def run(self, stream=None):
         """One full rebuild: extract, sort, bulk load (+ refined D-bitmap)."""

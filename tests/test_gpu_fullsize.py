@@ -80,3 +80,54 @@ def test_urls_64m_full_size():
     hck = ck.u32(r.tree["inner_high_ck"])[:ni * 4].reshape(ni, 4)
     sel = np.sort(rng.choice(ni, min(ni, 50_000), replace=False))
     assert np.array_equal(hck[sel], oracle.compress(keys[perm[t["high"][sel]]], dmask, 4))
+
+
+def check_full(keys, r, fanout):
+    n = len(keys)
+    kb = oracle.as_key_bytes(keys) if keys.ndim == 1 else keys
+    perm = ck.u32(r.rid_sorted)[:n]
+    assert np.all(np.bincount(perm, minlength=n) == 1)
+    assert rows_ordered(kb if kb.shape[1] % 8 == 0 else np.pad(kb, ((0, 0), (0, 8 - kb.shape[1] % 8))), perm)
+    D = oracle.dmask(kb, perm)
+    assert list(D) == list(ck.mask_to_host(r.refined))
+    t = oracle.btree(kb, perm, fanout)
+    assert np.array_equal(r.tree["leaf_dbit"].cpu().numpy().view(np.uint16)[:n], t["leaf_dbit"])
+    ni = int(r.shape.inner_entries)
+    assert np.array_equal(r.tree["inner_dbit"].cpu().numpy().view(np.uint16)[:ni], t["dbit"])
+    return perm
+
+
+@pytest.mark.parametrize("name,n,fanout", [("zipf", 256 * 2**20, 64), ("dna", 200_000_000, 256)])
+def test_learned_full_size(name, n, fanout):
+    """The learned configurations at the bench's sizes: 256M Zipf(0.9) uint64
+    keys and 200M DNA keys, learned partition in the bench's configuration."""
+    keys = synth.zipf_tagged_u64(n, synth.BASE_SEED + 4, 0.9) if name == "zipf" else synth.dna(n, synth.BASE_SEED + 5)
+    kd = torch.from_numpy(keys.view(np.int64) if keys.dtype == np.uint64 else keys).to("cuda:0")
+    dmask = pipeline.first_build_dmask(kd)
+    r = pipeline.Rebuild(kd, dmask, fanout=fanout, learned=True)
+    r.run()
+    torch.cuda.synchronize()
+    assert ck.ck_device_status()[0] == ck.CK_OK
+    assert r.learned_stats["fell_back"] == 0, r.learned_stats
+    perm = check_full(keys, r, fanout)
+    p = pipeline.Rebuild(kd, dmask, fanout=fanout)      # the plain path gives the same bits
+    p.run()
+    torch.cuda.synchronize()
+    assert np.array_equal(ck.u32(p.rid_sorted)[:n], perm)
+    assert torch.equal(p.ck_sorted, r.ck_sorted)
+
+
+def test_batched_table_full_size():
+    """16M rows x 6 indexes, batched graph with autotuned digit widths."""
+    n = 16 * 2**20
+    cols = synth.table_columns(n, synth.BASE_SEED + 3)
+    dev = [torch.from_numpy(c.view(np.int64) if c.dtype == np.uint64 else
+                            (c.view(np.int32) if c.dtype == np.uint32 else c)).to("cuda:0") for c in cols]
+    dmasks = [pipeline.first_build_dmask(c) for c in dev]
+    fan = [64, 64, 64, 64, 256, 256]
+    b = pipeline.BatchedRebuild(dev, dmasks, fan, tune_reps=2)
+    b.launch()
+    torch.cuda.synchronize()
+    for c, r, f in zip(cols, b.parts, fan):
+        check_full(c, r, f)
+    b.close()

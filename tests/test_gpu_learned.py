@@ -178,3 +178,46 @@ def test_model_gain_over_no_model(name):
              s["train_loss"]))
     if name in ("zipf", "uniform"):
         assert sm["mean_search_steps"] < 0.8 * sn["mean_search_steps"]
+
+
+def test_model_separators_keep_the_canonical_tree():
+    """Model-proposed inner separators (fanout 256, DNA keys): the tree equals
+    the plain rebuild's bit for bit, the hit count equals a host recount, and
+    sampled proposals agree with an fp64 bisection of the oracle's model."""
+    n = 2_000_000
+    keys = WORKLOADS["dna"](n)
+    kd = torch.from_numpy(keys).to(DEV)
+    D = pipeline.first_build_dmask(kd)
+    L = pipeline.Rebuild(kd, D, fanout=256, learned=True)
+    P = pipeline.Rebuild(kd, D, fanout=256)
+    L.run()
+    P.run()
+    prop, hits = L.separators()
+    torch.cuda.synchronize()
+    for name in P.tree:
+        assert torch.equal(L.tree[name], P.tree[name]), name
+    ni = int(L.shape.inner_entries)
+    K, nbits = L.K, L.nbits
+    hck = ck.u32(L.tree["inner_high_ck"])[:ni * K].reshape(ni, K).astype(np.uint64)
+    val = np.zeros(ni, dtype=object)
+    for w in range(K):
+        val = val + (hck[:, w].astype(object) << (32 * w))
+    top = np.array([int(v) >> (nbits - 24) for v in val], np.uint64)
+    pr = ck.u32(prop)[:ni]
+    assert int(hits.cpu()[0]) == int(np.sum(pr == top))
+    print("separator proposals: %d of %d hit" % (int(hits.cpu()[0]), ni))
+    params = L.learned_params.astype(np.float64)
+    f = L.shape.entries_per_node
+    offs = [int(L.shape.inner_offset[l]) for l in range(L.shape.levels)]
+    rng = np.random.default_rng(1)
+    for g in rng.choice(ni, min(ni, 40), replace=False):
+        l = max(k for k in range(1, L.shape.levels) if g >= offs[k])
+        e = g - offs[l]
+        hi = min((e + 1) * f ** l, n) - 1
+        target = (hi + 0.5) / n
+        # the proposal is where the model reaches the target: checked in fp64
+        # within the fp32 evaluation error of a 16-term sum of O(1) terms
+        eps = 2e-6
+        x = int(pr[g])
+        assert x == 2**24 - 1 or oracle.mlp_forward(params, x / 2**24) >= target - eps
+        assert x == 0 or oracle.mlp_forward(params, (x - 1) / 2**24) < target + eps
