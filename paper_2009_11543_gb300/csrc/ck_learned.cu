@@ -1,24 +1,30 @@
 // ck_learned.cu -- the learned-partition sort (not in the paper): a tiny fp32
 // CDF model, trained on the GPU on a sample of the compressed keys, places
-// every key in one of B = 2^bucket_bits key-range buckets; two radix passes on
-// the bucket id partition the pairs stably, and each bucket is then sorted in
-// shared memory.  The result is the same permutation as the plain radix sort:
+// every key in one of about B = 2^bucket_bits key-range buckets; two radix
+// passes on the bucket id partition the pairs stably, and each bucket is then
+// sorted in shared memory.  The result is the same permutation as the plain
+// radix sort:
 //
 //  * the buckets are ranges between monotone splitters (the B-quantiles of the
-//    sorted sample, with heavy keys isolated in buckets of their own), so a
-//    stable partition by bucket followed by a stable sort inside each bucket
-//    is a stable sort of the whole column;
+//    sorted sample moved to the nearer end of their run of equal keys, with
+//    heavy keys isolated in buckets of their own), so a stable partition by
+//    bucket followed by a stable sort inside each bucket is a stable sort of
+//    the whole column;
 //  * the model proposes each key's bucket as floor(y(x) * B) in O(1); a short
 //    walk against the splitters makes the assignment exact (a far-off guess
 //    falls back to binary search), so a poor model costs time, not
 //    correctness.  Without the model every key needs a binary search;
-//  * a verification pass checks every adjacent output pair; if it fails, or a
-//    non-constant bucket is larger than a block can sort, the plain radix sort
-//    recomputes the result from the untouched input (status CK_EVERIFY).
+//  * a bucket is sorted by the 32-bit window at its first varying bit, and
+//    ties are settled below the window; a non-constant bucket too large for a
+//    block is sorted by the plain radix sort on its segment;
+//  * a verification pass checks every adjacent output pair; if it fails, the
+//    plain radix sort recomputes the result from the untouched input (status
+//    CK_EVERIFY).
 //
 // The model: y(x) = b2 + sum_j w2_j relu(w1_j x + b1_j), 16 hidden units, on
 // x = the top 24 bits of the compressed key / 2^24, fitted by full-batch Adam
 // to the empirical CDF (rank + 0.5) / S of the sorted sample.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 
@@ -278,40 +284,119 @@ __device__ __forceinline__ int cmp_words(const uint32_t* a, const uint32_t* b, u
     return 0;
 }
 
-// Splitter b (1 <= b < B) is the sample key at idx_b = floor(b * S / B) of the
-// sorted sample (or at first[b] when given).
-__global__ void splitter_kernel(const uint32_t* __restrict__ sample, uint64_t ld_s, uint64_t S, uint32_t K,
-                                uint32_t B, const uint32_t* __restrict__ first, uint32_t* __restrict__ spl) {
+// Is the K-word key v the largest nbits-bit key (no v + 1)?
+__device__ __forceinline__ bool is_max_key(const uint32_t* v, uint32_t K, uint32_t nbits) {
+    for (uint32_t w = 0; w < K; ++w) {
+        const uint32_t bits = min(32u, nbits > 32 * w ? nbits - 32 * w : 0u);
+        const uint32_t full = bits == 32 ? 0xFFFFFFFFu : ((1u << bits) - 1u);
+        if (v[w] != full) return false;
+    }
+    return true;
+}
+
+// Splitters from the sorted sample.  Quantile b (1 <= b < B) sits at sample
+// position q_b = floor(b S / B) with value v.  The sample holds v at [i0, i1);
+// moving the bucket boundary off the quantile to the nearer end of that run
+// (splitter v puts the boundary at i0, v + 1 at i1) keeps every copy of v in
+// one bucket and moves the boundary by at most half the run.  A value with at
+// least `heavy` sample copies gets a bucket of its own, [v, v + 1) (splitters
+// v and v + 1 at its first quantile); later quantiles inside the same run
+// repeat the run's last splitter (empty buckets).  codes[b - 1]: bits 0-1 =
+// choice with heavy buckets, bits 2-3 = choice without (1: v, 2: v + 1,
+// 3: v and v + 1).
+__global__ void quantile_kernel(const uint32_t* __restrict__ sample, uint64_t ld_s, uint64_t S, uint32_t K,
+                                uint32_t B, uint32_t nbits, uint64_t heavy, uint8_t* __restrict__ codes) {
     for (uint32_t b = blockIdx.x * blockDim.x + threadIdx.x + 1; b < B; b += gridDim.x * blockDim.x) {
-        uint64_t idx = first ? first[b] : (uint64_t)b * S / B;
-        if (idx >= S) idx = S - 1;  // no sample reaches b / B: the largest sample key
-        for (uint32_t w = 0; w < K; ++w) spl[(uint64_t)(b - 1) * K + w] = sample[(uint64_t)w * ld_s + idx];
+        uint64_t q = (uint64_t)b * S / B;
+        if (q >= S) q = S - 1;
+        uint32_t v[kMaxLearnedWords];
+        for (uint32_t w = 0; w < K; ++w) v[w] = sample[(uint64_t)w * ld_s + q];
+        auto cmp_at = [&](uint64_t i) {  // sample[i] vs v
+            for (int w = (int)K - 1; w >= 0; --w) {
+                const uint32_t x = sample[(uint64_t)w * ld_s + i];
+                if (x != v[w]) return x < v[w] ? -1 : 1;
+            }
+            return 0;
+        };
+        uint64_t lo = 0, hi = q;  // i0: first position with sample >= v
+        while (lo < hi) {
+            const uint64_t mid = (lo + hi) >> 1;
+            if (cmp_at(mid) < 0) lo = mid + 1;
+            else hi = mid;
+        }
+        const uint64_t i0 = lo;
+        lo = q + 1;
+        hi = S;  // i1: first position with sample > v
+        while (lo < hi) {
+            const uint64_t mid = (lo + hi) >> 1;
+            if (cmp_at(mid) <= 0) lo = mid + 1;
+            else hi = mid;
+        }
+        const uint64_t i1 = lo;
+        // the first quantile inside the run decides for all of them
+        uint64_t bf = (i0 * B + S - 1) / S;  // smallest b' with floor(b' S / B) >= i0
+        if (bf < 1) bf = 1;
+        uint64_t qf = bf * S / B;
+        if (qf >= S) qf = S - 1;
+        const bool top = is_max_key(v, K, nbits);
+        const bool up = !top && (i1 - qf) < (qf - i0);
+        const bool is_heavy = !top && i1 - i0 >= heavy;
+        const uint32_t single = up ? 2u : 1u;
+        const uint32_t with_heavy = is_heavy ? (bf == b ? 3u : 2u) : single;
+        codes[b - 1] = (uint8_t)(with_heavy | (single << 2));
     }
 }
 
-// Heavy keys: in a run of equal splitters v (length >= 2) the last becomes
-// v + 1, so that bucket [v, v + 1) holds exactly the copies of v (a bucket of
-// equal keys needs no sorting).  Monotonicity is kept since the next splitter
-// is > v.  Writes the final splitters to out.
-__global__ void singleton_kernel(const uint32_t* __restrict__ spl, uint32_t K, uint32_t B, uint32_t nbits,
-                                 uint32_t* __restrict__ out) {
-    for (uint32_t b = blockIdx.x * blockDim.x + threadIdx.x; b + 1 < B; b += gridDim.x * blockDim.x) {
-        const uint32_t* v = spl + (uint64_t)b * K;
-        uint32_t* o = out + (uint64_t)b * K;
-        bool last_of_run = b > 0 && cmp_words(v, v - K, K) == 0 && (b + 2 == B || cmp_words(v, v + K, K) != 0);
-        uint32_t carry = last_of_run ? 1u : 0u;
-        // v + 1 must still fit nbits bits; the all-ones key keeps its value
-        bool all_ones = true;
-        for (uint32_t w = 0; w < K; ++w) {
-            const uint32_t bits = min(32u, nbits > 32 * w ? nbits - 32 * w : 0u);
-            const uint32_t full = bits == 32 ? 0xFFFFFFFFu : ((1u << bits) - 1u);
-            all_ones = all_ones && v[w] == full;
+// Writes the splitters in order (one block): with heavy buckets when all of
+// them fit max_buckets, else without.  nsplit[0] = number of splitters (the
+// buckets are [spl[b - 1], spl[b]), b = 0 .. nsplit, open at both ends).
+__global__ void __launch_bounds__(1024) emit_splitters_kernel(const uint32_t* __restrict__ sample, uint64_t ld_s,
+                                                              uint64_t S, uint32_t K, uint32_t B,
+                                                              uint32_t max_buckets,
+                                                              const uint8_t* __restrict__ codes,
+                                                              uint32_t* __restrict__ spl, uint32_t* nsplit) {
+    __shared__ uint32_t part[1024];
+    __shared__ uint32_t s_heavy;
+    const uint32_t tid = threadIdx.x, nq = B - 1;
+    const uint32_t per = (nq + 1023) / 1024, lo = tid * per, hi = min(nq, lo + per);
+    if (tid == 0) s_heavy = 0;
+    __syncthreads();
+    uint32_t extra = 0;
+    for (uint32_t c = lo; c < hi; ++c) extra += (codes[c] & 3u) == 3u ? 1u : 0u;
+    if (extra) atomicAdd(&s_heavy, extra);
+    __syncthreads();
+    const uint32_t shift = nq + s_heavy + 1 <= max_buckets ? 0u : 2u;
+    uint32_t cnt = 0;
+    for (uint32_t c = lo; c < hi; ++c) cnt += ((codes[c] >> shift) & 3u) == 3u ? 2u : 1u;
+    part[tid] = cnt;
+    __syncthreads();
+    if (tid == 0) {
+        uint32_t run = 0;
+        for (int t = 0; t < 1024; ++t) {
+            const uint32_t x = part[t];
+            part[t] = run;
+            run += x;
         }
-        if (all_ones) carry = 0;
-        for (uint32_t w = 0; w < K; ++w) {
-            const uint64_t sum = (uint64_t)v[w] + carry;
-            o[w] = (uint32_t)sum;
-            carry = (uint32_t)(sum >> 32);
+        *nsplit = run;
+    }
+    __syncthreads();
+    uint32_t at = part[tid];
+    for (uint32_t c = lo; c < hi; ++c) {
+        const uint32_t code = (codes[c] >> shift) & 3u;
+        uint64_t q = (uint64_t)(c + 1) * S / B;
+        if (q >= S) q = S - 1;
+        if (code & 1u) {  // v
+            for (uint32_t w = 0; w < K; ++w) spl[(uint64_t)at * K + w] = sample[(uint64_t)w * ld_s + q];
+            ++at;
+        }
+        if (code & 2u) {  // v + 1
+            uint32_t carry = 1;
+            for (uint32_t w = 0; w < K; ++w) {
+                const uint64_t sum = (uint64_t)sample[(uint64_t)w * ld_s + q] + carry;
+                spl[(uint64_t)at * K + w] = (uint32_t)sum;
+                carry = (uint32_t)(sum >> 32);
+            }
+            ++at;
         }
     }
 }
@@ -320,15 +405,18 @@ __global__ void singleton_kernel(const uint32_t* __restrict__ spl, uint32_t K, u
 struct BucketArgs {
     const uint32_t* ck;
     uint64_t ld, n;
-    uint32_t K, nbits, B, bucket_bits, use_model;
-    const uint32_t* spl;  // [(B - 1) * K], entry-major, non-decreasing
+    uint32_t K, nbits, max_buckets, use_model;
+    const uint32_t* nsplit;  // number of splitters (buckets - 1), on the device
+    const uint32_t* spl;     // [nsplit * K], entry-major, non-decreasing
     const float* params;
+    const float* loss;    // training loss (mean squared CDF error) of params
     uint32_t* bkt;        // [n]
     uint32_t* hist;       // [2][256] digit histograms of the bucket id (low byte, high bits)
     unsigned long long* steps;  // [0]: total search steps, [1]: max
 };
 
-// Compile-time-width comparisons for the bucket kernel (key in registers).
+// Compile-time-width helpers for the bucket kernel (key in registers; word
+// indices are resolved by unrolled selects so the key never leaves registers).
 template <int KW>
 __device__ __forceinline__ int cmp_key(const uint32_t (&key)[KW], const uint32_t* s) {
 #pragma unroll
@@ -337,87 +425,112 @@ __device__ __forceinline__ int cmp_key(const uint32_t (&key)[KW], const uint32_t
     return 0;
 }
 
-// Comparison of key x with splitter m: the shared table of splitter top words
-// decides unless the top words are equal, then the full splitter is read.
+// The top 32 bits of an nbits-bit key, left-aligned (zero-filled below a
+// shorter key).  Keys compare as their top32 values first.
 template <int KW>
-__device__ __forceinline__ int cmp_split(const uint32_t (&key)[KW], const uint32_t* top, const uint32_t* spl,
-                                         uint32_t m) {
-    const uint32_t t = top[m];
-    if (key[KW - 1] != t) return key[KW - 1] < t ? -1 : 1;
-    return cmp_key<KW>(key, spl + (uint64_t)m * KW);
+__device__ __forceinline__ uint32_t top32_regs(const uint32_t (&key)[KW], uint32_t nbits) {
+    if (nbits < 32) return key[0] << (32 - nbits);
+    const uint32_t lo = nbits - 32, w = lo >> 5, sh = lo & 31;
+    uint32_t a = 0, b = 0;
+#pragma unroll
+    for (int j = 0; j < KW; ++j) {
+        if ((uint32_t)j == w) a = key[j];
+        if ((uint32_t)j == w + 1) b = key[j];
+    }
+    return sh ? __funnelshift_r(a, b, sh) : a;
 }
 
+__device__ __forceinline__ uint32_t top32_mem(const uint32_t* key, uint32_t K, uint32_t nbits) {
+    if (nbits < 32) return key[0] << (32 - nbits);
+    const uint32_t lo = nbits - 32, w = lo >> 5, sh = lo & 31;
+    return sh ? __funnelshift_r(key[w], key[w + 1 < K ? w + 1 : w], sh) : key[w];
+}
+
+// Comparison of key x (top32 value t) with splitter m: the shared table of
+// splitter top32 values decides unless they are equal, then the full
+// splitter is read.
 template <int KW, bool STAGED>
-__device__ __forceinline__ int cmp_at(const uint32_t (&key)[KW], const uint32_t* top, const uint32_t* spl,
-                                      uint32_t m) {
-    return STAGED ? cmp_split<KW>(key, top, spl, m) : cmp_key<KW>(key, spl + (uint64_t)m * KW);
+__device__ __forceinline__ int cmp_at(const uint32_t (&key)[KW], uint32_t t, const uint32_t* top,
+                                      const uint32_t* spl, uint32_t m) {
+    if (STAGED) {
+        const uint32_t u = top[m];
+        if (t != u) return t < u ? -1 : 1;
+    }
+    return cmp_key<KW>(key, spl + (uint64_t)m * KW);
 }
 
 // Number of splitters <= x within [lo, hi] (binary search).
 template <int KW, bool STAGED>
-__device__ __forceinline__ uint32_t search_range(const uint32_t (&key)[KW], const uint32_t* top, const uint32_t* spl,
-                                                 uint32_t lo, uint32_t hi, uint32_t* cmp) {
+__device__ __forceinline__ uint32_t search_range(const uint32_t (&key)[KW], uint32_t t, const uint32_t* top,
+                                                 const uint32_t* spl, uint32_t lo, uint32_t hi, uint32_t* cmp) {
     while (lo < hi) {
         const uint32_t mid = (lo + hi) >> 1;
         ++*cmp;
-        if (cmp_at<KW, STAGED>(key, top, spl, mid) >= 0) lo = mid + 1;
+        if (cmp_at<KW, STAGED>(key, t, top, spl, mid) >= 0) lo = mid + 1;
         else hi = mid;
     }
     return lo;
 }
 
-// Exact bucket from a guess g: check the guess's range, then gallop away from
-// it (1, 2, 4, ... buckets) and finish with a binary search, so a guess that
-// is e buckets off costs about 2 log2(e) + 2 comparisons.
+// Exact bucket from a guess g in [lo, hi] (the key's bucket is known to lie
+// there): check the guess's range, then gallop away from it (1, 2, 4, ...
+// buckets) and finish with a binary search, so a guess that is e buckets off
+// costs about 2 log2(e) + 2 comparisons.
 template <int KW, bool STAGED>
-__device__ __forceinline__ uint32_t search_from_guess(const uint32_t (&key)[KW], const uint32_t* top,
-                                                      const uint32_t* spl, uint32_t B, uint32_t g, uint32_t* cmp) {
+__device__ __forceinline__ uint32_t search_from_guess(const uint32_t (&key)[KW], uint32_t t, const uint32_t* top,
+                                                      const uint32_t* spl, uint32_t lo, uint32_t hi, uint32_t g,
+                                                      uint32_t* cmp) {
     ++*cmp;
-    if (g > 0 && cmp_at<KW, STAGED>(key, top, spl, g - 1) < 0) {  // below: gallop down
-        uint32_t hi = g - 1, step = 1;
+    if (g > lo && cmp_at<KW, STAGED>(key, t, top, spl, g - 1) < 0) {  // below: gallop down
+        uint32_t h = g - 1, step = 1;
         while (true) {
-            const uint32_t probe = hi >= step ? hi - step : 0;
+            const uint32_t probe = h >= lo + step ? h - step : lo;
             ++*cmp;
-            if (cmp_at<KW, STAGED>(key, top, spl, probe) >= 0)
-                return search_range<KW, STAGED>(key, top, spl, probe + 1, hi, cmp);
-            if (probe == 0) return 0;
-            hi = probe;
+            if (cmp_at<KW, STAGED>(key, t, top, spl, probe) >= 0)
+                return search_range<KW, STAGED>(key, t, top, spl, probe + 1, h, cmp);
+            if (probe == lo) return lo;
+            h = probe;
             step <<= 1;
         }
     }
     ++*cmp;
-    if (g < B - 1 && cmp_at<KW, STAGED>(key, top, spl, g) >= 0) {  // above: gallop up
-        uint32_t lo = g + 1, step = 1;
+    if (g < hi && cmp_at<KW, STAGED>(key, t, top, spl, g) >= 0) {  // above: gallop up
+        uint32_t l = g + 1, step = 1;
         while (true) {
-            const uint32_t probe = lo + step - 1 < B - 1 ? lo + step - 1 : B - 2;
+            const uint32_t probe = l + step - 1 < hi ? l + step - 1 : hi - 1;
             ++*cmp;
-            if (cmp_at<KW, STAGED>(key, top, spl, probe) < 0)
-                return search_range<KW, STAGED>(key, top, spl, lo, probe, cmp);
-            lo = probe + 1;
-            if (probe == B - 2) return B - 1;
+            if (cmp_at<KW, STAGED>(key, t, top, spl, probe) < 0)
+                return search_range<KW, STAGED>(key, t, top, spl, l, probe, cmp);
+            l = probe + 1;
+            if (probe == hi - 1) return hi;
             step <<= 1;
         }
     }
     return g;
 }
 
-// Bucket id of every key.  With STAGED, the most significant word of every
-// splitter sits in shared memory ((B - 1) words), with a table over its top
-// kPrefixBits bits: pre[p] = first splitter whose top word is >= p << (32 -
-// kPrefixBits).  A key whose top word has prefix p has its bucket in
-// [pre[p], pre[p + 1]]; the model's guess is clamped into that range and the
-// search (galloping from the guess, or binary without the model) runs there.
+// Bucket id of every key (B = splitters + 1 buckets).  With STAGED, the top32
+// value of every splitter sits in shared memory, with a table over its top
+// kPrefixBits bits: pre[p] = first splitter whose top32 is >= p << (32 -
+// kPrefixBits).  A key whose top32 has prefix p has its bucket in [pre[p],
+// pre[p + 1]].  The model's guess, clamped into the range, starts a galloping
+// search where that is expected to be cheaper than a binary search of the
+// range: its error is about e = sqrt(loss) B buckets, so galloping costs about
+// 2 log2(e + 1) + 2 comparisons against log2(range + 1).  Without STAGED the
+// range is all buckets.
 constexpr int kPrefixBits = 12;
 
 template <int KW, bool STAGED>
 __global__ void __launch_bounds__(1024) bucket_kernel(const BucketArgs a) {
     extern __shared__ uint32_t top[];
-    uint32_t* pre = top + (a.B - 1);  // [2^kPrefixBits + 1] when staged
+    uint32_t* pre = top + (a.max_buckets - 1);  // [2^kPrefixBits + 1] when staged
     __shared__ float p[kParams];
     __shared__ uint32_t hlo[256], hhi[256];
     __shared__ unsigned long long s_sum, s_max;
     const int tid = threadIdx.x;
-    const uint32_t B = a.B;
+    const uint32_t B = min(*a.nsplit + 1, a.max_buckets), nbits = a.nbits;
+    const float err = a.use_model ? sqrtf(fmaxf(*a.loss, 0.0f)) * (float)B + 1.0f : 0.0f;
+    const float model_min_range = 4.0f * err * err;  // use the model on ranges wider than this
     if (tid < kParams) p[tid] = a.params ? a.params[tid] : 0.0f;
     if (tid < 256) {
         hlo[tid] = 0;
@@ -428,7 +541,7 @@ __global__ void __launch_bounds__(1024) bucket_kernel(const BucketArgs a) {
         s_max = 0;
     }
     if (STAGED) {
-        for (uint32_t m = tid; m + 1 < B; m += blockDim.x) top[m] = a.spl[(uint64_t)m * KW + KW - 1];
+        for (uint32_t m = tid; m + 1 < B; m += blockDim.x) top[m] = top32_mem(a.spl + (uint64_t)m * KW, KW, nbits);
         __syncthreads();
         for (uint32_t q = tid; q <= (1u << kPrefixBits); q += blockDim.x) {
             uint32_t lo = 0, hi = B - 1;  // first m with top[m] >= q << (32 - kPrefixBits)
@@ -447,19 +560,21 @@ __global__ void __launch_bounds__(1024) bucket_kernel(const BucketArgs a) {
         uint32_t key[KW];
 #pragma unroll
         for (int w = 0; w < KW; ++w) key[w] = a.ck[(uint64_t)w * a.ld + i];
+        const uint32_t t = top32_regs<KW>(key, nbits);
         uint32_t g, steps = 0, lo = 0, hi = B - 1;
         if (STAGED) {
-            const uint32_t q = key[KW - 1] >> (32 - kPrefixBits);
+            const uint32_t q = t >> (32 - kPrefixBits);
             lo = pre[q];
             hi = pre[q + 1];
         }
-        if (a.use_model) {
-            const float y = mlp_eval(p, key_feature(a.ck, a.ld, i, KW, a.nbits)) * (float)B;
+        if (a.use_model && (float)(hi - lo) + 1.0f > model_min_range) {
+            const float x = (float)(t >> 8) * (1.0f / 16777216.0f);  // the top 24 bits, as in training
+            const float y = mlp_eval(p, x) * (float)B;
             uint32_t guess = y <= 0.0f ? 0u : (y >= (float)(B - 1) ? B - 1 : (uint32_t)y);
             guess = guess < lo ? lo : (guess > hi ? hi : guess);
-            g = search_from_guess<KW, STAGED>(key, top, a.spl, B, guess, &steps);
+            g = search_from_guess<KW, STAGED>(key, t, top, a.spl, lo, hi, guess, &steps);
         } else {
-            g = search_range<KW, STAGED>(key, top, a.spl, lo, hi, &steps);
+            g = search_range<KW, STAGED>(key, t, top, a.spl, lo, hi, &steps);
         }
         a.bkt[i] = g;
         atomicAdd(&hlo[g & 255u], 1u);
@@ -558,9 +673,10 @@ struct LocalArgs {
     uint32_t* ck;          // partitioned, sorted in place; word-major, leading dimension ld
     uint32_t* rid;
     const uint32_t* start; // [B + 1]
-    const uint32_t* spl;   // final splitters
+    const uint32_t* spl;   // splitters
+    const uint32_t* nsplit;  // their number, on the device (buckets = nsplit + 1)
     uint64_t ld;
-    uint32_t K, B, nbits, cap;
+    uint32_t K, B, cap;    // B: size of the bucket id space (buckets past nsplit are empty)
     uint32_t* next;        // bucket queue
     uint32_t* flags;       // [0] oversize buckets (also the length of `over`)
     uint32_t* counts;      // [0] buckets sorted, [1] constant buckets, [2] max bucket
@@ -570,32 +686,213 @@ struct LocalArgs {
 
 constexpr int kLocalThreads = 1024;
 constexpr int kLocalWarps = kLocalThreads / 32;
+constexpr uint32_t kShortRun = 16;  // runs of equal windows up to this length: insertion sort by one thread
+constexpr int kRunList = 1024;      // longer runs of one round (disjoint, so at most cap / 17)
+
+// Key i < key j (bucket-local indices into the word-major shared key array).
+__device__ __forceinline__ bool key_less(const uint32_t* keys, uint32_t cap, uint32_t K, uint32_t i, uint32_t j) {
+    for (int w = (int)K - 1; w >= 0; --w) {
+        const uint32_t x = keys[(size_t)w * cap + i], y = keys[(size_t)w * cap + j];
+        if (x != y) return x < y;
+    }
+    return false;
+}
+
+// Stable insertion sort of positions [p, p + len) of idx by key (one thread).
+__device__ __forceinline__ void insertion_sort_run(uint16_t* idx, uint32_t p, uint32_t len, const uint32_t* keys,
+                                                   uint32_t cap, uint32_t K) {
+    for (uint32_t j = p + 1; j < p + len; ++j) {
+        const uint16_t v = idx[j];
+        uint32_t k = j;
+        while (k > p && key_less(keys, cap, K, v, idx[k - 1])) {
+            idx[k] = idx[k - 1];
+            --k;
+        }
+        idx[k] = v;
+    }
+}
+
+// Does any bit of [lo, lo + len) vary (mask over K words, bit 0 = word 0 bit 0)?
+__device__ __forceinline__ bool bits_vary(const uint32_t* vary, uint32_t lo, uint32_t len, uint32_t K) {
+    for (uint32_t w = lo >> 5; w < K && 32 * w < lo + len; ++w) {
+        const uint32_t a = lo > 32 * w ? lo - 32 * w : 0u;
+        const uint32_t e = lo + len - 32 * w;  // > a
+        const uint32_t hi_mask = e >= 32 ? 0xFFFFFFFFu : ((1u << e) - 1u);
+        if (vary[w] & hi_mask & (0xFFFFFFFFu << a)) return true;
+    }
+    return false;
+}
+
+// The sort window of a run: the 32 bits [base, base + 32) of the key that end
+// at the run's top varying bit (all keys of the run agree above it).
+struct Window {
+    const uint32_t* lo;
+    const uint32_t* hi;
+    uint32_t sh, base;
+    __device__ Window(const uint32_t* keys, uint32_t cap, uint32_t K, uint32_t top) {
+        base = top >= 31 ? top - 31 : 0u;
+        const uint32_t wl = base >> 5;
+        sh = base & 31;
+        lo = keys + (size_t)wl * cap;
+        hi = keys + (size_t)(sh && wl + 1 < K ? wl + 1 : wl) * cap;
+    }
+    __device__ __forceinline__ uint32_t operator()(uint32_t i) const {
+        return sh ? __funnelshift_r(lo[i], hi[i], sh) : lo[i];
+    }
+};
+
+__device__ __forceinline__ int top_bit(const uint32_t* vary, uint32_t K) {
+    for (int w = (int)K - 1; w >= 0; --w)
+        if (vary[w]) return 32 * w + 31 - __clz(vary[w]);
+    return -1;
+}
+
+// After a run is sorted by its window: items with equal windows (a sub-run)
+// still differ below it.  The first position of every sub-run finds the
+// sub-run's end by binary search (windows ascend), sorts a short one at once
+// and appends a long one to `list`.  Positions p0 + first, + step, ...
+__device__ __forceinline__ void settle_sub_runs(uint16_t* idx, uint32_t p0, uint32_t pe, uint32_t first,
+                                                uint32_t step, const Window& win, const uint32_t* keys, uint32_t cap,
+                                                uint32_t K, uint32_t* list, uint32_t* count, uint32_t* overflow) {
+    for (uint32_t p = p0 + first; p < pe; p += step) {
+        const uint32_t wv = win(idx[p]);
+        // (a sub-run's items all carry its window, so insertion sorts running
+        // meanwhile in other threads do not change what is read here)
+        if (p > p0 && win(idx[p - 1]) == wv) continue;      // not the first of its sub-run
+        if (p + 1 >= pe || win(idx[p + 1]) != wv) continue;  // a single item
+        uint32_t lo = p + 2, hi = pe;
+        while (lo < hi) {
+            const uint32_t mid = (lo + hi) >> 1;
+            if (win(idx[mid]) == wv) lo = mid + 1;
+            else hi = mid;
+        }
+        const uint32_t len = lo - p;
+        if (len <= kShortRun) {
+            insertion_sort_run(idx, p, len, keys, cap, K);
+        } else {
+            const uint32_t slot = atomicAdd(count, 1u);
+            if (slot < (uint32_t)kRunList) list[slot] = (len << 16) | p;
+            else atomicAdd(overflow, 1u);  // cannot happen (disjoint runs); verification then fails
+        }
+    }
+}
+
+// One warp sorts run [p0, p0 + r) by its window: LSD passes over the varying
+// window digits, ranks by ballots against the warp's own 256 counters (which
+// accumulate over the run's chunks, so a rank is the item's place among all
+// earlier items of its digit), then its sub-runs are settled.
+__device__ __forceinline__ void warp_sort_run(uint32_t p0, uint32_t r, const uint32_t* keys, uint32_t cap,
+                                              uint32_t K, uint16_t* idx, uint16_t* alt, uint16_t* rnk, uint8_t* dig,
+                                              uint16_t* wh, uint32_t* vary, uint32_t* list, uint32_t* count,
+                                              uint32_t* overflow) {
+    const uint32_t lane = threadIdx.x & 31, lt = (1u << lane) - 1u, pe = p0 + r;
+    const uint32_t first = idx[p0];
+    for (uint32_t w = 0; w < K; ++w) {
+        const uint32_t* kw = keys + (size_t)w * cap;
+        const uint32_t f = kw[first];
+        uint32_t diff = 0;
+        for (uint32_t p = p0 + lane; p < pe; p += 32) diff |= kw[idx[p]] ^ f;
+        diff = __reduce_or_sync(kFull, diff);
+        if (lane == 0) vary[w] = diff;
+    }
+    __syncwarp();
+    const int top = top_bit(vary, K);
+    if (top < 0) return;  // equal keys: already in order
+    const Window win(keys, cap, K, (uint32_t)top);
+    uint16_t* cur = idx;
+    uint16_t* nxt = alt;
+    for (uint32_t q = 0; q < 4; ++q) {
+        if (!bits_vary(vary, win.base + 8 * q, 8, K)) continue;
+        for (uint32_t i = lane; i < 256; i += 32) wh[i] = 0;
+        __syncwarp();
+        for (uint32_t c0 = p0; c0 < pe; c0 += 32) {
+            const uint32_t p = c0 + lane;
+            const bool valid = p < pe;
+            const uint32_t d = valid ? (win(cur[p]) >> (8 * q)) & 0xFFu : 0u;
+            uint32_t peers = __ballot_sync(kFull, valid);
+#pragma unroll
+            for (int bit = 0; bit < 8; ++bit) {
+                const bool x = (d >> bit) & 1u;
+                const uint32_t bal = __ballot_sync(kFull, x);
+                peers &= x ? bal : ~bal;
+            }
+            const uint32_t cnt = valid ? wh[d] : 0u;
+            __syncwarp();
+            if (valid && (peers & lt) == 0) wh[d] = (uint16_t)(cnt + __popc(peers));
+            __syncwarp();
+            if (valid) {
+                rnk[p] = (uint16_t)(cnt + __popc(peers & lt));
+                dig[p] = (uint8_t)d;
+            }
+        }
+        __syncwarp();
+        uint32_t v[8], sum = 0;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            v[i] = wh[lane * 8 + i];
+            sum += v[i];
+        }
+        uint32_t inc = sum;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t t = __shfl_up_sync(kFull, inc, o);
+            if (lane >= (uint32_t)o) inc += t;
+        }
+        uint32_t ex = inc - sum;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            wh[lane * 8 + i] = (uint16_t)ex;
+            ex += v[i];
+        }
+        __syncwarp();
+        for (uint32_t p = p0 + lane; p < pe; p += 32) nxt[p0 + wh[dig[p]] + rnk[p]] = cur[p];
+        __syncwarp();
+        uint16_t* t = cur;
+        cur = nxt;
+        nxt = t;
+    }
+    if (cur != idx) {
+        for (uint32_t p = p0 + lane; p < pe; p += 32) idx[p] = cur[p];
+        __syncwarp();
+    }
+    if (win.base > 0 && bits_vary(vary, 0, win.base, K))
+        settle_sub_runs(idx, p0, pe, lane, 32, win, keys, cap, K, list, count, overflow);
+    __syncwarp();
+}
 
 // Persistent blocks take buckets from a queue.  A bucket of m <= cap pairs is
-// loaded into shared memory and sorted by an LSD radix sort with 8-bit digits
-// over only the digits that vary inside the bucket (all others are equal
-// there); each pass ranks the items stably by warp ballots, in the current
-// order, and permutes a 16-bit index.  The keys then leave in sorted order and
-// the row ids are gathered through the permutation.  Constant buckets are left
-// as partitioned (already stable); other oversize buckets are queued for the
-// plain radix sort.
-__global__ void __launch_bounds__(kLocalThreads) local_sort_kernel(const LocalArgs a) {
+// loaded into shared memory and sorted by the 32-bit window that ends at its
+// top varying bit (all its keys agree above it; the window separates almost
+// all keys of a bucket, whose keys span a narrow key range): the whole block
+// runs an LSD radix sort over the window's varying 8-bit digits, ranking a
+// 16-bit index by warp ballots.  Items left with equal windows form sub-runs
+// that differ only below the window: up to kShortRun items are sorted at once
+// by a stable insertion sort of one thread; longer ones are sorted in rounds,
+// one warp per sub-run, by their own windows, until none is left.  A run of
+// equal keys is already in order (the partition is stable).  The keys then
+// leave in sorted order and the row ids are gathered through the index.
+// Constant buckets larger than cap are left as partitioned; other oversize
+// buckets are listed for the plain radix sort.
+__global__ void __launch_bounds__(kLocalThreads, 1) local_sort_kernel(const LocalArgs a) {
     extern __shared__ __align__(16) uint32_t lsm[];
     const uint32_t K = a.K, cap = a.cap;
-    uint32_t* keys = lsm;                                              // [K][cap]
-    uint16_t* idx_a = reinterpret_cast<uint16_t*>(keys + (size_t)K * cap);  // [cap]
-    uint16_t* idx_b = idx_a + cap;                                     // [cap]
-    uint16_t* rnk = idx_b + cap;                                       // [cap] rank within the warp
-    uint8_t* dig = reinterpret_cast<uint8_t*>(rnk + cap);              // [cap]
+    uint32_t* keys = lsm;                                                 // [K][cap]
+    uint16_t* idx = reinterpret_cast<uint16_t*>(keys + (size_t)K * cap);  // [cap] current order
+    uint16_t* alt = idx + cap;                                            // [cap]
+    uint16_t* rnk = alt + cap;                                            // [cap] rank within the warp
+    uint8_t* dig = reinterpret_cast<uint8_t*>(rnk + cap);                 // [cap]
     __shared__ uint16_t whist[kLocalWarps][256];
     __shared__ uint32_t dtot[256];
     __shared__ uint32_t vary[kMaxLearnedWords];
-    __shared__ uint32_t s_bucket;
+    __shared__ uint32_t wvary[kLocalWarps][kMaxLearnedWords];
+    __shared__ uint32_t lists[2][kRunList];
+    __shared__ uint32_t s_bucket, s_count[2], s_grab;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const uint32_t lt = (1u << lane) - 1u;
     for (;;) {
         if (tid == 0) s_bucket = atomicAdd(a.next, 1u);
         if (tid < kMaxLearnedWords) vary[tid] = 0;
+        if (tid < 2) s_count[tid] = 0;
         __syncthreads();
         const uint32_t b = s_bucket;
         if (b >= a.B) break;
@@ -607,7 +904,7 @@ __global__ void __launch_bounds__(kLocalThreads) local_sort_kernel(const LocalAr
         }
         if (m > cap) {
             if (tid == 0) {
-                if (constant_bucket(a.spl, K, a.B, b)) {
+                if (constant_bucket(a.spl, K, *a.nsplit + 1, b)) {
                     atomicAdd(&a.counts[1], 1u);
                 } else {
                     const uint32_t slot = atomicAdd(&a.flags[0], 1u);
@@ -622,102 +919,138 @@ __global__ void __launch_bounds__(kLocalThreads) local_sort_kernel(const LocalAr
         }
         // load, and find the bits that vary inside the bucket
         for (uint32_t w = 0; w < K; ++w) {
-            const uint32_t first = a.ck[(uint64_t)w * a.ld + s];
+            const uint32_t f = a.ck[(uint64_t)w * a.ld + s];
             uint32_t diff = 0;
             for (uint32_t t = tid; t < m; t += kLocalThreads) {
                 const uint32_t v = a.ck[(uint64_t)w * a.ld + s + t];
                 keys[(size_t)w * cap + t] = v;
-                diff |= v ^ first;
+                diff |= v ^ f;
             }
             diff = __reduce_or_sync(kFull, diff);
             if (lane == 0 && diff) atomicOr(&vary[w], diff);
         }
-        for (uint32_t t = tid; t < m; t += kLocalThreads) idx_a[t] = (uint16_t)t;
+        for (uint32_t t = tid; t < m; t += kLocalThreads) idx[t] = (uint16_t)t;
         __syncthreads();
-        // warp w ranks positions [w * per, (w + 1) * per), per a multiple of 32
-        const uint32_t per = ((m + kLocalWarps * 32 - 1) / (kLocalWarps * 32)) * 32;
-        const uint32_t pbeg = warp * per, pend = min(m, pbeg + per);
-        const uint32_t digits = (a.nbits + 7) / 8;
-        for (uint32_t q = 0; q < digits; ++q) {
-            const uint32_t shift = 8 * q, w = shift >> 5, sh = shift & 31;
-            if (((vary[w] >> sh) & 0xFFu) == 0) continue;  // digit constant in this bucket
-            for (int d = tid; d < kLocalWarps * 256; d += kLocalThreads) (&whist[0][0])[d] = 0;
-            __syncthreads();
-            const uint32_t* kw = keys + (size_t)w * cap;
-            for (uint32_t p0 = pbeg; p0 < pend; p0 += 32) {  // warp-uniform trip count
-                const uint32_t p = p0 + lane;
-                const bool valid = p < pend;
-                const uint32_t d = valid ? (kw[idx_a[p]] >> sh) & 0xFFu : 0u;
-                uint32_t peers = __ballot_sync(kFull, valid);
+        const int top = top_bit(vary, K);
+        if (top >= 0 && m <= kShortRun) {
+            if (tid == 0) insertion_sort_run(idx, 0, m, keys, cap, K);
+        } else if (top >= 0) {
+            // the whole bucket by its window, all warps
+            const Window win(keys, cap, K, (uint32_t)top);
+            uint16_t* cur = idx;
+            uint16_t* nxt = alt;
+            const uint32_t per = ((m + kLocalWarps * 32 - 1) / (kLocalWarps * 32)) * 32;
+            const uint32_t pbeg = warp * per, pend = min(m, pbeg + per);
+            for (uint32_t q = 0; q < 4; ++q) {
+                if (!bits_vary(vary, win.base + 8 * q, 8, K)) continue;
+                for (int d = tid; d < kLocalWarps * 256; d += kLocalThreads) (&whist[0][0])[d] = 0;
+                __syncthreads();
+                for (uint32_t c0 = pbeg; c0 < pend; c0 += 32) {  // warp-uniform trip count
+                    const uint32_t p = c0 + lane;
+                    const bool valid = p < pend;
+                    const uint32_t d = valid ? (win(cur[p]) >> (8 * q)) & 0xFFu : 0u;
+                    uint32_t peers = __ballot_sync(kFull, valid);
 #pragma unroll
-                for (int bit = 0; bit < 8; ++bit) {
-                    const bool x = (d >> bit) & 1u;
-                    const uint32_t bal = __ballot_sync(kFull, x);
-                    peers &= x ? bal : ~bal;
+                    for (int bit = 0; bit < 8; ++bit) {
+                        const bool x = (d >> bit) & 1u;
+                        const uint32_t bal = __ballot_sync(kFull, x);
+                        peers &= x ? bal : ~bal;
+                    }
+                    const uint32_t cnt = valid ? whist[warp][d] : 0u;
+                    __syncwarp();
+                    if (valid && (peers & lt) == 0) whist[warp][d] = (uint16_t)(cnt + __popc(peers));
+                    __syncwarp();
+                    if (valid) {
+                        rnk[p] = (uint16_t)(cnt + __popc(peers & lt));
+                        dig[p] = (uint8_t)d;
+                    }
                 }
-                const uint32_t base = valid ? whist[warp][d] : 0u;
-                __syncwarp();
-                if (valid && (peers & lt) == 0) whist[warp][d] = (uint16_t)(base + __popc(peers));
-                __syncwarp();
-                if (valid) {
-                    rnk[p] = (uint16_t)(base + __popc(peers & lt));
-                    dig[p] = (uint8_t)d;
+                __syncthreads();
+                // per digit: totals over warps, then exclusive offsets digit-major, warp-minor
+                if (tid < 256) {
+                    uint32_t sum = 0;
+                    for (int ww = 0; ww < kLocalWarps; ++ww) sum += whist[ww][tid];
+                    dtot[tid] = sum;
                 }
-            }
-            __syncthreads();
-            // per digit: totals over warps, then exclusive offsets digit-major, warp-minor
-            if (tid < 256) {
-                uint32_t sum = 0;
-                for (int ww = 0; ww < kLocalWarps; ++ww) sum += whist[ww][tid];
-                dtot[tid] = sum;
-            }
-            __syncthreads();
-            if (tid < 32) {  // exclusive scan of 256 totals by one warp, 8 per lane
-                uint32_t v[8], run = 0;
+                __syncthreads();
+                if (tid < 32) {  // exclusive scan of 256 totals by one warp, 8 per lane
+                    uint32_t v[8], run_sum = 0;
 #pragma unroll
-                for (int i = 0; i < 8; ++i) {
-                    v[i] = dtot[lane * 8 + i];
-                    run += v[i];
-                }
-                uint32_t inc = run;
+                    for (int i = 0; i < 8; ++i) {
+                        v[i] = dtot[lane * 8 + i];
+                        run_sum += v[i];
+                    }
+                    uint32_t inc = run_sum;
 #pragma unroll
-                for (int o = 1; o < 32; o <<= 1) {
-                    const uint32_t t = __shfl_up_sync(kFull, inc, o);
-                    if (lane >= o) inc += t;
-                }
-                uint32_t ex = inc - run;
+                    for (int o = 1; o < 32; o <<= 1) {
+                        const uint32_t t = __shfl_up_sync(kFull, inc, o);
+                        if (lane >= o) inc += t;
+                    }
+                    uint32_t ex = inc - run_sum;
 #pragma unroll
-                for (int i = 0; i < 8; ++i) {
-                    dtot[lane * 8 + i] = ex;
-                    ex += v[i];
+                    for (int i = 0; i < 8; ++i) {
+                        dtot[lane * 8 + i] = ex;
+                        ex += v[i];
+                    }
                 }
-            }
-            __syncthreads();
-            if (tid < 256) {
-                uint32_t off = dtot[tid];
-                for (int ww = 0; ww < kLocalWarps; ++ww) {
-                    const uint32_t c = whist[ww][tid];
-                    whist[ww][tid] = (uint16_t)off;
-                    off += c;
+                __syncthreads();
+                if (tid < 256) {
+                    uint32_t off = dtot[tid];
+                    for (int ww = 0; ww < kLocalWarps; ++ww) {
+                        const uint32_t c = whist[ww][tid];
+                        whist[ww][tid] = (uint16_t)off;
+                        off += c;
+                    }
                 }
+                __syncthreads();
+                for (uint32_t p = pbeg + lane; p < pend; p += 32) nxt[whist[warp][dig[p]] + rnk[p]] = cur[p];
+                __syncthreads();
+                uint16_t* t = cur;
+                cur = nxt;
+                nxt = t;
             }
+            if (cur != idx) {
+                for (uint32_t t = tid; t < m; t += kLocalThreads) idx[t] = cur[t];
+                __syncthreads();
+            }
+            if (win.base > 0 && bits_vary(vary, 0, win.base, K))
+                settle_sub_runs(idx, 0, m, tid, kLocalThreads, win, keys, cap, K, lists[0], &s_count[0], &a.flags[1]);
             __syncthreads();
-            for (uint32_t p = pbeg + lane; p < pend; p += 32) idx_b[whist[warp][dig[p]] + rnk[p]] = idx_a[p];
-            __syncthreads();
-            uint16_t* t = idx_a;
-            idx_a = idx_b;
-            idx_b = t;
+            // rounds: one warp per long sub-run, appending the next round's runs
+            uint32_t cur_list = 0;
+            for (;;) {
+                const uint32_t nruns = min(s_count[cur_list], (uint32_t)kRunList);
+                if (nruns == 0) break;
+                if (tid == 0) {
+                    s_count[cur_list ^ 1] = 0;
+                    s_grab = 0;
+                }
+                __syncthreads();
+                for (;;) {
+                    uint32_t e = 0;
+                    if (lane == 0) e = atomicAdd(&s_grab, 1u);
+                    e = __shfl_sync(kFull, e, 0);
+                    if (e >= nruns) break;
+                    const uint32_t run = lists[cur_list][e];
+                    warp_sort_run(run & 0xFFFFu, run >> 16, keys, cap, K, idx, alt, rnk, dig, whist[warp],
+                                  wvary[warp], lists[cur_list ^ 1], &s_count[cur_list ^ 1], &a.flags[1]);
+                }
+                __syncthreads();
+                if (tid == 0) s_count[cur_list] = 0;
+                cur_list ^= 1;
+            }
         }
+        __syncthreads();
         // write the bucket back in sorted order; row ids through the permutation
         for (uint32_t t = tid; t < m; t += kLocalThreads) {
-            const uint32_t src = idx_a[t];
+            const uint32_t src = idx[t];
             for (uint32_t w = 0; w < K; ++w) a.ck[(uint64_t)w * a.ld + s + t] = keys[(size_t)w * cap + src];
         }
         __syncthreads();
         uint32_t* rtmp = keys;  // the keys are written out; their space holds the row ids
         for (uint32_t t = tid; t < m; t += kLocalThreads) rtmp[t] = a.rid[s + t];
         __syncthreads();
-        for (uint32_t t = tid; t < m; t += kLocalThreads) a.rid[s + t] = rtmp[idx_a[t]];
+        for (uint32_t t = tid; t < m; t += kLocalThreads) a.rid[s + t] = rtmp[idx[t]];
         if (tid == 0) atomicAdd(&a.counts[0], 1u);
         __syncthreads();
     }
@@ -788,13 +1121,13 @@ __global__ void separators_kernel(const float* __restrict__ params, const __grid
 
 // ------------------------------------------------------------ workspace
 struct LearnedPlan {
-    uint32_t B, bucket_bits, passes, K, nbits;
+    uint32_t B, bucket_bits, max_buckets, id_bits, passes, K, nbits;
     uint64_t S, ld_s, n, ld, div, chunk;
     uint32_t cap, epochs, train_blocks, flags, max_over;
     float lr;
     SortPlan sample_sort, plain;
     size_t off_sample, off_sample_sorted, off_sample_rid, off_sample_ws, off_xs, off_params, off_partial,
-        off_misc, off_start, off_over, off_spl, off_spl_final, off_bkt, off_alt_bkt, off_alt_ck, off_alt_rid, off_hist,
+        off_misc, off_start, off_over, off_codes, off_spl, off_bkt, off_alt_bkt, off_alt_ck, off_alt_rid, off_hist,
         off_lookback, off_plain_ws, total;
 };
 
@@ -815,7 +1148,10 @@ static bool make_learned_plan(uint64_t n, uint32_t K, uint32_t nbits, const ck_l
     p->bucket_bits = o && o->bucket_bits ? o->bucket_bits : auto_bits;
     if (p->bucket_bits < 8 || p->bucket_bits > 16) return false;
     p->B = 1u << p->bucket_bits;
-    p->passes = p->bucket_bits > 8 ? 2 : 1;
+    // heavy values add up to one bucket each; the bucket ids stay below 2^16
+    p->max_buckets = p->bucket_bits <= 15 ? min(2 * p->B, p->B + 8192u) : p->B;
+    p->id_bits = p->max_buckets > p->B ? p->bucket_bits + 1 : p->bucket_bits;
+    p->passes = p->id_bits > 8 ? 2 : 1;
     p->div = o && o->sample_div ? o->sample_div : 100;
     p->epochs = o && o->epochs ? o->epochs : 100;
     p->lr = o && o->lr > 0.0f ? o->lr : 1e-3f;
@@ -847,10 +1183,10 @@ static bool make_learned_plan(uint64_t n, uint32_t K, uint32_t nbits, const ck_l
     p->off_partial = take(4ull * 2 * p->train_blocks * kRed);
     p->off_misc = take(256);  // barrier, loss, flags[2], counts[3], queue, steps[2] (u64)
     p->max_over = 4096;
-    p->off_start = take(4ull * (p->B + 1));
+    p->off_start = take(4ull * (p->max_buckets + 1));
     p->off_over = take(4ull * 2 * p->max_over);
-    p->off_spl = take(4ull * K * p->B);
-    p->off_spl_final = take(4ull * K * p->B);
+    p->off_codes = take(p->B);
+    p->off_spl = take(4ull * K * p->max_buckets);
     p->off_bkt = take(4ull * n);
     p->off_alt_bkt = take(4ull * n);
     p->off_alt_ck = take(4ull * K * p->ld);
@@ -873,6 +1209,7 @@ struct Misc {  // layout of the misc block of the learned workspace
     uint32_t flags[2];   // oversize buckets, order violations
     uint32_t counts[3];  // buckets sorted, constant buckets, max bucket
     uint32_t next;       // bucket queue of the local sorts
+    uint32_t nsplit;     // number of splitters
     unsigned long long steps[2];
 };
 }  // namespace
@@ -963,10 +1300,13 @@ ck_status ck_sort_learned(const uint32_t* ck_in, uint32_t* ck_out, uint32_t* rid
         count_launch();
     }
     // 3. splitters: sample quantiles (they cut through long shared prefixes that
-    //    a 24-bit feature cannot see), heavy-key singletons
-    splitter_kernel<<<(P.B + 255) / 256, 256, 0, s>>>(at(P.off_sample_sorted), P.ld_s, P.S, K, P.B, nullptr,
-                                                      at(P.off_spl));
-    singleton_kernel<<<(P.B + 255) / 256, 256, 0, s>>>(at(P.off_spl), K, P.B, nbits, at(P.off_spl_final));
+    //    a 24-bit feature cannot see) moved to run ends, heavy values isolated
+    const uint64_t heavy = std::max<uint64_t>(2, (P.S + 2ull * P.B - 1) / (2ull * P.B));
+    uint8_t* codes = reinterpret_cast<uint8_t*>(ws + P.off_codes);
+    quantile_kernel<<<(P.B + 255) / 256, 256, 0, s>>>(at(P.off_sample_sorted), P.ld_s, P.S, K, P.B, nbits, heavy,
+                                                      codes);
+    emit_splitters_kernel<<<1, 1024, 0, s>>>(at(P.off_sample_sorted), P.ld_s, P.S, K, P.B, P.max_buckets, codes,
+                                             at(P.off_spl), &misc->nsplit);
     count_launch(2);
 
     // 4. bucket id of every key (model guess + exact correction), digit histograms
@@ -976,16 +1316,17 @@ ck_status ck_sort_learned(const uint32_t* ck_in, uint32_t* ck_out, uint32_t* rid
     ba.n = n;
     ba.K = K;
     ba.nbits = nbits;
-    ba.B = P.B;
-    ba.bucket_bits = P.bucket_bits;
+    ba.max_buckets = P.max_buckets;
+    ba.nsplit = &misc->nsplit;
     ba.use_model = use_model ? 1u : 0u;
-    ba.spl = at(P.off_spl_final);
+    ba.spl = at(P.off_spl);
     ba.params = use_model ? params : nullptr;
+    ba.loss = &misc->loss;
     ba.bkt = at(P.off_bkt);
     ba.hist = at(P.off_hist);
     ba.steps = misc->steps;
-    const size_t top_bytes = 4ull * (P.B - 1) + 4ull * ((1u << kPrefixBits) + 1);
-    const bool staged = top_bytes <= 160 * 1024;
+    const size_t top_bytes = 4ull * (P.max_buckets - 1) + 4ull * ((1u << kPrefixBits) + 1);
+    const bool staged = top_bytes <= 200 * 1024;
     CK_TRY(launch_bucket(ba, staged, top_bytes, sms, s));
     count_launch();
     CK_TRY(launch_bucket_scan(at(P.off_hist), P.passes, 8, s));
@@ -1022,7 +1363,7 @@ ck_status ck_sort_learned(const uint32_t* ck_in, uint32_t* ck_out, uint32_t* rid
         a.n = n;
         a.narr = m;
         a.sh = 8 * q;
-        a.bits = last ? P.bucket_bits - 8 * q : 8;
+        a.bits = last ? P.id_bits - 8 * q : 8;
         a.straddle = 0;
         a.pass = q;
         a.bulk = bulk;
@@ -1037,21 +1378,22 @@ ck_status ck_sort_learned(const uint32_t* ck_in, uint32_t* ck_out, uint32_t* rid
 
     // 6. bucket starts, then every bucket sorted in shared memory, in place
     uint32_t* start = at(P.off_start);
-    CK_TRY(cudaMemsetAsync(start, 0xFF, 4ull * P.B, s));
-    const uint32_t n32 = (uint32_t)n;
-    CK_TRY(cudaMemcpyAsync(start + P.B, &n32, 4, cudaMemcpyHostToDevice, s));
+    CK_TRY(cudaMemsetAsync(start, 0xFF, 4ull * P.max_buckets, s));
+    static thread_local uint32_t n32;
+    n32 = (uint32_t)n;
+    CK_TRY(cudaMemcpyAsync(start + P.max_buckets, &n32, 4, cudaMemcpyHostToDevice, s));
     bucket_start_kernel<<<sms * 8, 256, 0, s>>>(bkt_final, n, start);
-    suffix_min_kernel<<<1, 1024, 0, s>>>(start, P.B + 1);
+    suffix_min_kernel<<<1, 1024, 0, s>>>(start, P.max_buckets + 1);
     count_launch(2);
     LocalArgs la;
     la.ck = ck_out;
     la.rid = rid_out;
     la.start = start;
-    la.spl = at(P.off_spl_final);
+    la.spl = at(P.off_spl);
+    la.nsplit = &misc->nsplit;
     la.ld = P.ld;
     la.K = K;
-    la.B = P.B;
-    la.nbits = nbits;
+    la.B = P.max_buckets;
     la.cap = P.cap;
     la.next = &misc->next;
     la.flags = misc->flags;
@@ -1096,7 +1438,7 @@ ck_status ck_sort_learned(const uint32_t* ck_in, uint32_t* ck_out, uint32_t* rid
         stats->train_loss = use_model ? host.loss : 0.0f;
         stats->mean_search_steps = (float)((double)host.steps[0] / (double)n);
         stats->max_search_steps = (uint32_t)host.steps[1];
-        stats->buckets = P.B;
+        stats->buckets = host.nsplit + 1;
         stats->sample_size = (uint32_t)P.S;
         stats->max_bucket = host.counts[2];
         stats->sorted_segments = host.counts[0];
