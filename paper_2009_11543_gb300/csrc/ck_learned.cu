@@ -622,36 +622,32 @@ static cudaError_t launch_bucket(const BucketArgs& ba, bool staged, size_t smem,
 }
 
 // ------------------------------------------------------------ bucket sorts
-// start[b] = first position of bucket b after the partition (bucket ids are
-// non-decreasing): written by the first position of every non-empty bucket,
-// then empty buckets take the start of the next non-empty one (suffix minimum,
-// start[B] = n).
-__global__ void bucket_start_kernel(const uint32_t* __restrict__ bkt, uint64_t n, uint32_t* __restrict__ start) {
-    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x)
-        if (i == 0 || bkt[i] != bkt[i - 1]) start[bkt[i]] = (uint32_t)i;
-}
-
-__global__ void suffix_min_kernel(uint32_t* v, uint32_t count) {  // one block; v[count - 1] is the sentinel
-    __shared__ uint32_t part[1024];
-    const uint32_t per = (count + blockDim.x - 1) / blockDim.x;
-    const uint32_t lo = threadIdx.x * per, hi = min(count, lo + per);
-    uint32_t m = 0xFFFFFFFFu;
-    for (uint32_t c = hi; c-- > lo;) m = min(m, v[c]);
-    part[threadIdx.x] = m;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        uint32_t r = 0xFFFFFFFFu;
-        for (int t = blockDim.x - 1; t >= 0; --t) {
-            const uint32_t x = part[t];
-            part[t] = r;
-            r = min(r, x);
+// start[b] = first position of bucket b in the partitioned keys: the first
+// position whose key is >= spl[b - 1].  The partition is by key range, so
+// that predicate is monotone in the position and a binary search finds it.
+// start[0] = 0; buckets past the last splitter are empty (start = n).
+__global__ void bucket_bounds_kernel(const uint32_t* __restrict__ ck, uint64_t ld, uint64_t n, uint32_t K,
+                                     const uint32_t* __restrict__ spl, const uint32_t* nsplit, uint32_t max_buckets,
+                                     uint32_t* __restrict__ start) {
+    const uint32_t ns = min(*nsplit, max_buckets - 1);
+    for (uint32_t b = blockIdx.x * blockDim.x + threadIdx.x; b <= max_buckets; b += gridDim.x * blockDim.x) {
+        uint64_t pos = b == 0 ? 0 : n;
+        if (b >= 1 && b <= ns) {
+            const uint32_t* v = spl + (uint64_t)(b - 1) * K;
+            uint64_t lo = 0, hi = n;
+            while (lo < hi) {
+                const uint64_t mid = (lo + hi) >> 1;
+                int c = 0;
+                for (int w = (int)K - 1; w >= 0 && c == 0; --w) {
+                    const uint32_t x = ck[(uint64_t)w * ld + mid];
+                    c = x < v[w] ? -1 : (x > v[w] ? 1 : 0);
+                }
+                if (c < 0) lo = mid + 1;
+                else hi = mid;
+            }
+            pos = lo;
         }
-    }
-    __syncthreads();
-    uint32_t r = part[threadIdx.x];
-    for (uint32_t c = hi; c-- > lo;) {
-        r = min(r, v[c]);
-        v[c] = r;
+        start[b] = (uint32_t)pos;
     }
 }
 
@@ -687,7 +683,9 @@ struct LocalArgs {
 constexpr int kLocalThreads = 1024;
 constexpr int kLocalWarps = kLocalThreads / 32;
 constexpr uint32_t kShortRun = 16;  // runs of equal windows up to this length: insertion sort by one thread
-constexpr int kRunList = 1024;      // longer runs of one round (disjoint, so at most cap / 17)
+constexpr uint32_t kBlockRun = 256; // runs from this length on are sorted by the whole block
+constexpr int kRunList = 1024;      // shorter runs of one warp round (disjoint, so at most cap / 17)
+constexpr int kBlockStack = 64;     // runs waiting for the block (disjoint, so at most cap / kBlockRun)
 
 // Key i < key j (bucket-local indices into the word-major shared key array).
 __device__ __forceinline__ bool key_less(const uint32_t* keys, uint32_t cap, uint32_t K, uint32_t i, uint32_t j) {
@@ -749,11 +747,14 @@ __device__ __forceinline__ int top_bit(const uint32_t* vary, uint32_t K) {
 
 // After a run is sorted by its window: items with equal windows (a sub-run)
 // still differ below it.  The first position of every sub-run finds the
-// sub-run's end by binary search (windows ascend), sorts a short one at once
-// and appends a long one to `list`.  Positions p0 + first, + step, ...
+// sub-run's end by binary search (windows ascend) and sorts a short one at
+// once; a longer one goes to the warp list, one of kBlockRun or more items
+// to the block's stack (bstack == nullptr: the warp list).  Positions
+// p0 + first, + step, ...
 __device__ __forceinline__ void settle_sub_runs(uint16_t* idx, uint32_t p0, uint32_t pe, uint32_t first,
                                                 uint32_t step, const Window& win, const uint32_t* keys, uint32_t cap,
-                                                uint32_t K, uint32_t* list, uint32_t* count, uint32_t* overflow) {
+                                                uint32_t K, uint32_t* list, uint32_t* count, uint32_t* bstack,
+                                                uint32_t* bcount, uint32_t* overflow) {
     for (uint32_t p = p0 + first; p < pe; p += step) {
         const uint32_t wv = win(idx[p]);
         // (a sub-run's items all carry its window, so insertion sorts running
@@ -769,11 +770,12 @@ __device__ __forceinline__ void settle_sub_runs(uint16_t* idx, uint32_t p0, uint
         const uint32_t len = lo - p;
         if (len <= kShortRun) {
             insertion_sort_run(idx, p, len, keys, cap, K);
-        } else {
-            const uint32_t slot = atomicAdd(count, 1u);
-            if (slot < (uint32_t)kRunList) list[slot] = (len << 16) | p;
-            else atomicAdd(overflow, 1u);  // cannot happen (disjoint runs); verification then fails
+            continue;
         }
+        const bool big = bstack && len >= kBlockRun;
+        const uint32_t slot = atomicAdd(big ? bcount : count, 1u);
+        if (slot < (big ? (uint32_t)kBlockStack : (uint32_t)kRunList)) (big ? bstack : list)[slot] = (len << 16) | p;
+        else atomicAdd(overflow, 1u);  // cannot happen (disjoint runs); verification then fails
     }
 }
 
@@ -856,8 +858,128 @@ __device__ __forceinline__ void warp_sort_run(uint32_t p0, uint32_t r, const uin
         __syncwarp();
     }
     if (win.base > 0 && bits_vary(vary, 0, win.base, K))
-        settle_sub_runs(idx, p0, pe, lane, 32, win, keys, cap, K, list, count, overflow);
+        settle_sub_runs(idx, p0, pe, lane, 32, win, keys, cap, K, list, count, nullptr, nullptr, overflow);
     __syncwarp();
+}
+
+// Shared state of a block sorting one bucket.
+struct LocalShared {
+    uint16_t whist[kLocalWarps][256];
+    uint32_t dtot[256];
+    uint32_t vary[kMaxLearnedWords];
+    uint32_t wvary[kLocalWarps][kMaxLearnedWords];
+    uint32_t lists[2][kRunList];
+    uint32_t bstack[kBlockStack];
+    uint32_t bucket, count[2], bcount, grab, run;
+};
+
+// The whole block sorts run [p0, p0 + r) of idx by its window: LSD passes
+// over the varying window digits, each ranking the items of every warp's
+// share (consecutive chunks of 32) by ballots against the warp's counters,
+// then exclusive offsets digit-major, warp-minor over the warps that hold
+// items, then the scatter.  Then its sub-runs are settled.
+__device__ __forceinline__ void block_sort_run(uint32_t p0, uint32_t r, const uint32_t* keys, uint32_t cap,
+                                               uint32_t K, uint16_t* idx, uint16_t* alt, uint16_t* rnk, uint8_t* dig,
+                                               LocalShared& S, uint32_t* overflow) {
+    const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, lt = (1u << lane) - 1u, pe = p0 + r;
+    if (tid < K) S.vary[tid] = 0;
+    __syncthreads();
+    {
+        const uint32_t first = idx[p0];
+        for (uint32_t w = 0; w < K; ++w) {
+            const uint32_t* kw = keys + (size_t)w * cap;
+            const uint32_t f = kw[first];
+            uint32_t diff = 0;
+            for (uint32_t p = p0 + tid; p < pe; p += kLocalThreads) diff |= kw[idx[p]] ^ f;
+            diff = __reduce_or_sync(kFull, diff);
+            if (lane == 0 && diff) atomicOr(&S.vary[w], diff);
+        }
+    }
+    __syncthreads();
+    const int top = top_bit(S.vary, K);
+    if (top < 0) return;  // equal keys: already in order (uniform: every thread returns)
+    const Window win(keys, cap, K, (uint32_t)top);
+    uint16_t* cur = idx;
+    uint16_t* nxt = alt;
+    const uint32_t per = ((r + kLocalWarps * 32 - 1) / (kLocalWarps * 32)) * 32;
+    const uint32_t nw = (r + per - 1) / per;  // warps that hold items
+    const uint32_t pbeg = p0 + warp * per, pend = min(pe, pbeg + per);
+    for (uint32_t q = 0; q < 4; ++q) {
+        if (!bits_vary(S.vary, win.base + 8 * q, 8, K)) continue;
+        for (uint32_t d = tid; d < nw * 256; d += kLocalThreads) (&S.whist[0][0])[d] = 0;
+        __syncthreads();
+        for (uint32_t c0 = pbeg; c0 < pend; c0 += 32) {  // warp-uniform trip count
+            const uint32_t p = c0 + lane;
+            const bool valid = p < pend;
+            const uint32_t d = valid ? (win(cur[p]) >> (8 * q)) & 0xFFu : 0u;
+            uint32_t peers = __ballot_sync(kFull, valid);
+#pragma unroll
+            for (int bit = 0; bit < 8; ++bit) {
+                const bool x = (d >> bit) & 1u;
+                const uint32_t bal = __ballot_sync(kFull, x);
+                peers &= x ? bal : ~bal;
+            }
+            const uint32_t cnt = valid ? S.whist[warp][d] : 0u;
+            __syncwarp();
+            if (valid && (peers & lt) == 0) S.whist[warp][d] = (uint16_t)(cnt + __popc(peers));
+            __syncwarp();
+            if (valid) {
+                rnk[p] = (uint16_t)(cnt + __popc(peers & lt));
+                dig[p] = (uint8_t)d;
+            }
+        }
+        __syncthreads();
+        // per digit: totals over warps, then exclusive offsets digit-major, warp-minor
+        if (tid < 256) {
+            uint32_t sum = 0;
+            for (uint32_t ww = 0; ww < nw; ++ww) sum += S.whist[ww][tid];
+            S.dtot[tid] = sum;
+        }
+        __syncthreads();
+        if (tid < 32) {  // exclusive scan of 256 totals by one warp, 8 per lane
+            uint32_t v[8], run_sum = 0;
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                v[i] = S.dtot[lane * 8 + i];
+                run_sum += v[i];
+            }
+            uint32_t inc = run_sum;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t t = __shfl_up_sync(kFull, inc, o);
+                if (lane >= (uint32_t)o) inc += t;
+            }
+            uint32_t ex = inc - run_sum;
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                S.dtot[lane * 8 + i] = ex;
+                ex += v[i];
+            }
+        }
+        __syncthreads();
+        if (tid < 256) {
+            uint32_t off = S.dtot[tid];
+            for (uint32_t ww = 0; ww < nw; ++ww) {
+                const uint32_t c = S.whist[ww][tid];
+                S.whist[ww][tid] = (uint16_t)off;
+                off += c;
+            }
+        }
+        __syncthreads();
+        for (uint32_t p = pbeg + lane; p < pend; p += 32) nxt[p0 + S.whist[warp][dig[p]] + rnk[p]] = cur[p];
+        __syncthreads();
+        uint16_t* t = cur;
+        cur = nxt;
+        nxt = t;
+    }
+    if (cur != idx) {
+        for (uint32_t p = p0 + tid; p < pe; p += kLocalThreads) idx[p] = cur[p];
+        __syncthreads();
+    }
+    if (win.base > 0 && bits_vary(S.vary, 0, win.base, K))
+        settle_sub_runs(idx, p0, pe, tid, kLocalThreads, win, keys, cap, K, S.lists[0], &S.count[0], S.bstack,
+                        &S.bcount, overflow);
+    __syncthreads();
 }
 
 // Persistent blocks take buckets from a queue.  A bucket of m <= cap pairs is
@@ -867,7 +989,8 @@ __device__ __forceinline__ void warp_sort_run(uint32_t p0, uint32_t r, const uin
 // runs an LSD radix sort over the window's varying 8-bit digits, ranking a
 // 16-bit index by warp ballots.  Items left with equal windows form sub-runs
 // that differ only below the window: up to kShortRun items are sorted at once
-// by a stable insertion sort of one thread; longer ones are sorted in rounds,
+// by a stable insertion sort of one thread; runs of kBlockRun or more items by
+// the whole block in the same way, one after another; the others in rounds,
 // one warp per sub-run, by their own windows, until none is left.  A run of
 // equal keys is already in order (the partition is stable).  The keys then
 // leave in sorted order and the row ids are gathered through the index.
@@ -881,20 +1004,17 @@ __global__ void __launch_bounds__(kLocalThreads, 1) local_sort_kernel(const Loca
     uint16_t* alt = idx + cap;                                            // [cap]
     uint16_t* rnk = alt + cap;                                            // [cap] rank within the warp
     uint8_t* dig = reinterpret_cast<uint8_t*>(rnk + cap);                 // [cap]
-    __shared__ uint16_t whist[kLocalWarps][256];
-    __shared__ uint32_t dtot[256];
-    __shared__ uint32_t vary[kMaxLearnedWords];
-    __shared__ uint32_t wvary[kLocalWarps][kMaxLearnedWords];
-    __shared__ uint32_t lists[2][kRunList];
-    __shared__ uint32_t s_bucket, s_count[2], s_grab;
+    __shared__ LocalShared S;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const uint32_t lt = (1u << lane) - 1u;
     for (;;) {
-        if (tid == 0) s_bucket = atomicAdd(a.next, 1u);
-        if (tid < kMaxLearnedWords) vary[tid] = 0;
-        if (tid < 2) s_count[tid] = 0;
+        if (tid == 0) {
+            S.bucket = atomicAdd(a.next, 1u);
+            S.count[0] = 0;
+            S.count[1] = 0;
+            S.bcount = 0;
+        }
         __syncthreads();
-        const uint32_t b = s_bucket;
+        const uint32_t b = S.bucket;
         if (b >= a.B) break;
         const uint32_t s = a.start[b], m = a.start[b + 1] - s;
         if (tid == 0 && m > 0) atomicMax(&a.counts[2], m);
@@ -917,126 +1037,48 @@ __global__ void __launch_bounds__(kLocalThreads, 1) local_sort_kernel(const Loca
             __syncthreads();
             continue;
         }
-        // load, and find the bits that vary inside the bucket
-        for (uint32_t w = 0; w < K; ++w) {
-            const uint32_t f = a.ck[(uint64_t)w * a.ld + s];
-            uint32_t diff = 0;
-            for (uint32_t t = tid; t < m; t += kLocalThreads) {
-                const uint32_t v = a.ck[(uint64_t)w * a.ld + s + t];
-                keys[(size_t)w * cap + t] = v;
-                diff |= v ^ f;
-            }
-            diff = __reduce_or_sync(kFull, diff);
-            if (lane == 0 && diff) atomicOr(&vary[w], diff);
-        }
+        for (uint32_t w = 0; w < K; ++w)
+            for (uint32_t t = tid; t < m; t += kLocalThreads)
+                keys[(size_t)w * cap + t] = a.ck[(uint64_t)w * a.ld + s + t];
         for (uint32_t t = tid; t < m; t += kLocalThreads) idx[t] = (uint16_t)t;
         __syncthreads();
-        const int top = top_bit(vary, K);
-        if (top >= 0 && m <= kShortRun) {
+        if (m <= kShortRun) {
             if (tid == 0) insertion_sort_run(idx, 0, m, keys, cap, K);
-        } else if (top >= 0) {
-            // the whole bucket by its window, all warps
-            const Window win(keys, cap, K, (uint32_t)top);
-            uint16_t* cur = idx;
-            uint16_t* nxt = alt;
-            const uint32_t per = ((m + kLocalWarps * 32 - 1) / (kLocalWarps * 32)) * 32;
-            const uint32_t pbeg = warp * per, pend = min(m, pbeg + per);
-            for (uint32_t q = 0; q < 4; ++q) {
-                if (!bits_vary(vary, win.base + 8 * q, 8, K)) continue;
-                for (int d = tid; d < kLocalWarps * 256; d += kLocalThreads) (&whist[0][0])[d] = 0;
-                __syncthreads();
-                for (uint32_t c0 = pbeg; c0 < pend; c0 += 32) {  // warp-uniform trip count
-                    const uint32_t p = c0 + lane;
-                    const bool valid = p < pend;
-                    const uint32_t d = valid ? (win(cur[p]) >> (8 * q)) & 0xFFu : 0u;
-                    uint32_t peers = __ballot_sync(kFull, valid);
-#pragma unroll
-                    for (int bit = 0; bit < 8; ++bit) {
-                        const bool x = (d >> bit) & 1u;
-                        const uint32_t bal = __ballot_sync(kFull, x);
-                        peers &= x ? bal : ~bal;
-                    }
-                    const uint32_t cnt = valid ? whist[warp][d] : 0u;
-                    __syncwarp();
-                    if (valid && (peers & lt) == 0) whist[warp][d] = (uint16_t)(cnt + __popc(peers));
-                    __syncwarp();
-                    if (valid) {
-                        rnk[p] = (uint16_t)(cnt + __popc(peers & lt));
-                        dig[p] = (uint8_t)d;
-                    }
-                }
-                __syncthreads();
-                // per digit: totals over warps, then exclusive offsets digit-major, warp-minor
-                if (tid < 256) {
-                    uint32_t sum = 0;
-                    for (int ww = 0; ww < kLocalWarps; ++ww) sum += whist[ww][tid];
-                    dtot[tid] = sum;
-                }
-                __syncthreads();
-                if (tid < 32) {  // exclusive scan of 256 totals by one warp, 8 per lane
-                    uint32_t v[8], run_sum = 0;
-#pragma unroll
-                    for (int i = 0; i < 8; ++i) {
-                        v[i] = dtot[lane * 8 + i];
-                        run_sum += v[i];
-                    }
-                    uint32_t inc = run_sum;
-#pragma unroll
-                    for (int o = 1; o < 32; o <<= 1) {
-                        const uint32_t t = __shfl_up_sync(kFull, inc, o);
-                        if (lane >= o) inc += t;
-                    }
-                    uint32_t ex = inc - run_sum;
-#pragma unroll
-                    for (int i = 0; i < 8; ++i) {
-                        dtot[lane * 8 + i] = ex;
-                        ex += v[i];
-                    }
-                }
-                __syncthreads();
-                if (tid < 256) {
-                    uint32_t off = dtot[tid];
-                    for (int ww = 0; ww < kLocalWarps; ++ww) {
-                        const uint32_t c = whist[ww][tid];
-                        whist[ww][tid] = (uint16_t)off;
-                        off += c;
-                    }
-                }
-                __syncthreads();
-                for (uint32_t p = pbeg + lane; p < pend; p += 32) nxt[whist[warp][dig[p]] + rnk[p]] = cur[p];
-                __syncthreads();
-                uint16_t* t = cur;
-                cur = nxt;
-                nxt = t;
+        } else {
+            if (tid == 0) {
+                S.bstack[0] = m << 16;  // run = (length << 16) | first position; m <= cap < 2^16
+                S.bcount = 1;
             }
-            if (cur != idx) {
-                for (uint32_t t = tid; t < m; t += kLocalThreads) idx[t] = cur[t];
-                __syncthreads();
-            }
-            if (win.base > 0 && bits_vary(vary, 0, win.base, K))
-                settle_sub_runs(idx, 0, m, tid, kLocalThreads, win, keys, cap, K, lists[0], &s_count[0], &a.flags[1]);
             __syncthreads();
-            // rounds: one warp per long sub-run, appending the next round's runs
+            for (;;) {  // runs for the whole block, one after another
+                if (tid == 0) S.run = S.bcount > 0 ? S.bstack[--S.bcount] : 0xFFFFFFFFu;
+                __syncthreads();
+                const uint32_t run = S.run;
+                if (run == 0xFFFFFFFFu) break;
+                block_sort_run(run & 0xFFFFu, run >> 16, keys, cap, K, idx, alt, rnk, dig, S, &a.flags[1]);
+                __syncthreads();
+            }
+            // rounds: one warp per shorter sub-run, appending the next round's runs
             uint32_t cur_list = 0;
             for (;;) {
-                const uint32_t nruns = min(s_count[cur_list], (uint32_t)kRunList);
+                const uint32_t nruns = min(S.count[cur_list], (uint32_t)kRunList);
                 if (nruns == 0) break;
                 if (tid == 0) {
-                    s_count[cur_list ^ 1] = 0;
-                    s_grab = 0;
+                    S.count[cur_list ^ 1] = 0;
+                    S.grab = 0;
                 }
                 __syncthreads();
                 for (;;) {
                     uint32_t e = 0;
-                    if (lane == 0) e = atomicAdd(&s_grab, 1u);
+                    if (lane == 0) e = atomicAdd(&S.grab, 1u);
                     e = __shfl_sync(kFull, e, 0);
                     if (e >= nruns) break;
-                    const uint32_t run = lists[cur_list][e];
-                    warp_sort_run(run & 0xFFFFu, run >> 16, keys, cap, K, idx, alt, rnk, dig, whist[warp],
-                                  wvary[warp], lists[cur_list ^ 1], &s_count[cur_list ^ 1], &a.flags[1]);
+                    const uint32_t run = S.lists[cur_list][e];
+                    warp_sort_run(run & 0xFFFFu, run >> 16, keys, cap, K, idx, alt, rnk, dig, S.whist[warp],
+                                  S.wvary[warp], S.lists[cur_list ^ 1], &S.count[cur_list ^ 1], &a.flags[1]);
                 }
                 __syncthreads();
-                if (tid == 0) s_count[cur_list] = 0;
+                if (tid == 0) S.count[cur_list] = 0;
                 cur_list ^= 1;
             }
         }
@@ -1256,10 +1298,9 @@ ck_status ck_sort_learned(const uint32_t* ck_in, uint32_t* ck_out, uint32_t* rid
     auto at = [&](size_t off) { return reinterpret_cast<uint32_t*>(ws + off); };
     const uint32_t K = ck_words;
     const bool use_model = !(P.flags & CK_LEARNED_NO_MODEL);
-    cudaError_t e = cudaSuccess;
-#define CK_TRY(x)                                \
-    do {                                         \
-        if ((e = (x)) != cudaSuccess) return CK_ECUDA; \
+#define CK_TRY(x)                                    \
+    do {                                             \
+        if ((x) != cudaSuccess) return CK_ECUDA;     \
     } while (0)
     Misc* misc = reinterpret_cast<Misc*>(ws + P.off_misc);
     CK_TRY(cudaMemsetAsync(misc, 0, sizeof(Misc), s));
@@ -1337,20 +1378,14 @@ ck_status ck_sort_learned(const uint32_t* ck_in, uint32_t* ck_out, uint32_t* rid
     const uint64_t tiles = (n + kPassTile - 1) / kPassTile;
     uint32_t* counters = at(P.off_lookback) + 256ull * tiles * P.passes;
     static thread_local PassArrays arr;
-    // bucket ids ping-pong between two buffers (never read and written in one
-    // pass); the last pass's copy locates the buckets for the local sorts
-    uint32_t* bkt_src = at(P.off_bkt);
-    uint32_t* bkt_final = bkt_src;
     for (uint32_t q = 0; q < P.passes; ++q) {
         const bool last = q + 1 == P.passes;
         uint32_t m = 0;
         const uint32_t* src_ck = q == 0 ? ck_in : at(P.off_alt_ck);
         uint32_t* dst_ck = last ? ck_out : at(P.off_alt_ck);
-        uint32_t* bkt_dst = (q % 2 == 0) ? at(P.off_alt_bkt) : at(P.off_bkt);
-        arr.src[m] = bkt_src;
-        arr.dst[m] = bkt_dst;
-        bkt_src = bkt_dst;
-        bkt_final = bkt_dst;
+        // bucket ids: read by every pass, kept for the next pass only
+        arr.src[m] = q == 0 ? at(P.off_bkt) : at(P.off_alt_bkt);
+        arr.dst[m] = last ? nullptr : at(P.off_alt_bkt);
         ++m;
         for (uint32_t w = 0; w < K; ++w, ++m) {
             arr.src[m] = src_ck + (uint64_t)w * P.ld;
@@ -1376,15 +1411,12 @@ ck_status ck_sort_learned(const uint32_t* ck_in, uint32_t* ck_out, uint32_t* rid
         CK_TRY(launch_onesweep_pass(8, a, arr, (uint32_t)tiles, s));
     }
 
-    // 6. bucket starts, then every bucket sorted in shared memory, in place
+    // 6. bucket starts (binary search of the splitters in the partitioned
+    //    keys), then every bucket sorted in shared memory, in place
     uint32_t* start = at(P.off_start);
-    CK_TRY(cudaMemsetAsync(start, 0xFF, 4ull * P.max_buckets, s));
-    static thread_local uint32_t n32;
-    n32 = (uint32_t)n;
-    CK_TRY(cudaMemcpyAsync(start + P.max_buckets, &n32, 4, cudaMemcpyHostToDevice, s));
-    bucket_start_kernel<<<sms * 8, 256, 0, s>>>(bkt_final, n, start);
-    suffix_min_kernel<<<1, 1024, 0, s>>>(start, P.max_buckets + 1);
-    count_launch(2);
+    bucket_bounds_kernel<<<(P.max_buckets + 256) / 256, 256, 0, s>>>(ck_out, P.ld, n, K, at(P.off_spl),
+                                                                     &misc->nsplit, P.max_buckets, start);
+    count_launch();
     LocalArgs la;
     la.ck = ck_out;
     la.rid = rid_out;
