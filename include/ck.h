@@ -64,6 +64,7 @@ enum { CK_KIND_BYTES = 0, CK_KIND_U32 = 1, CK_KIND_U64 = 2 };
 #define CK_NO_DBIT 0xFFFFu             /* "no distinction bit": first key or equal keys */
 #define CK_MAX_LEVELS 32u
 #define CK_LD(n) ((((uint64_t)(n)) + 63u) & ~(uint64_t)63u) /* leading dimension of ck columns */
+#define CK_SORT_TILE 4096u /* pairs per radix pass tile (one look-back word per tile and digit) */
 
 /* A key column in device memory.  CK_KIND_BYTES: binary-comparable byte
  * strings (fixed-size strings as they are, varchar with its terminating NUL and
@@ -156,8 +157,8 @@ typedef struct ck_sort_opts {
 #define CK_SORT_FLAGS_ALL 1u
 
 /* The first tile of the first pass never publishes its look-back entries, so
- * the second tile's wait runs out: exercises the CK_ETIMEOUT path without any
- * GPU fault. */
+ * the waits of the tiles after it run out: exercises the CK_ETIMEOUT path
+ * without any GPU fault. */
 #define CK_INJECT_STALL_FIRST_TILE 1u
 
 size_t ck_sort_workspace_bytes(uint64_t n, uint32_t ck_words, uint32_t nbits, const ck_sort_opts* opts);
@@ -419,7 +420,7 @@ ck_status ck_autotune_sort(const uint32_t* ck_in, uint32_t* ck_out, uint32_t* ri
  * Device status.  ck_device_status synchronises the device, returns the first
  * device-side error recorded since the last clear (CK_OK if none) and, if
  * detail is not NULL, a call-specific detail word (for CK_ETIMEOUT: the pass
- * in bits 0..15 and the waiting tile in bits 16..47).  The status is one word
+ * in bits 0..15 and, in bits 16..47, the waiting tile whose wait ran out first).  The status is one word
  * per device shared by all streams. */
 ck_status ck_device_status(uint64_t* detail);
 ck_status ck_clear_device_status(void);

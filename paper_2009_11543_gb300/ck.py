@@ -23,6 +23,7 @@ CK_MAX_ROWS = (1 << 30) - 1
 CK_MAX_KEY_BYTES = 512
 CK_NO_DBIT = 0xFFFF
 CK_MAX_LEVELS = 32
+CK_SORT_TILE = 4096
 CK_INJECT_STALL_FIRST_TILE = 1
 CK_SORT_PERM_ONLY = 1
 

@@ -60,26 +60,29 @@ __device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t b
                  : "memory");
 }
 
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+// Tests whether the phase with the given parity has completed; a thread
+// whose phase is not complete is suspended for up to about 1 us (it resumes as soon as the phase
+// completes), so a waiting warp does not compete for issue slots.
+__device__ __forceinline__ bool mbar_try_wait_sleep(uint64_t* bar, uint32_t parity) {
     uint32_t ok;
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
         "selp.u32 %0, 1, 0, p;\n\t}"
         : "=r"(ok)
-        : "r"(smem_addr(bar)), "r"(parity)
+        : "r"(smem_addr(bar)), "r"(parity), "n"(1000)
         : "memory");
     return ok != 0;
 }
 
 // Waits for the phase with the given parity to complete; gives up after
-// `limit` polls and returns false (the caller records the timeout).
+// about limit / 4 suspended tries (each up to 1 us) and returns false (the
+// caller records the timeout).
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint32_t limit) {
-    for (uint32_t i = 0;; ++i) {
-        if (mbar_try_wait(bar, parity)) return true;
-        if (i >= limit) return false;
-        if (i > 8) __nanosleep(32);
-    }
+    const uint32_t tries = limit / 4 + 1;
+    for (uint32_t i = 0; i < tries; ++i)
+        if (mbar_try_wait_sleep(bar, parity)) return true;
+    return false;
 }
 
 // ------------------------------------------------------------- key loading
@@ -195,7 +198,7 @@ cudaError_t launch_btree_keys(const KeyDesc& k, int vec, uint64_t n, const uint3
                               uint64_t* refined, cudaStream_t s);
 bool make_extract_plan(const KeyDesc& k, const uint64_t* dmask, uint32_t ck_words, ExtractPlan* plan);
 
-constexpr int kPassTile = 4096;                   // pairs per onesweep tile
+constexpr int kPassTile = (int)CK_SORT_TILE;      // pairs per onesweep tile
 constexpr int kMaxPassArrays = kMaxKeyWords + 2;  // key words, row ids, one extra
 constexpr uint32_t kLookbackFlagAgg = 1u << 30;
 

@@ -8,17 +8,17 @@
 //   upsweep  one read of the keys -> the digit histogram of every pass
 //   scan     per pass, exclusive scan of the histogram -> digit bucket bases
 //   pass     per digit, one kernel: each block takes the next tile (dynamic
-//            tile id), ranks its digits stably (warp ballots + per-warp
-//            counters), publishes its per-digit counts, obtains the counts of
-//            all earlier tiles by decoupled look-back, and scatters every key
+//            tile id), counts its digits and publishes the counts, ranks the
+//            digits stably (warp ballots + per-warp counters), obtains the
+//            counts of all earlier tiles by decoupled look-back, and scatters every key
 //            word and the row id through shared memory so that each digit run
 //            leaves as contiguous stores.
 //
 // Look-back words pack a 2-bit state (1 = tile aggregate, 2 = inclusive
 // prefix) over a 30-bit count, hence n <= 2^30 - 1.  Every wait on a
-// predecessor is bounded by spin_limit polls; when it runs out the block
-// records CK_ETIMEOUT, assumes zero for the missing count (which keeps every
-// store in bounds), and carries on so that later tiles never wait forever.
+// predecessor is bounded by spin_limit polls; when it runs out the block records CK_ETIMEOUT, assumes
+// zero for the missing counts (which keeps every store in bounds), and
+// carries on so that later tiles never wait forever.
 #include "ck_internal.cuh"
 
 namespace ck {
@@ -29,6 +29,7 @@ constexpr uint32_t kValMask = (1u << 30) - 1;
 constexpr int kPassThreads = 512;
 constexpr int kPassItems = 8;
 constexpr int kTile = kPassThreads * kPassItems;  // pairs per tile
+static_assert(kTile == kPassTile, "tile size of the pass kernel");
 constexpr int kRing = 3;                          // staging buffers per block
 constexpr int kPassBlocksPerSM = 3;
 constexpr int kUpThreads = 256;
@@ -156,6 +157,7 @@ __global__ void __launch_bounds__(kPassThreads, kPassBlocksPerSM)
         fence_mbar_init();
     }
     for (int i = tid; i < WARPS * BINS; i += kPassThreads) (&S.whist[0][0])[i] = 0;
+    for (int i = tid; i < BINS; i += kPassThreads) S.tile_total[i] = 0;
     __syncthreads();
     const uint32_t tile = S.scratch[WARPS + 1];
     const uint64_t tile_base = (uint64_t)tile * kTile;
@@ -213,9 +215,18 @@ __global__ void __launch_bounds__(kPassThreads, kPassBlocksPerSM)
             d &= dmask;
         }
         dr[j] = d;
+        if (e < count) atomicAdd(&S.tile_total[d], 1u);
     }
+    __syncthreads();
 
-    // 2. stable rank within the warp: lanes with equal digits found by RB ballots
+    // 2. the tile's digit counts are published before the ranking, so later
+    //    tiles' look-backs need not wait for it
+    const bool stall = (a.inject & CK_INJECT_STALL_FIRST_TILE) && a.pass == 0 && tile == 0;
+    if (!stall)
+        for (int b = tid; b < BINS; b += kPassThreads)
+            st_relaxed(&a.lookback[(uint64_t)tile * BINS + b], (tile == 0 ? kFlagPrefix : kFlagAgg) | S.tile_total[b]);
+
+    // 3. stable rank within the warp: lanes with equal digits found by RB ballots
     uint16_t* my = S.whist[warp];
     const uint32_t lt = (1u << lane) - 1u;
 #pragma unroll
@@ -237,8 +248,7 @@ __global__ void __launch_bounds__(kPassThreads, kPassBlocksPerSM)
     }
     __syncthreads();
 
-    // 3. per digit: exclusive prefix over warps, tile total, publish the aggregate
-    const bool stall = (a.inject & CK_INJECT_STALL_FIRST_TILE) && a.pass == 0 && tile == 0;
+    // 4. per digit: exclusive prefix over warps
     for (int b = tid; b < BINS; b += kPassThreads) {
         uint32_t sum = 0;
 #pragma unroll
@@ -247,40 +257,56 @@ __global__ void __launch_bounds__(kPassThreads, kPassBlocksPerSM)
             S.whist[w][b] = (uint16_t)sum;
             sum += t;
         }
-        S.tile_total[b] = sum;
         S.tile_excl[b] = sum;
-        if (!stall) st_relaxed(&a.lookback[(uint64_t)tile * BINS + b], (tile == 0 ? kFlagPrefix : kFlagAgg) | sum);
     }
     __syncthreads();
     block_exclusive_scan<kPassThreads>(S.tile_excl, BINS, S.scratch);
 
-    // 4. decoupled look-back: counts of every digit in all earlier tiles
+    // 5. decoupled look-back: counts of every digit in all earlier tiles.  The
+    //    thread of digit b reads the words of the kLookDepth tiles before the
+    //    current position at once (the warp's threads read consecutive digits,
+    //    so every word load is one line per warp), adds them up to the nearest
+    //    tile holding an inclusive prefix, and repeats further back while none
+    //    does; it waits (bounded) at a tile that has published nothing yet.
+    //    Tiles before tile 0 read as prefix 0.
     for (int b = tid; b < BINS; b += kPassThreads) {
+        constexpr int kLookDepth = 8;
         uint32_t excl = 0;
         if (tile > 0) {
-            int64_t p = (int64_t)tile - 1;
+            int64_t next = (int64_t)tile - 1;  // newest tile not yet added
             uint32_t polls = 0;
-            while (p >= 0) {
-                const uint32_t v = ld_relaxed(&a.lookback[(uint64_t)p * BINS + b]);
-                const uint32_t flag = v & ~kValMask;
-                if (flag == 0) {
+            while (next >= 0) {
+                uint32_t v[kLookDepth];
+#pragma unroll
+                for (int j = 0; j < kLookDepth; ++j)
+                    v[j] = next - j >= 0 ? ld_relaxed(&a.lookback[(uint64_t)(next - j) * BINS + b]) : kFlagPrefix;
+                bool done = false;
+#pragma unroll
+                for (int j = 0; j < kLookDepth; ++j) {
+                    const uint32_t flag = v[j] & ~kValMask;
+                    if (flag == 0) break;  // tile next - j has not published: wait for it
+                    excl += v[j] & kValMask;
+                    --next;
+                    if (flag == kFlagPrefix) {
+                        done = true;
+                        break;
+                    }
+                }
+                if (done || next < 0) break;
+                if ((v[0] & ~kValMask) == 0) {  // no progress: the newest word is not published yet
                     if (++polls > a.spin_limit) {
                         report(a.status, CK_ETIMEOUT, (uint64_t)a.pass | ((uint64_t)tile << 16));
                         break;
                     }
                     __nanosleep(64);
-                    continue;
                 }
-                excl += v & kValMask;
-                if (flag == kFlagPrefix) break;
-                --p;
             }
             st_relaxed(&a.lookback[(uint64_t)tile * BINS + b], kFlagPrefix | ((excl + S.tile_total[b]) & kValMask));
         }
         S.dest_base[b] = (int32_t)(a.bucket_base[b] + excl) - (int32_t)S.tile_excl[b];
     }
 
-    // 5. local slot of every item in digit order: record where it comes from
+    // 6. local slot of every item in digit order: record where it comes from
 #pragma unroll
     for (int j = 0; j < ITEMS; ++j) {
         const uint32_t e = warp * WITEMS + 32 * j + lane;
@@ -306,7 +332,7 @@ __global__ void __launch_bounds__(kPassThreads, kPassBlocksPerSM)
     }
     __syncthreads();  // every thread has read the digit words; their slots may be refilled
 
-    // 6. every array in staging order: wait for it, scatter it, refill its ring slot
+    // 7. every array in staging order: wait for it, scatter it, refill its ring slot
     for (uint32_t m = 0; m < M; ++m) {
         const bool digit_array = m == 0 || (straddle && m == 1);
         if (bulk) {

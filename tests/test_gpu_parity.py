@@ -22,7 +22,7 @@ _build.build()
 from paper_2009_11543_gb300 import ck, pipeline  # noqa: E402
 
 DEV = "cuda:0"
-TILE = 4096
+TILE = ck.CK_SORT_TILE
 
 
 # ---------------------------------------------------------------- helpers
@@ -258,8 +258,8 @@ def test_sort_zero_bits_and_all_equal():
 
 def test_sort_timeout_is_reported_and_gpu_stays_usable():
     """Fault injection on the host: the first tile never publishes, so the
-    second tile's bounded wait runs out; the call must report CK_ETIMEOUT and
-    the next sort must be exact."""
+    bounded waits of the tiles after it run out; the call must report
+    CK_ETIMEOUT for pass 0 and a waiting tile, and the next sort must be exact."""
     ck.ck_clear_device_status()
     rng = np.random.default_rng(9)
     n = 3 * TILE
@@ -271,7 +271,7 @@ def test_sort_timeout_is_reported_and_gpu_stays_usable():
     ck.ck_sort(ck_in, None, ck_out, rid_out, n, 1, 24, ws, spin_limit=2000, inject=ck.CK_INJECT_STALL_FIRST_TILE)
     status, detail = ck.ck_device_status()
     assert status == ck.CK_ETIMEOUT
-    assert detail == (1 << 16) | 0                     # pass 0, waiting tile 1
+    assert detail & 0xFFFF == 0 and (detail >> 16) in (1, 2)   # pass 0, a tile waiting on tile 0
     ck.ck_clear_device_status()
     assert ck.ck_device_status()[0] == ck.CK_OK
     check_sort(ckr, nbits=24)

@@ -103,7 +103,7 @@ def test_argument_errors_are_synchronous(ckmod):
 def test_workspace_size_formula(ckmod):
     n, K, nbits = 10**6, 4, 120
     ws = ckmod.ck_sort_workspace_bytes(n, K, nbits, 8)
-    tiles = (n + 4095) // 4096
+    tiles = (n + ckmod.CK_SORT_TILE - 1) // ckmod.CK_SORT_TILE
     passes = 15
     ld = ckmod.CK_LD(n)
     assert ld % 64 == 0 and ld >= n
@@ -143,3 +143,13 @@ def test_perm_only_pass_bytes():
     assert sum(r + w for r, w in arrs) == 108            # vs 16 * 10 = 160 when every word is carried
     assert mt.perm_only_sort_bytes(10, 4, 121, 8) == 4 * 10 * 108
     assert mt.perm_only_pass_arrays(1, 20, 8) == [(2, 2), (2, 2), (2, 1)]
+
+
+def test_header_constants_match_binding(ckmod):
+    """The binding's copies of the header's size constants."""
+    import re
+    with open(os.path.join(ROOT, "include", "ck.h")) as f:
+        hdr = f.read()
+    for name in ("CK_SORT_TILE", "CK_MAX_LEVELS", "CK_MLP_HIDDEN"):
+        m = re.search(r"#define %s (\d+)u?" % name, hdr)
+        assert m and int(m.group(1)) == getattr(ckmod, name), name
