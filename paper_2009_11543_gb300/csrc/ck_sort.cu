@@ -9,7 +9,7 @@
 //   scan     per pass, exclusive scan of the histogram -> digit bucket bases
 //   pass     per digit, one kernel: each block takes the next tile (dynamic
 //            tile id), counts its digits and publishes the counts, ranks the
-//            digits stably (one warp match + per-warp counters), obtains the
+//            digits stably (warp ballots + per-warp counters), obtains the
 //            counts of all earlier tiles by decoupled look-back, and scatters
 //            every key word and the row id through shared memory so that each
 //            digit run leaves as contiguous stores.
@@ -226,14 +226,20 @@ __global__ void __launch_bounds__(kPassThreads, kPassBlocksPerSM)
         for (int b = tid; b < BINS; b += kPassThreads)
             st_relaxed(&a.lookback[(uint64_t)tile * BINS + b], (tile == 0 ? kFlagPrefix : kFlagAgg) | S.tile_total[b]);
 
-    // 3. stable rank within the warp: lanes with equal digits found by one match
+    // 3. stable rank within the warp: lanes with equal digits found by RB ballots
     uint16_t* my = S.whist[warp];
     const uint32_t lt = (1u << lane) - 1u;
 #pragma unroll
     for (int j = 0; j < ITEMS; ++j) {
         const bool valid = warp * WITEMS + 32 * j + lane < count;
         const uint32_t d = dr[j];
-        const uint32_t peers = __match_any_sync(kFull, valid ? d : 0xFFFFu) & __ballot_sync(kFull, valid);
+        uint32_t peers = __ballot_sync(kFull, valid);
+#pragma unroll
+        for (int b = 0; b < RB; ++b) {
+            const bool bit = (d >> b) & 1u;
+            const uint32_t bal = __ballot_sync(kFull, bit);
+            peers &= bit ? bal : ~bal;
+        }
         const uint32_t base = valid ? my[d] : 0u;
         __syncwarp();
         if (valid && (peers & lt) == 0) my[d] = (uint16_t)(base + __popc(peers));
