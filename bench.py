@@ -46,10 +46,12 @@ WORKLOADS = {
     "urls8m": ("8M 32-byte URL keys (the 64M workload's generator, first 8M rows), fanout 64; profiling size",
                8 * 2**20, "urls", 64, 2_000_000, "plain"),
     "zipf256m": ("256M uint64 keys, Zipf(0.9) over 2^40 values under a constant 12-bit tag, learned partition "
-                 "(1% sample, 16-unit CDF model, 65536 buckets) vs plain radix, fanout 64", 256 * 2**20, "zipf", 64,
-                 8_000_000, "learned"),
+                 "(1% sample, 16-unit CDF model, about 32K key-range buckets) vs plain radix, fanout 64",
+                 256 * 2**20, "zipf", 64, 8_000_000, "learned"),
     "dna200m": ("200M 32-byte {A,C,G,T} keys, 20% sharing one of 65536 random 24-char prefixes, learned partition "
                 "+ bulk load with fanout 256", 200_000_000, "dna", 256, 4_000_000, "learned"),
+    "dna20m": ("20M 32-byte {A,C,G,T} keys (the 200M workload's generator, first 20M rows), learned partition, "
+               "fanout 256; profiling size", 20_000_000, "dna", 256, 2_000_000, "learned"),
     "int1m": ("1M uint64 keys with 24 seeded varying bit positions, fanout 64", 1_000_000, "int", 64, 1_000_000,
               "plain"),
     "table16m": ("one table of 16M rows with 6 indexes of key widths 4, 8, 12, 16, 32, 64 bytes (uint32 uniform, "
