@@ -83,6 +83,67 @@ __global__ void __launch_bounds__(256) leaf_kernel(const __grid_constant__ Btree
     }
 }
 
+// The same for keys of KW words: a thread loads its row's words once, takes
+// the previous row's from the neighbouring lane (lane 0 loads them), and
+// finds the D-bit from registers, so a run of equal high words costs no
+// dependent loads.
+template <int KW>
+__global__ void __launch_bounds__(256) leaf_kw_kernel(const __grid_constant__ BtreeArgs a, uint32_t* __restrict__ leaf_rid,
+                                                      uint16_t* __restrict__ leaf_dbit,
+                                                      uint32_t* __restrict__ leaf_high, uint64_t nodes0,
+                                                      uint64_t* __restrict__ refined, unsigned long long* status) {
+    __shared__ uint16_t doff[kMaxKeyBits];
+    __shared__ uint32_t rmask[kMaxKeyWords];
+    build_doffset(a.dmask, a.key_bits, doff);
+    const uint32_t nw32 = (a.key_bits + 31) / 32;
+    for (uint32_t i = threadIdx.x; i < nw32; i += blockDim.x) rmask[i] = 0;
+    __syncthreads();
+    const uint32_t lane = threadIdx.x & 31;
+    const uint64_t n = a.n;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t i0 = (uint64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31u); i0 < n; i0 += stride) {
+        const uint64_t i = i0 + lane;
+        uint32_t w[KW], pw[KW];
+#pragma unroll
+        for (int k = 0; k < KW; ++k) w[k] = i < n ? a.ck[(uint64_t)k * a.ld + i] : 0u;
+#pragma unroll
+        for (int k = 0; k < KW; ++k) {
+            pw[k] = __shfl_up_sync(kFull, w[k], 1);
+            if (lane == 0) pw[k] = i > 0 && i < n ? a.ck[(uint64_t)k * a.ld + i - 1] : 0u;
+        }
+        int32_t p = -1;
+        if (i < n) {
+            leaf_rid[i] = a.rid[i];
+            if (i > 0) {
+                int32_t q = -1;  // compressed D-bit; -2: a bit above nbits differs
+#pragma unroll
+                for (int k = KW - 1; k >= 0; --k) {
+                    const uint32_t x = w[k] ^ pw[k];
+                    if (q == -1 && x) {
+                        const uint32_t v = 32u * k + 31u - __clz(x);
+                        q = v < a.nbits ? (int32_t)(a.nbits - 1 - v) : -2;
+                    }
+                }
+                if (q >= 0) p = doff[q];
+                else if (q == -2) report(status, CK_EINVAL, i);
+            }
+            leaf_dbit[i] = p >= 0 ? (uint16_t)p : (uint16_t)CK_NO_DBIT;
+            if (i < nodes0) leaf_high[i] = (uint32_t)(min((i + 1) * (uint64_t)a.f, n) - 1);
+        }
+        if (refined) {
+            const uint32_t peers = __match_any_sync(kFull, p);
+            if (p >= 0 && (__ffs(peers) - 1) == (int)lane) atomicOr(&rmask[p >> 5], 0x80000000u >> (p & 31));
+        }
+    }
+    if (!refined) return;
+    __syncthreads();
+    for (uint32_t q = threadIdx.x; 2 * q < nw32; q += blockDim.x) {
+        const uint64_t hi = rmask[2 * q], lo = (2 * q + 1 < nw32) ? rmask[2 * q + 1] : 0u;
+        const uint64_t v = (hi << 32) | lo;
+        if (v) atomicOr(reinterpret_cast<unsigned long long*>(refined + q), (unsigned long long)v);
+    }
+}
+
 using InnerShape = InnerLevels;
 
 __global__ void __launch_bounds__(256) inner_kernel(const __grid_constant__ BtreeArgs a,
@@ -125,8 +186,23 @@ cudaError_t launch_btree(const BtreeArgs& a, const ck_btree_shape& shape, ck_btr
     if (a.n == 0) return cudaSuccess;
     const uint64_t cap = (uint64_t)num_sms() * 8;
     uint64_t grid = (a.n + 255) / 256;
-    leaf_kernel<<<(unsigned)(grid < cap ? grid : cap), 256, 0, s>>>(a, t->leaf_rid, t->leaf_dbit, t->leaf_high,
-                                                                   shape.level_nodes[0], refined, status_ptr());
+    const unsigned g = (unsigned)(grid < cap ? grid : cap);
+    uint32_t* lr = t->leaf_rid;
+    uint16_t* ld = t->leaf_dbit;
+    uint32_t* lh = t->leaf_high;
+    const uint64_t n0 = shape.level_nodes[0];
+    unsigned long long* st = status_ptr();
+    switch (a.K) {
+        case 1: leaf_kw_kernel<1><<<g, 256, 0, s>>>(a, lr, ld, lh, n0, refined, st); break;
+        case 2: leaf_kw_kernel<2><<<g, 256, 0, s>>>(a, lr, ld, lh, n0, refined, st); break;
+        case 3: leaf_kw_kernel<3><<<g, 256, 0, s>>>(a, lr, ld, lh, n0, refined, st); break;
+        case 4: leaf_kw_kernel<4><<<g, 256, 0, s>>>(a, lr, ld, lh, n0, refined, st); break;
+        case 5: leaf_kw_kernel<5><<<g, 256, 0, s>>>(a, lr, ld, lh, n0, refined, st); break;
+        case 6: leaf_kw_kernel<6><<<g, 256, 0, s>>>(a, lr, ld, lh, n0, refined, st); break;
+        case 7: leaf_kw_kernel<7><<<g, 256, 0, s>>>(a, lr, ld, lh, n0, refined, st); break;
+        case 8: leaf_kw_kernel<8><<<g, 256, 0, s>>>(a, lr, ld, lh, n0, refined, st); break;
+        default: leaf_kernel<<<g, 256, 0, s>>>(a, lr, ld, lh, n0, refined, st); break;
+    }
     count_launch();
     if (shape.inner_entries > 0) {
         InnerShape sh;

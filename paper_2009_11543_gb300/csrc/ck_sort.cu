@@ -108,6 +108,53 @@ __global__ void __launch_bounds__(kUpThreads) upsweep_kernel(const uint32_t* __r
         if (sh[i]) atomicAdd(&hist[(uint64_t)p0 * BINS + i], sh[i]);
 }
 
+// The same with the key's KW words held in registers: every digit is cut from
+// them (word indices are compile-time constants), so a key is read once.
+template <int RB, int KW>
+__global__ void __launch_bounds__(kUpThreads) upsweep_kw_kernel(const uint32_t* __restrict__ ck, uint64_t n,
+                                                                uint64_t ld, uint32_t nbits, uint32_t p0,
+                                                                uint32_t np, uint32_t* __restrict__ hist) {
+    constexpr int BINS = 1 << RB, DIGITS = (32 * KW + RB - 1) / RB;
+    extern __shared__ uint32_t sh[];
+    for (uint32_t i = threadIdx.x; i < np * BINS; i += blockDim.x) sh[i] = 0;
+    __syncthreads();
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t r = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += stride) {
+        uint32_t w[KW];
+#pragma unroll
+        for (int k = 0; k < KW; ++k) w[k] = ck[(uint64_t)k * ld + r];
+#pragma unroll
+        for (int q = 0; q < DIGITS; ++q) {
+            const uint32_t shift = (uint32_t)q * RB, wi = shift >> 5, s = shift & 31;
+            if (q < (int)p0 || q >= (int)(p0 + np) || shift >= nbits) continue;
+            uint32_t d = w[wi] >> s;
+            if (s + RB > 32 && wi + 1 < KW) d |= w[wi + 1] << (32 - s);
+            const uint32_t bits = nbits - shift < (uint32_t)RB ? nbits - shift : (uint32_t)RB;
+            atomicAdd(&sh[(q - p0) * BINS + (d & ((1u << bits) - 1u))], 1u);
+        }
+    }
+    __syncthreads();
+    for (uint32_t i = threadIdx.x; i < np * BINS; i += blockDim.x)
+        if (sh[i]) atomicAdd(&hist[(uint64_t)p0 * BINS + i], sh[i]);
+}
+
+template <int RB>
+static void launch_upsweep(const uint32_t* ck, uint64_t n, uint64_t ld, uint32_t K, uint32_t nbits, uint32_t p0,
+                           uint32_t np, uint32_t* hist, int grid, cudaStream_t s) {
+    const size_t smem = sizeof(uint32_t) * np * (1u << RB);
+    switch (K) {
+        case 1: upsweep_kw_kernel<RB, 1><<<grid, kUpThreads, smem, s>>>(ck, n, ld, nbits, p0, np, hist); break;
+        case 2: upsweep_kw_kernel<RB, 2><<<grid, kUpThreads, smem, s>>>(ck, n, ld, nbits, p0, np, hist); break;
+        case 3: upsweep_kw_kernel<RB, 3><<<grid, kUpThreads, smem, s>>>(ck, n, ld, nbits, p0, np, hist); break;
+        case 4: upsweep_kw_kernel<RB, 4><<<grid, kUpThreads, smem, s>>>(ck, n, ld, nbits, p0, np, hist); break;
+        case 5: upsweep_kw_kernel<RB, 5><<<grid, kUpThreads, smem, s>>>(ck, n, ld, nbits, p0, np, hist); break;
+        case 6: upsweep_kw_kernel<RB, 6><<<grid, kUpThreads, smem, s>>>(ck, n, ld, nbits, p0, np, hist); break;
+        case 7: upsweep_kw_kernel<RB, 7><<<grid, kUpThreads, smem, s>>>(ck, n, ld, nbits, p0, np, hist); break;
+        case 8: upsweep_kw_kernel<RB, 8><<<grid, kUpThreads, smem, s>>>(ck, n, ld, nbits, p0, np, hist); break;
+        default: upsweep_kernel<RB><<<grid, kUpThreads, smem, s>>>(ck, n, ld, nbits, p0, np, hist); break;
+    }
+}
+
 template <int RB>
 __global__ void __launch_bounds__(256) scan_kernel(uint32_t* hist) {
     __shared__ uint32_t scratch[256 / 32 + 1];
@@ -451,12 +498,21 @@ static cudaError_t run_sort_rb(const SortPlan& p, const uint32_t* ck_in, const u
     // upsweep: all pass histograms, in chunks that fit 64 KB of shared memory
     const uint32_t chunk = (uint32_t)(65536 / (sizeof(uint32_t) * BINS));
     const int up_grid = num_sms() * 4;
-    e = cudaFuncSetAttribute(upsweep_kernel<RB>, cudaFuncAttributeMaxDynamicSharedMemorySize, 65536);
-    if (e != cudaSuccess) return e;
+    if (p.passes * BINS * sizeof(uint32_t) > 48 * 1024) {  // chunks above the default shared-memory limit
+        e = cudaFuncSetAttribute(upsweep_kernel<RB>, cudaFuncAttributeMaxDynamicSharedMemorySize, 65536);
+        if (e != cudaSuccess) return e;
+        if (p.K <= 8) {
+            const void* fn[8] = {(const void*)upsweep_kw_kernel<RB, 1>, (const void*)upsweep_kw_kernel<RB, 2>,
+                                 (const void*)upsweep_kw_kernel<RB, 3>, (const void*)upsweep_kw_kernel<RB, 4>,
+                                 (const void*)upsweep_kw_kernel<RB, 5>, (const void*)upsweep_kw_kernel<RB, 6>,
+                                 (const void*)upsweep_kw_kernel<RB, 7>, (const void*)upsweep_kw_kernel<RB, 8>};
+            e = cudaFuncSetAttribute(fn[p.K - 1], cudaFuncAttributeMaxDynamicSharedMemorySize, 65536);
+            if (e != cudaSuccess) return e;
+        }
+    }
     for (uint32_t p0 = 0; p0 < p.passes; p0 += chunk) {
         const uint32_t np = min(chunk, p.passes - p0);
-        upsweep_kernel<RB><<<up_grid, kUpThreads, sizeof(uint32_t) * np * BINS, s>>>(ck_in, n, ld, nbits, p0, np,
-                                                                                     hist);
+        launch_upsweep<RB>(ck_in, n, ld, p.K, nbits, p0, np, hist, up_grid, s);
         count_launch();
     }
     scan_kernel<RB><<<p.passes, 256, 0, s>>>(hist);
