@@ -497,7 +497,7 @@ static cudaError_t run_sort_rb(const SortPlan& p, const uint32_t* ck_in, const u
 
     // upsweep: all pass histograms, in chunks that fit 64 KB of shared memory
     const uint32_t chunk = (uint32_t)(65536 / (sizeof(uint32_t) * BINS));
-    const int up_grid = num_sms() * 4;
+    const int up_grid = num_sms() * 8;  // 8 blocks of 256 threads per SM
     if (p.passes * BINS * sizeof(uint32_t) > 48 * 1024) {  // chunks above the default shared-memory limit
         e = cudaFuncSetAttribute(upsweep_kernel<RB>, cudaFuncAttributeMaxDynamicSharedMemorySize, 65536);
         if (e != cudaSuccess) return e;
