@@ -26,10 +26,12 @@ namespace ck {
 constexpr uint32_t kFlagAgg = 1u << 30;
 constexpr uint32_t kFlagPrefix = 2u << 30;
 constexpr uint32_t kValMask = (1u << 30) - 1;
-constexpr int kPassThreads = 512;
-constexpr int kPassItems = 8;
-constexpr int kTile = kPassThreads * kPassItems;  // pairs per tile
-static_assert(kTile == kPassTile, "tile size of the pass kernel");
+// Two shapes of the pass block over the same 4096-pair tile: 512 threads with
+// 8 pairs each, or 256 threads with 16 pairs each (more independent work per
+// thread, fewer warps; faster when a pass moves four or more arrays).
+constexpr int kTile = kPassTile;  // pairs per tile
+constexpr int kPassThreadsWide = 512, kPassThreadsDeep = 256;
+constexpr uint32_t kDeepMinArrays = 4;
 constexpr int kRing = 3;                          // staging buffers per block
 constexpr int kPassBlocksPerSM = 3;
 constexpr int kUpThreads = 256;
@@ -170,9 +172,9 @@ __global__ void iota_kernel(uint32_t* out, uint64_t n) {
 // Shared memory of one pass block: a ring of kRing staging buffers (one array
 // of the tile each), per-warp digit counters, per-slot source position,
 // per-digit tile counts and destinations, and the ring's mbarriers.
-template <int RB>
+template <int RB, int THREADS>
 struct PassSmem {
-    static constexpr int BINS = 1 << RB, WARPS = kPassThreads / 32;
+    static constexpr int BINS = 1 << RB, WARPS = THREADS / 32;
     uint32_t stage[kRing][kTile];
     uint16_t whist[WARPS][BINS];  // counts <= kTile fit 16 bits
     uint16_t src_pos[kTile];
@@ -184,12 +186,14 @@ struct PassSmem {
     alignas(8) uint64_t bar[kRing];
 };
 
-template <int RB>
-__global__ void __launch_bounds__(kPassThreads, kPassBlocksPerSM)
+template <int RB, int THREADS>
+__global__ void __launch_bounds__(THREADS, kPassBlocksPerSM)
     onesweep_pass_kernel(const PassArgs a, const __grid_constant__ PassArrays arr) {
-    constexpr int BINS = 1 << RB, WARPS = kPassThreads / 32, ITEMS = kPassItems, WITEMS = 32 * ITEMS;
+    constexpr int kPassThreads = THREADS;
+    constexpr int BINS = 1 << RB, WARPS = THREADS / 32, ITEMS = kTile / THREADS, WITEMS = 32 * ITEMS;
+    static_assert(ITEMS * THREADS == kTile, "tile size of the pass kernel");
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    PassSmem<RB>& S = *reinterpret_cast<PassSmem<RB>*>(smem_raw);
+    PassSmem<RB, THREADS>& S = *reinterpret_cast<PassSmem<RB, THREADS>*>(smem_raw);
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const uint64_t n = a.n;
@@ -412,16 +416,22 @@ __global__ void __launch_bounds__(kPassThreads, kPassBlocksPerSM)
 }
 
 // Launches one pass; `arrays` lists the arrays in staging order.
-template <int RB>
-static cudaError_t launch_pass(const PassArgs& a, const PassArrays& arrays, uint32_t tiles, cudaStream_t s) {
-    constexpr size_t smem = sizeof(PassSmem<RB>);
-    static_assert(sizeof(PassSmem<RB>) <= 227 * 1024, "pass block exceeds shared memory");
-    cudaError_t e = cudaFuncSetAttribute(onesweep_pass_kernel<RB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
+template <int RB, int THREADS>
+static cudaError_t launch_pass_shape(const PassArgs& a, const PassArrays& arrays, uint32_t tiles, cudaStream_t s) {
+    constexpr size_t smem = sizeof(PassSmem<RB, THREADS>);
+    static_assert(sizeof(PassSmem<RB, THREADS>) <= 227 * 1024, "pass block exceeds shared memory");
+    cudaError_t e = cudaFuncSetAttribute(onesweep_pass_kernel<RB, THREADS>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    onesweep_pass_kernel<RB><<<tiles, kPassThreads, smem, s>>>(a, arrays);
+    onesweep_pass_kernel<RB, THREADS><<<tiles, THREADS, smem, s>>>(a, arrays);
     count_launch();
     return cudaGetLastError();
+}
+
+template <int RB>
+static cudaError_t launch_pass(const PassArgs& a, const PassArrays& arrays, uint32_t tiles, cudaStream_t s) {
+    return a.narr >= kDeepMinArrays ? launch_pass_shape<RB, kPassThreadsDeep>(a, arrays, tiles, s)
+                                    : launch_pass_shape<RB, kPassThreadsWide>(a, arrays, tiles, s);
 }
 
 cudaError_t launch_onesweep_pass(uint32_t rb, const PassArgs& a, const PassArrays& arrays, uint32_t tiles,
