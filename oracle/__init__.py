@@ -70,6 +70,7 @@ def _load():
         lib.cko_btree_shape.restype = U32
         lib.cko_btree_leaf_dbits.argtypes = [P, U64, U32, U32, P, P]
         lib.cko_btree_inner.argtypes = [P, U64, U32, U32, P, U32, U32, P, P, P, P]
+        lib.cko_insert_batch.argtypes = [P, U64, U32, P, P, U64, P, P, P]
         lib.cko_mlp_forward.argtypes = [P, ctypes.c_double]
         lib.cko_mlp_forward.restype = ctypes.c_double
         lib.cko_mlp_loss_grad.argtypes = [P, P, P, U64, P]
@@ -140,6 +141,23 @@ def variant_mask(keys, ref_row: int = 0) -> np.ndarray:
     ref = np.ascontiguousarray(kb[ref_row])
     _load().cko_variant_mask(_ptr(kb), n, W, W, _ptr(ref), _ptr(out))
     return out
+
+
+def insert_batch(keys, perm, batch, ref_row: int, dmask_in: np.ndarray, vmask_in: np.ndarray):
+    """Sec. 4.3 (Insert): the D-bitmap and variant bitmap after inserting the
+    rows of `batch`, one by one in the given order, into the sorted keys
+    (order `perm`); the reference key is row ref_row of `keys`."""
+    kb = as_key_bytes(keys)
+    bb = as_key_bytes(batch)
+    n, W = kb.shape
+    assert bb.shape[1] == W or bb.shape[0] == 0
+    d = np.array(dmask_in, np.uint64, copy=True)
+    v = np.array(vmask_in, np.uint64, copy=True)
+    ref = np.ascontiguousarray(kb[ref_row])
+    p = np.ascontiguousarray(perm, np.uint32)
+    _load().cko_insert_batch(_ptr(kb), n, W, _ptr(p), _ptr(np.ascontiguousarray(bb)), bb.shape[0], _ptr(ref),
+                             _ptr(d), _ptr(v))
+    return d, v
 
 
 def popcount(mask: np.ndarray) -> int:

@@ -297,3 +297,46 @@ double cko_mlp_loss_grad(const double* p, const double* x, const double* t, uint
     }
     return loss / (double)S;
 }
+
+
+/* ---- Sec. 4.3, "Search and Update Operations": DS-metadata under inserts --
+ * Inserts the m keys of `batch` one after another, in the given order, into
+ * the sorted set that starts as the n keys of `keys` (sorted order `perm`).
+ * For each insert key K: search the current sorted set for the place of K,
+ * between A (the largest key < K) and B (the smallest key >= K); set in the
+ * D-bitmap the larger of D-bit(A, K) and D-bit(K, B) (only the defined ones:
+ * a missing neighbour or an equal key has none; D-bit(A, B) is the smaller
+ * one, Lemma 1, and is already set); OR (K xor reference key) into the variant
+ * bitmap; then add K to the set.  dmask and vmask are updated in place.  The
+ * current set is a plain sorted array of key copies, grown by memmove. */
+void cko_insert_batch(const uint8_t* keys, uint64_t n, uint32_t W, const uint32_t* perm, const uint8_t* batch,
+                      uint64_t m, const uint8_t* ref, uint64_t* dmask, uint64_t* vmask) {
+    uint8_t* set = (uint8_t*)malloc((size_t)(n + m) * W + 1);
+    for (uint64_t i = 0; i < n; ++i) memcpy(set + i * W, keys + (uint64_t)perm[i] * W, W);
+    uint64_t count = n;
+    for (uint64_t j = 0; j < m; ++j) {
+        const uint8_t* k = batch + j * W;
+        uint64_t lo = 0, hi = count;  /* first position whose key is >= K */
+        while (lo < hi) {
+            const uint64_t mid = (lo + hi) / 2;
+            if (memcmp(set + mid * W, k, W) < 0) lo = mid + 1;
+            else hi = mid;
+        }
+        int64_t best = -1;
+        if (lo > 0) {
+            const int64_t d = cko_dbit(set + (lo - 1) * W, k, W);
+            if (d > best) best = d;
+        }
+        if (lo < count) {
+            const int64_t d = cko_dbit(k, set + lo * W, W);
+            if (d > best) best = d;
+        }
+        if (best >= 0) map_set(dmask, (uint32_t)best);
+        for (uint32_t p = 0; p < 8 * W; ++p)
+            if (key_bit(k, p) != key_bit(ref, p)) map_set(vmask, p);
+        memmove(set + (lo + 1) * W, set + lo * W, (size_t)(count - lo) * W);
+        memcpy(set + lo * W, k, W);
+        ++count;
+    }
+    free(set);
+}

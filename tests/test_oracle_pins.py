@@ -446,3 +446,59 @@ def test_mlp_oracle_closed_forms():
     assert g[32] == pytest.approx(np.mean(2 * r * (x + 0.5)))
     assert g[0] == pytest.approx(np.mean(2 * r * 2.0 * x))
     assert g[16] == pytest.approx(np.mean(2 * r * 2.0))
+
+
+# ------------------------------------------- Sec. 4.3 DS-metadata under inserts
+def test_insert_rule_on_fig2_keys():
+    """Sec. 3.2 / 4.3 on the Fig. 2 carrier keys: with key3 deleted, position 7
+    is no distinction bit; inserting key3 back by the paper's rule (set the
+    larger of D-bit(A, K) and D-bit(K, B)) restores D = {1, 2, 5, 7}, and the
+    variant bitmap is unchanged (key3 was already counted)."""
+    g, vals = load_fig2()
+    rows = ints_to_rows(vals, g["key_bits"])
+    r3 = np.delete(rows, 3, axis=0)
+    d3, v3 = oracle.dmask(r3), oracle.variant_mask(r3)
+    assert 7 not in positions_of(d3, 16)
+    d, v = oracle.insert_batch(r3, oracle.sort_rows(r3), rows[3:4], 0, d3, v3)
+    assert positions_of(d, 16) == g["stated"]["distinction_positions"]
+    assert positions_of(v, 16) == g["stated"]["variant_positions"]
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_inserts_keep_the_d_bitmap_exact(seed):
+    """Sec. 4.3: with inserts only, the maintained D-bitmap is the D-bitmap of
+    the grown key set recomputed from scratch (Theorem 1 on the union) and the
+    variant bitmap is that of the union against the same reference key; the
+    result does not depend on the order of the inserts."""
+    rng = np.random.default_rng(700 + seed)
+    W = int(rng.integers(1, 6))
+    n_old, n_new = int(rng.integers(1, 300)), int(rng.integers(0, 200))
+    allk = random_structured_keys(rng, n_old + n_new, W, int(rng.integers(1, 8 * W)))
+    old, new = allk[:n_old].copy(), allk[n_old:].copy()
+    if len(new) and seed % 2:   # some inserts equal to existing keys, some at the ends
+        new[: len(new) // 3] = old[rng.integers(0, len(old), len(new) // 3)]
+        new[-1] = 0
+    ref = int(rng.integers(0, len(old)))
+    d0, v0 = oracle.dmask(old), oracle.variant_mask(old, ref)
+    d, v = oracle.insert_batch(old, oracle.sort_rows(old), new, ref, d0, v0)
+    union = np.concatenate([old, new]) if len(new) else old
+    assert np.array_equal(d, oracle.dmask(union))
+    assert np.array_equal(v, oracle.variant_mask(union, ref))
+    shuffled = new[rng.permutation(len(new))]
+    d2, v2 = oracle.insert_batch(old, oracle.sort_rows(old), shuffled, ref, d0, v0)
+    assert np.array_equal(d2, d) and np.array_equal(v2, v)
+
+
+def test_deletes_leave_a_valid_d_bitmap():
+    """Sec. 4.3 (Delete): deletes leave the D-bitmap as it is; the stale bitmap
+    is a superset of the remaining keys' D, so sorting their compressed keys
+    still gives the full-key order (Theorem 2 with any superset of D)."""
+    rng = np.random.default_rng(71)
+    keys = random_structured_keys(rng, 400, 4, 14)
+    d = oracle.dmask(keys)
+    keep = np.sort(rng.choice(400, 150, replace=False))
+    rest = keys[keep]
+    dr = oracle.dmask(rest)
+    assert np.all((dr & ~d) == 0)
+    K = (oracle.popcount(d) + 31) // 32
+    assert np.array_equal(oracle.sort_compressed(oracle.compress(rest, d, K)), oracle.sort_rows(rest))
