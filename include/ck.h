@@ -345,6 +345,34 @@ ck_status ck_build_index_keys(const ck_column* col, const uint32_t* sorted_rid, 
                               ck_stream stream);
 
 /* ---------------------------------------------------------------------------
+ * ck_insert_batch -- DS-metadata under inserts (Sec. 4.3, "Search and Update
+ * Operations", Insert).  A batch of new keys joins an index's sorted keys:
+ * for every new key K with neighbours A and B in the merged sorted order, the
+ * D-bits of (A, K) and (K, B) are set in the D-bitmap (the paper sets the
+ * larger of the two per insert; the smaller is D-bit(A, B) by Lemma 1, already
+ * set, or itself the D-bit of such a pair), and (K xor reference key) is ORed
+ * into the variant bitmap.  The result equals inserting the keys one by one,
+ * in any order; with inserts only it is the D-bitmap of the grown key set.
+ * Deletes need no call: the bitmaps are left as they are (Sec. 4.3).
+ *   keys       the indexed column (device), n >= 1 rows; not modified.
+ *   order      device, n uint32: the keys' sorted order (for instance the
+ *              tree's leaf_rid, or ck_sort's rid_out).
+ *   batch      the new keys (device), same key_bytes and kind as keys, m rows
+ *              (m = 0: nothing to do); not modified.
+ *   ref_row    row of keys holding the variant bitmap's reference key.
+ *   dmask, vmask  device bitmaps of ceil(8 * key_bytes / 64) words (the
+ *              layout of ck_distinction_bits), updated in place.
+ *   ws         device workspace of ck_insert_workspace_bytes(m, key_bytes)
+ *              bytes, 256-byte aligned (sorts the batch).
+ * The call synchronises the stream once (the batch's varying bits size its
+ * sort).  Errors: CK_EINVAL (shape or kind mismatch, n = 0, ref_row >= n, an
+ * order entry >= n is skipped and recorded in the device status word),
+ * CK_ENOMEM (ws too small), CK_ECUDA. */
+size_t ck_insert_workspace_bytes(uint64_t m, uint32_t key_bytes);
+ck_status ck_insert_batch(const ck_column* keys, const uint32_t* order, const ck_column* batch, uint64_t ref_row,
+                          uint64_t* dmask, uint64_t* vmask, void* ws, size_t ws_bytes, ck_stream stream);
+
+/* ---------------------------------------------------------------------------
  * ck_model_separators -- model-proposed inner separators (not in the paper).
  * For every inner entry of a built tree the CDF model (parameters as trained
  * by ck_sort_learned, device [CK_MLP_PARAMS]) proposes the top 24 bits of the
@@ -420,8 +448,8 @@ ck_status ck_autotune_sort(const uint32_t* ck_in, uint32_t* ck_out, uint32_t* ri
  * Device status.  ck_device_status synchronises the device, returns the first
  * device-side error recorded since the last clear (CK_OK if none) and, if
  * detail is not NULL, a call-specific detail word (for CK_ETIMEOUT: the pass
- * in bits 0..15 and, in bits 16..47, the waiting tile whose wait ran out first).  The status is one word
- * per device shared by all streams. */
+ * in bits 0..15 and, in bits 16..47, the waiting tile whose wait ran out
+ * first).  The status is one word per device shared by all streams. */
 ck_status ck_device_status(uint64_t* detail);
 ck_status ck_clear_device_status(void);
 

@@ -32,7 +32,7 @@ EXPORTED = ["ck_variant_bits", "ck_distinction_bits", "ck_extract", "ck_sort_wor
             "ck_status_string", "ck_launch_count", "ck_compress_word_host", "ck_sort_static", "ck_build_index_keys",
             "ck_sort_learned_workspace_bytes", "ck_sort_learned", "ck_mlp_workspace_bytes", "ck_mlp_loss_grad",
             "ck_build_batched", "ck_graph_capture_batched", "ck_graph_launch", "ck_graph_destroy",
-            "ck_autotune_sort", "ck_model_separators"]
+            "ck_autotune_sort", "ck_model_separators", "ck_insert_workspace_bytes", "ck_insert_batch"]
 CK_SORT_STATIC_SCRATCH_BYTES = 32 << 20
 
 
@@ -126,6 +126,9 @@ def _lib():
         lib.ck_autotune_sort.argtypes = [P, P, P, U64, U32, U32, P, ctypes.c_size_t, U32, ctypes.c_char_p,
                                          ctypes.POINTER(U32), ctypes.POINTER(ctypes.c_float), P]
         lib.ck_model_separators.argtypes = [P, ctypes.POINTER(ck_btree), U32, U32, P, P, P]
+        lib.ck_insert_workspace_bytes.argtypes = [U64, U32]
+        lib.ck_insert_workspace_bytes.restype = ctypes.c_size_t
+        lib.ck_insert_batch.argtypes = [CP, P, CP, U64, P, P, P, ctypes.c_size_t, P]
         lib.ck_device_status.argtypes = [ctypes.POINTER(U64)]
         lib.ck_status_string.argtypes = [I]
         lib.ck_status_string.restype = ctypes.c_char_p
@@ -170,9 +173,9 @@ def column(keys: torch.Tensor, kind: int | None = None) -> ck_column:
         if keys.element_size() != 1:
             raise ValueError("2-D key columns must be uint8 rows")
         n, W = keys.shape
-        stride = keys.stride(0)
+        stride = keys.stride(0) if n > 0 else W  # an empty column's strides carry no layout
         k = CK_KIND_BYTES if kind is None else kind
-        if keys.stride(1) != 1:
+        if n > 0 and keys.stride(1) != 1:
             raise ValueError("key rows must be contiguous")
     elif keys.dim() == 1:
         n = keys.shape[0]
@@ -214,6 +217,19 @@ def ck_distinction_bits(keys: torch.Tensor, order: torch.Tensor | None = None, o
     _check(_lib().ck_distinction_bits(ctypes.byref(col), _ptr(order), _ptr(out), _stream(stream)),
            "ck_distinction_bits")
     return out
+
+
+def ck_insert_batch(keys: torch.Tensor, order: torch.Tensor, batch: torch.Tensor, ref_row: int,
+                    dmask: torch.Tensor, vmask: torch.Tensor, kind=None, ws: torch.Tensor | None = None, stream=None):
+    """Updates dmask and vmask (device, in place) for the rows of `batch`
+    inserted into the index over `keys` whose sorted order is `order`."""
+    col, bcol = column(keys, kind), column(batch, kind)
+    need = _lib().ck_insert_workspace_bytes(bcol.n, bcol.key_bytes)
+    if ws is None:
+        ws = torch.empty(max(need, 256), dtype=torch.uint8, device=keys.device)
+    _check(_lib().ck_insert_batch(ctypes.byref(col), _ptr(order), ctypes.byref(bcol), ref_row, _ptr(dmask),
+                                  _ptr(vmask), _ptr(ws), ws.numel(), _stream(stream)), "ck_insert_batch")
+    return dmask, vmask
 
 
 def popcount(mask: np.ndarray) -> int:
