@@ -297,7 +297,9 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
     desc, n, kind, fanout, cpu_rows, main_path = WORKLOADS[args.workload]
-    keys_np = gen_keys(kind, n)
+    m_ins = min(1 << 20, n // 16)          # an insert batch: the generator's next rows
+    all_np = gen_keys(kind, n + m_ins)
+    keys_np, ins_np = all_np[:n], all_np[n:]
     keys_host = torch.from_numpy(keys_np.view(np.int64) if keys_np.dtype == np.uint64 else keys_np).pin_memory()
     keys = keys_host.to(dev)
     key_bytes = keys_np.shape[1] if keys_np.ndim == 2 else keys_np.dtype.itemsize
@@ -387,6 +389,24 @@ def run_ours(args, rank, world, local_rank):
     e1.record(stream)
     barrier()
     e2e_ms = e0.elapsed_time(e1)
+
+    # DS-metadata maintenance (Sec. 4.3): a batch of inserts into the index
+    ins = torch.from_numpy(ins_np.view(np.int64) if ins_np.dtype == np.uint64 else ins_np).to(dev)
+    ins_d = torch.from_numpy(np.ascontiguousarray(R.dmask).view(np.int64)).to(dev)
+    ins_v = ck.ck_variant_bits(keys, 0)
+    ins_ws = torch.empty(max(256, ck._lib().ck_insert_workspace_bytes(m_ins, key_bytes)), dtype=torch.uint8,
+                         device=dev)
+    ins_ms = []
+    for it in range(args.warmup + args.steps):
+        a0 = torch.cuda.Event(enable_timing=True)
+        a1 = torch.cuda.Event(enable_timing=True)
+        a0.record(stream)
+        ck.ck_insert_batch(keys, R.rid_sorted[:n], ins, 0, ins_d, ins_v, ws=ins_ws)
+        a1.record(stream)
+        a1.synchronize()
+        if it >= args.warmup:
+            ins_ms.append(a0.elapsed_time(a1))
+    ins_ms = float(np.median(ins_ms))
     clk = clocks.stop()
     status, detail = ck.ck_device_status()
     if status != ck.CK_OK:
@@ -467,6 +487,8 @@ def run_ours(args, rank, world, local_rank):
             "stats": L.learned_stats, "speedup_vs_plain": ms_step / l_ms_step},
         "gpu_launches": int(l_launches if V is L else launches),
         "clocks": clk,
+        "insert_batch": {"value": world * m_ins / (ins_ms / 1e3), "unit": "keys/s", "ms": ins_ms, "batch": m_ins,
+                         "index_rows": n, "note": "D-bitmap and variant bitmap maintenance (Sec. 4.3), median"},
     }
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.workload, dmask, cpu_rows)
