@@ -57,6 +57,7 @@ def _load():
         P = ctypes.c_void_p
         U64, U32, I64 = ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int64
         lib.cko_uint_to_bytes.argtypes = [P, U64, U32, P]
+        lib.cko_encode_numeric.argtypes = [P, U64, U32, P]
         lib.cko_dbit.argtypes = [P, P, U32]
         lib.cko_dbit.restype = I64
         lib.cko_sort_rows.argtypes = [P, U64, U32, U32, P]
@@ -83,19 +84,24 @@ def _ptr(a: np.ndarray):
     return a.ctypes.data_as(ctypes.c_void_p)
 
 
+_NUMERIC_KIND = {np.dtype(np.uint32): 1, np.dtype(np.uint64): 2, np.dtype(np.int32): 3, np.dtype(np.int64): 4,
+                 np.dtype(np.float32): 5, np.dtype(np.float64): 6}
+
+
 def as_key_bytes(keys: np.ndarray) -> np.ndarray:
-    """Sec. 4.1: uint32/uint64 columns become big-endian byte strings; a 2-D
-    uint8 array of rows is used as given.  Returns a C-contiguous [n, W] uint8."""
+    """Sec. 4.1: numeric columns (unsigned, signed, float) become their
+    binary-comparable big-endian index keys; a 2-D uint8 array of rows is used
+    as given.  Returns a C-contiguous [n, W] uint8."""
     keys = np.asarray(keys)
     if keys.dtype == np.uint8 and keys.ndim == 2:
         return np.ascontiguousarray(keys)
-    if keys.dtype in (np.uint32, np.uint64) and keys.ndim == 1:
+    if keys.dtype in _NUMERIC_KIND and keys.ndim == 1:
         k = np.ascontiguousarray(keys)
         w = k.dtype.itemsize
         out = np.empty((k.shape[0], w), np.uint8)
-        _load().cko_uint_to_bytes(_ptr(k), k.shape[0], 1 if w == 4 else 2, _ptr(out))
+        _load().cko_encode_numeric(_ptr(k), k.shape[0], _NUMERIC_KIND[k.dtype], _ptr(out))
         return out
-    raise TypeError("keys must be [n, W] uint8 rows or a 1-D uint32/uint64 column")
+    raise TypeError("keys must be [n, W] uint8 rows or a 1-D numeric column")
 
 
 def mask_words(key_bits: int) -> int:

@@ -48,6 +48,30 @@ static void map_set(uint64_t* map, uint32_t p) {
     map[p >> 6] |= (uint64_t)1 << (63 - (p & 63));
 }
 
+/* ---- Sec. 4.1: numeric columns as binary-comparable index keys ----------
+ * The index key format Sec. 4.1 takes from [LKN]: a signed integer's key is
+ * its two's-complement value with the sign bit flipped; a float's key is its
+ * IEEE bit pattern with every bit flipped if the sign bit is set, otherwise
+ * with the sign bit flipped; in both cases written big-endian, so that
+ * comparing the bytes compares the numbers.  kind: 1 uint32, 2 uint64,
+ * 3 int32, 4 int64, 5 binary32, 6 binary64 (native values). */
+void cko_encode_numeric(const void* in, uint64_t n, uint32_t kind, uint8_t* out) {
+    const uint32_t w = (kind == 1 || kind == 3 || kind == 5) ? 4 : 8;
+    const uint64_t sign = (uint64_t)1 << (8 * w - 1);
+    for (uint64_t r = 0; r < n; ++r) {
+        uint64_t v = 0;
+        memcpy(&v, (const uint8_t*)in + r * w, w);  /* the value's bit pattern (little-endian host) */
+        if (kind == 3 || kind == 4) {
+            v ^= sign;
+        } else if (kind == 5 || kind == 6) {
+            if (v & sign) v = ~v;
+            else v ^= sign;
+            if (w == 4) v &= 0xFFFFFFFFull;
+        }
+        for (uint32_t b = 0; b < w; ++b) out[r * w + b] = (uint8_t)(v >> (8 * (w - 1 - b)));
+    }
+}
+
 /* ---- Sec. 4.1: unsigned integers as binary-comparable index keys --------
  * An unsigned integer compares like its big-endian byte string ([LKN] mapping
  * referred to by Sec. 4.1).  kind 1 = uint32, kind 2 = uint64 (native values). */

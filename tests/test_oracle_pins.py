@@ -502,3 +502,34 @@ def test_deletes_leave_a_valid_d_bitmap():
     assert np.all((dr & ~d) == 0)
     K = (oracle.popcount(d) + 31) // 32
     assert np.array_equal(oracle.sort_compressed(oracle.compress(rest, d, K)), oracle.sort_rows(rest))
+
+
+# ------------------------------------------------ Sec. 4.1 numeric key formats
+@pytest.mark.parametrize("dtype", [np.int32, np.int64, np.float32, np.float64])
+def test_numeric_key_format_orders_like_the_numbers(dtype):
+    """Sec. 4.1 ([LKN] mapping): comparing the encoded keys byte by byte sorts
+    the values as numpy sorts the numbers (stable, ties by position)."""
+    rng = np.random.default_rng(int(np.dtype(dtype).itemsize) * 10 + (dtype in (np.float32, np.float64)))
+    if np.issubdtype(dtype, np.integer):
+        info = np.iinfo(dtype)
+        v = rng.integers(info.min, info.max, 5000, dtype=dtype, endpoint=True)
+        v[:6] = [info.min, info.min + 1, -1, 0, 1, info.max]
+    else:
+        v = (rng.standard_normal(5000) * 10.0 ** rng.integers(-40, 38, 5000)).astype(dtype)
+        v[:5] = [-np.inf, np.inf, np.finfo(dtype).tiny, -np.finfo(dtype).max, np.finfo(dtype).smallest_subnormal]
+        v[v == 0] = 1          # -0.0 and +0.0 are equal numbers but distinct keys: pinned below
+    v[100:200] = v[7]          # equal values keep their row order
+    kb = oracle.as_key_bytes(v)
+    assert kb.shape == (5000, np.dtype(dtype).itemsize)
+    assert np.array_equal(oracle.sort_rows(kb), np.argsort(v, kind="stable"))
+
+
+@pytest.mark.parametrize("dtype", [np.float32, np.float64])
+def test_float_key_format_chain(dtype):
+    """The float format is a total order: -inf < ... < -0.0 < +0.0 < ... < +inf."""
+    f = np.finfo(dtype)
+    chain = np.array([-np.inf, -f.max, -1.0, -f.tiny, -f.smallest_subnormal, -0.0, 0.0, f.smallest_subnormal,
+                      f.tiny, 1.0, f.max, np.inf], dtype=dtype)
+    kb = oracle.as_key_bytes(chain)
+    rows = [bytes(r) for r in kb]
+    assert all(a < b for a, b in zip(rows, rows[1:]))
