@@ -57,7 +57,15 @@ typedef enum ck_status {
     CK_EVERIFY = 6     /* a verification pass failed; the exact fallback produced the result */
 } ck_status;
 
-enum { CK_KIND_BYTES = 0, CK_KIND_U32 = 1, CK_KIND_U64 = 2 };
+enum {
+    CK_KIND_BYTES = 0,
+    CK_KIND_U32 = 1,
+    CK_KIND_U64 = 2,
+    CK_KIND_I32 = 3, /* two's-complement signed integers */
+    CK_KIND_I64 = 4,
+    CK_KIND_F32 = 5, /* IEEE 754 binary32 / binary64 */
+    CK_KIND_F64 = 6
+};
 
 #define CK_MAX_ROWS ((1ull << 30) - 1) /* look-back words pack a 30-bit count */
 #define CK_MAX_KEY_BYTES 512u          /* 4096 key positions; D-bits fit uint16 */
@@ -68,7 +76,14 @@ enum { CK_KIND_BYTES = 0, CK_KIND_U32 = 1, CK_KIND_U64 = 2 };
 
 /* A key column in device memory.  CK_KIND_BYTES: binary-comparable byte
  * strings (fixed-size strings as they are, varchar with its terminating NUL and
- * zero padding, Sec. 4.1).  CK_KIND_U32 / CK_KIND_U64: key_bytes must be 4 / 8. */
+ * zero padding, Sec. 4.1).  The numeric kinds hold native little-endian values
+ * (key_bytes 4 for U32 / I32 / F32, 8 for U64 / I64 / F64) and are read through
+ * the order-preserving index key format Sec. 4.1 refers to ([LKN]): the key is
+ * the big-endian bytes of the value, with the sign bit flipped for a signed
+ * integer, and for a float all bits inverted if its sign bit is set, else the
+ * sign bit flipped.  So -0.0 sorts just before +0.0, and NaNs past the
+ * infinities of their sign.  Bit positions, bitmaps and compressed keys refer
+ * to that key. */
 typedef struct ck_column {
     const void* keys;    /* device, n * row_stride readable bytes; row r starts at
                             (const char*)keys + r * row_stride */

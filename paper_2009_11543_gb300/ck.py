@@ -18,7 +18,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libck.so")
 
 CK_OK, CK_EINVAL, CK_ENOMEM, CK_ECUDA, CK_EOVERFLOW, CK_ETIMEOUT, CK_EVERIFY = range(7)
-CK_KIND_BYTES, CK_KIND_U32, CK_KIND_U64 = 0, 1, 2
+CK_KIND_BYTES, CK_KIND_U32, CK_KIND_U64, CK_KIND_I32, CK_KIND_I64, CK_KIND_F32, CK_KIND_F64 = 0, 1, 2, 3, 4, 5, 6
 CK_MAX_ROWS = (1 << 30) - 1
 CK_MAX_KEY_BYTES = 512
 CK_NO_DBIT = 0xFFFF
@@ -181,7 +181,12 @@ def column(keys: torch.Tensor, kind: int | None = None) -> ck_column:
         n = keys.shape[0]
         W = keys.element_size()
         stride = W * keys.stride(0)
-        k = kind if kind is not None else {4: CK_KIND_U32, 8: CK_KIND_U64}[W]
+        if kind is not None:
+            k = kind
+        elif keys.dtype in (torch.float32, torch.float64):
+            k = CK_KIND_F32 if W == 4 else CK_KIND_F64
+        else:
+            k = {4: CK_KIND_U32, 8: CK_KIND_U64}[W]   # integer tensors hold unsigned keys unless kind says so
     else:
         raise ValueError("keys must be 1-D or 2-D")
     return ck_column(keys.data_ptr(), n, W, stride, k)

@@ -59,9 +59,10 @@ bool make_key_desc(const ck_column* col, KeyDesc* d, int* vec) {
     if (col->n > CK_MAX_ROWS) return false;
     const uint32_t W = col->key_bytes;
     if (W == 0 || W > CK_MAX_KEY_BYTES || col->row_stride < W) return false;
-    if (col->kind == CK_KIND_U32 && W != 4) return false;
-    if (col->kind == CK_KIND_U64 && W != 8) return false;
-    if (col->kind > CK_KIND_U64) return false;
+    if (col->kind > CK_KIND_F64) return false;
+    const bool four = col->kind == CK_KIND_U32 || col->kind == CK_KIND_I32 || col->kind == CK_KIND_F32;
+    if (four && W != 4) return false;
+    if (col->kind != CK_KIND_BYTES && !four && W != 8) return false;
     const uintptr_t addr = reinterpret_cast<uintptr_t>(col->keys);
     const uint64_t stride = col->row_stride;
     if (col->kind != CK_KIND_BYTES && (addr % W != 0 || stride % W != 0)) return false;

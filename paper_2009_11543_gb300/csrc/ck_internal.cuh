@@ -90,7 +90,9 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint32
 // word w holds key positions [32w, 32w + 32), position 32w in bit 31.
 //   BYTES: word w = bytes 4w..4w+3 of the row, byte 4w most significant;
 //   U32:   word 0 = the value;
-//   U64:   word 0 = high half, word 1 = low half of the value.
+//   U64:   word 0 = high half, word 1 = low half of the value;
+//   I32 / I64, F32 / F64: the same for the value mapped to its order-preserving
+//   form (sign bit flipped; a negative float's bits all inverted).
 // Bytes at or past key_bytes read as zero.  VEC is the load width in bytes
 // (16, 8, 4 or 1), chosen by the host so that every vector load stays inside
 // the row's stride.
@@ -120,13 +122,27 @@ __device__ __forceinline__ void load_chunk(const KeyDesc& k, uint64_t r, uint32_
 template <int VEC>
 __device__ __forceinline__ void load_chunk_row(const KeyDesc& k, const unsigned char* row, uint32_t c,
                                                uint32_t (&w)[4]) {
-    if (k.kind == CK_KIND_U64) {            // 8-byte value; chunk 0 only
-        uint2 v = *reinterpret_cast<const uint2*>(row);
-        w[0] = v.y; w[1] = v.x; w[2] = 0; w[3] = 0;
+    if (k.kind == CK_KIND_U64 || k.kind == CK_KIND_I64 || k.kind == CK_KIND_F64) {  // 8-byte value; chunk 0 only
+        const uint2 v = *reinterpret_cast<const uint2*>(row);
+        uint32_t hi = v.y, lo = v.x;
+        if (k.kind == CK_KIND_I64) {
+            hi ^= 0x80000000u;
+        } else if (k.kind == CK_KIND_F64) {
+            if (hi >> 31) {
+                hi = ~hi;
+                lo = ~lo;
+            } else {
+                hi ^= 0x80000000u;
+            }
+        }
+        w[0] = hi; w[1] = lo; w[2] = 0; w[3] = 0;
         return;
     }
-    if (k.kind == CK_KIND_U32) {
-        w[0] = *reinterpret_cast<const uint32_t*>(row); w[1] = 0; w[2] = 0; w[3] = 0;
+    if (k.kind != CK_KIND_BYTES) {          // 4-byte value
+        uint32_t x = *reinterpret_cast<const uint32_t*>(row);
+        if (k.kind == CK_KIND_I32) x ^= 0x80000000u;
+        else if (k.kind == CK_KIND_F32) x = (x >> 31) ? ~x : (x ^ 0x80000000u);
+        w[0] = x; w[1] = 0; w[2] = 0; w[3] = 0;
         return;
     }
     const uint32_t first = 4 * c;

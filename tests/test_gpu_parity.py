@@ -127,6 +127,37 @@ def test_integer_kinds():
         assert np.array_equal(ck_rows(ck.ck_extract(kd, D), len(v)), oracle.compress(v, D))
 
 
+@pytest.mark.parametrize("dtype", [np.int32, np.int64, np.float32, np.float64])
+def test_signed_and_float_kinds(dtype):
+    """Sec. 4.1 key formats read by the kernels: D-bitmap, variant bitmap,
+    compressed keys, the sorted order and the tree of a signed or float column
+    equal the oracle's on the encoded keys."""
+    rng = np.random.default_rng(int(np.dtype(dtype).itemsize) + 40)
+    n = 3 * TILE + 41
+    if np.issubdtype(dtype, np.integer):
+        v = rng.integers(-2**20, 2**20, n).astype(dtype)
+    else:
+        v = (rng.standard_normal(n) * 10.0 ** rng.integers(-5, 5, n)).astype(dtype)
+        v[:4] = [-0.0, 0.0, -np.inf, np.inf]
+    v[50:90] = v[3]
+    kind = {np.int32: ck.CK_KIND_I32, np.int64: ck.CK_KIND_I64, np.float32: ck.CK_KIND_F32,
+            np.float64: ck.CK_KIND_F64}[dtype]
+    kd = to_dev(v)
+    kb = oracle.as_key_bytes(v)
+    perm = oracle.sort_rows(kb)
+    D = oracle.dmask(kb, perm)
+    assert list(ck.mask_to_host(ck.ck_distinction_bits(kd, to_dev(perm.view(np.int32)), kind=kind))) == list(D)
+    assert list(ck.mask_to_host(ck.ck_variant_bits(kd, 5, kind=kind))) == list(oracle.variant_mask(kb, 5))
+    assert np.array_equal(ck_rows(ck.ck_extract(kd, D, kind=kind), n), oracle.compress(kb, D))
+    assert list(pipeline.first_build_dmask(kd, kind=kind)) == list(D)
+    r = pipeline.Rebuild(kd, D, fanout=16, kind=kind)
+    r.run()
+    torch.cuda.synchronize()
+    assert np.array_equal(ck.u32(r.rid_sorted)[:n], perm)
+    t = oracle.btree(kb, perm, 16)
+    assert np.array_equal(r.tree["leaf_dbit"].cpu().numpy().view(np.uint16)[:n], t["leaf_dbit"])
+
+
 def test_dbits_small_and_degenerate():
     for keys in (np.zeros((0, 8), np.uint8), np.full((1, 8), 7, np.uint8), np.full((5000, 8), 9, np.uint8),
                  np.array([[0] * 8, [255] * 8], np.uint8)):
