@@ -104,6 +104,46 @@ def as_key_bytes(keys: np.ndarray) -> np.ndarray:
     raise TypeError("keys must be [n, W] uint8 rows or a 1-D numeric column")
 
 
+def encode_key(parts) -> np.ndarray:
+    """Sec. 4.1 (Index Key Format): the index key of a row of several columns
+    is the concatenation of the columns' index keys.  parts: a list of
+    (kind, values, width, nulls) with kind "bytes" (a [n, width] uint8 array:
+    fixed-size strings, or varchars zero-padded with their terminating NUL,
+    used as they are), "numeric" (a 1-D numpy integer or float column, its
+    Sec. 4.1 format) or "decimal" (int64 values scaled by 10^s, optional bool
+    nulls; Sec. 4.1 A: header byte with bit 1 = not null and bit 0 = sign,
+    then the magnitude in width - 1 big-endian bytes; the sign bit toggled and,
+    for a negative value, every magnitude bit).  Returns [n, total width] uint8."""
+    cols = []
+    for kind, values, width, nulls in parts:
+        if kind == "bytes":
+            b = np.ascontiguousarray(values, np.uint8)
+            assert b.shape[1] == width
+            cols.append(b)
+        elif kind == "numeric":
+            cols.append(as_key_bytes(np.asarray(values)))
+        elif kind == "decimal":
+            v = np.asarray(values, np.int64)
+            n = v.shape[0]
+            null = np.zeros(n, bool) if nulls is None else np.asarray(nulls, bool)
+            out = np.zeros((n, width), np.uint8)
+            for r in range(n):
+                x = 0 if null[r] else int(v[r])
+                neg = x < 0
+                header = (0 if null[r] else 2) | (1 if neg else 0)
+                mag = -x if neg else x
+                mb = width - 1
+                assert mag < 256 ** mb
+                if neg:
+                    mag = (256 ** mb - 1) - mag          # every magnitude bit toggled
+                out[r, 0] = header ^ 1                   # the sign bit toggled
+                out[r, 1:] = np.frombuffer(mag.to_bytes(mb, "big"), np.uint8)
+            cols.append(out)
+        else:
+            raise ValueError(kind)
+    return np.ascontiguousarray(np.concatenate(cols, axis=1))
+
+
 def mask_words(key_bits: int) -> int:
     return (key_bits + 63) // 64
 

@@ -533,3 +533,34 @@ def test_float_key_format_chain(dtype):
     kb = oracle.as_key_bytes(chain)
     rows = [bytes(r) for r in kb]
     assert all(a < b for a, b in zip(rows, rows[1:]))
+
+
+def test_multi_column_key_orders_like_tuples():
+    """Sec. 4.1: a key of several columns (int, varchar(8), decimal with NULLs,
+    float) concatenates the columns' index keys; comparing the keys byte by
+    byte is Python's lexicographic comparison of the tuples (a varchar as its
+    string, a NULL decimal before every value), ties by row.  The paper's
+    varchar example: AB followed by NUL sorts before ABA followed by NUL."""
+    rng = np.random.default_rng(81)
+    n = 3000
+    part_id = rng.integers(-50, 50, n).astype(np.int32)
+    words = [b"", b"A", b"AB", b"ABA", b"ABB", b"B", b"BA", b"ZZZZZZZ"]
+    names = [words[i] for i in rng.integers(0, len(words), n)]
+    name_rows = np.zeros((n, 8), np.uint8)
+    for r, w in enumerate(names):
+        name_rows[r, :len(w)] = np.frombuffer(w, np.uint8)
+    dec = rng.integers(-10**6, 10**6, n).astype(np.int64)
+    dec[rng.integers(0, n, 200)] = 0
+    nulls = rng.random(n) < 0.1
+    flt = rng.standard_normal(n).astype(np.float64)
+    flt[rng.integers(0, n, 300)] = 1.5
+    kb = oracle.encode_key([("numeric", part_id, 4, None), ("bytes", name_rows, 8, None),
+                            ("decimal", dec, 4, nulls), ("numeric", flt, 8, None)])
+    assert kb.shape == (n, 24)
+
+    def tup(r):
+        return (int(part_id[r]), names[r], (0,) if nulls[r] else (1, int(dec[r])), float(flt[r]), r)
+
+    assert list(oracle.sort_rows(kb)) == sorted(range(n), key=tup)
+    ab = oracle.encode_key([("bytes", np.array([[65, 66, 0, 0], [65, 66, 65, 0]], np.uint8), 4, None)])
+    assert bytes(ab[0]) < bytes(ab[1])
