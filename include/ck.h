@@ -64,7 +64,8 @@ enum {
     CK_KIND_I32 = 3, /* two's-complement signed integers */
     CK_KIND_I64 = 4,
     CK_KIND_F32 = 5, /* IEEE 754 binary32 / binary64 */
-    CK_KIND_F64 = 6
+    CK_KIND_F64 = 6,
+    CK_KIND_DECIMAL = 7 /* ck_encode_key parts only: scaled int64 values (Sec. 4.1 A) */
 };
 
 #define CK_MAX_ROWS ((1ull << 30) - 1) /* look-back words pack a 30-bit count */
@@ -92,6 +93,40 @@ typedef struct ck_column {
     uint32_t row_stride; /* bytes between rows, >= key_bytes */
     uint32_t kind;       /* CK_KIND_* */
 } ck_column;
+
+/* ---------------------------------------------------------------------------
+ * ck_encode_key -- index keys from several columns (Sec. 4.1, "Index Key
+ * Format"): row r of `out` is the concatenation, in part order, of each
+ * part's index key for row r, so comparing two rows byte by byte compares the
+ * tuples of column values lexicographically.  The result is a CK_KIND_BYTES
+ * column of width = the sum of the part widths, for every other call here.
+ * A part (ck_key_part) is one column, row r at values + r * stride:
+ *   CK_KIND_BYTES    a fixed-size string, or a varchar zero-padded to `width`
+ *                    bytes (its terminating NUL included, Sec. 4.1 C): copied.
+ *   CK_KIND_U32 .. CK_KIND_F64   a native numeric value (width 4 or 8): its
+ *                    big-endian order-preserving form (see ck_column).
+ *   CK_KIND_DECIMAL  decimal(m, s) as an int64 value * 10^s, with an optional
+ *                    null flag per row (nulls[r] != 0: NULL): a header byte
+ *                    (bit 1: not null, bit 0: sign, 1 for negative) and the
+ *                    magnitude in width - 1 big-endian bytes (Sec. 4.1 A); then
+ *                    the sign bit is toggled and, for a negative value, every
+ *                    magnitude bit, so NULL < negatives < non-negatives in value
+ *                    order.  A NULL's sign and magnitude are 0.  width 2 .. 9.
+ *   out        device, n rows of out_stride >= total width bytes.
+ * Errors: CK_EINVAL (kind, width or stride); a decimal whose magnitude does not
+ * fit width - 1 bytes is recorded as CK_EOVERFLOW in the device status word
+ * (its low bytes are written). */
+typedef struct ck_key_part {
+    const void* values;   /* device */
+    const uint8_t* nulls; /* device, n flags, or NULL (decimals only) */
+    uint32_t kind;        /* CK_KIND_* */
+    uint32_t width;       /* bytes of the part in the key */
+    uint32_t stride;      /* bytes between rows of values */
+} ck_key_part;
+#define CK_MAX_KEY_PARTS 16u
+
+ck_status ck_encode_key(const ck_key_part* parts, uint32_t nparts, uint64_t n, uint8_t* out, uint32_t out_stride,
+                        ck_stream stream);
 
 /* ---------------------------------------------------------------------------
  * ck_variant_bits -- the variant bitmap of Sec. 4.2: position p is set iff some

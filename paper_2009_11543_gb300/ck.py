@@ -19,6 +19,8 @@ LIB_PATH = os.path.join(_HERE, "libck.so")
 
 CK_OK, CK_EINVAL, CK_ENOMEM, CK_ECUDA, CK_EOVERFLOW, CK_ETIMEOUT, CK_EVERIFY = range(7)
 CK_KIND_BYTES, CK_KIND_U32, CK_KIND_U64, CK_KIND_I32, CK_KIND_I64, CK_KIND_F32, CK_KIND_F64 = 0, 1, 2, 3, 4, 5, 6
+CK_KIND_DECIMAL = 7
+CK_MAX_KEY_PARTS = 16
 CK_MAX_ROWS = (1 << 30) - 1
 CK_MAX_KEY_BYTES = 512
 CK_NO_DBIT = 0xFFFF
@@ -32,7 +34,7 @@ EXPORTED = ["ck_variant_bits", "ck_distinction_bits", "ck_extract", "ck_sort_wor
             "ck_status_string", "ck_launch_count", "ck_compress_word_host", "ck_sort_static", "ck_build_index_keys",
             "ck_sort_learned_workspace_bytes", "ck_sort_learned", "ck_mlp_workspace_bytes", "ck_mlp_loss_grad",
             "ck_build_batched", "ck_graph_capture_batched", "ck_graph_launch", "ck_graph_destroy",
-            "ck_autotune_sort", "ck_model_separators", "ck_insert_workspace_bytes", "ck_insert_batch"]
+            "ck_autotune_sort", "ck_model_separators", "ck_insert_workspace_bytes", "ck_insert_batch", "ck_encode_key"]
 CK_SORT_STATIC_SCRATCH_BYTES = 32 << 20
 
 
@@ -126,6 +128,7 @@ def _lib():
         lib.ck_autotune_sort.argtypes = [P, P, P, U64, U32, U32, P, ctypes.c_size_t, U32, ctypes.c_char_p,
                                          ctypes.POINTER(U32), ctypes.POINTER(ctypes.c_float), P]
         lib.ck_model_separators.argtypes = [P, ctypes.POINTER(ck_btree), U32, U32, P, P, P]
+        lib.ck_encode_key.argtypes = [ctypes.POINTER(ck_key_part), U32, U64, P, U32, P]
         lib.ck_insert_workspace_bytes.argtypes = [U64, U32]
         lib.ck_insert_workspace_bytes.restype = ctypes.c_size_t
         lib.ck_insert_batch.argtypes = [CP, P, CP, U64, P, P, P, ctypes.c_size_t, P]
@@ -164,6 +167,35 @@ def _ptr(t):
     if isinstance(t, np.ndarray):
         return ctypes.c_void_p(t.ctypes.data)
     return ctypes.c_void_p(t.data_ptr())
+
+
+class ck_key_part(ctypes.Structure):
+    _fields_ = [("values", ctypes.c_void_p), ("nulls", ctypes.c_void_p), ("kind", ctypes.c_uint32),
+                ("width", ctypes.c_uint32), ("stride", ctypes.c_uint32)]
+
+
+def ck_encode_key(parts, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """Index keys of several columns (ck_encode_key).  parts: a list of
+    (tensor, kind, width) or (tensor, kind, width, nulls) on the device;
+    byte parts are [n, width] uint8, numeric and decimal parts 1-D."""
+    arr = (ck_key_part * len(parts))()
+    n = None
+    total = 0
+    for i, part in enumerate(parts):
+        t, kind, width = part[0], part[1], part[2]
+        nulls = part[3] if len(part) > 3 else None
+        rows = t.shape[0]
+        n = rows if n is None else n
+        if rows != n:
+            raise ValueError("parts differ in row count")
+        stride = t.stride(0) * t.element_size() if rows > 0 else max(width, t.element_size())
+        arr[i] = ck_key_part(t.data_ptr(), nulls.data_ptr() if nulls is not None else None, kind, width, stride)
+        total += width
+    if out is None:
+        out = torch.empty((n, total), dtype=torch.uint8, device=parts[0][0].device)
+    _check(_lib().ck_encode_key(arr, len(parts), n, _ptr(out), out.stride(0) if n else total, _stream(stream)),
+           "ck_encode_key")
+    return out
 
 
 def column(keys: torch.Tensor, kind: int | None = None) -> ck_column:
