@@ -61,6 +61,7 @@ def _load():
         lib.synth_uniform_u32.argtypes = [U64, U64, P]
         lib.synth_sequential_noise_u64.argtypes = [U64, U64, P]
         lib.synth_zipf_tagged_u64.argtypes = [U64, U64, D, P]
+        lib.synth_zipf_letters.argtypes = [U64, U64, U32, U32, D, P]
         _lib = lib
     return _lib
 
@@ -95,6 +96,15 @@ def varying_bits_u64(n: int, seed: int, nvary: int = 24):
     out = np.empty(n, np.uint64)
     _load().synth_varying_bits_u64(n, seed, nvary, _p(pos), _p(out))
     return out, [int(p) for p in pos]
+
+
+def zipf_letters(n: int, seed: int, key_bytes: int, m: int, s: float) -> np.ndarray:
+    """The paper's Zipf(s, n, m) datasets: [n, key_bytes] uint8 keys whose
+    8-byte words start with m fixed characters followed by lowercase letters
+    drawn from Zipf(s) over 26 letters."""
+    out = np.empty((n, key_bytes), np.uint8)
+    _load().synth_zipf_letters(n, seed, key_bytes, m, s, _p(out))
+    return out
 
 
 def urls(n: int, seed: int, W: int = 32, nnames: int = 100_000, s: float = 1.1) -> np.ndarray:

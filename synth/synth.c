@@ -270,3 +270,23 @@ void synth_zipf_tagged_u64(uint64_t n, uint64_t seed, double s, uint64_t* out) {
         out[i] = (tag << 52) | x;
     }
 }
+
+
+/* ---- Zipf(s, n, m) letter keys (the paper's synthetic datasets) -------------
+ * n_keys keys of key_bytes bytes: in every 8-byte word of a key the first m
+ * bytes hold a fixed character (one seeded printable character per position,
+ * the same in all keys) and the other bytes hold lowercase letters drawn
+ * independently from Zipf(s) over the 26 letters, rank 1 = 'a'. */
+void synth_zipf_letters(uint64_t n_keys, uint64_t seed, uint32_t key_bytes, uint32_t m, double s, uint8_t* out) {
+    double* cdf = zipf_cdf(26, s);
+    const uint64_t bf = base_of(seed, 21), bz = base_of(seed, 22);
+    uint8_t fixed[512];
+    for (uint32_t p = 0; p < key_bytes && p < 512; ++p) fixed[p] = (uint8_t)(33 + below(bf, p, 94));
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < (int64_t)n_keys; ++i)
+        for (uint32_t p = 0; p < key_bytes; ++p)
+            out[(uint64_t)i * key_bytes + p] =
+                (p % 8) < m ? fixed[p]
+                            : (uint8_t)('a' + zipf_pick(cdf, 26, unif(bz, (uint64_t)i * key_bytes + p)));
+    free(cdf);
+}

@@ -564,3 +564,36 @@ def test_multi_column_key_orders_like_tuples():
     assert list(oracle.sort_rows(kb)) == sorted(range(n), key=tup)
     ab = oracle.encode_key([("bytes", np.array([[65, 66, 0, 0], [65, 66, 65, 0]], np.uint8), 4, None)])
     assert bytes(ab[0]) < bytes(ab[1])
+
+
+# ------------------------------------- Sec. 6.3 Zipf(s, n, m) synthetic datasets
+@pytest.mark.parametrize("s,n,m", [(2.5, 16, 0), (1.5, 24, 3), (1.5, 40, 5)])
+def test_zipf_letters_generator(s, n, m):
+    """The Zipf(s, n, m) definition: in every 8-byte word the first m bytes
+    are one fixed character (the same in every key), the others lowercase
+    letters with the Zipf(s) frequencies over 26 letters (rank 1 = 'a')."""
+    keys = synth.zipf_letters(200_000, synth.BASE_SEED + 9, n, m, s)
+    assert keys.shape == (200_000, n)
+    fixed = [p for p in range(n) if p % 8 < m]
+    free = [p for p in range(n) if p % 8 >= m]
+    for p in fixed:
+        assert np.all(keys[:, p] == keys[0, p])
+    letters = keys[:, free]
+    assert letters.min() >= ord("a") and letters.max() <= ord("z")
+    w = np.arange(1, 27, dtype=np.float64) ** -s
+    expect = w / w.sum() * letters.size
+    got = np.bincount(letters.ravel() - ord("a"), minlength=26)
+    assert np.all(np.abs(got - expect) <= 6 * np.sqrt(expect) + 1)
+
+
+def test_table4_sort_key_sizes_follow_the_formula():
+    """Table 4's full sort key sizes and sort key ratios follow the Sec. 6.2
+    formulas (key + 8-byte record id, in 8-byte words; full / compressed)."""
+    from paper_2009_11543_gb300 import metrics as mt
+    with open(os.path.join(GOLD, "table4_synthetic_stats.json")) as f:
+        g = json.load(f)
+    assert len(g["rows"]) == 20
+    for r in g["rows"]:
+        assert mt.full_sort_key_bytes(r["n"]) == r["full_sort_key_bytes"]
+        assert round(mt.sort_key_ratio(r["full_sort_key_bytes"], r["compressed_sort_key_bytes"]), 2) == \
+            r["sort_key_ratio"]
