@@ -52,6 +52,9 @@ WORKLOADS = {
                 "+ bulk load with fanout 256", 200_000_000, "dna", 256, 4_000_000, "learned"),
     "dna20m": ("20M 32-byte {A,C,G,T} keys (the 200M workload's generator, first 20M rows), learned partition, "
                "fanout 256; profiling size", 20_000_000, "dna", 256, 2_000_000, "learned"),
+    "zipfsweep": ("the Zipf(s, n, m) datasets of Table 4 (10M keys each: 8-byte words of m fixed characters and "
+                  "Zipf(s, 26) lowercase letters), compressed-key vs full-key rebuild, fanout 64", 10_000_000,
+                  "zipfletters", 64, 200_000, "plain"),
     "int1m": ("1M uint64 keys with 24 seeded varying bit positions, fanout 64", 1_000_000, "int", 64, 1_000_000,
               "plain"),
     "table16m": ("one table of 16M rows with 6 indexes of key widths 4, 8, 12, 16, 32, 64 bytes (uint32 uniform, "
@@ -77,6 +80,8 @@ def gen_keys(kind: str, n: int):
         return synth.dna(n, synth.BASE_SEED + 5)
     if kind == "zipf":
         return synth.zipf_tagged_u64(n, synth.BASE_SEED + 4, 0.9)
+    if kind == "zipfletters":   # Zipf(1.5, 64, 0) of Table 4, the sweep's representative
+        return synth.zipf_letters(n, synth.BASE_SEED + 30, 64, 0, 1.5)
     raise ValueError(kind)
 
 
@@ -286,6 +291,89 @@ def table_cpu_baseline(dmasks, rows):
     dt = time.perf_counter() - t
     return {"value": 6 * rows / dt, "unit": "keys/s", "cores": 1, "kind": "oracle",
             "sample": "first %d rows of the same seeded table, all 6 indexes rebuilt, single thread" % rows}
+
+
+# Table 4 of the paper (Sec. 6.3): (s, n, m) and its compressed sort key bytes
+# (distinction bits + record id variant bits, in 8-byte words) at 10M keys.
+# Table 4 leaves the record id's variant bits out; 29 (the top of Table 2's
+# 25 to 29) is the value that yields all of its compressed sizes.
+ZIPF_RID_VARIANT_BITS = 29
+ZIPF_SWEEP = [(2.5, n, 0, 40) for n in range(48, 113, 8)] + [(1.5, 40, m, 24) for m in range(5)] + \
+             [(1.5, 64, m, 24) for m in range(6)]
+
+
+def run_zipf_sweep(args, rank, world, local_rank):
+    """Every Zipf(s, n, m) dataset of Table 4: one compressed-key and one
+    full-key rebuild per step, timed with CUDA events (device-resident keys)."""
+    import torch
+    import synth
+    from paper_2009_11543_gb300 import build as b
+    b.build()
+    from paper_2009_11543_gb300 import ck, metrics, pipeline
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    desc, n_keys, _, fanout, _, _ = WORKLOADS[args.workload]
+    stream = torch.cuda.current_stream()
+
+    def timed(fn, steps, warmup):
+        for _ in range(warmup):
+            fn()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / steps
+
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    rows, tot_ms, tot_keys, l0 = [], 0.0, 0, ck.ck_launch_count()
+    steps = max(1, args.steps // 4)
+    for i, (zs, zn, zm, paper_ck_bytes) in enumerate(ZIPF_SWEEP):
+        keys = torch.from_numpy(synth.zipf_letters(n_keys, synth.BASE_SEED + 30 + i, zn, zm, zs)).to(dev)
+        dmask = pipeline.first_build_dmask(keys, digit_bits=args.digit_bits)
+        nbits = ck.popcount(dmask)
+        R = pipeline.Rebuild(keys, dmask, fanout=fanout, digit_bits=args.digit_bits)
+        F = pipeline.Rebuild(keys, pipeline.full_key_mask(8 * zn), fanout=fanout, digit_bits=args.digit_bits)
+        r_ms = timed(R.run, steps, args.warmup)
+        f_ms = timed(F.run, max(1, steps // 2), 2)
+        ours_ck = metrics.compressed_sort_key_bytes(nbits, ZIPF_RID_VARIANT_BITS)
+        full_ck = metrics.full_sort_key_bytes(zn)
+        rows.append({"function": "Zipf(%g,%d,%d)" % (zs, zn, zm), "distinction_bits": nbits, "ck_words": R.K,
+                     "radix_passes": metrics.radix_passes(nbits, args.digit_bits),
+                     "compressed_sort_key_bytes": ours_ck, "paper_compressed_sort_key_bytes": paper_ck_bytes,
+                     "pair_bytes": 4 * R.K + 4,
+                     "full_sort_key_bytes": full_ck, "sort_key_ratio": full_ck / ours_ck,
+                     "compressed_ms": r_ms, "full_key_ms": f_ms, "speedup": f_ms / r_ms})
+        tot_ms += r_ms
+        tot_keys += n_keys
+        del R, F, keys
+        torch.cuda.empty_cache()
+    clk = clocks.stop()
+    status, detail = ck.ck_device_status()
+    if status != ck.CK_OK:
+        raise RuntimeError("device status %s (detail %d)" % (ck.ck_status_string(status), detail))
+    speedups = np.array([r["speedup"] for r in rows])
+    return {
+        "metric": METRIC, "value": tot_keys / (tot_ms / 1e3), "unit": "keys/s", "n_gpus": 1, "steps": steps,
+        "warmup": args.warmup, "ms_per_step": tot_ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u32",
+        "data": "synthetic (the paper's Zipf(s, n, m) generator definition, Sec. 6.3)",
+        "config": {"workload": desc, "n_per_dataset": n_keys, "datasets": len(rows), "fanout": fanout,
+                   "rid_variant_bits": ZIPF_RID_VARIANT_BITS,
+                   "l2": "inputs larger than L2 (no flush)", "parallelism": "single GPU"},
+        "roofline": None,
+        "sweep": rows,
+        "speedup_geomean": float(np.exp(np.mean(np.log(speedups)))),
+        "paper_sort_key_sizes_matched": int(sum(r["compressed_sort_key_bytes"] == r["paper_compressed_sort_key_bytes"]
+                                                for r in rows)),
+        "gpu_launches": int(ck.ck_launch_count() - l0),
+        "clocks": clk,
+    }
 
 
 def run_ours(args, rank, world, local_rank):
@@ -583,6 +671,8 @@ def main():
         line = run_reference(args, rank, world)
     elif args.workload == "table16m":
         line = run_table(args, rank, world, local_rank)
+    elif args.workload == "zipfsweep":
+        line = run_zipf_sweep(args, rank, world, local_rank)
     else:
         line = run_ours(args, rank, world, local_rank)
     if line is not None and rank == 0:

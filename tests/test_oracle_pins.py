@@ -597,3 +597,17 @@ def test_table4_sort_key_sizes_follow_the_formula():
         assert mt.full_sort_key_bytes(r["n"]) == r["full_sort_key_bytes"]
         assert round(mt.sort_key_ratio(r["full_sort_key_bytes"], r["compressed_sort_key_bytes"]), 2) == \
             r["sort_key_ratio"]
+
+
+def test_table4_zipf_1_5_40_4_distinction_bits():
+    """Zipf(1.5, 40, 4) at the paper's 10M keys: only the 20 letter bytes vary,
+    five bits each ('a' to 'z'), so |D| <= 100; the oracle's |D| with the
+    record id's 29 variant bits gives Table 4's 24-byte compressed sort key,
+    and the 40 + 8 bytes of a full sort key give its sort key ratio of 2.00."""
+    from paper_2009_11543_gb300 import metrics as mt
+    keys = synth.zipf_letters(10_000_000, synth.BASE_SEED + 43, 40, 4, 1.5)
+    nd = oracle.popcount(oracle.dmask(keys))
+    assert 90 <= nd <= 100
+    ck_bytes = mt.compressed_sort_key_bytes(nd, 29)
+    assert ck_bytes == 24
+    assert mt.sort_key_ratio(mt.full_sort_key_bytes(40), ck_bytes) == 2.0
