@@ -16,6 +16,13 @@ passage of the paper it follows:
 * ``sort_compressed`` -- Sec. 3.2, compressed key sort
 * ``refine``          -- Sec. 4.3 rebuild step 1 with D-offset (Sec. 5.3)
 * ``btree``           -- Sec. 4.2 / 5.3, bottom-up bulk load
+* ``insert_batch``    -- Sec. 4.3 (Insert), the D-bitmap / variant bitmap rule
+* ``encode_key``      -- Sec. 4.1 index key formats (numpy)
+* ``partial_keys``    -- Sec. 4.2 partial keys (pk bits after the offset), numpy
+* ``partial_key_mask``-- Sec. 5.3 option C a), the extraction mask extended by
+                         the variant positions partial keys need, numpy
+* ``search``          -- lower bound of each query in the sorted keys (Python
+                         bisect): the result a search of Sec. 4.3 reaches
 * ``mlp_loss_grad``   -- the learned CDF model (not in the paper), fp64 forward
                          and backward by the chain rule
 
@@ -301,3 +308,77 @@ def mlp_loss_grad(params, x, t):
     g = np.zeros(MLP_PARAMS, np.float64)
     loss = _load().cko_mlp_loss_grad(_ptr(p), _ptr(xs), _ptr(ts), len(xs), _ptr(g))
     return float(loss), g
+
+
+# ------------------------------------------------------------- partial keys
+def _bits_after(kb: np.ndarray, rows: np.ndarray, start: np.ndarray, pk: int) -> np.ndarray:
+    """Bits [start, start + pk) of each key kb[rows] as a pk-bit integer (the
+    first bit most significant); positions past the key read 0."""
+    n, W = kb.shape
+    padded = np.zeros((n, W + 5), np.uint8)
+    padded[:, :W] = kb
+    b = (start >> 3).astype(np.int64)
+    window = np.zeros(len(rows), np.uint64)      # 40 bits from byte b on
+    for j in range(5):
+        window = (window << np.uint64(8)) | padded[rows, b + j].astype(np.uint64)
+    shift = (40 - (start & 7) - pk).astype(np.uint64)
+    return ((window >> shift) & np.uint64((1 << pk) - 1)).astype(np.uint32)
+
+
+def partial_keys(keys, perm: np.ndarray, tree: dict, pk: int):
+    """Sec. 4.2 (after [BMR]): the partial key of an entry is the pk bits of
+    its key that follow its distinction bit position, the offset.  Leaf entry
+    i holds sorted key i with offset D-bit(key_{i-1}, key_i); an inner entry
+    holds its highest key with the offset against the previous entry's highest
+    key.  An entry without an offset (the first of its level, or a key equal
+    to the previous one) takes the key's first pk bits.  Returns (leaf [n],
+    inner [inner entries]) as uint32, 1 <= pk <= 32."""
+    assert 1 <= pk <= 32
+    kb = as_key_bytes(keys)
+    perm = np.asarray(perm, np.int64)
+
+    def of(sorted_idx, offsets):
+        o = np.asarray(offsets, np.int64)
+        start = np.where(o == NO_DBIT, 0, o + 1)
+        return _bits_after(kb, perm[np.asarray(sorted_idx, np.int64)], start, pk)
+
+    n = kb.shape[0]
+    leaf = of(np.arange(n), tree["leaf_dbit"]) if n else np.zeros(0, np.uint32)
+    inner = of(tree["high"], tree["dbit"]) if len(tree["high"]) else np.zeros(0, np.uint32)
+    return leaf, inner
+
+
+def partial_key_mask(dmask: np.ndarray, vmask: np.ndarray, key_bits: int, pk: int) -> np.ndarray:
+    """Sec. 5.3 C a): every position a partial key can read is either in the
+    compressed key or invariant once the D-bitmap is extended by the variant
+    positions among the pk positions after each D position, and among the
+    first pk positions (entries without an offset)."""
+    D = [p for p in range(key_bits) if (int(dmask[p // 64]) >> (63 - p % 64)) & 1]
+    want = set(D)
+    for start in [0] + [d + 1 for d in D]:
+        for p in range(start, min(start + pk, key_bits)):
+            if (int(vmask[p // 64]) >> (63 - p % 64)) & 1:
+                want.add(p)
+    out = np.zeros(mask_words(key_bits), np.uint64)
+    for p in want:
+        out[p // 64] |= np.uint64(1 << (63 - p % 64))
+    return out
+
+
+def search(keys, perm: np.ndarray, queries):
+    """For each query: the first sorted position whose key is >= the query
+    (n if none), and the row id there if that key equals the query, else
+    0xFFFFFFFF.  Keys and queries compare as index-key bytes (Sec. 4.1)."""
+    import bisect
+    kb, qb = as_key_bytes(keys), as_key_bytes(queries)
+    perm = np.asarray(perm, np.int64)
+    srt = [kb[r].tobytes() for r in perm]
+    pos = np.empty(qb.shape[0], np.uint32)
+    rid = np.full(qb.shape[0], 0xFFFFFFFF, np.uint32)
+    for j in range(qb.shape[0]):
+        q = qb[j].tobytes()
+        i = bisect.bisect_left(srt, q)
+        pos[j] = i
+        if i < len(srt) and srt[i] == q:
+            rid[j] = perm[i]
+    return pos, rid

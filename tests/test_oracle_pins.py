@@ -611,3 +611,94 @@ def test_table4_zipf_1_5_40_4_distinction_bits():
     ck_bytes = mt.compressed_sort_key_bytes(nd, 29)
     assert ck_bytes == 24
     assert mt.sort_key_ratio(mt.full_sort_key_bytes(40), ck_bytes) == 2.0
+
+
+# ------------------------------------------------ partial keys and search
+def test_partial_key_of_fig2_key1():
+    """Sec. 4.2: with pk = 4 the partial key of key_1 (offset D_1 = 5) is 1010;
+    key_3 (offset D_3 = 7) takes positions 8..11 and key_0, with no offset,
+    its first four bits."""
+    g, vals = load_fig2()
+    nb = g["key_bits"]
+    rows = ints_to_rows(vals, nb)
+    perm = oracle.sort_rows(rows)
+    leaf, _ = oracle.partial_keys(rows, perm, oracle.btree(rows, perm, 4), 4)
+    assert format(int(leaf[1]), "04b") == g["stated"]["partial_key_of_key1_pk4"]
+    assert int(leaf[3]) == (vals[3] >> (nb - 12)) & 0xF
+    assert int(leaf[0]) == vals[0] >> (nb - 4)
+
+
+@pytest.mark.parametrize("W,n,nvary,f,pk", [(2, 300, 9, 3, 32), (5, 800, 20, 4, 7), (9, 500, 40, 5, 16)])
+def test_partial_keys_against_big_integers(W, n, nvary, f, pk):
+    """Every leaf and inner partial key equals the key, read as one big
+    integer, shifted so that the pk bits after the offset come out (positions
+    past the key's end are zeros); duplicates and short keys included."""
+    rng = np.random.default_rng(W * 31 + pk)
+    keys = random_structured_keys(rng, n, W, nvary)
+    keys[rng.integers(0, n, n // 5)] = keys[rng.integers(0, n, n // 5)]
+    perm = oracle.sort_rows(keys)
+    t = oracle.btree(keys, perm, f)
+    leaf, inner = oracle.partial_keys(keys, perm, t, pk)
+    kbits = 8 * W
+
+    def expect(row, off):
+        start = 0 if off == oracle.NO_DBIT else off + 1
+        v = row_int(keys[row]) << pk                   # pk zero bits appended past the end
+        return (v >> (kbits + pk - start - pk)) & ((1 << pk) - 1)
+
+    for i in range(n):
+        assert int(leaf[i]) == expect(perm[i], int(t["leaf_dbit"][i]))
+    assert len(inner) == len(t["high"]) > 0
+    for g_, (h, off) in enumerate(zip(t["high"], t["dbit"])):
+        assert int(inner[g_]) == expect(perm[int(h)], int(off))
+
+
+def test_partial_key_mask_covers_every_partial_key():
+    """Sec. 5.3 C a): with the extended mask, each bit a partial key reads is
+    in the compressed key or invariant; the mask lies between D and D plus the
+    variant positions; it still orders the keys (Theorem 2) and the D-offset
+    refinement of its compressed keys gives D back."""
+    rng = np.random.default_rng(77)
+    W, pk = 6, 5
+    keys = random_structured_keys(rng, 2000, W, 22)
+    keys[rng.integers(0, 2000, 300)] = keys[rng.integers(0, 2000, 300)]
+    kbits = 8 * W
+    perm = oracle.sort_rows(keys)
+    D = oracle.dmask(keys, perm)
+    V = oracle.variant_mask(keys, 3)
+    E = oracle.partial_key_mask(D, V, kbits, pk)
+    ps = set(positions_of(E, kbits))
+    assert set(positions_of(D, kbits)) <= ps <= set(positions_of(D, kbits)) | set(positions_of(V, kbits))
+    t = oracle.btree(keys, perm, 8)
+    var = set(positions_of(V, kbits))
+    for off in list(t["leaf_dbit"]) + list(t["dbit"]):
+        start = 0 if off == oracle.NO_DBIT else int(off) + 1
+        for p in range(start, min(start + pk, kbits)):
+            assert p in ps or p not in var
+    ck = oracle.compress(keys, E)
+    cperm = oracle.sort_compressed(ck)
+    assert np.array_equal(cperm, perm)
+    assert np.array_equal(oracle.refine(ck, cperm, E, kbits), D)
+
+
+def test_search_against_linear_scan():
+    """The search result (lower bound and the matching row id) against a
+    linear count of smaller keys, for queries equal to keys, one bit away from
+    keys, below the minimum and above the maximum."""
+    rng = np.random.default_rng(8)
+    W = 3
+    keys = random_structured_keys(rng, 400, W, 12)
+    keys[rng.integers(0, 400, 60)] = keys[rng.integers(0, 400, 60)]
+    perm = oracle.sort_rows(keys)
+    q = np.concatenate([keys[rng.integers(0, 400, 100)], keys[rng.integers(0, 400, 100)],
+                        np.zeros((1, W), np.uint8), np.full((1, W), 255, np.uint8)])
+    flip = rng.integers(0, 8 * W, 100)
+    for j in range(100):
+        q[100 + j, flip[j] // 8] ^= np.uint8(0x80 >> (flip[j] % 8))
+    pos, rid = oracle.search(keys, perm, q)
+    ints = [row_int(r) for r in keys]
+    for j in range(len(q)):
+        v = row_int(q[j])
+        assert pos[j] == sum(1 for x in ints if x < v)
+        eq = [r for r in range(len(ints)) if ints[r] == v]
+        assert rid[j] == (min(eq) if eq else 0xFFFFFFFF)          # ties keep row id order
