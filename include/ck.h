@@ -423,6 +423,87 @@ ck_status ck_insert_batch(const ck_column* keys, const uint32_t* order, const ck
                           uint64_t* dmask, uint64_t* vmask, void* ws, size_t ws_bytes, ck_stream stream);
 
 /* ---------------------------------------------------------------------------
+ * Partial keys (Sec. 4.2, after Bohannon, McIlroy and Rastogi's partial-key
+ * B+-tree) and search (Sec. 4.3, Search).
+ *
+ * The partial key of a tree entry is the pk bits (1 <= pk <= 32) of its key
+ * that follow the entry's D-bit position (its offset): key positions
+ * offset + 1 .. offset + pk, the first of them the most significant of the
+ * pk low bits of a uint32; positions past the key's end read 0.  An entry
+ * without an offset (CK_NO_DBIT: the first entry of its level, or a key equal
+ * to the previous one) takes positions 0 .. pk - 1.  Leaf entry i holds sorted
+ * key i; an inner entry holds the highest key under its child.
+ *
+ * Sec. 5.3 names the source of each bit: (A) a position of the extraction
+ * mask is read from the compressed key; (B) an invariant position (0 in the
+ * variant bitmap) from the reference key; (C) any other position either from
+ * bits added to the compressed key (option a, ck_partial_key_mask) or from
+ * the record itself (option b: the key column, by row id). */
+#define CK_MAX_PARTIAL_KEY_BITS 32u
+#define CK_NO_ROW 0xFFFFFFFFu
+
+/* ck_partial_key_mask -- host only (Sec. 5.3, C a).  out = dmask plus every
+ * variant position among 0 .. pk - 1 and among d + 1 .. d + pk for each set
+ * position d of dmask.  A superset of D (Theorem 2 keeps the order), with
+ * which every partial-key bit is a case A or B bit.  dmask, vmask, out: HOST,
+ * ceil(key_bits / 64) words (out may alias neither).  Errors: CK_EINVAL
+ * (key_bits = 0 or above 8 * CK_MAX_KEY_BYTES, pk outside 1 .. 32). */
+ck_status ck_partial_key_mask(const uint64_t* dmask, const uint64_t* vmask, uint32_t key_bits, uint32_t pk,
+                              uint64_t* out);
+
+/* ck_partial_keys -- the partial keys of every leaf and inner entry of a tree
+ * built by ck_build_index or ck_build_index_keys.
+ *   tree       HOST struct holding the built tree's device arrays.
+ *   sorted_ck  device, the word-major sorted compressed keys the tree was
+ *              built from (as given to ck_build_index), or NULL: the leaves'
+ *              case A bits then come from col.
+ *   ck_words   words of sorted_ck and of tree->inner_high_ck.
+ *   emask      HOST, the extraction mask of those compressed keys.
+ *   vmask      HOST, the variant bitmap (DS-metadata).
+ *   ref_key    HOST, key_bytes bytes: the reference key value in index-key
+ *              byte order (Sec. 4.1; for a numeric column its mapped
+ *              big-endian form).
+ *   col        the key column the tree's row ids refer to, or NULL when no
+ *              case C bit can occur (emask from ck_partial_key_mask over the
+ *              tree's D-bitmap) and sorted_ck is set.
+ *   key_bytes  W of the keys (col->key_bytes when col is given).
+ *   pk         1 .. 32.
+ *   leaf_pk    device [n] uint32;  inner_pk  device [inner_entries] uint32
+ *              (NULL allowed when the tree has no inner entries).
+ * Errors: CK_EINVAL (sizes; popcount(emask) > 32 * ck_words; sorted_ck and
+ * col both NULL).  A case C bit met without a column, or a row id >= col->n,
+ * reads as 0 and is recorded as CK_EINVAL in the device status word (detail:
+ * the row id). */
+ck_status ck_partial_keys(const ck_btree* tree, const uint32_t* sorted_ck, uint32_t ck_words, const uint64_t* emask,
+                          const uint64_t* vmask, const uint8_t* ref_key, const ck_column* col, uint32_t key_bytes,
+                          uint32_t pk, uint32_t* leaf_pk, uint32_t* inner_pk, ck_stream stream);
+
+/* ck_search -- lower-bound search of a batch of query keys (Sec. 4.3,
+ * Search).  In an inner node the query is compared with the entries' highest
+ * keys as full keys (binary search over the node; each comparison also gives
+ * the D-bit of the two keys).  In a leaf the entries are scanned in order
+ * with their offsets and partial keys (Bohannon et al.): with d the D-bit of
+ * the query against the previous key (which the query exceeds), an entry
+ * whose offset is below d is above the query, one whose offset is above d is
+ * below it, and at offset = d the partial key decides unless it equals the
+ * query's bits at the same positions; only then is the entry's full key read.
+ *   tree, col  the built tree and the key column its row ids refer to.
+ *   leaf_pk    device [n], from ck_partial_keys with the same pk.
+ *   queries    column of q keys with col's kind and key_bytes.
+ *   pos_out    device [q]: the first sorted position whose key is >= the
+ *              query (n if there is none).
+ *   rid_out    device [q] or NULL: the row id at pos_out when that key equals
+ *              the query (the smallest row id among equal keys), else
+ *              CK_NO_ROW.
+ *   derefs_out device [q] or NULL: full keys read in the leaf per query.
+ * Errors: CK_EINVAL (kind or width mismatch, pk outside 1 .. 32, a tree
+ * whose n is not col->n; a row id >= n in the tree is recorded in the device
+ * status word and ends that query's search with pos_out = n). */
+ck_status ck_search(const ck_btree* tree, const ck_column* col, const uint32_t* leaf_pk, uint32_t pk,
+                    const ck_column* queries, uint32_t* pos_out, uint32_t* rid_out, uint32_t* derefs_out,
+                    ck_stream stream);
+
+/* ---------------------------------------------------------------------------
  * ck_model_separators -- model-proposed inner separators (not in the paper).
  * For every inner entry of a built tree the CDF model (parameters as trained
  * by ck_sort_learned, device [CK_MLP_PARAMS]) proposes the top 24 bits of the

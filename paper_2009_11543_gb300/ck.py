@@ -28,13 +28,16 @@ CK_MAX_LEVELS = 32
 CK_SORT_TILE = 4096
 CK_INJECT_STALL_FIRST_TILE = 1
 CK_SORT_PERM_ONLY = 1
+CK_MAX_PARTIAL_KEY_BITS = 32
+CK_NO_ROW = 0xFFFFFFFF
 
 EXPORTED = ["ck_variant_bits", "ck_distinction_bits", "ck_extract", "ck_sort_workspace_bytes", "ck_sort",
             "ck_btree_plan", "ck_build_index", "ck_device_status", "ck_clear_device_status",
             "ck_status_string", "ck_launch_count", "ck_compress_word_host", "ck_sort_static", "ck_build_index_keys",
             "ck_sort_learned_workspace_bytes", "ck_sort_learned", "ck_mlp_workspace_bytes", "ck_mlp_loss_grad",
             "ck_build_batched", "ck_graph_capture_batched", "ck_graph_launch", "ck_graph_destroy",
-            "ck_autotune_sort", "ck_model_separators", "ck_insert_workspace_bytes", "ck_insert_batch", "ck_encode_key"]
+            "ck_autotune_sort", "ck_model_separators", "ck_insert_workspace_bytes", "ck_insert_batch", "ck_encode_key",
+            "ck_partial_key_mask", "ck_partial_keys", "ck_search"]
 CK_SORT_STATIC_SCRATCH_BYTES = 32 << 20
 
 
@@ -132,6 +135,9 @@ def _lib():
         lib.ck_insert_workspace_bytes.argtypes = [U64, U32]
         lib.ck_insert_workspace_bytes.restype = ctypes.c_size_t
         lib.ck_insert_batch.argtypes = [CP, P, CP, U64, P, P, P, ctypes.c_size_t, P]
+        lib.ck_partial_key_mask.argtypes = [P, P, U32, U32, P]
+        lib.ck_partial_keys.argtypes = [ctypes.POINTER(ck_btree), P, U32, P, P, P, CP, U32, U32, P, P, P]
+        lib.ck_search.argtypes = [ctypes.POINTER(ck_btree), CP, P, U32, CP, P, P, P, P]
         lib.ck_device_status.argtypes = [ctypes.POINTER(U64)]
         lib.ck_status_string.argtypes = [I]
         lib.ck_status_string.restype = ctypes.c_char_p
@@ -465,6 +471,76 @@ def ck_model_separators(params: torch.Tensor, shape: ck_btree_shape, arrays: dic
     _check(_lib().ck_model_separators(_ptr(params), ctypes.byref(t), ck_words, nbits, _ptr(prop), _ptr(hits),
                                       _stream(stream)), "ck_model_separators")
     return prop, hits
+
+
+def _tree(shape: ck_btree_shape, arrays: dict) -> ck_btree:
+    t = ck_btree()
+    t.shape = shape
+    for name, tensor in arrays.items():
+        setattr(t, name, tensor.data_ptr())
+    return t
+
+
+def ck_partial_key_mask(dmask: np.ndarray, vmask: np.ndarray, key_bits: int, pk: int) -> np.ndarray:
+    """The extraction mask with the bits partial keys need (host only)."""
+    d = np.ascontiguousarray(np.asarray(dmask, np.uint64))
+    v = np.ascontiguousarray(np.asarray(vmask, np.uint64))
+    out = np.zeros(mask_words(key_bits), np.uint64)
+    _check(_lib().ck_partial_key_mask(_ptr(d), _ptr(v), key_bits, pk, _ptr(out)), "ck_partial_key_mask")
+    return out
+
+
+def reference_key(keys: torch.Tensor, ref_row: int, kind=None) -> np.ndarray:
+    """Row ref_row of a key column in index-key byte order (through ck_encode_key)."""
+    col = column(keys, kind)
+    row = keys[ref_row:ref_row + 1]
+    width = int(col.key_bytes)
+    enc = ck_encode_key([(row, int(col.kind), width)])
+    return enc.cpu().numpy().reshape(-1)[:width].copy()
+
+
+def ck_partial_keys(shape: ck_btree_shape, arrays: dict, sorted_ck: torch.Tensor | None, ck_words: int,
+                    emask: np.ndarray, vmask: np.ndarray, ref_key: np.ndarray, pk: int,
+                    keys: torch.Tensor | None = None, key_bytes: int | None = None, kind=None,
+                    leaf_pk: torch.Tensor | None = None, inner_pk: torch.Tensor | None = None, stream=None):
+    """Partial keys of every leaf and inner entry; returns (leaf_pk, inner_pk)
+    device int32 tensors (uint32 values)."""
+    t = _tree(shape, arrays)
+    col = column(keys, kind) if keys is not None else None
+    W = int(col.key_bytes) if col is not None else int(key_bytes)
+    dev = arrays["leaf_rid"].device
+    n, ni = int(shape.n), int(shape.inner_entries)
+    if leaf_pk is None:
+        leaf_pk = torch.empty(max(n, 1), dtype=torch.int32, device=dev)
+    if inner_pk is None:
+        inner_pk = torch.empty(max(ni, 1), dtype=torch.int32, device=dev)
+    e = np.ascontiguousarray(np.asarray(emask, np.uint64))
+    v = np.ascontiguousarray(np.asarray(vmask, np.uint64))
+    r = np.ascontiguousarray(np.asarray(ref_key, np.uint8))
+    _check(_lib().ck_partial_keys(ctypes.byref(t), _ptr(sorted_ck), ck_words, _ptr(e), _ptr(v), _ptr(r),
+                                  ctypes.byref(col) if col is not None else None, W, pk, _ptr(leaf_pk),
+                                  _ptr(inner_pk), _stream(stream)), "ck_partial_keys")
+    return leaf_pk, inner_pk
+
+
+def ck_search(shape: ck_btree_shape, arrays: dict, keys: torch.Tensor, leaf_pk: torch.Tensor, pk: int,
+              queries: torch.Tensor, kind=None, pos: torch.Tensor | None = None, rid: torch.Tensor | None = None,
+              derefs: torch.Tensor | None = None, want_rid: bool = True, want_derefs: bool = False, stream=None):
+    """Lower-bound search of every query row; returns (pos, rid, derefs)
+    device int32 tensors (rid / derefs None unless wanted or given)."""
+    t = _tree(shape, arrays)
+    col, qcol = column(keys, kind), column(queries, kind)
+    q = int(qcol.n)
+    dev = queries.device
+    if pos is None:
+        pos = torch.empty(max(q, 1), dtype=torch.int32, device=dev)
+    if rid is None and want_rid:
+        rid = torch.empty(max(q, 1), dtype=torch.int32, device=dev)
+    if derefs is None and want_derefs:
+        derefs = torch.empty(max(q, 1), dtype=torch.int32, device=dev)
+    _check(_lib().ck_search(ctypes.byref(t), ctypes.byref(col), _ptr(leaf_pk), pk, ctypes.byref(qcol), _ptr(pos),
+                            _ptr(rid), _ptr(derefs), _stream(stream)), "ck_search")
+    return pos, rid, derefs
 
 
 def ck_device_status() -> tuple[int, int]:

@@ -176,6 +176,45 @@ __device__ __forceinline__ void load_chunk_row(const KeyDesc& k, const unsigned 
         else if (first + i >= k.nwords) w[i] = 0;
 }
 
+
+// A key of a column: row r of column k.
+struct KeyRef {
+    const KeyDesc* k;
+    uint64_t r;
+};
+
+// -1, 0, 1: lexicographic comparison of two keys of equal width (Sec. 4.1).
+template <int VEC>
+__device__ __forceinline__ int cmp_keys(const KeyRef& a, const KeyRef& b) {
+    const uint32_t nchunks = (a.k->nwords + 3) / 4;
+    for (uint32_t c = 0; c < nchunks; ++c) {
+        uint32_t wa[4], wb[4];
+        load_chunk<VEC>(*a.k, a.r, c, wa);
+        load_chunk<VEC>(*b.k, b.r, c, wb);
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+            if (wa[i] != wb[i]) return wa[i] < wb[i] ? -1 : 1;
+    }
+    return 0;
+}
+
+// D-bit of two keys (Sec. 3.1): the first differing position; -1 if equal.
+template <int VEC>
+__device__ __forceinline__ int32_t dbit_keys(const KeyRef& a, const KeyRef& b) {
+    const uint32_t nchunks = (a.k->nwords + 3) / 4;
+    for (uint32_t c = 0; c < nchunks; ++c) {
+        uint32_t wa[4], wb[4];
+        load_chunk<VEC>(*a.k, a.r, c, wa);
+        load_chunk<VEC>(*b.k, b.r, c, wb);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const uint32_t x = wa[i] ^ wb[i];
+            if (x) return (int32_t)(32 * (4 * c + i) + __clz(x));
+        }
+    }
+    return -1;
+}
+
 }  // namespace ck
 
 // ------------------------------------------------------------ host helpers

@@ -1,0 +1,407 @@
+// ck_search.cu -- partial keys of the index tree (Sec. 4.2, after Bohannon,
+// McIlroy and Rastogi's partial-key B+-tree; bit sources of Sec. 5.3) and the
+// lower-bound search of Sec. 4.3 that uses them.
+//
+// Partial keys: one thread per tree entry.  The pk positions after the
+// entry's offset are read one by one from the compressed key (a position of
+// the extraction mask; its bit index there is the position's rank in the
+// mask, counted from the most significant compressed bit), from the
+// reference key (an invariant position), or from the key row (any other).
+//
+// Search: one thread per query.  Inner nodes: binary search over the node's
+// highest keys, compared as full keys; every comparison also yields the D-bit
+// of the two keys, and the last highest key found below the query is the key
+// just before the leaf the search lands in (the fence).  Leaf: the entries are
+// scanned in order knowing d = D-bit(query, previous key), query > previous
+// key.  For entry i with offset o = D-bit(key_{i-1}, key_i):
+//   o < d   key_i has a 1 at o where the query (equal to key_{i-1} there) has
+//           a 0: key_i is the first key >= the query.
+//   o > d   key_i equals key_{i-1} at d, so the query stays above it; d holds.
+//   o = d   query and key_i agree up to d; the partial key (positions o + 1 ..
+//           o + pk) decides at its first differing bit, and only when it
+//           equals the query's bits is the full key of entry i read.
+#include "ck_internal.cuh"
+
+#include <cstring>
+
+namespace ck {
+
+namespace {
+
+constexpr int kPkThreads = 256;
+constexpr int kSearchThreads = 128;
+
+struct PkArgs {
+    const uint32_t* ck;       // leaves' sorted compressed keys, word-major (NULL: read the rows)
+    uint64_t ld;
+    const uint32_t* high_ck;  // inner entries' compressed highest keys, entry-major
+    const uint32_t* leaf_rid;
+    const uint16_t* leaf_dbit;
+    const uint32_t* inner_rid;
+    const uint16_t* inner_dbit;
+    uint64_t n, inner;
+    uint64_t rows;            // rows of the key column (0: no column)
+    uint32_t K, nbits, key_bits, pk;
+    uint64_t emask[kMaxMaskWords];
+    uint64_t vmask[kMaxMaskWords];
+    uint32_t erank[kMaxMaskWords];  // set positions of emask before word w
+    uint32_t ref[kMaxKeyWords];     // reference key, big-endian words
+};
+
+__device__ __forceinline__ bool bit_of(const uint64_t* m, uint32_t p) { return (m[p >> 6] >> (63 - (p & 63))) & 1ull; }
+
+// Word w of row r (0 past the key).
+template <int VEC>
+__device__ __forceinline__ uint32_t key_word(const KeyDesc& k, uint64_t r, uint32_t w) {
+    if (w >= k.nwords) return 0u;
+    uint32_t c[4];
+    load_chunk<VEC>(k, r, w >> 2, c);
+    return c[w & 3];
+}
+
+template <int VEC>
+__global__ void __launch_bounds__(kPkThreads) partial_keys_kernel(const __grid_constant__ PkArgs a,
+                                                                   const __grid_constant__ KeyDesc col,
+                                                                   uint32_t* __restrict__ leaf_pk,
+                                                                   uint32_t* __restrict__ inner_pk,
+                                                                   unsigned long long* status) {
+    const uint64_t total = a.n + a.inner;
+    for (uint64_t g = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; g < total;
+         g += (uint64_t)gridDim.x * blockDim.x) {
+        const bool leaf = g < a.n;
+        const uint64_t e = leaf ? g : g - a.n;
+        const uint32_t off = leaf ? a.leaf_dbit[e] : a.inner_dbit[e];
+        const uint64_t row = leaf ? a.leaf_rid[e] : a.inner_rid[e];
+        const bool from_ck = leaf ? a.ck != nullptr : true;
+        const uint32_t start = off == CK_NO_DBIT ? 0u : off + 1u;
+        uint32_t v = 0;
+        uint32_t cw_idx = 0xFFFFFFFFu, cw = 0, rw_idx = 0xFFFFFFFFu, rw = 0;
+        for (uint32_t t = 0; t < a.pk; ++t) {
+            const uint32_t p = start + t;
+            uint32_t b = 0;
+            if (p < a.key_bits) {
+                if (from_ck && bit_of(a.emask, p)) {          // (A) from the compressed key
+                    const uint32_t w = p >> 6, in = p & 63;
+                    const uint32_t q = a.erank[w] + (in ? (uint32_t)__popcll(a.emask[w] >> (64 - in)) : 0u);
+                    const uint32_t vb = a.nbits - 1 - q;      // bit index, least significant word first
+                    if ((vb >> 5) != cw_idx) {
+                        cw_idx = vb >> 5;
+                        cw = leaf ? a.ck[(uint64_t)cw_idx * a.ld + e] : a.high_ck[e * a.K + cw_idx];
+                    }
+                    b = (cw >> (vb & 31)) & 1u;
+                } else if (!bit_of(a.vmask, p)) {             // (B) invariant: the reference key
+                    b = (a.ref[p >> 5] >> (31 - (p & 31))) & 1u;
+                } else if (row < a.rows) {                    // (C) option b: the record's key
+                    if ((p >> 5) != rw_idx) {
+                        rw_idx = p >> 5;
+                        rw = key_word<VEC>(col, row, rw_idx);
+                    }
+                    b = (rw >> (31 - (p & 31))) & 1u;
+                } else {                                      // no such row (or no column): read as 0
+                    report(status, CK_EINVAL, row);
+                }
+            }
+            v = (v << 1) | b;
+        }
+        if (leaf) leaf_pk[e] = v;
+        else inner_pk[e] = v;
+    }
+}
+
+struct SearchArgs {
+    const uint32_t* leaf_rid;
+    const uint16_t* leaf_dbit;
+    const uint32_t* leaf_pk;
+    const uint32_t* inner_child;
+    const uint32_t* inner_high;
+    const uint32_t* inner_rid;
+    uint64_t n, q;
+    uint32_t f, levels, pk;
+    uint64_t level_entries[CK_MAX_LEVELS];
+    uint64_t offset[CK_MAX_LEVELS];
+};
+
+// Sign of a - b and, when they differ, their D-bit.
+template <int VEC>
+__device__ __forceinline__ int cmp_dbit(const KeyRef& a, const KeyRef& b, int32_t* d) {
+    const uint32_t nchunks = (a.k->nwords + 3) / 4;
+    for (uint32_t c = 0; c < nchunks; ++c) {
+        uint32_t wa[4], wb[4];
+        load_chunk<VEC>(*a.k, a.r, c, wa);
+        load_chunk<VEC>(*b.k, b.r, c, wb);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const uint32_t x = wa[i] ^ wb[i];
+            if (x) {
+                *d = (int32_t)(32 * (4 * c + i) + __clz(x));
+                return wa[i] < wb[i] ? -1 : 1;
+            }
+        }
+    }
+    *d = -1;
+    return 0;
+}
+
+template <int VEC>
+__global__ void __launch_bounds__(kSearchThreads) search_kernel(const __grid_constant__ SearchArgs a,
+                                                                const __grid_constant__ KeyDesc col,
+                                                                const __grid_constant__ KeyDesc qk,
+                                                                uint32_t* __restrict__ pos_out,
+                                                                uint32_t* __restrict__ rid_out,
+                                                                uint32_t* __restrict__ derefs_out,
+                                                                unsigned long long* status) {
+    for (uint64_t j = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; j < a.q; j += (uint64_t)gridDim.x * blockDim.x) {
+        const KeyRef Q{&qk, j};
+        uint64_t pos = a.n;
+        bool found = false;
+        uint32_t derefs = 0;
+        if (a.n == 0) goto done;
+        {
+            // ---- inner levels: the first entry of the node whose highest key is >= Q
+            uint64_t node = 0;
+            int64_t fence = -1;  // sorted index of the last highest key found below Q
+            int32_t fence_d = -1;
+            for (int32_t l = (int32_t)a.levels - 1; l >= 1; --l) {
+                const uint64_t m = a.level_entries[l];
+                uint64_t lo = node * a.f, hi = min(lo + a.f, m);
+                const uint64_t end = hi;
+                while (lo < hi) {
+                    const uint64_t mid = (lo + hi) >> 1;
+                    const uint64_t g = a.offset[l] + mid;
+                    const uint32_t r = a.inner_rid[g];
+                    if (r >= a.n) {
+                        report(status, CK_EINVAL, g);
+                        goto done;
+                    }
+                    int32_t d;
+                    if (cmp_dbit<VEC>(KeyRef{&col, r}, Q, &d) < 0) {
+                        lo = mid + 1;
+                        fence = a.inner_high[g];
+                        fence_d = d;
+                    } else {
+                        hi = mid;
+                    }
+                }
+                if (lo == end) goto done;  // Q is above every key
+                node = a.inner_child[a.offset[l] + lo];
+            }
+            // ---- leaf: scan with offsets and partial keys
+            const uint64_t s = node * a.f, t = min(s + a.f, a.n);
+            uint64_t i = s;
+            int32_t d = fence_d;
+            if (s == 0 || fence != (int64_t)(s - 1)) {
+                // no key before the leaf was compared: compare with it (or with the first key)
+                const uint64_t prev = s == 0 ? 0 : s - 1;
+                const uint32_t r = a.leaf_rid[prev];
+                if (r >= a.n) {
+                    report(status, CK_EINVAL, prev);
+                    goto done;
+                }
+                ++derefs;
+                const int c = cmp_dbit<VEC>(KeyRef{&col, r}, Q, &d);
+                if (s == 0) {
+                    if (c >= 0) {
+                        pos = 0;
+                        found = c == 0;
+                        goto done;
+                    }
+                    i = 1;
+                }
+            }
+            const uint32_t pk = a.pk;
+            for (; i < t; ++i) {
+                const uint32_t o = a.leaf_dbit[i];
+                if (o == CK_NO_DBIT) continue;  // equal to the previous key: still below Q
+                if ((int32_t)o < d) {
+                    pos = i;
+                    goto done;
+                }
+                if ((int32_t)o > d) continue;
+                // o == d: compare Q's bits o + 1 .. o + pk with the partial key
+                const uint32_t p0 = o + 1, w = p0 >> 5;
+                const uint64_t win = ((uint64_t)key_word<VEC>(qk, j, w) << 32) | key_word<VEC>(qk, j, w + 1);
+                const uint32_t qb = (uint32_t)((win << (p0 & 31)) >> (64 - pk));
+                const uint32_t x = qb ^ a.leaf_pk[i];
+                if (x) {
+                    const uint32_t lead = __clz(x) - (32 - pk);  // first differing bit among the pk
+                    if ((qb >> (pk - 1 - lead)) & 1u) {
+                        d = (int32_t)(p0 + lead);                // Q above key_i
+                        continue;
+                    }
+                    pos = i;
+                    goto done;
+                }
+                const uint32_t r = a.leaf_rid[i];
+                if (r >= a.n) {
+                    report(status, CK_EINVAL, i);
+                    goto done;
+                }
+                ++derefs;
+                const int c = cmp_dbit<VEC>(KeyRef{&col, r}, Q, &d);
+                if (c >= 0) {
+                    pos = i;
+                    found = c == 0;
+                    goto done;
+                }
+            }
+            pos = t;
+        }
+    done:
+        pos_out[j] = (uint32_t)pos;
+        if (rid_out) rid_out[j] = found ? a.leaf_rid[pos] : CK_NO_ROW;
+        if (derefs_out) derefs_out[j] = derefs;
+    }
+}
+
+bool load_mask(const uint64_t* src, uint32_t key_bits, uint64_t* dst) {
+    if (!src) return false;
+    const uint32_t words = (key_bits + 63) / 64;
+    memset(dst, 0, sizeof(uint64_t) * kMaxMaskWords);
+    memcpy(dst, src, sizeof(uint64_t) * words);
+    if (key_bits & 63) dst[words - 1] &= ~0ull << (64 - (key_bits & 63));
+    return true;
+}
+
+bool host_bit(const uint64_t* m, uint32_t p) { return (m[p >> 6] >> (63 - (p & 63))) & 1ull; }
+
+}  // namespace
+}  // namespace ck
+
+using namespace ck;
+
+extern "C" {
+
+ck_status ck_partial_key_mask(const uint64_t* dmask, const uint64_t* vmask, uint32_t key_bits, uint32_t pk,
+                              uint64_t* out) {
+    if (!dmask || !vmask || !out || key_bits == 0 || key_bits > kMaxKeyBits || pk == 0 ||
+        pk > CK_MAX_PARTIAL_KEY_BITS)
+        return CK_EINVAL;
+    const uint32_t words = (key_bits + 63) / 64;
+    uint64_t res[kMaxMaskWords] = {0};
+    auto add_after = [&](uint32_t start) {
+        for (uint32_t p = start; p < start + pk && p < key_bits; ++p)
+            if (host_bit(vmask, p)) res[p >> 6] |= 1ull << (63 - (p & 63));
+    };
+    add_after(0);
+    for (uint32_t p = 0; p < key_bits; ++p)
+        if (host_bit(dmask, p)) {
+            res[p >> 6] |= 1ull << (63 - (p & 63));
+            add_after(p + 1);
+        }
+    memcpy(out, res, sizeof(uint64_t) * words);
+    return CK_OK;
+}
+
+ck_status ck_partial_keys(const ck_btree* tree, const uint32_t* sorted_ck, uint32_t ck_words, const uint64_t* emask,
+                          const uint64_t* vmask, const uint8_t* ref_key, const ck_column* col, uint32_t key_bytes,
+                          uint32_t pk, uint32_t* leaf_pk, uint32_t* inner_pk, ck_stream stream) {
+    if (!tree || !emask || !vmask || !ref_key || pk == 0 || pk > CK_MAX_PARTIAL_KEY_BITS || key_bytes == 0 ||
+        key_bytes > CK_MAX_KEY_BYTES || ck_words == 0 || ck_words > kMaxKeyWords)
+        return CK_EINVAL;
+    const ck_btree_shape& sh = tree->shape;
+    const uint64_t n = sh.n;
+    if (n == 0) return CK_OK;
+    if (!leaf_pk || !tree->leaf_rid || !tree->leaf_dbit) return CK_EINVAL;
+    if (sh.inner_entries > 0 && (!inner_pk || !tree->inner_high_rid || !tree->inner_dbit || !tree->inner_high_ck))
+        return CK_EINVAL;
+    KeyDesc k;
+    memset(&k, 0, sizeof(k));
+    int vec = 1;
+    if (col) {
+        if (!make_key_desc(col, &k, &vec) || col->key_bytes != key_bytes) return CK_EINVAL;
+    }
+    static thread_local PkArgs a;
+    memset(&a, 0, sizeof(a));
+    a.key_bits = 8 * key_bytes;
+    load_mask(emask, a.key_bits, a.emask);
+    load_mask(vmask, a.key_bits, a.vmask);
+    uint32_t nbits = 0;
+    for (uint32_t w = 0; w < kMaxMaskWords; ++w) {
+        a.erank[w] = nbits;
+        nbits += (uint32_t)__builtin_popcountll(a.emask[w]);
+    }
+    if (nbits > 32 * ck_words) return CK_EINVAL;
+    if (!sorted_ck && !col) return CK_EINVAL;  // the leaves' bits need a source
+    for (uint32_t b = 0; b < key_bytes; ++b) a.ref[b >> 2] |= (uint32_t)ref_key[b] << (8 * (3 - (b & 3)));
+    a.ck = sorted_ck;
+    a.ld = CK_LD(n);
+    a.high_ck = tree->inner_high_ck;
+    a.leaf_rid = tree->leaf_rid;
+    a.leaf_dbit = tree->leaf_dbit;
+    a.inner_rid = tree->inner_high_rid;
+    a.inner_dbit = tree->inner_dbit;
+    a.n = n;
+    a.inner = sh.inner_entries;
+    a.rows = col ? col->n : 0;
+    a.K = ck_words;
+    a.nbits = nbits;
+    a.pk = pk;
+    unsigned long long* status = status_ptr();
+    if (!status) return CK_ECUDA;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const uint64_t total = n + sh.inner_entries;
+    const uint64_t want = (total + kPkThreads - 1) / kPkThreads, cap = (uint64_t)num_sms() * 8;
+    const unsigned grid = (unsigned)(want < cap ? want : cap);
+    switch (col ? vec : 1) {
+        case 16: partial_keys_kernel<16><<<grid, kPkThreads, 0, s>>>(a, k, leaf_pk, inner_pk, status); break;
+        case 8: partial_keys_kernel<8><<<grid, kPkThreads, 0, s>>>(a, k, leaf_pk, inner_pk, status); break;
+        case 4: partial_keys_kernel<4><<<grid, kPkThreads, 0, s>>>(a, k, leaf_pk, inner_pk, status); break;
+        default: partial_keys_kernel<1><<<grid, kPkThreads, 0, s>>>(a, k, leaf_pk, inner_pk, status); break;
+    }
+    count_launch();
+    return cudaGetLastError() == cudaSuccess ? CK_OK : CK_ECUDA;
+}
+
+ck_status ck_search(const ck_btree* tree, const ck_column* col, const uint32_t* leaf_pk, uint32_t pk,
+                    const ck_column* queries, uint32_t* pos_out, uint32_t* rid_out, uint32_t* derefs_out,
+                    ck_stream stream) {
+    if (!tree || pk == 0 || pk > CK_MAX_PARTIAL_KEY_BITS) return CK_EINVAL;
+    KeyDesc ck_, qk;
+    int vc = 1, vq = 1;
+    if (!make_key_desc(col, &ck_, &vc) || !make_key_desc(queries, &qk, &vq)) return CK_EINVAL;
+    if (col->key_bytes != queries->key_bytes || col->kind != queries->kind) return CK_EINVAL;
+    const ck_btree_shape& sh = tree->shape;
+    if (sh.n != col->n || sh.levels > CK_MAX_LEVELS) return CK_EINVAL;
+    const uint64_t q = queries->n;
+    if (q == 0) return CK_OK;
+    if (!pos_out) return CK_EINVAL;
+    if (sh.n > 0 && (!leaf_pk || !tree->leaf_rid || !tree->leaf_dbit || sh.levels == 0 || sh.entries_per_node == 0))
+        return CK_EINVAL;
+    if (sh.levels > 1 && (!tree->inner_child || !tree->inner_high || !tree->inner_high_rid)) return CK_EINVAL;
+    SearchArgs a;
+    memset(&a, 0, sizeof(a));
+    a.leaf_rid = tree->leaf_rid;
+    a.leaf_dbit = tree->leaf_dbit;
+    a.leaf_pk = leaf_pk;
+    a.inner_child = tree->inner_child;
+    a.inner_high = tree->inner_high;
+    a.inner_rid = tree->inner_high_rid;
+    a.n = sh.n;
+    a.q = q;
+    a.f = sh.entries_per_node;
+    a.levels = sh.levels;
+    a.pk = pk;
+    for (uint32_t l = 0; l < CK_MAX_LEVELS; ++l) {
+        a.level_entries[l] = sh.level_entries[l];
+        a.offset[l] = sh.inner_offset[l];
+    }
+    unsigned long long* status = status_ptr();
+    if (!status) return CK_ECUDA;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const uint64_t want = (q + kSearchThreads - 1) / kSearchThreads, cap = (uint64_t)num_sms() * 16;
+    const unsigned grid = (unsigned)(want < cap ? want : cap);
+    const int vec = vc < vq ? vc : vq;
+#define CK_SEARCH_LAUNCH(V) \
+    search_kernel<V><<<grid, kSearchThreads, 0, s>>>(a, ck_, qk, pos_out, rid_out, derefs_out, status)
+    switch (vec) {
+        case 16: CK_SEARCH_LAUNCH(16); break;
+        case 8: CK_SEARCH_LAUNCH(8); break;
+        case 4: CK_SEARCH_LAUNCH(4); break;
+        default: CK_SEARCH_LAUNCH(1); break;
+    }
+#undef CK_SEARCH_LAUNCH
+    count_launch();
+    return cudaGetLastError() == cudaSuccess ? CK_OK : CK_ECUDA;
+}
+
+}  // extern "C"

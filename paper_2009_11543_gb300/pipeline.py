@@ -88,6 +88,22 @@ class Rebuild:
         prop, hits = ck.ck_model_separators(params, self.shape, self.tree, self.K, self.nbits, stream=stream)
         return prop, hits
 
+    def partial_keys(self, vmask: np.ndarray, ref_key: np.ndarray, pk: int, stream=None):
+        """Partial keys of the built tree (Sec. 4.2): bits at positions of the
+        extraction mask from the compressed keys, invariant ones from ref_key,
+        any other from the key rows (Sec. 5.3 C b).  Kept for search()."""
+        sorted_ck = None if self.perm_only else self.ck_sorted
+        self.pk = pk
+        self.leaf_pk, self.inner_pk = ck.ck_partial_keys(
+            self.shape, self.tree, sorted_ck, self.K, self.dmask, vmask, ref_key, pk, keys=self.keys, kind=self.kind,
+            leaf_pk=getattr(self, "leaf_pk", None), inner_pk=getattr(self, "inner_pk", None), stream=stream)
+        return self.leaf_pk, self.inner_pk
+
+    def search(self, queries: torch.Tensor, pos=None, rid=None, derefs=None, want_derefs: bool = False, stream=None):
+        """Lower-bound search of the query rows in the built tree (Sec. 4.3)."""
+        return ck.ck_search(self.shape, self.tree, self.keys, self.leaf_pk, self.pk, queries, kind=self.kind,
+                            pos=pos, rid=rid, derefs=derefs, want_derefs=want_derefs, stream=stream)
+
     def run(self, stream=None):
         """One full rebuild: extract, sort, bulk load (+ refined D-bitmap)."""
         self.extract(stream)

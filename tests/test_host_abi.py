@@ -150,6 +150,32 @@ def test_header_constants_match_binding(ckmod):
     import re
     with open(os.path.join(ROOT, "include", "ck.h")) as f:
         hdr = f.read()
-    for name in ("CK_SORT_TILE", "CK_MAX_LEVELS", "CK_MLP_HIDDEN"):
+    for name in ("CK_SORT_TILE", "CK_MAX_LEVELS", "CK_MLP_HIDDEN", "CK_MAX_PARTIAL_KEY_BITS"):
         m = re.search(r"#define %s (\d+)u?" % name, hdr)
         assert m and int(m.group(1)) == getattr(ckmod, name), name
+    m = re.search(r"#define CK_NO_ROW (0x[0-9A-Fa-f]+)u?", hdr)
+    assert m and int(m.group(1), 16) == ckmod.CK_NO_ROW
+
+
+@pytest.mark.parametrize("W,nvary,pk", [(1, 5, 1), (4, 14, 3), (9, 30, 16), (33, 60, 32), (64, 200, 7)])
+def test_partial_key_mask_matches_oracle(ckmod, W, nvary, pk):
+    """ck_partial_key_mask (host only, Sec. 5.3 C a) against the oracle's
+    extension of the D-bitmap, on the D and variant bitmaps of random keys."""
+    rng = np.random.default_rng(W * 7 + pk)
+    base = rng.integers(0, 256, W, dtype=np.uint8)
+    pos = rng.choice(8 * W, size=min(nvary, 8 * W), replace=False)
+    keys = np.repeat(base[None, :], 300, axis=0)
+    bits = np.unpackbits(keys, axis=1)
+    bits[:, pos] = rng.integers(0, 2, (300, len(pos)), dtype=np.uint8)
+    keys = np.packbits(bits, axis=1)
+    D, V = oracle.dmask(keys), oracle.variant_mask(keys, 0)
+    got = ckmod.ck_partial_key_mask(D, V, 8 * W, pk)
+    assert np.array_equal(got, oracle.partial_key_mask(D, V, 8 * W, pk))
+
+
+def test_partial_key_mask_argument_errors(ckmod):
+    z = np.zeros(1, np.uint64)
+    for key_bits, pk in ((0, 4), (8, 0), (8, 33)):
+        with pytest.raises(ckmod.CkError) as e:
+            ckmod.ck_partial_key_mask(z, z, key_bits, pk)
+        assert e.value.status == ckmod.CK_EINVAL
