@@ -139,6 +139,61 @@ def first_build_dmask(keys: torch.Tensor, kind: int | None = None, digit_bits: i
     return ck.mask_to_host(r.refined)
 
 
+class OverlappedRebuild:
+    """Rebuilds of a stream of key batches of one shape and D-bitmap, with the
+    copies hidden behind the kernels: while batch i is rebuilt on the compute
+    stream, batch i + 1 travels host -> device on one copy stream and the
+    sorted row ids of batch i - 1 travel device -> host on another.  Two
+    Rebuild slots alternate; events order every reuse of a slot (its keys are
+    overwritten only after its previous rebuild, its row ids only after they
+    reached the host).  Extra keyword arguments go to Rebuild."""
+
+    def __init__(self, shape, dtype, dmask: np.ndarray, device, **rebuild_kw):
+        self.slots = [Rebuild(torch.empty(shape, dtype=dtype, device=device), dmask, **rebuild_kw) for _ in range(2)]
+        self.h2d = torch.cuda.Stream(device)
+        self.d2h = torch.cuda.Stream(device)
+        self.copied = [torch.cuda.Event() for _ in range(2)]   # slot's keys are on the device
+        self.built = [torch.cuda.Event() for _ in range(2)]    # slot's rebuild finished
+        self.fetched = [torch.cuda.Event() for _ in range(2)]  # slot's row ids reached the host
+        cur = torch.cuda.current_stream(device)
+        for e in self.copied + self.built + self.fetched:
+            e.record(cur)
+        self.i = 0
+
+    def begin(self, stream=None):
+        """Orders the copy streams after the work queued so far on `stream`."""
+        comp = stream or torch.cuda.current_stream()
+        self.h2d.wait_stream(comp)
+        self.d2h.wait_stream(comp)
+
+    def submit(self, host_keys: torch.Tensor, host_rid: torch.Tensor, stream=None) -> Rebuild:
+        """Queues one batch (pinned host keys in, sorted row ids out to pinned
+        host_rid); asynchronous.  Returns the slot that rebuilds it."""
+        s = self.i % 2
+        r = self.slots[s]
+        comp = stream or torch.cuda.current_stream()
+        self.h2d.wait_event(self.built[s])
+        with torch.cuda.stream(self.h2d):
+            r.keys.copy_(host_keys, non_blocking=True)
+            self.copied[s].record(self.h2d)
+        comp.wait_event(self.copied[s])
+        comp.wait_event(self.fetched[s])
+        r.run(comp)
+        self.built[s].record(comp)
+        self.d2h.wait_event(self.built[s])
+        with torch.cuda.stream(self.d2h):
+            host_rid.copy_(r.rid_sorted[:r.n], non_blocking=True)
+            self.fetched[s].record(self.d2h)
+        self.i += 1
+        return r
+
+    def finish(self, stream=None):
+        """Makes `stream` wait for every queued copy."""
+        comp = stream or torch.cuda.current_stream()
+        comp.wait_stream(self.h2d)
+        comp.wait_stream(self.d2h)
+
+
 class BatchedRebuild:
     """All the indexes of one table rebuilt together (one Rebuild per column,
     concurrently through ck_build_batched, optionally as one CUDA graph).

@@ -87,3 +87,24 @@ def test_batched_equals_unbatched():
         assert torch.equal(u.ck_sorted[:, :n], r.ck_sorted[:, :n])
         for name in ("leaf_dbit", "inner_dbit", "inner_high_ck"):
             assert torch.equal(u.tree[name], r.tree[name])
+
+
+def test_overlapped_rebuild_matches_oracle():
+    """A stream of five batches through pipeline.OverlappedRebuild (copies of
+    neighbouring batches beside each rebuild): every batch's sorted row ids on
+    the host equal the oracle's order of that batch."""
+    n = 200_003
+    batches = [synth.urls(n, synth.BASE_SEED + 60 + k) for k in range(5)]
+    allk = np.concatenate(batches)
+    vmask = oracle.variant_mask(allk, 0)          # a superset of every batch's D-bitmap
+    hosts = [torch.from_numpy(b).pin_memory() for b in batches]
+    outs = [torch.empty(n, dtype=torch.int32, pin_memory=True) for _ in batches]
+    O = pipeline.OverlappedRebuild((n, 32), torch.uint8, vmask, DEV, fanout=64)
+    O.begin()
+    for h, o in zip(hosts, outs):
+        O.submit(h, o)
+    O.finish()
+    torch.cuda.synchronize()
+    for b, o in zip(batches, outs):
+        assert np.array_equal(o.numpy().view(np.uint32), oracle.sort_rows(b))
+    assert ck.ck_device_status()[0] == ck.CK_OK
