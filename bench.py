@@ -480,6 +480,16 @@ def run_ours(args, rank, world, local_rank):
     e2e_ms = e0.elapsed_time(e1)
     e2e_ok = bool(np.array_equal(rid_hosts[(args.steps - 1) % 2].numpy(), ck.u32(V.rid_sorted)[:n].view(np.int32)))
     del O
+    # the host link's own rate for context: one copy of the keys in, alone
+    h2d_ms = []
+    for _ in range(3):
+        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a0.record(stream)
+        keys.copy_(keys_host, non_blocking=True)
+        a1.record(stream)
+        a1.synchronize()
+        h2d_ms.append(a0.elapsed_time(a1))
+    h2d_gbs = keys_np.nbytes / (min(h2d_ms) / 1e3) / 1e9
 
     # DS-metadata maintenance (Sec. 4.3): a batch of inserts into the index
     ins = torch.from_numpy(ins_np.view(np.int64) if ins_np.dtype == np.uint64 else ins_np).to(dev)
@@ -584,7 +594,7 @@ def run_ours(args, rank, world, local_rank):
                    "ck_words": R.K, "digit_bits": args.digit_bits, "radix_passes": passes, "fanout": fanout,
                    "tree_levels": int(R.shape.levels), "l2": "inputs larger than L2 (no flush)",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
-        "roofline": {"bound": "hbm", "kernel": "onesweep_pass_kernel<%d, %d>" % (args.digit_bits, 256 if R.K + 1 >= 4 else 512),
+        "roofline": {"bound": "hbm", "kernel": "onesweep_pass_kernel<%d, %d>" % (args.digit_bits, 256 if R.K + 1 >= 3 or n > (1 << 22) else 512),
                      "achieved": achieved,
                      "peak": peak, "peak_source": peak_src, "unit": "GB/s", "frac": achieved / peak,
                      "traffic": traffic, "alg_bytes_per_launch": pb, "avg_launch_ms": avg_pass_ms},
@@ -603,7 +613,7 @@ def run_ours(args, rank, world, local_rank):
                 "h2d_bytes_per_step": int(keys_np.nbytes), "d2h_bytes_per_step": 4 * n,
                 "overlap": "pipeline.OverlappedRebuild: the copies of steps i + 1 and i - 1 run beside the rebuild "
                            "of step i; the timed region spans the first copy in to the last copy out",
-                "last_result_matches_device_run": e2e_ok},
+                "last_result_matches_device_run": e2e_ok, "h2d_copy_gbs_alone": h2d_gbs},
         "path": "learned" if V is L else "plain",
         "plain": {"value": world * n / (ms_step / 1e3), "unit": "keys/s", "ms_per_step": ms_step,
                   "phases_ms": {"extract": float(ph[0]), "sort": float(ph[1]), "build": float(ph[2])}},

@@ -26,14 +26,18 @@ namespace ck {
 constexpr uint32_t kFlagAgg = 1u << 30;
 constexpr uint32_t kFlagPrefix = 2u << 30;
 constexpr uint32_t kValMask = (1u << 30) - 1;
-// Two shapes of the pass block over the same 4096-pair tile: 512 threads with
-// 8 pairs each, or 256 threads with 16 pairs each (more independent work per
-// thread, fewer warps; faster when a pass moves four or more arrays).
+// Two shapes of the pass block over the same 4096-pair tile: 256 threads with
+// 16 pairs each (more independent work per thread; 64 registers and a
+// two-slot staging ring, so four blocks fit on an SM), or 512 threads with 8
+// pairs each (three blocks), which is faster only for small passes of one key
+// word that stay in L2.
 constexpr int kTile = kPassTile;  // pairs per tile
 constexpr int kPassThreadsWide = 512, kPassThreadsDeep = 256;
-constexpr uint32_t kDeepMinArrays = 4;
-constexpr int kRing = 3;                          // staging buffers per block
-constexpr int kPassBlocksPerSM = 3;
+constexpr uint32_t kDeepMinArrays = 3;           // deep shape from this many arrays on,
+constexpr uint64_t kWideMaxPairs = 1ull << 22;   // or above this many pairs
+constexpr int kRing = 2;                         // staging buffers per block
+constexpr int kPassBlocksPerSM = 3;              // resident blocks of the 512-thread shape
+constexpr int kPassDeepBlocksPerSM = 4;          // of the 256-thread shape
 constexpr int kUpThreads = 256;
 
 // Exclusive scan in place over count entries of arr (shared or global memory)
@@ -187,7 +191,7 @@ struct PassSmem {
 };
 
 template <int RB, int THREADS>
-__global__ void __launch_bounds__(THREADS, kPassBlocksPerSM)
+__global__ void __launch_bounds__(THREADS, THREADS == 256 ? kPassDeepBlocksPerSM : kPassBlocksPerSM)
     onesweep_pass_kernel(const PassArgs a, const __grid_constant__ PassArrays arr) {
     constexpr int kPassThreads = THREADS;
     constexpr int BINS = 1 << RB, WARPS = THREADS / 32, ITEMS = kTile / THREADS, WITEMS = 32 * ITEMS;
@@ -430,8 +434,9 @@ static cudaError_t launch_pass_shape(const PassArgs& a, const PassArrays& arrays
 
 template <int RB>
 static cudaError_t launch_pass(const PassArgs& a, const PassArrays& arrays, uint32_t tiles, cudaStream_t s) {
-    return a.narr >= kDeepMinArrays ? launch_pass_shape<RB, kPassThreadsDeep>(a, arrays, tiles, s)
-                                    : launch_pass_shape<RB, kPassThreadsWide>(a, arrays, tiles, s);
+    return a.narr >= kDeepMinArrays || a.n > kWideMaxPairs
+               ? launch_pass_shape<RB, kPassThreadsDeep>(a, arrays, tiles, s)
+               : launch_pass_shape<RB, kPassThreadsWide>(a, arrays, tiles, s);
 }
 
 cudaError_t launch_onesweep_pass(uint32_t rb, const PassArgs& a, const PassArrays& arrays, uint32_t tiles,
