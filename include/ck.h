@@ -367,7 +367,8 @@ typedef struct ck_btree {
  * pass over the leaves, recomputes the D-bitmap (Sec. 4.3 rebuild, step 1):
  * refined = { D-offset[D-bit(Compress(key_{i-1}), Compress(key_i))] }, where
  * D-offset[q] is the position of the (q+1)-st set bit of dmask (Sec. 5.3).
- *   sorted_ck, sorted_rid  device, as produced by ck_sort (word-major ck).
+ *   sorted_ck, sorted_rid  device, as produced by ck_sort (word-major ck);
+ *             sorted_rid may be tree->leaf_rid itself (nothing is copied).
  *   dmask     HOST, ceil(key_bits / 64) words: the bitmap used by ck_extract.
  *   key_bits  8 * key_bytes of the column.
  *   tree      its shape is recomputed and written; its arrays are written.
@@ -385,7 +386,8 @@ ck_status ck_build_index(const uint32_t* sorted_ck, const uint32_t* sorted_rid, 
  * the compressed D-bit to, so the tree and the refined D-bitmap are
  * identical.  Inner entries' compressed highest keys are extracted with dmask.
  *   col         the key column (device) the row ids refer to.
- *   sorted_rid  device, n row ids in ascending key order (ties by row id).
+ *   sorted_rid  device, n row ids in ascending key order (ties by row id);
+ *               may be tree->leaf_rid itself (nothing is copied).
  *   dmask       HOST, ceil(8 * key_bytes / 64) words (as given to ck_extract).
  *   ck_words, fanout, fill, tree, refined_mask: as ck_build_index.
  * Errors: CK_EINVAL, CK_EOVERFLOW; a row id >= n is skipped and recorded as

@@ -60,7 +60,7 @@ __global__ void __launch_bounds__(256) leaf_kernel(const __grid_constant__ Btree
         const uint64_t i = i0 + lane;
         int32_t p = -1;
         if (i < n) {
-            leaf_rid[i] = a.rid[i];
+            if (leaf_rid) leaf_rid[i] = a.rid[i];  // NULL: the sort wrote the tree's row ids
             if (i > 0) {
                 const int32_t q = ck_dbit(a.ck, a.ld, a.K, a.nbits, i - 1, i);
                 if (q >= 0) p = doff[q];
@@ -113,7 +113,7 @@ __global__ void __launch_bounds__(256) leaf_kw_kernel(const __grid_constant__ Bt
         }
         int32_t p = -1;
         if (i < n) {
-            leaf_rid[i] = a.rid[i];
+            if (leaf_rid) leaf_rid[i] = a.rid[i];  // NULL: the sort wrote the tree's row ids
             if (i > 0) {
                 int32_t q = -1;  // compressed D-bit; -2: a bit above nbits differs
 #pragma unroll
@@ -187,7 +187,8 @@ cudaError_t launch_btree(const BtreeArgs& a, const ck_btree_shape& shape, ck_btr
     const uint64_t cap = (uint64_t)num_sms() * 8;
     uint64_t grid = (a.n + 255) / 256;
     const unsigned g = (unsigned)(grid < cap ? grid : cap);
-    uint32_t* lr = t->leaf_rid;
+    // row ids sorted straight into the tree's leaf array need no copy
+    uint32_t* lr = t->leaf_rid == a.rid ? nullptr : t->leaf_rid;
     uint16_t* ld = t->leaf_dbit;
     uint32_t* lh = t->leaf_high;
     const uint64_t n0 = shape.level_nodes[0];

@@ -274,7 +274,7 @@ __global__ void __launch_bounds__(256) leaf_keys_kernel(const KeyDesc k, uint64_
         int32_t p = -1;
         if (i < n) {
             const uint32_t b = rid[i];
-            leaf_rid[i] = b;
+            if (leaf_rid) leaf_rid[i] = b;  // NULL: the row ids already are the tree's
             if (i > 0) {
                 const uint32_t a = rid[i - 1];
                 if (a < n && b < n) p = key_dbit<VEC>(k, a, b);
@@ -379,7 +379,8 @@ cudaError_t launch_btree_keys(const KeyDesc& k, int vec, uint64_t n, const uint3
     }
     if (n == 0) return cudaSuccess;
     unsigned grid = grid_for(n, 256);
-    CK_DISPATCH_VEC(vec, leaf_keys_kernel, k, n, rid, f, t->leaf_rid, t->leaf_dbit, t->leaf_high, nodes0, refined,
+    uint32_t* lr = t->leaf_rid == rid ? nullptr : t->leaf_rid;
+    CK_DISPATCH_VEC(vec, leaf_keys_kernel, k, n, rid, f, lr, t->leaf_dbit, t->leaf_high, nodes0, refined,
                     status_ptr());
     count_launch();
     if (lv.inner_entries > 0) {

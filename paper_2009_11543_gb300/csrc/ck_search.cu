@@ -2,11 +2,11 @@
 // McIlroy and Rastogi's partial-key B+-tree; bit sources of Sec. 5.3) and the
 // lower-bound search of Sec. 4.3 that uses them.
 //
-// Partial keys: one thread per tree entry.  The pk positions after the
-// entry's offset are read one by one from the compressed key (a position of
-// the extraction mask; its bit index there is the position's rank in the
-// mask, counted from the most significant compressed bit), from the
-// reference key (an invariant position), or from the key row (any other).
+// Partial keys: one thread per tree entry, word-wide.  The pk positions after
+// the entry's offset form a window; the mask positions in it have consecutive
+// ranks in the extraction mask, so their bits are one run of the compressed
+// key (read as a 64-bit window) deposited at those positions; the invariant
+// positions take the reference key's window, any other the key row's.
 //
 // Search: one thread per query.  Inner nodes: binary search over the node's
 // highest keys, compared as full keys; every comparison also yields the D-bit
@@ -42,13 +42,12 @@ struct PkArgs {
     uint64_t n, inner;
     uint64_t rows;            // rows of the key column (0: no column)
     uint32_t K, nbits, key_bits, pk;
-    uint64_t emask[kMaxMaskWords];
-    uint64_t vmask[kMaxMaskWords];
-    uint32_t erank[kMaxMaskWords];  // set positions of emask before word w
-    uint32_t ref[kMaxKeyWords];     // reference key, big-endian words
+    // big-endian 32-bit words: position 32w + i is bit 31 - i of word w
+    uint32_t emask[kMaxKeyWords];
+    uint32_t vmask[kMaxKeyWords];
+    uint32_t ref[kMaxKeyWords];
+    uint32_t erank[kMaxKeyWords];  // set positions of emask before word w
 };
-
-__device__ __forceinline__ bool bit_of(const uint64_t* m, uint32_t p) { return (m[p >> 6] >> (63 - (p & 63))) & 1ull; }
 
 // Word w of row r (0 past the key).
 template <int VEC>
@@ -59,12 +58,32 @@ __device__ __forceinline__ uint32_t key_word(const KeyDesc& k, uint64_t r, uint3
     return c[w & 3];
 }
 
+// Positions [start, start + pk) of a big-endian word array (two words from
+// w = start / 32 on; hi and lo are words w and w + 1) as a pk-bit value, the
+// first position most significant.
+__device__ __forceinline__ uint32_t window_of(uint32_t hi, uint32_t lo, uint32_t start, uint32_t pk) {
+    const uint64_t v = ((uint64_t)hi << 32) | lo;
+    return (uint32_t)((v << (start & 31)) >> (64 - pk));
+}
+
 template <int VEC>
 __global__ void __launch_bounds__(kPkThreads) partial_keys_kernel(const __grid_constant__ PkArgs a,
                                                                    const __grid_constant__ KeyDesc col,
                                                                    uint32_t* __restrict__ leaf_pk,
                                                                    uint32_t* __restrict__ inner_pk,
                                                                    unsigned long long* status) {
+    __shared__ uint32_t em[kMaxKeyWords + 1], vm[kMaxKeyWords + 1], rf[kMaxKeyWords + 1], er[kMaxKeyWords + 1];
+    const uint32_t words = (a.key_bits + 31) / 32;
+    for (uint32_t i = threadIdx.x; i <= words; i += blockDim.x) {
+        const bool in = i < words;
+        em[i] = in ? a.emask[i] : 0u;
+        vm[i] = in ? a.vmask[i] : 0u;
+        rf[i] = in ? a.ref[i] : 0u;
+        er[i] = in ? a.erank[i] : a.nbits;
+    }
+    __syncthreads();
+    const uint32_t pk = a.pk;
+    const uint32_t all = pk == 32 ? 0xFFFFFFFFu : (1u << pk) - 1u;
     const uint64_t total = a.n + a.inner;
     for (uint64_t g = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; g < total;
          g += (uint64_t)gridDim.x * blockDim.x) {
@@ -74,34 +93,48 @@ __global__ void __launch_bounds__(kPkThreads) partial_keys_kernel(const __grid_c
         const uint64_t row = leaf ? a.leaf_rid[e] : a.inner_rid[e];
         const bool from_ck = leaf ? a.ck != nullptr : true;
         const uint32_t start = off == CK_NO_DBIT ? 0u : off + 1u;
-        uint32_t v = 0;
-        uint32_t cw_idx = 0xFFFFFFFFu, cw = 0, rw_idx = 0xFFFFFFFFu, rw = 0;
-        for (uint32_t t = 0; t < a.pk; ++t) {
-            const uint32_t p = start + t;
-            uint32_t b = 0;
-            if (p < a.key_bits) {
-                if (from_ck && bit_of(a.emask, p)) {          // (A) from the compressed key
-                    const uint32_t w = p >> 6, in = p & 63;
-                    const uint32_t q = a.erank[w] + (in ? (uint32_t)__popcll(a.emask[w] >> (64 - in)) : 0u);
-                    const uint32_t vb = a.nbits - 1 - q;      // bit index, least significant word first
-                    if ((vb >> 5) != cw_idx) {
-                        cw_idx = vb >> 5;
-                        cw = leaf ? a.ck[(uint64_t)cw_idx * a.ld + e] : a.high_ck[e * a.K + cw_idx];
+        uint32_t v = 0, rest = all;
+        if (start < a.key_bits) {
+            const uint32_t w = start >> 5;
+            const uint32_t wv = window_of(vm[w], vm[w + 1], start, pk);
+            const uint32_t wr = window_of(rf[w], rf[w + 1], start, pk);
+            if (from_ck) {                                    // (A) a run of the compressed key
+                const uint32_t we = window_of(em[w], em[w + 1], start, pk);
+                const uint32_t c = __popc(we);
+                if (c) {
+                    const uint32_t q0 = er[w] + ((start & 31) ? __popc(em[w] >> (32 - (start & 31))) : 0u);
+                    const uint32_t lo = a.nbits - q0 - c;     // integer bit of the run's last rank
+                    const uint32_t k0 = lo >> 5;
+                    uint32_t x0, x1;
+                    if (leaf) {
+                        x0 = a.ck[(uint64_t)k0 * a.ld + e];
+                        x1 = k0 + 1 < a.K ? a.ck[(uint64_t)(k0 + 1) * a.ld + e] : 0u;
+                    } else {
+                        x0 = a.high_ck[e * a.K + k0];
+                        x1 = k0 + 1 < a.K ? a.high_ck[e * a.K + k0 + 1] : 0u;
                     }
-                    b = (cw >> (vb & 31)) & 1u;
-                } else if (!bit_of(a.vmask, p)) {             // (B) invariant: the reference key
-                    b = (a.ref[p >> 5] >> (31 - (p & 31))) & 1u;
-                } else if (row < a.rows) {                    // (C) option b: the record's key
-                    if ((p >> 5) != rw_idx) {
-                        rw_idx = p >> 5;
-                        rw = key_word<VEC>(col, row, rw_idx);
+                    const uint32_t run = (uint32_t)(((((uint64_t)x1 << 32) | x0) >> (lo & 31)) & ((1ull << c) - 1));
+                    // deposit the run, first rank first, at the window's mask positions
+                    uint32_t m = we;
+                    for (int r = (int)c - 1; r >= 0; --r) {
+                        const uint32_t top = 31u - __clz(m);
+                        v |= ((run >> r) & 1u) << top;
+                        m &= ~(1u << top);
                     }
-                    b = (rw >> (31 - (p & 31))) & 1u;
+                }
+                rest &= ~we;
+            }
+            v |= wr & ~wv & rest;                             // (B) invariant: the reference key
+            const uint32_t need = wv & rest;                  // (C) option b: the record's key
+            if (need) {
+                if (row < a.rows) {
+                    const uint32_t wr0 = key_word<VEC>(col, row, w), wr1 = key_word<VEC>(col, row, w + 1);
+                    v |= window_of(wr0, wr1, start, pk) & need;
                 } else {                                      // no such row (or no column): read as 0
                     report(status, CK_EINVAL, row);
                 }
             }
-            v = (v << 1) | b;
+            // positions past the key's end read 0: the windows hold zeros there
         }
         if (leaf) leaf_pk[e] = v;
         else inner_pk[e] = v;
@@ -313,12 +346,16 @@ ck_status ck_partial_keys(const ck_btree* tree, const uint32_t* sorted_ck, uint3
     static thread_local PkArgs a;
     memset(&a, 0, sizeof(a));
     a.key_bits = 8 * key_bytes;
-    load_mask(emask, a.key_bits, a.emask);
-    load_mask(vmask, a.key_bits, a.vmask);
+    uint64_t e64[kMaxMaskWords], v64[kMaxMaskWords];
+    load_mask(emask, a.key_bits, e64);
+    load_mask(vmask, a.key_bits, v64);
     uint32_t nbits = 0;
-    for (uint32_t w = 0; w < kMaxMaskWords; ++w) {
+    for (uint32_t w = 0; w < kMaxKeyWords; ++w) {
+        const uint32_t sh = (w & 1) ? 0 : 32;
+        a.emask[w] = (uint32_t)(e64[w >> 1] >> sh);
+        a.vmask[w] = (uint32_t)(v64[w >> 1] >> sh);
         a.erank[w] = nbits;
-        nbits += (uint32_t)__builtin_popcountll(a.emask[w]);
+        nbits += (uint32_t)__builtin_popcount(a.emask[w]);
     }
     if (nbits > 32 * ck_words) return CK_EINVAL;
     if (!sorted_ck && !col) return CK_EINVAL;  // the leaves' bits need a source

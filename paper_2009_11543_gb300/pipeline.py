@@ -57,6 +57,7 @@ class Rebuild:
         self.ws = torch.empty(max(wsb, 256), dtype=torch.uint8, device=dev)
         self.shape = ck.ck_btree_plan(self.n, fanout, fill)
         self.tree = ck.alloc_btree(self.shape, self.K, dev)
+        self.tree["leaf_rid"] = self.rid_sorted      # the sort writes the leaves' row ids in place
         self.refined = torch.empty(ck.mask_words(self.key_bits), dtype=torch.int64, device=dev)
 
     def extract(self, stream=None):
