@@ -481,29 +481,34 @@ ck_status ck_partial_keys(const ck_btree* tree, const uint32_t* sorted_ck, uint3
                           uint32_t pk, uint32_t* leaf_pk, uint32_t* inner_pk, ck_stream stream);
 
 /* ck_search -- lower-bound search of a batch of query keys (Sec. 4.3,
- * Search).  In an inner node the query is compared with the entries' highest
- * keys as full keys (binary search over the node; each comparison also gives
- * the D-bit of the two keys).  In a leaf the entries are scanned in order
- * with their offsets and partial keys (Bohannon et al.): with d the D-bit of
- * the query against the previous key (which the query exceeds), an entry
- * whose offset is below d is above the query, one whose offset is above d is
- * below it, and at offset = d the partial key decides unless it equals the
- * query's bits at the same positions; only then is the entry's full key read.
+ * Search).  In a leaf the entries are scanned in order with their offsets and
+ * partial keys (Bohannon et al.): with d the D-bit of the query against the
+ * previous key (which the query exceeds), an entry whose offset is below d is
+ * above the query, one whose offset is above d is below it, and at offset = d
+ * the partial key decides unless it equals the query's bits at the same
+ * positions; only then is the entry's full key read.  Inner nodes either
+ * compare the query with the entries' highest keys as full keys (inner_pk
+ * NULL: the paper's search; binary search over the node, each comparison also
+ * giving the D-bit that starts the leaf scan), or are scanned the same way
+ * as leaves with the inner entries' partial keys (inner_pk given; the D-bit
+ * state carries from a node to its child, whose first key follows the highest
+ * key of the entry before).  Both give the same result.
  *   tree, col  the built tree and the key column its row ids refer to.
  *   leaf_pk    device [n], from ck_partial_keys with the same pk.
+ *   inner_pk   device [inner_entries] from the same call, or NULL.
  *   queries    column of q keys with col's kind and key_bytes.
  *   pos_out    device [q]: the first sorted position whose key is >= the
  *              query (n if there is none).
  *   rid_out    device [q] or NULL: the row id at pos_out when that key equals
  *              the query (the smallest row id among equal keys), else
  *              CK_NO_ROW.
- *   derefs_out device [q] or NULL: full keys read in the leaf per query.
+ *   derefs_out device [q] or NULL: full keys read per query.
  * Errors: CK_EINVAL (kind or width mismatch, pk outside 1 .. 32, a tree
  * whose n is not col->n; a row id >= n in the tree is recorded in the device
  * status word and ends that query's search with pos_out = n). */
-ck_status ck_search(const ck_btree* tree, const ck_column* col, const uint32_t* leaf_pk, uint32_t pk,
-                    const ck_column* queries, uint32_t* pos_out, uint32_t* rid_out, uint32_t* derefs_out,
-                    ck_stream stream);
+ck_status ck_search(const ck_btree* tree, const ck_column* col, const uint32_t* leaf_pk, const uint32_t* inner_pk,
+                    uint32_t pk, const ck_column* queries, uint32_t* pos_out, uint32_t* rid_out,
+                    uint32_t* derefs_out, ck_stream stream);
 
 /* ---------------------------------------------------------------------------
  * ck_model_separators -- model-proposed inner separators (not in the paper).

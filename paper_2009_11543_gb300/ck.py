@@ -137,7 +137,7 @@ def _lib():
         lib.ck_insert_batch.argtypes = [CP, P, CP, U64, P, P, P, ctypes.c_size_t, P]
         lib.ck_partial_key_mask.argtypes = [P, P, U32, U32, P]
         lib.ck_partial_keys.argtypes = [ctypes.POINTER(ck_btree), P, U32, P, P, P, CP, U32, U32, P, P, P]
-        lib.ck_search.argtypes = [ctypes.POINTER(ck_btree), CP, P, U32, CP, P, P, P, P]
+        lib.ck_search.argtypes = [ctypes.POINTER(ck_btree), CP, P, P, U32, CP, P, P, P, P]
         lib.ck_device_status.argtypes = [ctypes.POINTER(U64)]
         lib.ck_status_string.argtypes = [I]
         lib.ck_status_string.restype = ctypes.c_char_p
@@ -525,9 +525,11 @@ def ck_partial_keys(shape: ck_btree_shape, arrays: dict, sorted_ck: torch.Tensor
 
 def ck_search(shape: ck_btree_shape, arrays: dict, keys: torch.Tensor, leaf_pk: torch.Tensor, pk: int,
               queries: torch.Tensor, kind=None, pos: torch.Tensor | None = None, rid: torch.Tensor | None = None,
-              derefs: torch.Tensor | None = None, want_rid: bool = True, want_derefs: bool = False, stream=None):
+              derefs: torch.Tensor | None = None, want_rid: bool = True, want_derefs: bool = False,
+              inner_pk: torch.Tensor | None = None, stream=None):
     """Lower-bound search of every query row; returns (pos, rid, derefs)
-    device int32 tensors (rid / derefs None unless wanted or given)."""
+    device int32 tensors (rid / derefs None unless wanted or given).  With
+    inner_pk the inner nodes are scanned by partial keys too."""
     t = _tree(shape, arrays)
     col, qcol = column(keys, kind), column(queries, kind)
     q = int(qcol.n)
@@ -538,8 +540,8 @@ def ck_search(shape: ck_btree_shape, arrays: dict, keys: torch.Tensor, leaf_pk: 
         rid = torch.empty(max(q, 1), dtype=torch.int32, device=dev)
     if derefs is None and want_derefs:
         derefs = torch.empty(max(q, 1), dtype=torch.int32, device=dev)
-    _check(_lib().ck_search(ctypes.byref(t), ctypes.byref(col), _ptr(leaf_pk), pk, ctypes.byref(qcol), _ptr(pos),
-                            _ptr(rid), _ptr(derefs), _stream(stream)), "ck_search")
+    _check(_lib().ck_search(ctypes.byref(t), ctypes.byref(col), _ptr(leaf_pk), _ptr(inner_pk), pk,
+                            ctypes.byref(qcol), _ptr(pos), _ptr(rid), _ptr(derefs), _stream(stream)), "ck_search")
     return pos, rid, derefs
 
 

@@ -148,6 +148,8 @@ struct SearchArgs {
     const uint32_t* inner_child;
     const uint32_t* inner_high;
     const uint32_t* inner_rid;
+    const uint16_t* inner_dbit;
+    const uint32_t* inner_pk;  // NULL: inner nodes compare full keys
     uint64_t n, q;
     uint32_t f, levels, pk;
     uint64_t level_entries[CK_MAX_LEVELS];
@@ -175,6 +177,55 @@ __device__ __forceinline__ int cmp_dbit(const KeyRef& a, const KeyRef& b, int32_
     return 0;
 }
 
+constexpr uint64_t kScanError = ~0ull;
+
+// Scans entries i .. t - 1 of one level in key order (offsets dbit, partial
+// keys pks, row ids rids), knowing that Q is above the key before entry i and
+// that d is their D-bit.  Returns the first entry whose key is >= Q (t if
+// none; kScanError after a bad row id) and sets eq when a full comparison
+// found that key equal to Q.  On return d is still the D-bit of Q against the
+// key before the returned entry.
+template <int VEC>
+__device__ __forceinline__ uint64_t scan_level(const uint16_t* dbit, const uint32_t* pks, const uint32_t* rids,
+                                               uint64_t i, uint64_t t, int32_t& d, const KeyDesc& col,
+                                               const KeyDesc& qk, uint64_t j, uint32_t pk, uint64_t n, bool& eq,
+                                               uint32_t& derefs, unsigned long long* status) {
+    eq = false;
+    for (; i < t; ++i) {
+        const uint32_t o = dbit[i];
+        if (o == CK_NO_DBIT) continue;  // equal to the previous key: still below Q
+        if ((int32_t)o < d) return i;
+        if ((int32_t)o > d) continue;
+        // o == d: compare Q's bits o + 1 .. o + pk with the partial key
+        const uint32_t p0 = o + 1, w = p0 >> 5;
+        const uint64_t win = ((uint64_t)key_word<VEC>(qk, j, w) << 32) | key_word<VEC>(qk, j, w + 1);
+        const uint32_t qb = (uint32_t)((win << (p0 & 31)) >> (64 - pk));
+        const uint32_t x = qb ^ pks[i];
+        if (x) {
+            const uint32_t lead = __clz(x) - (32 - pk);  // first differing bit among the pk
+            if ((qb >> (pk - 1 - lead)) & 1u) {
+                d = (int32_t)(p0 + lead);                // Q above key_i
+                continue;
+            }
+            return i;
+        }
+        const uint32_t r = rids[i];
+        if (r >= n) {
+            report(status, CK_EINVAL, i);
+            return kScanError;
+        }
+        ++derefs;
+        int32_t dd;
+        const int c = cmp_dbit<VEC>(KeyRef{&col, r}, KeyRef{&qk, j}, &dd);
+        if (c >= 0) {
+            eq = c == 0;
+            return i;
+        }
+        d = dd;
+    }
+    return t;
+}
+
 template <int VEC>
 __global__ void __launch_bounds__(kSearchThreads) search_kernel(const __grid_constant__ SearchArgs a,
                                                                 const __grid_constant__ KeyDesc col,
@@ -189,8 +240,61 @@ __global__ void __launch_bounds__(kSearchThreads) search_kernel(const __grid_con
         bool found = false;
         uint32_t derefs = 0;
         if (a.n == 0) goto done;
+        if (a.inner_pk) {
+            // ---- every level scanned with offsets and partial keys; the state d
+            //      (Q against the key before the current node) carries down, since
+            //      the key before child i's first entry is entry i - 1's highest key
+            uint64_t node = 0;
+            bool has_prev = false;  // false on the leftmost path: no key before the node
+            int32_t d = -1;
+            for (int32_t l = (int32_t)a.levels - 1; l >= 0; --l) {
+                const bool inner = l >= 1;
+                const uint64_t base = inner ? a.offset[l] : 0;
+                const uint64_t m = inner ? a.level_entries[l] : a.n;
+                const uint64_t s = node * a.f, t = min(s + a.f, m);
+                const uint16_t* dbit = inner ? a.inner_dbit + base : a.leaf_dbit;
+                const uint32_t* pks = inner ? a.inner_pk + base : a.leaf_pk;
+                const uint32_t* rids = inner ? a.inner_rid + base : a.leaf_rid;
+                uint64_t i = s;
+                bool eq = false, first_ge = false;
+                if (!has_prev) {  // the node's first key has no offset: compare it in full
+                    const uint32_t r = rids[s];
+                    if (r >= a.n) {
+                        report(status, CK_EINVAL, s);
+                        goto done;
+                    }
+                    ++derefs;
+                    int32_t dd;
+                    const int c = cmp_dbit<VEC>(KeyRef{&col, r}, Q, &dd);
+                    if (c >= 0) {
+                        eq = c == 0;
+                        first_ge = true;
+                    } else {
+                        d = dd;
+                        has_prev = true;
+                        i = s + 1;
+                    }
+                }
+                if (!first_ge) {
+                    i = scan_level<VEC>(dbit, pks, rids, i, t, d, col, qk, j, a.pk, a.n, eq, derefs, status);
+                    if (i == kScanError) goto done;
+                }
+                if (i == t) {  // Q above every key under this node: only at the root or the last leaf
+                    pos = inner ? a.n : t;
+                    goto done;
+                }
+                if (!inner) {
+                    pos = i;
+                    found = eq;
+                    goto done;
+                }
+                node = a.inner_child[base + i];
+            }
+            goto done;
+        }
         {
-            // ---- inner levels: the first entry of the node whose highest key is >= Q
+            // ---- inner levels compare full keys (Sec. 4.3): the first entry of
+            //      the node whose highest key is >= Q, by binary search
             uint64_t node = 0;
             int64_t fence = -1;  // sorted index of the last highest key found below Q
             int32_t fence_d = -1;
@@ -241,43 +345,12 @@ __global__ void __launch_bounds__(kSearchThreads) search_kernel(const __grid_con
                     i = 1;
                 }
             }
-            const uint32_t pk = a.pk;
-            for (; i < t; ++i) {
-                const uint32_t o = a.leaf_dbit[i];
-                if (o == CK_NO_DBIT) continue;  // equal to the previous key: still below Q
-                if ((int32_t)o < d) {
-                    pos = i;
-                    goto done;
-                }
-                if ((int32_t)o > d) continue;
-                // o == d: compare Q's bits o + 1 .. o + pk with the partial key
-                const uint32_t p0 = o + 1, w = p0 >> 5;
-                const uint64_t win = ((uint64_t)key_word<VEC>(qk, j, w) << 32) | key_word<VEC>(qk, j, w + 1);
-                const uint32_t qb = (uint32_t)((win << (p0 & 31)) >> (64 - pk));
-                const uint32_t x = qb ^ a.leaf_pk[i];
-                if (x) {
-                    const uint32_t lead = __clz(x) - (32 - pk);  // first differing bit among the pk
-                    if ((qb >> (pk - 1 - lead)) & 1u) {
-                        d = (int32_t)(p0 + lead);                // Q above key_i
-                        continue;
-                    }
-                    pos = i;
-                    goto done;
-                }
-                const uint32_t r = a.leaf_rid[i];
-                if (r >= a.n) {
-                    report(status, CK_EINVAL, i);
-                    goto done;
-                }
-                ++derefs;
-                const int c = cmp_dbit<VEC>(KeyRef{&col, r}, Q, &d);
-                if (c >= 0) {
-                    pos = i;
-                    found = c == 0;
-                    goto done;
-                }
-            }
-            pos = t;
+            bool eq = false;
+            i = scan_level<VEC>(a.leaf_dbit, a.leaf_pk, a.leaf_rid, i, t, d, col, qk, j, a.pk, a.n, eq, derefs,
+                                status);
+            if (i == kScanError) goto done;
+            pos = i;
+            found = eq;
         }
     done:
         pos_out[j] = (uint32_t)pos;
@@ -389,9 +462,9 @@ ck_status ck_partial_keys(const ck_btree* tree, const uint32_t* sorted_ck, uint3
     return cudaGetLastError() == cudaSuccess ? CK_OK : CK_ECUDA;
 }
 
-ck_status ck_search(const ck_btree* tree, const ck_column* col, const uint32_t* leaf_pk, uint32_t pk,
-                    const ck_column* queries, uint32_t* pos_out, uint32_t* rid_out, uint32_t* derefs_out,
-                    ck_stream stream) {
+ck_status ck_search(const ck_btree* tree, const ck_column* col, const uint32_t* leaf_pk, const uint32_t* inner_pk,
+                    uint32_t pk, const ck_column* queries, uint32_t* pos_out, uint32_t* rid_out,
+                    uint32_t* derefs_out, ck_stream stream) {
     if (!tree || pk == 0 || pk > CK_MAX_PARTIAL_KEY_BITS) return CK_EINVAL;
     KeyDesc ck_, qk;
     int vc = 1, vq = 1;
@@ -405,6 +478,7 @@ ck_status ck_search(const ck_btree* tree, const ck_column* col, const uint32_t* 
     if (sh.n > 0 && (!leaf_pk || !tree->leaf_rid || !tree->leaf_dbit || sh.levels == 0 || sh.entries_per_node == 0))
         return CK_EINVAL;
     if (sh.levels > 1 && (!tree->inner_child || !tree->inner_high || !tree->inner_high_rid)) return CK_EINVAL;
+    if (sh.levels > 1 && inner_pk && !tree->inner_dbit) return CK_EINVAL;
     SearchArgs a;
     memset(&a, 0, sizeof(a));
     a.leaf_rid = tree->leaf_rid;
@@ -413,6 +487,8 @@ ck_status ck_search(const ck_btree* tree, const ck_column* col, const uint32_t* 
     a.inner_child = tree->inner_child;
     a.inner_high = tree->inner_high;
     a.inner_rid = tree->inner_high_rid;
+    a.inner_dbit = tree->inner_dbit;
+    a.inner_pk = sh.levels > 1 ? inner_pk : nullptr;
     a.n = sh.n;
     a.q = q;
     a.f = sh.entries_per_node;

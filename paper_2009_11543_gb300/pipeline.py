@@ -100,10 +100,17 @@ class Rebuild:
             leaf_pk=getattr(self, "leaf_pk", None), inner_pk=getattr(self, "inner_pk", None), stream=stream)
         return self.leaf_pk, self.inner_pk
 
-    def search(self, queries: torch.Tensor, pos=None, rid=None, derefs=None, want_derefs: bool = False, stream=None):
-        """Lower-bound search of the query rows in the built tree (Sec. 4.3)."""
+    def search(self, queries: torch.Tensor, pos=None, rid=None, derefs=None, want_derefs: bool = False,
+               inner_partial: bool = False, stream=None):
+        """Lower-bound search of the query rows in the built tree (Sec. 4.3):
+        full keys in the inner nodes, partial keys in the leaves;
+        inner_partial=True scans the inner nodes by partial keys as well
+        (same result; slower on wide nodes, where the binary search over full
+        keys takes fewer dependent steps)."""
         return ck.ck_search(self.shape, self.tree, self.keys, self.leaf_pk, self.pk, queries, kind=self.kind,
-                            pos=pos, rid=rid, derefs=derefs, want_derefs=want_derefs, stream=stream)
+                            pos=pos, rid=rid, derefs=derefs, want_derefs=want_derefs,
+                            inner_pk=self.inner_pk if inner_partial and self.shape.inner_entries else None,
+                            stream=stream)
 
     def run(self, stream=None):
         """One full rebuild: extract, sort, bulk load (+ refined D-bitmap)."""
