@@ -169,6 +169,20 @@ ck_status ck_distinction_bits(const ck_column* col, const uint32_t* order, uint6
 ck_status ck_extract(const ck_column* col, const uint64_t* dmask, uint32_t ck_words, uint32_t* ck_out,
                      ck_stream stream);
 
+/* ck_extract_hist -- ck_extract that also counts, in the same pass over the
+ * keys, the radix digits of the compressed keys: hist[q][v] = the number of
+ * keys whose digit q (bits [q * digit_bits, (q + 1) * digit_bits) of the
+ * compressed value) is v, for q < passes = ceil(popcount(dmask) / digit_bits).
+ * Passing hist to ck_sort (ck_sort_opts.hist, same digit_bits) spares the sort
+ * a read of all compressed keys.
+ *   digit_bits  4 .. 11 (0 = 8), as the sort will use.
+ *   hist        device, passes * 2^digit_bits uint32; zeroed and written.
+ * Other arguments and errors as ck_extract (CK_EINVAL also for a bad
+ * digit_bits, or hist NULL with passes > 0).  With more than 16 KB of
+ * counters the digits are counted by a second kernel over ck_out. */
+ck_status ck_extract_hist(const ck_column* col, const uint64_t* dmask, uint32_t ck_words, uint32_t* ck_out,
+                          uint32_t digit_bits, uint32_t* hist, ck_stream stream);
+
 /* ---------------------------------------------------------------------------
  * ck_sort -- stable least-significant-digit radix sort of the pairs
  * (compressed key, row id) by compressed key (the sort step of Sec. 5, done
@@ -197,6 +211,10 @@ typedef struct ck_sort_opts {
                             recorded on the stream before the first digit pass and event
                             p + 1 after pass p (passes = ceil(nbits / digit_bits)).  NULL
                             records nothing. */
+    const uint32_t* hist; /* optional, device [passes][2^digit_bits]: the digit counts of
+                            ck_in as ck_extract_hist writes them (same digit_bits); the
+                            sort then skips its own counting pass over the keys.  NULL:
+                            counted here. */
 } ck_sort_opts;
 
 /* Only the permutation is wanted: ck_out is used as scratch and its contents

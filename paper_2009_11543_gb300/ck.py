@@ -37,7 +37,7 @@ EXPORTED = ["ck_variant_bits", "ck_distinction_bits", "ck_extract", "ck_sort_wor
             "ck_sort_learned_workspace_bytes", "ck_sort_learned", "ck_mlp_workspace_bytes", "ck_mlp_loss_grad",
             "ck_build_batched", "ck_graph_capture_batched", "ck_graph_launch", "ck_graph_destroy",
             "ck_autotune_sort", "ck_model_separators", "ck_insert_workspace_bytes", "ck_insert_batch", "ck_encode_key",
-            "ck_partial_key_mask", "ck_partial_keys", "ck_search"]
+            "ck_partial_key_mask", "ck_partial_keys", "ck_search", "ck_extract_hist"]
 CK_SORT_STATIC_SCRATCH_BYTES = 32 << 20
 
 
@@ -54,7 +54,7 @@ class ck_column(ctypes.Structure):
 
 class ck_sort_opts(ctypes.Structure):
     _fields_ = [("digit_bits", ctypes.c_uint32), ("spin_limit", ctypes.c_uint32), ("inject", ctypes.c_uint32),
-                ("flags", ctypes.c_uint32), ("pass_events", ctypes.c_void_p)]
+                ("flags", ctypes.c_uint32), ("pass_events", ctypes.c_void_p), ("hist", ctypes.c_void_p)]
 
 
 class ck_learned_opts(ctypes.Structure):
@@ -109,6 +109,7 @@ def _lib():
         lib.ck_variant_bits.argtypes = [CP, U64, P, P]
         lib.ck_distinction_bits.argtypes = [CP, P, P, P]
         lib.ck_extract.argtypes = [CP, P, U32, P, P]
+        lib.ck_extract_hist.argtypes = [CP, P, U32, P, U32, P, P]
         lib.ck_sort_workspace_bytes.argtypes = [U64, U32, U32, ctypes.POINTER(ck_sort_opts)]
         lib.ck_sort_workspace_bytes.restype = ctypes.c_size_t
         lib.ck_sort.argtypes = [P, P, P, P, U64, U32, U32, ctypes.POINTER(ck_sort_opts), P, ctypes.c_size_t, P]
@@ -295,8 +296,25 @@ def ck_extract(keys: torch.Tensor, dmask: np.ndarray, ck_words: int | None = Non
     return out
 
 
-def _opts(digit_bits=0, spin_limit=0, inject=0, pass_events=None, flags=0):
-    return ck_sort_opts(digit_bits, spin_limit, inject, flags, pass_events)
+def ck_extract_hist(keys: torch.Tensor, dmask: np.ndarray, ck_words: int, digit_bits: int = 8,
+                    out: torch.Tensor | None = None, hist: torch.Tensor | None = None, kind=None, stream=None):
+    """Compressed keys and, in the same pass, their radix digit counts;
+    returns (ck, hist) with hist [passes, 2^digit_bits] int32 (uint32 counts)."""
+    col = column(keys, kind)
+    m = np.ascontiguousarray(np.asarray(dmask, np.uint64))
+    passes = (popcount(m) + digit_bits - 1) // digit_bits
+    if out is None:
+        out = ck_buffer(ck_words, col.n, keys.device)
+    if hist is None:
+        hist = torch.empty((max(passes, 1), 1 << digit_bits), dtype=torch.int32, device=keys.device)
+    _check(_lib().ck_extract_hist(ctypes.byref(col), _ptr(m), ck_words, _ptr(out), digit_bits, _ptr(hist),
+                                  _stream(stream)), "ck_extract_hist")
+    return out, hist
+
+
+def _opts(digit_bits=0, spin_limit=0, inject=0, pass_events=None, flags=0, hist=None):
+    return ck_sort_opts(digit_bits, spin_limit, inject, flags, pass_events,
+                        hist.data_ptr() if hist is not None else None)
 
 
 def event_handles(events) -> ctypes.Array:
@@ -314,10 +332,10 @@ def ck_sort_workspace_bytes(n: int, ck_words: int, nbits: int, digit_bits: int =
 
 def ck_sort(ck_in: torch.Tensor, rid_in: torch.Tensor | None, ck_out: torch.Tensor, rid_out: torch.Tensor, n: int,
             ck_words: int, nbits: int, ws: torch.Tensor, digit_bits: int = 0, spin_limit: int = 0, inject: int = 0,
-            pass_events=None, perm_only: bool = False, stream=None) -> None:
+            pass_events=None, perm_only: bool = False, hist: torch.Tensor | None = None, stream=None) -> None:
     o = _opts(digit_bits, spin_limit, inject,
               ctypes.cast(pass_events, ctypes.c_void_p) if pass_events is not None else None,
-              CK_SORT_PERM_ONLY if perm_only else 0)
+              CK_SORT_PERM_ONLY if perm_only else 0, hist)
     _check(_lib().ck_sort(_ptr(ck_in), _ptr(rid_in), _ptr(ck_out), _ptr(rid_out), n, ck_words, nbits,
                           ctypes.byref(o), _ptr(ws), ws.numel() * ws.element_size(), _stream(stream)), "ck_sort")
 

@@ -200,6 +200,37 @@ ck_status ck_extract(const ck_column* col, const uint64_t* dmask, uint32_t ck_wo
     return cuda_status(launch_extract(k, vec, col->n, CK_LD(col->n), plan, ck_out, s));
 }
 
+ck_status ck_extract_hist(const ck_column* col, const uint64_t* dmask, uint32_t ck_words, uint32_t* ck_out,
+                          uint32_t digit_bits, uint32_t* hist, ck_stream stream) {
+    if (digit_bits == 0) digit_bits = 8;
+    if (digit_bits < 4 || digit_bits > 11) return CK_EINVAL;
+    KeyDesc k;
+    int vec = 1;
+    if (!make_key_desc(col, &k, &vec) || !dmask || ck_words == 0 || (col->n > 0 && !ck_out)) return CK_EINVAL;
+    const uint32_t key_bits = 8 * k.key_bytes;
+    if (!mask_fits(dmask, key_bits)) return CK_EINVAL;
+    const uint32_t nbits = popcount64(dmask, key_bits);
+    if (nbits > 32u * ck_words) return CK_EOVERFLOW;
+    const uint32_t passes = (nbits + digit_bits - 1) / digit_bits;
+    if (passes > 0 && !hist) return CK_EINVAL;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const size_t hist_bytes = sizeof(uint32_t) * ((size_t)passes << digit_bits);
+    if (passes > 0) {
+        const cudaError_t e = cudaMemsetAsync(hist, 0, hist_bytes, s);
+        if (e != cudaSuccess) return CK_ECUDA;
+    }
+    if (col->n == 0) return CK_OK;
+    if (nbits == 0)
+        return cuda_status(cudaMemsetAsync(ck_out, 0, sizeof(uint32_t) * (size_t)ck_words * CK_LD(col->n), s));
+    static thread_local ExtractPlan plan;
+    make_extract_plan(k, dmask, ck_words, &plan);
+    if (hist_bytes <= kExtractHistMaxBytes)  // counted while extracting
+        return cuda_status(launch_extract(k, vec, col->n, CK_LD(col->n), plan, ck_out, s, hist, digit_bits, passes));
+    const cudaError_t e = launch_extract(k, vec, col->n, CK_LD(col->n), plan, ck_out, s);
+    if (e != cudaSuccess) return CK_ECUDA;
+    return cuda_status(launch_upsweep_all(ck_out, col->n, CK_LD(col->n), ck_words, nbits, digit_bits, hist, s));
+}
+
 size_t ck_sort_workspace_bytes(uint64_t n, uint32_t ck_words, uint32_t nbits, const ck_sort_opts* opts) {
     SortPlan p;
     if (!make_sort_plan(n, ck_words, nbits, opts ? opts->digit_bits : 0, &p)) return 0;
@@ -225,7 +256,8 @@ ck_status ck_sort(const uint32_t* ck_in, const uint32_t* rid_in, uint32_t* ck_ou
     if (!status_ptr()) return CK_ECUDA;
     cudaEvent_t* ev = opts ? static_cast<cudaEvent_t*>(opts->pass_events) : nullptr;
     return cuda_status(run_sort(p, ck_in, rid_in, ck_out, rid_out, n, nbits, spin, inject, flags, ev,
-                                static_cast<unsigned char*>(ws), reinterpret_cast<cudaStream_t>(stream)));
+                                static_cast<unsigned char*>(ws), reinterpret_cast<cudaStream_t>(stream),
+                                opts ? opts->hist : nullptr));
 }
 
 ck_status ck_btree_plan(uint64_t n, uint32_t fanout, float fill, ck_btree_shape* shape) {

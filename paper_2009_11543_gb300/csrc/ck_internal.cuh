@@ -239,8 +239,15 @@ struct ExtractPlan {
     uint32_t mv[5][kMaxKeyWords];    // move masks of the compress network
     uint8_t pc[kMaxKeyWords];        // popcount of mask[w]
 };
+// hist (device, passes * 2^rb counters, zeroed by the caller) != NULL: the
+// digit counts of the compressed keys are added to it in the same pass.
 cudaError_t launch_extract(const KeyDesc& k, int vec, uint64_t n, uint64_t ld, const ExtractPlan& plan,
-                           uint32_t* ck_out, cudaStream_t s);
+                           uint32_t* ck_out, cudaStream_t s, uint32_t* hist = nullptr, uint32_t rb = 0,
+                           uint32_t passes = 0);
+constexpr size_t kExtractHistMaxBytes = 16 * 1024;  // counters the fused extraction keeps in shared memory
+// All digit histograms of compressed keys already in memory (the sort's upsweep).
+cudaError_t launch_upsweep_all(const uint32_t* ck, uint64_t n, uint64_t ld, uint32_t K, uint32_t nbits, uint32_t rb,
+                               uint32_t* hist, cudaStream_t s);
 constexpr uint32_t kDefaultSpin = 1u << 22;  // polls before a device wait gives up
 
 struct InnerLevels {
@@ -294,7 +301,7 @@ struct SortPlan {
 bool make_sort_plan(uint64_t n, uint32_t K, uint32_t nbits, uint32_t digit_bits, SortPlan* p, uint64_t ld = 0);
 cudaError_t run_sort(const SortPlan& p, const uint32_t* ck_in, const uint32_t* rid_in, uint32_t* ck_out,
                      uint32_t* rid_out, uint64_t n, uint32_t nbits, uint32_t spin_limit, uint32_t inject,
-                     uint32_t flags, cudaEvent_t* pass_events, unsigned char* ws, cudaStream_t s);
+                     uint32_t flags, cudaEvent_t* pass_events, unsigned char* ws, cudaStream_t s, const uint32_t* hist_in = nullptr);
 
 struct BtreeArgs {
     const uint32_t* ck;  // word-major, K words, leading dimension ld

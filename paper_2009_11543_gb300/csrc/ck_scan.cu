@@ -116,18 +116,51 @@ struct WordPlan {
     uint32_t mask, mv[5], pc, pad;
 };
 
+// Digit counts of the compressed keys, gathered while they are extracted (the
+// histograms a radix sort of them needs first): digit q of a key is bits
+// [q * rb, q * rb + rb) of its compressed value and is counted when the word
+// holding its lowest bit is emitted (the word above it, emitted just before,
+// supplies the rest).  sm: passes * 2^rb shared counters; NULL: no counting.
+struct HistSink {
+    uint32_t* sm;
+    uint32_t rb, passes;
+};
+
+__device__ __forceinline__ void count_digits(const HistSink& h, uint32_t k, uint32_t prev, uint32_t v) {
+    if (h.rb == 8) {  // the bytes of the word, least significant first, are digits 4k .. 4k + 3
+#pragma unroll
+        for (uint32_t b = 0; b < 4; ++b)
+            if (4u * k + b < h.passes) atomicAdd(&h.sm[((4u * k + b) << 8) | ((v >> (8u * b)) & 255u)], 1u);
+        return;
+    }
+    const uint32_t lo_bit = 32u * k, bins = 1u << h.rb;
+    const uint32_t q_lo = (lo_bit + h.rb - 1) / h.rb;
+    uint32_t q_hi = (lo_bit + 31u) / h.rb;
+    if (q_hi + 1 > h.passes) q_hi = h.passes - 1;
+    const uint64_t both = ((uint64_t)prev << 32) | v;
+    for (uint32_t q = q_lo; q <= q_hi && q < h.passes; ++q)
+        atomicAdd(&h.sm[q * bins + ((uint32_t)(both >> (q * h.rb - lo_bit)) & (bins - 1u))], 1u);
+}
+
 // Compress of R rows at once: row q's chunks come from rows[q] (global or
 // shared memory); each plan word is read once for all R rows.
-template <int VEC, int R>
+template <int VEC, int R, bool HIST = false>
 __device__ __forceinline__ void extract_rows(const KeyDesc& k, const unsigned char* const (&rows)[R],
                                              const uint64_t (&r)[R], const bool (&valid)[R], uint64_t ld,
-                                             const ExtractPlan& plan, const WordPlan* wp, uint32_t* __restrict__ out) {
+                                             const ExtractPlan& plan, const WordPlan* wp, uint32_t* __restrict__ out,
+                                             const HistSink& hs = HistSink{nullptr, 0, 0}) {
     uint32_t kout = plan.K;
+    uint32_t prev[R];
+#pragma unroll
+    for (int q = 0; q < R; ++q) prev[q] = 0u;
     for (uint32_t z = 0; z < plan.lead_zero_words; ++z) {
         --kout;
 #pragma unroll
         for (int q = 0; q < R; ++q)
-            if (valid[q]) out[(uint64_t)kout * ld + r[q]] = 0u;
+            if (valid[q]) {
+                out[(uint64_t)kout * ld + r[q]] = 0u;
+                if (HIST) count_digits(hs, kout, 0u, 0u);
+            }
     }
     uint64_t acc[R];
 #pragma unroll
@@ -163,7 +196,14 @@ __device__ __forceinline__ void extract_rows(const KeyDesc& k, const unsigned ch
                 --kout;
 #pragma unroll
                 for (int q = 0; q < R; ++q)
-                    if (valid[q]) out[(uint64_t)kout * ld + r[q]] = (uint32_t)(acc[q] >> cnt);
+                    if (valid[q]) {
+                        const uint32_t word = (uint32_t)(acc[q] >> cnt);
+                        out[(uint64_t)kout * ld + r[q]] = word;
+                        if (HIST) {
+                            count_digits(hs, kout, prev[q], word);
+                            prev[q] = word;
+                        }
+                    }
             }
         }
     }
@@ -175,21 +215,29 @@ __device__ __forceinline__ void extract_rows(const KeyDesc& k, const unsigned ch
 // kExtractStages shared buffers by one bulk copy, issued kExtractStages tiles
 // ahead.  The ragged last tile is read straight from global memory.  Each
 // thread extracts kExtractRows rows of a tile together.
-constexpr int kExtractStages = 4;
+constexpr int kExtractStages = 4;       // ring depth without digit counting
+constexpr int kExtractStagesHist = 3;   // with it (room for the counters, three blocks per SM)
 constexpr int kExtractThreads = 256;
 constexpr int kExtractRows = 2;
 
-template <int VEC>
+template <int VEC, bool HIST>
 __global__ void __launch_bounds__(kExtractThreads) extract_kernel(const KeyDesc k, uint64_t n, uint64_t ld,
                                                                   uint32_t rows_per_tile, uint32_t staged,
                                                                   const __grid_constant__ ExtractPlan plan,
                                                                   uint32_t* __restrict__ out, uint32_t spin_limit,
-                                                                  unsigned long long* status) {
+                                                                  unsigned long long* status,
+                                                                  uint32_t* __restrict__ hist, uint32_t rb,
+                                                                  uint32_t passes) {
     constexpr int R = kExtractRows;
+    constexpr int kExtractStages = HIST ? kExtractStagesHist : ck::kExtractStages;
     extern __shared__ __align__(128) unsigned char sm[];
     const uint32_t tile_bytes = staged ? rows_per_tile * (uint32_t)k.stride : 0u;
     uint64_t* bar = reinterpret_cast<uint64_t*>(sm + (size_t)kExtractStages * tile_bytes);
     WordPlan* wp = reinterpret_cast<WordPlan*>(bar + kExtractStages);
+    uint32_t* hsm = reinterpret_cast<uint32_t*>(wp + kMaxKeyWords);
+    const uint32_t nctr = HIST ? passes << rb : 0u;
+    for (uint32_t i = threadIdx.x; i < nctr; i += kExtractThreads) hsm[i] = 0u;
+    const HistSink hs{hsm, rb, passes};
     const uint64_t tiles = (n + rows_per_tile - 1) / rows_per_tile;
     const uint64_t full_tiles = staged ? n / rows_per_tile : 0;  // tiles that arrive by bulk copy
     const uint32_t tid = threadIdx.x;
@@ -238,13 +286,18 @@ __global__ void __launch_bounds__(kExtractThreads) extract_kernel(const KeyDesc 
                 r[q] = r0 + j;
                 rows[q] = base + (valid[q] ? j : 0) * k.stride;
             }
-            extract_rows<VEC, R>(k, rows, r, valid, ld, plan, wp, out);
+            extract_rows<VEC, R, HIST>(k, rows, r, valid, ld, plan, wp, out, hs);
         }
         __syncthreads();  // stage i % kExtractStages is free again
         if (tid == 0) {
             fence_proxy_async_smem();
             issue(i + kExtractStages);
         }
+    }
+    if (HIST) {
+        __syncthreads();
+        for (uint32_t i = threadIdx.x; i < nctr; i += kExtractThreads)
+            if (hsm[i]) atomicAdd(&hist[i], hsm[i]);
     }
 }
 
@@ -393,33 +446,42 @@ cudaError_t launch_btree_keys(const KeyDesc& k, int vec, uint64_t n, const uint3
 }
 
 cudaError_t launch_extract(const KeyDesc& k, int vec, uint64_t n, uint64_t ld, const ExtractPlan& plan,
-                           uint32_t* ck_out, cudaStream_t s) {
+                           uint32_t* ck_out, cudaStream_t s, uint32_t* hist, uint32_t rb, uint32_t passes) {
     // rows per tile: a multiple of 16 (so that tiles start 16-byte aligned),
     // about 16 KB of keys, at most kExtractRows rows per thread.  Staging needs
     // a 16-byte aligned column and a ring that fits shared memory.
+    const bool counting = hist != nullptr && passes > 0;
+    const uint32_t stages = counting ? kExtractStagesHist : kExtractStages;
     uint32_t rows = (uint32_t)(16384 / k.stride) & ~15u;
     if (rows > (uint32_t)(kExtractRows * kExtractThreads)) rows = kExtractRows * kExtractThreads;
     if (rows < 16) rows = 16;
     const bool staged = (reinterpret_cast<uintptr_t>(k.base) & 15) == 0 &&
-                        (uint64_t)kExtractStages * rows * k.stride <= 160 * 1024;
+                        (uint64_t)stages * rows * k.stride <= 160 * 1024;
     if (!staged) rows = kExtractRows * kExtractThreads;
-    const size_t smem = (staged ? (size_t)kExtractStages * rows * k.stride : 0) +
-                        kExtractStages * sizeof(uint64_t) + sizeof(WordPlan) * kMaxKeyWords;
+    const size_t smem = (staged ? (size_t)stages * rows * k.stride : 0) + stages * sizeof(uint64_t) +
+                        sizeof(WordPlan) * kMaxKeyWords + (counting ? sizeof(uint32_t) * ((size_t)passes << rb) : 0);
     const uint64_t tiles = (n + rows - 1) / rows;
     const uint64_t cap = (uint64_t)num_sms() * 3;
     const unsigned grid = (unsigned)(tiles < cap ? tiles : cap);
     cudaError_t e = cudaSuccess;
-#define CK_EXTRACT_LAUNCH(V)                                                                                  \
-    e = cudaFuncSetAttribute(extract_kernel<V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);     \
-    if (e != cudaSuccess) return e;                                                                           \
-    extract_kernel<V><<<grid, kExtractThreads, smem, s>>>(k, n, ld, rows, staged ? 1u : 0u, plan, ck_out,      \
-                                                           kDefaultSpin, status_ptr());
-    switch (vec) {
-        case 16: CK_EXTRACT_LAUNCH(16); break;
-        case 8: CK_EXTRACT_LAUNCH(8); break;
-        case 4: CK_EXTRACT_LAUNCH(4); break;
-        default: CK_EXTRACT_LAUNCH(1); break;
+#define CK_EXTRACT_LAUNCH(V, H)                                                                                 \
+    e = cudaFuncSetAttribute(extract_kernel<V, H>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);    \
+    if (e != cudaSuccess) return e;                                                                             \
+    extract_kernel<V, H><<<grid, kExtractThreads, smem, s>>>(k, n, ld, rows, staged ? 1u : 0u, plan, ck_out,     \
+                                                              kDefaultSpin, status_ptr(), hist, rb, passes);
+#define CK_EXTRACT_VEC(H)                          \
+    switch (vec) {                                 \
+        case 16: CK_EXTRACT_LAUNCH(16, H); break;  \
+        case 8: CK_EXTRACT_LAUNCH(8, H); break;    \
+        case 4: CK_EXTRACT_LAUNCH(4, H); break;    \
+        default: CK_EXTRACT_LAUNCH(1, H); break;   \
     }
+    if (counting) {
+        CK_EXTRACT_VEC(true)
+    } else {
+        CK_EXTRACT_VEC(false)
+    }
+#undef CK_EXTRACT_VEC
 #undef CK_EXTRACT_LAUNCH
     count_launch();
     return cudaGetLastError();

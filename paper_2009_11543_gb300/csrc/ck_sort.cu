@@ -496,10 +496,39 @@ bool make_sort_plan(uint64_t n, uint32_t K, uint32_t nbits, uint32_t digit_bits,
     return true;
 }
 
+// All pass histograms of compressed keys, in chunks that fit 64 KB of shared memory.
+template <int RB>
+static cudaError_t upsweep_all(const uint32_t* ck_in, uint64_t n, uint64_t ld, uint32_t K, uint32_t nbits,
+                               uint32_t passes, uint32_t* hist, cudaStream_t s) {
+    constexpr int BINS = 1 << RB;
+    cudaError_t e = cudaSuccess;
+    const uint32_t chunk = (uint32_t)(65536 / (sizeof(uint32_t) * BINS));
+    const int up_grid = num_sms() * 8;  // 8 blocks of 256 threads per SM
+    if (passes * BINS * sizeof(uint32_t) > 48 * 1024) {  // chunks above the default shared-memory limit
+        e = cudaFuncSetAttribute(upsweep_kernel<RB>, cudaFuncAttributeMaxDynamicSharedMemorySize, 65536);
+        if (e != cudaSuccess) return e;
+        if (K <= 8) {
+            const void* fn[8] = {(const void*)upsweep_kw_kernel<RB, 1>, (const void*)upsweep_kw_kernel<RB, 2>,
+                                 (const void*)upsweep_kw_kernel<RB, 3>, (const void*)upsweep_kw_kernel<RB, 4>,
+                                 (const void*)upsweep_kw_kernel<RB, 5>, (const void*)upsweep_kw_kernel<RB, 6>,
+                                 (const void*)upsweep_kw_kernel<RB, 7>, (const void*)upsweep_kw_kernel<RB, 8>};
+            e = cudaFuncSetAttribute(fn[K - 1], cudaFuncAttributeMaxDynamicSharedMemorySize, 65536);
+            if (e != cudaSuccess) return e;
+        }
+    }
+    for (uint32_t p0 = 0; p0 < passes; p0 += chunk) {
+        const uint32_t np = min(chunk, passes - p0);
+        launch_upsweep<RB>(ck_in, n, ld, K, nbits, p0, np, hist, up_grid, s);
+        count_launch();
+    }
+    return cudaGetLastError();
+}
+
 template <int RB>
 static cudaError_t run_sort_rb(const SortPlan& p, const uint32_t* ck_in, const uint32_t* rid_in, uint32_t* ck_out,
                                uint32_t* rid_out, uint64_t n, uint32_t nbits, uint32_t spin_limit, uint32_t inject,
-                               uint32_t flags, cudaEvent_t* ev, unsigned char* ws, cudaStream_t s) {
+                               uint32_t flags, cudaEvent_t* ev, unsigned char* ws, cudaStream_t s,
+                               const uint32_t* hist_in) {
     constexpr int BINS = 1 << RB;
     uint32_t* hist = reinterpret_cast<uint32_t*>(ws + p.off_hist);
     uint32_t* counters = reinterpret_cast<uint32_t*>(ws + p.off_counter);
@@ -510,25 +539,12 @@ static cudaError_t run_sort_rb(const SortPlan& p, const uint32_t* ck_in, const u
     cudaError_t e = cudaMemsetAsync(ws, 0, p.off_alt_ck, s);
     if (e != cudaSuccess) return e;
 
-    // upsweep: all pass histograms, in chunks that fit 64 KB of shared memory
-    const uint32_t chunk = (uint32_t)(65536 / (sizeof(uint32_t) * BINS));
-    const int up_grid = num_sms() * 8;  // 8 blocks of 256 threads per SM
-    if (p.passes * BINS * sizeof(uint32_t) > 48 * 1024) {  // chunks above the default shared-memory limit
-        e = cudaFuncSetAttribute(upsweep_kernel<RB>, cudaFuncAttributeMaxDynamicSharedMemorySize, 65536);
+    if (hist_in) {  // counted during extraction (ck_extract_hist)
+        e = cudaMemcpyAsync(hist, hist_in, sizeof(uint32_t) * BINS * p.passes, cudaMemcpyDeviceToDevice, s);
         if (e != cudaSuccess) return e;
-        if (p.K <= 8) {
-            const void* fn[8] = {(const void*)upsweep_kw_kernel<RB, 1>, (const void*)upsweep_kw_kernel<RB, 2>,
-                                 (const void*)upsweep_kw_kernel<RB, 3>, (const void*)upsweep_kw_kernel<RB, 4>,
-                                 (const void*)upsweep_kw_kernel<RB, 5>, (const void*)upsweep_kw_kernel<RB, 6>,
-                                 (const void*)upsweep_kw_kernel<RB, 7>, (const void*)upsweep_kw_kernel<RB, 8>};
-            e = cudaFuncSetAttribute(fn[p.K - 1], cudaFuncAttributeMaxDynamicSharedMemorySize, 65536);
-            if (e != cudaSuccess) return e;
-        }
-    }
-    for (uint32_t p0 = 0; p0 < p.passes; p0 += chunk) {
-        const uint32_t np = min(chunk, p.passes - p0);
-        launch_upsweep<RB>(ck_in, n, ld, p.K, nbits, p0, np, hist, up_grid, s);
-        count_launch();
+    } else {
+        e = upsweep_all<RB>(ck_in, n, ld, p.K, nbits, p.passes, hist, s);
+        if (e != cudaSuccess) return e;
     }
     scan_kernel<RB><<<p.passes, 256, 0, s>>>(hist);
     count_launch();
@@ -598,7 +614,7 @@ static cudaError_t run_sort_rb(const SortPlan& p, const uint32_t* ck_in, const u
 
 cudaError_t run_sort(const SortPlan& p, const uint32_t* ck_in, const uint32_t* rid_in, uint32_t* ck_out,
                      uint32_t* rid_out, uint64_t n, uint32_t nbits, uint32_t spin_limit, uint32_t inject,
-                     uint32_t flags, cudaEvent_t* ev, unsigned char* ws, cudaStream_t s) {
+                     uint32_t flags, cudaEvent_t* ev, unsigned char* ws, cudaStream_t s, const uint32_t* hist_in) {
     if (p.passes == 0) {  // nothing to order: outputs are the inputs
         cudaError_t e = cudaSuccess;
         if (ck_out != ck_in)
@@ -615,14 +631,31 @@ cudaError_t run_sort(const SortPlan& p, const uint32_t* ck_in, const uint32_t* r
         return cudaGetLastError();
     }
     switch (p.digit_bits) {
-        case 4: return run_sort_rb<4>(p, ck_in, rid_in, ck_out, rid_out, n, nbits, spin_limit, inject, flags, ev, ws, s);
-        case 5: return run_sort_rb<5>(p, ck_in, rid_in, ck_out, rid_out, n, nbits, spin_limit, inject, flags, ev, ws, s);
-        case 6: return run_sort_rb<6>(p, ck_in, rid_in, ck_out, rid_out, n, nbits, spin_limit, inject, flags, ev, ws, s);
-        case 7: return run_sort_rb<7>(p, ck_in, rid_in, ck_out, rid_out, n, nbits, spin_limit, inject, flags, ev, ws, s);
-        case 8: return run_sort_rb<8>(p, ck_in, rid_in, ck_out, rid_out, n, nbits, spin_limit, inject, flags, ev, ws, s);
-        case 9: return run_sort_rb<9>(p, ck_in, rid_in, ck_out, rid_out, n, nbits, spin_limit, inject, flags, ev, ws, s);
-        case 10: return run_sort_rb<10>(p, ck_in, rid_in, ck_out, rid_out, n, nbits, spin_limit, inject, flags, ev, ws, s);
-        case 11: return run_sort_rb<11>(p, ck_in, rid_in, ck_out, rid_out, n, nbits, spin_limit, inject, flags, ev, ws, s);
+        case 4: return run_sort_rb<4>(p, ck_in, rid_in, ck_out, rid_out, n, nbits, spin_limit, inject, flags, ev, ws, s, hist_in);
+        case 5: return run_sort_rb<5>(p, ck_in, rid_in, ck_out, rid_out, n, nbits, spin_limit, inject, flags, ev, ws, s, hist_in);
+        case 6: return run_sort_rb<6>(p, ck_in, rid_in, ck_out, rid_out, n, nbits, spin_limit, inject, flags, ev, ws, s, hist_in);
+        case 7: return run_sort_rb<7>(p, ck_in, rid_in, ck_out, rid_out, n, nbits, spin_limit, inject, flags, ev, ws, s, hist_in);
+        case 8: return run_sort_rb<8>(p, ck_in, rid_in, ck_out, rid_out, n, nbits, spin_limit, inject, flags, ev, ws, s, hist_in);
+        case 9: return run_sort_rb<9>(p, ck_in, rid_in, ck_out, rid_out, n, nbits, spin_limit, inject, flags, ev, ws, s, hist_in);
+        case 10: return run_sort_rb<10>(p, ck_in, rid_in, ck_out, rid_out, n, nbits, spin_limit, inject, flags, ev, ws, s, hist_in);
+        case 11: return run_sort_rb<11>(p, ck_in, rid_in, ck_out, rid_out, n, nbits, spin_limit, inject, flags, ev, ws, s, hist_in);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_upsweep_all(const uint32_t* ck, uint64_t n, uint64_t ld, uint32_t K, uint32_t nbits, uint32_t rb,
+                               uint32_t* hist, cudaStream_t s) {
+    const uint32_t passes = (nbits + rb - 1) / rb;
+    if (passes == 0) return cudaSuccess;
+    switch (rb) {
+        case 4: return upsweep_all<4>(ck, n, ld, K, nbits, passes, hist, s);
+        case 5: return upsweep_all<5>(ck, n, ld, K, nbits, passes, hist, s);
+        case 6: return upsweep_all<6>(ck, n, ld, K, nbits, passes, hist, s);
+        case 7: return upsweep_all<7>(ck, n, ld, K, nbits, passes, hist, s);
+        case 8: return upsweep_all<8>(ck, n, ld, K, nbits, passes, hist, s);
+        case 9: return upsweep_all<9>(ck, n, ld, K, nbits, passes, hist, s);
+        case 10: return upsweep_all<10>(ck, n, ld, K, nbits, passes, hist, s);
+        case 11: return upsweep_all<11>(ck, n, ld, K, nbits, passes, hist, s);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -77,6 +77,6 @@ extern "C" ck_status ck_sort_static(const uint32_t* ck_in, const uint32_t* rid_i
     const uint32_t flags = opts ? opts->flags : 0u;
     cudaEvent_t* ev = opts ? static_cast<cudaEvent_t*>(opts->pass_events) : nullptr;
     const cudaError_t e = run_sort(p, ck_in, rid_in, ck_out, rid_out, n, nbits, spin, inject, flags, ev, ws,
-                                   reinterpret_cast<cudaStream_t>(stream));
+                                   reinterpret_cast<cudaStream_t>(stream), opts ? opts->hist : nullptr);
     return e == cudaSuccess ? CK_OK : CK_ECUDA;
 }

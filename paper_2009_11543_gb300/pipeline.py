@@ -46,6 +46,7 @@ class Rebuild:
         self.learned_opts = learned_opts
         self.learned_stats = None
         self.learned_params = None
+        self.hist = None                  # digit counts from the last extract (plain sort)
         dev = keys.device
         n = max(self.n, 1)
         self.ck_in = ck.ck_buffer(self.K, n, dev)
@@ -61,7 +62,16 @@ class Rebuild:
         self.refined = torch.empty(ck.mask_words(self.key_bits), dtype=torch.int64, device=dev)
 
     def extract(self, stream=None):
-        ck.ck_extract(self.keys, self.dmask, self.K, out=self.ck_in, kind=self.kind, stream=stream)
+        if self.learned:
+            ck.ck_extract(self.keys, self.dmask, self.K, out=self.ck_in, kind=self.kind, stream=stream)
+            return
+        # the plain sort's digit counts come out of the extraction pass
+        passes = (self.nbits + self.digit_bits - 1) // self.digit_bits
+        if getattr(self, "hist", None) is None or self.hist.shape != (max(passes, 1), 1 << self.digit_bits):
+            self.hist = torch.empty((max(passes, 1), 1 << self.digit_bits), dtype=torch.int32,
+                                    device=self.keys.device)
+        ck.ck_extract_hist(self.keys, self.dmask, self.K, self.digit_bits, out=self.ck_in, hist=self.hist,
+                           kind=self.kind, stream=stream)
 
     def sort(self, stream=None, pass_events=None):
         if self.learned:
@@ -70,7 +80,8 @@ class Rebuild:
                 stream=stream)
             return
         ck.ck_sort(self.ck_in, None, self.ck_sorted, self.rid_sorted, self.n, self.K, self.nbits, self.ws,
-                   digit_bits=self.digit_bits, pass_events=pass_events, perm_only=self.perm_only, stream=stream)
+                   digit_bits=self.digit_bits, pass_events=pass_events, perm_only=self.perm_only, hist=self.hist,
+                   stream=stream)
 
     def build(self, stream=None):
         if self.perm_only:

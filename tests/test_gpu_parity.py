@@ -416,3 +416,57 @@ def test_full_key_baseline_same_permutation():
     r = pipeline.Rebuild(to_dev(keys), pipeline.full_key_mask(256))
     r.run()
     assert np.array_equal(ck.u32(r.rid_sorted), oracle.sort_rows(keys))
+
+
+def oracle_digit_hist(ckr, nbits, rb):
+    """Digit counts of the oracle's compressed keys ([n, K] words, least
+    significant first): hist[q][v] = #keys with bits [q*rb, q*rb+rb) = v."""
+    passes = (nbits + rb - 1) // rb
+    vals = [sum(int(w) << (32 * k) for k, w in enumerate(row)) for row in ckr]
+    h = np.zeros((passes, 1 << rb), np.int64)
+    for v in vals:
+        for q in range(passes):
+            h[q, (v >> (q * rb)) & ((1 << rb) - 1)] += 1
+    return h
+
+
+@pytest.mark.parametrize("W,npos,rb", [(32, 117, 8), (8, 40, 4), (16, 100, 11), (5, 17, 8), (40, 200, 8),
+                                       (12, 96, 7)])
+def test_extract_hist_matches_oracle(W, npos, rb):
+    """ck_extract_hist: the compressed keys as ck_extract's, and the digit
+    counts those of the oracle's compressed keys -- counted in the extraction
+    pass (up to 16 KB of counters) or by the sort's counting kernel after it
+    (200 positions in 8-bit digits: 25 KB)."""
+    rng = np.random.default_rng(W * 31 + rb)
+    n = 2 * TILE + 777
+    keys = structured(rng, n, W, npos, dup_frac=0.2)
+    m = oracle.variant_mask(keys, 0)
+    nbits = oracle.popcount(m)
+    ckd, hist = ck.ck_extract_hist(to_dev(keys), m, ck.words_for(nbits), rb)
+    want = oracle.compress(keys, m)
+    assert np.array_equal(ck_rows(ckd, n), want)
+    passes = (nbits + rb - 1) // rb
+    got = hist[:passes].cpu().numpy().astype(np.int64)
+    assert np.array_equal(got, oracle_digit_hist(want, nbits, rb))
+    assert got.sum(axis=1).tolist() == [n] * passes
+
+
+def test_sort_with_extracted_hist_equals_sort():
+    """ck_sort given the extraction's digit counts gives the same pairs as
+    ck_sort counting them itself, and the oracle's order."""
+    rng = np.random.default_rng(17)
+    n, W = 5 * TILE + 123, 32
+    keys = structured(rng, n, W, 110)
+    D = oracle.dmask(keys)
+    nbits = oracle.popcount(D)
+    K = ck.words_for(nbits)
+    ckd, hist = ck.ck_extract_hist(to_dev(keys), D, K, 8)
+    outs = []
+    for h in (hist, None):
+        ck_out = ck.ck_buffer(K, n, DEV)
+        rid = torch.empty(n, dtype=torch.int32, device=DEV)
+        ws = torch.empty(ck.ck_sort_workspace_bytes(n, K, nbits), dtype=torch.uint8, device=DEV)
+        ck.ck_sort(ckd, None, ck_out, rid, n, K, nbits, ws, hist=h)
+        outs.append((ck_rows(ck_out, n), ck.u32(rid)[:n]))
+    assert np.array_equal(outs[0][0], outs[1][0]) and np.array_equal(outs[0][1], outs[1][1])
+    assert np.array_equal(outs[0][1], oracle.sort_rows(keys))
