@@ -35,7 +35,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "keys/sec sorted+indexed (1 GB300) and % of HBM roofline, compressed vs full-key sort"
 FALLBACK_HBM_GBS = 6800.0
-SORT_SRC = os.path.join(ROOT, "paper_2009_11543_gb300", "csrc", "ck_sort.cu")
+PASS_SRC = os.path.join(ROOT, "paper_2009_11543_gb300", "csrc", "ck_pass.cu")
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "onesweep_pass_traffic.json")
 
 WORKLOADS = {
@@ -104,7 +104,7 @@ def ncu_traffic(n: int, ck_words: int):
     try:
         with open(TRAFFIC_FILE) as f:
             t = json.load(f)
-        if t.get("kernel_src_sha") != file_sha(SORT_SRC) or t.get("ck_words") != ck_words:
+        if t.get("kernel_src_sha") != file_sha(PASS_SRC) or t.get("ck_words") != ck_words:
             return None
         return t["dram_bytes_per_launch"] * n / t["n"]
     except Exception:

@@ -215,6 +215,50 @@ __device__ __forceinline__ int32_t dbit_keys(const KeyRef& a, const KeyRef& b) {
     return -1;
 }
 
+
+// Exclusive scan in place over count entries of arr (shared or global memory)
+// by one block; returns the total.  scratch: THREADS/32 + 1 shared words.
+template <int THREADS>
+__device__ uint32_t block_exclusive_scan(uint32_t* arr, int count, uint32_t* scratch) {
+    constexpr int WARPS = THREADS / 32;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int per = (count + THREADS - 1) / THREADS;
+    const int beg = tid * per;
+    uint32_t sum = 0;
+    for (int i = 0; i < per; ++i)
+        if (beg + i < count) sum += arr[beg + i];
+    uint32_t inc = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t t = __shfl_up_sync(kFull, inc, o);
+        if (lane >= o) inc += t;
+    }
+    if (lane == 31) scratch[warp] = inc;
+    __syncthreads();
+    if (warp == 0) {
+        const uint32_t v = lane < WARPS ? scratch[lane] : 0u;
+        uint32_t vi = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t t = __shfl_up_sync(kFull, vi, o);
+            if (lane >= o) vi += t;
+        }
+        if (lane < WARPS) scratch[lane] = vi - v;
+        if (lane == 31) scratch[WARPS] = vi;
+    }
+    __syncthreads();
+    uint32_t run = scratch[warp] + inc - sum;
+    for (int i = 0; i < per; ++i)
+        if (beg + i < count) {
+            const uint32_t t = arr[beg + i];
+            arr[beg + i] = run;
+            run += t;
+        }
+    const uint32_t total = scratch[WARPS];
+    __syncthreads();
+    return total;
+}
+
 }  // namespace ck
 
 // ------------------------------------------------------------ host helpers
