@@ -98,6 +98,19 @@ def file_sha(path: str) -> str:
         return hashlib.sha256(f.read()).hexdigest()[:16]
 
 
+def max_over_ranks(times, world: int) -> np.ndarray:
+    """Element-wise maximum of the ranks' timings (every rank gets it); the
+    job is as slow as its slowest replica."""
+    times = np.asarray(times, np.float64)
+    if world <= 1:
+        return times
+    import torch
+    import torch.distributed as dist
+    t = torch.from_numpy(times.copy())
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return t.numpy()
+
+
 def ncu_traffic(n: int, ck_words: int):
     """DRAM bytes per pass launch from the committed ncu summary, scaled to n
     keys, if the pass kernel's source is unchanged since the capture."""
@@ -237,12 +250,7 @@ def run_table(args, rank, world, local_rank):
     if status != ck.CK_OK:
         raise RuntimeError("device status %s (detail %d)" % (ck.ck_status_string(status), detail))
     B.close()
-    times = np.array([graph_ms, e2e_ms, seq_ms, full_ms], np.float64)
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.from_numpy(times)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        times = t.numpy()
+    times = max_over_ranks([graph_ms, e2e_ms, seq_ms, full_ms], world)
     graph_ms, e2e_ms, seq_ms, full_ms = (float(x) for x in times)
     if rank != 0:
         return None
@@ -357,15 +365,18 @@ def run_zipf_sweep(args, rank, world, local_rank):
     status, detail = ck.ck_device_status()
     if status != ck.CK_OK:
         raise RuntimeError("device status %s (detail %d)" % (ck.ck_status_string(status), detail))
+    tot_ms = float(max_over_ranks([tot_ms], world)[0])
+    if rank != 0:
+        return None
     speedups = np.array([r["speedup"] for r in rows])
     return {
-        "metric": METRIC, "value": tot_keys / (tot_ms / 1e3), "unit": "keys/s", "n_gpus": 1, "steps": steps,
+        "metric": METRIC, "value": world * tot_keys / (tot_ms / 1e3), "unit": "keys/s", "n_gpus": world, "steps": steps,
         "warmup": args.warmup, "ms_per_step": tot_ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "u32",
         "data": "synthetic (the paper's Zipf(s, n, m) generator definition, Sec. 6.3)",
         "config": {"workload": desc, "n_per_dataset": n_keys, "datasets": len(rows), "fanout": fanout,
                    "rid_variant_bits": ZIPF_RID_VARIANT_BITS,
-                   "l2": "inputs larger than L2 (no flush)", "parallelism": "single GPU"},
+                   "l2": "inputs larger than L2 (no flush)", "parallelism": "replicas" if world > 1 else "single GPU"},
         "roofline": None,
         "sweep": rows,
         "speedup_geomean": float(np.exp(np.mean(np.log(speedups)))),
@@ -551,12 +562,7 @@ def run_ours(args, rank, world, local_rank):
         raise RuntimeError("device status %s (detail %d)" % (ck.ck_status_string(status), detail))
 
     # max over ranks
-    times = np.array([total_ms, e2e_ms, f_total_ms, l_total_ms or 0.0], np.float64)
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.from_numpy(times)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        times = t.numpy()
+    times = max_over_ranks([total_ms, e2e_ms, f_total_ms, l_total_ms or 0.0], world)
     total_ms, e2e_ms, f_total_ms = (float(x) for x in times[:3])
     if L is not None:
         l_total_ms = float(times[3])
