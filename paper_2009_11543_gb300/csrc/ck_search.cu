@@ -177,6 +177,67 @@ __device__ __forceinline__ int cmp_dbit(const KeyRef& a, const KeyRef& b, int32_
     return 0;
 }
 
+// The query of one thread.  QW > 0: its key words (QW >= the key's words) are
+// held in registers, so a comparison loads only the other key and the
+// partial-key window costs no load; QW = 0: read from the query column.
+template <int VEC, int QW>
+struct QueryView {
+    const KeyDesc* qk;
+    uint64_t j;
+    uint32_t w[QW > 0 ? QW : 1];
+
+    __device__ __forceinline__ QueryView(const KeyDesc& k, uint64_t row) : qk(&k), j(row) {
+        if (QW > 0) {
+#pragma unroll
+            for (int c = 0; c < (QW + 3) / 4; ++c) {
+                uint32_t x[4];
+                load_chunk<VEC>(k, row, c, x);
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+                    if (4 * c + i < QW) w[4 * c + i] = x[i];
+            }
+        }
+    }
+
+    // Sign of key(col, r) - query and, when they differ, their D-bit.
+    __device__ __forceinline__ int cmp(const KeyDesc& col, uint64_t r, int32_t* d) const {
+        if (QW == 0) return cmp_dbit<VEC>(KeyRef{&col, r}, KeyRef{qk, j}, d);
+#pragma unroll
+        for (int c = 0; c < (QW + 3) / 4; ++c) {
+            uint32_t x[4];
+            load_chunk<VEC>(col, r, c, x);
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                if (4 * c + i >= QW) break;
+                const uint32_t y = x[i] ^ w[4 * c + i];
+                if (y) {
+                    *d = (int32_t)(32 * (4 * c + i) + __clz(y));
+                    return x[i] < w[4 * c + i] ? -1 : 1;
+                }
+            }
+        }
+        *d = -1;
+        return 0;
+    }
+
+    // The query's positions p0 .. p0 + pk - 1 as a pk-bit value.
+    __device__ __forceinline__ uint32_t window(uint32_t p0, uint32_t pk) const {
+        const uint32_t wi = p0 >> 5;
+        uint32_t hi = 0, lo = 0;
+        if (QW == 0) {
+            hi = key_word<VEC>(*qk, j, wi);
+            lo = key_word<VEC>(*qk, j, wi + 1);
+        } else {
+#pragma unroll
+            for (int k = 0; k < (QW > 0 ? QW : 1); ++k) {
+                hi |= w[k] & (0u - (uint32_t)((uint32_t)k == wi));      // masks, not an index:
+                lo |= w[k] & (0u - (uint32_t)((uint32_t)k == wi + 1));  // w stays in registers
+            }
+        }
+        return (uint32_t)(((((uint64_t)hi << 32) | lo) << (p0 & 31)) >> (64 - pk));
+    }
+};
+
 constexpr uint64_t kScanError = ~0ull;
 
 // Scans entries i .. t - 1 of one level in key order (offsets dbit, partial
@@ -185,10 +246,10 @@ constexpr uint64_t kScanError = ~0ull;
 // none; kScanError after a bad row id) and sets eq when a full comparison
 // found that key equal to Q.  On return d is still the D-bit of Q against the
 // key before the returned entry.
-template <int VEC>
+template <int VEC, int QW>
 __device__ __forceinline__ uint64_t scan_level(const uint16_t* dbit, const uint32_t* pks, const uint32_t* rids,
                                                uint64_t i, uint64_t t, int32_t& d, const KeyDesc& col,
-                                               const KeyDesc& qk, uint64_t j, uint32_t pk, uint64_t n, bool& eq,
+                                               const QueryView<VEC, QW> Q, uint32_t pk, uint64_t n, bool& eq,
                                                uint32_t& derefs, unsigned long long* status) {
     eq = false;
     for (; i < t; ++i) {
@@ -197,9 +258,8 @@ __device__ __forceinline__ uint64_t scan_level(const uint16_t* dbit, const uint3
         if ((int32_t)o < d) return i;
         if ((int32_t)o > d) continue;
         // o == d: compare Q's bits o + 1 .. o + pk with the partial key
-        const uint32_t p0 = o + 1, w = p0 >> 5;
-        const uint64_t win = ((uint64_t)key_word<VEC>(qk, j, w) << 32) | key_word<VEC>(qk, j, w + 1);
-        const uint32_t qb = (uint32_t)((win << (p0 & 31)) >> (64 - pk));
+        const uint32_t p0 = o + 1;
+        const uint32_t qb = Q.window(p0, pk);
         const uint32_t x = qb ^ pks[i];
         if (x) {
             const uint32_t lead = __clz(x) - (32 - pk);  // first differing bit among the pk
@@ -216,7 +276,7 @@ __device__ __forceinline__ uint64_t scan_level(const uint16_t* dbit, const uint3
         }
         ++derefs;
         int32_t dd;
-        const int c = cmp_dbit<VEC>(KeyRef{&col, r}, KeyRef{&qk, j}, &dd);
+        const int c = Q.cmp(col, r, &dd);
         if (c >= 0) {
             eq = c == 0;
             return i;
@@ -226,8 +286,8 @@ __device__ __forceinline__ uint64_t scan_level(const uint16_t* dbit, const uint3
     return t;
 }
 
-template <int VEC>
-__global__ void __launch_bounds__(kSearchThreads) search_kernel(const __grid_constant__ SearchArgs a,
+template <int VEC, int QW, bool INNER_PK>
+__global__ void __launch_bounds__(kSearchThreads, 10) search_kernel(const __grid_constant__ SearchArgs a,
                                                                 const __grid_constant__ KeyDesc col,
                                                                 const __grid_constant__ KeyDesc qk,
                                                                 uint32_t* __restrict__ pos_out,
@@ -235,12 +295,12 @@ __global__ void __launch_bounds__(kSearchThreads) search_kernel(const __grid_con
                                                                 uint32_t* __restrict__ derefs_out,
                                                                 unsigned long long* status) {
     for (uint64_t j = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; j < a.q; j += (uint64_t)gridDim.x * blockDim.x) {
-        const KeyRef Q{&qk, j};
+        const QueryView<VEC, QW> Q(qk, j);
         uint64_t pos = a.n;
         bool found = false;
         uint32_t derefs = 0;
         if (a.n == 0) goto done;
-        if (a.inner_pk) {
+        if (INNER_PK) {
             // ---- every level scanned with offsets and partial keys; the state d
             //      (Q against the key before the current node) carries down, since
             //      the key before child i's first entry is entry i - 1's highest key
@@ -265,7 +325,7 @@ __global__ void __launch_bounds__(kSearchThreads) search_kernel(const __grid_con
                     }
                     ++derefs;
                     int32_t dd;
-                    const int c = cmp_dbit<VEC>(KeyRef{&col, r}, Q, &dd);
+                    const int c = Q.cmp(col, r, &dd);
                     if (c >= 0) {
                         eq = c == 0;
                         first_ge = true;
@@ -276,7 +336,7 @@ __global__ void __launch_bounds__(kSearchThreads) search_kernel(const __grid_con
                     }
                 }
                 if (!first_ge) {
-                    i = scan_level<VEC>(dbit, pks, rids, i, t, d, col, qk, j, a.pk, a.n, eq, derefs, status);
+                    i = scan_level<VEC, QW>(dbit, pks, rids, i, t, d, col, Q, a.pk, a.n, eq, derefs, status);
                     if (i == kScanError) goto done;
                 }
                 if (i == t) {  // Q above every key under this node: only at the root or the last leaf
@@ -311,7 +371,7 @@ __global__ void __launch_bounds__(kSearchThreads) search_kernel(const __grid_con
                         goto done;
                     }
                     int32_t d;
-                    if (cmp_dbit<VEC>(KeyRef{&col, r}, Q, &d) < 0) {
+                    if (Q.cmp(col, r, &d) < 0) {
                         lo = mid + 1;
                         fence = a.inner_high[g];
                         fence_d = d;
@@ -335,7 +395,7 @@ __global__ void __launch_bounds__(kSearchThreads) search_kernel(const __grid_con
                     goto done;
                 }
                 ++derefs;
-                const int c = cmp_dbit<VEC>(KeyRef{&col, r}, Q, &d);
+                const int c = Q.cmp(col, r, &d);
                 if (s == 0) {
                     if (c >= 0) {
                         pos = 0;
@@ -346,8 +406,8 @@ __global__ void __launch_bounds__(kSearchThreads) search_kernel(const __grid_con
                 }
             }
             bool eq = false;
-            i = scan_level<VEC>(a.leaf_dbit, a.leaf_pk, a.leaf_rid, i, t, d, col, qk, j, a.pk, a.n, eq, derefs,
-                                status);
+            i = scan_level<VEC, QW>(a.leaf_dbit, a.leaf_pk, a.leaf_rid, i, t, d, col, Q, a.pk, a.n, eq, derefs,
+                                    status);
             if (i == kScanError) goto done;
             pos = i;
             found = eq;
@@ -504,14 +564,31 @@ ck_status ck_search(const ck_btree* tree, const ck_column* col, const uint32_t* 
     const uint64_t want = (q + kSearchThreads - 1) / kSearchThreads, cap = (uint64_t)num_sms() * 16;
     const unsigned grid = (unsigned)(want < cap ? want : cap);
     const int vec = vc < vq ? vc : vq;
-#define CK_SEARCH_LAUNCH(V) \
-    search_kernel<V><<<grid, kSearchThreads, 0, s>>>(a, ck_, qk, pos_out, rid_out, derefs_out, status)
-    switch (vec) {
-        case 16: CK_SEARCH_LAUNCH(16); break;
-        case 8: CK_SEARCH_LAUNCH(8); break;
-        case 4: CK_SEARCH_LAUNCH(4); break;
-        default: CK_SEARCH_LAUNCH(1); break;
+    // the query's key words in registers up to 8 words (32-byte keys)
+    const uint32_t nw = qk.nwords;
+    const int qw = nw <= 1 ? 1 : nw <= 2 ? 2 : nw <= 4 ? 4 : nw <= 8 ? 8 : 0;
+#define CK_SEARCH_LAUNCH(V, QW)                                                                               \
+    if (a.inner_pk)                                                                                           \
+        search_kernel<V, QW, true><<<grid, kSearchThreads, 0, s>>>(a, ck_, qk, pos_out, rid_out, derefs_out,   \
+                                                                    status);                                  \
+    else                                                                                                      \
+        search_kernel<V, QW, false><<<grid, kSearchThreads, 0, s>>>(a, ck_, qk, pos_out, rid_out, derefs_out,  \
+                                                                     status)
+#define CK_SEARCH_QW(V)                          \
+    switch (qw) {                                \
+        case 1: CK_SEARCH_LAUNCH(V, 1); break;   \
+        case 2: CK_SEARCH_LAUNCH(V, 2); break;   \
+        case 4: CK_SEARCH_LAUNCH(V, 4); break;   \
+        case 8: CK_SEARCH_LAUNCH(V, 8); break;   \
+        default: CK_SEARCH_LAUNCH(V, 0); break;  \
     }
+    switch (vec) {
+        case 16: CK_SEARCH_QW(16) break;
+        case 8: CK_SEARCH_QW(8) break;
+        case 4: CK_SEARCH_QW(4) break;
+        default: CK_SEARCH_QW(1) break;
+    }
+#undef CK_SEARCH_QW
 #undef CK_SEARCH_LAUNCH
     count_launch();
     return cudaGetLastError() == cudaSuccess ? CK_OK : CK_ECUDA;
