@@ -8,8 +8,19 @@
  *   ck_variant_bits      variant bitmap of the keys              (Sec. 4.2, 4.3)
  *   ck_distinction_bits  D-bitmap of sorted keys                 (Sec. 3.1, Theorem 1)
  *   ck_extract           Compress(key) for every row             (Sec. 3.2, 5.1)
+ *   ck_extract_hist      the same, counting the sort's digits    (Sec. 3.2, 5.1)
  *   ck_sort              stable LSD radix sort of (ck, row id)   (Sec. 3.2, 5.2)
+ *   ck_sort_static       the same without a caller workspace
  *   ck_build_index       bottom-up bulk load + D refinement      (Sec. 4.3, 5.3)
+ *   ck_build_index_keys  the same from the key column and row ids
+ *
+ * and around that path:
+ *
+ *   ck_build_batched, ck_graph_*, ck_autotune_sort   all indexes of a table at once
+ *   ck_sort_learned, ck_mlp_loss_grad, ck_model_separators   learned CDF partition
+ *   ck_insert_batch      DS-metadata under inserts               (Sec. 4.3)
+ *   ck_encode_key        index keys of several columns           (Sec. 4.1)
+ *   ck_partial_key_mask, ck_partial_keys, ck_search   partial keys and search (Sec. 4.2, 4.3)
  *
  * Conventions shared by every call:
  *   - Bit position p of a key (0 = most significant bit of byte 0) is bit
@@ -28,7 +39,10 @@
  *     starts 256-byte aligned.  The padding entries are never read as keys.
  *   - Row ids are uint32; n <= CK_MAX_ROWS.
  *   - Every call is asynchronous on the given stream (NULL = the legacy default
- *     stream) and allocates no device memory.  The caller owns every buffer.
+ *     stream) and allocates no device memory, except where its comment says
+ *     otherwise (ck_insert_batch and ck_autotune_sort synchronise the stream;
+ *     ck_btree_plan and ck_partial_key_mask touch no device).  The caller owns
+ *     every buffer.
  *     Device pointers must come from cudaMalloc (or torch) on the current
  *     device; HOST pointers are read before the call returns.
  *   - Argument errors are returned synchronously.  Device-side failures (a
