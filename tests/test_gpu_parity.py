@@ -470,3 +470,27 @@ def test_sort_with_extracted_hist_equals_sort():
         outs.append((ck_rows(ck_out, n), ck.u32(rid)[:n]))
     assert np.array_equal(outs[0][0], outs[1][0]) and np.array_equal(outs[0][1], outs[1][1])
     assert np.array_equal(outs[0][1], oracle.sort_rows(keys))
+
+
+def test_extract_hist_edge_cases():
+    """Empty column (counts zeroed), all-equal keys (no digits: no counts
+    needed), a digit width outside 4..11, and a one-row column."""
+    W = 8
+    empty = torch.empty((0, W), dtype=torch.uint8, device=DEV)
+    m = mask_of([3, 17, 40], 8 * W)
+    hist = torch.full((1, 256), 7, dtype=torch.int32, device=DEV)
+    ck.ck_extract_hist(empty, m, 1, 8, out=torch.empty(64, dtype=torch.int32, device=DEV), hist=hist)
+    assert int(hist.abs().sum()) == 0
+    same = to_dev(np.repeat(np.arange(W, dtype=np.uint8)[None, :], 1000, axis=0))
+    z = np.zeros(1, np.uint64)
+    ckd, _ = ck.ck_extract_hist(same, z, 1, 8)
+    assert int(ckd[:, :1000].abs().sum()) == 0
+    with pytest.raises(ck.CkError) as e:
+        ck.ck_extract_hist(same, m, 1, 12)
+    assert e.value.status == ck.CK_EINVAL
+    one = to_dev(np.full((1, W), 0xA5, np.uint8))
+    ckd, h = ck.ck_extract_hist(one, m, 1, 4)
+    v = int(oracle.compress(np.full((1, W), 0xA5, np.uint8), m)[0, 0])
+    want = np.zeros((1, 16), np.int64)
+    want[0, v & 15] = 1
+    assert np.array_equal(h.cpu().numpy().astype(np.int64), want)
