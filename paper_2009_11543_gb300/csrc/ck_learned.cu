@@ -556,10 +556,18 @@ __global__ void __launch_bounds__(1024) bucket_kernel(const BucketArgs a) {
     }
     __syncthreads();
     unsigned long long my_sum = 0, my_max = 0;
-    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + tid; i < a.n; i += (uint64_t)gridDim.x * blockDim.x) {
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    uint32_t next[KW];  // the following key's words, loaded while this key is searched
+    uint64_t i = (uint64_t)blockIdx.x * blockDim.x + tid;
+#pragma unroll
+    for (int w = 0; w < KW; ++w) next[w] = i < a.n ? a.ck[(uint64_t)w * a.ld + i] : 0u;
+    for (; i < a.n; i += stride) {
         uint32_t key[KW];
 #pragma unroll
-        for (int w = 0; w < KW; ++w) key[w] = a.ck[(uint64_t)w * a.ld + i];
+        for (int w = 0; w < KW; ++w) {
+            key[w] = next[w];
+            next[w] = i + stride < a.n ? a.ck[(uint64_t)w * a.ld + i + stride] : 0u;
+        }
         const uint32_t t = top32_regs<KW>(key, nbits);
         uint32_t g, steps = 0, lo = 0, hi = B - 1;
         if (STAGED) {
