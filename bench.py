@@ -520,6 +520,25 @@ def run_ours(args, rank, world, local_rank):
             ins_ms.append(a0.elapsed_time(a1))
     ins_ms = float(np.median(ins_ms))
 
+    # the D-bitmap from the sorted order (Theorem 1) and the variant bitmap
+    # (Sec. 4.2), the first build's inputs, timed on their own
+    dm_out = torch.empty(ck.mask_words(8 * key_bytes), dtype=torch.int64, device=dev)
+    vm_out = torch.empty_like(dm_out)
+    db_ms, vb_ms = [], []
+    for it in range(args.warmup + args.steps):
+        a0, a1, a2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        a0.record(stream)
+        ck.ck_distinction_bits(keys, R.rid_sorted[:n], out=dm_out)
+        a1.record(stream)
+        ck.ck_variant_bits(keys, 0, out=vm_out)
+        a2.record(stream)
+        a2.synchronize()
+        if it >= args.warmup:
+            db_ms.append(a0.elapsed_time(a1))
+            vb_ms.append(a1.elapsed_time(a2))
+    db_ms, vb_ms = float(np.median(db_ms)), float(np.median(vb_ms))
+    dmask_ok = bool(np.array_equal(ck.mask_to_host(dm_out), R.dmask))
+
     # partial keys (Sec. 4.2) and lower-bound search (Sec. 4.3) on the index
     # the timed rebuilds left in R: queries are indexed keys and the insert
     # batch's rows (not in the index)
@@ -634,6 +653,12 @@ def run_ours(args, rank, world, local_rank):
             "stats": L.learned_stats, "speedup_vs_plain": ms_step / l_ms_step},
         "gpu_launches": int(l_launches if V is L else launches),
         "clocks": clk,
+        "dmask": {"distinction_bits_ms": db_ms, "distinction_bits_keys_per_s": world * n / (db_ms / 1e3),
+                  "variant_bits_ms": vb_ms,
+                  "variant_bits_gbs": n * key_bytes / (vb_ms / 1e3) / 1e9,
+                  "matches_stored_dmask": dmask_ok,
+                  "note": "D-bitmap from adjacent keys in sorted order (rows gathered through the permutation), "
+                          "variant bitmap (one read of the keys), medians"},
         "insert_batch": {"value": world * m_ins / (ins_ms / 1e3), "unit": "keys/s", "ms": ins_ms, "batch": m_ins,
                          "index_rows": n, "note": "D-bitmap and variant bitmap maintenance (Sec. 4.3), median"},
         "search": {"value": world * m_q / (se_ms / 1e3), "unit": "lookups/s", "ms": se_ms, "queries": m_q,

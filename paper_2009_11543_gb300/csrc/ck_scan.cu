@@ -32,7 +32,10 @@ __device__ __forceinline__ void warp_mark(uint32_t* sm, int32_t p) {
 }
 
 // ------------------------------------------------------------------ variant
-template <int VEC>
+// NW > 0 (keys of at most NW words): every thread ORs (row xor reference) into
+// NW registers over all its rows, and the warp reduces them once at the end;
+// NW = 0: a warp reduction and a shared atomic per word and 32 rows.
+template <int VEC, int NW>
 __global__ void __launch_bounds__(256) variant_kernel(const KeyDesc k, uint64_t n, uint64_t ref_row,
                                                       uint64_t* __restrict__ mask_out) {
     __shared__ uint32_t sm[kMaxKeyWords];
@@ -41,18 +44,47 @@ __global__ void __launch_bounds__(256) variant_kernel(const KeyDesc k, uint64_t 
     const uint32_t lane = threadIdx.x & 31;
     const uint32_t nchunks = (k.nwords + 3) / 4;
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-    // warp-uniform trip count so that every lane takes part in the reductions
-    for (uint64_t r0 = (uint64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31u); r0 < n; r0 += stride) {
-        const uint64_t r = r0 + lane;
-        const bool valid = r < n;
-        for (uint32_t c = 0; c < nchunks; ++c) {
-            uint32_t w[4] = {0, 0, 0, 0}, ref[4];
-            load_chunk<VEC>(k, ref_row, c, ref);
-            if (valid) load_chunk<VEC>(k, r, c, w);
+    if (NW > 0) {
+        constexpr int NC = NW > 0 ? (NW + 3) / 4 : 1;
+        uint32_t ref[4 * NC], acc[4 * NC];
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+            uint32_t x[4];
+            load_chunk<VEC>(k, ref_row, c, x);
 #pragma unroll
             for (int i = 0; i < 4; ++i) {
-                const uint32_t x = __reduce_or_sync(kFull, valid ? (w[i] ^ ref[i]) : 0u);
-                if (lane == 0 && x && 4 * c + i < k.nwords) atomicOr(&sm[4 * c + i], x);
+                ref[4 * c + i] = x[i];
+                acc[4 * c + i] = 0u;
+            }
+        }
+        for (uint64_t r = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += stride) {
+#pragma unroll
+            for (int c = 0; c < NC; ++c) {
+                uint32_t x[4];
+                load_chunk<VEC>(k, r, c, x);
+#pragma unroll
+                for (int i = 0; i < 4; ++i) acc[4 * c + i] |= x[i] ^ ref[4 * c + i];
+            }
+        }
+#pragma unroll
+        for (int w = 0; w < 4 * NC; ++w) {
+            const uint32_t x = __reduce_or_sync(kFull, acc[w]);
+            if (lane == 0 && x && (uint32_t)w < k.nwords) atomicOr(&sm[w], x);
+        }
+    } else {
+        // warp-uniform trip count so that every lane takes part in the reductions
+        for (uint64_t r0 = (uint64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31u); r0 < n; r0 += stride) {
+            const uint64_t r = r0 + lane;
+            const bool valid = r < n;
+            for (uint32_t c = 0; c < nchunks; ++c) {
+                uint32_t w[4] = {0, 0, 0, 0}, ref[4];
+                load_chunk<VEC>(k, ref_row, c, ref);
+                if (valid) load_chunk<VEC>(k, r, c, w);
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const uint32_t x = __reduce_or_sync(kFull, valid ? (w[i] ^ ref[i]) : 0u);
+                    if (lane == 0 && x && 4 * c + i < k.nwords) atomicOr(&sm[4 * c + i], x);
+                }
             }
         }
     }
@@ -235,8 +267,9 @@ __global__ void __launch_bounds__(kExtractThreads) extract_kernel(const KeyDesc 
     uint64_t* bar = reinterpret_cast<uint64_t*>(sm + (size_t)kExtractStages * tile_bytes);
     WordPlan* wp = reinterpret_cast<WordPlan*>(bar + kExtractStages);
     uint32_t* hsm = reinterpret_cast<uint32_t*>(wp + kMaxKeyWords);
-    const uint32_t nctr = HIST ? passes << rb : 0u;
-    for (uint32_t i = threadIdx.x; i < nctr; i += kExtractThreads) hsm[i] = 0u;
+    const uint32_t nctr = passes << rb;
+    if constexpr (HIST)
+        for (uint32_t i = threadIdx.x; i < nctr; i += kExtractThreads) hsm[i] = 0u;
     const HistSink hs{hsm, rb, passes};
     const uint64_t tiles = (n + rows_per_tile - 1) / rows_per_tile;
     const uint64_t full_tiles = staged ? n / rows_per_tile : 0;  // tiles that arrive by bulk copy
@@ -294,7 +327,7 @@ __global__ void __launch_bounds__(kExtractThreads) extract_kernel(const KeyDesc 
             issue(i + kExtractStages);
         }
     }
-    if (HIST) {
+    if constexpr (HIST) {
         __syncthreads();
         for (uint32_t i = threadIdx.x; i < nctr; i += kExtractThreads)
             if (hsm[i]) atomicAdd(&hist[i], hsm[i]);
@@ -407,10 +440,23 @@ static unsigned grid_for(uint64_t n, unsigned threads) {
         default: KERNEL<1><<<grid, 256, 0, s>>>(__VA_ARGS__); break;           \
     }
 
+template <int NW>
+static void launch_variant_nw(const KeyDesc& k, int vec, uint64_t n, uint64_t ref_row, uint64_t* mask_out,
+                              unsigned grid, cudaStream_t s) {
+    switch (vec) {
+        case 16: variant_kernel<16, NW><<<grid, 256, 0, s>>>(k, n, ref_row, mask_out); break;
+        case 8: variant_kernel<8, NW><<<grid, 256, 0, s>>>(k, n, ref_row, mask_out); break;
+        case 4: variant_kernel<4, NW><<<grid, 256, 0, s>>>(k, n, ref_row, mask_out); break;
+        default: variant_kernel<1, NW><<<grid, 256, 0, s>>>(k, n, ref_row, mask_out); break;
+    }
+}
+
 cudaError_t launch_variant(const KeyDesc& k, int vec, uint64_t n, uint64_t ref_row, uint64_t* mask_out,
                            cudaStream_t s) {
     const unsigned grid = grid_for(n, 256);
-    CK_DISPATCH_VEC(vec, variant_kernel, k, n, ref_row, mask_out);
+    if (k.nwords <= 4) launch_variant_nw<4>(k, vec, n, ref_row, mask_out, grid, s);
+    else if (k.nwords <= 8) launch_variant_nw<8>(k, vec, n, ref_row, mask_out, grid, s);
+    else launch_variant_nw<0>(k, vec, n, ref_row, mask_out, grid, s);
     count_launch();
     return cudaGetLastError();
 }
