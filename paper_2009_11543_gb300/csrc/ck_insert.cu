@@ -40,7 +40,7 @@ __global__ void iota_u32(uint32_t* out, uint64_t m) {
 
 // One thread per batch key in sorted position j (grid-stride, warp-uniform
 // trip count for the warp-wide marking).
-template <int VEC>
+template <int VEC, int QW>
 __global__ void __launch_bounds__(kInsertThreads) insert_kernel(const __grid_constant__ KeyDesc old_k, uint64_t n,
                                                                const uint32_t* __restrict__ order,
                                                                const __grid_constant__ KeyDesc new_k, uint64_t m,
@@ -63,6 +63,7 @@ __global__ void __launch_bounds__(kInsertThreads) insert_kernel(const __grid_con
             const uint32_t rb = border[j];
             const KeyRef key{&new_k, rb < m ? rb : 0};
             if (rb >= m) report(status, CK_EINVAL, j);
+            const QueryView<VEC, QW> K(new_k, key.r);  // the new key, in registers when it is short
             // place among the old keys: the first sorted position whose key is >= K
             uint64_t lo = 0, hi = n;
             while (lo < hi) {
@@ -73,7 +74,8 @@ __global__ void __launch_bounds__(kInsertThreads) insert_kernel(const __grid_con
                     lo = mid + 1;
                     continue;
                 }
-                if (cmp_keys<VEC>(KeyRef{&old_k, r}, key) < 0) lo = mid + 1;
+                int32_t dd;
+                if (K.cmp(old_k, r, &dd) < 0) lo = mid + 1;
                 else hi = mid;
             }
             // neighbours in the merged order
@@ -97,8 +99,8 @@ __global__ void __launch_bounds__(kInsertThreads) insert_kernel(const __grid_con
                 if (!has_b || cmp_keys<VEC>(next, b) < 0) b = next;
                 has_b = true;
             }
-            if (has_a) pl = dbit_keys<VEC>(a, key);
-            if (has_b) pr = dbit_keys<VEC>(key, b);
+            if (has_a) K.cmp(*a.k, a.r, &pl);  // the D-bit of the two keys (-1 if equal)
+            if (has_b) K.cmp(*b.k, b.r, &pr);
         }
         mark(sd, pl);
         mark(sd, pr);
@@ -209,14 +211,24 @@ ck_status ck_insert_batch(const ck_column* keys, const uint32_t* order, const ck
     const int vec = vo < vn ? vo : vn;
     const uint64_t want = (m + kInsertThreads - 1) / kInsertThreads, cap = (uint64_t)num_sms() * 8;
     const unsigned grid = (unsigned)(want < cap ? want : cap);
-#define CK_INSERT_LAUNCH(V)                                                                                        \
-    insert_kernel<V><<<grid, kInsertThreads, 0, s>>>(ok, n, order, nk, m, border, ref_row, dmask, vmask, status)
-    switch (vec) {
-        case 16: CK_INSERT_LAUNCH(16); break;
-        case 8: CK_INSERT_LAUNCH(8); break;
-        case 4: CK_INSERT_LAUNCH(4); break;
-        default: CK_INSERT_LAUNCH(1); break;
+    const uint32_t nw = nk.nwords;
+    const int qw = nw <= 2 ? 2 : nw <= 4 ? 4 : nw <= 8 ? 8 : 0;  // the new key's words kept in registers
+#define CK_INSERT_LAUNCH(V, Q) \
+    insert_kernel<V, Q><<<grid, kInsertThreads, 0, s>>>(ok, n, order, nk, m, border, ref_row, dmask, vmask, status)
+#define CK_INSERT_QW(V)                          \
+    switch (qw) {                                \
+        case 2: CK_INSERT_LAUNCH(V, 2); break;   \
+        case 4: CK_INSERT_LAUNCH(V, 4); break;   \
+        case 8: CK_INSERT_LAUNCH(V, 8); break;   \
+        default: CK_INSERT_LAUNCH(V, 0); break;  \
     }
+    switch (vec) {
+        case 16: CK_INSERT_QW(16) break;
+        case 8: CK_INSERT_QW(8) break;
+        case 4: CK_INSERT_QW(4) break;
+        default: CK_INSERT_QW(1) break;
+    }
+#undef CK_INSERT_QW
 #undef CK_INSERT_LAUNCH
     count_launch();
     return cudaGetLastError() == cudaSuccess ? CK_OK : CK_ECUDA;

@@ -49,15 +49,6 @@ struct PkArgs {
     uint32_t erank[kMaxKeyWords];  // set positions of emask before word w
 };
 
-// Word w of row r (0 past the key).
-template <int VEC>
-__device__ __forceinline__ uint32_t key_word(const KeyDesc& k, uint64_t r, uint32_t w) {
-    if (w >= k.nwords) return 0u;
-    uint32_t c[4];
-    load_chunk<VEC>(k, r, w >> 2, c);
-    return c[w & 3];
-}
-
 // Positions [start, start + pk) of a big-endian word array (two words from
 // w = start / 32 on; hi and lo are words w and w + 1) as a pk-bit value, the
 // first position most significant.
@@ -154,88 +145,6 @@ struct SearchArgs {
     uint32_t f, levels, pk;
     uint64_t level_entries[CK_MAX_LEVELS];
     uint64_t offset[CK_MAX_LEVELS];
-};
-
-// Sign of a - b and, when they differ, their D-bit.
-template <int VEC>
-__device__ __forceinline__ int cmp_dbit(const KeyRef& a, const KeyRef& b, int32_t* d) {
-    const uint32_t nchunks = (a.k->nwords + 3) / 4;
-    for (uint32_t c = 0; c < nchunks; ++c) {
-        uint32_t wa[4], wb[4];
-        load_chunk<VEC>(*a.k, a.r, c, wa);
-        load_chunk<VEC>(*b.k, b.r, c, wb);
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            const uint32_t x = wa[i] ^ wb[i];
-            if (x) {
-                *d = (int32_t)(32 * (4 * c + i) + __clz(x));
-                return wa[i] < wb[i] ? -1 : 1;
-            }
-        }
-    }
-    *d = -1;
-    return 0;
-}
-
-// The query of one thread.  QW > 0: its key words (QW >= the key's words) are
-// held in registers, so a comparison loads only the other key and the
-// partial-key window costs no load; QW = 0: read from the query column.
-template <int VEC, int QW>
-struct QueryView {
-    const KeyDesc* qk;
-    uint64_t j;
-    uint32_t w[QW > 0 ? QW : 1];
-
-    __device__ __forceinline__ QueryView(const KeyDesc& k, uint64_t row) : qk(&k), j(row) {
-        if (QW > 0) {
-#pragma unroll
-            for (int c = 0; c < (QW + 3) / 4; ++c) {
-                uint32_t x[4];
-                load_chunk<VEC>(k, row, c, x);
-#pragma unroll
-                for (int i = 0; i < 4; ++i)
-                    if (4 * c + i < QW) w[4 * c + i] = x[i];
-            }
-        }
-    }
-
-    // Sign of key(col, r) - query and, when they differ, their D-bit.
-    __device__ __forceinline__ int cmp(const KeyDesc& col, uint64_t r, int32_t* d) const {
-        if (QW == 0) return cmp_dbit<VEC>(KeyRef{&col, r}, KeyRef{qk, j}, d);
-#pragma unroll
-        for (int c = 0; c < (QW + 3) / 4; ++c) {
-            uint32_t x[4];
-            load_chunk<VEC>(col, r, c, x);
-#pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                if (4 * c + i >= QW) break;
-                const uint32_t y = x[i] ^ w[4 * c + i];
-                if (y) {
-                    *d = (int32_t)(32 * (4 * c + i) + __clz(y));
-                    return x[i] < w[4 * c + i] ? -1 : 1;
-                }
-            }
-        }
-        *d = -1;
-        return 0;
-    }
-
-    // The query's positions p0 .. p0 + pk - 1 as a pk-bit value.
-    __device__ __forceinline__ uint32_t window(uint32_t p0, uint32_t pk) const {
-        const uint32_t wi = p0 >> 5;
-        uint32_t hi = 0, lo = 0;
-        if (QW == 0) {
-            hi = key_word<VEC>(*qk, j, wi);
-            lo = key_word<VEC>(*qk, j, wi + 1);
-        } else {
-#pragma unroll
-            for (int k = 0; k < (QW > 0 ? QW : 1); ++k) {
-                hi |= w[k] & (0u - (uint32_t)((uint32_t)k == wi));      // masks, not an index:
-                lo |= w[k] & (0u - (uint32_t)((uint32_t)k == wi + 1));  // w stays in registers
-            }
-        }
-        return (uint32_t)(((((uint64_t)hi << 32) | lo) << (p0 & 31)) >> (64 - pk));
-    }
 };
 
 constexpr uint64_t kScanError = ~0ull;
