@@ -35,6 +35,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "keys/sec sorted+indexed (1 GB300) and % of HBM roofline, compressed vs full-key sort"
 FALLBACK_HBM_GBS = 6800.0
+SPEC_HBM_GBS = 7900.0  # nominal HBM3e bandwidth of a GB300, for context beside the measured peak
 PASS_SRC = os.path.join(ROOT, "paper_2009_11543_gb300", "csrc", "ck_pass.cu")
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "onesweep_pass_traffic.json")
 
@@ -629,6 +630,12 @@ def run_ours(args, rank, world, local_rank):
                      "peak": peak, "peak_source": peak_src, "unit": "GB/s", "frac": achieved / peak,
                      "traffic": traffic, "alg_bytes_per_launch": pb, "avg_launch_ms": avg_pass_ms},
         "phases_ms": {"extract": float(ph[0]), "sort": float(ph[1]), "build": float(ph[2])},
+        "spec_hbm_gbs": SPEC_HBM_GBS,
+        "build_roofline": {"alg_bytes": metrics.build_bytes(n, R.K),
+                           "achieved_gbs": metrics.build_bytes(n, R.K) / (float(ph[2]) / 1e3) / 1e9,
+                           "frac": metrics.build_bytes(n, R.K) / (float(ph[2]) / 1e3) / 1e9 / peak,
+                           "note": "leaves: sorted (ck, rid) read, rid + D-bit written per key; inner levels "
+                                   "(n / f entries) not counted"},
         "extract_sort_roofline_frac": alg / ((ph[0] + ph[1]) / 1e3) / 1e9 / peak,
         "extract_sort": {"value": world * n / ((ph[0] + ph[1]) / 1e3), "unit": "keys/s",
                          "ms_per_step": float(ph[0] + ph[1])},
