@@ -65,3 +65,19 @@ def test_reference_arm_under_torchrun_prints_one_line():
     line = json.loads(lines[0])
     assert line["impl"] == "reference" and line["n_gpus"] == 2 and line["value"] > 0
     assert line["cpu_baseline"]["kind"] == "oracle"
+
+
+def test_bench_roofline_inputs():
+    """The bench's roofline inputs: the measured HBM peak from the committed
+    peaks file, and the ncu traffic record scaled by n only while the pass
+    kernel's source still has the hash it was captured with."""
+    sys.path.insert(0, ROOT)
+    import bench
+    peak, src = bench.peaks()
+    assert src == "measured" and peak > 1000
+    with open(bench.TRAFFIC_FILE) as f:
+        rec = json.load(f)
+    assert rec["kernel_src_sha"] == bench.file_sha(bench.PASS_SRC)   # the record matches this kernel
+    t = bench.ncu_traffic(2 * rec["n"], rec["ck_words"])
+    assert t == 2 * rec["dram_bytes_per_launch"]
+    assert bench.ncu_traffic(rec["n"], rec["ck_words"] + 1) is None
