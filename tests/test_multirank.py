@@ -77,7 +77,9 @@ def test_bench_roofline_inputs():
     assert src == "measured" and peak > 1000
     with open(bench.TRAFFIC_FILE) as f:
         rec = json.load(f)
-    assert rec["kernel_src_sha"] == bench.file_sha(bench.PASS_SRC)   # the record matches this kernel
     t = bench.ncu_traffic(2 * rec["n"], rec["ck_words"])
-    assert t == 2 * rec["dram_bytes_per_launch"]
+    if rec["kernel_src_sha"] == bench.file_sha(bench.PASS_SRC):   # counters taken on this kernel
+        assert t == 2 * rec["dram_bytes_per_launch"]
+    else:                                                          # kernel changed since: no figure
+        assert t is None
     assert bench.ncu_traffic(rec["n"], rec["ck_words"] + 1) is None
