@@ -4,9 +4,10 @@ TEST INFRASTRUCTURE ONLY: only ``tests/``, ``__graft_entry__.smoke()`` and the
 ``cpu_baseline`` / ``--impl reference`` legs of ``bench.py`` may import this
 package.  It shares no code with the CUDA path and never imports it.
 
-The arithmetic lives in ``ck_oracle.c`` (plain C, single thread); this module
-only builds it with gcc and marshals numpy arrays.  Each wrapper names the
-passage of the paper it follows:
+Most of the arithmetic lives in ``ck_oracle.c`` (plain C, single thread),
+which this module builds with gcc and calls on numpy arrays; the key formats,
+partial keys, the partial-key mask and the search are written here in plain
+numpy / Python.  Each function names the passage of the paper it follows:
 
 * ``dbit``            -- Sec. 3.1, definition of the distinction bit position
 * ``sort_rows``       -- Sec. 3.1, sorted (lexicographic) order; ties by row id
