@@ -19,6 +19,38 @@ import torch
 from . import ck
 
 
+class DSMetadata:
+    """The state an index keeps across restarts (Sec. 4.2): the D-bitmap, the
+    variant bitmap and the reference key value.  The index itself is never
+    persisted; after a restart it is rebuilt from the table with the stored
+    D-bitmap (Sec. 4.3).  save() / load() use one numpy .npz file."""
+
+    def __init__(self, dmask: np.ndarray, vmask: np.ndarray, ref_key: np.ndarray, key_bits: int):
+        words = ck.mask_words(key_bits)
+        self.dmask = np.ascontiguousarray(np.asarray(dmask, np.uint64))
+        self.vmask = np.ascontiguousarray(np.asarray(vmask, np.uint64))
+        self.ref_key = np.ascontiguousarray(np.asarray(ref_key, np.uint8))
+        self.key_bits = int(key_bits)
+        if self.dmask.shape != (words,) or self.vmask.shape != (words,) or self.ref_key.size * 8 != key_bits:
+            raise ValueError("DS-metadata sizes do not match a key of %d bits" % key_bits)
+
+    @classmethod
+    def from_keys(cls, keys: torch.Tensor, ref_row: int = 0, kind: int | None = None) -> "DSMetadata":
+        """First build: the exact D-bitmap, the variant bitmap and the reference key of a column."""
+        col = ck.column(keys, kind)
+        return cls(first_build_dmask(keys, kind=kind), ck.mask_to_host(ck.ck_variant_bits(keys, ref_row, kind=kind)),
+                   ck.reference_key(keys, ref_row, kind=kind), 8 * int(col.key_bytes))
+
+    def save(self, path: str) -> None:
+        np.savez(path, dmask=self.dmask, vmask=self.vmask, ref_key=self.ref_key,
+                 key_bits=np.array([self.key_bits], np.int64))
+
+    @classmethod
+    def load(cls, path: str) -> "DSMetadata":
+        with np.load(path) as z:
+            return cls(z["dmask"], z["vmask"], z["ref_key"], int(z["key_bits"][0]))
+
+
 class Rebuild:
     """Buffers and launches for one key column and one D-bitmap.
 

@@ -494,3 +494,23 @@ def test_extract_hist_edge_cases():
     want = np.zeros((1, 16), np.int64)
     want[0, v & 15] = 1
     assert np.array_equal(h.cpu().numpy().astype(np.int64), want)
+
+
+def test_ds_metadata_restart(tmp_path):
+    """Checkpoint / resume as the paper has it (Sec. 4.2, 4.3): the first build's
+    DS-metadata is saved; after a 'restart' the loaded D-bitmap drives the
+    rebuild, which reproduces the oracle's order and refines to the same D."""
+    keys = synth.urls(3 * TILE + 9, synth.BASE_SEED + 91)
+    kd = to_dev(keys)
+    m = pipeline.DSMetadata.from_keys(kd, ref_row=5)
+    assert np.array_equal(m.dmask, oracle.dmask(keys))
+    assert np.array_equal(m.vmask, oracle.variant_mask(keys, 5))
+    assert np.array_equal(m.ref_key, keys[5])
+    path = str(tmp_path / "ds.npz")
+    m.save(path)
+    loaded = pipeline.DSMetadata.load(path)
+    r = pipeline.Rebuild(kd, loaded.dmask, fanout=64)
+    r.run()
+    torch.cuda.synchronize()
+    assert np.array_equal(ck.u32(r.rid_sorted)[:len(keys)], oracle.sort_rows(keys))
+    assert np.array_equal(ck.mask_to_host(r.refined), loaded.dmask)

@@ -179,3 +179,19 @@ def test_partial_key_mask_argument_errors(ckmod):
         with pytest.raises(ckmod.CkError) as e:
             ckmod.ck_partial_key_mask(z, z, key_bits, pk)
         assert e.value.status == ckmod.CK_EINVAL
+
+
+def test_ds_metadata_round_trip(tmp_path, ckmod):
+    """The persisted DS-metadata (Sec. 4.2) survives a save and a load
+    unchanged, and mismatched sizes are refused."""
+    from paper_2009_11543_gb300 import pipeline
+    rng = np.random.default_rng(12)
+    keys = rng.integers(0, 256, (500, 12), dtype=np.uint8)
+    m = pipeline.DSMetadata(oracle.dmask(keys), oracle.variant_mask(keys, 4), keys[4], 96)
+    path = str(tmp_path / "ds.npz")
+    m.save(path)
+    r = pipeline.DSMetadata.load(path)
+    assert np.array_equal(r.dmask, m.dmask) and np.array_equal(r.vmask, m.vmask)
+    assert np.array_equal(r.ref_key, keys[4]) and r.key_bits == 96
+    with pytest.raises(ValueError):
+        pipeline.DSMetadata(m.dmask, m.vmask, keys[4, :8], 96)
