@@ -569,7 +569,10 @@ ck_status ck_model_separators(const float* params, const ck_btree* tree, uint32_
  * Every buffer of a job is the caller's; jobs must not share buffers.
  *   digit_bits  radix digit width of the job's sort, 4 .. 11 (0 = 8); see
  *               ck_autotune_sort.
- *   ws          the job's sort workspace (ck_sort_workspace_bytes).
+ *   ws          the job's sort workspace (ck_sort_workspace_bytes); when it
+ *               holds, after that size rounded up to 256 bytes, a further
+ *               ceil(nbits / digit_bits) * 2^digit_bits uint32, the digit
+ *               counts are taken there while extracting (ck_extract_hist).
  * Errors: those of the underlying calls; CK_EINVAL for njobs == 0 or
  * njobs > CK_MAX_JOBS. */
 #define CK_MAX_JOBS 64u

@@ -83,13 +83,22 @@ ck_status ck_build_batched(const ck_index_job* jobs, uint32_t njobs, ck_stream s
         ck_stream jst = reinterpret_cast<ck_stream>(js);
         const uint32_t key_bits = 8 * jb.col.key_bytes;
         const uint32_t nbits = popcount_mask(jb.dmask, key_bits);
-        ck_status st = ck_extract(&jb.col, jb.dmask, jb.ck_words, jb.ck, jst);
+        ck_sort_opts o;
+        memset(&o, 0, sizeof(o));
+        o.digit_bits = jb.digit_bits;
+        // room after the sort's workspace for the digit counts: take them while extracting
+        const uint32_t rb = jb.digit_bits ? jb.digit_bits : 8u;
+        const size_t sort_bytes = (ck_sort_workspace_bytes(jb.col.n, jb.ck_words, nbits, &o) + 255) & ~(size_t)255;
+        const size_t hist_bytes = sizeof(uint32_t) * ((size_t)((nbits + rb - 1) / rb) << rb);
+        uint32_t* hist = nullptr;
+        if (nbits > 0 && jb.ws && jb.ws_bytes >= sort_bytes + hist_bytes)
+            hist = reinterpret_cast<uint32_t*>(static_cast<unsigned char*>(jb.ws) + sort_bytes);
+        ck_status st = hist ? ck_extract_hist(&jb.col, jb.dmask, jb.ck_words, jb.ck, rb, hist, jst)
+                            : ck_extract(&jb.col, jb.dmask, jb.ck_words, jb.ck, jst);
         if (st == CK_OK) {
-            ck_sort_opts o;
-            memset(&o, 0, sizeof(o));
-            o.digit_bits = jb.digit_bits;
+            o.hist = hist;
             st = ck_sort(jb.ck, nullptr, jb.ck_sorted, jb.rid_sorted, jb.col.n, jb.ck_words, nbits, &o, jb.ws,
-                         jb.ws_bytes, jst);
+                         hist ? sort_bytes : jb.ws_bytes, jst);
         }
         if (st == CK_OK)
             st = ck_build_index(jb.ck_sorted, jb.rid_sorted, jb.col.n, jb.ck_words, jb.dmask, key_bits, jb.fanout,

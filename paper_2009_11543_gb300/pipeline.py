@@ -269,7 +269,9 @@ class BatchedRebuild:
                 r.digit_bits, ms = ck.ck_autotune_sort(r.ck_in, r.ck_sorted, r.rid_sorted, r.n, r.K, r.nbits,
                                                        r.ws, tune_reps, cache_path)
                 self.tuned_ms.append(ms)
-            need = ck.ck_sort_workspace_bytes(r.n, r.K, r.nbits, r.digit_bits)
+            # the sort's workspace, then room for the digit counts taken while extracting
+            need = (ck.ck_sort_workspace_bytes(r.n, r.K, r.nbits, r.digit_bits) + 255) // 256 * 256
+            need += 4 * ((r.nbits + r.digit_bits - 1) // r.digit_bits << r.digit_bits)
             if need > r.ws.numel():
                 r.ws = torch.empty(need, dtype=torch.uint8, device=r.keys.device)
         self._trees = []
