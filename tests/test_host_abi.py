@@ -195,3 +195,34 @@ def test_ds_metadata_round_trip(tmp_path, ckmod):
     assert np.array_equal(r.ref_key, keys[4]) and r.key_bits == 96
     with pytest.raises(ValueError):
         pipeline.DSMetadata(m.dmask, m.vmask, keys[4, :8], 96)
+
+
+def test_argument_errors_of_later_entry_points(ckmod):
+    """Digit counting, partial keys, search, inserts and key encoding refuse
+    bad arguments synchronously, before any device work (the device pointers
+    below are never touched)."""
+    import ctypes
+    lib = ckmod._lib()
+    col = ckmod.ck_column(4096, 10, 8, 8, ckmod.CK_KIND_BYTES)
+    m = np.array([0xFFFFF00000000000], np.uint64)                    # 20 positions
+    for rb in (3, 12):
+        assert lib.ck_extract_hist(ctypes.byref(col), m.ctypes.data, 1, 4096, rb, 8192, None) == ckmod.CK_EINVAL
+    assert lib.ck_extract_hist(ctypes.byref(col), m.ctypes.data, 1, 4096, 8, None, None) == ckmod.CK_EINVAL
+    t = ckmod.ck_btree()
+    z = np.zeros(1, np.uint64)
+    ref = np.zeros(8, np.uint8)
+    for pk in (0, 33):
+        assert lib.ck_partial_keys(ctypes.byref(t), 4096, 1, z.ctypes.data, z.ctypes.data, ref.ctypes.data,
+                                   ctypes.byref(col), 8, pk, 8192, 8192, None) == ckmod.CK_EINVAL
+        assert lib.ck_search(ctypes.byref(t), ctypes.byref(col), 4096, None, pk, ctypes.byref(col), 8192, None,
+                             None, None) == ckmod.CK_EINVAL
+    q32 = ckmod.ck_column(4096, 10, 4, 4, ckmod.CK_KIND_U32)            # queries of another kind
+    assert lib.ck_search(ctypes.byref(t), ctypes.byref(col), 4096, None, 16, ctypes.byref(q32), 8192, None,
+                         None, None) == ckmod.CK_EINVAL
+    narrow = ckmod.ck_column(4096, 5, 4, 4, ckmod.CK_KIND_BYTES)        # batch of another width
+    assert lib.ck_insert_batch(ctypes.byref(col), 8192, ctypes.byref(narrow), 0, 12288, 16384, None, 0,
+                               None) == ckmod.CK_EINVAL
+    parts = (ckmod.ck_key_part * 1)()
+    assert lib.ck_encode_key(parts, 0, 10, 4096, 16, None) == ckmod.CK_EINVAL
+    parts[0] = ckmod.ck_key_part(4096, None, ckmod.CK_KIND_DECIMAL, 10, 8)   # decimal of 10 bytes
+    assert lib.ck_encode_key(parts, 1, 10, 8192, 16, None) == ckmod.CK_EINVAL
