@@ -281,33 +281,50 @@ ck_status ck_sort_static(const uint32_t* ck_in, const uint32_t* rid_in, uint32_t
  * parameters packed [w1, b1, w2, b2] (CK_MLP_PARAMS floats), on the feature
  * x = (top 24 bits of the nbits-bit compressed key) / 2^24, is trained on the
  * GPU by full-batch Adam to the empirical CDF (rank + 0.5) / S of a sorted
- * stride sample of S = n / sample_div keys (fitted on at most 65536 of its
- * points, taken at a fixed stride).  The buckets are the 2^bucket_bits
- * key ranges between the quantiles of the sorted sample (a key value that
- * fills several quantiles gets a bucket of its own); the model proposes each
- * key's bucket as floor(y(x) * B) and a short walk against the splitters makes
- * the assignment exact.  Two radix passes on the bucket id partition the pairs
- * stably, and each bucket is sorted in shared memory.
+ * stride sample of S = n / sample_div keys (fitted on at most 2048 of its
+ * points, taken at a fixed stride; one block, fixed-order sums, so the same
+ * input trains the same bits).
+ *
+ * The model proposes the bucket boundaries: over the sorted sample, the
+ * running maximum of y crosses b / B (B = 2^bucket_bits model buckets) at
+ * sample position c_b, and the boundary is the sample key there (moved to the
+ * start of its run of equal keys).  A key value with at least half an average
+ * bucket of sample copies gets a bucket of its own, [v, v + 1).  Where a
+ * model bucket holds more sample keys than a shared-memory sort can take
+ * (with a margin for sampling noise), sample quantiles cut it further;
+ * stats.model_boundary_frac is the share of boundaries the model set.  Every
+ * key's bucket is found from the model's guess by a short search against the
+ * boundaries (exact).  Two radix passes on the bucket id partition the pairs
+ * stably; each bucket (a contiguous key range in row-id order) is then sorted
+ * in shared memory and checked: adjacent keys ascend, the keys lie inside the
+ * bucket's range, equal keys keep row-id order, and a sum of 64-bit hashes of
+ * all (key, row id) pairs equals the input's (every row once, with its own
+ * key).
  *
  * ck_sort_learned gives exactly the output of ck_sort (stable, ties by row id,
- * sorted ck and rid).  A bucket whose keys are not all equal and that
- * exceeds what one block can sort is sorted by the plain radix sort on just
- * its segment.  A verification pass checks every adjacent output pair; if it
- * fails, the plain radix sort recomputes the result from ck_in and the call
- * returns CK_EVERIFY (the output is still exact).  The call synchronises its
- * stream (to read the oversize-bucket list and the verification flag).
+ * sorted ck and rid).  Everything is decided on the device: if a check fails,
+ * a bucket exceeds the shared-memory capacity, or the boundaries exceed the
+ * bucket id space, the plain radix sort (launched gated by the call, idle
+ * otherwise) recomputes the result from ck_in and the device status word
+ * records CK_EVERIFY (the output is still exact).  The call does not wait for
+ * the device and can be captured in a CUDA graph (the library looks up its
+ * device status word on the first call of any entry point on a device: make
+ * one call before capturing).
  *   ck_in      device, ck_words * CK_LD(n), word-major; read only.
  *   ck_out, rid_out  device outputs as ck_sort (ck_out != ck_in).
  *   ck_words   1 .. 8.
- *   opts       NULL for defaults.  stats: HOST, optional.
+ *   opts       NULL for defaults.
+ *   stats      DEVICE, optional: one ck_learned_stats, written by the call's
+ *              last kernel (read it after the stream has reached it).
+ *   params_out DEVICE, optional: CK_MLP_PARAMS floats, the trained model.
  *   ws         device, >= ck_sort_learned_workspace_bytes(), 256-byte aligned.
- * Errors: CK_EINVAL, CK_ENOMEM; CK_EVERIFY as above. */
+ * Errors (synchronous): CK_EINVAL, CK_ENOMEM, CK_ECUDA. */
 #define CK_MLP_HIDDEN 16
 #define CK_MLP_PARAMS (3 * CK_MLP_HIDDEN + 1)
 
 typedef struct ck_learned_opts {
-    uint32_t bucket_bits; /* log2 of the bucket count, 8 .. 16; 0 = chosen from n (about half the
-                             pairs one block sorts in shared memory per bucket) */
+    uint32_t bucket_bits; /* log2 of the model's bucket count B, 1 .. 15; 0 = chosen from n (an average
+                             bucket about half of what one block sorts in shared memory) */
     uint32_t sample_div;  /* one sample per sample_div keys; 0 = 100 (1%) */
     uint32_t epochs;      /* Adam epochs; 0 = 100 */
     float lr;             /* Adam learning rate; 0 = 1e-3 */
@@ -315,24 +332,33 @@ typedef struct ck_learned_opts {
     uint32_t reserved;    /* must be 0 */
 } ck_learned_opts;
 
-/* No model: buckets are plain sample quantiles and every key's bucket is found
- * by binary search over the splitters (the method without the network). */
+/* No model: the boundaries are sample quantiles and every key's bucket is
+ * found by binary search (the method without the network). */
 #define CK_LEARNED_NO_MODEL 1u
-/* Test-only: the verification pass reports a failure, forcing the fallback. */
+/* Test-only: the final check reports a failure, forcing the fallback. */
 #define CK_LEARNED_INJECT_VERIFY_FAIL 2u
+/* Test-only: the local sort exchanges the row ids of the first two pairs of
+ * every bucket it sorts, which the checks must catch (fallback). */
+#define CK_LEARNED_INJECT_RID_SWAP 4u
 
 typedef struct ck_learned_stats {
-    float train_loss;           /* mean squared error of the model on the sample */
+    float train_loss;           /* mean squared error of the model on its training points */
     float mean_search_steps;    /* splitter comparisons per key to reach the exact bucket: from the model's
                                    guess (galloping search), or a binary search without the model */
     uint32_t max_search_steps;  /* most comparisons for one key */
-    uint32_t buckets;           /* 2^bucket_bits */
+    uint32_t buckets;           /* buckets after the boundaries were placed (splitters + 1) */
     uint32_t sample_size;       /* S */
     uint32_t max_bucket;        /* largest bucket (pairs) */
     uint32_t sorted_segments;   /* buckets sorted in shared memory */
-    uint32_t constant_buckets;  /* large buckets of equal keys left as partitioned */
-    uint32_t oversize_buckets;  /* large non-constant buckets sorted by the plain radix on their segment */
-    uint32_t fell_back;         /* 1 if verification failed and the plain radix sort produced the result */
+    uint32_t constant_buckets;  /* buckets of one key value, left as partitioned */
+    uint32_t oversize_buckets;  /* buckets over the shared-memory capacity (they force the fallback) */
+    uint32_t fell_back;         /* 1 if the plain radix sort produced the result */
+    uint32_t model_buckets;     /* B */
+    uint32_t model_boundaries;  /* boundaries placed at a model crossing */
+    float model_boundary_frac;  /* model_boundaries / (buckets - 1) */
+    uint32_t heavy_keys;        /* key values given a bucket of their own */
+    uint32_t capacity;          /* pairs one block sorts in shared memory */
+    uint32_t reserved;
 } ck_learned_stats;
 
 size_t ck_sort_learned_workspace_bytes(uint64_t n, uint32_t ck_words, uint32_t nbits, const ck_learned_opts* opts);

@@ -39,6 +39,7 @@ EXPORTED = ["ck_variant_bits", "ck_distinction_bits", "ck_extract", "ck_sort_wor
             "ck_autotune_sort", "ck_model_separators", "ck_insert_workspace_bytes", "ck_insert_batch", "ck_encode_key",
             "ck_partial_key_mask", "ck_partial_keys", "ck_search", "ck_extract_hist"]
 CK_SORT_STATIC_SCRATCH_BYTES = 32 << 20
+CK_LEARNED_STATS_BYTES = 64
 
 
 class CkError(RuntimeError):
@@ -67,10 +68,13 @@ class ck_learned_stats(ctypes.Structure):
                 ("max_search_steps", ctypes.c_uint32), ("buckets", ctypes.c_uint32),
                 ("sample_size", ctypes.c_uint32), ("max_bucket", ctypes.c_uint32),
                 ("sorted_segments", ctypes.c_uint32), ("constant_buckets", ctypes.c_uint32),
-                ("oversize_buckets", ctypes.c_uint32), ("fell_back", ctypes.c_uint32)]
+                ("oversize_buckets", ctypes.c_uint32), ("fell_back", ctypes.c_uint32),
+                ("model_buckets", ctypes.c_uint32), ("model_boundaries", ctypes.c_uint32),
+                ("model_boundary_frac", ctypes.c_float), ("heavy_keys", ctypes.c_uint32),
+                ("capacity", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
 
     def as_dict(self) -> dict:
-        return {name: getattr(self, name) for name, _ in self._fields_}
+        return {name: getattr(self, name) for name, _ in self._fields_ if name != "reserved"}
 
 
 class ck_btree_shape(ctypes.Structure):
@@ -120,8 +124,7 @@ def _lib():
         LO = ctypes.POINTER(ck_learned_opts)
         lib.ck_sort_learned_workspace_bytes.argtypes = [U64, U32, U32, LO]
         lib.ck_sort_learned_workspace_bytes.restype = ctypes.c_size_t
-        lib.ck_sort_learned.argtypes = [P, P, P, U64, U32, U32, LO, ctypes.POINTER(ck_learned_stats), P, P,
-                                        ctypes.c_size_t, P]
+        lib.ck_sort_learned.argtypes = [P, P, P, U64, U32, U32, LO, P, P, P, ctypes.c_size_t, P]
         lib.ck_mlp_workspace_bytes.restype = ctypes.c_size_t
         lib.ck_mlp_loss_grad.argtypes = [P, P, P, U64, P, P, P, ctypes.c_size_t, P]
         JP = ctypes.POINTER(ck_index_job)
@@ -405,6 +408,7 @@ CK_MLP_HIDDEN = 16
 CK_MLP_PARAMS = 3 * CK_MLP_HIDDEN + 1
 CK_LEARNED_NO_MODEL = 1
 CK_LEARNED_INJECT_VERIFY_FAIL = 2
+CK_LEARNED_INJECT_RID_SWAP = 4
 
 
 def learned_opts(bucket_bits=0, sample_div=0, epochs=0, lr=0.0, flags=0) -> ck_learned_opts:
@@ -416,19 +420,31 @@ def ck_sort_learned_workspace_bytes(n: int, ck_words: int, nbits: int, opts: ck_
                                                       ctypes.byref(opts) if opts is not None else None))
 
 
+def learned_stats_buffer(device) -> torch.Tensor:
+    """Device buffer for one ck_learned_stats (read it with learned_stats())."""
+    return torch.zeros(CK_LEARNED_STATS_BYTES // 4, dtype=torch.int32, device=device)
+
+
+def learned_stats(buf: torch.Tensor) -> dict:
+    """The ck_learned_stats a learned sort wrote into buf (synchronises with the copy)."""
+    raw = buf.cpu().numpy().tobytes()
+    return ck_learned_stats.from_buffer_copy(raw).as_dict()
+
+
 def ck_sort_learned(ck_in: torch.Tensor, ck_out: torch.Tensor, rid_out: torch.Tensor, n: int, ck_words: int,
-                    nbits: int, ws: torch.Tensor, opts: ck_learned_opts | None = None, stream=None):
-    """Returns (status, stats dict, trained parameters as numpy float32 or None).
-    CK_EVERIFY (the exact fallback ran) is returned, not raised."""
-    stats = ck_learned_stats()
-    params = np.zeros(CK_MLP_PARAMS, np.float32)
+                    nbits: int, ws: torch.Tensor, opts: ck_learned_opts | None = None, stats: torch.Tensor | None = None,
+                    params: torch.Tensor | None = None, stream=None) -> None:
+    """Queues the learned sort (asynchronous; nothing is read back).  stats: a
+    learned_stats_buffer() or None; params: a device float32 tensor of
+    CK_MLP_PARAMS or None.  A fallback to the plain sort shows as CK_EVERIFY in
+    ck_device_status()."""
     st = _lib().ck_sort_learned(_ptr(ck_in), _ptr(ck_out), _ptr(rid_out), n, ck_words, nbits,
-                                ctypes.byref(opts) if opts is not None else None, ctypes.byref(stats), _ptr(params),
+                                ctypes.byref(opts) if opts is not None else None,
+                                _ptr(stats) if stats is not None else None,
+                                _ptr(params) if params is not None else None,
                                 _ptr(ws), ws.numel() * ws.element_size(), _stream(stream))
-    if st not in (CK_OK, CK_EVERIFY):
+    if st != CK_OK:
         raise CkError(st, "ck_sort_learned")
-    no_model = opts is not None and (opts.flags & CK_LEARNED_NO_MODEL)
-    return st, stats.as_dict(), (None if no_model else params)
 
 
 def ck_mlp_workspace_bytes() -> int:

@@ -420,6 +420,9 @@ struct PassArgs {
     uint32_t* tile_counter;       // zeroed
     uint32_t spin_limit, inject;
     unsigned long long* status;
+    const uint32_t* gate;         // NULL, or: the pass runs only while *gate == gate_run (decided on the device)
+    uint32_t gate_run;
+    uint32_t tiles;               // set by the launcher
 };
 
 // One onesweep pass with digit width rb (4..11); tiles = ceil(n / kPassTile).
@@ -435,9 +438,14 @@ struct SortPlan {
 };
 // ld == 0 selects CK_LD(n); a larger ld sorts a segment of wider arrays in place.
 bool make_sort_plan(uint64_t n, uint32_t K, uint32_t nbits, uint32_t digit_bits, SortPlan* p, uint64_t ld = 0);
+// gate != NULL: every kernel of the sort returns at once unless *gate != 0
+// when it runs (a sort the device decides to need; the launches are made
+// either way, so the host never waits for the decision).  A gated sort must
+// not be in place, must have passes > 0 and takes no hist_in.
 cudaError_t run_sort(const SortPlan& p, const uint32_t* ck_in, const uint32_t* rid_in, uint32_t* ck_out,
                      uint32_t* rid_out, uint64_t n, uint32_t nbits, uint32_t spin_limit, uint32_t inject,
-                     uint32_t flags, cudaEvent_t* pass_events, unsigned char* ws, cudaStream_t s, const uint32_t* hist_in = nullptr);
+                     uint32_t flags, cudaEvent_t* pass_events, unsigned char* ws, cudaStream_t s,
+                     const uint32_t* hist_in = nullptr, const uint32_t* gate = nullptr);
 
 struct BtreeArgs {
     const uint32_t* ck;  // word-major, K words, leading dimension ld

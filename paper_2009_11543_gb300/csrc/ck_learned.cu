@@ -1,25 +1,23 @@
 // ck_learned.cu -- the learned-partition sort (not in the paper): a tiny fp32
-// CDF model, trained on the GPU on a sample of the compressed keys, places
-// every key in one of about B = 2^bucket_bits key-range buckets; two radix
-// passes on the bucket id partition the pairs stably, and each bucket is then
-// sorted in shared memory.  The result is the same permutation as the plain
-// radix sort:
+// CDF model, trained on the GPU on a sample of the compressed keys, proposes
+// the bucket boundaries of a stable partition; every bucket is then sorted in
+// shared memory (ck_local_sort.cu).  The result is the same permutation as the
+// plain radix sort:
 //
-//  * the buckets are ranges between monotone splitters (the B-quantiles of the
-//    sorted sample moved to the nearer end of their run of equal keys, with
-//    heavy keys isolated in buckets of their own), so a stable partition by
-//    bucket followed by a stable sort inside each bucket is a stable sort of
-//    the whole column;
-//  * the model proposes each key's bucket as floor(y(x) * B) in O(1); a short
-//    walk against the splitters makes the assignment exact (a far-off guess
-//    falls back to binary search), so a poor model costs time, not
-//    correctness.  Without the model every key needs a binary search;
-//  * a bucket is sorted by the 32-bit window at its first varying bit, and
-//    ties are settled below the window; a non-constant bucket too large for a
-//    block is sorted by the plain radix sort on its segment;
-//  * a verification pass checks every adjacent output pair; if it fails, the
-//    plain radix sort recomputes the result from the untouched input (status
-//    CK_EVERIFY).
+//  * the buckets are key ranges between strictly increasing splitters: the
+//    model's crossings of b / B over the sorted sample (moved to the start of
+//    their run of equal keys), a bucket [v, v + 1) of its own for every heavy
+//    key value, and sample quantiles inside any model bucket too large for a
+//    shared-memory sort.  A stable partition by bucket followed by a stable
+//    sort inside each bucket is a stable sort of the whole column;
+//  * the model also proposes each key's bucket; a short search against the
+//    splitters makes the assignment exact, so a poor model costs time, never
+//    correctness;
+//  * every check and decision runs on the device: when a check fails, the
+//    plain radix sort -- launched gated on a device flag by every call, and
+//    idle otherwise -- recomputes the output from the untouched input, and the
+//    device status word records CK_EVERIFY.  Nothing waits for the host, so
+//    the call can be captured in a CUDA graph.
 //
 // The model: y(x) = b2 + sum_j w2_j relu(w1_j x + b1_j), 16 hidden units, on
 // x = the top 24 bits of the compressed key / 2^24, fitted by full-batch Adam
@@ -28,7 +26,7 @@
 #include <cmath>
 #include <cstring>
 
-#include "ck_internal.cuh"
+#include "ck_learned.cuh"
 
 namespace ck {
 
@@ -36,8 +34,16 @@ constexpr int kHidden = CK_MLP_HIDDEN;
 constexpr int kParams = CK_MLP_PARAMS;  // [w1(16), b1(16), w2(16), b2]
 constexpr int kRed = kParams + 1;       // gradient + loss
 constexpr int kTrainThreads = 256;
-constexpr int kMaxLearnedWords = 8;
-constexpr uint64_t kMaxTrainPoints = 65536;  // training uses a stride subsample of the sorted sample
+constexpr uint64_t kTrainPoints = 2048;  // training points: a stride subsample of the sorted sample
+constexpr int kScanBlock = 1024;         // elements per block of the sample scans and gap compactions
+constexpr uint32_t kMaxModelBuckets = 1u << 15;
+constexpr uint32_t kMaxBucketIds = 1u << 16;  // bucket ids of two 8-bit partition passes
+constexpr uint32_t kMaxConst = 1024;          // large constant buckets listed for the chunked check
+constexpr uint32_t kStagedSplitters = 48 * 1024;  // splitters whose top 32 bits the bucket kernel stages
+constexpr int kPrefixBits = 12;
+
+// flags of a boundary gap g (between sample keys g - 1 and g)
+constexpr uint32_t kGapModel = 1, kGapQuant = 2, kGapHeavyStart = 4, kGapHeavyEnd = 8;
 
 __device__ __forceinline__ float mlp_eval(const float* p, float x) {
     float y = p[3 * kHidden];
@@ -184,104 +190,77 @@ __global__ void mlp_grad_sum_kernel(const float* __restrict__ partial, uint32_t 
 }
 
 // ------------------------------------------------------------ training
-struct TrainArgs {
-    const float* xs;      // features of the sorted sample, [S]
-    uint64_t S;           // sample size (targets (i + 0.5) / S)
-    uint64_t T, stride;   // training points: sample indices 0, stride, ..., (T - 1) * stride
-    float* params;        // in: initial parameters, out: trained
-    float* partial;       // [2][gridDim][kRed]
-    unsigned* barrier;    // zeroed
-    float* loss;          // out: loss of the last epoch
-    uint32_t epochs;
-    float lr;
-    uint32_t spin_limit;
-    unsigned long long* status;
-};
-
-__device__ __forceinline__ uint32_t ld_acquire(const unsigned* p) {
-    uint32_t v;
-    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-    return v;
-}
-
-// All blocks of the (cooperatively launched, hence co-resident) grid arrive;
-// the wait is bounded and reports CK_ETIMEOUT instead of hanging.
-__device__ void grid_barrier(unsigned* ctr, unsigned target, uint32_t limit, unsigned long long* status) {
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        __threadfence();
-        atomicAdd(ctr, 1u);
-        uint32_t polls = 0;
-        while (ld_acquire(ctr) < target) {
-            if (++polls > limit) {
-                report(status, CK_ETIMEOUT, (1ull << 46) | target);
-                break;
-            }
-            __nanosleep(64);
-        }
-        __threadfence();
-    }
-    __syncthreads();
-}
-
-// Full-batch Adam (beta1 0.9, beta2 0.999, eps 1e-8).  Every block keeps the
-// parameters and the moments in shared memory and applies the same update to
-// the same fixed-order gradient sum, so all copies stay identical.
-__global__ void __launch_bounds__(kTrainThreads) mlp_train_kernel(const TrainArgs a) {
+// Full-batch Adam (beta1 0.9, beta2 0.999, eps 1e-8) by one block on T points
+// of the sorted sample (indices 0, stride, 2 stride, ...; targets (i + 0.5) /
+// S): the features sit in shared memory, the gradient is summed in a fixed
+// order, so the same input trains the same bits.
+__global__ void __launch_bounds__(kTrainThreads) mlp_train_kernel(const float* __restrict__ xs, uint64_t S,
+                                                                   uint64_t T, uint64_t stride, float* params,
+                                                                   float* loss, uint32_t epochs, float lr) {
     __shared__ float p[kParams], m1[kParams], m2[kParams];
     __shared__ float red[(kTrainThreads / 32) * kRed];
     __shared__ float out[kRed];
+    __shared__ float xt[kTrainPoints];
     const int tid = threadIdx.x;
+    for (uint64_t i = tid; i < T; i += kTrainThreads) xt[i] = xs[i * stride];
     if (tid < kParams) {
-        p[tid] = a.params[tid];
+        p[tid] = params[tid];
         m1[tid] = 0.0f;
         m2[tid] = 0.0f;
     }
     __syncthreads();
-    const float scale = 1.0f / (float)a.T, tscale = 1.0f / (float)a.S;
-    const uint64_t i0 = a.T * blockIdx.x / gridDim.x, i1 = a.T * (blockIdx.x + 1) / gridDim.x;
-    float b1t = 1.0f, b2t = 1.0f, last_loss = 0.0f;
-    for (uint32_t ep = 0; ep < a.epochs; ++ep) {
+    const float scale = 1.0f / (float)T, tscale = 1.0f / (float)S;
+    float b1t = 1.0f, b2t = 1.0f, last = 0.0f;
+    for (uint32_t ep = 0; ep < epochs; ++ep) {
         float g[kRed];
 #pragma unroll
         for (int q = 0; q < kRed; ++q) g[q] = 0.0f;
-        for (uint64_t i = i0 + tid; i < i1; i += kTrainThreads) {
-            const uint64_t si = i * a.stride;
-            g[kParams] += mlp_accumulate(p, a.xs[si], ((float)si + 0.5f) * tscale, scale, g);
-        }
+        for (uint64_t i = tid; i < T; i += kTrainThreads)
+            g[kParams] += mlp_accumulate(p, xt[i], ((float)(i * stride) + 0.5f) * tscale, scale, g);
         block_reduce_red(g, red, out);
-        float* part = a.partial + (uint64_t)(ep & 1) * gridDim.x * kRed;
-        if (tid < kRed) part[(uint64_t)blockIdx.x * kRed + tid] = out[tid];
-        grid_barrier(a.barrier, (ep + 1) * gridDim.x, a.spin_limit, a.status);
         b1t *= 0.9f;
         b2t *= 0.999f;
-        if (tid < kRed) {
-            float s = 0.0f;
-            for (uint32_t b = 0; b < gridDim.x; ++b) s += __ldcg(&part[(uint64_t)b * kRed + tid]);
-            if (tid < kParams) {
-                m1[tid] = 0.9f * m1[tid] + 0.1f * s;
-                m2[tid] = 0.999f * m2[tid] + 0.001f * s * s;
-                const float mh = m1[tid] / (1.0f - b1t), vh = m2[tid] / (1.0f - b2t);
-                p[tid] -= a.lr * mh / (sqrtf(vh) + 1e-8f);
-            } else {
-                last_loss = s * scale;
-            }
+        if (tid < kParams) {
+            const float s = out[tid];
+            m1[tid] = 0.9f * m1[tid] + 0.1f * s;
+            m2[tid] = 0.999f * m2[tid] + 0.001f * s * s;
+            const float mh = m1[tid] / (1.0f - b1t), vh = m2[tid] / (1.0f - b2t);
+            p[tid] -= lr * mh / (sqrtf(vh) + 1e-8f);
+        } else if (tid == kParams) {
+            last = out[kParams] * scale;
         }
         __syncthreads();
     }
-    if (blockIdx.x == 0) {
-        if (tid < kParams) a.params[tid] = p[tid];
-        if (tid == kParams && a.loss) *a.loss = last_loss;
-    }
+    if (tid < kParams) params[tid] = p[tid];
+    if (tid == kParams) *loss = last;
 }
 
-
-// ------------------------------------------------------------ splitters
-// Multi-word comparison of key a (K words, entry-major or registers) with b.
-__device__ __forceinline__ int cmp_words(const uint32_t* a, const uint32_t* b, uint32_t K) {
-    for (int w = (int)K - 1; w >= 0; --w)
-        if (a[w] != b[w]) return a[w] < b[w] ? -1 : 1;
+// ------------------------------------------------------------ sample keys
+// Sample key i against the K words v: -1, 0, 1.
+__device__ __forceinline__ int cmp_sample(const uint32_t* smp, uint64_t ld_s, uint32_t K, uint64_t i,
+                                          const uint32_t* v) {
+    for (int w = (int)K - 1; w >= 0; --w) {
+        const uint32_t x = smp[(uint64_t)w * ld_s + i];
+        if (x != v[w]) return x < v[w] ? -1 : 1;
+    }
     return 0;
+}
+
+__device__ __forceinline__ void load_sample(const uint32_t* smp, uint64_t ld_s, uint32_t K, uint64_t i, uint32_t* v) {
+    for (uint32_t w = 0; w < K; ++w) v[w] = smp[(uint64_t)w * ld_s + i];
+}
+
+// First position in [a, c] whose key equals sample key c (the start of its run).
+__device__ uint64_t run_start(const uint32_t* smp, uint64_t ld_s, uint32_t K, uint64_t a, uint64_t c) {
+    uint32_t v[kMaxLearnedWords];
+    load_sample(smp, ld_s, K, c, v);
+    uint64_t lo = a, hi = c;
+    while (lo < hi) {
+        const uint64_t mid = (lo + hi) >> 1;
+        if (cmp_sample(smp, ld_s, K, mid, v) < 0) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
 }
 
 // Is the K-word key v the largest nbits-bit key (no v + 1)?
@@ -294,110 +273,344 @@ __device__ __forceinline__ bool is_max_key(const uint32_t* v, uint32_t K, uint32
     return true;
 }
 
-// Splitters from the sorted sample.  Quantile b (1 <= b < B) sits at sample
-// position q_b = floor(b S / B) with value v.  The sample holds v at [i0, i1);
-// moving the bucket boundary off the quantile to the nearer end of that run
-// (splitter v puts the boundary at i0, v + 1 at i1) keeps every copy of v in
-// one bucket and moves the boundary by at most half the run.  A value with at
-// least `heavy` sample copies gets a bucket of its own, [v, v + 1) (splitters
-// v and v + 1 at its first quantile); later quantiles inside the same run
-// repeat the run's last splitter (empty buckets).  codes[b - 1]: bits 0-1 =
-// choice with heavy buckets, bits 2-3 = choice without (1: v, 2: v + 1,
-// 3: v and v + 1).
-__global__ void quantile_kernel(const uint32_t* __restrict__ sample, uint64_t ld_s, uint64_t S, uint32_t K,
-                                uint32_t B, uint32_t nbits, uint64_t heavy, uint8_t* __restrict__ codes) {
-    for (uint32_t b = blockIdx.x * blockDim.x + threadIdx.x + 1; b < B; b += gridDim.x * blockDim.x) {
-        uint64_t q = (uint64_t)b * S / B;
-        if (q >= S) q = S - 1;
-        uint32_t v[kMaxLearnedWords];
-        for (uint32_t w = 0; w < K; ++w) v[w] = sample[(uint64_t)w * ld_s + q];
-        auto cmp_at = [&](uint64_t i) {  // sample[i] vs v
-            for (int w = (int)K - 1; w >= 0; --w) {
-                const uint32_t x = sample[(uint64_t)w * ld_s + i];
-                if (x != v[w]) return x < v[w] ? -1 : 1;
-            }
-            return 0;
-        };
-        uint64_t lo = 0, hi = q;  // i0: first position with sample >= v
-        while (lo < hi) {
-            const uint64_t mid = (lo + hi) >> 1;
-            if (cmp_at(mid) < 0) lo = mid + 1;
-            else hi = mid;
-        }
-        const uint64_t i0 = lo;
-        lo = q + 1;
-        hi = S;  // i1: first position with sample > v
-        while (lo < hi) {
-            const uint64_t mid = (lo + hi) >> 1;
-            if (cmp_at(mid) <= 0) lo = mid + 1;
-            else hi = mid;
-        }
-        const uint64_t i1 = lo;
-        // the first quantile inside the run decides for all of them
-        uint64_t bf = (i0 * B + S - 1) / S;  // smallest b' with floor(b' S / B) >= i0
-        if (bf < 1) bf = 1;
-        uint64_t qf = bf * S / B;
-        if (qf >= S) qf = S - 1;
-        const bool top = is_max_key(v, K, nbits);
-        const bool up = !top && (i1 - qf) < (qf - i0);
-        const bool is_heavy = !top && i1 - i0 >= heavy;
-        const uint32_t single = up ? 2u : 1u;
-        const uint32_t with_heavy = is_heavy ? (bf == b ? 3u : 2u) : single;
-        codes[b - 1] = (uint8_t)(with_heavy | (single << 2));
+// ------------------------------------------------------------ boundaries
+// 1. the model over the sorted sample and the running maximum of its output,
+//    block by block (ys = block-local running maximum, bmax = block maximum).
+__global__ void __launch_bounds__(256) model_ys_kernel(const float* __restrict__ xs, uint64_t S,
+                                                       const float* __restrict__ params, float* __restrict__ ys,
+                                                       float* __restrict__ bmax) {
+    __shared__ float p[kParams];
+    __shared__ float wtot[8];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid < kParams) p[tid] = params[tid];
+    __syncthreads();
+    const uint64_t base = (uint64_t)blockIdx.x * kScanBlock + 4 * (uint64_t)tid;
+    float y[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        y[k] = base + k < S ? mlp_eval(p, xs[base + k]) : -INFINITY;
+        if (k) y[k] = fmaxf(y[k], y[k - 1]);
+    }
+    float inc = y[3];
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const float t = __shfl_up_sync(kFull, inc, o);
+        if (lane >= o) inc = fmaxf(inc, t);
+    }
+    if (lane == 31) wtot[warp] = inc;
+    __syncthreads();
+    float before = -INFINITY;
+    for (int w = 0; w < warp; ++w) before = fmaxf(before, wtot[w]);
+    float excl = __shfl_up_sync(kFull, inc, 1);
+    excl = fmaxf(before, lane ? excl : -INFINITY);
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+        if (base + k < S) ys[base + k] = fmaxf(excl, y[k]);
+    if (tid == 0) {
+        float m = wtot[0];
+        for (int w = 1; w < 8; ++w) m = fmaxf(m, wtot[w]);
+        bmax[blockIdx.x] = m;
     }
 }
 
-// Writes the splitters in order (one block): with heavy buckets when all of
-// them fit max_buckets, else without.  nsplit[0] = number of splitters (the
-// buckets are [spl[b - 1], spl[b]), b = 0 .. nsplit, open at both ends).
-__global__ void __launch_bounds__(1024) emit_splitters_kernel(const uint32_t* __restrict__ sample, uint64_t ld_s,
-                                                              uint64_t S, uint32_t K, uint32_t B,
-                                                              uint32_t max_buckets,
-                                                              const uint8_t* __restrict__ codes,
-                                                              uint32_t* __restrict__ spl, uint32_t* nsplit) {
-    __shared__ uint32_t part[1024];
-    __shared__ uint32_t s_heavy;
-    const uint32_t tid = threadIdx.x, nq = B - 1;
-    const uint32_t per = (nq + 1023) / 1024, lo = tid * per, hi = min(nq, lo + per);
-    if (tid == 0) s_heavy = 0;
-    __syncthreads();
-    uint32_t extra = 0;
-    for (uint32_t c = lo; c < hi; ++c) extra += (codes[c] & 3u) == 3u ? 1u : 0u;
-    if (extra) atomicAdd(&s_heavy, extra);
-    __syncthreads();
-    const uint32_t shift = nq + s_heavy + 1 <= max_buckets ? 0u : 2u;
-    uint32_t cnt = 0;
-    for (uint32_t c = lo; c < hi; ++c) cnt += ((codes[c] >> shift) & 3u) == 3u ? 2u : 1u;
-    part[tid] = cnt;
+// 2. the maximum of all earlier blocks (one block).
+__global__ void __launch_bounds__(1024) max_carry_kernel(const float* __restrict__ bmax, uint32_t nblk,
+                                                         float* __restrict__ carry) {
+    __shared__ float part[1024];
+    const uint32_t tid = threadIdx.x, per = (nblk + 1023) / 1024, lo = tid * per, hi = min(nblk, lo + per);
+    float m = -INFINITY;
+    for (uint32_t j = lo; j < hi; ++j) m = fmaxf(m, bmax[j]);
+    part[tid] = m;
     __syncthreads();
     if (tid == 0) {
-        uint32_t run = 0;
+        float run = -INFINITY;
         for (int t = 0; t < 1024; ++t) {
-            const uint32_t x = part[t];
+            const float x = part[t];
             part[t] = run;
-            run += x;
+            run = fmaxf(run, x);
         }
-        *nsplit = run;
     }
     __syncthreads();
-    uint32_t at = part[tid];
-    for (uint32_t c = lo; c < hi; ++c) {
-        const uint32_t code = (codes[c] >> shift) & 3u;
-        uint64_t q = (uint64_t)(c + 1) * S / B;
-        if (q >= S) q = S - 1;
-        if (code & 1u) {  // v
-            for (uint32_t w = 0; w < K; ++w) spl[(uint64_t)at * K + w] = sample[(uint64_t)w * ld_s + q];
-            ++at;
+    float run = part[tid];
+    for (uint32_t j = lo; j < hi; ++j) {
+        carry[j] = run;
+        run = fmaxf(run, bmax[j]);
+    }
+}
+
+// 3. model boundary b (0 < b < B): the first sample position where the running
+//    maximum of y reaches b / B, moved to the start of its run of equal keys.
+__global__ void model_cross_kernel(const float* __restrict__ ys, const float* __restrict__ bmax,
+                                   const float* __restrict__ carry, uint32_t nblk, uint64_t S, uint32_t B,
+                                   const uint32_t* __restrict__ smp, uint64_t ld_s, uint32_t K,
+                                   uint32_t* __restrict__ mgap, uint32_t* __restrict__ flag) {
+    for (uint32_t b = blockIdx.x * blockDim.x + threadIdx.x; b <= B; b += gridDim.x * blockDim.x) {
+        if (b == 0 || b == B) {
+            mgap[b] = b == 0 ? 0u : (uint32_t)S;
+            continue;
         }
-        if (code & 2u) {  // v + 1
-            uint32_t carry = 1;
-            for (uint32_t w = 0; w < K; ++w) {
-                const uint64_t sum = (uint64_t)sample[(uint64_t)w * ld_s + q] + carry;
-                spl[(uint64_t)at * K + w] = (uint32_t)sum;
-                carry = (uint32_t)(sum >> 32);
+        const float target = (float)b / (float)B;
+        uint32_t lo = 0, hi = nblk;
+        while (lo < hi) {
+            const uint32_t mid = (lo + hi) >> 1;
+            if (fmaxf(carry[mid], bmax[mid]) >= target) hi = mid;
+            else lo = mid + 1;
+        }
+        uint64_t c = S;
+        if (lo < nblk) {
+            const uint64_t b0 = (uint64_t)lo * kScanBlock;
+            if (carry[lo] >= target) {
+                c = b0;
+            } else {
+                uint64_t l = b0, h = min(S, b0 + kScanBlock) - 1;  // ys[h] >= target
+                while (l < h) {
+                    const uint64_t mid = (l + h) >> 1;
+                    if (ys[mid] >= target) h = mid;
+                    else l = mid + 1;
+                }
+                c = l;
             }
-            ++at;
         }
+        const uint64_t p = c >= S ? S : run_start(smp, ld_s, K, 0, c);
+        mgap[b] = (uint32_t)p;
+        if (p > 0 && p < S) atomicOr(&flag[p], kGapModel);
+    }
+}
+
+// Without the model: the B-quantiles of the sample, moved to run starts.
+__global__ void quantile_flag_kernel(uint64_t S, uint32_t B, const uint32_t* __restrict__ smp, uint64_t ld_s,
+                                     uint32_t K, uint32_t* __restrict__ flag) {
+    for (uint32_t b = blockIdx.x * blockDim.x + threadIdx.x + 1; b < B; b += gridDim.x * blockDim.x) {
+        const uint64_t c = (uint64_t)b * S / B;
+        const uint64_t p = run_start(smp, ld_s, K, 0, c);
+        if (p > 0 && p < S) atomicOr(&flag[p], kGapQuant);
+    }
+}
+
+// 4. heavy keys: a run of at least h equal sample keys [i, r1) gets the bucket
+//    [v, v + 1): boundary gaps i (value v) and r1 (value v + 1).
+__global__ void heavy_kernel(uint64_t S, uint64_t h, const uint32_t* __restrict__ smp, uint64_t ld_s, uint32_t K,
+                             uint32_t nbits, uint32_t* __restrict__ flag, LearnedMisc* misc) {
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i + h <= S;
+         i += (uint64_t)gridDim.x * blockDim.x) {
+        uint32_t v[kMaxLearnedWords];
+        load_sample(smp, ld_s, K, i, v);
+        if (i > 0 && cmp_sample(smp, ld_s, K, i - 1, v) == 0) continue;  // not a run start
+        if (cmp_sample(smp, ld_s, K, i + h - 1, v) != 0) continue;       // run shorter than h
+        uint64_t lo = i + h, hi = S;  // first position past the run
+        while (lo < hi) {
+            const uint64_t mid = (lo + hi) >> 1;
+            if (cmp_sample(smp, ld_s, K, mid, v) <= 0) lo = mid + 1;
+            else hi = mid;
+        }
+        atomicOr(&flag[i], kGapHeavyStart);
+        if (!is_max_key(v, K, nbits)) atomicOr(&flag[lo], kGapHeavyEnd);
+        atomicAdd(&misc->counts[5], 1u);
+    }
+}
+
+// Splitter values at gap g: an end value (sample g - 1 plus one) for a heavy
+// run ending there, a start value (sample g) for any other boundary; one value
+// when the two coincide.
+__device__ __forceinline__ void gap_values(const uint32_t* smp, uint64_t ld_s, uint32_t K, uint32_t nbits, uint64_t S,
+                                           uint64_t g, uint32_t f, bool* has_end, bool* has_start) {
+    *has_start = (f & (kGapModel | kGapQuant | kGapHeavyStart)) && g < S;
+    *has_end = false;
+    if ((f & kGapHeavyEnd) && g >= 1) {
+        uint32_t a[kMaxLearnedWords];
+        load_sample(smp, ld_s, K, g - 1, a);
+        if (!is_max_key(a, K, nbits)) {
+            *has_end = true;
+            if (*has_start) {  // a + 1 == sample g ?
+                uint32_t carry = 1;
+                bool eq = true;
+                for (uint32_t w = 0; w < K; ++w) {
+                    const uint64_t sum = (uint64_t)a[w] + carry;
+                    eq &= (uint32_t)sum == smp[(uint64_t)w * ld_s + g];
+                    carry = (uint32_t)(sum >> 32);
+                }
+                if (eq) *has_end = false;
+            }
+        }
+    }
+}
+
+// Gap compaction, one gap per thread, kScanBlock gaps per block.
+// mode 0: count flagged gaps; mode 1: count splitter values.
+template <int MODE>
+__device__ __forceinline__ uint32_t gap_weight(const uint32_t* flag, uint64_t g, uint64_t S, const uint32_t* smp,
+                                               uint64_t ld_s, uint32_t K, uint32_t nbits) {
+    if (g > S) return 0;
+    const uint32_t f = flag[g];
+    if (!f) return 0;
+    if (MODE == 0) return 1;
+    bool e, s;
+    gap_values(smp, ld_s, K, nbits, S, g, f, &e, &s);
+    return (e ? 1u : 0u) + (s ? 1u : 0u);
+}
+
+// Block-wide exclusive prefix of one small value per thread (1024 threads).
+__device__ __forceinline__ uint32_t block_excl_1024(uint32_t x, uint32_t* wsum /*[33]*/, uint32_t* total) {
+    const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t inc = x;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t t = __shfl_up_sync(kFull, inc, o);
+        if (lane >= (uint32_t)o) inc += t;
+    }
+    if (lane == 31) wsum[warp] = inc;
+    __syncthreads();
+    if (warp == 0) {
+        const uint32_t v = wsum[lane];
+        uint32_t vi = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t t = __shfl_up_sync(kFull, vi, o);
+            if (lane >= (uint32_t)o) vi += t;
+        }
+        wsum[lane] = vi - v;
+        if (lane == 31) wsum[32] = vi;
+    }
+    __syncthreads();
+    const uint32_t r = wsum[warp] + inc - x;
+    *total = wsum[32];
+    __syncthreads();
+    return r;
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(kScanBlock) gap_count_kernel(const uint32_t* __restrict__ flag, uint64_t S,
+                                                               const uint32_t* __restrict__ smp, uint64_t ld_s,
+                                                               uint32_t K, uint32_t nbits, uint32_t* __restrict__ bcnt) {
+    __shared__ uint32_t wsum[33];
+    const uint64_t g = (uint64_t)blockIdx.x * kScanBlock + threadIdx.x;
+    uint32_t total;
+    block_excl_1024(gap_weight<MODE>(flag, g, S, smp, ld_s, K, nbits), wsum, &total);
+    if (threadIdx.x == 0) bcnt[blockIdx.x] = total;
+}
+
+// Single-block exclusive scan of cnt[0, *len or len) in place; the total goes
+// to *total; with limit > 0, a total >= limit sets *gate.
+__global__ void __launch_bounds__(1024) scan_counts_kernel(uint32_t* cnt, uint32_t len, const uint32_t* len_dev,
+                                                           uint32_t* total, uint32_t limit, uint32_t* gate) {
+    __shared__ uint32_t wsum[33];
+    const uint32_t L = len_dev ? *len_dev + 1 : len;
+    const uint32_t per = (L + 1023) / 1024, lo = threadIdx.x * per, hi = min(L, lo + per);
+    uint32_t s = 0;
+    for (uint32_t j = lo; j < hi; ++j) s += cnt[j];
+    uint32_t tot;
+    uint32_t run = block_excl_1024(s, wsum, &tot);
+    for (uint32_t j = lo; j < hi; ++j) {
+        const uint32_t x = cnt[j];
+        cnt[j] = run;
+        run += x;
+    }
+    if (threadIdx.x == 0) {
+        *total = tot;
+        if (limit && tot >= limit) *gate = 1;
+    }
+}
+
+// Flagged gaps in order.
+__global__ void __launch_bounds__(kScanBlock) gap_write_kernel(const uint32_t* __restrict__ flag, uint64_t S,
+                                                               const uint32_t* __restrict__ boff,
+                                                               uint32_t* __restrict__ gaps) {
+    __shared__ uint32_t wsum[33];
+    const uint64_t g = (uint64_t)blockIdx.x * kScanBlock + threadIdx.x;
+    const uint32_t x = gap_weight<0>(flag, g, S, nullptr, 0, 0, 0);
+    uint32_t total;
+    const uint32_t r = block_excl_1024(x, wsum, &total) + boff[blockIdx.x];
+    if (x) gaps[r] = (uint32_t)g;
+}
+
+// 5. model buckets with more sample keys than a bucket may hold (u) are cut
+//    into pieces of about t sample keys: the number of cuts of every segment.
+__device__ __forceinline__ void segment_of(const uint32_t* gaps, uint32_t g1, uint64_t S, uint32_t j, uint64_t* a,
+                                           uint64_t* e) {
+    *a = j ? gaps[j - 1] : 0;
+    *e = j < g1 ? gaps[j] : S;
+}
+
+__device__ __forceinline__ uint32_t segment_cuts(const uint32_t* smp, uint64_t ld_s, uint32_t K, uint64_t a, uint64_t e,
+                                                 float t_s, uint32_t u_s) {
+    if (e <= a || e - a <= u_s) return 0;
+    uint32_t v[kMaxLearnedWords];
+    load_sample(smp, ld_s, K, a, v);
+    if (cmp_sample(smp, ld_s, K, e - 1, v) == 0) return 0;  // one key value (a heavy run)
+    const uint64_t pieces = (uint64_t)ceilf((float)(e - a) / t_s);
+    return (uint32_t)(pieces > 1 ? pieces - 1 : 0);
+}
+
+__global__ void subdiv_count_kernel(const uint32_t* __restrict__ gaps, const LearnedMisc* misc, uint64_t S,
+                                    const uint32_t* __restrict__ smp, uint64_t ld_s, uint32_t K, float t_s,
+                                    uint32_t u_s, uint32_t* __restrict__ segcnt) {
+    const uint32_t g1 = misc->g1;
+    for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j <= g1; j += gridDim.x * blockDim.x) {
+        uint64_t a, e;
+        segment_of(gaps, g1, S, j, &a, &e);
+        segcnt[j] = segment_cuts(smp, ld_s, K, a, e, t_s, u_s);
+    }
+}
+
+__global__ void subdiv_flag_kernel(const uint32_t* __restrict__ gaps, const LearnedMisc* misc, uint64_t S,
+                                   const uint32_t* __restrict__ smp, uint64_t ld_s, uint32_t K, float t_s,
+                                   uint32_t u_s, const uint32_t* __restrict__ segoff, uint32_t* __restrict__ flag) {
+    const uint32_t g1 = misc->g1, nsub = misc->nsub;
+    for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < nsub; q += gridDim.x * blockDim.x) {
+        uint32_t lo = 0, hi = g1;  // last segment with segoff <= q
+        while (lo < hi) {
+            const uint32_t mid = (lo + hi + 1) >> 1;
+            if (segoff[mid] <= q) lo = mid;
+            else hi = mid - 1;
+        }
+        uint64_t a, e;
+        segment_of(gaps, g1, S, lo, &a, &e);
+        const uint64_t pieces = segment_cuts(smp, ld_s, K, a, e, t_s, u_s) + 1ull;
+        const uint64_t k = q - segoff[lo] + 1;
+        const uint64_t pos = a + k * (e - a) / pieces;
+        const uint64_t p = run_start(smp, ld_s, K, a, pos);
+        if (p > a && p < S) atomicOr(&flag[p], kGapQuant);
+    }
+}
+
+// 6. splitter values in order; gidx[g] = index of gap g's start value.
+__global__ void __launch_bounds__(kScanBlock) value_write_kernel(const uint32_t* __restrict__ flag, uint64_t S,
+                                                                 const uint32_t* __restrict__ smp, uint64_t ld_s,
+                                                                 uint32_t K, uint32_t nbits,
+                                                                 const uint32_t* __restrict__ boff,
+                                                                 uint32_t max_splitters, uint32_t* __restrict__ spl,
+                                                                 uint32_t* __restrict__ gidx, LearnedMisc* misc) {
+    __shared__ uint32_t wsum[33];
+    const uint64_t g = (uint64_t)blockIdx.x * kScanBlock + threadIdx.x;
+    const uint32_t f = g <= S ? flag[g] : 0u;
+    bool e = false, s = false;
+    if (f) gap_values(smp, ld_s, K, nbits, S, g, f, &e, &s);
+    const uint32_t x = (e ? 1u : 0u) + (s ? 1u : 0u);
+    uint32_t total;
+    uint32_t r = block_excl_1024(x, wsum, &total) + boff[blockIdx.x];
+    if (e && r < max_splitters) {
+        uint32_t carry = 1;
+        for (uint32_t w = 0; w < K; ++w) {
+            const uint64_t sum = (uint64_t)smp[(uint64_t)w * ld_s + g - 1] + carry;
+            spl[(uint64_t)r * K + w] = (uint32_t)sum;
+            carry = (uint32_t)(sum >> 32);
+        }
+        ++r;
+    }
+    if (s && r < max_splitters) {
+        for (uint32_t w = 0; w < K; ++w) spl[(uint64_t)r * K + w] = smp[(uint64_t)w * ld_s + g];
+        gidx[g] = r;
+        if (f & kGapModel) atomicAdd(&misc->counts[4], 1u);
+    }
+}
+
+// 7. the model's guess: model bucket b starts at final bucket map[b].
+__global__ void guess_map_kernel(const uint32_t* __restrict__ mgap, const uint32_t* __restrict__ gidx, uint64_t S,
+                                 uint32_t B, const LearnedMisc* misc, uint32_t* __restrict__ map) {
+    const uint32_t ns = misc->nsplit;
+    for (uint32_t b = blockIdx.x * blockDim.x + threadIdx.x; b <= B; b += gridDim.x * blockDim.x) {
+        const uint32_t p = mgap[b];
+        map[b] = p == 0 ? 0u : (p >= S ? ns : min(gidx[p] + 1, ns));
     }
 }
 
@@ -405,18 +618,15 @@ __global__ void __launch_bounds__(1024) emit_splitters_kernel(const uint32_t* __
 struct BucketArgs {
     const uint32_t* ck;
     uint64_t ld, n;
-    uint32_t K, nbits, max_buckets, use_model;
-    const uint32_t* nsplit;  // number of splitters (buckets - 1), on the device
-    const uint32_t* spl;     // [nsplit * K], entry-major, non-decreasing
+    uint32_t K, nbits, max_buckets, B, use_model, passes;
     const float* params;
-    const float* loss;    // training loss (mean squared CDF error) of params
+    const uint32_t* spl;  // strictly increasing, entry-major
+    const uint32_t* map;  // [B + 1]
+    LearnedMisc* misc;
     uint32_t* bkt;        // [n]
-    uint32_t* hist;       // [2][256] digit histograms of the bucket id (low byte, high bits)
-    unsigned long long* steps;  // [0]: total search steps, [1]: max
+    uint32_t* hist;       // [2][256] digit counts of the bucket id (low byte, high byte)
 };
 
-// Compile-time-width helpers for the bucket kernel (key in registers; word
-// indices are resolved by unrolled selects so the key never leaves registers).
 template <int KW>
 __device__ __forceinline__ int cmp_key(const uint32_t (&key)[KW], const uint32_t* s) {
 #pragma unroll
@@ -446,13 +656,12 @@ __device__ __forceinline__ uint32_t top32_mem(const uint32_t* key, uint32_t K, u
     return sh ? __funnelshift_r(key[w], key[w + 1 < K ? w + 1 : w], sh) : key[w];
 }
 
-// Comparison of key x (top32 value t) with splitter m: the shared table of
-// splitter top32 values decides unless they are equal, then the full
-// splitter is read.
-template <int KW, bool STAGED>
-__device__ __forceinline__ int cmp_at(const uint32_t (&key)[KW], uint32_t t, const uint32_t* top,
+// Comparison of key x (top32 value t) with splitter m: with `staged`, the
+// shared table of splitter top32 values decides unless they are equal.
+template <int KW>
+__device__ __forceinline__ int cmp_at(const uint32_t (&key)[KW], uint32_t t, const uint32_t* top, bool staged,
                                       const uint32_t* spl, uint32_t m) {
-    if (STAGED) {
+    if (staged) {
         const uint32_t u = top[m];
         if (t != u) return t < u ? -1 : 1;
     }
@@ -460,13 +669,14 @@ __device__ __forceinline__ int cmp_at(const uint32_t (&key)[KW], uint32_t t, con
 }
 
 // Number of splitters <= x within [lo, hi] (binary search).
-template <int KW, bool STAGED>
+template <int KW>
 __device__ __forceinline__ uint32_t search_range(const uint32_t (&key)[KW], uint32_t t, const uint32_t* top,
-                                                 const uint32_t* spl, uint32_t lo, uint32_t hi, uint32_t* cmp) {
+                                                 bool staged, const uint32_t* spl, uint32_t lo, uint32_t hi,
+                                                 uint32_t* cmp) {
     while (lo < hi) {
         const uint32_t mid = (lo + hi) >> 1;
         ++*cmp;
-        if (cmp_at<KW, STAGED>(key, t, top, spl, mid) >= 0) lo = mid + 1;
+        if (cmp_at<KW>(key, t, top, staged, spl, mid) >= 0) lo = mid + 1;
         else hi = mid;
     }
     return lo;
@@ -476,31 +686,31 @@ __device__ __forceinline__ uint32_t search_range(const uint32_t (&key)[KW], uint
 // there): check the guess's range, then gallop away from it (1, 2, 4, ...
 // buckets) and finish with a binary search, so a guess that is e buckets off
 // costs about 2 log2(e) + 2 comparisons.
-template <int KW, bool STAGED>
+template <int KW>
 __device__ __forceinline__ uint32_t search_from_guess(const uint32_t (&key)[KW], uint32_t t, const uint32_t* top,
-                                                      const uint32_t* spl, uint32_t lo, uint32_t hi, uint32_t g,
-                                                      uint32_t* cmp) {
+                                                      bool staged, const uint32_t* spl, uint32_t lo, uint32_t hi,
+                                                      uint32_t g, uint32_t* cmp) {
     ++*cmp;
-    if (g > lo && cmp_at<KW, STAGED>(key, t, top, spl, g - 1) < 0) {  // below: gallop down
+    if (g > lo && cmp_at<KW>(key, t, top, staged, spl, g - 1) < 0) {  // below: gallop down
         uint32_t h = g - 1, step = 1;
         while (true) {
             const uint32_t probe = h >= lo + step ? h - step : lo;
             ++*cmp;
-            if (cmp_at<KW, STAGED>(key, t, top, spl, probe) >= 0)
-                return search_range<KW, STAGED>(key, t, top, spl, probe + 1, h, cmp);
+            if (cmp_at<KW>(key, t, top, staged, spl, probe) >= 0)
+                return search_range<KW>(key, t, top, staged, spl, probe + 1, h, cmp);
             if (probe == lo) return lo;
             h = probe;
             step <<= 1;
         }
     }
     ++*cmp;
-    if (g < hi && cmp_at<KW, STAGED>(key, t, top, spl, g) >= 0) {  // above: gallop up
+    if (g < hi && cmp_at<KW>(key, t, top, staged, spl, g) >= 0) {  // above: gallop up
         uint32_t l = g + 1, step = 1;
         while (true) {
             const uint32_t probe = l + step - 1 < hi ? l + step - 1 : hi - 1;
             ++*cmp;
-            if (cmp_at<KW, STAGED>(key, t, top, spl, probe) < 0)
-                return search_range<KW, STAGED>(key, t, top, spl, l, probe, cmp);
+            if (cmp_at<KW>(key, t, top, staged, spl, probe) < 0)
+                return search_range<KW>(key, t, top, staged, spl, l, probe, cmp);
             l = probe + 1;
             if (probe == hi - 1) return hi;
             step <<= 1;
@@ -509,42 +719,39 @@ __device__ __forceinline__ uint32_t search_from_guess(const uint32_t (&key)[KW],
     return g;
 }
 
-// Bucket id of every key (B = splitters + 1 buckets).  With STAGED, the top32
-// value of every splitter sits in shared memory, with a table over its top
-// kPrefixBits bits: pre[p] = first splitter whose top32 is >= p << (32 -
-// kPrefixBits).  A key whose top32 has prefix p has its bucket in [pre[p],
-// pre[p + 1]].  The model's guess, clamped into the range, starts a galloping
-// search where that is expected to be cheaper than a binary search of the
-// range: its error is about e = sqrt(loss) B buckets, so galloping costs about
-// 2 log2(e + 1) + 2 comparisons against log2(range + 1).  Without STAGED the
-// range is all buckets.
-constexpr int kPrefixBits = 12;
-
-template <int KW, bool STAGED>
+// Bucket id of every key, the digit counts of the two partition passes, and
+// the hash sum of the input pairs (key, row id = position).  When the
+// splitters fit, the top 32 bits of each sit in shared memory with a table
+// over their top kPrefixBits bits: pre[p] = first splitter whose top32 is >=
+// p << (32 - kPrefixBits), so a key whose top32 has prefix p has its bucket in
+// [pre[p], pre[p + 1]].  The model's guess (its bucket b maps to final bucket
+// map[b]), clamped into that range, starts a galloping search where that is
+// expected to be cheaper than a binary search of the range: the model's
+// error is about e = sqrt(loss) B buckets, so galloping costs about
+// 2 log2(e + 1) + 2 comparisons against log2(range + 1).
+template <int KW>
 __global__ void __launch_bounds__(1024) bucket_kernel(const BucketArgs a) {
     extern __shared__ uint32_t top[];
-    uint32_t* pre = top + (a.max_buckets - 1);  // [2^kPrefixBits + 1] when staged
+    uint32_t* pre = top + kStagedSplitters;
     __shared__ float p[kParams];
     __shared__ uint32_t hlo[256], hhi[256];
-    __shared__ unsigned long long s_sum, s_max;
+    LearnedMisc* misc = a.misc;
+    if (*(volatile uint32_t*)&misc->gate) return;
     const int tid = threadIdx.x;
-    const uint32_t B = min(*a.nsplit + 1, a.max_buckets), nbits = a.nbits;
-    const float err = a.use_model ? sqrtf(fmaxf(*a.loss, 0.0f)) * (float)B + 1.0f : 0.0f;
+    const uint32_t ns = min(misc->nsplit, a.max_buckets - 1), nbits = a.nbits, B = a.B;
+    const bool staged = ns <= kStagedSplitters;
+    const float err = a.use_model ? sqrtf(fmaxf(misc->loss, 0.0f)) * (float)(ns + 1) + 1.0f : 0.0f;
     const float model_min_range = 4.0f * err * err;  // use the model on ranges wider than this
     if (tid < kParams) p[tid] = a.params ? a.params[tid] : 0.0f;
     if (tid < 256) {
         hlo[tid] = 0;
         hhi[tid] = 0;
     }
-    if (tid == 0) {
-        s_sum = 0;
-        s_max = 0;
-    }
-    if (STAGED) {
-        for (uint32_t m = tid; m + 1 < B; m += blockDim.x) top[m] = top32_mem(a.spl + (uint64_t)m * KW, KW, nbits);
+    if (staged) {
+        for (uint32_t m = tid; m < ns; m += blockDim.x) top[m] = top32_mem(a.spl + (uint64_t)m * KW, KW, nbits);
         __syncthreads();
         for (uint32_t q = tid; q <= (1u << kPrefixBits); q += blockDim.x) {
-            uint32_t lo = 0, hi = B - 1;  // first m with top[m] >= q << (32 - kPrefixBits)
+            uint32_t lo = 0, hi = ns;  // first m with top[m] >= q << (32 - kPrefixBits)
             const uint64_t bound = (uint64_t)q << (32 - kPrefixBits);
             while (lo < hi) {
                 const uint32_t mid = (lo + hi) >> 1;
@@ -556,6 +763,7 @@ __global__ void __launch_bounds__(1024) bucket_kernel(const BucketArgs a) {
     }
     __syncthreads();
     unsigned long long my_sum = 0, my_max = 0;
+    uint64_t my_hash = 0;
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     uint32_t next[KW];  // the following key's words, loaded while this key is searched
     uint64_t i = (uint64_t)blockIdx.x * blockDim.x + tid;
@@ -569,8 +777,8 @@ __global__ void __launch_bounds__(1024) bucket_kernel(const BucketArgs a) {
             next[w] = i + stride < a.n ? a.ck[(uint64_t)w * a.ld + i + stride] : 0u;
         }
         const uint32_t t = top32_regs<KW>(key, nbits);
-        uint32_t g, steps = 0, lo = 0, hi = B - 1;
-        if (STAGED) {
+        uint32_t g, steps = 0, lo = 0, hi = ns;
+        if (staged) {
             const uint32_t q = t >> (32 - kPrefixBits);
             lo = pre[q];
             hi = pre[q + 1];
@@ -578,66 +786,71 @@ __global__ void __launch_bounds__(1024) bucket_kernel(const BucketArgs a) {
         if (a.use_model && (float)(hi - lo) + 1.0f > model_min_range) {
             const float x = (float)(t >> 8) * (1.0f / 16777216.0f);  // the top 24 bits, as in training
             const float y = mlp_eval(p, x) * (float)B;
-            uint32_t guess = y <= 0.0f ? 0u : (y >= (float)(B - 1) ? B - 1 : (uint32_t)y);
+            const uint32_t mb = y <= 0.0f ? 0u : (y >= (float)(B - 1) ? B - 1 : (uint32_t)y);
+            uint32_t guess = a.map[mb];
             guess = guess < lo ? lo : (guess > hi ? hi : guess);
-            g = search_from_guess<KW, STAGED>(key, t, top, a.spl, lo, hi, guess, &steps);
+            g = search_from_guess<KW>(key, t, top, staged, a.spl, lo, hi, guess, &steps);
         } else {
-            g = search_range<KW, STAGED>(key, t, top, a.spl, lo, hi, &steps);
+            g = search_range<KW>(key, t, top, staged, a.spl, lo, hi, &steps);
         }
         a.bkt[i] = g;
         atomicAdd(&hlo[g & 255u], 1u);
-        atomicAdd(&hhi[g >> 8], 1u);
+        if (a.passes > 1) atomicAdd(&hhi[g >> 8], 1u);
         my_sum += steps;
         my_max = my_max > steps ? my_max : steps;
+        uint64_t h = pair_hash_start((uint32_t)i);
+#pragma unroll
+        for (int w = 0; w < KW; ++w) h = pair_hash_word(h, key[w]);
+        my_hash += pair_hash_end(h);
     }
-    atomicAdd(&s_sum, my_sum);
-    atomicMax(&s_max, my_max);
+    for (int o = 16; o > 0; o >>= 1) {
+        my_sum += __shfl_xor_sync(kFull, my_sum, o);
+        my_max = max(my_max, __shfl_xor_sync(kFull, my_max, o));
+        my_hash += __shfl_xor_sync(kFull, my_hash, o);
+    }
+    if ((tid & 31) == 0) {
+        atomicAdd(&misc->steps[0], my_sum);
+        atomicMax(&misc->steps[1], my_max);
+        atomicAdd(&misc->hash_in, (unsigned long long)my_hash);
+    }
     __syncthreads();
     if (tid < 256) {
         if (hlo[tid]) atomicAdd(&a.hist[tid], hlo[tid]);
         if (hhi[tid]) atomicAdd(&a.hist[256 + tid], hhi[tid]);
     }
-    if (tid == 0) {
-        atomicAdd(&a.steps[0], s_sum);
-        atomicMax(&a.steps[1], s_max);
-    }
 }
 
 template <int KW>
-static cudaError_t launch_bucket_kw(const BucketArgs& ba, bool staged, size_t smem, int sms, cudaStream_t s) {
-    if (staged) {
-        cudaError_t e = cudaFuncSetAttribute(bucket_kernel<KW, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)smem);
-        if (e != cudaSuccess) return e;
-        bucket_kernel<KW, true><<<sms, 1024, smem, s>>>(ba);
-    } else {
-        bucket_kernel<KW, false><<<sms, 1024, 0, s>>>(ba);
-    }
+static cudaError_t launch_bucket_kw(const BucketArgs& ba, size_t smem, int sms, cudaStream_t s) {
+    cudaError_t e = cudaFuncSetAttribute(bucket_kernel<KW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    bucket_kernel<KW><<<sms, 1024, smem, s>>>(ba);
     return cudaGetLastError();
 }
 
-static cudaError_t launch_bucket(const BucketArgs& ba, bool staged, size_t smem, int sms, cudaStream_t s) {
+static cudaError_t launch_bucket(const BucketArgs& ba, int sms, cudaStream_t s) {
+    const size_t smem = 4ull * kStagedSplitters + 4ull * ((1u << kPrefixBits) + 1);
     switch (ba.K) {
-        case 1: return launch_bucket_kw<1>(ba, staged, smem, sms, s);
-        case 2: return launch_bucket_kw<2>(ba, staged, smem, sms, s);
-        case 3: return launch_bucket_kw<3>(ba, staged, smem, sms, s);
-        case 4: return launch_bucket_kw<4>(ba, staged, smem, sms, s);
-        case 5: return launch_bucket_kw<5>(ba, staged, smem, sms, s);
-        case 6: return launch_bucket_kw<6>(ba, staged, smem, sms, s);
-        case 7: return launch_bucket_kw<7>(ba, staged, smem, sms, s);
-        default: return launch_bucket_kw<8>(ba, staged, smem, sms, s);
+        case 1: return launch_bucket_kw<1>(ba, smem, sms, s);
+        case 2: return launch_bucket_kw<2>(ba, smem, sms, s);
+        case 3: return launch_bucket_kw<3>(ba, smem, sms, s);
+        case 4: return launch_bucket_kw<4>(ba, smem, sms, s);
+        case 5: return launch_bucket_kw<5>(ba, smem, sms, s);
+        case 6: return launch_bucket_kw<6>(ba, smem, sms, s);
+        case 7: return launch_bucket_kw<7>(ba, smem, sms, s);
+        default: return launch_bucket_kw<8>(ba, smem, sms, s);
     }
 }
 
-// ------------------------------------------------------------ bucket sorts
 // start[b] = first position of bucket b in the partitioned keys: the first
 // position whose key is >= spl[b - 1].  The partition is by key range, so
 // that predicate is monotone in the position and a binary search finds it.
 // start[0] = 0; buckets past the last splitter are empty (start = n).
 __global__ void bucket_bounds_kernel(const uint32_t* __restrict__ ck, uint64_t ld, uint64_t n, uint32_t K,
-                                     const uint32_t* __restrict__ spl, const uint32_t* nsplit, uint32_t max_buckets,
+                                     const uint32_t* __restrict__ spl, const LearnedMisc* misc, uint32_t max_buckets,
                                      uint32_t* __restrict__ start) {
-    const uint32_t ns = min(*nsplit, max_buckets - 1);
+    if (*(volatile const uint32_t*)&misc->gate) return;
+    const uint32_t ns = min(misc->nsplit, max_buckets - 1);
     for (uint32_t b = blockIdx.x * blockDim.x + threadIdx.x; b <= max_buckets; b += gridDim.x * blockDim.x) {
         uint64_t pos = b == 0 ? 0 : n;
         if (b >= 1 && b <= ns) {
@@ -659,467 +872,35 @@ __global__ void bucket_bounds_kernel(const uint32_t* __restrict__ ck, uint64_t l
     }
 }
 
-// Bucket b holds only equal keys when its range is [v, v + 1).
-__device__ bool constant_bucket(const uint32_t* spl, uint32_t K, uint32_t B, uint32_t b) {
-    if (b == 0 || b + 1 >= B) return false;
-    const uint32_t* lo = spl + (uint64_t)(b - 1) * K;
-    const uint32_t* hi = spl + (uint64_t)b * K;
-    uint32_t carry = 1;
-    for (uint32_t w = 0; w < K; ++w) {  // hi == lo + 1 ?
-        const uint64_t sum = (uint64_t)lo[w] + carry;
-        if ((uint32_t)sum != hi[w]) return false;
-        carry = (uint32_t)(sum >> 32);
-    }
-    return carry == 0;
-}
-
-struct LocalArgs {
-    uint32_t* ck;          // partitioned, sorted in place; word-major, leading dimension ld
-    uint32_t* rid;
-    const uint32_t* start; // [B + 1]
-    const uint32_t* spl;   // splitters
-    const uint32_t* nsplit;  // their number, on the device (buckets = nsplit + 1)
-    uint64_t ld;
-    uint32_t K, B, cap;    // B: size of the bucket id space (buckets past nsplit are empty)
-    uint32_t* next;        // bucket queue
-    uint32_t* flags;       // [0] oversize buckets (also the length of `over`)
-    uint32_t* counts;      // [0] buckets sorted, [1] constant buckets, [2] max bucket
-    uint32_t* over;        // [2 * max_over] start/end of oversize buckets
-    uint32_t max_over;
-};
-
-constexpr int kLocalThreads = 1024;
-constexpr int kLocalWarps = kLocalThreads / 32;
-constexpr uint32_t kShortRun = 16;  // runs of equal windows up to this length: insertion sort by one thread
-constexpr uint32_t kBlockRun = 256; // runs from this length on are sorted by the whole block
-constexpr int kRunList = 1024;      // shorter runs of one warp round (disjoint, so at most cap / 17)
-constexpr int kBlockStack = 64;     // runs waiting for the block (disjoint, so at most cap / kBlockRun)
-
-// Key i < key j (bucket-local indices into the word-major shared key array).
-__device__ __forceinline__ bool key_less(const uint32_t* keys, uint32_t cap, uint32_t K, uint32_t i, uint32_t j) {
-    for (int w = (int)K - 1; w >= 0; --w) {
-        const uint32_t x = keys[(size_t)w * cap + i], y = keys[(size_t)w * cap + j];
-        if (x != y) return x < y;
-    }
-    return false;
-}
-
-// Stable insertion sort of positions [p, p + len) of idx by key (one thread).
-__device__ __forceinline__ void insertion_sort_run(uint16_t* idx, uint32_t p, uint32_t len, const uint32_t* keys,
-                                                   uint32_t cap, uint32_t K) {
-    for (uint32_t j = p + 1; j < p + len; ++j) {
-        const uint16_t v = idx[j];
-        uint32_t k = j;
-        while (k > p && key_less(keys, cap, K, v, idx[k - 1])) {
-            idx[k] = idx[k - 1];
-            --k;
-        }
-        idx[k] = v;
-    }
-}
-
-// Does any bit of [lo, lo + len) vary (mask over K words, bit 0 = word 0 bit 0)?
-__device__ __forceinline__ bool bits_vary(const uint32_t* vary, uint32_t lo, uint32_t len, uint32_t K) {
-    for (uint32_t w = lo >> 5; w < K && 32 * w < lo + len; ++w) {
-        const uint32_t a = lo > 32 * w ? lo - 32 * w : 0u;
-        const uint32_t e = lo + len - 32 * w;  // > a
-        const uint32_t hi_mask = e >= 32 ? 0xFFFFFFFFu : ((1u << e) - 1u);
-        if (vary[w] & hi_mask & (0xFFFFFFFFu << a)) return true;
-    }
-    return false;
-}
-
-// The sort window of a run: the 32 bits [base, base + 32) of the key that end
-// at the run's top varying bit (all keys of the run agree above it).
-struct Window {
-    const uint32_t* lo;
-    const uint32_t* hi;
-    uint32_t sh, base;
-    __device__ Window(const uint32_t* keys, uint32_t cap, uint32_t K, uint32_t top) {
-        base = top >= 31 ? top - 31 : 0u;
-        const uint32_t wl = base >> 5;
-        sh = base & 31;
-        lo = keys + (size_t)wl * cap;
-        hi = keys + (size_t)(sh && wl + 1 < K ? wl + 1 : wl) * cap;
-    }
-    __device__ __forceinline__ uint32_t operator()(uint32_t i) const {
-        return sh ? __funnelshift_r(lo[i], hi[i], sh) : lo[i];
-    }
-};
-
-__device__ __forceinline__ int top_bit(const uint32_t* vary, uint32_t K) {
-    for (int w = (int)K - 1; w >= 0; --w)
-        if (vary[w]) return 32 * w + 31 - __clz(vary[w]);
-    return -1;
-}
-
-// After a run is sorted by its window: items with equal windows (a sub-run)
-// still differ below it.  The first position of every sub-run finds the
-// sub-run's end by binary search (windows ascend) and sorts a short one at
-// once; a longer one goes to the warp list, one of kBlockRun or more items
-// to the block's stack (bstack == nullptr: the warp list).  Positions
-// p0 + first, + step, ...
-__device__ __forceinline__ void settle_sub_runs(uint16_t* idx, uint32_t p0, uint32_t pe, uint32_t first,
-                                                uint32_t step, const Window& win, const uint32_t* keys, uint32_t cap,
-                                                uint32_t K, uint32_t* list, uint32_t* count, uint32_t* bstack,
-                                                uint32_t* bcount, uint32_t* overflow) {
-    for (uint32_t p = p0 + first; p < pe; p += step) {
-        const uint32_t wv = win(idx[p]);
-        // (a sub-run's items all carry its window, so insertion sorts running
-        // meanwhile in other threads do not change what is read here)
-        if (p > p0 && win(idx[p - 1]) == wv) continue;      // not the first of its sub-run
-        if (p + 1 >= pe || win(idx[p + 1]) != wv) continue;  // a single item
-        uint32_t lo = p + 2, hi = pe;
-        while (lo < hi) {
-            const uint32_t mid = (lo + hi) >> 1;
-            if (win(idx[mid]) == wv) lo = mid + 1;
-            else hi = mid;
-        }
-        const uint32_t len = lo - p;
-        if (len <= kShortRun) {
-            insertion_sort_run(idx, p, len, keys, cap, K);
-            continue;
-        }
-        const bool big = bstack && len >= kBlockRun;
-        const uint32_t slot = atomicAdd(big ? bcount : count, 1u);
-        if (slot < (big ? (uint32_t)kBlockStack : (uint32_t)kRunList)) (big ? bstack : list)[slot] = (len << 16) | p;
-        else atomicAdd(overflow, 1u);  // cannot happen (disjoint runs); verification then fails
-    }
-}
-
-// One warp sorts run [p0, p0 + r) by its window: LSD passes over the varying
-// window digits, ranks by ballots against the warp's own 256 counters (which
-// accumulate over the run's chunks, so a rank is the item's place among all
-// earlier items of its digit), then its sub-runs are settled.
-__device__ __forceinline__ void warp_sort_run(uint32_t p0, uint32_t r, const uint32_t* keys, uint32_t cap,
-                                              uint32_t K, uint16_t* idx, uint16_t* alt, uint16_t* rnk, uint8_t* dig,
-                                              uint16_t* wh, uint32_t* vary, uint32_t* list, uint32_t* count,
-                                              uint32_t* overflow) {
-    const uint32_t lane = threadIdx.x & 31, lt = (1u << lane) - 1u, pe = p0 + r;
-    const uint32_t first = idx[p0];
-    for (uint32_t w = 0; w < K; ++w) {
-        const uint32_t* kw = keys + (size_t)w * cap;
-        const uint32_t f = kw[first];
-        uint32_t diff = 0;
-        for (uint32_t p = p0 + lane; p < pe; p += 32) diff |= kw[idx[p]] ^ f;
-        diff = __reduce_or_sync(kFull, diff);
-        if (lane == 0) vary[w] = diff;
-    }
-    __syncwarp();
-    const int top = top_bit(vary, K);
-    if (top < 0) return;  // equal keys: already in order
-    const Window win(keys, cap, K, (uint32_t)top);
-    uint16_t* cur = idx;
-    uint16_t* nxt = alt;
-    for (uint32_t q = 0; q < 4; ++q) {
-        if (!bits_vary(vary, win.base + 8 * q, 8, K)) continue;
-        for (uint32_t i = lane; i < 256; i += 32) wh[i] = 0;
-        __syncwarp();
-        for (uint32_t c0 = p0; c0 < pe; c0 += 32) {
-            const uint32_t p = c0 + lane;
-            const bool valid = p < pe;
-            const uint32_t d = valid ? (win(cur[p]) >> (8 * q)) & 0xFFu : 0u;
-            uint32_t peers = __ballot_sync(kFull, valid);
-#pragma unroll
-            for (int bit = 0; bit < 8; ++bit) {
-                const bool x = (d >> bit) & 1u;
-                const uint32_t bal = __ballot_sync(kFull, x);
-                peers &= x ? bal : ~bal;
-            }
-            const uint32_t cnt = valid ? wh[d] : 0u;
-            __syncwarp();
-            if (valid && (peers & lt) == 0) wh[d] = (uint16_t)(cnt + __popc(peers));
-            __syncwarp();
-            if (valid) {
-                rnk[p] = (uint16_t)(cnt + __popc(peers & lt));
-                dig[p] = (uint8_t)d;
-            }
-        }
-        __syncwarp();
-        uint32_t v[8], sum = 0;
-#pragma unroll
-        for (int i = 0; i < 8; ++i) {
-            v[i] = wh[lane * 8 + i];
-            sum += v[i];
-        }
-        uint32_t inc = sum;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t t = __shfl_up_sync(kFull, inc, o);
-            if (lane >= (uint32_t)o) inc += t;
-        }
-        uint32_t ex = inc - sum;
-#pragma unroll
-        for (int i = 0; i < 8; ++i) {
-            wh[lane * 8 + i] = (uint16_t)ex;
-            ex += v[i];
-        }
-        __syncwarp();
-        for (uint32_t p = p0 + lane; p < pe; p += 32) nxt[p0 + wh[dig[p]] + rnk[p]] = cur[p];
-        __syncwarp();
-        uint16_t* t = cur;
-        cur = nxt;
-        nxt = t;
-    }
-    if (cur != idx) {
-        for (uint32_t p = p0 + lane; p < pe; p += 32) idx[p] = cur[p];
-        __syncwarp();
-    }
-    if (win.base > 0 && bits_vary(vary, 0, win.base, K))
-        settle_sub_runs(idx, p0, pe, lane, 32, win, keys, cap, K, list, count, nullptr, nullptr, overflow);
-    __syncwarp();
-}
-
-// Shared state of a block sorting one bucket.
-struct LocalShared {
-    uint16_t whist[kLocalWarps][256];
-    uint32_t dtot[256];
-    uint32_t vary[kMaxLearnedWords];
-    uint32_t wvary[kLocalWarps][kMaxLearnedWords];
-    uint32_t lists[2][kRunList];
-    uint32_t bstack[kBlockStack];
-    uint32_t bucket, count[2], bcount, grab, run;
-};
-
-// The whole block sorts run [p0, p0 + r) of idx by its window: LSD passes
-// over the varying window digits, each ranking the items of every warp's
-// share (consecutive chunks of 32) by ballots against the warp's counters,
-// then exclusive offsets digit-major, warp-minor over the warps that hold
-// items, then the scatter.  Then its sub-runs are settled.
-__device__ __forceinline__ void block_sort_run(uint32_t p0, uint32_t r, const uint32_t* keys, uint32_t cap,
-                                               uint32_t K, uint16_t* idx, uint16_t* alt, uint16_t* rnk, uint8_t* dig,
-                                               LocalShared& S, uint32_t* overflow) {
-    const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, lt = (1u << lane) - 1u, pe = p0 + r;
-    if (tid < K) S.vary[tid] = 0;
-    __syncthreads();
-    {
-        const uint32_t first = idx[p0];
-        for (uint32_t w = 0; w < K; ++w) {
-            const uint32_t* kw = keys + (size_t)w * cap;
-            const uint32_t f = kw[first];
-            uint32_t diff = 0;
-            for (uint32_t p = p0 + tid; p < pe; p += kLocalThreads) diff |= kw[idx[p]] ^ f;
-            diff = __reduce_or_sync(kFull, diff);
-            if (lane == 0 && diff) atomicOr(&S.vary[w], diff);
+// Last step: the checks' verdict (the gate of the plain fallback), the
+// status word, the statistics and the trained parameters.
+__global__ void finalize_kernel(LearnedMisc* misc, uint32_t force_fail, uint32_t use_model, uint32_t B, uint64_t S,
+                                uint64_t n, uint32_t cap, unsigned long long* status, ck_learned_stats* stats,
+                                const float* params, float* params_out) {
+    if (threadIdx.x == 0) {
+        if (!misc->gate && (misc->fail || misc->hash_in != misc->hash_out || force_fail)) misc->gate = 1;
+        if (misc->gate) report(status, CK_EVERIFY, misc->fail);
+        if (stats) {
+            const uint32_t ns = misc->nsplit;
+            stats->train_loss = use_model ? misc->loss : 0.0f;
+            stats->mean_search_steps = (float)((double)misc->steps[0] / (double)n);
+            stats->max_search_steps = (uint32_t)misc->steps[1];
+            stats->buckets = ns + 1;
+            stats->sample_size = (uint32_t)S;
+            stats->max_bucket = misc->counts[2];
+            stats->sorted_segments = misc->counts[0];
+            stats->constant_buckets = misc->counts[1];
+            stats->oversize_buckets = misc->counts[3];
+            stats->fell_back = misc->gate;
+            stats->model_buckets = B;
+            stats->model_boundaries = use_model ? misc->counts[4] : 0u;
+            stats->model_boundary_frac = use_model && ns ? (float)misc->counts[4] / (float)ns : 0.0f;
+            stats->heavy_keys = misc->counts[5];
+            stats->capacity = cap;
+            stats->reserved = 0;
         }
     }
-    __syncthreads();
-    const int top = top_bit(S.vary, K);
-    if (top < 0) return;  // equal keys: already in order (uniform: every thread returns)
-    const Window win(keys, cap, K, (uint32_t)top);
-    uint16_t* cur = idx;
-    uint16_t* nxt = alt;
-    const uint32_t per = ((r + kLocalWarps * 32 - 1) / (kLocalWarps * 32)) * 32;
-    const uint32_t nw = (r + per - 1) / per;  // warps that hold items
-    const uint32_t pbeg = p0 + warp * per, pend = min(pe, pbeg + per);
-    for (uint32_t q = 0; q < 4; ++q) {
-        if (!bits_vary(S.vary, win.base + 8 * q, 8, K)) continue;
-        for (uint32_t d = tid; d < nw * 256; d += kLocalThreads) (&S.whist[0][0])[d] = 0;
-        __syncthreads();
-        for (uint32_t c0 = pbeg; c0 < pend; c0 += 32) {  // warp-uniform trip count
-            const uint32_t p = c0 + lane;
-            const bool valid = p < pend;
-            const uint32_t d = valid ? (win(cur[p]) >> (8 * q)) & 0xFFu : 0u;
-            uint32_t peers = __ballot_sync(kFull, valid);
-#pragma unroll
-            for (int bit = 0; bit < 8; ++bit) {
-                const bool x = (d >> bit) & 1u;
-                const uint32_t bal = __ballot_sync(kFull, x);
-                peers &= x ? bal : ~bal;
-            }
-            const uint32_t cnt = valid ? S.whist[warp][d] : 0u;
-            __syncwarp();
-            if (valid && (peers & lt) == 0) S.whist[warp][d] = (uint16_t)(cnt + __popc(peers));
-            __syncwarp();
-            if (valid) {
-                rnk[p] = (uint16_t)(cnt + __popc(peers & lt));
-                dig[p] = (uint8_t)d;
-            }
-        }
-        __syncthreads();
-        // per digit: totals over warps, then exclusive offsets digit-major, warp-minor
-        if (tid < 256) {
-            uint32_t sum = 0;
-            for (uint32_t ww = 0; ww < nw; ++ww) sum += S.whist[ww][tid];
-            S.dtot[tid] = sum;
-        }
-        __syncthreads();
-        if (tid < 32) {  // exclusive scan of 256 totals by one warp, 8 per lane
-            uint32_t v[8], run_sum = 0;
-#pragma unroll
-            for (int i = 0; i < 8; ++i) {
-                v[i] = S.dtot[lane * 8 + i];
-                run_sum += v[i];
-            }
-            uint32_t inc = run_sum;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const uint32_t t = __shfl_up_sync(kFull, inc, o);
-                if (lane >= (uint32_t)o) inc += t;
-            }
-            uint32_t ex = inc - run_sum;
-#pragma unroll
-            for (int i = 0; i < 8; ++i) {
-                S.dtot[lane * 8 + i] = ex;
-                ex += v[i];
-            }
-        }
-        __syncthreads();
-        if (tid < 256) {
-            uint32_t off = S.dtot[tid];
-            for (uint32_t ww = 0; ww < nw; ++ww) {
-                const uint32_t c = S.whist[ww][tid];
-                S.whist[ww][tid] = (uint16_t)off;
-                off += c;
-            }
-        }
-        __syncthreads();
-        for (uint32_t p = pbeg + lane; p < pend; p += 32) nxt[p0 + S.whist[warp][dig[p]] + rnk[p]] = cur[p];
-        __syncthreads();
-        uint16_t* t = cur;
-        cur = nxt;
-        nxt = t;
-    }
-    if (cur != idx) {
-        for (uint32_t p = p0 + tid; p < pe; p += kLocalThreads) idx[p] = cur[p];
-        __syncthreads();
-    }
-    if (win.base > 0 && bits_vary(S.vary, 0, win.base, K))
-        settle_sub_runs(idx, p0, pe, tid, kLocalThreads, win, keys, cap, K, S.lists[0], &S.count[0], S.bstack,
-                        &S.bcount, overflow);
-    __syncthreads();
-}
-
-// Persistent blocks take buckets from a queue.  A bucket of m <= cap pairs is
-// loaded into shared memory and sorted by the 32-bit window that ends at its
-// top varying bit (all its keys agree above it; the window separates almost
-// all keys of a bucket, whose keys span a narrow key range): the whole block
-// runs an LSD radix sort over the window's varying 8-bit digits, ranking a
-// 16-bit index by warp ballots.  Items left with equal windows form sub-runs
-// that differ only below the window: up to kShortRun items are sorted at once
-// by a stable insertion sort of one thread; runs of kBlockRun or more items by
-// the whole block in the same way, one after another; the others in rounds,
-// one warp per sub-run, by their own windows, until none is left.  A run of
-// equal keys is already in order (the partition is stable).  The keys then
-// leave in sorted order and the row ids are gathered through the index.
-// Constant buckets larger than cap are left as partitioned; other oversize
-// buckets are listed for the plain radix sort.
-__global__ void __launch_bounds__(kLocalThreads, 1) local_sort_kernel(const LocalArgs a) {
-    extern __shared__ __align__(16) uint32_t lsm[];
-    const uint32_t K = a.K, cap = a.cap;
-    uint32_t* keys = lsm;                                                 // [K][cap]
-    uint16_t* idx = reinterpret_cast<uint16_t*>(keys + (size_t)K * cap);  // [cap] current order
-    uint16_t* alt = idx + cap;                                            // [cap]
-    uint16_t* rnk = alt + cap;                                            // [cap] rank within the warp
-    uint8_t* dig = reinterpret_cast<uint8_t*>(rnk + cap);                 // [cap]
-    __shared__ LocalShared S;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    for (;;) {
-        if (tid == 0) {
-            S.bucket = atomicAdd(a.next, 1u);
-            S.count[0] = 0;
-            S.count[1] = 0;
-            S.bcount = 0;
-        }
-        __syncthreads();
-        const uint32_t b = S.bucket;
-        if (b >= a.B) break;
-        const uint32_t s = a.start[b], m = a.start[b + 1] - s;
-        if (tid == 0 && m > 0) atomicMax(&a.counts[2], m);
-        if (m <= 1) {
-            __syncthreads();
-            continue;
-        }
-        if (m > cap) {
-            if (tid == 0) {
-                if (constant_bucket(a.spl, K, *a.nsplit + 1, b)) {
-                    atomicAdd(&a.counts[1], 1u);
-                } else {
-                    const uint32_t slot = atomicAdd(&a.flags[0], 1u);
-                    if (slot < a.max_over) {
-                        a.over[2 * slot] = s;
-                        a.over[2 * slot + 1] = s + m;
-                    }
-                }
-            }
-            __syncthreads();
-            continue;
-        }
-        for (uint32_t w = 0; w < K; ++w)
-            for (uint32_t t = tid; t < m; t += kLocalThreads)
-                keys[(size_t)w * cap + t] = a.ck[(uint64_t)w * a.ld + s + t];
-        for (uint32_t t = tid; t < m; t += kLocalThreads) idx[t] = (uint16_t)t;
-        __syncthreads();
-        if (m <= kShortRun) {
-            if (tid == 0) insertion_sort_run(idx, 0, m, keys, cap, K);
-        } else {
-            if (tid == 0) {
-                S.bstack[0] = m << 16;  // run = (length << 16) | first position; m <= cap < 2^16
-                S.bcount = 1;
-            }
-            __syncthreads();
-            for (;;) {  // runs for the whole block, one after another
-                if (tid == 0) S.run = S.bcount > 0 ? S.bstack[--S.bcount] : 0xFFFFFFFFu;
-                __syncthreads();
-                const uint32_t run = S.run;
-                if (run == 0xFFFFFFFFu) break;
-                block_sort_run(run & 0xFFFFu, run >> 16, keys, cap, K, idx, alt, rnk, dig, S, &a.flags[1]);
-                __syncthreads();
-            }
-            // rounds: one warp per shorter sub-run, appending the next round's runs
-            uint32_t cur_list = 0;
-            for (;;) {
-                const uint32_t nruns = min(S.count[cur_list], (uint32_t)kRunList);
-                if (nruns == 0) break;
-                if (tid == 0) {
-                    S.count[cur_list ^ 1] = 0;
-                    S.grab = 0;
-                }
-                __syncthreads();
-                for (;;) {
-                    uint32_t e = 0;
-                    if (lane == 0) e = atomicAdd(&S.grab, 1u);
-                    e = __shfl_sync(kFull, e, 0);
-                    if (e >= nruns) break;
-                    const uint32_t run = S.lists[cur_list][e];
-                    warp_sort_run(run & 0xFFFFu, run >> 16, keys, cap, K, idx, alt, rnk, dig, S.whist[warp],
-                                  S.wvary[warp], S.lists[cur_list ^ 1], &S.count[cur_list ^ 1], &a.flags[1]);
-                }
-                __syncthreads();
-                if (tid == 0) S.count[cur_list] = 0;
-                cur_list ^= 1;
-            }
-        }
-        __syncthreads();
-        // write the bucket back in sorted order; row ids through the permutation
-        for (uint32_t t = tid; t < m; t += kLocalThreads) {
-            const uint32_t src = idx[t];
-            for (uint32_t w = 0; w < K; ++w) a.ck[(uint64_t)w * a.ld + s + t] = keys[(size_t)w * cap + src];
-        }
-        __syncthreads();
-        uint32_t* rtmp = keys;  // the keys are written out; their space holds the row ids
-        for (uint32_t t = tid; t < m; t += kLocalThreads) rtmp[t] = a.rid[s + t];
-        __syncthreads();
-        for (uint32_t t = tid; t < m; t += kLocalThreads) a.rid[s + t] = rtmp[idx[t]];
-        if (tid == 0) atomicAdd(&a.counts[0], 1u);
-        __syncthreads();
-    }
-}
-
-// Every adjacent output pair must be in (key, row id) order.
-__global__ void verify_kernel(const uint32_t* __restrict__ ck, const uint32_t* __restrict__ rid, uint64_t ld,
-                              uint64_t n, uint32_t K, uint32_t* __restrict__ flags) {
-    uint32_t bad = 0;
-    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x + 1; i < n;
-         i += (uint64_t)gridDim.x * blockDim.x) {
-        int c = 0;
-        for (int w = (int)K - 1; w >= 0 && c == 0; --w) {
-            const uint32_t x = ck[(uint64_t)w * ld + i - 1], y = ck[(uint64_t)w * ld + i];
-            c = x < y ? -1 : (x > y ? 1 : 0);
-        }
-        if (c > 0 || (c == 0 && rid[i - 1] >= rid[i])) ++bad;
-    }
-    if (bad) atomicAdd(&flags[1], bad);
+    if (params_out && use_model && threadIdx.x < kParams) params_out[threadIdx.x] = params[threadIdx.x];
 }
 
 // ------------------------------------------------------------ separators
@@ -1169,52 +950,68 @@ __global__ void separators_kernel(const float* __restrict__ params, const __grid
     if (my_hits) atomicAdd(hits, my_hits);
 }
 
+__global__ void identity_rid_kernel(uint32_t* rid, uint64_t n) {
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x)
+        rid[i] = (uint32_t)i;
+}
+
 // ------------------------------------------------------------ workspace
 struct LearnedPlan {
-    uint32_t B, bucket_bits, max_buckets, id_bits, passes, K, nbits;
-    uint64_t S, ld_s, n, ld, div, chunk;
-    uint32_t cap, epochs, train_blocks, flags, max_over;
-    float lr;
+    uint32_t B, max_buckets, passes, K, nbits, cap, epochs, flags, u_s;
+    uint32_t nblk_s, nblk_g;  // blocks of the sample scans (S entries) and of the gap scans (S + 1 gaps)
+    uint64_t S, ld_s, n, ld, div, T, tstride, h_s;
+    float lr, t_s;
     SortPlan sample_sort, plain;
-    size_t off_sample, off_sample_sorted, off_sample_rid, off_sample_ws, off_xs, off_params, off_partial,
-        off_misc, off_start, off_over, off_codes, off_spl, off_bkt, off_alt_bkt, off_alt_ck, off_alt_rid, off_hist,
-        off_lookback, off_plain_ws, total;
+    size_t off_sample, off_sample_sorted, off_sample_rid, off_sample_ws, off_xs, off_ys, off_bmax, off_carry, off_flag,
+        off_bcnt, off_gaps, off_seg, off_mgap, off_gidx, off_map, off_params, off_misc, off_spl, off_start, off_const,
+        off_bkt, off_alt_bkt, off_alt_ck, off_alt_rid, off_hist, off_lookback, off_plain_ws, total;
 };
 
 static size_t a256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 static bool make_learned_plan(uint64_t n, uint32_t K, uint32_t nbits, const ck_learned_opts* o, LearnedPlan* p) {
     memset(p, 0, sizeof(*p));
-    // bucket capacity of one block: K key words, two 16-bit indices, a 16-bit
-    // rank and an 8-bit digit per pair in <= 200 KB, a multiple of 512
-    uint32_t cap = (uint32_t)((200 * 1024) / (4 * K + 7)) / 512 * 512;
-    if (cap > 16384) cap = 16384;
-    p->cap = cap;
-    // default bucket count: about 0.6 cap pairs per bucket (headroom for the
-    // sampling noise of the quantiles), between 2^8 and 2^16 buckets
-    uint32_t auto_bits = 8;
-    while (auto_bits < 16 && (n >> auto_bits) > cap * 6 / 10) ++auto_bits;
-    if (auto_bits == 16 && (n >> 15) <= cap * 3 / 4) auto_bits = 15;  // keeps the splitter table in shared memory
-    p->bucket_bits = o && o->bucket_bits ? o->bucket_bits : auto_bits;
-    if (p->bucket_bits < 8 || p->bucket_bits > 16) return false;
-    p->B = 1u << p->bucket_bits;
-    // heavy values add up to one bucket each; the bucket ids stay below 2^16
-    p->max_buckets = p->bucket_bits <= 15 ? min(2 * p->B, p->B + 8192u) : p->B;
-    p->id_bits = p->max_buckets > p->B ? p->bucket_bits + 1 : p->bucket_bits;
-    p->passes = p->id_bits > 8 ? 2 : 1;
-    p->div = o && o->sample_div ? o->sample_div : 100;
-    p->epochs = o && o->epochs ? o->epochs : 100;
-    p->lr = o && o->lr > 0.0f ? o->lr : 1e-3f;
-    p->flags = o ? o->flags : 0u;
+    if (K == 0 || K > kMaxLearnedWords || n < 2) return false;
     p->K = K;
     p->nbits = nbits;
     p->n = n;
     p->ld = CK_LD(n);
+    p->cap = local_sort_cap(K);
+    // model buckets: about 0.55 of a block's capacity per bucket on average
+    uint32_t B = 2;
+    if (o && o->bucket_bits) {
+        if (o->bucket_bits > 15) return false;
+        B = 1u << o->bucket_bits;
+    } else {
+        const double want = (double)n / (0.55 * p->cap);
+        while (B < kMaxModelBuckets && (double)B < want) B <<= 1;
+    }
+    p->B = B;
+    p->max_buckets = std::min<uint32_t>(kMaxBucketIds, std::max<uint32_t>(256u, 4u * B));
+    p->passes = p->max_buckets > 256 ? 2 : 1;
+    p->div = o && o->sample_div ? o->sample_div : 100;
+    p->epochs = o && o->epochs ? o->epochs : 100;
+    p->lr = o && o->lr > 0.0f ? o->lr : 1e-3f;
+    p->flags = o ? o->flags : 0u;
     p->S = n / p->div;
-    if (p->S < 2) p->S = n < 2 ? n : 2;
+    if (p->S < 2) {  // at least two sample keys: a stride that keeps both inside the column
+        p->S = 2;
+        p->div = n / 2;
+    }
     p->ld_s = CK_LD(p->S);
-    p->chunk = 4096;
-    p->train_blocks = (uint32_t)min(num_sms(), 32);
+    p->tstride = (p->S + kTrainPoints - 1) / kTrainPoints;
+    p->T = (p->S + p->tstride - 1) / p->tstride;
+    p->t_s = (float)((double)p->S / (double)B);
+    // u_s: most sample keys a bucket may hold so that its pairs (about
+    // u_s * n / S, with a relative spread of 1 / sqrt(u_s)) stay within the
+    // capacity at five standard deviations
+    const double per = (double)n / (double)p->S;
+    uint32_t u = 1;
+    while ((double)(u + 1) * per * (1.0 + 5.0 / std::sqrt((double)(u + 1))) <= (double)p->cap && u < (1u << 30)) ++u;
+    p->u_s = u;
+    p->h_s = std::max<uint64_t>(2, std::min<uint64_t>(u, (uint64_t)(p->t_s / 2.0f)));
+    p->nblk_s = (uint32_t)((p->S + kScanBlock - 1) / kScanBlock);
+    p->nblk_g = (uint32_t)((p->S + 1 + kScanBlock - 1) / kScanBlock);
     if (!make_sort_plan(p->S, K, nbits, 8, &p->sample_sort)) return false;
     if (!make_sort_plan(n, K, nbits, 8, &p->plain)) return false;
     const uint64_t tiles = (n + kPassTile - 1) / kPassTile;
@@ -1229,14 +1026,21 @@ static bool make_learned_plan(uint64_t n, uint32_t K, uint32_t nbits, const ck_l
     p->off_sample_rid = take(4ull * p->S);
     p->off_sample_ws = take(p->sample_sort.total);
     p->off_xs = take(4ull * p->S);
+    p->off_ys = take(4ull * p->nblk_s * kScanBlock);
+    p->off_bmax = take(4ull * p->nblk_s);
+    p->off_carry = take(4ull * p->nblk_s);
+    p->off_flag = take(4ull * (p->S + 1));
+    p->off_bcnt = take(4ull * p->nblk_g);
+    p->off_gaps = take(4ull * (p->S + 1));
+    p->off_seg = take(4ull * (p->S + 2));
+    p->off_mgap = take(4ull * (B + 1));
+    p->off_gidx = take(4ull * (p->S + 1));
+    p->off_map = take(4ull * (B + 1));
     p->off_params = take(4ull * kParams);
-    p->off_partial = take(4ull * 2 * p->train_blocks * kRed);
-    p->off_misc = take(256);  // barrier, loss, flags[2], counts[3], queue, steps[2] (u64)
-    p->max_over = 4096;
-    p->off_start = take(4ull * (p->max_buckets + 1));
-    p->off_over = take(4ull * 2 * p->max_over);
-    p->off_codes = take(p->B);
+    p->off_misc = take(sizeof(LearnedMisc));
     p->off_spl = take(4ull * K * p->max_buckets);
+    p->off_start = take(4ull * (p->max_buckets + 1));
+    p->off_const = take(4ull * 3 * kMaxConst);
     p->off_bkt = take(4ull * n);
     p->off_alt_bkt = take(4ull * n);
     p->off_alt_ck = take(4ull * K * p->ld);
@@ -1251,18 +1055,6 @@ static bool make_learned_plan(uint64_t n, uint32_t K, uint32_t nbits, const ck_l
 }  // namespace ck
 
 using namespace ck;
-
-namespace {
-struct Misc {  // layout of the misc block of the learned workspace
-    unsigned barrier;
-    float loss;
-    uint32_t flags[2];   // oversize buckets, order violations
-    uint32_t counts[3];  // buckets sorted, constant buckets, max bucket
-    uint32_t next;       // bucket queue of the local sorts
-    uint32_t nsplit;     // number of splitters
-    unsigned long long steps[2];
-};
-}  // namespace
 
 extern "C" {
 
@@ -1284,7 +1076,9 @@ ck_status ck_mlp_loss_grad(const float* params, const float* x, const float* t, 
 
 size_t ck_sort_learned_workspace_bytes(uint64_t n, uint32_t ck_words, uint32_t nbits, const ck_learned_opts* opts) {
     LearnedPlan p;
-    if (ck_words == 0 || ck_words > kMaxLearnedWords || !make_learned_plan(n, ck_words, nbits, opts, &p)) return 0;
+    if (ck_words == 0 || ck_words > kMaxLearnedWords) return 0;
+    if (n < 2) return 256;
+    if (!make_learned_plan(n, ck_words, nbits, opts, &p)) return 0;
     return p.total;
 }
 
@@ -1292,101 +1086,120 @@ ck_status ck_sort_learned(const uint32_t* ck_in, uint32_t* ck_out, uint32_t* rid
                           uint32_t nbits, const ck_learned_opts* opts, ck_learned_stats* stats, float* params_out,
                           void* ws_v, size_t ws_bytes, ck_stream stream) {
     if (n > CK_MAX_ROWS || ck_words == 0 || ck_words > kMaxLearnedWords || nbits > 32u * ck_words) return CK_EINVAL;
-    if (opts && (opts->reserved != 0 || (opts->flags & ~3u))) return CK_EINVAL;
-    if (stats) memset(stats, 0, sizeof(*stats));
+    if (opts && (opts->reserved != 0 || (opts->flags & ~7u) || opts->bucket_bits > 15)) return CK_EINVAL;
     if (n == 0) return CK_OK;
     if (!ck_in || !ck_out || !rid_out || ck_in == ck_out) return CK_EINVAL;
-    LearnedPlan P;
-    if (!make_learned_plan(n, ck_words, nbits, opts, &P)) return CK_EINVAL;
-    if (!ws_v || ws_bytes < P.total || (reinterpret_cast<uintptr_t>(ws_v) & 255)) return CK_ENOMEM;
     unsigned long long* status = status_ptr();
     if (!status) return CK_ECUDA;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-    unsigned char* ws = static_cast<unsigned char*>(ws_v);
-    auto at = [&](size_t off) { return reinterpret_cast<uint32_t*>(ws + off); };
-    const uint32_t K = ck_words;
-    const bool use_model = !(P.flags & CK_LEARNED_NO_MODEL);
 #define CK_TRY(x)                                    \
     do {                                             \
         if ((x) != cudaSuccess) return CK_ECUDA;     \
     } while (0)
-    Misc* misc = reinterpret_cast<Misc*>(ws + P.off_misc);
-    CK_TRY(cudaMemsetAsync(misc, 0, sizeof(Misc), s));
+    const uint32_t K = ck_words;
+    const uint64_t ld = CK_LD(n);
+    if (n < 2 || nbits == 0) {  // nothing to order: the keys as they are, row ids 0 .. n - 1
+        CK_TRY(cudaMemcpy2DAsync(ck_out, 4 * ld, ck_in, 4 * ld, 4 * n, K, cudaMemcpyDeviceToDevice, s));
+        identity_rid_kernel<<<num_sms() * 4, 256, 0, s>>>(rid_out, n);
+        count_launch();
+        if (stats) CK_TRY(cudaMemsetAsync(stats, 0, sizeof(ck_learned_stats), s));
+        return cudaGetLastError() == cudaSuccess ? CK_OK : CK_ECUDA;
+    }
+    LearnedPlan P;
+    if (!make_learned_plan(n, K, nbits, opts, &P)) return CK_EINVAL;
+    if (!ws_v || ws_bytes < P.total || (reinterpret_cast<uintptr_t>(ws_v) & 255)) return CK_ENOMEM;
+    unsigned char* ws = static_cast<unsigned char*>(ws_v);
+    auto at = [&](size_t off) { return reinterpret_cast<uint32_t*>(ws + off); };
+    auto atf = [&](size_t off) { return reinterpret_cast<float*>(ws + off); };
+    const bool use_model = !(P.flags & CK_LEARNED_NO_MODEL);
+    LearnedMisc* misc = reinterpret_cast<LearnedMisc*>(ws + P.off_misc);
+    const uint64_t tiles = (n + kPassTile - 1) / kPassTile;
+    CK_TRY(cudaMemsetAsync(misc, 0, sizeof(LearnedMisc), s));
+    CK_TRY(cudaMemsetAsync(ws + P.off_flag, 0, 4ull * (P.S + 1), s));
     CK_TRY(cudaMemsetAsync(ws + P.off_hist, 0, 4ull * 512, s));
-    CK_TRY(cudaMemsetAsync(ws + P.off_lookback, 0, P.off_plain_ws - P.off_lookback, s));
+    CK_TRY(cudaMemsetAsync(ws + P.off_lookback, 0, 4ull * 256 * tiles * P.passes + 4 * P.passes, s));
     const int sms = num_sms();
+    const uint32_t* smp = at(P.off_sample_sorted);
 
     // 1. sample, sort the sample, features
-    sample_kernel<<<sms * 4, 256, 0, s>>>(ck_in, P.ld, K, P.div, P.S, at(P.off_sample), P.ld_s);
+    sample_kernel<<<sms * 4, 256, 0, s>>>(ck_in, ld, K, P.div, P.S, at(P.off_sample), P.ld_s);
     count_launch();
     CK_TRY(run_sort(P.sample_sort, at(P.off_sample), nullptr, at(P.off_sample_sorted), at(P.off_sample_rid), P.S,
                     nbits, kDefaultSpin, 0, 0, nullptr, ws + P.off_sample_ws, s));
-    float* xs = reinterpret_cast<float*>(ws + P.off_xs);
-    features_kernel<<<sms * 4, 256, 0, s>>>(at(P.off_sample_sorted), P.ld_s, P.S, K, nbits, xs);
+    float* xs = atf(P.off_xs);
+    features_kernel<<<sms * 4, 256, 0, s>>>(smp, P.ld_s, P.S, K, nbits, xs);
     count_launch();
 
-    // 2. model: spline initialisation, full-batch Adam (cooperative launch)
-    float* params = reinterpret_cast<float*>(ws + P.off_params);
+    // 2. model: spline initialisation, full-batch Adam
+    float* params = atf(P.off_params);
     if (use_model) {
         mlp_init_kernel<<<1, 32, 0, s>>>(xs, P.S, params);
-        count_launch();
-        TrainArgs ta;
-        ta.xs = xs;
-        ta.S = P.S;
-        ta.stride = (P.S + kMaxTrainPoints - 1) / kMaxTrainPoints;
-        ta.T = (P.S + ta.stride - 1) / ta.stride;
-        ta.params = params;
-        ta.partial = reinterpret_cast<float*>(ws + P.off_partial);
-        ta.barrier = &misc->barrier;
-        ta.loss = &misc->loss;
-        ta.epochs = P.epochs;
-        ta.lr = P.lr;
-        ta.spin_limit = kDefaultSpin;
-        ta.status = status;
-        void* args[] = {&ta};
-        CK_TRY(cudaLaunchCooperativeKernel((const void*)mlp_train_kernel, dim3(P.train_blocks), dim3(kTrainThreads),
-                                           args, 0, s));
+        mlp_train_kernel<<<1, kTrainThreads, 0, s>>>(xs, P.S, P.T, P.tstride, params, &misc->loss, P.epochs, P.lr);
+        count_launch(2);
+    }
+
+    // 3. boundaries: the model's crossings (or plain quantiles), heavy keys,
+    //    quantile cuts inside oversized model buckets; then the splitter values
+    uint32_t* flag = at(P.off_flag);
+    const uint32_t gb = (P.B + 256) / 256;
+    if (use_model) {
+        model_ys_kernel<<<P.nblk_s, 256, 0, s>>>(xs, P.S, params, atf(P.off_ys), atf(P.off_bmax));
+        max_carry_kernel<<<1, 1024, 0, s>>>(atf(P.off_bmax), P.nblk_s, atf(P.off_carry));
+        model_cross_kernel<<<gb, 256, 0, s>>>(atf(P.off_ys), atf(P.off_bmax), atf(P.off_carry), P.nblk_s, P.S, P.B,
+                                              smp, P.ld_s, K, at(P.off_mgap), flag);
+        count_launch(3);
+    } else {
+        quantile_flag_kernel<<<gb, 256, 0, s>>>(P.S, P.B, smp, P.ld_s, K, flag);
         count_launch();
     }
-    // 3. splitters: sample quantiles (they cut through long shared prefixes that
-    //    a 24-bit feature cannot see) moved to run ends, heavy values isolated
-    const uint64_t heavy = std::max<uint64_t>(2, (P.S + 2ull * P.B - 1) / (2ull * P.B));
-    uint8_t* codes = reinterpret_cast<uint8_t*>(ws + P.off_codes);
-    quantile_kernel<<<(P.B + 255) / 256, 256, 0, s>>>(at(P.off_sample_sorted), P.ld_s, P.S, K, P.B, nbits, heavy,
-                                                      codes);
-    emit_splitters_kernel<<<1, 1024, 0, s>>>(at(P.off_sample_sorted), P.ld_s, P.S, K, P.B, P.max_buckets, codes,
-                                             at(P.off_spl), &misc->nsplit);
-    count_launch(2);
+    heavy_kernel<<<sms * 4, 256, 0, s>>>(P.S, P.h_s, smp, P.ld_s, K, nbits, flag, misc);
+    gap_count_kernel<0><<<P.nblk_g, kScanBlock, 0, s>>>(flag, P.S, smp, P.ld_s, K, nbits, at(P.off_bcnt));
+    scan_counts_kernel<<<1, 1024, 0, s>>>(at(P.off_bcnt), P.nblk_g, nullptr, &misc->g1, 0, nullptr);
+    gap_write_kernel<<<P.nblk_g, kScanBlock, 0, s>>>(flag, P.S, at(P.off_bcnt), at(P.off_gaps));
+    subdiv_count_kernel<<<sms * 4, 256, 0, s>>>(at(P.off_gaps), misc, P.S, smp, P.ld_s, K, P.t_s, P.u_s,
+                                                 at(P.off_seg));
+    scan_counts_kernel<<<1, 1024, 0, s>>>(at(P.off_seg), 0, &misc->g1, &misc->nsub, 0, nullptr);
+    subdiv_flag_kernel<<<sms * 4, 256, 0, s>>>(at(P.off_gaps), misc, P.S, smp, P.ld_s, K, P.t_s, P.u_s,
+                                                at(P.off_seg), flag);
+    gap_count_kernel<1><<<P.nblk_g, kScanBlock, 0, s>>>(flag, P.S, smp, P.ld_s, K, nbits, at(P.off_bcnt));
+    scan_counts_kernel<<<1, 1024, 0, s>>>(at(P.off_bcnt), P.nblk_g, nullptr, &misc->nsplit, P.max_buckets,
+                                          &misc->gate);
+    value_write_kernel<<<P.nblk_g, kScanBlock, 0, s>>>(flag, P.S, smp, P.ld_s, K, nbits, at(P.off_bcnt),
+                                                       P.max_buckets - 1, at(P.off_spl), at(P.off_gidx), misc);
+    count_launch(9);
+    if (use_model) {
+        guess_map_kernel<<<gb, 256, 0, s>>>(at(P.off_mgap), at(P.off_gidx), P.S, P.B, misc, at(P.off_map));
+        count_launch();
+    }
 
-    // 4. bucket id of every key (model guess + exact correction), digit histograms
+    // 4. bucket id of every key (model guess + exact correction), digit
+    //    counts, input hash
     BucketArgs ba;
     ba.ck = ck_in;
-    ba.ld = P.ld;
+    ba.ld = ld;
     ba.n = n;
     ba.K = K;
     ba.nbits = nbits;
     ba.max_buckets = P.max_buckets;
-    ba.nsplit = &misc->nsplit;
+    ba.B = P.B;
     ba.use_model = use_model ? 1u : 0u;
-    ba.spl = at(P.off_spl);
+    ba.passes = P.passes;
     ba.params = use_model ? params : nullptr;
-    ba.loss = &misc->loss;
+    ba.spl = at(P.off_spl);
+    ba.map = at(P.off_map);
+    ba.misc = misc;
     ba.bkt = at(P.off_bkt);
     ba.hist = at(P.off_hist);
-    ba.steps = misc->steps;
-    const size_t top_bytes = 4ull * (P.max_buckets - 1) + 4ull * ((1u << kPrefixBits) + 1);
-    const bool staged = top_bytes <= 200 * 1024;
-    CK_TRY(launch_bucket(ba, staged, top_bytes, sms, s));
+    CK_TRY(launch_bucket(ba, sms, s));
     count_launch();
     CK_TRY(launch_bucket_scan(at(P.off_hist), P.passes, 8, s));
 
-    // 5. stable partition by bucket id: radix passes over its low 8 bits, then the rest
+    // 5. stable partition by bucket id: radix passes over its low byte, then its high byte
     auto al16 = [](const void* q) { return (reinterpret_cast<uintptr_t>(q) & 15) == 0; };
     const uint32_t bulk = al16(ck_in) && al16(ck_out) && al16(rid_out) ? 1u : 0u;
-    const uint64_t tiles = (n + kPassTile - 1) / kPassTile;
     uint32_t* counters = at(P.off_lookback) + 256ull * tiles * P.passes;
-    static thread_local PassArrays arr;
     for (uint32_t q = 0; q < P.passes; ++q) {
+        PassArrays arr;
         const bool last = q + 1 == P.passes;
         uint32_t m = 0;
         const uint32_t* src_ck = q == 0 ? ck_in : at(P.off_alt_ck);
@@ -1396,8 +1209,8 @@ ck_status ck_sort_learned(const uint32_t* ck_in, uint32_t* ck_out, uint32_t* rid
         arr.dst[m] = last ? nullptr : at(P.off_alt_bkt);
         ++m;
         for (uint32_t w = 0; w < K; ++w, ++m) {
-            arr.src[m] = src_ck + (uint64_t)w * P.ld;
-            arr.dst[m] = dst_ck + (uint64_t)w * P.ld;
+            arr.src[m] = src_ck + (uint64_t)w * ld;
+            arr.dst[m] = dst_ck + (uint64_t)w * ld;
         }
         arr.src[m] = q == 0 ? nullptr : at(P.off_alt_rid);
         arr.dst[m] = last ? rid_out : at(P.off_alt_rid);
@@ -1406,7 +1219,7 @@ ck_status ck_sort_learned(const uint32_t* ck_in, uint32_t* ck_out, uint32_t* rid
         a.n = n;
         a.narr = m;
         a.sh = 8 * q;
-        a.bits = last ? P.id_bits - 8 * q : 8;
+        a.bits = 8;
         a.straddle = 0;
         a.pass = q;
         a.bulk = bulk;
@@ -1416,82 +1229,40 @@ ck_status ck_sort_learned(const uint32_t* ck_in, uint32_t* ck_out, uint32_t* rid
         a.spin_limit = kDefaultSpin;
         a.inject = 0;
         a.status = status;
+        a.gate = &misc->gate;
+        a.gate_run = 0;
         CK_TRY(launch_onesweep_pass(8, a, arr, (uint32_t)tiles, s));
     }
 
-    // 6. bucket starts (binary search of the splitters in the partitioned
-    //    keys), then every bucket sorted in shared memory, in place
+    // 6. bucket starts, then every bucket sorted and checked
     uint32_t* start = at(P.off_start);
-    bucket_bounds_kernel<<<(P.max_buckets + 256) / 256, 256, 0, s>>>(ck_out, P.ld, n, K, at(P.off_spl),
-                                                                     &misc->nsplit, P.max_buckets, start);
+    bucket_bounds_kernel<<<(P.max_buckets + 256) / 256, 256, 0, s>>>(ck_out, ld, n, K, at(P.off_spl), misc,
+                                                                     P.max_buckets, start);
     count_launch();
-    LocalArgs la;
+    LocalSortArgs la;
     la.ck = ck_out;
     la.rid = rid_out;
+    la.ld = ld;
+    la.n = n;
+    la.K = K;
+    la.cap = P.cap;
+    la.max_buckets = P.max_buckets;
     la.start = start;
     la.spl = at(P.off_spl);
-    la.nsplit = &misc->nsplit;
-    la.ld = P.ld;
-    la.K = K;
-    la.B = P.max_buckets;
-    la.cap = P.cap;
-    la.next = &misc->next;
-    la.flags = misc->flags;
-    la.counts = misc->counts;
-    la.over = at(P.off_over);
-    la.max_over = P.max_over;
-    const size_t lsmem = (size_t)P.cap * (4 * K + 7) + 16;
-    CK_TRY(cudaFuncSetAttribute(local_sort_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lsmem));
-    int per_sm = 1;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, local_sort_kernel, kLocalThreads, lsmem);
-    local_sort_kernel<<<sms * (per_sm > 0 ? per_sm : 1), kLocalThreads, lsmem, s>>>(la);
-    count_launch();
-    Misc host;
-    CK_TRY(cudaMemcpyAsync(&host, misc, sizeof(Misc), cudaMemcpyDeviceToHost, s));
-    CK_TRY(cudaStreamSynchronize(s));
-    // 7. buckets too large for a block (keys not all equal): the plain radix
-    //    sort on just that segment, in place (the partition order is stable)
-    bool failed = host.flags[0] > P.max_over;
-    if (!failed && host.flags[0] > 0) {
-        static thread_local uint32_t over[2 * 4096];
-        CK_TRY(cudaMemcpy(over, at(P.off_over), 8ull * host.flags[0], cudaMemcpyDeviceToHost));
-        for (uint32_t k = 0; k < host.flags[0] && !failed; ++k) {
-            const uint64_t b0 = over[2 * k], m = over[2 * k + 1] - b0;
-            SortPlan sp;
-            if (!make_sort_plan(m, K, nbits, 8, &sp, P.ld) || sp.total > P.plain.total) {
-                failed = true;
-                break;
-            }
-            CK_TRY(run_sort(sp, ck_out + b0, rid_out + b0, ck_out + b0, rid_out + b0, m, nbits, kDefaultSpin, 0, 0,
-                            nullptr, ws + P.off_plain_ws, s));
-        }
-    }
+    la.misc = misc;
+    la.const_list = at(P.off_const);
+    la.max_const = kMaxConst;
+    la.inject = P.flags;
+    CK_TRY(launch_local_sort(la, s));
 
-    // 8. verification of every adjacent pair
-    verify_kernel<<<sms * 8, 256, 0, s>>>(ck_out, rid_out, P.ld, n, K, misc->flags);
+    // 7. verdict, statistics; the plain radix sort runs only if the verdict says so
+    finalize_kernel<<<1, 64, 0, s>>>(misc, (P.flags & CK_LEARNED_INJECT_VERIFY_FAIL) ? 1u : 0u, use_model ? 1u : 0u,
+                                     P.B, P.S, n, P.cap, status, stats, params, params_out);
     count_launch();
-    CK_TRY(cudaMemcpyAsync(&host, misc, sizeof(Misc), cudaMemcpyDeviceToHost, s));
-    CK_TRY(cudaStreamSynchronize(s));
-    if (params_out && use_model) CK_TRY(cudaMemcpy(params_out, params, 4 * kParams, cudaMemcpyDeviceToHost));
-    failed = failed || host.flags[1] != 0 || (P.flags & CK_LEARNED_INJECT_VERIFY_FAIL);
-    if (stats) {
-        stats->train_loss = use_model ? host.loss : 0.0f;
-        stats->mean_search_steps = (float)((double)host.steps[0] / (double)n);
-        stats->max_search_steps = (uint32_t)host.steps[1];
-        stats->buckets = host.nsplit + 1;
-        stats->sample_size = (uint32_t)P.S;
-        stats->max_bucket = host.counts[2];
-        stats->sorted_segments = host.counts[0];
-        stats->constant_buckets = host.counts[1];
-        stats->oversize_buckets = host.flags[0];
-        stats->fell_back = failed ? 1u : 0u;
-    }
-    if (!failed) return CK_OK;
-    // fallback: the plain radix sort from the untouched input
     CK_TRY(run_sort(P.plain, ck_in, nullptr, ck_out, rid_out, n, nbits, kDefaultSpin, 0, 0, nullptr,
-                    ws + P.off_plain_ws, s));
+                    ws + P.off_plain_ws, s, nullptr, &misc->gate));
 #undef CK_TRY
-    return CK_EVERIFY;
+    return cudaGetLastError() == cudaSuccess ? CK_OK : CK_ECUDA;
 }
 
 ck_status ck_model_separators(const float* params, const ck_btree* tree, uint32_t ck_words, uint32_t nbits,

@@ -48,7 +48,11 @@ struct PassSmem {
     alignas(8) uint64_t bar[kRing];
 };
 
-template <int RB, int THREADS>
+// PERSIST: a fixed grid whose blocks take tiles until none is left, staging
+// with plain loads (the shape of a gated sort that usually does not run: when
+// the gate is shut, a few hundred blocks return at once instead of one block
+// per tile).  Without PERSIST every block takes one tile.
+template <int RB, int THREADS, bool PERSIST>
 __global__ void __launch_bounds__(THREADS, THREADS == 256 ? kPassDeepBlocksPerSM : kPassBlocksPerSM)
     onesweep_pass_kernel(const PassArgs a, const __grid_constant__ PassArrays arr) {
     constexpr int kPassThreads = THREADS;
@@ -57,25 +61,28 @@ __global__ void __launch_bounds__(THREADS, THREADS == 256 ? kPassDeepBlocksPerSM
     extern __shared__ __align__(128) unsigned char smem_raw[];
     PassSmem<RB, THREADS>& S = *reinterpret_cast<PassSmem<RB, THREADS>*>(smem_raw);
 
+    if (a.gate && *(volatile const uint32_t*)a.gate != a.gate_run) return;  // decided on the device
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const uint64_t n = a.n;
     const uint32_t sh = a.sh;
     const bool straddle = a.straddle != 0;
     const uint32_t M = a.narr;
     if (tid == 0) {
-        S.scratch[WARPS + 1] = atomicAdd(a.tile_counter, 1u);
         int16_t u = 0;
         for (uint32_t m = 0; m < M; ++m) S.use[m] = arr.src[m] ? u++ : (int16_t)-1;
         for (int b = 0; b < kRing; ++b) mbar_init(&S.bar[b], 1);
         fence_mbar_init();
     }
+  for (;;) {
+    if (tid == 0) S.scratch[WARPS + 1] = atomicAdd(a.tile_counter, 1u);
     for (int i = tid; i < WARPS * BINS; i += kPassThreads) (&S.whist[0][0])[i] = 0;
     for (int i = tid; i < BINS; i += kPassThreads) S.tile_total[i] = 0;
     __syncthreads();
     const uint32_t tile = S.scratch[WARPS + 1];
+    if (PERSIST && tile >= a.tiles) break;
     const uint64_t tile_base = (uint64_t)tile * kTile;
     const uint32_t count = (uint32_t)min((uint64_t)kTile, n - tile_base);
-    const bool bulk = a.bulk && count == (uint32_t)kTile;
+    const bool bulk = !PERSIST && a.bulk && count == (uint32_t)kTile;
 
     // array m lives in ring slot use[m] % kRing; its k-th use is phase k of that slot's barrier
     auto buf_of = [&](uint32_t m) -> uint32_t* { return S.stage[S.use[m] % kRing]; };
@@ -275,17 +282,32 @@ __global__ void __launch_bounds__(THREADS, THREADS == 256 ? kPassDeepBlocksPerSM
             __syncthreads();
         }
     }
+    if (!PERSIST) break;
+    __syncthreads();  // the tile's shared state is free for the next tile
+  }
 }
 
-// Launches one pass; `arrays` lists the arrays in staging order.
+// Launches one pass; `arrays` lists the arrays in staging order.  A pass
+// gated to run only on the device's say-so (a fallback) takes the persistent
+// shape.
 template <int RB, int THREADS>
-static cudaError_t launch_pass_shape(const PassArgs& a, const PassArrays& arrays, uint32_t tiles, cudaStream_t s) {
+static cudaError_t launch_pass_shape(const PassArgs& a_in, const PassArrays& arrays, uint32_t tiles, cudaStream_t s) {
     constexpr size_t smem = sizeof(PassSmem<RB, THREADS>);
     static_assert(sizeof(PassSmem<RB, THREADS>) <= 227 * 1024, "pass block exceeds shared memory");
-    cudaError_t e = cudaFuncSetAttribute(onesweep_pass_kernel<RB, THREADS>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    PassArgs a = a_in;
+    a.tiles = tiles;
+    const bool persist = a.gate != nullptr && a.gate_run != 0;
+    const void* fn = persist ? (const void*)onesweep_pass_kernel<RB, THREADS, true>
+                             : (const void*)onesweep_pass_kernel<RB, THREADS, false>;
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    onesweep_pass_kernel<RB, THREADS><<<tiles, THREADS, smem, s>>>(a, arrays);
+    if (persist) {
+        const uint32_t per_sm = THREADS == 256 ? kPassDeepBlocksPerSM : kPassBlocksPerSM;
+        const uint32_t grid = (uint32_t)min((uint64_t)tiles, (uint64_t)num_sms() * per_sm);
+        onesweep_pass_kernel<RB, THREADS, true><<<grid, THREADS, smem, s>>>(a, arrays);
+    } else {
+        onesweep_pass_kernel<RB, THREADS, false><<<tiles, THREADS, smem, s>>>(a, arrays);
+    }
     count_launch();
     return cudaGetLastError();
 }

@@ -24,12 +24,18 @@ __device__ __forceinline__ uint32_t digit_of(const uint32_t* ck, uint64_t ld, ui
 }
 
 // ------------------------------------------------------------------ upsweep
+// A gated kernel (gate != NULL) returns at once unless *gate != 0.
+__device__ __forceinline__ bool gated_off(const uint32_t* gate) {
+    return gate != nullptr && *(volatile const uint32_t*)gate == 0;
+}
+
 template <int RB>
 __global__ void __launch_bounds__(kUpThreads) upsweep_kernel(const uint32_t* __restrict__ ck, uint64_t n, uint64_t ld,
                                                              uint32_t nbits, uint32_t p0, uint32_t np,
-                                                             uint32_t* __restrict__ hist) {
+                                                             uint32_t* __restrict__ hist, const uint32_t* gate) {
     constexpr int BINS = 1 << RB;
     extern __shared__ uint32_t sh[];
+    if (gated_off(gate)) return;
     for (uint32_t i = threadIdx.x; i < np * BINS; i += blockDim.x) sh[i] = 0;
     __syncthreads();
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
@@ -50,9 +56,11 @@ __global__ void __launch_bounds__(kUpThreads) upsweep_kernel(const uint32_t* __r
 template <int RB, int KW>
 __global__ void __launch_bounds__(kUpThreads) upsweep_kw_kernel(const uint32_t* __restrict__ ck, uint64_t n,
                                                                 uint64_t ld, uint32_t nbits, uint32_t p0,
-                                                                uint32_t np, uint32_t* __restrict__ hist) {
+                                                                uint32_t np, uint32_t* __restrict__ hist,
+                                                                const uint32_t* gate) {
     constexpr int BINS = 1 << RB, DIGITS = (32 * KW + RB - 1) / RB;
     extern __shared__ uint32_t sh[];
+    if (gated_off(gate)) return;
     for (uint32_t i = threadIdx.x; i < np * BINS; i += blockDim.x) sh[i] = 0;
     __syncthreads();
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
@@ -77,25 +85,33 @@ __global__ void __launch_bounds__(kUpThreads) upsweep_kw_kernel(const uint32_t* 
 
 template <int RB>
 static void launch_upsweep(const uint32_t* ck, uint64_t n, uint64_t ld, uint32_t K, uint32_t nbits, uint32_t p0,
-                           uint32_t np, uint32_t* hist, int grid, cudaStream_t s) {
+                           uint32_t np, uint32_t* hist, int grid, cudaStream_t s, const uint32_t* g) {
     const size_t smem = sizeof(uint32_t) * np * (1u << RB);
     switch (K) {
-        case 1: upsweep_kw_kernel<RB, 1><<<grid, kUpThreads, smem, s>>>(ck, n, ld, nbits, p0, np, hist); break;
-        case 2: upsweep_kw_kernel<RB, 2><<<grid, kUpThreads, smem, s>>>(ck, n, ld, nbits, p0, np, hist); break;
-        case 3: upsweep_kw_kernel<RB, 3><<<grid, kUpThreads, smem, s>>>(ck, n, ld, nbits, p0, np, hist); break;
-        case 4: upsweep_kw_kernel<RB, 4><<<grid, kUpThreads, smem, s>>>(ck, n, ld, nbits, p0, np, hist); break;
-        case 5: upsweep_kw_kernel<RB, 5><<<grid, kUpThreads, smem, s>>>(ck, n, ld, nbits, p0, np, hist); break;
-        case 6: upsweep_kw_kernel<RB, 6><<<grid, kUpThreads, smem, s>>>(ck, n, ld, nbits, p0, np, hist); break;
-        case 7: upsweep_kw_kernel<RB, 7><<<grid, kUpThreads, smem, s>>>(ck, n, ld, nbits, p0, np, hist); break;
-        case 8: upsweep_kw_kernel<RB, 8><<<grid, kUpThreads, smem, s>>>(ck, n, ld, nbits, p0, np, hist); break;
-        default: upsweep_kernel<RB><<<grid, kUpThreads, smem, s>>>(ck, n, ld, nbits, p0, np, hist); break;
+        case 1: upsweep_kw_kernel<RB, 1><<<grid, kUpThreads, smem, s>>>(ck, n, ld, nbits, p0, np, hist, g); break;
+        case 2: upsweep_kw_kernel<RB, 2><<<grid, kUpThreads, smem, s>>>(ck, n, ld, nbits, p0, np, hist, g); break;
+        case 3: upsweep_kw_kernel<RB, 3><<<grid, kUpThreads, smem, s>>>(ck, n, ld, nbits, p0, np, hist, g); break;
+        case 4: upsweep_kw_kernel<RB, 4><<<grid, kUpThreads, smem, s>>>(ck, n, ld, nbits, p0, np, hist, g); break;
+        case 5: upsweep_kw_kernel<RB, 5><<<grid, kUpThreads, smem, s>>>(ck, n, ld, nbits, p0, np, hist, g); break;
+        case 6: upsweep_kw_kernel<RB, 6><<<grid, kUpThreads, smem, s>>>(ck, n, ld, nbits, p0, np, hist, g); break;
+        case 7: upsweep_kw_kernel<RB, 7><<<grid, kUpThreads, smem, s>>>(ck, n, ld, nbits, p0, np, hist, g); break;
+        case 8: upsweep_kw_kernel<RB, 8><<<grid, kUpThreads, smem, s>>>(ck, n, ld, nbits, p0, np, hist, g); break;
+        default: upsweep_kernel<RB><<<grid, kUpThreads, smem, s>>>(ck, n, ld, nbits, p0, np, hist, g); break;
     }
 }
 
 template <int RB>
-__global__ void __launch_bounds__(256) scan_kernel(uint32_t* hist) {
+__global__ void __launch_bounds__(256) scan_kernel(uint32_t* hist, const uint32_t* gate) {
     __shared__ uint32_t scratch[256 / 32 + 1];
+    if (gated_off(gate)) return;
     block_exclusive_scan<256>(hist + (uint64_t)blockIdx.x * (1u << RB), 1 << RB, scratch);
+}
+
+// Zeroes words [0, count) unless gated off (the gated sort's workspace clear).
+__global__ void gated_zero_kernel(uint32_t* p, uint64_t count, const uint32_t* gate) {
+    if (gated_off(gate)) return;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (uint64_t)gridDim.x * blockDim.x)
+        p[i] = 0;
 }
 
 __global__ void iota_kernel(uint32_t* out, uint64_t n) {
@@ -105,11 +121,11 @@ __global__ void iota_kernel(uint32_t* out, uint64_t n) {
 
 cudaError_t launch_bucket_scan(uint32_t* hist, uint32_t sets, uint32_t rb, cudaStream_t s) {
     switch (rb) {
-        case 4: scan_kernel<4><<<sets, 256, 0, s>>>(hist); break;
-        case 5: scan_kernel<5><<<sets, 256, 0, s>>>(hist); break;
-        case 6: scan_kernel<6><<<sets, 256, 0, s>>>(hist); break;
-        case 7: scan_kernel<7><<<sets, 256, 0, s>>>(hist); break;
-        case 8: scan_kernel<8><<<sets, 256, 0, s>>>(hist); break;
+        case 4: scan_kernel<4><<<sets, 256, 0, s>>>(hist, nullptr); break;
+        case 5: scan_kernel<5><<<sets, 256, 0, s>>>(hist, nullptr); break;
+        case 6: scan_kernel<6><<<sets, 256, 0, s>>>(hist, nullptr); break;
+        case 7: scan_kernel<7><<<sets, 256, 0, s>>>(hist, nullptr); break;
+        case 8: scan_kernel<8><<<sets, 256, 0, s>>>(hist, nullptr); break;
         default: return cudaErrorInvalidValue;
     }
     count_launch();
@@ -148,7 +164,7 @@ bool make_sort_plan(uint64_t n, uint32_t K, uint32_t nbits, uint32_t digit_bits,
 // All pass histograms of compressed keys, in chunks that fit 64 KB of shared memory.
 template <int RB>
 static cudaError_t upsweep_all(const uint32_t* ck_in, uint64_t n, uint64_t ld, uint32_t K, uint32_t nbits,
-                               uint32_t passes, uint32_t* hist, cudaStream_t s) {
+                               uint32_t passes, uint32_t* hist, cudaStream_t s, const uint32_t* gate = nullptr) {
     constexpr int BINS = 1 << RB;
     cudaError_t e = cudaSuccess;
     const uint32_t chunk = (uint32_t)(65536 / (sizeof(uint32_t) * BINS));
@@ -167,7 +183,7 @@ static cudaError_t upsweep_all(const uint32_t* ck_in, uint64_t n, uint64_t ld, u
     }
     for (uint32_t p0 = 0; p0 < passes; p0 += chunk) {
         const uint32_t np = min(chunk, passes - p0);
-        launch_upsweep<RB>(ck_in, n, ld, K, nbits, p0, np, hist, up_grid, s);
+        launch_upsweep<RB>(ck_in, n, ld, K, nbits, p0, np, hist, up_grid, s, gate);
         count_launch();
     }
     return cudaGetLastError();
@@ -177,7 +193,7 @@ template <int RB>
 static cudaError_t run_sort_rb(const SortPlan& p, const uint32_t* ck_in, const uint32_t* rid_in, uint32_t* ck_out,
                                uint32_t* rid_out, uint64_t n, uint32_t nbits, uint32_t spin_limit, uint32_t inject,
                                uint32_t flags, cudaEvent_t* ev, unsigned char* ws, cudaStream_t s,
-                               const uint32_t* hist_in) {
+                               const uint32_t* hist_in, const uint32_t* gate) {
     constexpr int BINS = 1 << RB;
     uint32_t* hist = reinterpret_cast<uint32_t*>(ws + p.off_hist);
     uint32_t* counters = reinterpret_cast<uint32_t*>(ws + p.off_counter);
@@ -185,17 +201,23 @@ static cudaError_t run_sort_rb(const SortPlan& p, const uint32_t* ck_in, const u
     uint32_t* alt_ck = reinterpret_cast<uint32_t*>(ws + p.off_alt_ck);
     uint32_t* alt_rid = reinterpret_cast<uint32_t*>(ws + p.off_alt_rid);
     const uint64_t ld = p.ld;
-    cudaError_t e = cudaMemsetAsync(ws, 0, p.off_alt_ck, s);
-    if (e != cudaSuccess) return e;
+    cudaError_t e = cudaSuccess;
+    if (gate) {
+        gated_zero_kernel<<<num_sms() * 4, 256, 0, s>>>(reinterpret_cast<uint32_t*>(ws), p.off_alt_ck / 4, gate);
+        count_launch();
+    } else {
+        e = cudaMemsetAsync(ws, 0, p.off_alt_ck, s);
+        if (e != cudaSuccess) return e;
+    }
 
     if (hist_in) {  // counted during extraction (ck_extract_hist)
         e = cudaMemcpyAsync(hist, hist_in, sizeof(uint32_t) * BINS * p.passes, cudaMemcpyDeviceToDevice, s);
         if (e != cudaSuccess) return e;
     } else {
-        e = upsweep_all<RB>(ck_in, n, ld, p.K, nbits, p.passes, hist, s);
+        e = upsweep_all<RB>(ck_in, n, ld, p.K, nbits, p.passes, hist, s, gate);
         if (e != cudaSuccess) return e;
     }
-    scan_kernel<RB><<<p.passes, 256, 0, s>>>(hist);
+    scan_kernel<RB><<<p.passes, 256, 0, s>>>(hist, gate);
     count_launch();
 
     const bool perm_only = (flags & CK_SORT_PERM_ONLY) != 0;
@@ -243,6 +265,8 @@ static cudaError_t run_sort_rb(const SortPlan& p, const uint32_t* ck_in, const u
         a.spin_limit = spin_limit;
         a.inject = inject;
         a.status = status_ptr();
+        a.gate = gate;
+        a.gate_run = 1;
         e = launch_onesweep_pass(RB, a, arrays, p.tiles, s);
         if (e != cudaSuccess) return e;
         if (ev && (e = cudaEventRecord(ev[q + 1], s)) != cudaSuccess) return e;
@@ -263,7 +287,10 @@ static cudaError_t run_sort_rb(const SortPlan& p, const uint32_t* ck_in, const u
 
 cudaError_t run_sort(const SortPlan& p, const uint32_t* ck_in, const uint32_t* rid_in, uint32_t* ck_out,
                      uint32_t* rid_out, uint64_t n, uint32_t nbits, uint32_t spin_limit, uint32_t inject,
-                     uint32_t flags, cudaEvent_t* ev, unsigned char* ws, cudaStream_t s, const uint32_t* hist_in) {
+                     uint32_t flags, cudaEvent_t* ev, unsigned char* ws, cudaStream_t s, const uint32_t* hist_in,
+                     const uint32_t* gate) {
+    if (gate && (p.passes == 0 || hist_in || ck_in == ck_out || (rid_in != nullptr && rid_in == rid_out)))
+        return cudaErrorInvalidValue;
     if (p.passes == 0) {  // nothing to order: outputs are the inputs
         cudaError_t e = cudaSuccess;
         if (ck_out != ck_in)
@@ -280,14 +307,14 @@ cudaError_t run_sort(const SortPlan& p, const uint32_t* ck_in, const uint32_t* r
         return cudaGetLastError();
     }
     switch (p.digit_bits) {
-        case 4: return run_sort_rb<4>(p, ck_in, rid_in, ck_out, rid_out, n, nbits, spin_limit, inject, flags, ev, ws, s, hist_in);
-        case 5: return run_sort_rb<5>(p, ck_in, rid_in, ck_out, rid_out, n, nbits, spin_limit, inject, flags, ev, ws, s, hist_in);
-        case 6: return run_sort_rb<6>(p, ck_in, rid_in, ck_out, rid_out, n, nbits, spin_limit, inject, flags, ev, ws, s, hist_in);
-        case 7: return run_sort_rb<7>(p, ck_in, rid_in, ck_out, rid_out, n, nbits, spin_limit, inject, flags, ev, ws, s, hist_in);
-        case 8: return run_sort_rb<8>(p, ck_in, rid_in, ck_out, rid_out, n, nbits, spin_limit, inject, flags, ev, ws, s, hist_in);
-        case 9: return run_sort_rb<9>(p, ck_in, rid_in, ck_out, rid_out, n, nbits, spin_limit, inject, flags, ev, ws, s, hist_in);
-        case 10: return run_sort_rb<10>(p, ck_in, rid_in, ck_out, rid_out, n, nbits, spin_limit, inject, flags, ev, ws, s, hist_in);
-        case 11: return run_sort_rb<11>(p, ck_in, rid_in, ck_out, rid_out, n, nbits, spin_limit, inject, flags, ev, ws, s, hist_in);
+        case 4: return run_sort_rb<4>(p, ck_in, rid_in, ck_out, rid_out, n, nbits, spin_limit, inject, flags, ev, ws, s, hist_in, gate);
+        case 5: return run_sort_rb<5>(p, ck_in, rid_in, ck_out, rid_out, n, nbits, spin_limit, inject, flags, ev, ws, s, hist_in, gate);
+        case 6: return run_sort_rb<6>(p, ck_in, rid_in, ck_out, rid_out, n, nbits, spin_limit, inject, flags, ev, ws, s, hist_in, gate);
+        case 7: return run_sort_rb<7>(p, ck_in, rid_in, ck_out, rid_out, n, nbits, spin_limit, inject, flags, ev, ws, s, hist_in, gate);
+        case 8: return run_sort_rb<8>(p, ck_in, rid_in, ck_out, rid_out, n, nbits, spin_limit, inject, flags, ev, ws, s, hist_in, gate);
+        case 9: return run_sort_rb<9>(p, ck_in, rid_in, ck_out, rid_out, n, nbits, spin_limit, inject, flags, ev, ws, s, hist_in, gate);
+        case 10: return run_sort_rb<10>(p, ck_in, rid_in, ck_out, rid_out, n, nbits, spin_limit, inject, flags, ev, ws, s, hist_in, gate);
+        case 11: return run_sort_rb<11>(p, ck_in, rid_in, ck_out, rid_out, n, nbits, spin_limit, inject, flags, ev, ws, s, hist_in, gate);
         default: return cudaErrorInvalidValue;
     }
 }

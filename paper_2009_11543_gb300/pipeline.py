@@ -76,8 +76,6 @@ class Rebuild:
         # learned: the sort is the learned-partition sort (same output bits)
         self.learned = learned
         self.learned_opts = learned_opts
-        self.learned_stats = None
-        self.learned_params = None
         self.hist = None                  # digit counts from the last extract (plain sort)
         dev = keys.device
         n = max(self.n, 1)
@@ -87,6 +85,8 @@ class Rebuild:
         wsb = ck.ck_sort_workspace_bytes(self.n, self.K, self.nbits, digit_bits)
         if learned:
             wsb = max(wsb, ck.ck_sort_learned_workspace_bytes(self.n, self.K, self.nbits, learned_opts))
+            self.stats_buf = ck.learned_stats_buffer(dev)
+            self.params_buf = torch.zeros(ck.CK_MLP_PARAMS, dtype=torch.float32, device=dev)
         self.ws = torch.empty(max(wsb, 256), dtype=torch.uint8, device=dev)
         self.shape = ck.ck_btree_plan(self.n, fanout, fill)
         self.tree = ck.alloc_btree(self.shape, self.K, dev)
@@ -107,9 +107,8 @@ class Rebuild:
 
     def sort(self, stream=None, pass_events=None):
         if self.learned:
-            st, self.learned_stats, self.learned_params = ck.ck_sort_learned(
-                self.ck_in, self.ck_sorted, self.rid_sorted, self.n, self.K, self.nbits, self.ws, self.learned_opts,
-                stream=stream)
+            ck.ck_sort_learned(self.ck_in, self.ck_sorted, self.rid_sorted, self.n, self.K, self.nbits, self.ws,
+                               self.learned_opts, stats=self.stats_buf, params=self.params_buf, stream=stream)
             return
         ck.ck_sort(self.ck_in, None, self.ck_sorted, self.rid_sorted, self.n, self.K, self.nbits, self.ws,
                    digit_bits=self.digit_bits, pass_events=pass_events, perm_only=self.perm_only, hist=self.hist,
@@ -123,13 +122,24 @@ class Rebuild:
             ck.ck_build_index(self.ck_sorted, self.rid_sorted, self.n, self.K, self.dmask, self.key_bits,
                               self.fanout, self.fill, arrays=self.tree, refined_out=self.refined, stream=stream)
 
+    @property
+    def learned_stats(self) -> dict:
+        """Statistics of the last learned sort (reads them back: synchronises)."""
+        return ck.learned_stats(self.stats_buf) if self.learned else None
+
+    @property
+    def learned_params(self):
+        """The model the last learned sort trained, as numpy float32 (synchronises)."""
+        no_model = self.learned_opts is not None and (self.learned_opts.flags & ck.CK_LEARNED_NO_MODEL)
+        return None if not self.learned or no_model else self.params_buf.cpu().numpy()
+
     def separators(self, stream=None):
         """Model-proposed inner separators of the built tree (learned mode):
         returns (proposals, hit count); the tree itself is not changed."""
-        if self.learned_params is None:
-            raise RuntimeError("no trained model: run a learned sort first")
-        params = torch.from_numpy(self.learned_params).to(self.keys.device)
-        prop, hits = ck.ck_model_separators(params, self.shape, self.tree, self.K, self.nbits, stream=stream)
+        if not self.learned:
+            raise RuntimeError("no trained model: not a learned rebuild")
+        prop, hits = ck.ck_model_separators(self.params_buf, self.shape, self.tree, self.K, self.nbits,
+                                            stream=stream)
         return prop, hits
 
     def partial_keys(self, vmask: np.ndarray, ref_key: np.ndarray, pk: int, stream=None):

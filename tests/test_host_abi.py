@@ -226,3 +226,34 @@ def test_argument_errors_of_later_entry_points(ckmod):
     assert lib.ck_encode_key(parts, 0, 10, 4096, 16, None) == ckmod.CK_EINVAL
     parts[0] = ckmod.ck_key_part(4096, None, ckmod.CK_KIND_DECIMAL, 10, 8)   # decimal of 10 bytes
     assert lib.ck_encode_key(parts, 1, 10, 8192, 16, None) == ckmod.CK_EINVAL
+
+
+def test_learned_sort_argument_errors(ckmod):
+    """The learned sort's binding marshals every argument (device stats and
+    parameter buffers included) and the call refuses bad arguments
+    synchronously, before any device work (the buffers below are host memory
+    that is never touched)."""
+    import torch
+    ck_in = torch.zeros((1, 256), dtype=torch.int32)
+    out = torch.zeros((1, 256), dtype=torch.int32)
+    rid = torch.zeros(256, dtype=torch.int32)
+    ws = torch.zeros(256, dtype=torch.uint8)
+    stats = torch.zeros(ckmod.CK_LEARNED_STATS_BYTES // 4, dtype=torch.int32)
+    params = torch.zeros(ckmod.CK_MLP_PARAMS, dtype=torch.float32)
+    bad = [dict(ck_words=0), dict(ck_words=9), dict(nbits=33), dict(opts=ckmod.learned_opts(bucket_bits=16)),
+           dict(opts=ckmod.learned_opts(flags=8)), dict(same=True)]
+    for b in bad:
+        kw = dict(ck_words=1, nbits=20, opts=None)
+        kw.update({k: v for k, v in b.items() if k != "same"})
+        src = out if b.get("same") else ck_in
+        with pytest.raises(ckmod.CkError) as e:
+            ckmod.ck_sort_learned(src, out, rid, 256, kw["ck_words"], kw["nbits"], ws, kw["opts"], stats=stats,
+                                  params=params, stream=0)
+        assert e.value.status == ckmod.CK_EINVAL, b
+    assert ckmod.ck_learned_stats.from_buffer_copy(bytes(ckmod.CK_LEARNED_STATS_BYTES)).fell_back == 0
+    assert ctypes_sizeof_stats(ckmod) == ckmod.CK_LEARNED_STATS_BYTES
+
+
+def ctypes_sizeof_stats(ckmod):
+    import ctypes
+    return ctypes.sizeof(ckmod.ck_learned_stats)
