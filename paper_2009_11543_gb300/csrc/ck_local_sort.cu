@@ -10,7 +10,11 @@
 //
 //  1. the block takes the 32-bit window of the composite key that ends at its
 //     highest varying bit, subtracts the bucket's smallest window value and
-//     shifts right until the values fit F bits (2^F >= m, at most 8192 bins):
+//     shifts right until the values fit F bits (2^F >= m, at most 8192 bins;
+//     when the window's top byte takes few values, as for keys over a small
+//     alphabet, the digit is instead the mixed-radix number of the dense codes
+//     of the values its two top bytes take, which keeps the order and fills
+//     far more bins):
 //     one counting pass (shared-memory atomics; the scatter order inside a bin
 //     does not matter, since the bin is then sorted by the composite key)
 //     places almost every pair, the keys of a bucket spanning a narrow key
@@ -51,7 +55,7 @@ constexpr uint32_t kLsMaxCap = kLsPerThread * kLsThreads;
 constexpr int kLsList = 1024;                        // pending ranges: disjoint, > 32 pairs each, so < cap / 33
 constexpr uint32_t kConstInline = 16384;             // constant buckets up to this size are checked inline
 constexpr uint32_t kConstChunk = 65536;              // chunk of the constant-bucket check
-constexpr size_t kLsStaticSmem = 2 * kLsList * 4 + 1536;
+constexpr size_t kLsStaticSmem = 2 * kLsList * 4 + 3584;
 constexpr size_t kSmemLimit = 227 * 1024;
 
 static_assert(kLsWarpBins == (1 << kLsWarpBinBits), "warp bins");
@@ -397,6 +401,8 @@ struct LsBlockState {
     uint32_t* orw;     // [KC]
     uint32_t* mm;      // [2]: window minimum, maximum
     uint32_t* wsum;    // [kLsWarps + 1]
+    uint32_t* bytes;   // [2][256]: counts, then dense codes, of the window's top two bytes
+    uint32_t* nbytes;  // [2]: values in use of each byte
 };
 
 // Step 1 on range A[p0, p0 + r) by the whole block.  ident: the range is the
@@ -437,40 +443,83 @@ __device__ void block_split(const LsView<KW>& v, uint32_t p0, uint32_t r, bool i
     const LsWin W((uint32_t)(P >= 31 ? P - 31 : 0), KC);
     uint32_t F = 32 - __clz(r - 1);  // 2^F >= r
     F = F < 8 ? 8u : (F > (uint32_t)kLsBinBits ? (uint32_t)kLsBinBits : F);
-    const uint32_t bins = 1u << F;
-    for (uint32_t d = tid; d < bins; d += kLsThreads) hist[d] = 0;
+    for (uint32_t d = tid; d < (uint32_t)kLsBins; d += kLsThreads) hist[d] = 0;
+    for (uint32_t d = tid; d < 512; d += kLsThreads) st.bytes[d] = 0;
     if (tid == 0) {
         st.mm[0] = 0xFFFFFFFFu;
         st.mm[1] = 0;
     }
-    {
+    __syncthreads();  // mm initialised, bins and byte counts zeroed
+    {  // window range, and which values the window's top two bytes take
         uint32_t lo = 0xFFFFFFFFu, hi = 0;
         for (uint32_t p = p0 + tid; p < pe; p += kLsThreads) {
             const uint32_t x = W(v, ident ? p : v.A[p]);
             lo = min(lo, x);
             hi = max(hi, x);
+            atomicAdd(&st.bytes[x >> 24], 1u);
+            atomicAdd(&st.bytes[256 + ((x >> 16) & 255u)], 1u);
         }
         lo = __reduce_min_sync(kFull, lo);
         hi = __reduce_max_sync(kFull, hi);
-        __syncthreads();  // mm initialised, bins zeroed
         if (lane == 0) {
             atomicMin(&st.mm[0], lo);
             atomicMax(&st.mm[1], hi);
         }
     }
     __syncthreads();
+    if (tid < 64) {  // dense codes of the values each byte takes (warp 0: top byte, warp 1: next)
+        uint32_t* tb = st.bytes + 256 * (tid >> 5);
+        uint32_t f[8], c = 0;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            f[i] = tb[lane * 8 + i] ? 1u : 0u;
+            c += f[i];
+        }
+        uint32_t inc = c;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t t = __shfl_up_sync(kFull, inc, o);
+            if (lane >= (uint32_t)o) inc += t;
+        }
+        uint32_t run = inc - c;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            tb[lane * 8 + i] = run;
+            run += f[i];
+        }
+        if (lane == 31) st.nbytes[tid >> 5] = inc;
+    }
+    __syncthreads();
+    // The digit: the window's top bits after subtracting its minimum (2^F
+    // bins), unless the top byte is sparse (at most 128 of its values occur,
+    // as for keys over a small alphabet whose codes use few bit patterns) and
+    // the two top bytes' values in use give 1024 .. kLsBins combinations:
+    // then the mixed-radix number of their dense codes, which keeps the order
+    // of the windows and spreads the pairs over far more bins.
+    const uint32_t n1 = st.nbytes[0], n2 = st.nbytes[1];
+    const bool dense = n1 <= 128 && n1 * n2 <= (uint32_t)kLsBins && n1 * n2 >= 1024;
+    uint32_t bins = 1u << F;
+    if (dense) {
+        bins = 256;
+        while (bins < n1 * n2) bins <<= 1;
+    }
     const uint32_t wmin = st.mm[0];
     const uint32_t bl = 32 - __clz(st.mm[1] - wmin);
     const uint32_t sh = bl > F ? bl - F : 0u;
-    for (uint32_t p = p0 + tid; p < pe; p += kLsThreads) atomicAdd(&hist[(W(v, ident ? p : v.A[p]) - wmin) >> sh], 1u);
+    const uint32_t* c1 = st.bytes;
+    const uint32_t* c2 = st.bytes + 256;
+    auto digit = [&](uint32_t x) -> uint32_t {
+        return dense ? c1[x >> 24] * n2 + c2[(x >> 16) & 255u] : (x - wmin) >> sh;
+    };
+    for (uint32_t p = p0 + tid; p < pe; p += kLsThreads) atomicAdd(&hist[digit(W(v, ident ? p : v.A[p]))], 1u);
     __syncthreads();
     bins_exclusive_scan(hist, bins, st.wsum);
     if (ident) {
-        for (uint32_t p = tid; p < r; p += kLsThreads) v.A[atomicAdd(&hist[(W(v, p) - wmin) >> sh], 1u)] = (uint16_t)p;
+        for (uint32_t p = tid; p < r; p += kLsThreads) v.A[atomicAdd(&hist[digit(W(v, p))], 1u)] = (uint16_t)p;
     } else {
         for (uint32_t p = p0 + tid; p < pe; p += kLsThreads) {
             const uint32_t e = v.A[p];
-            v.T[p0 + atomicAdd(&hist[(W(v, e) - wmin) >> sh], 1u)] = (uint16_t)e;
+            v.T[p0 + atomicAdd(&hist[digit(W(v, e))], 1u)] = (uint16_t)e;
         }
         __syncthreads();
         for (uint32_t p = p0 + tid; p < pe; p += kLsThreads) v.A[p] = v.T[p];
@@ -862,6 +911,7 @@ __global__ void __launch_bounds__(kLsThreads, 1) local_sort_kernel(const LocalSo
     __shared__ uint32_t s_or[kMaxLearnedWords + 1];
     __shared__ uint32_t s_mm[2], s_bucket, s_cnt[2], s_grab, s_bcnt, s_bad;
     __shared__ uint32_t s_bstack[kLsBlockStack];
+    __shared__ uint32_t s_bytes[512], s_nbytes[2];
     __shared__ uint32_t s_scan[kLsWarps + 1];
     const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     constexpr uint32_t K = KW, KC = KW + 1;
@@ -884,6 +934,8 @@ __global__ void __launch_bounds__(kLsThreads, 1) local_sort_kernel(const LocalSo
     bst.orw = s_or;
     bst.mm = s_mm;
     bst.wsum = s_scan;
+    bst.bytes = s_bytes;
+    bst.nbytes = s_nbytes;
     uint64_t my_hash = 0;
     uint32_t my_bad = 0;
     for (;;) {
