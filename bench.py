@@ -1,15 +1,23 @@
 """Benchmark: keys/s sorted + indexed on one GB300, compressed key sort vs a
 full-key sort on the same kernels, with the HBM roofline fraction of the
-dominant kernel (the onesweep radix pass).
+dominant kernel (the onesweep radix pass of the plain path; the partition
+passes or the bucket sorts of the learned path).
 
 A step is one index rebuild from stored DS-metadata (Sec. 5 of the paper):
-extract the compressed keys with the stored D-bitmap, radix-sort the
-(compressed key, row id) pairs, bulk-load the tree and recompute the D-bitmap.
-Inputs are resident in HBM when the timed region starts and are larger than
-L2 (no flush needed).
+extract the compressed keys with the stored D-bitmap, sort the (compressed
+key, row id) pairs, bulk-load the tree and recompute the D-bitmap.  Inputs
+are resident in HBM when the timed region starts; they are larger than L2,
+except the 1M-key configuration, between whose timed steps a 256 MiB buffer
+is written (outside the timed events).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--workload urls64m|int1m|dna200m]
+                    [--workload all|urls64m|int1m|zipf256m|dna200m|table16m|zipfsweep|...]
+
+The default (all) measures the five benchmark configurations in one line:
+the headline is the largest single-GPU one, 200M DNA keys through the
+learned partition with the fanout-256 bulk load (config C5); 1M uint64 keys
+(C1), 64M URL keys (C2), the 16M-row table of six indexes (C3) and 256M Zipf
+keys (C4) are sub-records, each with the plain, learned and full-key times.
 
 Under torchrun (N > 1) every rank rebuilds its own replica of the workload
 (the path has no exchange step); value is the keys of all ranks over the
@@ -176,7 +184,7 @@ class ClockSampler:
 
 
 # --------------------------------------------------------------------- ours
-def run_table(args, rank, world, local_rank):
+def run_table(args, rank, world, local_rank, own_clocks=True):
     """The batched workload: every index of one table per step, one graph launch."""
     import torch
     import synth
@@ -222,8 +230,9 @@ def run_table(args, rank, world, local_rank):
         return e0.elapsed_time(e1) / steps, ck.ck_launch_count() - l0
 
     clocks = ClockSampler(local_rank)
-    clocks.start()
-    time.sleep(0.2)
+    if own_clocks:
+        clocks.start()
+        time.sleep(0.2)
     B.capture()
     graph_ms, graph_launches = timed(B.launch, args.steps, args.warmup)
     streams_ms, stream_launches = timed(B.run, args.steps, args.warmup)
@@ -246,7 +255,7 @@ def run_table(args, rank, world, local_rank):
         for r, h in zip(B.parts, rid_hosts):
             h.copy_(r.rid_sorted[:n], non_blocking=True)
     e2e_ms, _ = timed(e2e_step, args.steps, args.warmup)
-    clk = clocks.stop()
+    clk = clocks.stop() if own_clocks else None
     status, detail = ck.ck_device_status()
     if status != ck.CK_OK:
         raise RuntimeError("device status %s (detail %d)" % (ck.ck_status_string(status), detail))
@@ -388,21 +397,42 @@ def run_zipf_sweep(args, rank, world, local_rank):
     }
 
 
-def run_ours(args, rank, world, local_rank):
+LEARNED_PHASE_NAMES = ("sample_model_boundaries", "bucket_ids", "partition", "bucket_sorts_checks", "verdict_fallback")
+
+
+def learned_phase_bytes(n: int, ck_words: int) -> dict:
+    """Algorithmic bytes of the learned sort's two main phases: the partition
+    (two radix passes: the first reads the bucket id and the key words and
+    writes them with the row id, the second reads all three and writes the key
+    words and the row id) and the bucket sorts (every pair read and written
+    once)."""
+    K = ck_words
+    return {"partition": n * ((4 + 4 * K) + (4 + 4 * K + 4)) + n * ((4 + 4 * K + 4) + (4 * K + 4)),
+            "bucket_sorts_checks": n * 2 * (4 * K + 4)}
+
+
+def measure_config(args, workload, world, local_rank, headline=False, extras=False):
+    """Times one rebuild configuration: the plain compressed-key path, the
+    learned path and the full-key baseline (device-resident keys, CUDA events
+    per step on the launching stream), plus end-to-end host transfers for the
+    headline workload.  Returns (record, dmask) on every rank after the
+    max over ranks."""
     import torch
-    from paper_2009_11543_gb300 import build as b
-    b.build()
     from paper_2009_11543_gb300 import ck, metrics, pipeline
 
-    torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
-    desc, n, kind, fanout, cpu_rows, main_path = WORKLOADS[args.workload]
-    m_ins = min(1 << 20, n // 16)          # an insert batch: the generator's next rows
+    desc, n, kind, fanout, cpu_rows, main_path = WORKLOADS[workload]
+    m_ins = min(1 << 20, n // 16) if extras else 0
     all_np = gen_keys(kind, n + m_ins)
     keys_np, ins_np = all_np[:n], all_np[n:]
-    keys_host = torch.from_numpy(keys_np.view(np.int64) if keys_np.dtype == np.uint64 else keys_np).pin_memory()
-    keys = keys_host.to(dev)
+    del all_np
     key_bytes = keys_np.shape[1] if keys_np.ndim == 2 else keys_np.dtype.itemsize
+    keys_host = torch.from_numpy(keys_np.view(np.int64) if keys_np.dtype == np.uint64 else keys_np)
+    if headline:
+        keys_host = keys_host.pin_memory()
+    keys = keys_host.to(dev)
+    fits_l2 = n * key_bytes < 64 * 2**20
+    flush_buf = torch.empty(256 * 2**20, dtype=torch.uint8, device=dev) if fits_l2 else None
 
     # stored DS-metadata: the D-bitmap of a first build (untimed set-up)
     dmask = pipeline.first_build_dmask(keys, digit_bits=args.digit_bits)
@@ -410,7 +440,6 @@ def run_ours(args, rank, world, local_rank):
     R = pipeline.Rebuild(keys, dmask, fanout=fanout, digit_bits=args.digit_bits)
     F = pipeline.Rebuild(keys, pipeline.full_key_mask(8 * key_bytes), fanout=fanout, digit_bits=args.digit_bits)
     L = pipeline.Rebuild(keys, dmask, fanout=fanout, digit_bits=args.digit_bits, learned=True) if R.K <= 8 else None
-    V = L if (main_path == "learned" and L is not None) else R
     passes = metrics.radix_passes(nbits, args.digit_bits)
     fpasses = metrics.radix_passes(8 * key_bytes, args.digit_bits)
     stream = torch.cuda.current_stream()
@@ -421,89 +450,213 @@ def run_ours(args, rank, world, local_rank):
             import torch.distributed as dist
             dist.barrier()
 
-    def timed(fn, steps, warmup, pass_count):
+    def flush():
+        if flush_buf is not None:
+            flush_buf.zero_()
+
+    def timed(r, steps, warmup, n_ev):
+        """Per-step events around extract / sort / build (an L2 flush between
+        steps, outside the events, when the keys fit in L2); n_ev events
+        around the sort's passes or phases."""
         for _ in range(warmup):
-            fn(None)
+            r.run()
         barrier()
-        ev = [[torch.cuda.Event(enable_timing=True) for _ in range(pass_count + 1)] for _ in range(steps)]
-        for row in ev:                   # torch creates an event on its first record
+        ev = [[torch.cuda.Event(enable_timing=True) for _ in range(n_ev)] for _ in range(steps)]
+        ph = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(steps)]
+        for row in ev + ph:                    # torch creates an event on its first record
             for e in row:
                 e.record(stream)
-        ph = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(steps)]
+        barrier()
         l0 = ck.ck_launch_count()
-        start = torch.cuda.Event(enable_timing=True)
-        end = torch.cuda.Event(enable_timing=True)
-        start.record(stream)
         for s in range(steps):
-            fn((ph[s], ck.event_handles(ev[s])))
-        end.record(stream)
+            flush()
+            ph[s][0].record(stream)
+            r.extract()
+            ph[s][1].record(stream)
+            r.sort(pass_events=ck.event_handles(ev[s]) if n_ev else None)
+            ph[s][2].record(stream)
+            r.build()
+            ph[s][3].record(stream)
         barrier()
         launches = ck.ck_launch_count() - l0
-        total_ms = start.elapsed_time(end)
-        pass_ms = [[ev[s][q].elapsed_time(ev[s][q + 1]) for q in range(pass_count)] for s in range(steps)]
-        if pass_count == 0:
-            pass_ms = [[0.0] for _ in range(steps)]
-        phase = [[ph[s][i].elapsed_time(ph[s][i + 1]) for i in range(3)] for s in range(steps)]
-        return total_ms, pass_ms, phase, launches
+        phase = np.array([[ph[s][i].elapsed_time(ph[s][i + 1]) for i in range(3)] for s in range(steps)])
+        evt = np.array([[ev[s][q].elapsed_time(ev[s][q + 1]) for q in range(n_ev - 1)] for s in range(steps)]) \
+            if n_ev > 1 else np.zeros((steps, 1))
+        return float(phase.sum(axis=1).mean()), phase.mean(axis=0), evt.mean(axis=0), launches / steps
 
-    def step_fn(r):
-        def fn(hooks):
-            if hooks is None:
-                r.run()
-                return
-            ph, evh = hooks
-            ph[0].record(stream)
-            r.extract()
-            ph[1].record(stream)
-            r.sort(pass_events=None if r.learned else evh)
-            ph[2].record(stream)
-            r.build()
-            ph[3].record(stream)
-        return fn
-
-    clocks = ClockSampler(local_rank)
-    clocks.start()
-    time.sleep(0.2)
-    total_ms, pass_ms, phase, launches = timed(step_fn(R), args.steps, args.warmup, passes)
-    f_total_ms, f_pass_ms, f_phase, _ = timed(step_fn(F), max(1, args.steps // 2), args.warmup, fpasses)
-    l_total_ms, l_phase, l_launches = None, None, 0
+    p_ms, p_ph, p_pass, p_launch = timed(R, args.steps, args.warmup, passes + 1 if passes else 0)
+    f_ms, f_ph, f_pass, _ = timed(F, max(1, args.steps // 2), args.warmup, fpasses + 1)
+    l_ms = l_ph = l_phase = None
+    l_launch = 0
     if L is not None:
-        l_total_ms, _, l_phase, l_launches = timed(step_fn(L), args.steps, args.warmup, 0)
+        l_ms, l_ph, l_phase, l_launch = timed(L, args.steps, args.warmup, ck.CK_LEARNED_PHASES + 1)
+    headline_learned = main_path == "learned" and L is not None
+    v_ms = l_ms if headline_learned else p_ms
 
-    # end to end: every step copies its keys host -> device, rebuilds, and
-    # copies the sorted row ids device -> host; the copies of steps i + 1 and
-    # i - 1 overlap the rebuild of step i (two buffer slots, two copy streams)
-    rid_hosts = [torch.empty(n, dtype=torch.int32, pin_memory=True) for _ in range(2)]
-    O = pipeline.OverlappedRebuild(keys.shape, keys.dtype, dmask, dev, fanout=fanout, digit_bits=args.digit_bits,
-                                   learned=V is L)
-    for i in range(args.warmup):
-        O.submit(keys_host, rid_hosts[i % 2], stream)
-    O.finish(stream)
-    barrier()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    O.begin(stream)
-    for i in range(args.steps):
-        O.submit(keys_host, rid_hosts[i % 2], stream)
-    O.finish(stream)
-    e1.record(stream)
-    barrier()
-    e2e_ms = e0.elapsed_time(e1)
-    e2e_ok = bool(np.array_equal(rid_hosts[(args.steps - 1) % 2].numpy(), ck.u32(V.rid_sorted)[:n].view(np.int32)))
-    del O
-    # the host link's own rate for context: one copy of the keys in, alone
-    h2d_ms = []
-    for _ in range(3):
-        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a0.record(stream)
-        keys.copy_(keys_host, non_blocking=True)
-        a1.record(stream)
-        a1.synchronize()
-        h2d_ms.append(a0.elapsed_time(a1))
-    h2d_gbs = keys_np.nbytes / (min(h2d_ms) / 1e3) / 1e9
+    rec = {"workload": desc, "n": n, "key_bytes": key_bytes, "distinction_bits": nbits, "ck_words": R.K,
+           "digit_bits": args.digit_bits, "radix_passes": passes, "fanout": fanout,
+           "tree_levels": int(R.shape.levels),
+           "l2": ("keys fit in L2: a 256 MiB buffer is written between timed steps (outside the timed events)"
+                  if fits_l2 else "inputs larger than L2 (no flush)"),
+           "path": "learned" if headline_learned else "plain",
+           "ms_per_step": v_ms, "value": world * n / (v_ms / 1e3), "unit": "keys/s",
+           "plain": {"ms_per_step": p_ms, "value": world * n / (p_ms / 1e3),
+                     "phases_ms": dict(zip(("extract", "sort", "build"), map(float, p_ph))),
+                     "launches_per_step": p_launch},
+           "full_key": {"ms_per_step": f_ms, "value": world * n / (f_ms / 1e3), "radix_passes": fpasses,
+                        "ck_words": F.K, "phases_ms": dict(zip(("extract", "sort", "build"), map(float, f_ph)))},
+           "compressed_vs_full_speedup": f_ms / v_ms,
+           "plain_vs_full_speedup": f_ms / p_ms,
+           "compression_ratio": metrics.compression_ratio(8 * key_bytes, nbits) if nbits else None}
+    peak, peak_src = peaks()
+    # roofline of the plain path's dominant kernel: the radix pass
+    sort_bytes = passes * metrics.pass_bytes(n, R.K)
+    pass_ms = float(np.sum(p_pass)) if passes else 0.0
+    alg = n * key_bytes + sort_bytes   # W read once per key, 2 (c + 4) per pass (extraction's write not counted)
+    plain_roof = None
+    if passes:
+        avg_pass = pass_ms / passes
+        plain_roof = {"bound": "hbm", "kernel": "onesweep_pass_kernel<%d, %d>" % (
+                          args.digit_bits, 256 if R.K + 1 >= 3 or n > (1 << 22) else 512),
+                      "achieved": sort_bytes / (pass_ms / 1e3) / 1e9, "peak": peak, "peak_source": peak_src,
+                      "unit": "GB/s", "frac": sort_bytes / (pass_ms / 1e3) / 1e9 / peak,
+                      "traffic": ncu_traffic(n, R.K), "alg_bytes_per_launch": sort_bytes / passes,
+                      "avg_launch_ms": avg_pass, "launches_per_step": passes}
+        rec["plain"]["extract_sort_roofline_frac"] = alg / ((p_ph[0] + p_ph[1]) / 1e3) / 1e9 / peak
+        rec["plain"]["extract_sort_alg_bytes"] = alg
+    rec["plain"]["roofline"] = plain_roof
+    if L is not None:
+        st = L.learned_stats
+        phases = dict(zip(LEARNED_PHASE_NAMES, map(float, l_phase)))
+        pb = learned_phase_bytes(n, R.K)
+        dom = max(("partition", "bucket_sorts_checks"), key=lambda k: phases[k])
+        kern = {"partition": "onesweep_pass_kernel<8, 256> (2 launches, bucket-id digits)",
+                "bucket_sorts_checks": "local_sort_kernel<%d> + const_check_kernel" % R.K}[dom]
+        ach = pb[dom] / (phases[dom] / 1e3) / 1e9
+        rec["learned"] = {"ms_per_step": l_ms, "value": world * n / (l_ms / 1e3),
+                          "phases_ms": dict(zip(("extract", "sort", "build"), map(float, l_ph))),
+                          "sort_phases_ms": phases, "stats": st, "speedup_vs_plain": p_ms / l_ms,
+                          "launches_per_step": l_launch,
+                          "roofline": {"bound": "hbm", "kernel": kern, "achieved": ach, "peak": peak,
+                                       "peak_source": peak_src, "unit": "GB/s", "frac": ach / peak,
+                                       "traffic": None, "alg_bytes_per_launch": pb[dom],
+                                       "avg_launch_ms": phases[dom],
+                                       "phase_alg_bytes": pb}}
+    rec["roofline"] = rec["learned"]["roofline"] if headline_learned else plain_roof
+    rec["gpu_launches_per_step"] = l_launch if headline_learned else p_launch
+    V = L if headline_learned else R
 
-    # DS-metadata maintenance (Sec. 4.3): a batch of inserts into the index
+    if headline:
+        # end to end: every step copies its keys host -> device, rebuilds, and
+        # copies the sorted row ids device -> host; the copies of steps i + 1
+        # and i - 1 overlap the rebuild of step i (two buffer slots, two copy streams)
+        del R, F
+        torch.cuda.empty_cache()
+        rid_hosts = [torch.empty(n, dtype=torch.int32, pin_memory=True) for _ in range(2)]
+        O = pipeline.OverlappedRebuild(keys.shape, keys.dtype, dmask, dev, fanout=fanout, digit_bits=args.digit_bits,
+                                       learned=headline_learned)
+        for i in range(args.warmup):
+            O.submit(keys_host, rid_hosts[i % 2], stream)
+        O.finish(stream)
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        O.begin(stream)
+        for i in range(args.steps):
+            O.submit(keys_host, rid_hosts[i % 2], stream)
+        O.finish(stream)
+        e1.record(stream)
+        barrier()
+        e2e_ms = e0.elapsed_time(e1) / args.steps
+        e2e_ok = bool(np.array_equal(rid_hosts[(args.steps - 1) % 2].numpy(), ck.u32(V.rid_sorted)[:n].view(np.int32)))
+        del O
+        torch.cuda.empty_cache()
+        h2d_ms = []
+        for _ in range(3):
+            a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a0.record(stream)
+            keys.copy_(keys_host, non_blocking=True)
+            a1.record(stream)
+            a1.synchronize()
+            h2d_ms.append(a0.elapsed_time(a1))
+        rec["e2e"] = {"value": world * n / (e2e_ms / 1e3), "unit": "keys/s", "ms_per_step": e2e_ms,
+                      "h2d_bytes_per_step": int(keys_np.nbytes), "d2h_bytes_per_step": 4 * n,
+                      "overlap": "pipeline.OverlappedRebuild: the copies of steps i + 1 and i - 1 run beside the "
+                                 "rebuild of step i; the timed region spans the first copy in to the last copy out",
+                      "last_result_matches_device_run": e2e_ok,
+                      "h2d_copy_gbs_alone": keys_np.nbytes / (min(h2d_ms) / 1e3) / 1e9}
+        if headline_learned:
+            # model-proposed inner separators (verified, the tree keeps the
+            # canonical ones), and the whole learned rebuild as one CUDA graph
+            seps_ms = []
+            for it in range(args.warmup + args.steps):
+                a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a0.record(stream)
+                prop, hits = L.separators()
+                a1.record(stream)
+                a1.synchronize()
+                if it >= args.warmup:
+                    seps_ms.append(a0.elapsed_time(a1))
+            ni = int(L.shape.inner_entries)
+            rec["learned"]["separators"] = {"inner_entries": ni, "model_hits": int(hits.cpu()[0]),
+                                            "hit_rate": int(hits.cpu()[0]) / max(1, ni),
+                                            "ms": float(np.median(seps_ms)),
+                                            "note": "model proposal of each inner separator's top 24 bits, "
+                                                    "checked against the canonical separator (the tree always "
+                                                    "keeps the canonical key); timed on the side, not in the step"}
+            g = torch.cuda.CUDAGraph()
+            side = torch.cuda.Stream(dev)
+            side.wait_stream(stream)
+            with torch.cuda.stream(side):
+                L.run()
+            stream.wait_stream(side)
+            barrier()
+            with torch.cuda.graph(g):
+                L.run()
+            for _ in range(args.warmup):
+                g.replay()
+            barrier()
+            a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a0.record(stream)
+            for _ in range(args.steps):
+                g.replay()
+            a1.record(stream)
+            barrier()
+            rec["learned"]["graph_ms_per_step"] = a0.elapsed_time(a1) / args.steps
+            rec["learned"]["graph_note"] = ("extract -> learned sort -> bulk load captured as one CUDA graph "
+                                            "(the learned sort decides on the device) and replayed")
+            del g
+    if extras:
+        rec.update(measure_extras(args, keys, ins_np, dmask, V if not headline_learned else pipeline.Rebuild(
+            keys, dmask, fanout=fanout, digit_bits=args.digit_bits), n, key_bytes, m_ins, world, stream))
+    status, detail = ck.ck_device_status()
+    if status != ck.CK_OK:
+        raise RuntimeError("device status %s (detail %d)" % (ck.ck_status_string(status), detail))
+    # max over ranks of every timing that feeds a value
+    t = max_over_ranks([rec["ms_per_step"], rec["plain"]["ms_per_step"], rec["full_key"]["ms_per_step"],
+                        rec["learned"]["ms_per_step"] if "learned" in rec else 0.0,
+                        rec["e2e"]["ms_per_step"] if "e2e" in rec else 0.0], world)
+    rec["ms_per_step"], rec["plain"]["ms_per_step"], rec["full_key"]["ms_per_step"] = (float(x) for x in t[:3])
+    rec["value"] = world * n / (rec["ms_per_step"] / 1e3)
+    rec["plain"]["value"] = world * n / (rec["plain"]["ms_per_step"] / 1e3)
+    rec["full_key"]["value"] = world * n / (rec["full_key"]["ms_per_step"] / 1e3)
+    if "learned" in rec:
+        rec["learned"]["ms_per_step"] = float(t[3])
+        rec["learned"]["value"] = world * n / (float(t[3]) / 1e3)
+    if "e2e" in rec:
+        rec["e2e"]["ms_per_step"] = float(t[4])
+        rec["e2e"]["value"] = world * n / (float(t[4]) / 1e3)
+    rec["data"] = DATA_NOTE.get(kind, "synthetic")
+    return rec, dmask
+
+
+def measure_extras(args, keys, ins_np, dmask, R, n, key_bytes, m_ins, world, stream):
+    """DS-metadata maintenance (Sec. 4.3), the first build's bitmaps, partial
+    keys (Sec. 4.2) and lower-bound search (Sec. 4.3) on the rebuilt index."""
+    import torch
+    from paper_2009_11543_gb300 import ck
+    dev = keys.device
+    R.run()
     ins = torch.from_numpy(ins_np.view(np.int64) if ins_np.dtype == np.uint64 else ins_np).to(dev)
     ins_d = torch.from_numpy(np.ascontiguousarray(R.dmask).view(np.int64)).to(dev)
     ins_v = ck.ck_variant_bits(keys, 0)
@@ -511,8 +664,7 @@ def run_ours(args, rank, world, local_rank):
                          device=dev)
     ins_ms = []
     for it in range(args.warmup + args.steps):
-        a0 = torch.cuda.Event(enable_timing=True)
-        a1 = torch.cuda.Event(enable_timing=True)
+        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a0.record(stream)
         ck.ck_insert_batch(keys, R.rid_sorted[:n], ins, 0, ins_d, ins_v, ws=ins_ws)
         a1.record(stream)
@@ -520,9 +672,6 @@ def run_ours(args, rank, world, local_rank):
         if it >= args.warmup:
             ins_ms.append(a0.elapsed_time(a1))
     ins_ms = float(np.median(ins_ms))
-
-    # the D-bitmap from the sorted order (Theorem 1) and the variant bitmap
-    # (Sec. 4.2), the first build's inputs, timed on their own
     dm_out = torch.empty(ck.mask_words(8 * key_bytes), dtype=torch.int64, device=dev)
     vm_out = torch.empty_like(dm_out)
     db_ms, vb_ms = [], []
@@ -539,16 +688,11 @@ def run_ours(args, rank, world, local_rank):
             vb_ms.append(a1.elapsed_time(a2))
     db_ms, vb_ms = float(np.median(db_ms)), float(np.median(vb_ms))
     dmask_ok = bool(np.array_equal(ck.mask_to_host(dm_out), R.dmask))
-
-    # partial keys (Sec. 4.2) and lower-bound search (Sec. 4.3) on the index
-    # the timed rebuilds left in R: queries are indexed keys and the insert
-    # batch's rows (not in the index)
     pk_bits = 16
     R.run()
     sv = ck.mask_to_host(ck.ck_variant_bits(keys, 0))
     sref = ck.reference_key(keys, 0)
-    m_hit = 3 * m_ins
-    qidx = torch.from_numpy(np.random.default_rng(9).integers(0, n, m_hit)).to(dev)
+    qidx = torch.from_numpy(np.random.default_rng(9).integers(0, n, 3 * m_ins)).to(dev)
     queries = torch.cat([keys[qidx], ins])
     m_q = int(queries.shape[0])
     spos = torch.empty(m_q, dtype=torch.int32, device=dev)
@@ -576,93 +720,9 @@ def run_ours(args, rank, world, local_rank):
             se_ms.append(a1.elapsed_time(a2))
             sf_ms.append(a2.elapsed_time(a3))
     pk_ms, se_ms, sf_ms = float(np.median(pk_ms)), float(np.median(se_ms)), float(np.median(sf_ms))
-    clk = clocks.stop()
-    status, detail = ck.ck_device_status()
-    if status != ck.CK_OK:
-        raise RuntimeError("device status %s (detail %d)" % (ck.ck_status_string(status), detail))
-
-    # max over ranks
-    times = max_over_ranks([total_ms, e2e_ms, f_total_ms, l_total_ms or 0.0], world)
-    total_ms, e2e_ms, f_total_ms = (float(x) for x in times[:3])
-    if L is not None:
-        l_total_ms = float(times[3])
-    if rank != 0:
-        return None
-
-    ms_step = total_ms / args.steps
-    f_ms_step = f_total_ms / max(1, args.steps // 2)
-    l_ms_step = l_total_ms / args.steps if L is not None else None
-    v_ms_step = l_ms_step if V is L else ms_step
-    value = world * n / (v_ms_step / 1e3)
-    peak, peak_src = peaks()
-    # achieved = all passes' algorithmic bytes / all passes' time
-    sort_bytes = passes * metrics.pass_bytes(n, R.K)
-    pass_total_ms = float(np.mean([sum(p) for p in pass_ms]))
-    avg_pass_ms = pass_total_ms / passes
-    pb = sort_bytes / passes
-    achieved = sort_bytes / (pass_total_ms / 1e3) / 1e9
-    traffic = ncu_traffic(n, R.K)
-    ph = np.mean(np.array(phase), axis=0)
-    fph = np.mean(np.array(f_phase), axis=0)
-    alg = metrics.extract_bytes(n, key_bytes, R.K) + sort_bytes
-    f_sort_bytes = fpasses * metrics.pass_bytes(n, F.K)
-    f_alg = metrics.extract_bytes(n, key_bytes, F.K) + f_sort_bytes
-    f_pass_gbs = f_sort_bytes / (float(np.mean([sum(p) for p in f_pass_ms])) / 1e3) / 1e9
-    line = {
-        "metric": METRIC,
-        "value": value,
-        "unit": "keys/s",
-        "n_gpus": world,
-        "steps": args.steps,
-        "warmup": args.warmup,
-        "ms_per_step": v_ms_step,
-        "higher_is_better": True,
-        "scaling": "weak",
-        "vs_baseline": None,
-        "dtype": "u32",
-        "data": DATA_NOTE.get(kind, "synthetic"),
-        "config": {"workload": desc, "n": n, "key_bytes": key_bytes, "distinction_bits": nbits,
-                   "ck_words": R.K, "digit_bits": args.digit_bits, "radix_passes": passes, "fanout": fanout,
-                   "tree_levels": int(R.shape.levels), "l2": "inputs larger than L2 (no flush)",
-                   "parallelism": "replicas" if world > 1 else "single GPU"},
-        "roofline": {"bound": "hbm", "kernel": "onesweep_pass_kernel<%d, %d>" % (args.digit_bits, 256 if R.K + 1 >= 3 or n > (1 << 22) else 512),
-                     "achieved": achieved,
-                     "peak": peak, "peak_source": peak_src, "unit": "GB/s", "frac": achieved / peak,
-                     "traffic": traffic, "alg_bytes_per_launch": pb, "avg_launch_ms": avg_pass_ms},
-        "phases_ms": {"extract": float(ph[0]), "sort": float(ph[1]), "build": float(ph[2])},
-        "spec_hbm_gbs": SPEC_HBM_GBS,
-        "build_roofline": {"alg_bytes": metrics.build_bytes(n, R.K),
-                           "achieved_gbs": metrics.build_bytes(n, R.K) / (float(ph[2]) / 1e3) / 1e9,
-                           "frac": metrics.build_bytes(n, R.K) / (float(ph[2]) / 1e3) / 1e9 / peak,
-                           "note": "leaves: sorted (ck, rid) read, rid + D-bit written per key; inner levels "
-                                   "(n / f entries) not counted"},
-        "extract_sort_roofline_frac": alg / ((ph[0] + ph[1]) / 1e3) / 1e9 / peak,
-        "extract_sort": {"value": world * n / ((ph[0] + ph[1]) / 1e3), "unit": "keys/s",
-                         "ms_per_step": float(ph[0] + ph[1])},
-        "full_key": {"value": world * n / (f_ms_step / 1e3), "unit": "keys/s", "ms_per_step": f_ms_step,
-                     "radix_passes": fpasses, "ck_words": F.K,
-                     "phases_ms": {"extract": float(fph[0]), "sort": float(fph[1]), "build": float(fph[2])},
-                     "pass_gbs": f_pass_gbs, "extract_sort_roofline_frac":
-                         f_alg / ((fph[0] + fph[1]) / 1e3) / 1e9 / peak},
-        "compressed_vs_full_speedup": f_ms_step / v_ms_step,
-        "compression_ratio": metrics.compression_ratio(8 * key_bytes, nbits) if nbits else None,
-        "e2e": {"value": world * n / (e2e_ms / args.steps / 1e3), "unit": "keys/s", "ms_per_step": e2e_ms / args.steps,
-                "h2d_bytes_per_step": int(keys_np.nbytes), "d2h_bytes_per_step": 4 * n,
-                "overlap": "pipeline.OverlappedRebuild: the copies of steps i + 1 and i - 1 run beside the rebuild "
-                           "of step i; the timed region spans the first copy in to the last copy out",
-                "last_result_matches_device_run": e2e_ok, "h2d_copy_gbs_alone": h2d_gbs},
-        "path": "learned" if V is L else "plain",
-        "plain": {"value": world * n / (ms_step / 1e3), "unit": "keys/s", "ms_per_step": ms_step,
-                  "phases_ms": {"extract": float(ph[0]), "sort": float(ph[1]), "build": float(ph[2])}},
-        "learned": None if L is None else {
-            "value": world * n / (l_ms_step / 1e3), "unit": "keys/s", "ms_per_step": l_ms_step,
-            "phases_ms": dict(zip(("extract", "sort", "build"), (float(x) for x in np.mean(np.array(l_phase), 0)))),
-            "stats": L.learned_stats, "speedup_vs_plain": ms_step / l_ms_step},
-        "gpu_launches": int(l_launches if V is L else launches),
-        "clocks": clk,
+    return {
         "dmask": {"distinction_bits_ms": db_ms, "distinction_bits_keys_per_s": world * n / (db_ms / 1e3),
-                  "variant_bits_ms": vb_ms,
-                  "variant_bits_gbs": n * key_bytes / (vb_ms / 1e3) / 1e9,
+                  "variant_bits_ms": vb_ms, "variant_bits_gbs": n * key_bytes / (vb_ms / 1e3) / 1e9,
                   "matches_stored_dmask": dmask_ok,
                   "note": "D-bitmap from adjacent keys in sorted order (rows gathered through the permutation), "
                           "variant bitmap (one read of the keys), medians"},
@@ -671,15 +731,98 @@ def run_ours(args, rank, world, local_rank):
         "search": {"value": world * m_q / (se_ms / 1e3), "unit": "lookups/s", "ms": se_ms, "queries": m_q,
                    "hits_frac": hits_frac, "full_keys_read_in_leaf_per_query": derefs_mean, "pk_bits": pk_bits,
                    "inner_nodes": "full keys, binary search (Sec. 4.3)",
-                   "partial_key_inner_nodes": {"value": world * m_q / (sf_ms / 1e3), "unit": "lookups/s", "ms": sf_ms,
-                                               "full_keys_read_per_query": derefs_mean_p},
-                   "partial_keys_ms": pk_ms, "partial_keys_per_s": world * (n + int(R.shape.inner_entries)) / (pk_ms / 1e3),
+                   "partial_key_inner_nodes": {"value": world * m_q / (sf_ms / 1e3), "unit": "lookups/s",
+                                               "ms": sf_ms, "full_keys_read_per_query": derefs_mean_p},
+                   "partial_keys_ms": pk_ms,
+                   "partial_keys_per_s": world * (n + int(R.shape.inner_entries)) / (pk_ms / 1e3),
                    "note": "lower-bound search, full-key compares in inner nodes, partial keys in leaves "
                            "(Sec. 4.3), median; every node scanned by partial keys in partial_key_inner_nodes; "
                            "partial keys of every entry (Sec. 4.2) timed separately"},
     }
+
+
+def headline_line(args, world, rec, workload, clk, launches):
+    return {
+        "metric": METRIC, "value": rec["value"], "unit": "keys/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": rec["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u32", "data": rec["data"],
+        "config": {k: rec[k] for k in ("workload", "n", "key_bytes", "distinction_bits", "ck_words", "digit_bits",
+                                       "radix_passes", "fanout", "tree_levels", "l2", "path")} |
+                  {"parallelism": "replicas" if world > 1 else "single GPU"},
+        "roofline": rec["roofline"],
+        "e2e": rec.get("e2e"),
+        "gpu_launches": int(launches),
+        "clocks": clk,
+        "spec_hbm_gbs": SPEC_HBM_GBS,
+    }
+
+
+def run_ours(args, rank, world, local_rank):
+    """One workload (--workload): its record is the line."""
+    import torch
+    from paper_2009_11543_gb300 import build as b
+    b.build()
+    torch.cuda.set_device(local_rank)
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    time.sleep(0.2)
+    rec, dmask = measure_config(args, args.workload, world, local_rank, headline=True,
+                                extras=args.workload == "urls64m")
+    clk = clocks.stop()
+    if rank != 0:
+        return None
+    line = headline_line(args, world, rec, args.workload, clk, rec["gpu_launches_per_step"] * args.steps)
+    line["detail"] = rec
     if world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(args.workload, dmask, cpu_rows)
+        line["cpu_baseline"] = cpu_baseline(args.workload, dmask, WORKLOADS[args.workload][4])
+    return line
+
+
+# The five configurations of the benchmark: the headline is the largest
+# single-GPU one, 200M DNA keys through the learned path.
+ALL_CONFIGS = [("C1", "int1m"), ("C2", "urls64m"), ("C3", "table16m"), ("C4", "zipf256m"), ("C5", "dna200m")]
+
+
+def run_all(args, rank, world, local_rank):
+    """Every configuration in one process and one JSON line: the 200M DNA
+    workload (learned partition + bulk load with fanout 256, model
+    separators) is the headline; the others are sub-records."""
+    import torch
+    from paper_2009_11543_gb300 import build as b
+    b.build()
+    torch.cuda.set_device(local_rank)
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    time.sleep(0.2)
+    subs = {}
+    t_run = time.perf_counter()
+    for cname, wl in ALL_CONFIGS[:-1]:
+        t0 = time.perf_counter()
+        if wl == "table16m":
+            a2 = argparse.Namespace(**vars(args))
+            a2.workload = wl
+            a2.no_cpu_baseline = True
+            rec = run_table(a2, rank, world, local_rank, own_clocks=False)
+        else:
+            rec, _ = measure_config(args, wl, world, local_rank, extras=wl == "urls64m")
+        if rec is not None:
+            rec["wall_s"] = time.perf_counter() - t0
+        subs[cname] = rec
+        torch.cuda.empty_cache()
+    rec, dmask = measure_config(args, "dna200m", world, local_rank, headline=True)
+    clk = clocks.stop()
+    if rank != 0:
+        return None
+    line = headline_line(args, world, rec, "dna200m", clk, rec["gpu_launches_per_step"] * args.steps)
+    line["config"]["configs"] = "C5 headline (200M DNA, learned); C1-C4 in `configs`"
+    line["C5"] = rec
+    line["configs"] = subs
+    line["learned_vs_plain"] = {c: (subs[c] or {}).get("learned", {}).get("speedup_vs_plain")
+                                for c in ("C1", "C2", "C4")} | {"C5": rec["learned"]["speedup_vs_plain"]}
+    line["batched_vs_sequential_C3"] = (subs["C3"] or {}).get("batched_vs_plain_speedup")
+    line["bench_wall_s"] = time.perf_counter() - t_run
+    if world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline("dna200m", dmask, WORKLOADS["dna200m"][4])
     return line
 
 
@@ -711,7 +854,8 @@ def run_reference(args, rank, world):
     if rank != 0:
         return None
     import oracle
-    desc, n, kind, fanout, rows, _ = WORKLOADS[args.workload]
+    workload = "dna200m" if args.workload == "all" else args.workload   # the headline configuration
+    desc, n, kind, fanout, rows, _ = WORKLOADS[workload]
     if kind == "table":
         import synth
         rows = min(rows, 500_000)
@@ -756,7 +900,7 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="urls64m", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="all", choices=["all"] + sorted(WORKLOADS))
     ap.add_argument("--digit-bits", type=int, default=8)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
@@ -769,6 +913,8 @@ def main():
         dist.init_process_group("gloo")
     if args.impl == "reference":
         line = run_reference(args, rank, world)
+    elif args.workload == "all":
+        line = run_all(args, rank, world, local_rank)
     elif args.workload == "table16m":
         line = run_table(args, rank, world, local_rank)
     elif args.workload == "zipfsweep":

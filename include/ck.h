@@ -330,7 +330,12 @@ typedef struct ck_learned_opts {
     float lr;             /* Adam learning rate; 0 = 1e-3 */
     uint32_t flags;       /* CK_LEARNED_* bits */
     uint32_t reserved;    /* must be 0 */
+    void* phase_events;   /* NULL, or CK_LEARNED_PHASES + 1 cudaEvent_t recorded on the stream at the start
+                             and after each phase: sample + model + boundaries, bucket ids, partition,
+                             bucket sorts + checks, verdict + gated fallback */
 } ck_learned_opts;
+
+#define CK_LEARNED_PHASES 5
 
 /* No model: the boundaries are sample quantiles and every key's bucket is
  * found by binary search (the method without the network). */

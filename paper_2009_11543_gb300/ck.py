@@ -60,7 +60,8 @@ class ck_sort_opts(ctypes.Structure):
 
 class ck_learned_opts(ctypes.Structure):
     _fields_ = [("bucket_bits", ctypes.c_uint32), ("sample_div", ctypes.c_uint32), ("epochs", ctypes.c_uint32),
-                ("lr", ctypes.c_float), ("flags", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
+                ("lr", ctypes.c_float), ("flags", ctypes.c_uint32), ("reserved", ctypes.c_uint32),
+                ("phase_events", ctypes.c_void_p)]
 
 
 class ck_learned_stats(ctypes.Structure):
@@ -411,8 +412,13 @@ CK_LEARNED_INJECT_VERIFY_FAIL = 2
 CK_LEARNED_INJECT_RID_SWAP = 4
 
 
-def learned_opts(bucket_bits=0, sample_div=0, epochs=0, lr=0.0, flags=0) -> ck_learned_opts:
-    return ck_learned_opts(bucket_bits, sample_div, epochs, lr, flags, 0)
+CK_LEARNED_PHASES = 5
+
+
+def learned_opts(bucket_bits=0, sample_div=0, epochs=0, lr=0.0, flags=0, phase_events=None) -> ck_learned_opts:
+    """phase_events: None, or a ctypes array of CK_LEARNED_PHASES + 1 event handles (event_handles())."""
+    return ck_learned_opts(bucket_bits, sample_div, epochs, lr, flags, 0,
+                           ctypes.cast(phase_events, ctypes.c_void_p) if phase_events is not None else None)
 
 
 def ck_sort_learned_workspace_bytes(n: int, ck_words: int, nbits: int, opts: ck_learned_opts | None = None) -> int:

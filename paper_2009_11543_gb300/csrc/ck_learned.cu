@@ -1120,6 +1120,9 @@ ck_status ck_sort_learned(const uint32_t* ck_in, uint32_t* ck_out, uint32_t* rid
     CK_TRY(cudaMemsetAsync(ws + P.off_lookback, 0, 4ull * 256 * tiles * P.passes + 4 * P.passes, s));
     const int sms = num_sms();
     const uint32_t* smp = at(P.off_sample_sorted);
+    cudaEvent_t* ev = opts ? static_cast<cudaEvent_t*>(opts->phase_events) : nullptr;
+    auto mark = [&](int k) { return ev ? cudaEventRecord(ev[k], s) : cudaSuccess; };
+    CK_TRY(mark(0));
 
     // 1. sample, sort the sample, features
     sample_kernel<<<sms * 4, 256, 0, s>>>(ck_in, ld, K, P.div, P.S, at(P.off_sample), P.ld_s);
@@ -1172,6 +1175,7 @@ ck_status ck_sort_learned(const uint32_t* ck_in, uint32_t* ck_out, uint32_t* rid
         count_launch();
     }
 
+    CK_TRY(mark(1));
     // 4. bucket id of every key (model guess + exact correction), digit
     //    counts, input hash
     BucketArgs ba;
@@ -1194,6 +1198,7 @@ ck_status ck_sort_learned(const uint32_t* ck_in, uint32_t* ck_out, uint32_t* rid
     count_launch();
     CK_TRY(launch_bucket_scan(at(P.off_hist), P.passes, 8, s));
 
+    CK_TRY(mark(2));
     // 5. stable partition by bucket id: radix passes over its low byte, then its high byte
     auto al16 = [](const void* q) { return (reinterpret_cast<uintptr_t>(q) & 15) == 0; };
     const uint32_t bulk = al16(ck_in) && al16(ck_out) && al16(rid_out) ? 1u : 0u;
@@ -1234,6 +1239,7 @@ ck_status ck_sort_learned(const uint32_t* ck_in, uint32_t* ck_out, uint32_t* rid
         CK_TRY(launch_onesweep_pass(8, a, arr, (uint32_t)tiles, s));
     }
 
+    CK_TRY(mark(3));
     // 6. bucket starts, then every bucket sorted and checked
     uint32_t* start = at(P.off_start);
     bucket_bounds_kernel<<<(P.max_buckets + 256) / 256, 256, 0, s>>>(ck_out, ld, n, K, at(P.off_spl), misc,
@@ -1255,12 +1261,14 @@ ck_status ck_sort_learned(const uint32_t* ck_in, uint32_t* ck_out, uint32_t* rid
     la.inject = P.flags;
     CK_TRY(launch_local_sort(la, s));
 
+    CK_TRY(mark(4));
     // 7. verdict, statistics; the plain radix sort runs only if the verdict says so
     finalize_kernel<<<1, 64, 0, s>>>(misc, (P.flags & CK_LEARNED_INJECT_VERIFY_FAIL) ? 1u : 0u, use_model ? 1u : 0u,
                                      P.B, P.S, n, P.cap, status, stats, params, params_out);
     count_launch();
     CK_TRY(run_sort(P.plain, ck_in, nullptr, ck_out, rid_out, n, nbits, kDefaultSpin, 0, 0, nullptr,
                     ws + P.off_plain_ws, s, nullptr, &misc->gate));
+    CK_TRY(mark(5));
 #undef CK_TRY
     return cudaGetLastError() == cudaSuccess ? CK_OK : CK_ECUDA;
 }

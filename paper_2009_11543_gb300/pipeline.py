@@ -106,9 +106,16 @@ class Rebuild:
                            kind=self.kind, stream=stream)
 
     def sort(self, stream=None, pass_events=None):
+        """pass_events: ctypes event handles recorded around every radix pass
+        (plain sort) or at the CK_LEARNED_PHASES phase boundaries (learned sort)."""
         if self.learned:
+            o = self.learned_opts
+            if pass_events is not None:
+                base = o or ck.learned_opts()
+                o = ck.learned_opts(base.bucket_bits, base.sample_div, base.epochs, base.lr, base.flags,
+                                    phase_events=pass_events)
             ck.ck_sort_learned(self.ck_in, self.ck_sorted, self.rid_sorted, self.n, self.K, self.nbits, self.ws,
-                               self.learned_opts, stats=self.stats_buf, params=self.params_buf, stream=stream)
+                               o, stats=self.stats_buf, params=self.params_buf, stream=stream)
             return
         ck.ck_sort(self.ck_in, None, self.ck_sorted, self.rid_sorted, self.n, self.K, self.nbits, self.ws,
                    digit_bits=self.digit_bits, pass_events=pass_events, perm_only=self.perm_only, hist=self.hist,
