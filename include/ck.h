@@ -259,16 +259,20 @@ ck_status ck_sort(const uint32_t* ck_in, const uint32_t* rid_in, uint32_t* ck_ou
  * latency-bound rebuild path cannot afford.
  *   Arguments, outputs and errors are those of ck_sort without ws / ws_bytes.
  *   Limit: the call is accepted only if ck_sort_workspace_bytes(n, ck_words,
- *   nbits, opts) <= CK_SORT_STATIC_SCRATCH_BYTES (32 MiB, about 1.4M pairs of
- *   128-bit keys); larger sorts return CK_ENOMEM without launching anything
- *   and should use ck_sort with a workspace.
- *   The array is allocated once per GPU when the library is loaded and held
- *   until the process exits.  The first call on each device looks up the
- *   array's device address (with that device current); make that first call
- *   before any stream capture.  Every call on a device uses the same array:
- *   calls whose execution overlaps on the GPU (other streams, other threads)
- *   race and give wrong results, so serialise them.  Nothing is allocated or
- *   freed by the call. */
+ *   nbits, opts) <= CK_SORT_STATIC_SCRATCH_BYTES (32 MiB: up to 1,396,736
+ *   pairs of 128-bit keys with 8-bit digits); larger sorts return CK_ENOMEM
+ *   without launching anything and should use ck_sort with a workspace.
+ *   The array belongs to the library's device code and is held until the
+ *   process exits.  CUDA loads that code on a device lazily by default (unless
+ *   CUDA_MODULE_LOADING=EAGER), so the 32 MiB are committed on each device at
+ *   the latest by the first ck_sort_static call there, which also looks up the
+ *   array's device address (with that device current).  A caller whose path
+ *   must see no device allocation makes one call at start-up (a warm-up), and
+ *   makes it before any stream capture; when the device has no room left for
+ *   the array that first call returns CK_ENOMEM.  Every call on a device uses
+ *   the same array: calls whose execution overlaps on the GPU (other streams,
+ *   other threads) race and give wrong results, so serialise them.  After the
+ *   first call on a device nothing is allocated or freed. */
 #define CK_SORT_STATIC_SCRATCH_BYTES (32u << 20)
 
 ck_status ck_sort_static(const uint32_t* ck_in, const uint32_t* rid_in, uint32_t* ck_out, uint32_t* rid_out,
@@ -598,6 +602,11 @@ ck_status ck_model_separators(const float* params, const ck_btree* tree, uint32_
  * jobs run concurrently and the call is asynchronous; it can be captured into
  * a CUDA graph (ck_graph_capture_batched does that and instantiates it).
  * Every buffer of a job is the caller's; jobs must not share buffers.
+ * The internal streams and the fork event are shared by every call on a
+ * device, so the library serialises batched calls and captures: a call holds
+ * an internal lock from its fork through its last join while it queues its
+ * work (a capture from its begin to its end), and the work of two calls runs
+ * one after the other on the GPU.
  *   digit_bits  radix digit width of the job's sort, 4 .. 11 (0 = 8); see
  *               ck_autotune_sort.
  *   ws          the job's sort workspace (ck_sort_workspace_bytes); when it

@@ -345,10 +345,11 @@ def ck_sort(ck_in: torch.Tensor, rid_in: torch.Tensor | None, ck_out: torch.Tens
 
 
 def ck_sort_static(ck_in: torch.Tensor, rid_in: torch.Tensor | None, ck_out: torch.Tensor, rid_out: torch.Tensor,
-                   n: int, ck_words: int, nbits: int, digit_bits: int = 0, stream=None) -> None:
+                   n: int, ck_words: int, nbits: int, digit_bits: int = 0, perm_only: bool = False,
+                   stream=None) -> None:
     """ck_sort without a caller workspace: the library's fixed scratch array is
     used instead (for callers that cannot allocate device memory; see ck.h)."""
-    o = _opts(digit_bits)
+    o = _opts(digit_bits, flags=CK_SORT_PERM_ONLY if perm_only else 0)
     _check(_lib().ck_sort_static(_ptr(ck_in), _ptr(rid_in), _ptr(ck_out), _ptr(rid_out), n, ck_words, nbits,
                                  ctypes.byref(o), _stream(stream)), "ck_sort_static")
 

@@ -30,6 +30,11 @@ struct DeviceStreams {
 
 std::mutex g_batch_mu;
 DeviceStreams g_dev[kMaxDev];
+// Held by a batched call from its fork event through its last join, and by a
+// capture from its begin to its end: every call shares the internal streams
+// and the fork event, so two calls (or a call and a capture) must not
+// interleave their records and waits.
+std::mutex g_batch_call_mu;
 
 // Internal non-blocking streams and events of the current device (created once).
 DeviceStreams* device_streams(uint32_t need) {
@@ -65,9 +70,10 @@ struct ck_graph_st {
     cudaGraphExec_t exec;
 };
 
-extern "C" {
+namespace {
 
-ck_status ck_build_batched(const ck_index_job* jobs, uint32_t njobs, ck_stream stream) {
+// The batched rebuild; the caller holds g_batch_call_mu.
+ck_status build_batched_locked(const ck_index_job* jobs, uint32_t njobs, ck_stream stream) {
     if (!jobs || njobs == 0 || njobs > CK_MAX_JOBS) return CK_EINVAL;
     for (uint32_t j = 0; j < njobs; ++j)
         if (!jobs[j].dmask || !jobs[j].tree) return CK_EINVAL;
@@ -110,9 +116,19 @@ ck_status ck_build_batched(const ck_index_job* jobs, uint32_t njobs, ck_stream s
     return first_error;
 }
 
+}  // namespace
+
+extern "C" {
+
+ck_status ck_build_batched(const ck_index_job* jobs, uint32_t njobs, ck_stream stream) {
+    std::lock_guard<std::mutex> lk(g_batch_call_mu);
+    return build_batched_locked(jobs, njobs, stream);
+}
+
 ck_status ck_graph_capture_batched(const ck_index_job* jobs, uint32_t njobs, ck_graph* graph_out) {
     if (!graph_out) return CK_EINVAL;
     *graph_out = nullptr;
+    std::lock_guard<std::mutex> lk(g_batch_call_mu);
     cudaStream_t cs;
     if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) return CK_ECUDA;
     ck_status st = CK_OK;
@@ -121,7 +137,7 @@ ck_status ck_graph_capture_batched(const ck_index_job* jobs, uint32_t njobs, ck_
         cudaStreamDestroy(cs);
         return CK_ECUDA;
     }
-    st = ck_build_batched(jobs, njobs, reinterpret_cast<ck_stream>(cs));
+    st = build_batched_locked(jobs, njobs, reinterpret_cast<ck_stream>(cs));
     const cudaError_t e = cudaStreamEndCapture(cs, &g);
     cudaStreamDestroy(cs);
     if (st != CK_OK) {

@@ -12,7 +12,10 @@
 // comes from here.
 //
 // The scratch is one file-scope device array of CK_SORT_STATIC_SCRATCH_BYTES
-// bytes.  Every GPU that loads the library holds it until the process exits.
+// bytes.  Every GPU that loads this code holds it until the process exits;
+// with CUDA's lazy module loading (the default) the code, and with it the
+// array, is loaded on a device at the latest by the first call there, so a
+// caller that must see no allocation on its path makes one call at start-up.
 // All calls on a device share it and it keeps the previous call's contents;
 // the sort clears the parts that must start at zero (histograms, tile
 // counters, look-back words) at the start of every call.  Two calls whose
@@ -42,8 +45,9 @@ static unsigned char* static_scratch(ck_status* st) {
     std::lock_guard<std::mutex> lk(g_static_mu);
     if (!g_static_addr[d]) {
         void* p = nullptr;
-        if (cudaGetSymbolAddress(&p, g_sort_scratch) != cudaSuccess || !p) {
-            *st = CK_ECUDA;
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_sort_scratch);
+        if (e != cudaSuccess || !p) {  // the module (and the array) could not be loaded on this device
+            *st = e == cudaErrorMemoryAllocation ? CK_ENOMEM : CK_ECUDA;
             return nullptr;
         }
         g_static_addr[d] = static_cast<unsigned char*>(p);
