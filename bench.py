@@ -30,6 +30,7 @@ import argparse
 import hashlib
 import json
 import os
+import platform
 import statistics
 import subprocess
 import sys
@@ -822,7 +823,7 @@ def run_all(args, rank, world, local_rank):
     line["batched_vs_sequential_C3"] = (subs["C3"] or {}).get("batched_vs_plain_speedup")
     line["bench_wall_s"] = time.perf_counter() - t_run
     if world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline("dna200m", dmask, WORKLOADS["dna200m"][4])
+        line["cpu_baseline"] = cpu_baseline("dna200m", dmask, WORKLOADS["dna200m"][4], par_rows=16_000_000)
     return line
 
 
@@ -838,16 +839,55 @@ def oracle_step(keys, dmask, fanout, key_bits):
     oracle.btree(keys, perm, fanout)
 
 
-def cpu_baseline(workload, dmask, rows):
+def cpu_model() -> str:
+    """The host CPU's model name (lscpu, else /proc/cpuinfo)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith(("model name", "cpu part")):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return platform.processor() or platform.machine()
+
+
+def all_cores_sort(keys, dmask, rows):
+    """The paper's multi-core CPU comparison (Sec. 6): GCC parallel-mode
+    stable sort of the sample's (compressed key, row id) pairs on every host
+    core.  The compression before it is set-up, untimed."""
+    import oracle
+    K = max(1, (oracle.popcount(dmask) + 31) // 32)
+    c = oracle.compress(keys, dmask, K)
+    oracle.sort_compressed_parallel(c[: min(rows, 100_000)])          # warm-up (thread pool, pages)
+    t = time.perf_counter()
+    _, used = oracle.sort_compressed_parallel(c)
+    dt = time.perf_counter() - t
+    return {"value": rows / dt, "unit": "keys/s", "cores": used, "nproc": os.cpu_count(), "cpu_model": cpu_model(),
+            "kind": "gcc_parallel_stable_sort",
+            "sample": "the compressed-key sort step alone (Sec. 3.2) on the first %d rows of the same seeded "
+                      "workload, %d threads" % (rows, used)}
+
+
+def cpu_baseline(workload, dmask, rows, par_rows=None):
     desc, n, kind, fanout, _, _ = WORKLOADS[workload]
-    keys = gen_keys(kind, rows)          # the first rows of the same seeded column
+    keys = gen_keys(kind, max(rows, par_rows or 0))   # the first rows of the same seeded column
     kb = 8 * (keys.shape[1] if keys.ndim == 2 else keys.dtype.itemsize)
     t = time.perf_counter()
-    oracle_step(keys, dmask, fanout, kb)
+    oracle_step(keys[:rows], dmask, fanout, kb)
     dt = time.perf_counter() - t
-    return {"value": rows / dt, "unit": "keys/s", "cores": 1, "kind": "oracle",
-            "sample": "first %d rows of the same seeded workload, one rebuild (compress, sort, refine, bulk load), "
-                      "single thread" % rows}
+    rec = {"value": rows / dt, "unit": "keys/s", "cores": 1, "kind": "oracle", "cpu_model": cpu_model(),
+           "sample": "first %d rows of the same seeded workload, one rebuild (compress, sort, refine, bulk load), "
+                     "single thread" % rows}
+    if par_rows:
+        rec["all_cores_sort"] = all_cores_sort(keys[:par_rows], dmask, par_rows)
+    return rec
 
 
 def run_reference(args, rank, world):

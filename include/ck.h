@@ -679,6 +679,12 @@ uint64_t ck_launch_count(void);
  * For host tests of the extraction plan; touches no device. */
 uint32_t ck_compress_word_host(uint32_t x, uint32_t mask);
 
+/* The same gather in the form ck_extract's kernel runs for a key word with
+ * this mask: two shift-and-mask terms when the mask has at most two contiguous
+ * runs, else only the compress-network rounds whose move masks are non-zero.
+ * For host tests of the extraction plan; touches no device. */
+uint32_t ck_compress_word_program_host(uint32_t x, uint32_t mask);
+
 #ifdef __cplusplus
 }
 #endif

@@ -42,18 +42,25 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "ck_oracle.c")
 _LIB = os.path.join(_HERE, "libck_oracle.so")
+_PAR_SRC = os.path.join(_HERE, "ck_oracle_par.cpp")
+_PAR_LIB = os.path.join(_HERE, "libck_oracle_par.so")
 NO_DBIT = 0xFFFF
 MAX_LEVELS = 64
 
 _lib = None
+_par_lib = None
 
 
 def build(force: bool = False) -> str:
-    """Compile ck_oracle.c with gcc into oracle/libck_oracle.so."""
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
-        tmp = _LIB + ".tmp%d" % os.getpid()
-        subprocess.check_call(["gcc", "-O2", "-std=c11", "-shared", "-fPIC", "-o", tmp, _SRC])
-        os.replace(tmp, _LIB)
+    """Compile ck_oracle.c with gcc into oracle/libck_oracle.so, and the
+    all-cores comparison sort (ck_oracle_par.cpp, g++ with OpenMP) into
+    oracle/libck_oracle_par.so."""
+    for src, lib, cmd in ((_SRC, _LIB, ["gcc", "-O2", "-std=c11"]),
+                          (_PAR_SRC, _PAR_LIB, ["g++", "-O2", "-std=c++17", "-fopenmp"])):
+        if force or not os.path.exists(lib) or os.path.getmtime(lib) < os.path.getmtime(src):
+            tmp = lib + ".tmp%d" % os.getpid()
+            subprocess.check_call(cmd + ["-shared", "-fPIC", "-o", tmp, src])
+            os.replace(tmp, lib)
     return _LIB
 
 
@@ -241,6 +248,28 @@ def sort_compressed(ck: np.ndarray) -> np.ndarray:
     perm = np.empty(n, np.uint32)
     _load().cko_sort_compressed(_ptr(ck), n, K, _ptr(perm))
     return perm
+
+
+def sort_compressed_parallel(ck: np.ndarray, threads: int = 0) -> tuple[np.ndarray, int]:
+    """Sec. 3.2's sort of the rows by compressed value (ties by row id) with
+    GCC's parallel-mode stable sort on `threads` host threads (0: every
+    core), the multi-core CPU sort of the paper's evaluation (Sec. 6).
+    Returns (perm, threads used)."""
+    global _par_lib
+    if _par_lib is None:
+        build()
+        lib = ctypes.CDLL(_PAR_LIB)
+        lib.cko_par_sort_compressed.argtypes = [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint32,
+                                                ctypes.c_void_p, ctypes.c_int]
+        lib.cko_par_sort_compressed.restype = ctypes.c_int
+        _par_lib = lib
+    ck = np.ascontiguousarray(ck, np.uint32)
+    n, K = ck.shape
+    perm = np.empty(n, np.uint32)
+    t = _par_lib.cko_par_sort_compressed(_ptr(ck), n, K, _ptr(perm), int(threads))
+    if t < 0:
+        raise ValueError("compressed keys of %d words are not supported (1..8)" % K)
+    return perm, t
 
 
 def refine(ck: np.ndarray, perm: np.ndarray, old_mask: np.ndarray, key_bits: int) -> np.ndarray:

@@ -33,7 +33,8 @@ CK_NO_ROW = 0xFFFFFFFF
 
 EXPORTED = ["ck_variant_bits", "ck_distinction_bits", "ck_extract", "ck_sort_workspace_bytes", "ck_sort",
             "ck_btree_plan", "ck_build_index", "ck_device_status", "ck_clear_device_status",
-            "ck_status_string", "ck_launch_count", "ck_compress_word_host", "ck_sort_static", "ck_build_index_keys",
+            "ck_status_string", "ck_launch_count", "ck_compress_word_host", "ck_compress_word_program_host",
+            "ck_sort_static", "ck_build_index_keys",
             "ck_sort_learned_workspace_bytes", "ck_sort_learned", "ck_mlp_workspace_bytes", "ck_mlp_loss_grad",
             "ck_build_batched", "ck_graph_capture_batched", "ck_graph_launch", "ck_graph_destroy",
             "ck_autotune_sort", "ck_model_separators", "ck_insert_workspace_bytes", "ck_insert_batch", "ck_encode_key",
@@ -149,9 +150,12 @@ def _lib():
         lib.ck_launch_count.restype = U64
         lib.ck_compress_word_host.argtypes = [U32, U32]
         lib.ck_compress_word_host.restype = U32
+        lib.ck_compress_word_program_host.argtypes = [U32, U32]
+        lib.ck_compress_word_program_host.restype = U32
         for name in EXPORTED:
             if name not in ("ck_sort_workspace_bytes", "ck_status_string", "ck_launch_count",
-                            "ck_compress_word_host", "ck_sort_learned_workspace_bytes", "ck_mlp_workspace_bytes"):
+                            "ck_compress_word_host", "ck_compress_word_program_host",
+                            "ck_sort_learned_workspace_bytes", "ck_mlp_workspace_bytes"):
                 getattr(lib, name).restype = I
         _LIB = lib
     return _LIB
@@ -606,6 +610,10 @@ def ck_launch_count() -> int:
 
 def ck_compress_word_host(x: int, mask: int) -> int:
     return int(_lib().ck_compress_word_host(x & 0xFFFFFFFF, mask & 0xFFFFFFFF))
+
+
+def ck_compress_word_program_host(x: int, mask: int) -> int:
+    return int(_lib().ck_compress_word_program_host(x & 0xFFFFFFFF, mask & 0xFFFFFFFF))
 
 
 def mask_to_host(mask: torch.Tensor) -> np.ndarray:

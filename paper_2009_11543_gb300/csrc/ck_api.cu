@@ -127,9 +127,63 @@ static bool mask_fits(const uint64_t* mask, uint32_t key_bits) {
 
 static ck_status cuda_status(cudaError_t e) { return e == cudaSuccess ? CK_OK : CK_ECUDA; }
 
-// Extraction plan of a D-bitmap: per 32-bit key word its mask, the move masks
-// of its compress network and its popcount, plus the output padding.  With no
-// set bit, first_word > last_word and only the leading zero words are written.
+// Program of one non-zero mask word (see WordProg): the runs form when the
+// mask has at most two contiguous runs, else the network with only its
+// non-zero rounds.  The appending fields (s1, s2, emit, kout) are set by the
+// caller.
+static WordProg word_program(uint32_t m) {
+    WordProg p;
+    memset(&p, 0, sizeof(p));
+    p.mask = m;
+    p.pc = (uint32_t)__builtin_popcount(m);
+    uint32_t runs = 0, lo[2] = {0, 0}, len[2] = {0, 0};
+    for (uint32_t b = 0; b < 32;) {  // runs from the least significant bit up
+        if (!((m >> b) & 1u)) {
+            ++b;
+            continue;
+        }
+        uint32_t e = b;
+        while (e < 32 && ((m >> e) & 1u)) ++e;
+        if (runs < 2) {
+            lo[runs] = b;
+            len[runs] = e - b;
+        }
+        ++runs;
+        b = e;
+    }
+    if (runs <= 2) {
+        // run j moves down by the zeros below it; it lands at lo - zeros
+        for (uint32_t j = 0; j < runs; ++j) {
+            const uint32_t zeros = lo[j] - (j == 0 ? 0u : len[0]);
+            const uint32_t field = len[j] == 32 ? 0xFFFFFFFFu : ((1u << len[j]) - 1u);
+            p.mv[2 * j] = zeros;
+            p.mv[2 * j + 1] = field << (lo[j] - zeros);
+        }
+        p.ctl = kProgRuns;
+        return p;
+    }
+    compress_network(m, p.mv);
+    for (int s = 0; s < 5; ++s)
+        if (p.mv[s]) p.ctl |= 1u << s;
+    return p;
+}
+
+// Host copy of the device's compress of one word under its program.
+static uint32_t run_program(const WordProg& p, uint32_t x) {
+    if (p.ctl & kProgRuns) return ((x >> p.mv[0]) & p.mv[1]) | ((x >> p.mv[2]) & p.mv[3]);
+    x &= p.mask;
+    for (int s = 0; s < 5; ++s)
+        if (p.ctl & (1u << s)) {
+            const uint32_t t = x & p.mv[s];
+            x = (x ^ t) | (t >> (1u << s));
+        }
+    return x;
+}
+
+// Extraction plan of a D-bitmap: per 32-bit key word its program (how its
+// D-bits are gathered and where they go in the output), plus the output
+// padding.  With no set bit, first_word > last_word and only the leading zero
+// words are written.
 bool make_extract_plan(const KeyDesc& k, const uint64_t* dmask, uint32_t ck_words, ExtractPlan* plan) {
     memset(plan, 0, sizeof(*plan));
     const uint32_t nbits = popcount64(dmask, 8 * k.key_bytes);
@@ -140,15 +194,22 @@ bool make_extract_plan(const KeyDesc& k, const uint64_t* dmask, uint32_t ck_word
     plan->pad_bits = 32 * used - nbits;
     plan->first_word = 0xFFFFFFFFu;
     plan->last_word = 0;
+    uint32_t fill = plan->pad_bits, kout = used - 1;  // bits in the output word under construction; its index
     for (uint32_t w = 0; w < k.nwords; ++w) {
         const uint64_t mw = dmask[w / 2];
         const uint32_t m = (w % 2 == 0) ? (uint32_t)(mw >> 32) : (uint32_t)mw;
-        plan->mask[w] = m;
         if (!m) continue;
-        uint32_t mv[5];
-        compress_network(m, mv);
-        for (int st = 0; st < 5; ++st) plan->mv[st][w] = mv[st];
-        plan->pc[w] = (uint8_t)__builtin_popcount(m);
+        WordProg p = word_program(m);
+        const uint32_t e = fill + p.pc;
+        if (e < 32) {
+            p.ctl |= (32u - e) << 8;
+            fill = e;
+        } else {
+            p.ctl |= ((e - 32u) << 8) | ((64u - e) << 16) | kProgEmit | (kout << 24);
+            fill = e - 32u;
+            --kout;
+        }
+        plan->prog[w] = p;
         if (plan->first_word == 0xFFFFFFFFu) plan->first_word = w;
         plan->last_word = w;
     }
@@ -385,6 +446,11 @@ uint32_t ck_compress_word_host(uint32_t x, uint32_t mask) {
     uint32_t mv[5];
     compress_network(mask, mv);
     return apply_network(x, mask, mv);
+}
+
+uint32_t ck_compress_word_program_host(uint32_t x, uint32_t mask) {
+    if (!mask) return 0u;
+    return run_program(word_program(mask), x);
 }
 
 }  // extern "C"

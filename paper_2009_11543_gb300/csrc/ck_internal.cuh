@@ -109,7 +109,7 @@ __device__ __forceinline__ uint32_t bswap32(uint32_t x) { return __byte_perm(x, 
 
 // Loads 16 bytes worth of words starting at word 4c of row r.  Words past the
 // key read 0.  Only the word indices [4c, 4c+4) are produced.
-template <int VEC>
+template <int VEC, bool TAIL = true>
 __device__ __forceinline__ void load_chunk_row(const KeyDesc& k, const unsigned char* row, uint32_t c,
                                                uint32_t (&w)[4]);
 
@@ -118,8 +118,10 @@ __device__ __forceinline__ void load_chunk(const KeyDesc& k, uint64_t r, uint32_
     load_chunk_row<VEC>(k, k.base + r * k.stride, c, w);
 }
 
-// Same, for a row that starts at `row` (global or shared memory).
-template <int VEC>
+// Same, for a row that starts at `row` (global or shared memory).  TAIL =
+// false leaves the bytes past key_bytes of byte keys as loaded (for callers
+// that mask them away).
+template <int VEC, bool TAIL>
 __device__ __forceinline__ void load_chunk_row(const KeyDesc& k, const unsigned char* row, uint32_t c,
                                                uint32_t (&w)[4]) {
     if (k.kind == CK_KIND_U64 || k.kind == CK_KIND_I64 || k.kind == CK_KIND_F64) {  // 8-byte value; chunk 0 only
@@ -170,10 +172,12 @@ __device__ __forceinline__ void load_chunk_row(const KeyDesc& k, const unsigned 
         }
     }
     // zero the bytes past key_bytes inside the last word
+    if (TAIL) {
 #pragma unroll
-    for (int i = 0; i < 4; ++i)
-        if (first + i == k.nwords - 1) w[i] &= k.tail_mask;
-        else if (first + i >= k.nwords) w[i] = 0;
+        for (int i = 0; i < 4; ++i)
+            if (first + i == k.nwords - 1) w[i] &= k.tail_mask;
+            else if (first + i >= k.nwords) w[i] = 0;
+    }
 }
 
 
@@ -366,14 +370,34 @@ cudaError_t launch_variant(const KeyDesc& k, int vec, uint64_t n, uint64_t ref_r
 cudaError_t launch_dbits(const KeyDesc& k, int vec, uint64_t n, const uint32_t* order, uint64_t* mask_out,
                          cudaStream_t s);
 
+// The extraction's program for one 32-bit key word, the same for every row.
+// Its D-bits are gathered into the low popcount(mask) bits of a value x in one
+// of two forms, then x is appended to the output word under construction.
+//   network form: x = word & mask, then the rounds of the compress network
+//     whose move masks are non-zero (ctl bits 0-4; mv[s] moves by 2^s);
+//   runs form (ctl kProgRuns; masks of at most two contiguous runs):
+//     x = ((word >> mv[0]) & mv[1]) | ((word >> mv[2]) & mv[3]).
+// Appending: with e = (bits already in the output word) + popcount(mask),
+//   e < 32:  cur |= x << s1;
+//   e >= 32: the output word cur | (x >> s1) is complete and stored as
+//            compressed word `kout` (ctl bits 24-31); cur = x << s2 (s2 = 32:
+//            nothing is left over).
+struct WordProg {
+    uint32_t mask;   // D's positions in this word, big-endian bit order; 0: the word adds nothing
+    uint32_t mv[5];  // network: move masks; runs: shift, mask, shift, mask
+    uint32_t ctl;    // bits 0-4 rounds, 5 runs form, 8-13 s1, 16-21 s2, 22 emits, 24-31 kout
+    uint32_t pc;     // popcount(mask)
+};
+constexpr uint32_t kProgRuns = 1u << 5;
+constexpr uint32_t kProgEmit = 1u << 22;
+
 struct ExtractPlan {
     uint32_t first_word, last_word;  // words with a non-zero mask
     uint32_t K;                      // output words
     uint32_t lead_zero_words;        // whole zero words at the top of the output
     uint32_t pad_bits;               // zero bits at the top of the first non-zero output word
-    uint32_t mask[kMaxKeyWords];     // per key word, big-endian bit order
-    uint32_t mv[5][kMaxKeyWords];    // move masks of the compress network
-    uint8_t pc[kMaxKeyWords];        // popcount of mask[w]
+    uint32_t pad[3];
+    WordProg prog[kMaxKeyWords];     // per key word (zero outside first_word .. last_word)
 };
 // hist (device, passes * 2^rb counters, zeroed by the caller) != NULL: the
 // digit counts of the compressed keys are added to it in the same pass.

@@ -493,11 +493,11 @@ __device__ void block_split(const LsView<KW>& v, uint32_t p0, uint32_t r, bool i
     // The digit: the window's top bits after subtracting its minimum (2^F
     // bins), unless the top byte is sparse (at most 128 of its values occur,
     // as for keys over a small alphabet whose codes use few bit patterns) and
-    // the two top bytes' values in use give 1024 .. kLsBins combinations:
+    // the two top bytes' values in use give 256 .. kLsBins combinations:
     // then the mixed-radix number of their dense codes, which keeps the order
     // of the windows and spreads the pairs over far more bins.
     const uint32_t n1 = st.nbytes[0], n2 = st.nbytes[1];
-    const bool dense = n1 <= 128 && n1 * n2 <= (uint32_t)kLsBins && n1 * n2 >= 1024;
+    const bool dense = n1 <= 128 && n1 * n2 <= (uint32_t)kLsBins && n1 * n2 >= 256;
     uint32_t bins = 1u << F;
     if (dense) {
         bins = 256;

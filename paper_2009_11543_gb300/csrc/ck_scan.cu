@@ -135,18 +135,18 @@ __global__ void __launch_bounds__(256) dbits_kernel(const KeyDesc k, uint64_t n,
 
 // ------------------------------------------------------------------ extract
 // Compress network (H. S. Warren, Hacker's Delight, 2nd ed., Sec. 7-4): with
-// move masks mv[s] precomputed for the word's mask, five rounds of
+// move masks mv[s] precomputed for the word's mask, the rounds
 //   t = x & mv[s];  x = (x ^ t) | (t >> 2^s)
 // gather the masked bits of x, in order, into its low popcount(mask) bits.
-// The compressed bits of successive key words are appended (most significant
-// key word first) to a bit stream that begins with the output's leading zero
-// padding; every full 32 bits leave as one output word, top word first.
-// The per-word extraction plan, copied once per block into shared memory so
-// that every lookup is a broadcast shared load (indexing the kernel parameter
-// with a runtime word index would serialise on the indexed constant cache).
-struct WordPlan {
-    uint32_t mask, mv[5], pc, pad;
-};
+// The host plans each key word once (WordProg): only the rounds whose move
+// mask is non-zero run, and a mask of at most two contiguous runs takes two
+// shift-and-mask terms instead.  The compressed bits of successive key words
+// are appended (most significant key word first) to the output word under
+// construction, which starts with the output's leading zero padding; every
+// full 32 bits leave as one output word, top word first.  The plan is copied
+// once per block into shared memory so that every lookup is a broadcast
+// shared load (indexing the kernel parameter with a runtime word index would
+// serialise on the indexed constant cache).
 
 // Digit counts of the compressed keys, gathered while they are extracted (the
 // histograms a radix sort of them needs first): digit q of a key is bits
@@ -160,9 +160,10 @@ struct HistSink {
 
 __device__ __forceinline__ void count_digits(const HistSink& h, uint32_t k, uint32_t prev, uint32_t v) {
     if (h.rb == 8) {  // the bytes of the word, least significant first, are digits 4k .. 4k + 3
+        uint32_t* base = h.sm + (k << 10);
 #pragma unroll
         for (uint32_t b = 0; b < 4; ++b)
-            if (4u * k + b < h.passes) atomicAdd(&h.sm[((4u * k + b) << 8) | ((v >> (8u * b)) & 255u)], 1u);
+            if (4u * k + b < h.passes) atomicAdd(base + (b << 8) + ((v >> (8u * b)) & 255u), 1u);
         return;
     }
     const uint32_t lo_bit = 32u * k, bins = 1u << h.rb;
@@ -174,19 +175,64 @@ __device__ __forceinline__ void count_digits(const HistSink& h, uint32_t k, uint
         atomicAdd(&h.sm[q * bins + ((uint32_t)(both >> (q * h.rb - lo_bit)) & (bins - 1u))], 1u);
 }
 
+// The network rounds selected by RM (bit s: round s) on R values at once.
+template <uint32_t RM, int R>
+__device__ __forceinline__ void network_rounds(uint32_t (&x)[R], const WordProg& p) {
+#pragma unroll
+    for (int s = 0; s < 5; ++s)
+        if (RM & (1u << s)) {
+#pragma unroll
+            for (int q = 0; q < R; ++q) {
+                const uint32_t t = x[q] & p.mv[s];
+                x[q] = (x[q] ^ t) | (t >> (1u << s));
+            }
+        }
+}
+
+// x[q] = compressed bits of word w[q] under program p.
+template <int R>
+__device__ __forceinline__ void compress_word(const WordProg& p, const uint32_t (&w)[R], uint32_t (&x)[R]) {
+    if (p.ctl & kProgRuns) {
+#pragma unroll
+        for (int q = 0; q < R; ++q) x[q] = ((w[q] >> p.mv[0]) & p.mv[1]) | ((w[q] >> p.mv[2]) & p.mv[3]);
+        return;
+    }
+#pragma unroll
+    for (int q = 0; q < R; ++q) x[q] = w[q] & p.mask;
+#define CK_ROUNDS_CASE(M) \
+    case M: network_rounds<M, R>(x, p); break;
+    switch (p.ctl & 31u) {
+        CK_ROUNDS_CASE(0) CK_ROUNDS_CASE(1) CK_ROUNDS_CASE(2) CK_ROUNDS_CASE(3) CK_ROUNDS_CASE(4) CK_ROUNDS_CASE(5)
+        CK_ROUNDS_CASE(6) CK_ROUNDS_CASE(7) CK_ROUNDS_CASE(8) CK_ROUNDS_CASE(9) CK_ROUNDS_CASE(10)
+        CK_ROUNDS_CASE(11) CK_ROUNDS_CASE(12) CK_ROUNDS_CASE(13) CK_ROUNDS_CASE(14) CK_ROUNDS_CASE(15)
+        CK_ROUNDS_CASE(16) CK_ROUNDS_CASE(17) CK_ROUNDS_CASE(18) CK_ROUNDS_CASE(19) CK_ROUNDS_CASE(20)
+        CK_ROUNDS_CASE(21) CK_ROUNDS_CASE(22) CK_ROUNDS_CASE(23) CK_ROUNDS_CASE(24) CK_ROUNDS_CASE(25)
+        CK_ROUNDS_CASE(26) CK_ROUNDS_CASE(27) CK_ROUNDS_CASE(28) CK_ROUNDS_CASE(29) CK_ROUNDS_CASE(30)
+        default: network_rounds<31, R>(x, p); break;
+    }
+#undef CK_ROUNDS_CASE
+}
+
+// Copies the word programs of the chunks extract_rows visits (whole 16-byte
+// chunks from first_word's to last_word's) into shared memory.
+__device__ __forceinline__ void stage_programs(const ExtractPlan& plan, WordProg* wp) {
+    if (plan.first_word > plan.last_word) return;
+    const uint32_t w0 = plan.first_word & ~3u, w1 = plan.last_word | 3u;
+    for (uint32_t w = w0 + threadIdx.x; w <= w1; w += blockDim.x) wp[w] = plan.prog[w];
+}
+
 // Compress of R rows at once: row q's chunks come from rows[q] (global or
-// shared memory); each plan word is read once for all R rows.
+// shared memory); each word's program is read once for all R rows.
 template <int VEC, int R, bool HIST = false>
 __device__ __forceinline__ void extract_rows(const KeyDesc& k, const unsigned char* const (&rows)[R],
                                              const uint64_t (&r)[R], const bool (&valid)[R], uint64_t ld,
-                                             const ExtractPlan& plan, const WordPlan* wp, uint32_t* __restrict__ out,
+                                             const ExtractPlan& plan, const WordProg* wp, uint32_t* __restrict__ out,
                                              const HistSink& hs = HistSink{nullptr, 0, 0}) {
-    uint32_t kout = plan.K;
-    uint32_t prev[R];
+    uint32_t prev[R], cur[R];
 #pragma unroll
-    for (int q = 0; q < R; ++q) prev[q] = 0u;
+    for (int q = 0; q < R; ++q) prev[q] = cur[q] = 0u;
     for (uint32_t z = 0; z < plan.lead_zero_words; ++z) {
-        --kout;
+        const uint32_t kout = plan.K - 1 - z;
 #pragma unroll
         for (int q = 0; q < R; ++q)
             if (valid[q]) {
@@ -194,48 +240,41 @@ __device__ __forceinline__ void extract_rows(const KeyDesc& k, const unsigned ch
                 if (HIST) count_digits(hs, kout, 0u, 0u);
             }
     }
-    uint64_t acc[R];
-#pragma unroll
-    for (int q = 0; q < R; ++q) acc[q] = 0;
-    uint32_t cnt = plan.pad_bits;
     const uint32_t c0 = plan.first_word >> 2, c1 = plan.last_word >> 2;
     for (uint32_t c = c0; c <= c1; ++c) {
         uint32_t w[R][4];
 #pragma unroll
         for (int q = 0; q < R; ++q) {
-            if (valid[q]) load_chunk_row<VEC>(k, rows[q], c, w[q]);
+            if (valid[q]) load_chunk_row<VEC, false>(k, rows[q], c, w[q]);
             else w[q][0] = w[q][1] = w[q][2] = w[q][3] = 0;
         }
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
-            const uint32_t wi = 4 * c + i;
-            if (wi < plan.first_word || wi > plan.last_word) continue;
-            const WordPlan p = wp[wi];
+            const WordProg p = wp[4 * c + i];
             if (p.mask == 0) continue;
+            uint32_t wi[R], x[R];
+#pragma unroll
+            for (int q = 0; q < R; ++q) wi[q] = w[q][i];
+            compress_word<R>(p, wi, x);
+            const uint32_t s1 = (p.ctl >> 8) & 63u;
+            if (!(p.ctl & kProgEmit)) {
+#pragma unroll
+                for (int q = 0; q < R; ++q) cur[q] |= x[q] << s1;
+                continue;
+            }
+            const uint32_t s2 = (p.ctl >> 16) & 63u, kout = p.ctl >> 24;
+            uint32_t* o = out + (uint64_t)kout * ld;
 #pragma unroll
             for (int q = 0; q < R; ++q) {
-                uint32_t x = w[q][i] & p.mask;
-#pragma unroll
-                for (int s = 0; s < 5; ++s) {
-                    const uint32_t t = x & p.mv[s];
-                    x = (x ^ t) | (t >> (1u << s));
-                }
-                acc[q] = (acc[q] << p.pc) | x;
-            }
-            cnt += p.pc;
-            if (cnt >= 32) {
-                cnt -= 32;
-                --kout;
-#pragma unroll
-                for (int q = 0; q < R; ++q)
-                    if (valid[q]) {
-                        const uint32_t word = (uint32_t)(acc[q] >> cnt);
-                        out[(uint64_t)kout * ld + r[q]] = word;
-                        if (HIST) {
-                            count_digits(hs, kout, prev[q], word);
-                            prev[q] = word;
-                        }
+                const uint32_t word = cur[q] | (x[q] >> s1);
+                cur[q] = __funnelshift_lc(0u, x[q], s2);  // x << s2; 0 for s2 = 32
+                if (valid[q]) {
+                    o[r[q]] = word;
+                    if (HIST) {
+                        count_digits(hs, kout, prev[q], word);
+                        prev[q] = word;
                     }
+                }
             }
         }
     }
@@ -265,7 +304,7 @@ __global__ void __launch_bounds__(kExtractThreads) extract_kernel(const KeyDesc 
     extern __shared__ __align__(128) unsigned char sm[];
     const uint32_t tile_bytes = staged ? rows_per_tile * (uint32_t)k.stride : 0u;
     uint64_t* bar = reinterpret_cast<uint64_t*>(sm + (size_t)kExtractStages * tile_bytes);
-    WordPlan* wp = reinterpret_cast<WordPlan*>(bar + kExtractStages);
+    WordProg* wp = reinterpret_cast<WordProg*>(bar + kExtractStages);
     uint32_t* hsm = reinterpret_cast<uint32_t*>(wp + kMaxKeyWords);
     const uint32_t nctr = passes << rb;
     if constexpr (HIST)
@@ -274,15 +313,7 @@ __global__ void __launch_bounds__(kExtractThreads) extract_kernel(const KeyDesc 
     const uint64_t tiles = (n + rows_per_tile - 1) / rows_per_tile;
     const uint64_t full_tiles = staged ? n / rows_per_tile : 0;  // tiles that arrive by bulk copy
     const uint32_t tid = threadIdx.x;
-    for (uint32_t w = plan.first_word + tid; plan.first_word <= plan.last_word && w <= plan.last_word;
-         w += kExtractThreads) {
-        WordPlan p;
-        p.mask = plan.mask[w];
-        for (int s = 0; s < 5; ++s) p.mv[s] = plan.mv[s][w];
-        p.pc = plan.pc[w];
-        p.pad = 0;
-        wp[w] = p;
-    }
+    stage_programs(plan, wp);
     if (tid == 0 && staged) {
         for (int b = 0; b < kExtractStages; ++b) mbar_init(&bar[b], 1);
         fence_mbar_init();
@@ -384,16 +415,8 @@ __global__ void __launch_bounds__(256) inner_keys_kernel(const KeyDesc k, uint64
                                                          uint32_t* __restrict__ high_rid,
                                                          uint32_t* __restrict__ high_ck, uint16_t* __restrict__ dbit,
                                                          unsigned long long* status) {
-    __shared__ WordPlan wp[kMaxKeyWords];
-    for (uint32_t w = plan.first_word + threadIdx.x; plan.first_word <= plan.last_word && w <= plan.last_word;
-         w += blockDim.x) {
-        WordPlan q;
-        q.mask = plan.mask[w];
-        for (int s = 0; s < 5; ++s) q.mv[s] = plan.mv[s][w];
-        q.pc = plan.pc[w];
-        q.pad = 0;
-        wp[w] = q;
-    }
+    __shared__ WordProg wp[kMaxKeyWords];
+    stage_programs(plan, wp);
     __syncthreads();
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     for (uint64_t g = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; g < lv.inner_entries; g += stride) {
@@ -505,7 +528,7 @@ cudaError_t launch_extract(const KeyDesc& k, int vec, uint64_t n, uint64_t ld, c
                         (uint64_t)stages * rows * k.stride <= 160 * 1024;
     if (!staged) rows = kExtractRows * kExtractThreads;
     const size_t smem = (staged ? (size_t)stages * rows * k.stride : 0) + stages * sizeof(uint64_t) +
-                        sizeof(WordPlan) * kMaxKeyWords + (counting ? sizeof(uint32_t) * ((size_t)passes << rb) : 0);
+                        sizeof(WordProg) * kMaxKeyWords + (counting ? sizeof(uint32_t) * ((size_t)passes << rb) : 0);
     const uint64_t tiles = (n + rows - 1) / rows;
     const uint64_t cap = (uint64_t)num_sms() * 3;
     const unsigned grid = (unsigned)(tiles < cap ? tiles : cap);

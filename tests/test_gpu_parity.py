@@ -196,6 +196,47 @@ def test_extract_masks(W, npos):
     assert np.array_equal(got, oracle.compress(keys, m))
 
 
+def word_mask(words):
+    """D-bitmap (uint64 words, big-endian bit order) from 32-bit mask words."""
+    words = list(words) + [0] * (len(words) % 2)
+    return np.array([(words[2 * i] << 32) | words[2 * i + 1] for i in range(len(words) // 2)], np.uint64)
+
+
+WORD_FORM_MASKS = {
+    # ASCII bytes (one run per byte), the URL column's words
+    "ascii": [0, 0, 0x0000001F, 0x1F1F1F5F, 0x5F180000, 0x7F7F7F7F, 0x7F7F7F7F, 0x7F7F7F7F],
+    # two runs per byte, the DNA column's words
+    "dna": [0x16161616] * 4 + [0x16141400, 0, 0x16161616, 0x16161404],
+    # one- and two-run words: full, top, bottom, middle, split; then scattered bits
+    "runs": [0xFFFFFFFF, 0xFFFFFFF8, 0x000000FF, 0x80000000, 0x00000001, 0x00FFFF00, 0xF000000F, 0x0003C000,
+             0xCA94A8A1, 0x30BA202C, 0x55555555, 0],
+}
+
+
+@pytest.mark.parametrize("name", sorted(WORD_FORM_MASKS))
+@pytest.mark.parametrize("extra_words", [0, 2])
+def test_extract_word_forms(name, extra_words):
+    """Every form of the per-word program (shift-and-mask runs, the network
+    with some or all rounds) and every way a word's bits meet the output words
+    (inside one, ending one exactly, straddling two), on a ragged row count;
+    extra_words > 0 adds whole zero words at the top of the output.  The
+    digit counts of the same pass match the oracle's compressed keys."""
+    words = WORD_FORM_MASKS[name]
+    m = word_mask(words)
+    W = 4 * len(words)
+    rng = np.random.default_rng(len(words) * 7 + extra_words)
+    n = 3 * TILE + 301
+    keys = rng.integers(0, 256, (n, W), dtype=np.uint8)
+    nbits = oracle.popcount(m)
+    K = ck.words_for(nbits) + extra_words
+    want = oracle.compress(keys, m, K)
+    assert np.array_equal(ck_rows(ck.ck_extract(to_dev(keys), m, K), n), want)
+    ckd, hist = ck.ck_extract_hist(to_dev(keys), m, K, 8)
+    assert np.array_equal(ck_rows(ckd, n), want)
+    passes = (nbits + 7) // 8
+    assert np.array_equal(hist[:passes].cpu().numpy().astype(np.int64), oracle_digit_hist(want, nbits, 8))
+
+
 def test_extract_full_mask_is_the_key():
     rng = np.random.default_rng(3)
     keys = rng.integers(0, 256, (1000, 16), dtype=np.uint8)

@@ -55,6 +55,26 @@ def test_compress_network_matches_pext(ckmod):
             assert ckmod.ck_compress_word_host(x, m) == pext32(x, m)
 
 
+def test_word_programs_match_pext(ckmod):
+    """The per-word form the extraction kernel runs: one- and two-run masks
+    (shift-and-mask terms, including a full word and runs touching bit 0 or
+    bit 31), masks of three or more runs (the network with its zero rounds
+    skipped), and mask words of the URL, DNA, Zipf and integer workloads."""
+    rng = np.random.default_rng(1)
+    masks = [0xFFFFFFFF, 0x80000000, 0x00000001, 0x0000001F, 0xFFFFFFF8, 0x7F000000, 0xF000000F,
+             0x00FF0F00, 0x7F7F7F7F, 0x1F1F1F5F, 0x5F180000, 0x16161616, 0x16141400, 0xCA94A8A1,
+             0x30BA202C, 0x55555555, 0xAAAAAAAA]
+    for _ in range(200):                       # random one- and two-run masks
+        a, b = sorted(int(v) for v in rng.integers(0, 33, 2))
+        c, d = sorted(int(v) for v in rng.integers(0, 33, 2))
+        run = lambda lo, hi: ((1 << hi) - 1) ^ ((1 << lo) - 1)
+        masks += [run(a, b), run(a, b) | run(c, d)]
+    masks += [int(x) for x in rng.integers(0, 2**32, 300, dtype=np.uint64)]
+    for m in masks:
+        for x in [0, 0xFFFFFFFF] + [int(v) for v in rng.integers(0, 2**32, 16, dtype=np.uint64)]:
+            assert ckmod.ck_compress_word_program_host(x, m) == pext32(x, m), (hex(x), hex(m))
+
+
 def test_btree_plan_matches_oracle(ckmod):
     for n in (0, 1, 2, 14, 15, 1000, 4097, 10**6, 200 * 10**6):
         for fanout, fill in ((64, 1.0), (256, 1.0), (14, 0.9), (9, 0.9), (10, 0.7)):

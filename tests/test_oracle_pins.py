@@ -322,6 +322,24 @@ def test_theorem2_compressed_order_equals_full_order(seed):
         assert list(oracle.sort_compressed(ck)) == list(perm_full)
 
 
+@pytest.mark.parametrize("K", [1, 2, 3, 4, 8])
+def test_parallel_sort_matches_sort_compressed(K):
+    """The all-cores comparison sort (GCC parallel-mode stable sort) orders
+    compressed keys as the single-thread oracle sort does, ties by row id:
+    many equal values and values that differ only in the low word; 50,000
+    rows so that the parallel sort splits the input across threads."""
+    rng = np.random.default_rng(K)
+    n = 50_000
+    ck = rng.integers(0, 4, (n, K), dtype=np.uint64).astype(np.uint32)   # few distinct values
+    ck[: n // 3, 0] = rng.integers(0, 2**32, n // 3, dtype=np.uint64).astype(np.uint32)
+    for threads in (1, 0):
+        perm, used = oracle.sort_compressed_parallel(ck, threads)
+        assert used >= 1
+        assert list(perm) == list(oracle.sort_compressed(ck))
+    with pytest.raises(ValueError):
+        oracle.sort_compressed_parallel(np.zeros((4, 9), np.uint32))
+
+
 def test_theorem2_needs_every_dbit():
     """Dropping any position of D breaks the order for some row arrangement."""
     g, vals = load_fig2()
