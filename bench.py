@@ -55,6 +55,8 @@ WORKLOADS = {
                 "plain"),
     "urls8m": ("8M 32-byte URL keys (the 64M workload's generator, first 8M rows), fanout 64; profiling size",
                8 * 2**20, "urls", 64, 2_000_000, "plain"),
+    "urls32m": ("32M 32-byte URL keys (the 64M workload's generator, first 32M rows), fanout 64; profiling size "
+                "for one-launch DRAM counters of a radix pass", 32 * 2**20, "urls", 64, 2_000_000, "plain"),
     "zipf256m": ("256M uint64 keys, Zipf(0.9) over 2^40 values under a constant 12-bit tag, learned partition "
                  "(1% sample, 16-unit CDF model, about 32K key-range buckets) vs plain radix, fanout 64",
                  256 * 2**20, "zipf", 64, 8_000_000, "learned"),
@@ -281,6 +283,8 @@ def run_table(args, rank, world, local_rank, own_clocks=True):
         "config": {"workload": desc, "rows": n, "indexes": 6,
                    "key_bytes": [r.key_bits // 8 for r in B.parts], "distinction_bits": [r.nbits for r in B.parts],
                    "ck_words": [r.K for r in B.parts], "digit_bits_autotuned": [r.digit_bits for r in B.parts],
+                   "tile_autotuned": [r.tile for r in B.parts],
+                   "tuned_digit_tile": [[r.digit_bits, r.tile] for r in B.parts],
                    "fanouts": TABLE_FANOUTS, "l2": "inputs larger than L2 (no flush)",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "roofline": {"bound": "hbm", "kernel": "whole batched rebuild (all kernels of 6 indexes)",

@@ -87,7 +87,9 @@ enum {
 #define CK_NO_DBIT 0xFFFFu             /* "no distinction bit": first key or equal keys */
 #define CK_MAX_LEVELS 32u
 #define CK_LD(n) ((((uint64_t)(n)) + 63u) & ~(uint64_t)63u) /* leading dimension of ck columns */
-#define CK_SORT_TILE 4096u /* pairs per radix pass tile (one look-back word per tile and digit) */
+#define CK_SORT_TILE 4096u /* default pairs per radix pass tile (one look-back word per tile and digit) */
+#define CK_SORT_TILE_MIN 2048u /* the tile sizes a sort takes: 2048, 4096, 8192 */
+#define CK_SORT_TILE_MAX 8192u
 
 /* A key column in device memory.  CK_KIND_BYTES: binary-comparable byte
  * strings (fixed-size strings as they are, varchar with its terminating NUL and
@@ -229,6 +231,10 @@ typedef struct ck_sort_opts {
                             ck_in as ck_extract_hist writes them (same digit_bits); the
                             sort then skips its own counting pass over the keys.  NULL:
                             counted here. */
+    uint32_t tile;       /* pairs per radix pass tile: 0 = CK_SORT_TILE (4096), or 2048 /
+                            8192 (see ck_autotune_sort).  The workspace depends on it:
+                            size it with the same opts. */
+    uint32_t reserved;   /* 0 */
 } ck_sort_opts;
 
 /* Only the permutation is wanted: ck_out is used as scratch and its contents
@@ -622,6 +628,7 @@ typedef struct ck_index_job {
     const uint64_t* dmask;  /* HOST, the stored D-bitmap of the column */
     uint32_t ck_words;      /* words per compressed key */
     uint32_t digit_bits;    /* 0 = 8 */
+    uint32_t tile;          /* radix pass tile, 0 = CK_SORT_TILE; see ck_autotune_sort */
     uint32_t fanout;
     float fill;
     uint32_t* ck;           /* device, ck_words * CK_LD(n): extracted keys */
@@ -643,19 +650,22 @@ ck_status ck_graph_destroy(ck_graph graph);
 
 /* ---------------------------------------------------------------------------
  * ck_autotune_sort -- picks the radix digit width (4 .. 11, hence the pass
- * count) for one index by timing ck_sort on its own extracted keys: every
- * width whose workspace fits ws runs once untimed and `reps` times timed with
- * CUDA events on `stream`; the fastest median wins.  The result is kept in a
- * text cache file (one line per GPU name, n rounded up to a power of two,
- * ck_words and nbits) when cache_path is not NULL, and read from it when
+ * count) and the pass tile (2048, 4096 or 8192 pairs) for one index by timing
+ * ck_sort on its own extracted keys: every (width, tile) whose workspace fits
+ * ws runs once untimed and `reps` times timed with CUDA events on `stream`;
+ * the fastest median wins.  best_tile == NULL keeps the default tile and
+ * tunes the width alone.  The result is kept in a text cache file (one line
+ * per GPU name, n rounded up to a power of two, ck_words, nbits and whether
+ * the tile was tuned) when cache_path is not NULL, and read from it when
  * present, in which case nothing runs.  Synchronises `stream`.
  *   ck_in, n, ck_words, nbits  as ck_sort (ck_in is read only).
  *   ck_out, rid_out            scratch outputs of the trial sorts.
- *   best_digit_bits, best_ms   HOST outputs (best_ms may be NULL; 0 from cache).
- * Errors: CK_EINVAL, CK_ENOMEM (no width fits ws), CK_ECUDA. */
+ *   best_digit_bits, best_tile, best_ms   HOST outputs (best_tile and best_ms
+ *                              may be NULL; best_ms is 0 from the cache).
+ * Errors: CK_EINVAL, CK_ENOMEM (no candidate fits ws), CK_ECUDA. */
 ck_status ck_autotune_sort(const uint32_t* ck_in, uint32_t* ck_out, uint32_t* rid_out, uint64_t n, uint32_t ck_words,
                            uint32_t nbits, void* ws, size_t ws_bytes, uint32_t reps, const char* cache_path,
-                           uint32_t* best_digit_bits, float* best_ms, ck_stream stream);
+                           uint32_t* best_digit_bits, uint32_t* best_tile, float* best_ms, ck_stream stream);
 
 /* ---------------------------------------------------------------------------
  * Device status.  ck_device_status synchronises the device, returns the first

@@ -26,6 +26,7 @@ CK_MAX_KEY_BYTES = 512
 CK_NO_DBIT = 0xFFFF
 CK_MAX_LEVELS = 32
 CK_SORT_TILE = 4096
+CK_SORT_TILES = (2048, 4096, 8192)
 CK_INJECT_STALL_FIRST_TILE = 1
 CK_SORT_PERM_ONLY = 1
 CK_MAX_PARTIAL_KEY_BITS = 32
@@ -56,7 +57,8 @@ class ck_column(ctypes.Structure):
 
 class ck_sort_opts(ctypes.Structure):
     _fields_ = [("digit_bits", ctypes.c_uint32), ("spin_limit", ctypes.c_uint32), ("inject", ctypes.c_uint32),
-                ("flags", ctypes.c_uint32), ("pass_events", ctypes.c_void_p), ("hist", ctypes.c_void_p)]
+                ("flags", ctypes.c_uint32), ("pass_events", ctypes.c_void_p), ("hist", ctypes.c_void_p),
+                ("tile", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
 
 
 class ck_learned_opts(ctypes.Structure):
@@ -94,7 +96,8 @@ class ck_btree(ctypes.Structure):
 
 class ck_index_job(ctypes.Structure):
     _fields_ = [("col", ck_column), ("dmask", ctypes.c_void_p), ("ck_words", ctypes.c_uint32),
-                ("digit_bits", ctypes.c_uint32), ("fanout", ctypes.c_uint32), ("fill", ctypes.c_float),
+                ("digit_bits", ctypes.c_uint32), ("tile", ctypes.c_uint32), ("fanout", ctypes.c_uint32),
+                ("fill", ctypes.c_float),
                 ("ck", ctypes.c_void_p), ("ck_sorted", ctypes.c_void_p), ("rid_sorted", ctypes.c_void_p),
                 ("tree", ctypes.POINTER(ck_btree)), ("refined_mask", ctypes.c_void_p), ("ws", ctypes.c_void_p),
                 ("ws_bytes", ctypes.c_size_t)]
@@ -135,7 +138,7 @@ def _lib():
         lib.ck_graph_launch.argtypes = [P, P]
         lib.ck_graph_destroy.argtypes = [P]
         lib.ck_autotune_sort.argtypes = [P, P, P, U64, U32, U32, P, ctypes.c_size_t, U32, ctypes.c_char_p,
-                                         ctypes.POINTER(U32), ctypes.POINTER(ctypes.c_float), P]
+                                         ctypes.POINTER(U32), ctypes.POINTER(U32), ctypes.POINTER(ctypes.c_float), P]
         lib.ck_model_separators.argtypes = [P, ctypes.POINTER(ck_btree), U32, U32, P, P, P]
         lib.ck_encode_key.argtypes = [ctypes.POINTER(ck_key_part), U32, U64, P, U32, P]
         lib.ck_insert_workspace_bytes.argtypes = [U64, U32]
@@ -320,9 +323,9 @@ def ck_extract_hist(keys: torch.Tensor, dmask: np.ndarray, ck_words: int, digit_
     return out, hist
 
 
-def _opts(digit_bits=0, spin_limit=0, inject=0, pass_events=None, flags=0, hist=None):
+def _opts(digit_bits=0, spin_limit=0, inject=0, pass_events=None, flags=0, hist=None, tile=0):
     return ck_sort_opts(digit_bits, spin_limit, inject, flags, pass_events,
-                        hist.data_ptr() if hist is not None else None)
+                        hist.data_ptr() if hist is not None else None, tile, 0)
 
 
 def event_handles(events) -> ctypes.Array:
@@ -333,17 +336,18 @@ def event_handles(events) -> ctypes.Array:
     return arr
 
 
-def ck_sort_workspace_bytes(n: int, ck_words: int, nbits: int, digit_bits: int = 0) -> int:
-    o = _opts(digit_bits)
+def ck_sort_workspace_bytes(n: int, ck_words: int, nbits: int, digit_bits: int = 0, tile: int = 0) -> int:
+    o = _opts(digit_bits, tile=tile)
     return int(_lib().ck_sort_workspace_bytes(n, ck_words, nbits, ctypes.byref(o)))
 
 
 def ck_sort(ck_in: torch.Tensor, rid_in: torch.Tensor | None, ck_out: torch.Tensor, rid_out: torch.Tensor, n: int,
             ck_words: int, nbits: int, ws: torch.Tensor, digit_bits: int = 0, spin_limit: int = 0, inject: int = 0,
-            pass_events=None, perm_only: bool = False, hist: torch.Tensor | None = None, stream=None) -> None:
+            pass_events=None, perm_only: bool = False, hist: torch.Tensor | None = None, tile: int = 0,
+            stream=None) -> None:
     o = _opts(digit_bits, spin_limit, inject,
               ctypes.cast(pass_events, ctypes.c_void_p) if pass_events is not None else None,
-              CK_SORT_PERM_ONLY if perm_only else 0, hist)
+              CK_SORT_PERM_ONLY if perm_only else 0, hist, tile)
     _check(_lib().ck_sort(_ptr(ck_in), _ptr(rid_in), _ptr(ck_out), _ptr(rid_out), n, ck_words, nbits,
                           ctypes.byref(o), _ptr(ws), ws.numel() * ws.element_size(), _stream(stream)), "ck_sort")
 
@@ -492,15 +496,19 @@ def ck_graph_destroy(graph) -> None:
 
 
 def ck_autotune_sort(ck_in: torch.Tensor, ck_out: torch.Tensor, rid_out: torch.Tensor, n: int, ck_words: int,
-                     nbits: int, ws: torch.Tensor, reps: int = 3, cache_path: str | None = None, stream=None):
-    """Returns (best digit width, its median ms; 0.0 when read from the cache)."""
+                     nbits: int, ws: torch.Tensor, reps: int = 3, cache_path: str | None = None,
+                     tune_tile: bool = True, stream=None):
+    """Returns (best digit width, best tile, its median ms; 0.0 when read from
+    the cache).  tune_tile=False keeps the default tile."""
     d = ctypes.c_uint32(0)
+    t = ctypes.c_uint32(CK_SORT_TILE)
     ms = ctypes.c_float(0.0)
     _check(_lib().ck_autotune_sort(_ptr(ck_in), _ptr(ck_out), _ptr(rid_out), n, ck_words, nbits, _ptr(ws),
                                    ws.numel() * ws.element_size(), reps,
-                                   cache_path.encode() if cache_path else None, ctypes.byref(d), ctypes.byref(ms),
+                                   cache_path.encode() if cache_path else None, ctypes.byref(d),
+                                   ctypes.byref(t) if tune_tile else None, ctypes.byref(ms),
                                    _stream(stream)), "ck_autotune_sort")
-    return int(d.value), float(ms.value)
+    return int(d.value), int(t.value), float(ms.value)
 
 
 def ck_model_separators(params: torch.Tensor, shape: ck_btree_shape, arrays: dict, ck_words: int, nbits: int,

@@ -294,7 +294,7 @@ ck_status ck_extract_hist(const ck_column* col, const uint64_t* dmask, uint32_t 
 
 size_t ck_sort_workspace_bytes(uint64_t n, uint32_t ck_words, uint32_t nbits, const ck_sort_opts* opts) {
     SortPlan p;
-    if (!make_sort_plan(n, ck_words, nbits, opts ? opts->digit_bits : 0, &p)) return 0;
+    if (!make_sort_plan(n, ck_words, nbits, opts ? opts->digit_bits : 0, &p, 0, opts ? opts->tile : 0)) return 0;
     return p.total;
 }
 
@@ -302,13 +302,15 @@ ck_status ck_sort(const uint32_t* ck_in, const uint32_t* rid_in, uint32_t* ck_ou
                   uint32_t ck_words, uint32_t nbits, const ck_sort_opts* opts, void* ws, size_t ws_bytes,
                   ck_stream stream) {
     if (n > CK_MAX_ROWS || ck_words == 0 || nbits > 32u * ck_words) return CK_EINVAL;
-    if (opts && ((opts->flags & ~CK_SORT_FLAGS_ALL) != 0 ||
-                 (opts->digit_bits != 0 && (opts->digit_bits < 4 || opts->digit_bits > 11))))
+    if (opts && ((opts->flags & ~CK_SORT_FLAGS_ALL) != 0 || opts->reserved != 0 ||
+                 (opts->digit_bits != 0 && (opts->digit_bits < 4 || opts->digit_bits > 11)) ||
+                 (opts->tile != 0 && opts->tile != 2048 && opts->tile != 4096 && opts->tile != 8192)))
         return CK_EINVAL;
     if (n == 0) return CK_OK;
     if (!ck_in || !ck_out || !rid_out) return CK_EINVAL;
     SortPlan p;
-    if (!make_sort_plan(n, ck_words, nbits, opts ? opts->digit_bits : 0, &p)) return CK_EINVAL;
+    if (!make_sort_plan(n, ck_words, nbits, opts ? opts->digit_bits : 0, &p, 0, opts ? opts->tile : 0))
+        return CK_EINVAL;
     if (p.passes > 0 && (!ws || ws_bytes < p.total)) return CK_ENOMEM;
     if (p.passes > 0 && (reinterpret_cast<uintptr_t>(ws) & 255)) return CK_EINVAL;
     const uint32_t spin = (opts && opts->spin_limit) ? opts->spin_limit : (1u << 22);

@@ -92,6 +92,7 @@ ck_status build_batched_locked(const ck_index_job* jobs, uint32_t njobs, ck_stre
         ck_sort_opts o;
         memset(&o, 0, sizeof(o));
         o.digit_bits = jb.digit_bits;
+        o.tile = jb.tile;
         // room after the sort's workspace for the digit counts: take them while extracting
         const uint32_t rb = jb.digit_bits ? jb.digit_bits : 8u;
         const size_t sort_bytes = (ck_sort_workspace_bytes(jb.col.n, jb.ck_words, nbits, &o) + 255) & ~(size_t)255;
@@ -171,7 +172,7 @@ ck_status ck_graph_destroy(ck_graph graph) {
 
 ck_status ck_autotune_sort(const uint32_t* ck_in, uint32_t* ck_out, uint32_t* rid_out, uint64_t n, uint32_t ck_words,
                            uint32_t nbits, void* ws, size_t ws_bytes, uint32_t reps, const char* cache_path,
-                           uint32_t* best_digit_bits, float* best_ms, ck_stream stream) {
+                           uint32_t* best_digit_bits, uint32_t* best_tile, float* best_ms, ck_stream stream) {
     if (!best_digit_bits || !ck_in || !ck_out || !rid_out || ck_words == 0 || n == 0) return CK_EINVAL;
     if (reps == 0) reps = 3;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
@@ -180,20 +181,27 @@ ck_status ck_autotune_sort(const uint32_t* ck_in, uint32_t* ck_out, uint32_t* ri
     if (cudaGetDevice(&dev) != cudaSuccess || cudaGetDeviceProperties(&prop, dev) != cudaSuccess) return CK_ECUDA;
     uint64_t nb = 1;
     while (nb < n) nb <<= 1;
+    const bool tune_tile = best_tile != nullptr;
     char key[384];
-    snprintf(key, sizeof(key), "%s|%llu|%u|%u", prop.name, (unsigned long long)nb, ck_words, nbits);
-    if (cache_path) {  // cached choice?
+    snprintf(key, sizeof(key), "%s|%llu|%u|%u|%s", prop.name, (unsigned long long)nb, ck_words, nbits,
+             tune_tile ? "tile" : "width");
+    if (cache_path) {  // cached choice?  lines: key|digit bits|tile
         if (FILE* f = fopen(cache_path, "r")) {
             char line[512];
             while (fgets(line, sizeof(line), f)) {
-                char* bar = strrchr(line, '|');
-                if (!bar) continue;
-                *bar = 0;
+                char* bar2 = strrchr(line, '|');
+                if (!bar2) continue;
+                *bar2 = 0;
+                char* bar1 = strrchr(line, '|');
+                if (!bar1) continue;
+                *bar1 = 0;
                 if (strcmp(line, key) == 0) {
-                    const unsigned d = (unsigned)strtoul(bar + 1, nullptr, 10);
-                    if (d >= 4 && d <= 11) {
+                    const unsigned d = (unsigned)strtoul(bar1 + 1, nullptr, 10);
+                    const unsigned t = (unsigned)strtoul(bar2 + 1, nullptr, 10);
+                    if (d >= 4 && d <= 11 && (t == 2048 || t == 4096 || t == 8192)) {
                         fclose(f);
                         *best_digit_bits = d;
+                        if (best_tile) *best_tile = t;
                         if (best_ms) *best_ms = 0.0f;
                         return CK_OK;
                     }
@@ -204,48 +212,54 @@ ck_status ck_autotune_sort(const uint32_t* ck_in, uint32_t* ck_out, uint32_t* ri
     }
     cudaEvent_t e0, e1;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return CK_ECUDA;
-    uint32_t best = 0;
+    uint32_t best = 0, best_t_tile = CK_SORT_TILE;
     float best_t = 0.0f;
-    for (uint32_t d = 4; d <= 11; ++d) {
-        ck_sort_opts o;
-        memset(&o, 0, sizeof(o));
-        o.digit_bits = d;
-        if (ck_sort_workspace_bytes(n, ck_words, nbits, &o) > ws_bytes) continue;
-        ck_status st = ck_sort(ck_in, nullptr, ck_out, rid_out, n, ck_words, nbits, &o, ws, ws_bytes, stream);
-        if (st != CK_OK) {
-            cudaEventDestroy(e0);
-            cudaEventDestroy(e1);
-            return st;
-        }
-        std::vector<float> t;
-        for (uint32_t r = 0; r < reps; ++r) {
-            cudaEventRecord(e0, s);
-            ck_sort(ck_in, nullptr, ck_out, rid_out, n, ck_words, nbits, &o, ws, ws_bytes, stream);
-            cudaEventRecord(e1, s);
-            if (cudaEventSynchronize(e1) != cudaSuccess) {
+    const uint32_t tiles[3] = {CK_SORT_TILE, 2048u, 8192u};
+    for (uint32_t ti = 0; ti < (tune_tile ? 3u : 1u); ++ti)
+        for (uint32_t d = 4; d <= 11; ++d) {
+            ck_sort_opts o;
+            memset(&o, 0, sizeof(o));
+            o.digit_bits = d;
+            o.tile = tiles[ti];
+            const size_t need = ck_sort_workspace_bytes(n, ck_words, nbits, &o);
+            if (need == 0 || need > ws_bytes) continue;
+            ck_status st = ck_sort(ck_in, nullptr, ck_out, rid_out, n, ck_words, nbits, &o, ws, ws_bytes, stream);
+            if (st != CK_OK) {
                 cudaEventDestroy(e0);
                 cudaEventDestroy(e1);
-                return CK_ECUDA;
+                return st;
             }
-            float ms = 0.0f;
-            cudaEventElapsedTime(&ms, e0, e1);
-            t.push_back(ms);
+            std::vector<float> t;
+            for (uint32_t r = 0; r < reps; ++r) {
+                cudaEventRecord(e0, s);
+                ck_sort(ck_in, nullptr, ck_out, rid_out, n, ck_words, nbits, &o, ws, ws_bytes, stream);
+                cudaEventRecord(e1, s);
+                if (cudaEventSynchronize(e1) != cudaSuccess) {
+                    cudaEventDestroy(e0);
+                    cudaEventDestroy(e1);
+                    return CK_ECUDA;
+                }
+                float ms = 0.0f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                t.push_back(ms);
+            }
+            std::sort(t.begin(), t.end());
+            const float med = t[t.size() / 2];
+            if (best == 0 || med < best_t) {
+                best = d;
+                best_t_tile = tiles[ti];
+                best_t = med;
+            }
         }
-        std::sort(t.begin(), t.end());
-        const float med = t[t.size() / 2];
-        if (best == 0 || med < best_t) {
-            best = d;
-            best_t = med;
-        }
-    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (best == 0) return CK_ENOMEM;
     *best_digit_bits = best;
+    if (best_tile) *best_tile = best_t_tile;
     if (best_ms) *best_ms = best_t;
     if (cache_path)
         if (FILE* f = fopen(cache_path, "a")) {
-            fprintf(f, "%s|%u\n", key, best);
+            fprintf(f, "%s|%u|%u\n", key, best, best_t_tile);
             fclose(f);
         }
     return CK_OK;

@@ -450,8 +450,9 @@ struct PassArgs {
 };
 
 // One onesweep pass with digit width rb (4..11); tiles = ceil(n / kPassTile).
+// tile: pairs per tile, kPassTile (default), 2048 or 8192.
 cudaError_t launch_onesweep_pass(uint32_t rb, const PassArgs& a, const PassArrays& arrays, uint32_t tiles,
-                                 cudaStream_t s);
+                                 cudaStream_t s, uint32_t tile = kPassTile);
 // Exclusive scan, in place, of `sets` histograms of 2^rb bins (rb <= 8).
 cudaError_t launch_bucket_scan(uint32_t* hist, uint32_t sets, uint32_t rb, cudaStream_t s);
 
@@ -461,7 +462,9 @@ struct SortPlan {
     size_t off_hist, off_counter, off_lookback, off_alt_ck, off_alt_rid, total;
 };
 // ld == 0 selects CK_LD(n); a larger ld sorts a segment of wider arrays in place.
-bool make_sort_plan(uint64_t n, uint32_t K, uint32_t nbits, uint32_t digit_bits, SortPlan* p, uint64_t ld = 0);
+// tile: pairs per radix tile, 0 = kPassTile; 2048, 4096 and 8192 are valid.
+bool make_sort_plan(uint64_t n, uint32_t K, uint32_t nbits, uint32_t digit_bits, SortPlan* p, uint64_t ld = 0,
+                    uint32_t tile = 0);
 // gate != NULL: every kernel of the sort returns at once unless *gate != 0
 // when it runs (a sort the device decides to need; the launches are made
 // either way, so the host never waits for the decision).  A gated sort must

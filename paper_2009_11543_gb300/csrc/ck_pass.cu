@@ -17,29 +17,35 @@ namespace ck {
 constexpr uint32_t kFlagAgg = 1u << 30;
 constexpr uint32_t kFlagPrefix = 2u << 30;
 constexpr uint32_t kValMask = (1u << 30) - 1;
-// Two shapes of the pass block over the same 4096-pair tile: 256 threads with
-// 16 pairs each (more independent work per thread; 64 registers and a
+// Shapes of the pass block.  The default 4096-pair tile has two: 256 threads
+// with 16 pairs each (more independent work per thread; 64 registers and a
 // two-slot staging ring, so four blocks fit on an SM), or 512 threads with 8
 // pairs each (three blocks), which is faster only for small passes of one key
-// word that stay in L2.
-constexpr int kTile = kPassTile;  // pairs per tile
+// word that stay in L2.  The tile size is a tuning knob of the sort
+// (ck_sort_opts.tile): 2048-pair tiles take 256 threads with 8 pairs (six
+// blocks per SM), 8192-pair tiles 512 threads with 16 pairs (two blocks).
+// Smaller tiles mean more look-back words and more blocks in flight, larger
+// ones fewer tiles and longer contiguous runs per digit.
 constexpr int kPassThreadsWide = 512, kPassThreadsDeep = 256;
 constexpr uint32_t kDeepMinArrays = 3;           // deep shape from this many arrays on,
 constexpr uint64_t kWideMaxPairs = 1ull << 22;   // or above this many pairs
 constexpr int kRing = 2;                         // staging buffers per block
-constexpr int kPassBlocksPerSM = 3;              // resident blocks of the 512-thread shape
-constexpr int kPassDeepBlocksPerSM = 4;          // of the 256-thread shape
+
+// resident blocks per SM of a (threads, tile) shape
+__host__ __device__ constexpr int pass_blocks_per_sm(int threads, int tile) {
+    return tile == 2048 ? 6 : tile == 8192 ? 2 : threads == 256 ? 4 : 3;
+}
 
 // ------------------------------------------------------------------ pass
 // Shared memory of one pass block: a ring of kRing staging buffers (one array
 // of the tile each), per-warp digit counters, per-slot source position,
 // per-digit tile counts and destinations, and the ring's mbarriers.
-template <int RB, int THREADS>
+template <int RB, int THREADS, int TILE>
 struct PassSmem {
     static constexpr int BINS = 1 << RB, WARPS = THREADS / 32;
-    uint32_t stage[kRing][kTile];
-    uint16_t whist[WARPS][BINS];  // counts <= kTile fit 16 bits
-    uint16_t src_pos[kTile];
+    uint32_t stage[kRing][TILE];
+    uint16_t whist[WARPS][BINS];  // counts <= TILE fit 16 bits
+    uint16_t src_pos[TILE];
     uint32_t tile_total[BINS];
     uint32_t tile_excl[BINS];
     int32_t dest_base[BINS];
@@ -52,14 +58,14 @@ struct PassSmem {
 // with plain loads (the shape of a gated sort that usually does not run: when
 // the gate is shut, a few hundred blocks return at once instead of one block
 // per tile).  Without PERSIST every block takes one tile.
-template <int RB, int THREADS, bool PERSIST>
-__global__ void __launch_bounds__(THREADS, THREADS == 256 ? kPassDeepBlocksPerSM : kPassBlocksPerSM)
+template <int RB, int THREADS, bool PERSIST, int TILE>
+__global__ void __launch_bounds__(THREADS, pass_blocks_per_sm(THREADS, TILE))
     onesweep_pass_kernel(const PassArgs a, const __grid_constant__ PassArrays arr) {
-    constexpr int kPassThreads = THREADS;
+    constexpr int kPassThreads = THREADS, kTile = TILE;
     constexpr int BINS = 1 << RB, WARPS = THREADS / 32, ITEMS = kTile / THREADS, WITEMS = 32 * ITEMS;
     static_assert(ITEMS * THREADS == kTile, "tile size of the pass kernel");
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    PassSmem<RB, THREADS>& S = *reinterpret_cast<PassSmem<RB, THREADS>*>(smem_raw);
+    PassSmem<RB, THREADS, TILE>& S = *reinterpret_cast<PassSmem<RB, THREADS, TILE>*>(smem_raw);
 
     if (a.gate && *(volatile const uint32_t*)a.gate != a.gate_run) return;  // decided on the device
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -289,47 +295,55 @@ __global__ void __launch_bounds__(THREADS, THREADS == 256 ? kPassDeepBlocksPerSM
 
 // Launches one pass; `arrays` lists the arrays in staging order.  A pass
 // gated to run only on the device's say-so (a fallback) takes the persistent
-// shape.
-template <int RB, int THREADS>
+// shape (default tile only).
+template <int RB, int THREADS, int TILE>
 static cudaError_t launch_pass_shape(const PassArgs& a_in, const PassArrays& arrays, uint32_t tiles, cudaStream_t s) {
-    constexpr size_t smem = sizeof(PassSmem<RB, THREADS>);
-    static_assert(sizeof(PassSmem<RB, THREADS>) <= 227 * 1024, "pass block exceeds shared memory");
+    constexpr size_t smem = sizeof(PassSmem<RB, THREADS, TILE>);
+    static_assert(sizeof(PassSmem<RB, THREADS, TILE>) <= 227 * 1024, "pass block exceeds shared memory");
     PassArgs a = a_in;
     a.tiles = tiles;
     const bool persist = a.gate != nullptr && a.gate_run != 0;
-    const void* fn = persist ? (const void*)onesweep_pass_kernel<RB, THREADS, true>
-                             : (const void*)onesweep_pass_kernel<RB, THREADS, false>;
+    if (persist && TILE != kPassTile) return cudaErrorInvalidValue;
+    const void* fn = persist ? (const void*)onesweep_pass_kernel<RB, THREADS, true, kPassTile>
+                             : (const void*)onesweep_pass_kernel<RB, THREADS, false, TILE>;
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     if (persist) {
-        const uint32_t per_sm = THREADS == 256 ? kPassDeepBlocksPerSM : kPassBlocksPerSM;
+        const uint32_t per_sm = pass_blocks_per_sm(THREADS, kPassTile);
         const uint32_t grid = (uint32_t)min((uint64_t)tiles, (uint64_t)num_sms() * per_sm);
-        onesweep_pass_kernel<RB, THREADS, true><<<grid, THREADS, smem, s>>>(a, arrays);
+        onesweep_pass_kernel<RB, THREADS, true, kPassTile><<<grid, THREADS, smem, s>>>(a, arrays);
     } else {
-        onesweep_pass_kernel<RB, THREADS, false><<<tiles, THREADS, smem, s>>>(a, arrays);
+        onesweep_pass_kernel<RB, THREADS, false, TILE><<<tiles, THREADS, smem, s>>>(a, arrays);
     }
     count_launch();
     return cudaGetLastError();
 }
 
 template <int RB>
-static cudaError_t launch_pass(const PassArgs& a, const PassArrays& arrays, uint32_t tiles, cudaStream_t s) {
-    return a.narr >= kDeepMinArrays || a.n > kWideMaxPairs
-               ? launch_pass_shape<RB, kPassThreadsDeep>(a, arrays, tiles, s)
-               : launch_pass_shape<RB, kPassThreadsWide>(a, arrays, tiles, s);
+static cudaError_t launch_pass(const PassArgs& a, const PassArrays& arrays, uint32_t tile, uint32_t tiles,
+                               cudaStream_t s) {
+    switch (tile) {
+        case 2048: return launch_pass_shape<RB, kPassThreadsDeep, 2048>(a, arrays, tiles, s);
+        case 8192: return launch_pass_shape<RB, kPassThreadsWide, 8192>(a, arrays, tiles, s);
+        case kPassTile:
+            return a.narr >= kDeepMinArrays || a.n > kWideMaxPairs
+                       ? launch_pass_shape<RB, kPassThreadsDeep, kPassTile>(a, arrays, tiles, s)
+                       : launch_pass_shape<RB, kPassThreadsWide, kPassTile>(a, arrays, tiles, s);
+        default: return cudaErrorInvalidValue;
+    }
 }
 
 cudaError_t launch_onesweep_pass(uint32_t rb, const PassArgs& a, const PassArrays& arrays, uint32_t tiles,
-                                 cudaStream_t s) {
+                                 cudaStream_t s, uint32_t tile) {
     switch (rb) {
-        case 4: return launch_pass<4>(a, arrays, tiles, s);
-        case 5: return launch_pass<5>(a, arrays, tiles, s);
-        case 6: return launch_pass<6>(a, arrays, tiles, s);
-        case 7: return launch_pass<7>(a, arrays, tiles, s);
-        case 8: return launch_pass<8>(a, arrays, tiles, s);
-        case 9: return launch_pass<9>(a, arrays, tiles, s);
-        case 10: return launch_pass<10>(a, arrays, tiles, s);
-        case 11: return launch_pass<11>(a, arrays, tiles, s);
+        case 4: return launch_pass<4>(a, arrays, tile, tiles, s);
+        case 5: return launch_pass<5>(a, arrays, tile, tiles, s);
+        case 6: return launch_pass<6>(a, arrays, tile, tiles, s);
+        case 7: return launch_pass<7>(a, arrays, tile, tiles, s);
+        case 8: return launch_pass<8>(a, arrays, tile, tiles, s);
+        case 9: return launch_pass<9>(a, arrays, tile, tiles, s);
+        case 10: return launch_pass<10>(a, arrays, tile, tiles, s);
+        case 11: return launch_pass<11>(a, arrays, tile, tiles, s);
         default: return cudaErrorInvalidValue;
     }
 }

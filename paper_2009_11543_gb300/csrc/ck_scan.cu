@@ -176,6 +176,10 @@ __device__ __forceinline__ void count_digits(const HistSink& h, uint32_t k, uint
 }
 
 // The network rounds selected by RM (bit s: round s) on R values at once.
+// The moved bits t land on zeros of x ^ t, so the OR of a round is an
+// addition, and t >> 2^s is the high word of t * 2^(32 - 2^s): one
+// multiply-add (on the multiply pipe) in place of a shift and an OR (on the
+// integer pipe, which the extraction saturates).
 template <uint32_t RM, int R>
 __device__ __forceinline__ void network_rounds(uint32_t (&x)[R], const WordProg& p) {
 #pragma unroll
@@ -184,13 +188,16 @@ __device__ __forceinline__ void network_rounds(uint32_t (&x)[R], const WordProg&
 #pragma unroll
             for (int q = 0; q < R; ++q) {
                 const uint32_t t = x[q] & p.mv[s];
-                x[q] = (x[q] ^ t) | (t >> (1u << s));
+                x[q] = __umulhi(t, 1u << (32 - (1u << s))) + (x[q] ^ t);
             }
         }
 }
 
-// x[q] = compressed bits of word w[q] under program p.
-template <int R>
+// x[q] = compressed bits of word w[q] under program p.  ALL: run every round
+// of the network (a round with a zero move mask changes nothing) instead of
+// branching to the rounds the word needs; the host picks ALL when most words
+// need most rounds, where the branch costs more than it saves.
+template <int R, bool ALL>
 __device__ __forceinline__ void compress_word(const WordProg& p, const uint32_t (&w)[R], uint32_t (&x)[R]) {
     if (p.ctl & kProgRuns) {
 #pragma unroll
@@ -199,6 +206,10 @@ __device__ __forceinline__ void compress_word(const WordProg& p, const uint32_t 
     }
 #pragma unroll
     for (int q = 0; q < R; ++q) x[q] = w[q] & p.mask;
+    if (ALL) {
+        network_rounds<31, R>(x, p);
+        return;
+    }
 #define CK_ROUNDS_CASE(M) \
     case M: network_rounds<M, R>(x, p); break;
     switch (p.ctl & 31u) {
@@ -223,7 +234,7 @@ __device__ __forceinline__ void stage_programs(const ExtractPlan& plan, WordProg
 
 // Compress of R rows at once: row q's chunks come from rows[q] (global or
 // shared memory); each word's program is read once for all R rows.
-template <int VEC, int R, bool HIST = false>
+template <int VEC, int R, bool HIST = false, bool ALL = false>
 __device__ __forceinline__ void extract_rows(const KeyDesc& k, const unsigned char* const (&rows)[R],
                                              const uint64_t (&r)[R], const bool (&valid)[R], uint64_t ld,
                                              const ExtractPlan& plan, const WordProg* wp, uint32_t* __restrict__ out,
@@ -255,7 +266,7 @@ __device__ __forceinline__ void extract_rows(const KeyDesc& k, const unsigned ch
             uint32_t wi[R], x[R];
 #pragma unroll
             for (int q = 0; q < R; ++q) wi[q] = w[q][i];
-            compress_word<R>(p, wi, x);
+            compress_word<R, ALL>(p, wi, x);
             const uint32_t s1 = (p.ctl >> 8) & 63u;
             if (!(p.ctl & kProgEmit)) {
 #pragma unroll
@@ -285,14 +296,15 @@ __device__ __forceinline__ void extract_rows(const KeyDesc& k, const unsigned ch
 // because row_stride * rows_per_tile is a multiple of 16) arrives in a ring of
 // kExtractStages shared buffers by one bulk copy, issued kExtractStages tiles
 // ahead.  The ragged last tile is read straight from global memory.  Each
-// thread extracts kExtractRows rows of a tile together.
+// thread extracts kExtractRows rows of a tile together, as often as the tile
+// needs.
 constexpr int kExtractStages = 4;       // ring depth without digit counting
 constexpr int kExtractStagesHist = 3;   // with it (room for the counters, three blocks per SM)
 constexpr int kExtractThreads = 256;
 constexpr int kExtractRows = 2;
 
-template <int VEC, bool HIST>
-__global__ void __launch_bounds__(kExtractThreads) extract_kernel(const KeyDesc k, uint64_t n, uint64_t ld,
+template <int VEC, bool HIST, bool ALL>
+__global__ void __launch_bounds__(kExtractThreads, 3) extract_kernel(const KeyDesc k, uint64_t n, uint64_t ld,
                                                                   uint32_t rows_per_tile, uint32_t staged,
                                                                   const __grid_constant__ ExtractPlan plan,
                                                                   uint32_t* __restrict__ out, uint32_t spin_limit,
@@ -350,7 +362,7 @@ __global__ void __launch_bounds__(kExtractThreads) extract_kernel(const KeyDesc 
                 r[q] = r0 + j;
                 rows[q] = base + (valid[q] ? j : 0) * k.stride;
             }
-            extract_rows<VEC, R, HIST>(k, rows, r, valid, ld, plan, wp, out, hs);
+            extract_rows<VEC, R, HIST, ALL>(k, rows, r, valid, ld, plan, wp, out, hs);
         }
         __syncthreads();  // stage i % kExtractStages is free again
         if (tid == 0) {
@@ -517,12 +529,11 @@ cudaError_t launch_btree_keys(const KeyDesc& k, int vec, uint64_t n, const uint3
 cudaError_t launch_extract(const KeyDesc& k, int vec, uint64_t n, uint64_t ld, const ExtractPlan& plan,
                            uint32_t* ck_out, cudaStream_t s, uint32_t* hist, uint32_t rb, uint32_t passes) {
     // rows per tile: a multiple of 16 (so that tiles start 16-byte aligned),
-    // about 16 KB of keys, at most kExtractRows rows per thread.  Staging needs
-    // a 16-byte aligned column and a ring that fits shared memory.
+    // about 16 KB of keys (short keys: several rows per thread and tile).
+    // Staging needs a 16-byte aligned column and a ring that fits shared memory.
     const bool counting = hist != nullptr && passes > 0;
     const uint32_t stages = counting ? kExtractStagesHist : kExtractStages;
     uint32_t rows = (uint32_t)(16384 / k.stride) & ~15u;
-    if (rows > (uint32_t)(kExtractRows * kExtractThreads)) rows = kExtractRows * kExtractThreads;
     if (rows < 16) rows = 16;
     const bool staged = (reinterpret_cast<uintptr_t>(k.base) & 15) == 0 &&
                         (uint64_t)stages * rows * k.stride <= 160 * 1024;
@@ -533,22 +544,39 @@ cudaError_t launch_extract(const KeyDesc& k, int vec, uint64_t n, uint64_t ld, c
     const uint64_t cap = (uint64_t)num_sms() * 3;
     const unsigned grid = (unsigned)(tiles < cap ? tiles : cap);
     cudaError_t e = cudaSuccess;
-#define CK_EXTRACT_LAUNCH(V, H)                                                                                 \
-    e = cudaFuncSetAttribute(extract_kernel<V, H>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);    \
+    // every network round for all words when the network words need, on
+    // average, at least four of the five rounds
+    uint32_t nnet = 0, rounds = 0;
+    for (uint32_t w = plan.first_word; plan.first_word <= plan.last_word && w <= plan.last_word; ++w)
+        if (plan.prog[w].mask && !(plan.prog[w].ctl & kProgRuns)) {
+            ++nnet;
+            rounds += (uint32_t)__builtin_popcount(plan.prog[w].ctl & 31u);
+        }
+    const bool all = nnet > 0 && rounds >= 4 * nnet;
+#define CK_EXTRACT_LAUNCH(V, H, A)                                                                              \
+    e = cudaFuncSetAttribute(extract_kernel<V, H, A>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
     if (e != cudaSuccess) return e;                                                                             \
-    extract_kernel<V, H><<<grid, kExtractThreads, smem, s>>>(k, n, ld, rows, staged ? 1u : 0u, plan, ck_out,     \
-                                                              kDefaultSpin, status_ptr(), hist, rb, passes);
-#define CK_EXTRACT_VEC(H)                          \
-    switch (vec) {                                 \
-        case 16: CK_EXTRACT_LAUNCH(16, H); break;  \
-        case 8: CK_EXTRACT_LAUNCH(8, H); break;    \
-        case 4: CK_EXTRACT_LAUNCH(4, H); break;    \
-        default: CK_EXTRACT_LAUNCH(1, H); break;   \
+    extract_kernel<V, H, A><<<grid, kExtractThreads, smem, s>>>(k, n, ld, rows, staged ? 1u : 0u, plan, ck_out,  \
+                                                                 kDefaultSpin, status_ptr(), hist, rb, passes);
+#define CK_EXTRACT_VEC(H, A)                          \
+    switch (vec) {                                    \
+        case 16: CK_EXTRACT_LAUNCH(16, H, A); break;  \
+        case 8: CK_EXTRACT_LAUNCH(8, H, A); break;    \
+        case 4: CK_EXTRACT_LAUNCH(4, H, A); break;    \
+        default: CK_EXTRACT_LAUNCH(1, H, A); break;   \
     }
     if (counting) {
-        CK_EXTRACT_VEC(true)
+        if (all) {
+            CK_EXTRACT_VEC(true, true)
+        } else {
+            CK_EXTRACT_VEC(true, false)
+        }
     } else {
-        CK_EXTRACT_VEC(false)
+        if (all) {
+            CK_EXTRACT_VEC(false, true)
+        } else {
+            CK_EXTRACT_VEC(false, false)
+        }
     }
 #undef CK_EXTRACT_VEC
 #undef CK_EXTRACT_LAUNCH

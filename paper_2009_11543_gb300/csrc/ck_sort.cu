@@ -135,15 +135,18 @@ cudaError_t launch_bucket_scan(uint32_t* hist, uint32_t sets, uint32_t rb, cudaS
 // ------------------------------------------------------------------ host
 static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
-bool make_sort_plan(uint64_t n, uint32_t K, uint32_t nbits, uint32_t digit_bits, SortPlan* p, uint64_t ld) {
+bool make_sort_plan(uint64_t n, uint32_t K, uint32_t nbits, uint32_t digit_bits, SortPlan* p, uint64_t ld,
+                    uint32_t tile) {
     if (digit_bits == 0) digit_bits = 8;
+    if (tile == 0) tile = kPassTile;
+    if (tile != 2048 && tile != kPassTile && tile != 8192) return false;
     p->ld = ld ? ld : CK_LD(n);
     if (p->ld < n) return false;
     if (digit_bits < 4 || digit_bits > 11) return false;
     p->digit_bits = digit_bits;
     p->passes = (nbits + digit_bits - 1) / digit_bits;
-    p->tile = kPassTile;
-    p->tiles = (uint32_t)((n + kPassTile - 1) / kPassTile);
+    p->tile = tile;
+    p->tiles = (uint32_t)((n + tile - 1) / tile);
     p->K = K;
     const size_t bins = (size_t)1 << digit_bits;
     size_t off = 0;
@@ -267,7 +270,7 @@ static cudaError_t run_sort_rb(const SortPlan& p, const uint32_t* ck_in, const u
         a.status = status_ptr();
         a.gate = gate;
         a.gate_run = 1;
-        e = launch_onesweep_pass(RB, a, arrays, p.tiles, s);
+        e = launch_onesweep_pass(RB, a, arrays, p.tiles, s, p.tile);
         if (e != cudaSuccess) return e;
         if (ev && (e = cudaEventRecord(ev[q + 1], s)) != cudaSuccess) return e;
         cur_ck = out_ck;

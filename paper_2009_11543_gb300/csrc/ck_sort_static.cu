@@ -64,13 +64,15 @@ extern "C" ck_status ck_sort_static(const uint32_t* ck_in, const uint32_t* rid_i
                                     uint32_t* rid_out, uint64_t n, uint32_t ck_words, uint32_t nbits,
                                     const ck_sort_opts* opts, ck_stream stream) {
     if (n > CK_MAX_ROWS || ck_words == 0 || nbits > 32u * ck_words) return CK_EINVAL;
-    if (opts && ((opts->flags & ~CK_SORT_FLAGS_ALL) != 0 ||
-                 (opts->digit_bits != 0 && (opts->digit_bits < 4 || opts->digit_bits > 11))))
+    if (opts && ((opts->flags & ~CK_SORT_FLAGS_ALL) != 0 || opts->reserved != 0 ||
+                 (opts->digit_bits != 0 && (opts->digit_bits < 4 || opts->digit_bits > 11)) ||
+                 (opts->tile != 0 && opts->tile != 2048 && opts->tile != 4096 && opts->tile != 8192)))
         return CK_EINVAL;
     if (n == 0) return CK_OK;
     if (!ck_in || !ck_out || !rid_out) return CK_EINVAL;
     SortPlan p;
-    if (!make_sort_plan(n, ck_words, nbits, opts ? opts->digit_bits : 0, &p)) return CK_EINVAL;
+    if (!make_sort_plan(n, ck_words, nbits, opts ? opts->digit_bits : 0, &p, 0, opts ? opts->tile : 0))
+        return CK_EINVAL;
     if (p.passes > 0 && p.total > (size_t)CK_SORT_STATIC_SCRATCH_BYTES) return CK_ENOMEM;  // beyond the fixed array
     ck_status st = CK_OK;
     unsigned char* ws = static_scratch(&st);

@@ -60,7 +60,7 @@ class Rebuild:
 
     def __init__(self, keys: torch.Tensor, dmask: np.ndarray, fanout: int = 64, fill: float = 1.0,
                  digit_bits: int = 8, ck_words: int | None = None, kind: int | None = None, perm_only: bool = False,
-                 learned: bool = False, learned_opts=None):
+                 learned: bool = False, learned_opts=None, tile: int = 0):
         self.keys = keys
         self.kind = kind
         self.col = ck.column(keys, kind)
@@ -69,7 +69,7 @@ class Rebuild:
         self.dmask = np.ascontiguousarray(np.asarray(dmask, np.uint64))
         self.nbits = ck.popcount(self.dmask)
         self.K = ck_words or ck.words_for(self.nbits)
-        self.fanout, self.fill, self.digit_bits = fanout, fill, digit_bits
+        self.fanout, self.fill, self.digit_bits, self.tile = fanout, fill, digit_bits, tile
         # perm_only: the sort returns only the permutation (and stops carrying
         # consumed key words); the tree is then built from the key column
         self.perm_only = perm_only
@@ -82,7 +82,7 @@ class Rebuild:
         self.ck_in = ck.ck_buffer(self.K, n, dev)
         self.ck_sorted = ck.ck_buffer(self.K, n, dev)
         self.rid_sorted = torch.empty(n, dtype=torch.int32, device=dev)
-        wsb = ck.ck_sort_workspace_bytes(self.n, self.K, self.nbits, digit_bits)
+        wsb = ck.ck_sort_workspace_bytes(self.n, self.K, self.nbits, digit_bits, tile)
         if learned:
             wsb = max(wsb, ck.ck_sort_learned_workspace_bytes(self.n, self.K, self.nbits, learned_opts))
             self.stats_buf = ck.learned_stats_buffer(dev)
@@ -119,7 +119,7 @@ class Rebuild:
             return
         ck.ck_sort(self.ck_in, None, self.ck_sorted, self.rid_sorted, self.n, self.K, self.nbits, self.ws,
                    digit_bits=self.digit_bits, pass_events=pass_events, perm_only=self.perm_only, hist=self.hist,
-                   stream=stream)
+                   tile=self.tile, stream=stream)
 
     def build(self, stream=None):
         if self.perm_only:
@@ -268,26 +268,30 @@ class BatchedRebuild:
 
     columns: list of CUDA key columns (same row count); dmasks: their stored
     D-bitmaps; digit_bits: per column, or None to run the autotuner on each
-    column's own keys (ck_autotune_sort, cached in cache_path)."""
+    column's own keys (ck_autotune_sort over digit width and pass tile, cached
+    in cache_path); tiles: per column when digit_bits is given (default tile
+    otherwise)."""
 
     def __init__(self, columns, dmasks, fanouts, fill: float = 1.0, digit_bits=None, cache_path: str | None = None,
-                 tune_reps: int = 3):
+                 tune_reps: int = 3, tiles=None, tune_tile: bool = True):
         import ctypes
         self.parts = [Rebuild(c, m, fanout=f, fill=fill, digit_bits=8) for c, m, f in zip(columns, dmasks, fanouts)]
         self.tuned_ms = []
         for k, r in enumerate(self.parts):
             if digit_bits is not None:
                 r.digit_bits = int(digit_bits[k])
+                r.tile = int(tiles[k]) if tiles is not None else 0
             else:
                 r.extract()
-                wsb = max(ck.ck_sort_workspace_bytes(r.n, r.K, r.nbits, d) for d in range(4, 12))
+                wsb = max(ck.ck_sort_workspace_bytes(r.n, r.K, r.nbits, d, t)
+                          for d in range(4, 12) for t in ck.CK_SORT_TILES)
                 if wsb > r.ws.numel():
                     r.ws = torch.empty(wsb, dtype=torch.uint8, device=r.keys.device)
-                r.digit_bits, ms = ck.ck_autotune_sort(r.ck_in, r.ck_sorted, r.rid_sorted, r.n, r.K, r.nbits,
-                                                       r.ws, tune_reps, cache_path)
+                r.digit_bits, r.tile, ms = ck.ck_autotune_sort(r.ck_in, r.ck_sorted, r.rid_sorted, r.n, r.K, r.nbits,
+                                                               r.ws, tune_reps, cache_path, tune_tile=tune_tile)
                 self.tuned_ms.append(ms)
             # the sort's workspace, then room for the digit counts taken while extracting
-            need = (ck.ck_sort_workspace_bytes(r.n, r.K, r.nbits, r.digit_bits) + 255) // 256 * 256
+            need = (ck.ck_sort_workspace_bytes(r.n, r.K, r.nbits, r.digit_bits, r.tile) + 255) // 256 * 256
             need += 4 * ((r.nbits + r.digit_bits - 1) // r.digit_bits << r.digit_bits)
             if need > r.ws.numel():
                 r.ws = torch.empty(need, dtype=torch.uint8, device=r.keys.device)
@@ -301,7 +305,7 @@ class BatchedRebuild:
             j = self.jobs[k]
             j.col = r.col
             j.dmask = r.dmask.ctypes.data
-            j.ck_words, j.digit_bits, j.fanout, j.fill = r.K, r.digit_bits, r.fanout, r.fill
+            j.ck_words, j.digit_bits, j.tile, j.fanout, j.fill = r.K, r.digit_bits, r.tile, r.fanout, r.fill
             j.ck, j.ck_sorted, j.rid_sorted = r.ck_in.data_ptr(), r.ck_sorted.data_ptr(), r.rid_sorted.data_ptr()
             j.tree = ctypes.pointer(t)
             j.refined_mask = r.refined.data_ptr()

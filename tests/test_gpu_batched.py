@@ -51,6 +51,7 @@ def test_batched_streams_and_graph_match_oracle(tmp_path):
     cache = str(tmp_path / "tune.txt")
     b = pipeline.BatchedRebuild(dev, dmasks, FANOUTS, cache_path=cache, tune_reps=2)
     assert all(4 <= r.digit_bits <= 11 for r in b.parts)
+    assert all(r.tile in ck.CK_SORT_TILES for r in b.parts)
     b.run()
     torch.cuda.synchronize()
     for r, c, p, m, f in zip(b.parts, cols, perms, dmasks, FANOUTS):
@@ -69,6 +70,7 @@ def test_batched_streams_and_graph_match_oracle(tmp_path):
     # the autotuner's cache serves the same widths without timing anything
     b2 = pipeline.BatchedRebuild(dev, dmasks, FANOUTS, cache_path=cache)
     assert [r.digit_bits for r in b2.parts] == [r.digit_bits for r in b.parts]
+    assert [r.tile for r in b2.parts] == [r.tile for r in b.parts]
     assert all(ms == 0.0 for ms in b2.tuned_ms)
     assert os.path.getsize(cache) > 0
 
@@ -76,7 +78,8 @@ def test_batched_streams_and_graph_match_oracle(tmp_path):
 def test_batched_equals_unbatched():
     n = 100_003
     cols, dev, perms, dmasks = table(n)
-    b = pipeline.BatchedRebuild(dev, dmasks, FANOUTS, digit_bits=[4, 5, 6, 8, 9, 11])
+    b = pipeline.BatchedRebuild(dev, dmasks, FANOUTS, digit_bits=[4, 5, 6, 8, 9, 11],
+                                tiles=[2048, 4096, 8192, 2048, 8192, 4096])
     b.run()
     torch.cuda.synchronize()
     for k, r in enumerate(b.parts):

@@ -252,20 +252,21 @@ def test_extract_empty_mask_zeroes():
 
 
 # ------------------------------------------------------------------ sort
-def check_sort(ckr, rid_in=None, nbits=None, digit_bits=8, inplace=False):
+def check_sort(ckr, rid_in=None, nbits=None, digit_bits=8, inplace=False, tile=0):
     """ckr: row-major [n, K] uint32 compressed keys (high bits above nbits zero)."""
     n, K = ckr.shape
     nbits = 32 * K if nbits is None else nbits
     ck_in = ck_dev_of(ckr)
     rid_dev = to_dev(rid_in.view(np.int32)) if rid_in is not None else None
-    ws = torch.empty(max(ck.ck_sort_workspace_bytes(n, K, nbits, digit_bits), 256), dtype=torch.uint8, device=DEV)
+    ws = torch.empty(max(ck.ck_sort_workspace_bytes(n, K, nbits, digit_bits, tile), 256), dtype=torch.uint8,
+                     device=DEV)
     if inplace:
         ck_out = ck_in
         rid_out = rid_dev if rid_dev is not None else torch.empty(max(n, 1), dtype=torch.int32, device=DEV)
     else:
         ck_out = torch.empty_like(ck_in)
         rid_out = torch.empty(max(n, 1), dtype=torch.int32, device=DEV)
-    ck.ck_sort(ck_in, rid_dev, ck_out, rid_out, n, K, nbits, ws, digit_bits=digit_bits)
+    ck.ck_sort(ck_in, rid_dev, ck_out, rid_out, n, K, nbits, ws, digit_bits=digit_bits, tile=tile)
     torch.cuda.synchronize()
     perm = oracle.sort_compressed(ckr)
     exp_rid = perm if rid_in is None else rid_in[perm]
@@ -283,6 +284,22 @@ def test_sort_digit_widths(digit_bits):
     v[rng.integers(0, n, 3000)] = v[rng.integers(0, n, 3000)]        # ties keep row order
     ckr = np.stack([(v & np.uint64(0xFFFFFFFF)).astype(np.uint32), (v >> np.uint64(32)).astype(np.uint32)], 1)
     check_sort(ckr, nbits=nbits, digit_bits=digit_bits)
+
+
+@pytest.mark.parametrize("tile,digit_bits,nbits", [(2048, 8, 45), (8192, 8, 45), (2048, 4, 45), (8192, 11, 45),
+                                                   (2048, 11, 96), (8192, 5, 96), (2048, 7, 1), (8192, 8, 128)])
+def test_sort_tiles(tile, digit_bits, nbits):
+    """The pass tiles the autotuner may pick (2048 and 8192 pairs besides the
+    default): several tiles of each and a ragged last tile, ties by row id."""
+    rng = np.random.default_rng(tile + digit_bits + nbits)
+    n = 3 * 8192 + 77
+    K = max(1, (nbits + 31) // 32)
+    ckr = rng.integers(0, 2**32, (n, K), dtype=np.uint64).astype(np.uint32)
+    top = nbits - 32 * (K - 1)
+    if top < 32:
+        ckr[:, K - 1] &= np.uint32((1 << top) - 1)
+    ckr[rng.integers(0, n, 2000)] = ckr[rng.integers(0, n, 2000)]
+    check_sort(ckr, nbits=nbits, digit_bits=digit_bits, tile=tile)
 
 
 @pytest.mark.parametrize("nbits", [1, 7, 8, 24, 32, 33, 64, 65, 96, 120, 128])

@@ -116,14 +116,24 @@ def test_argument_errors_are_synchronous(ckmod):
     assert lib.ck_sort(4096, None, 8192, 12288, 100, 1, 20, ctypes.byref(o), None, 0, None) == ckmod.CK_ENOMEM
     assert lib.ck_sort(4096, None, 8192, 12288, 100, 1, 40, ctypes.byref(o), None, 0, None) == ckmod.CK_EINVAL
     assert lib.ck_sort(4096, None, 8192, 12288, 1 << 30, 1, 20, None, None, 0, None) == ckmod.CK_EINVAL
+    for tile in (1024, 3000, 16384):                                    # not a pass tile
+        o = ckmod._opts(8, tile=tile)
+        assert lib.ck_sort(4096, None, 8192, 12288, 100, 1, 20, ctypes.byref(o), None, 0, None) == ckmod.CK_EINVAL
+        assert lib.ck_sort_workspace_bytes(100, 1, 20, ctypes.byref(o)) == 0
+    o = ckmod._opts(8)
+    o.reserved = 1
+    assert lib.ck_sort(4096, None, 8192, 12288, 100, 1, 20, ctypes.byref(o), None, 0, None) == ckmod.CK_EINVAL
     s = ckmod.ck_btree_shape()
     assert lib.ck_btree_plan(100, 1, ctypes.c_float(1.0), ctypes.byref(s)) == ckmod.CK_EINVAL
 
 
-def test_workspace_size_formula(ckmod):
+@pytest.mark.parametrize("tile", [0, 2048, 4096, 8192])
+def test_workspace_size_formula(ckmod, tile):
+    """One look-back word per tile, digit and pass: the tile sets the count."""
     n, K, nbits = 10**6, 4, 120
-    ws = ckmod.ck_sort_workspace_bytes(n, K, nbits, 8)
-    tiles = (n + ckmod.CK_SORT_TILE - 1) // ckmod.CK_SORT_TILE
+    ws = ckmod.ck_sort_workspace_bytes(n, K, nbits, 8, tile)
+    t = tile or ckmod.CK_SORT_TILE
+    tiles = (n + t - 1) // t
     passes = 15
     ld = ckmod.CK_LD(n)
     assert ld % 64 == 0 and ld >= n
