@@ -493,8 +493,28 @@ def measure_config(args, workload, world, local_rank, headline=False, extras=Fal
     f_ms, f_ph, f_pass, _ = timed(F, max(1, args.steps // 2), args.warmup, fpasses + 1)
     l_ms = l_ph = l_phase = None
     l_launch = 0
+    variants = {}
     if L is not None:
         l_ms, l_ph, l_phase, l_launch = timed(L, args.steps, args.warmup, ck.CK_LEARNED_PHASES + 1)
+        # what the model buys (the same sort with sample-quantile boundaries
+        # and no guesses) and, for the learned workloads, the 4096 model
+        # buckets the configuration names (quantile cuts then split the
+        # over-capacity ones)
+        vopts = {"no_model": ck.learned_opts(flags=ck.CK_LEARNED_NO_MODEL)}
+        if main_path == "learned":
+            vopts["model_buckets_4096"] = ck.learned_opts(bucket_bits=12)
+        for name, o in vopts.items():
+            Lv = pipeline.Rebuild(keys, dmask, fanout=fanout, digit_bits=args.digit_bits, learned=True,
+                                  learned_opts=o)
+            v_ms_, _, v_phase, _ = timed(Lv, max(2, args.steps // 2), args.warmup, ck.CK_LEARNED_PHASES + 1)
+            vst = Lv.learned_stats
+            variants[name] = {"ms_per_step": v_ms_, "sort_phases_ms": dict(zip(LEARNED_PHASE_NAMES, map(float, v_phase))),
+                              "buckets": vst["buckets"], "model_buckets": vst["model_buckets"],
+                              "model_boundary_frac": vst["model_boundary_frac"],
+                              "mean_search_steps": vst["mean_search_steps"], "max_bucket": vst["max_bucket"],
+                              "fell_back": vst["fell_back"]}
+            del Lv
+            torch.cuda.empty_cache()
     headline_learned = main_path == "learned" and L is not None
     v_ms = l_ms if headline_learned else p_ms
 
@@ -541,7 +561,8 @@ def measure_config(args, workload, world, local_rank, headline=False, extras=Fal
         rec["learned"] = {"ms_per_step": l_ms, "value": world * n / (l_ms / 1e3),
                           "phases_ms": dict(zip(("extract", "sort", "build"), map(float, l_ph))),
                           "sort_phases_ms": phases, "stats": st, "speedup_vs_plain": p_ms / l_ms,
-                          "launches_per_step": l_launch,
+                          "launches_per_step": l_launch, "variants": variants,
+                          "model_vs_no_model_speedup": variants["no_model"]["ms_per_step"] / l_ms,
                           "roofline": {"bound": "hbm", "kernel": kern, "achieved": ach, "peak": peak,
                                        "peak_source": peak_src, "unit": "GB/s", "frac": ach / peak,
                                        "traffic": None, "alg_bytes_per_launch": pb[dom],

@@ -39,8 +39,9 @@ constexpr int kScanBlock = 1024;         // elements per block of the sample sca
 constexpr uint32_t kMaxModelBuckets = 1u << 15;
 constexpr uint32_t kMaxBucketIds = 1u << 16;  // bucket ids of two 8-bit partition passes
 constexpr uint32_t kMaxConst = 1024;          // large constant buckets listed for the chunked check
-constexpr uint32_t kStagedSplitters = 48 * 1024;  // splitters whose top 32 bits the bucket kernel stages
-constexpr int kPrefixBits = 12;
+constexpr uint32_t kStagedSplitters = 40 * 1024;  // splitters whose bits 16..31 the bucket kernel stages
+constexpr uint32_t kPrefixCells = 1u << 16;        // prefix table over the top 16 bits of a key
+constexpr uint32_t kPrefixEntries = kPrefixCells + 8;  // kPrefixCells + 1, rounded up to 16 bytes
 
 // flags of a boundary gap g (between sample keys g - 1 and g)
 constexpr uint32_t kGapModel = 1, kGapQuant = 2, kGapHeavyStart = 4, kGapHeavyEnd = 8;
@@ -622,6 +623,7 @@ struct BucketArgs {
     const float* params;
     const uint32_t* spl;  // strictly increasing, entry-major
     const uint32_t* map;  // [B + 1]
+    const uint16_t* pre;  // [kPrefixEntries] prefix table (prefix_table_kernel)
     LearnedMisc* misc;
     uint32_t* bkt;        // [n]
     uint32_t* hist;       // [2][256] digit counts of the bucket id (low byte, high byte)
@@ -656,21 +658,22 @@ __device__ __forceinline__ uint32_t top32_mem(const uint32_t* key, uint32_t K, u
     return sh ? __funnelshift_r(key[w], key[w + 1 < K ? w + 1 : w], sh) : key[w];
 }
 
-// Comparison of key x (top32 value t) with splitter m: with `staged`, the
-// shared table of splitter top32 values decides unless they are equal.
+// Comparison of key x (top32 value t) with splitter m of the key's prefix
+// cell (the same top 16 bits): with `staged`, the shared table of the
+// splitters' bits 16..31 decides unless they are equal too.
 template <int KW>
-__device__ __forceinline__ int cmp_at(const uint32_t (&key)[KW], uint32_t t, const uint32_t* top, bool staged,
+__device__ __forceinline__ int cmp_at(const uint32_t (&key)[KW], uint32_t t, const uint16_t* low, bool staged,
                                       const uint32_t* spl, uint32_t m) {
     if (staged) {
-        const uint32_t u = top[m];
-        if (t != u) return t < u ? -1 : 1;
+        const uint32_t u = low[m], tl = t & 0xFFFFu;
+        if (tl != u) return tl < u ? -1 : 1;
     }
     return cmp_key<KW>(key, spl + (uint64_t)m * KW);
 }
 
 // Number of splitters <= x within [lo, hi] (binary search).
 template <int KW>
-__device__ __forceinline__ uint32_t search_range(const uint32_t (&key)[KW], uint32_t t, const uint32_t* top,
+__device__ __forceinline__ uint32_t search_range(const uint32_t (&key)[KW], uint32_t t, const uint16_t* top,
                                                  bool staged, const uint32_t* spl, uint32_t lo, uint32_t hi,
                                                  uint32_t* cmp) {
     while (lo < hi) {
@@ -687,7 +690,7 @@ __device__ __forceinline__ uint32_t search_range(const uint32_t (&key)[KW], uint
 // buckets) and finish with a binary search, so a guess that is e buckets off
 // costs about 2 log2(e) + 2 comparisons.
 template <int KW>
-__device__ __forceinline__ uint32_t search_from_guess(const uint32_t (&key)[KW], uint32_t t, const uint32_t* top,
+__device__ __forceinline__ uint32_t search_from_guess(const uint32_t (&key)[KW], uint32_t t, const uint16_t* top,
                                                       bool staged, const uint32_t* spl, uint32_t lo, uint32_t hi,
                                                       uint32_t g, uint32_t* cmp) {
     ++*cmp;
@@ -719,20 +722,40 @@ __device__ __forceinline__ uint32_t search_from_guess(const uint32_t (&key)[KW],
     return g;
 }
 
+// Prefix table over the top 16 bits of a key: pre[q] = the first splitter
+// whose top 16 bits are >= q (q = 0 .. 2^16), so the splitters of cell q --
+// those sharing the top 16 bits q -- are [pre[q], pre[q + 1]).
+__global__ void prefix_table_kernel(const uint32_t* __restrict__ spl, uint32_t K, uint32_t nbits,
+                                    const LearnedMisc* misc, uint32_t max_buckets, uint16_t* __restrict__ pre) {
+    if (*(volatile const uint32_t*)&misc->gate) return;
+    const uint32_t ns = min(misc->nsplit, max_buckets - 1);
+    for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < kPrefixEntries; q += gridDim.x * blockDim.x) {
+        uint32_t lo = 0, hi = ns;
+        if (q <= kPrefixCells)
+            while (lo < hi) {
+                const uint32_t mid = (lo + hi) >> 1;
+                if ((top32_mem(spl + (uint64_t)mid * K, K, nbits) >> 16) >= q) hi = mid;
+                else lo = mid + 1;
+            }
+        pre[q] = (uint16_t)(q <= kPrefixCells ? lo : ns);
+    }
+}
+
 // Bucket id of every key, the digit counts of the two partition passes, and
-// the hash sum of the input pairs (key, row id = position).  When the
-// splitters fit, the top 32 bits of each sit in shared memory with a table
-// over their top kPrefixBits bits: pre[p] = first splitter whose top32 is >=
-// p << (32 - kPrefixBits), so a key whose top32 has prefix p has its bucket in
-// [pre[p], pre[p + 1]].  The model's guess (its bucket b maps to final bucket
-// map[b]), clamped into that range, starts a galloping search where that is
-// expected to be cheaper than a binary search of the range: the model's
-// error is about e = sqrt(loss) B buckets, so galloping costs about
-// 2 log2(e + 1) + 2 comparisons against log2(range + 1).
+// the hash sum of the input pairs (key, row id = position).  The prefix table
+// over the top 16 bits sits in shared memory, and when the splitters fit,
+// bits 16..31 of each: a key's bucket lies in the range of its prefix cell,
+// where those 16 bits decide every comparison unless they are equal too.  The
+// model's guess (its bucket b maps to final bucket map[b]), clamped into that
+// range, starts a galloping search where that is expected to be cheaper than
+// a binary search of the range: the model's error is about e = sqrt(loss) B
+// buckets, so galloping costs about 2 log2(e + 1) + 2 comparisons against
+// log2(range + 1).
 template <int KW>
 __global__ void __launch_bounds__(1024) bucket_kernel(const BucketArgs a) {
-    extern __shared__ uint32_t top[];
-    uint32_t* pre = top + kStagedSplitters;
+    extern __shared__ uint16_t sm16[];
+    uint16_t* pre = sm16;                    // [kPrefixEntries]
+    uint16_t* low = sm16 + kPrefixEntries;   // [kStagedSplitters]
     __shared__ float p[kParams];
     __shared__ uint32_t hlo[256], hhi[256];
     LearnedMisc* misc = a.misc;
@@ -747,20 +770,11 @@ __global__ void __launch_bounds__(1024) bucket_kernel(const BucketArgs a) {
         hlo[tid] = 0;
         hhi[tid] = 0;
     }
-    if (staged) {
-        for (uint32_t m = tid; m < ns; m += blockDim.x) top[m] = top32_mem(a.spl + (uint64_t)m * KW, KW, nbits);
-        __syncthreads();
-        for (uint32_t q = tid; q <= (1u << kPrefixBits); q += blockDim.x) {
-            uint32_t lo = 0, hi = ns;  // first m with top[m] >= q << (32 - kPrefixBits)
-            const uint64_t bound = (uint64_t)q << (32 - kPrefixBits);
-            while (lo < hi) {
-                const uint32_t mid = (lo + hi) >> 1;
-                if ((uint64_t)top[mid] >= bound) hi = mid;
-                else lo = mid + 1;
-            }
-            pre[q] = lo;
-        }
-    }
+    for (uint32_t i = tid; i < kPrefixEntries / 8; i += blockDim.x)
+        reinterpret_cast<uint4*>(pre)[i] = reinterpret_cast<const uint4*>(a.pre)[i];
+    if (staged)
+        for (uint32_t m = tid; m < ns; m += blockDim.x)
+            low[m] = (uint16_t)(top32_mem(a.spl + (uint64_t)m * KW, KW, nbits) & 0xFFFFu);
     __syncthreads();
     unsigned long long my_sum = 0, my_max = 0;
     uint64_t my_hash = 0;
@@ -777,21 +791,17 @@ __global__ void __launch_bounds__(1024) bucket_kernel(const BucketArgs a) {
             next[w] = i + stride < a.n ? a.ck[(uint64_t)w * a.ld + i + stride] : 0u;
         }
         const uint32_t t = top32_regs<KW>(key, nbits);
-        uint32_t g, steps = 0, lo = 0, hi = ns;
-        if (staged) {
-            const uint32_t q = t >> (32 - kPrefixBits);
-            lo = pre[q];
-            hi = pre[q + 1];
-        }
+        uint32_t g, steps = 0;
+        const uint32_t lo = pre[t >> 16], hi = pre[(t >> 16) + 1];
         if (a.use_model && (float)(hi - lo) + 1.0f > model_min_range) {
             const float x = (float)(t >> 8) * (1.0f / 16777216.0f);  // the top 24 bits, as in training
             const float y = mlp_eval(p, x) * (float)B;
             const uint32_t mb = y <= 0.0f ? 0u : (y >= (float)(B - 1) ? B - 1 : (uint32_t)y);
             uint32_t guess = a.map[mb];
             guess = guess < lo ? lo : (guess > hi ? hi : guess);
-            g = search_from_guess<KW>(key, t, top, staged, a.spl, lo, hi, guess, &steps);
+            g = search_from_guess<KW>(key, t, low, staged, a.spl, lo, hi, guess, &steps);
         } else {
-            g = search_range<KW>(key, t, top, staged, a.spl, lo, hi, &steps);
+            g = search_range<KW>(key, t, low, staged, a.spl, lo, hi, &steps);
         }
         a.bkt[i] = g;
         atomicAdd(&hlo[g & 255u], 1u);
@@ -829,7 +839,7 @@ static cudaError_t launch_bucket_kw(const BucketArgs& ba, size_t smem, int sms, 
 }
 
 static cudaError_t launch_bucket(const BucketArgs& ba, int sms, cudaStream_t s) {
-    const size_t smem = 4ull * kStagedSplitters + 4ull * ((1u << kPrefixBits) + 1);
+    const size_t smem = 2ull * kPrefixEntries + 2ull * kStagedSplitters;
     switch (ba.K) {
         case 1: return launch_bucket_kw<1>(ba, smem, sms, s);
         case 2: return launch_bucket_kw<2>(ba, smem, sms, s);
@@ -964,7 +974,7 @@ struct LearnedPlan {
     SortPlan sample_sort, plain;
     size_t off_sample, off_sample_sorted, off_sample_rid, off_sample_ws, off_xs, off_ys, off_bmax, off_carry, off_flag,
         off_bcnt, off_gaps, off_seg, off_mgap, off_gidx, off_map, off_params, off_misc, off_spl, off_start, off_const,
-        off_bkt, off_alt_bkt, off_alt_ck, off_alt_rid, off_hist, off_lookback, off_plain_ws, total;
+        off_bkt, off_alt_bkt, off_alt_ck, off_alt_rid, off_hist, off_lookback, off_plain_ws, off_pre, total;
 };
 
 static size_t a256(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -1048,6 +1058,7 @@ static bool make_learned_plan(uint64_t n, uint32_t K, uint32_t nbits, const ck_l
     p->off_hist = take(4ull * 512);
     p->off_lookback = take(4ull * 256 * tiles * p->passes + 4 * p->passes);
     p->off_plain_ws = take(p->plain.total);
+    p->off_pre = take(2ull * kPrefixEntries);
     p->total = off;
     return true;
 }
@@ -1175,6 +1186,10 @@ ck_status ck_sort_learned(const uint32_t* ck_in, uint32_t* ck_out, uint32_t* rid
         count_launch();
     }
 
+    prefix_table_kernel<<<(kPrefixEntries + 255) / 256, 256, 0, s>>>(at(P.off_spl), K, nbits, misc, P.max_buckets,
+                                                                     reinterpret_cast<uint16_t*>(ws + P.off_pre));
+    count_launch();
+
     CK_TRY(mark(1));
     // 4. bucket id of every key (model guess + exact correction), digit
     //    counts, input hash
@@ -1191,6 +1206,7 @@ ck_status ck_sort_learned(const uint32_t* ck_in, uint32_t* ck_out, uint32_t* rid
     ba.params = use_model ? params : nullptr;
     ba.spl = at(P.off_spl);
     ba.map = at(P.off_map);
+    ba.pre = reinterpret_cast<const uint16_t*>(ws + P.off_pre);
     ba.misc = misc;
     ba.bkt = at(P.off_bkt);
     ba.hist = at(P.off_hist);

@@ -55,7 +55,7 @@ constexpr uint32_t kLsMaxCap = kLsPerThread * kLsThreads;
 constexpr int kLsList = 1024;                        // pending ranges: disjoint, > 32 pairs each, so < cap / 33
 constexpr uint32_t kConstInline = 16384;             // constant buckets up to this size are checked inline
 constexpr uint32_t kConstChunk = 65536;              // chunk of the constant-bucket check
-constexpr size_t kLsStaticSmem = 2 * kLsList * 4 + 3584;
+constexpr size_t kLsStaticSmem = 2 * kLsList * 4 + 4096;
 constexpr size_t kSmemLimit = 227 * 1024;
 
 static_assert(kLsWarpBins == (1 << kLsWarpBinBits), "warp bins");
@@ -401,8 +401,9 @@ struct LsBlockState {
     uint32_t* orw;     // [KC]
     uint32_t* mm;      // [2]: window minimum, maximum
     uint32_t* wsum;    // [kLsWarps + 1]
-    uint32_t* bytes;   // [2][256]: counts, then dense codes, of the window's top two bytes
-    uint32_t* nbytes;  // [2]: values in use of each byte
+    uint32_t* bytes;   // [3][256]: dense codes (digit terms) of the window's top three bytes
+    uint32_t* pres;    // [3][8]: which values each of those bytes takes (bitmaps)
+    uint32_t* nbytes;  // [3]: values in use of each byte
 };
 
 // Step 1 on range A[p0, p0 + r) by the whole block.  ident: the range is the
@@ -444,20 +445,27 @@ __device__ void block_split(const LsView<KW>& v, uint32_t p0, uint32_t r, bool i
     uint32_t F = 32 - __clz(r - 1);  // 2^F >= r
     F = F < 8 ? 8u : (F > (uint32_t)kLsBinBits ? (uint32_t)kLsBinBits : F);
     for (uint32_t d = tid; d < (uint32_t)kLsBins; d += kLsThreads) hist[d] = 0;
-    for (uint32_t d = tid; d < 512; d += kLsThreads) st.bytes[d] = 0;
+    if (tid < 24) st.pres[tid] = 0;
     if (tid == 0) {
         st.mm[0] = 0xFFFFFFFFu;
         st.mm[1] = 0;
     }
-    __syncthreads();  // mm initialised, bins and byte counts zeroed
-    {  // window range, and which values the window's top two bytes take
+    __syncthreads();  // mm initialised, bins and byte bitmaps zeroed
+    {  // window range, and which values the window's top three bytes take: a
+       // value's bit is set once (a plain read first), so keys over a small
+       // alphabet, whose bytes take few values, do not queue on a few words
         uint32_t lo = 0xFFFFFFFFu, hi = 0;
+        volatile uint32_t* pr = st.pres;
         for (uint32_t p = p0 + tid; p < pe; p += kLsThreads) {
             const uint32_t x = W(v, ident ? p : v.A[p]);
             lo = min(lo, x);
             hi = max(hi, x);
-            atomicAdd(&st.bytes[x >> 24], 1u);
-            atomicAdd(&st.bytes[256 + ((x >> 16) & 255u)], 1u);
+            const uint32_t w1 = x >> 29, m1 = 1u << ((x >> 24) & 31u);
+            const uint32_t w2 = 8u + ((x >> 21) & 7u), m2 = 1u << ((x >> 16) & 31u);
+            const uint32_t w3 = 16u + ((x >> 13) & 7u), m3 = 1u << ((x >> 8) & 31u);
+            if (!(pr[w1] & m1)) atomicOr(&st.pres[w1], m1);
+            if (!(pr[w2] & m2)) atomicOr(&st.pres[w2], m2);
+            if (!(pr[w3] & m3)) atomicOr(&st.pres[w3], m3);
         }
         lo = __reduce_min_sync(kFull, lo);
         hi = __reduce_max_sync(kFull, hi);
@@ -467,49 +475,57 @@ __device__ void block_split(const LsView<KW>& v, uint32_t p0, uint32_t r, bool i
         }
     }
     __syncthreads();
-    if (tid < 64) {  // dense codes of the values each byte takes (warp 0: top byte, warp 1: next)
-        uint32_t* tb = st.bytes + 256 * (tid >> 5);
-        uint32_t f[8], c = 0;
-#pragma unroll
-        for (int i = 0; i < 8; ++i) {
-            f[i] = tb[lane * 8 + i] ? 1u : 0u;
-            c += f[i];
-        }
+    if (tid < 96) {  // dense codes of the values each byte takes (warp j: byte j; lane l: values 8l .. 8l + 7)
+        const uint32_t j = tid >> 5;
+        const uint32_t bits = (st.pres[8 * j + (lane >> 2)] >> (8 * (lane & 3u))) & 255u;
+        const uint32_t c = __popc(bits);
         uint32_t inc = c;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
             const uint32_t t = __shfl_up_sync(kFull, inc, o);
             if (lane >= (uint32_t)o) inc += t;
         }
-        uint32_t run = inc - c;
+        const uint32_t run = inc - c;
 #pragma unroll
-        for (int i = 0; i < 8; ++i) {
-            tb[lane * 8 + i] = run;
-            run += f[i];
-        }
-        if (lane == 31) st.nbytes[tid >> 5] = inc;
+        for (uint32_t i = 0; i < 8; ++i) st.bytes[256 * j + 8 * lane + i] = run + __popc(bits & ((1u << i) - 1u));
+        if (lane == 31) st.nbytes[j] = inc;
     }
     __syncthreads();
     // The digit: the window's top bits after subtracting its minimum (2^F
     // bins), unless the top byte is sparse (at most 128 of its values occur,
-    // as for keys over a small alphabet whose codes use few bit patterns) and
-    // the two top bytes' values in use give 256 .. kLsBins combinations:
-    // then the mixed-radix number of their dense codes, which keeps the order
-    // of the windows and spreads the pairs over far more bins.
-    const uint32_t n1 = st.nbytes[0], n2 = st.nbytes[1];
-    const bool dense = n1 <= 128 && n1 * n2 <= (uint32_t)kLsBins && n1 * n2 >= 256;
+    // as for keys over a small alphabet whose codes use few bit patterns):
+    // then the mixed-radix number of the dense codes of the window's top
+    // bytes -- all values of the first, of the second as far as kLsBins
+    // allows (scaled down to k2 levels otherwise), of the third within what is
+    // left (k3 levels) -- which keeps the order of the windows and spreads the
+    // pairs over far more of the bins, if that gives 256 bins or more.
+    const uint32_t n1 = st.nbytes[0], n2 = st.nbytes[1], n3 = st.nbytes[2];
+    uint32_t k2 = 1, k3 = 1;
+    bool dense = false;
+    if (n1 <= 128) {
+        k2 = min(n2, (uint32_t)kLsBins / n1);
+        k3 = k2 == n2 ? min(n3, (uint32_t)kLsBins / (n1 * n2)) : 1u;
+        dense = n1 * k2 * k3 >= 256;
+    }
     uint32_t bins = 1u << F;
     if (dense) {
-        bins = 256;
-        while (bins < n1 * n2) bins <<= 1;
+        bins = (n1 * k2 * k3 + 31) & ~31u;  // whole segments of the bin scan; the extra bins stay empty
+        // codes -> digit terms: c1 k2 k3, scaled c2 times k3, scaled c3
+        for (uint32_t i = tid; i < 768; i += kLsThreads) {
+            const uint32_t j = i >> 8, c = st.bytes[i];
+            st.bytes[i] = j == 0 ? c * k2 * k3
+                                 : (j == 1 ? (k2 == n2 ? c : c * k2 / n2) * k3 : (k3 == n3 ? c : c * k3 / n3));
+        }
+        __syncthreads();
     }
     const uint32_t wmin = st.mm[0];
     const uint32_t bl = 32 - __clz(st.mm[1] - wmin);
     const uint32_t sh = bl > F ? bl - F : 0u;
     const uint32_t* c1 = st.bytes;
     const uint32_t* c2 = st.bytes + 256;
+    const uint32_t* c3 = st.bytes + 512;
     auto digit = [&](uint32_t x) -> uint32_t {
-        return dense ? c1[x >> 24] * n2 + c2[(x >> 16) & 255u] : (x - wmin) >> sh;
+        return dense ? c1[x >> 24] + c2[(x >> 16) & 255u] + c3[(x >> 8) & 255u] : (x - wmin) >> sh;
     };
     for (uint32_t p = p0 + tid; p < pe; p += kLsThreads) atomicAdd(&hist[digit(W(v, ident ? p : v.A[p]))], 1u);
     __syncthreads();
@@ -911,7 +927,7 @@ __global__ void __launch_bounds__(kLsThreads, 1) local_sort_kernel(const LocalSo
     __shared__ uint32_t s_or[kMaxLearnedWords + 1];
     __shared__ uint32_t s_mm[2], s_bucket, s_cnt[2], s_grab, s_bcnt, s_bad;
     __shared__ uint32_t s_bstack[kLsBlockStack];
-    __shared__ uint32_t s_bytes[512], s_nbytes[2];
+    __shared__ uint32_t s_bytes[768], s_pres[24], s_nbytes[3];
     __shared__ uint32_t s_scan[kLsWarps + 1];
     const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     constexpr uint32_t K = KW, KC = KW + 1;
@@ -935,6 +951,7 @@ __global__ void __launch_bounds__(kLsThreads, 1) local_sort_kernel(const LocalSo
     bst.mm = s_mm;
     bst.wsum = s_scan;
     bst.bytes = s_bytes;
+    bst.pres = s_pres;
     bst.nbytes = s_nbytes;
     uint64_t my_hash = 0;
     uint32_t my_bad = 0;
