@@ -45,8 +45,7 @@ sys.path.insert(0, ROOT)
 METRIC = "keys/sec sorted+indexed (1 GB300) and % of HBM roofline, compressed vs full-key sort"
 FALLBACK_HBM_GBS = 6800.0
 SPEC_HBM_GBS = 7900.0  # nominal HBM3e bandwidth of a GB300, for context beside the measured peak
-PASS_SRC = os.path.join(ROOT, "paper_2009_11543_gb300", "csrc", "ck_pass.cu")
-TRAFFIC_FILE = os.path.join(ROOT, "profiles", "onesweep_pass_traffic.json")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "kernel_traffic.json")
 
 WORKLOADS = {
     # name: (description, n, generator, fanout, cpu sample rows, path the headline value uses)
@@ -123,13 +122,15 @@ def max_over_ranks(times, world: int) -> np.ndarray:
     return t.numpy()
 
 
-def ncu_traffic(n: int, ck_words: int):
-    """DRAM bytes per pass launch from the committed ncu summary, scaled to n
-    keys, if the pass kernel's source is unchanged since the capture."""
+def ncu_traffic(kernel: str, n: int, ck_words: int):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary
+    (dram__bytes_read.sum + dram__bytes_write.sum of one launch), scaled to n
+    keys, if the kernel's source file is unchanged since the capture and the
+    key width matches; else None."""
     try:
         with open(TRAFFIC_FILE) as f:
-            t = json.load(f)
-        if t.get("kernel_src_sha") != file_sha(PASS_SRC) or t.get("ck_words") != ck_words:
+            t = json.load(f)[kernel]
+        if t.get("kernel_src_sha") != file_sha(os.path.join(ROOT, t["kernel_src"])) or t.get("ck_words") != ck_words:
             return None
         return t["dram_bytes_per_launch"] * n / t["n"]
     except Exception:
@@ -508,11 +509,16 @@ def measure_config(args, workload, world, local_rank, headline=False, extras=Fal
                                   learned_opts=o)
             v_ms_, _, v_phase, _ = timed(Lv, max(2, args.steps // 2), args.warmup, ck.CK_LEARNED_PHASES + 1)
             vst = Lv.learned_stats
+            # a variant may fall back to the plain sort (exact, CK_EVERIFY in
+            # the status word): that is its result, recorded here and cleared
+            v_status = ck.ck_status_string(ck.ck_device_status()[0])
+            ck.ck_clear_device_status()
             variants[name] = {"ms_per_step": v_ms_, "sort_phases_ms": dict(zip(LEARNED_PHASE_NAMES, map(float, v_phase))),
                               "buckets": vst["buckets"], "model_buckets": vst["model_buckets"],
                               "model_boundary_frac": vst["model_boundary_frac"],
                               "mean_search_steps": vst["mean_search_steps"], "max_bucket": vst["max_bucket"],
-                              "fell_back": vst["fell_back"]}
+                              "fell_back": vst["fell_back"], "oversize_buckets": vst["oversize_buckets"],
+                              "device_status": v_status}
             del Lv
             torch.cuda.empty_cache()
     headline_learned = main_path == "learned" and L is not None
@@ -545,7 +551,8 @@ def measure_config(args, workload, world, local_rank, headline=False, extras=Fal
                           args.digit_bits, 256 if R.K + 1 >= 3 or n > (1 << 22) else 512),
                       "achieved": sort_bytes / (pass_ms / 1e3) / 1e9, "peak": peak, "peak_source": peak_src,
                       "unit": "GB/s", "frac": sort_bytes / (pass_ms / 1e3) / 1e9 / peak,
-                      "traffic": ncu_traffic(n, R.K), "alg_bytes_per_launch": sort_bytes / passes,
+                      "traffic": ncu_traffic("onesweep_pass_kernel", n, R.K),
+                      "alg_bytes_per_launch": sort_bytes / passes,
                       "avg_launch_ms": avg_pass, "launches_per_step": passes}
         rec["plain"]["extract_sort_roofline_frac"] = alg / ((p_ph[0] + p_ph[1]) / 1e3) / 1e9 / peak
         rec["plain"]["extract_sort_alg_bytes"] = alg
@@ -565,7 +572,9 @@ def measure_config(args, workload, world, local_rank, headline=False, extras=Fal
                           "model_vs_no_model_speedup": variants["no_model"]["ms_per_step"] / l_ms,
                           "roofline": {"bound": "hbm", "kernel": kern, "achieved": ach, "peak": peak,
                                        "peak_source": peak_src, "unit": "GB/s", "frac": ach / peak,
-                                       "traffic": None, "alg_bytes_per_launch": pb[dom],
+                                       "traffic": ncu_traffic("local_sort_kernel" if dom == "bucket_sorts_checks"
+                                                              else "onesweep_pass_kernel_partition", n, R.K),
+                                       "alg_bytes_per_launch": pb[dom],
                                        "avg_launch_ms": phases[dom],
                                        "phase_alg_bytes": pb}}
     rec["roofline"] = rec["learned"]["roofline"] if headline_learned else plain_roof

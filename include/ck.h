@@ -298,13 +298,18 @@ ck_status ck_sort_static(const uint32_t* ck_in, const uint32_t* rid_in, uint32_t
  * The model proposes the bucket boundaries: over the sorted sample, the
  * running maximum of y crosses b / B (B = 2^bucket_bits model buckets) at
  * sample position c_b, and the boundary is the sample key there (moved to the
- * start of its run of equal keys).  A key value with at least half an average
- * bucket of sample copies gets a bucket of its own, [v, v + 1).  Where a
- * model bucket holds more sample keys than a shared-memory sort can take
- * (with a margin for sampling noise), sample quantiles cut it further;
+ * start of its run of equal keys).  A key value with at least h sample copies
+ * gets a bucket of its own, [v, v + 1).  Where a model bucket holds more
+ * sample keys than a shared-memory sort can take (u, with a margin for
+ * sampling noise), sample quantiles cut it into pieces of t = S / B sample
+ * keys, or of t = 2u / 3 when S / B > u (few model buckets); h = t / 2, so
+ * that such a piece, whose cut may move back over a run of fewer than h
+ * equal keys, stays within u.
  * stats.model_boundary_frac is the share of boundaries the model set.  Every
- * key's bucket is found from the model's guess by a short search against the
- * boundaries (exact).  Two radix passes on the bucket id partition the pairs
+ * key's bucket lies in the range of splitters sharing its top 16 bits (a
+ * prefix table), where a short search finds it, started from the model's
+ * guess when that range is wide (exact).  Two radix passes on the bucket id
+ * partition the pairs
  * stably; each bucket (a contiguous key range in row-id order) is then sorted
  * in shared memory and checked: adjacent keys ascend, the keys lie inside the
  * bucket's range, equal keys keep row-id order, and a sum of 64-bit hashes of

@@ -39,7 +39,7 @@ constexpr int kScanBlock = 1024;         // elements per block of the sample sca
 constexpr uint32_t kMaxModelBuckets = 1u << 15;
 constexpr uint32_t kMaxBucketIds = 1u << 16;  // bucket ids of two 8-bit partition passes
 constexpr uint32_t kMaxConst = 1024;          // large constant buckets listed for the chunked check
-constexpr uint32_t kStagedSplitters = 40 * 1024;  // splitters whose bits 16..31 the bucket kernel stages
+constexpr uint32_t kStagedSplitters = 48 * 1024;  // splitters whose bits 16..31 the bucket kernel stages
 constexpr uint32_t kPrefixCells = 1u << 16;        // prefix table over the top 16 bits of a key
 constexpr uint32_t kPrefixEntries = kPrefixCells + 8;  // kPrefixCells + 1, rounded up to 16 bytes
 
@@ -997,8 +997,6 @@ static bool make_learned_plan(uint64_t n, uint32_t K, uint32_t nbits, const ck_l
         while (B < kMaxModelBuckets && (double)B < want) B <<= 1;
     }
     p->B = B;
-    p->max_buckets = std::min<uint32_t>(kMaxBucketIds, std::max<uint32_t>(256u, 4u * B));
-    p->passes = p->max_buckets > 256 ? 2 : 1;
     p->div = o && o->sample_div ? o->sample_div : 100;
     p->epochs = o && o->epochs ? o->epochs : 100;
     p->lr = o && o->lr > 0.0f ? o->lr : 1e-3f;
@@ -1011,7 +1009,6 @@ static bool make_learned_plan(uint64_t n, uint32_t K, uint32_t nbits, const ck_l
     p->ld_s = CK_LD(p->S);
     p->tstride = (p->S + kTrainPoints - 1) / kTrainPoints;
     p->T = (p->S + p->tstride - 1) / p->tstride;
-    p->t_s = (float)((double)p->S / (double)B);
     // u_s: most sample keys a bucket may hold so that its pairs (about
     // u_s * n / S, with a relative spread of 1 / sqrt(u_s)) stay within the
     // capacity at five standard deviations
@@ -1019,7 +1016,20 @@ static bool make_learned_plan(uint64_t n, uint32_t K, uint32_t nbits, const ck_l
     uint32_t u = 1;
     while ((double)(u + 1) * per * (1.0 + 5.0 / std::sqrt((double)(u + 1))) <= (double)p->cap && u < (1u << 30)) ++u;
     p->u_s = u;
+    // t_s: sample keys per piece of an over-capacity model bucket -- those of
+    // an average model bucket, or 2 u_s / 3 when an average model bucket is
+    // itself over capacity (few model buckets, a small B): a cut moves back to
+    // the start of its run of equal keys, and runs shorter than the heavy
+    // threshold h_s = t_s / 2 stay in the piece, so such a piece holds at most
+    // t_s + h_s <= u_s sample keys
+    p->t_s = (float)((double)p->S / (double)B > (double)u ? 2.0 * (double)u / 3.0 : (double)p->S / (double)B);
     p->h_s = std::max<uint64_t>(2, std::min<uint64_t>(u, (uint64_t)(p->t_s / 2.0f)));
+    // bucket id space: room for four times the buckets of a column cut into
+    // pieces of t_s sample keys throughout (4 B when t_s = S / B), heavy keys
+    // and model boundaries included; more needs the fallback
+    const double pieces = std::ceil((double)p->S / (double)p->t_s);
+    p->max_buckets = (uint32_t)std::min<double>(kMaxBucketIds, std::max<double>(256.0, 4.0 * pieces));
+    p->passes = p->max_buckets > 256 ? 2 : 1;
     p->nblk_s = (uint32_t)((p->S + kScanBlock - 1) / kScanBlock);
     p->nblk_g = (uint32_t)((p->S + 1 + kScanBlock - 1) / kScanBlock);
     if (!make_sort_plan(p->S, K, nbits, 8, &p->sample_sort)) return false;

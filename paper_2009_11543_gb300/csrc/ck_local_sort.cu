@@ -55,7 +55,7 @@ constexpr uint32_t kLsMaxCap = kLsPerThread * kLsThreads;
 constexpr int kLsList = 1024;                        // pending ranges: disjoint, > 32 pairs each, so < cap / 33
 constexpr uint32_t kConstInline = 16384;             // constant buckets up to this size are checked inline
 constexpr uint32_t kConstChunk = 65536;              // chunk of the constant-bucket check
-constexpr size_t kLsStaticSmem = 2 * kLsList * 4 + 4096;
+constexpr size_t kLsStaticSmem = 2 * kLsList * 4 + 6144;
 constexpr size_t kSmemLimit = 227 * 1024;
 
 static_assert(kLsWarpBins == (1 << kLsWarpBinBits), "warp bins");
@@ -204,8 +204,8 @@ __device__ __forceinline__ uint32_t block_exclusive_sum(uint32_t x, uint32_t* ws
 // Step 2: one warp splits range A[p0, p0 + r) (r > kLsRank) into 256 bins of
 // its own window; short bins are finished at once, longer ones listed.
 template <int KW>
-__device__ void warp_split_range(const LsView<KW>& v, uint32_t p0, uint32_t r, uint32_t* wh, uint32_t* next,
-                                 uint32_t* next_count, uint32_t* fail) {
+__device__ void warp_split_range(const LsView<KW>& v, uint32_t p0, uint32_t r, uint32_t* wh, uint32_t* wpres,
+                                 uint32_t* next, uint32_t* next_count, uint32_t* fail) {
     constexpr uint32_t KC = KW + 1;
     const uint32_t lane = threadIdx.x & 31, pe = p0 + r;
     const uint32_t e0 = v.A[p0];
@@ -225,19 +225,64 @@ __device__ void warp_split_range(const LsView<KW>& v, uint32_t p0, uint32_t r, u
         return;
     }
     const LsWin W((uint32_t)(P >= 31 ? P - 31 : 0), KC);
+    // window range, and which values the window's top two bytes take (the
+    // warp's 2 x 256-bit bitmaps, a value's bit set once)
+    if (lane < 16) wpres[lane] = 0;
+    __syncwarp();
     uint32_t lo = 0xFFFFFFFFu, hi = 0;
-    for (uint32_t p = p0 + lane; p < pe; p += 32) {
-        const uint32_t x = W(v, v.A[p]);
-        lo = min(lo, x);
-        hi = max(hi, x);
+    {
+        volatile uint32_t* pr = wpres;
+        for (uint32_t p = p0 + lane; p < pe; p += 32) {
+            const uint32_t x = W(v, v.A[p]);
+            lo = min(lo, x);
+            hi = max(hi, x);
+            const uint32_t w1 = x >> 29, m1 = 1u << ((x >> 24) & 31u);
+            const uint32_t w2 = 8u + ((x >> 21) & 7u), m2 = 1u << ((x >> 16) & 31u);
+            if (!(pr[w1] & m1)) atomicOr(&wpres[w1], m1);
+            if (!(pr[w2] & m2)) atomicOr(&wpres[w2], m2);
+        }
     }
     lo = __reduce_min_sync(kFull, lo);
     hi = __reduce_max_sync(kFull, hi);
+    __syncwarp();
+    // The digit: 8 bits of the window above its minimum, unless the top byte
+    // is sparse (at most 64 of its values occur, as for keys over a small
+    // alphabet): then the dense code of the top byte times k2 plus the dense
+    // code of the second byte scaled to k2 levels (k2 = min(n2, 256 / n1)),
+    // which keeps the order and fills far more of the 256 bins (used when it
+    // reaches at least 128 of them).  Lane j < 16
+    // holds bitmap word j and the number of set bits before it in its byte, so
+    // a code is two shuffles and a popcount.
+    const uint32_t wj = lane < 16 ? wpres[lane] : 0u, cj = __popc(wj);
+    uint32_t incj = cj;
+#pragma unroll
+    for (int o = 1; o < 8; o <<= 1) {
+        const uint32_t t = __shfl_up_sync(kFull, incj, o);
+        if ((lane & 7u) >= (uint32_t)o) incj += t;
+    }
+    const uint32_t exj = incj - cj;
+    const uint32_t n1 = __shfl_sync(kFull, incj, 7), n2 = __shfl_sync(kFull, incj, 15);
+    uint32_t k2 = n1 >= 1 && n1 <= 64 ? min(n2, (uint32_t)kLsWarpBins / n1) : 1u;
+    const bool dense = n1 <= 64 && n1 * k2 >= 128;  // at least half the bins reachable
+    if (!dense) k2 = 1;
     const uint32_t bl = 32 - __clz(hi - lo);  // hi > lo: the window holds the top varying bit
     const uint32_t sh = bl > (uint32_t)kLsWarpBinBits ? bl - kLsWarpBinBits : 0u;
+    // every lane of the warp calls this (shuffles)
+    auto digit = [&](uint32_t x) -> uint32_t {
+        const uint32_t b1 = x >> 24, b2 = (x >> 16) & 255u;
+        const uint32_t c1 = __shfl_sync(kFull, exj, b1 >> 5) +
+                            __popc(__shfl_sync(kFull, wj, b1 >> 5) & ((1u << (b1 & 31u)) - 1u));
+        const uint32_t c2 = __shfl_sync(kFull, exj, 8u + (b2 >> 5)) +
+                            __popc(__shfl_sync(kFull, wj, 8u + (b2 >> 5)) & ((1u << (b2 & 31u)) - 1u));
+        return dense ? c1 * k2 + (k2 == n2 ? c2 : c2 * k2 / n2) : (x - lo) >> sh;
+    };
     for (uint32_t i = lane; i < (uint32_t)kLsWarpBins; i += 32) wh[i] = 0;
     __syncwarp();
-    for (uint32_t p = p0 + lane; p < pe; p += 32) atomicAdd(&wh[(W(v, v.A[p]) - lo) >> sh], 1u);
+    for (uint32_t q0 = p0; q0 < pe; q0 += 32) {  // warp-uniform trip count: digit() shuffles
+        const uint32_t p = q0 + lane;
+        const uint32_t d = digit(p < pe ? W(v, v.A[p]) : lo);
+        if (p < pe) atomicAdd(&wh[d], 1u);
+    }
     __syncwarp();
     {  // exclusive scan, 8 bins per lane
         uint32_t c[8], sum = 0;
@@ -260,10 +305,11 @@ __device__ void warp_split_range(const LsView<KW>& v, uint32_t p0, uint32_t r, u
         }
     }
     __syncwarp();
-    for (uint32_t p = p0 + lane; p < pe; p += 32) {
-        const uint32_t e = v.A[p];
-        const uint32_t q = atomicAdd(&wh[(W(v, e) - lo) >> sh], 1u);
-        v.T[p0 + q] = (uint16_t)e;
+    for (uint32_t q0 = p0; q0 < pe; q0 += 32) {
+        const uint32_t p = q0 + lane;
+        const uint32_t e = p < pe ? v.A[p] : 0u;
+        const uint32_t d = digit(p < pe ? W(v, e) : lo);
+        if (p < pe) v.T[p0 + atomicAdd(&wh[d], 1u)] = (uint16_t)e;
     }
     __syncwarp();
     for (uint32_t p = p0 + lane; p < pe; p += 32) v.A[p] = v.T[p];
@@ -444,7 +490,10 @@ __device__ void block_split(const LsView<KW>& v, uint32_t p0, uint32_t r, bool i
     const LsWin W((uint32_t)(P >= 31 ? P - 31 : 0), KC);
     uint32_t F = 32 - __clz(r - 1);  // 2^F >= r
     F = F < 8 ? 8u : (F > (uint32_t)kLsBinBits ? (uint32_t)kLsBinBits : F);
-    for (uint32_t d = tid; d < (uint32_t)kLsBins; d += kLsThreads) hist[d] = 0;
+    // bins of the dense digit: twice the power of two above the range's
+    // length (the scan and the bin lists cost in proportion to the bins)
+    const uint32_t dbins = F + 1 > (uint32_t)kLsBinBits ? (uint32_t)kLsBins : 2u << F;
+    for (uint32_t d = tid; d < dbins; d += kLsThreads) hist[d] = 0;
     if (tid < 24) st.pres[tid] = 0;
     if (tid == 0) {
         st.mm[0] = 0xFFFFFFFFu;
@@ -495,7 +544,7 @@ __device__ void block_split(const LsView<KW>& v, uint32_t p0, uint32_t r, bool i
     // bins), unless the top byte is sparse (at most 128 of its values occur,
     // as for keys over a small alphabet whose codes use few bit patterns):
     // then the mixed-radix number of the dense codes of the window's top
-    // bytes -- all values of the first, of the second as far as kLsBins
+    // bytes -- all values of the first, of the second as far as the bins
     // allows (scaled down to k2 levels otherwise), of the third within what is
     // left (k3 levels) -- which keeps the order of the windows and spreads the
     // pairs over far more of the bins, if that gives 256 bins or more.
@@ -503,8 +552,8 @@ __device__ void block_split(const LsView<KW>& v, uint32_t p0, uint32_t r, bool i
     uint32_t k2 = 1, k3 = 1;
     bool dense = false;
     if (n1 <= 128) {
-        k2 = min(n2, (uint32_t)kLsBins / n1);
-        k3 = k2 == n2 ? min(n3, (uint32_t)kLsBins / (n1 * n2)) : 1u;
+        k2 = min(n2, dbins / n1);
+        k3 = k2 == n2 ? min(n3, dbins / (n1 * n2)) : 1u;
         dense = n1 * k2 * k3 >= 256;
     }
     uint32_t bins = 1u << F;
@@ -928,6 +977,7 @@ __global__ void __launch_bounds__(kLsThreads, 1) local_sort_kernel(const LocalSo
     __shared__ uint32_t s_mm[2], s_bucket, s_cnt[2], s_grab, s_bcnt, s_bad;
     __shared__ uint32_t s_bstack[kLsBlockStack];
     __shared__ uint32_t s_bytes[768], s_pres[24], s_nbytes[3];
+    __shared__ uint32_t s_wpres[kLsWarps][16];  // warp splits: bitmaps of the window's top two bytes
     __shared__ uint32_t s_scan[kLsWarps + 1];
     const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     constexpr uint32_t K = KW, KC = KW + 1;
@@ -1074,8 +1124,8 @@ __global__ void __launch_bounds__(kLsThreads, 1) local_sort_kernel(const LocalSo
                     e = __shfl_sync(kFull, e, 0);
                     if (e >= nr) break;
                     const uint32_t r = s_list[cur][e];
-                    warp_split_range<KW>(v, r & 0xFFFFu, r >> 16, hist + warp * kLsWarpBins, s_list[cur ^ 1],
-                                         &s_cnt[cur ^ 1], &s_bad);
+                    warp_split_range<KW>(v, r & 0xFFFFu, r >> 16, hist + warp * kLsWarpBins, s_wpres[warp],
+                                         s_list[cur ^ 1], &s_cnt[cur ^ 1], &s_bad);
                 }
                 __syncthreads();
                 cur ^= 1;

@@ -96,6 +96,21 @@ WORKLOADS = {
 }
 
 
+@pytest.mark.parametrize("name,bucket_bits", [("urls", 8), ("dna", 8), ("zipf", 6)])
+def test_few_model_buckets_are_cut_to_capacity(name, bucket_bits):
+    """Model buckets far larger than a block holds (2^bucket_bits of them for
+    3M keys) are cut at sample quantiles into pieces a block can sort: no
+    bucket over capacity, no fallback, and the plain sort's bits."""
+    n = 3_000_000
+    keys = WORKLOADS[name](n)
+    kd, D, ck_in, K, nbits = compressed_column(keys)
+    st, s, _, out, rid = learned_sort(ck_in, n, K, nbits, bucket_bits=bucket_bits)
+    p_out, p_rid = plain_sort(ck_in, n, K, nbits)
+    assert st == ck.CK_OK and s["fell_back"] == 0 and s["oversize_buckets"] == 0, s
+    assert s["model_buckets"] == 1 << bucket_bits and s["buckets"] > n // s["capacity"], s
+    assert torch.equal(rid, p_rid) and torch.equal(out[:, :n], p_out[:, :n])
+
+
 @pytest.mark.parametrize("name", sorted(WORKLOADS))
 def test_learned_equals_plain(name):
     n = 2_000_003
