@@ -69,18 +69,21 @@ def test_reference_arm_under_torchrun_prints_one_line():
 
 def test_bench_roofline_inputs():
     """The bench's roofline inputs: the measured HBM peak from the committed
-    peaks file, and the ncu traffic record scaled by n only while the pass
-    kernel's source still has the hash it was captured with."""
+    peaks file, and each kernel's ncu traffic record scaled by n only while
+    the kernel's source file still has the hash it was captured with."""
     sys.path.insert(0, ROOT)
     import bench
     peak, src = bench.peaks()
     have = os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json"))
     assert src == ("measured" if have else "fallback") and peak > 1000
     with open(bench.TRAFFIC_FILE) as f:
-        rec = json.load(f)
-    t = bench.ncu_traffic(2 * rec["n"], rec["ck_words"])
-    if rec["kernel_src_sha"] == bench.file_sha(bench.PASS_SRC):   # counters taken on this kernel
-        assert t == 2 * rec["dram_bytes_per_launch"]
-    else:                                                          # kernel changed since: no figure
-        assert t is None
-    assert bench.ncu_traffic(rec["n"], rec["ck_words"] + 1) is None
+        recs = json.load(f)
+    assert recs
+    for kernel, rec in recs.items():
+        t = bench.ncu_traffic(kernel, 2 * rec["n"], rec["ck_words"])
+        if rec["kernel_src_sha"] == bench.file_sha(os.path.join(ROOT, rec["kernel_src"])):  # counters of this kernel
+            assert t == 2 * rec["dram_bytes_per_launch"]
+        else:                                                                        # changed since: no figure
+            assert t is None
+        assert bench.ncu_traffic(kernel, rec["n"], rec["ck_words"] + 1) is None
+    assert bench.ncu_traffic("no_such_kernel", 1000, 1) is None
