@@ -48,14 +48,15 @@ constexpr int kLsWarpBins = kLsBins / kLsWarps;      // 256 bins per warp in ste
 constexpr int kLsWarpBinBits = 8;
 constexpr uint32_t kLsSmall = 4;                     // bins up to this length: insertion sort by one thread
 constexpr uint32_t kLsRank = 32;                     // bins up to this length: rank sort by one warp
-constexpr uint32_t kLsBlockRange = 256;              // ranges from this length on are split by the whole block
+constexpr uint32_t kLsBlockRange = 256;              // ranges from this length on are split by a block group:
+constexpr uint32_t kLsGroupRange = 1024;             // a quarter of the block below this length, else the block
 constexpr int kLsBlockStack = 64;                    // such ranges are disjoint: at most cap / 256
 constexpr int kLsPerThread = 16;                     // register staging of row ids: cap <= 16 * 1024
 constexpr uint32_t kLsMaxCap = kLsPerThread * kLsThreads;
-constexpr int kLsList = 1024;                        // pending ranges: disjoint, > 32 pairs each, so < cap / 33
+constexpr int kLsList = 512;                         // pending ranges: disjoint, > 32 pairs each, so < cap / 33
 constexpr uint32_t kConstInline = 16384;             // constant buckets up to this size are checked inline
 constexpr uint32_t kConstChunk = 65536;              // chunk of the constant-bucket check
-constexpr size_t kLsStaticSmem = 2 * kLsList * 4 + 6144;
+constexpr size_t kLsStaticSmem = 2 * kLsList * 4 + 11264;
 constexpr size_t kSmemLimit = 227 * 1024;
 
 static_assert(kLsWarpBins == (1 << kLsWarpBinBits), "warp bins");
@@ -171,10 +172,28 @@ __device__ __forceinline__ void push_range(uint32_t* list, uint32_t* count, uint
     else atomicAdd(fail, 1u);  // cannot happen (disjoint ranges of more than kLsRank pairs)
 }
 
-// Block-wide exclusive prefix of one value per thread; *total = the sum.
-__device__ __forceinline__ uint32_t block_exclusive_sum(uint32_t x, uint32_t* wsum /*[kLsWarps + 1]*/,
-                                                        uint32_t* total) {
-    const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+// A group of G consecutive threads of the block that splits one range: the
+// whole block (G = kLsThreads, barrier 0), or a quarter of it (G = 256),
+// which waits on its own named barrier 1 + gid so that four ranges are split
+// side by side.
+template <int G>
+struct LsGroup {
+    static constexpr uint32_t kThreads = G, kWarps = G / 32;
+    uint32_t gid;
+    __device__ __forceinline__ uint32_t tid() const { return threadIdx.x % G; }
+    __device__ __forceinline__ void sync() const {
+        if (G == kLsThreads) __syncthreads();
+        else asm volatile("bar.sync %0, %1;" ::"r"(1u + gid), "r"(G) : "memory");
+    }
+};
+using LsBlock = LsGroup<kLsThreads>;
+
+// Group-wide exclusive prefix of one value per thread; *total = the sum.
+template <int G = kLsThreads>
+__device__ __forceinline__ uint32_t block_exclusive_sum(uint32_t x, uint32_t* wsum /*[kWarps + 1]*/,
+                                                        uint32_t* total, LsGroup<G> grp = LsGroup<G>{0}) {
+    constexpr uint32_t kWarps = LsGroup<G>::kWarps;
+    const uint32_t lane = threadIdx.x & 31, warp = grp.tid() >> 5;
     uint32_t inc = x;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
@@ -182,22 +201,22 @@ __device__ __forceinline__ uint32_t block_exclusive_sum(uint32_t x, uint32_t* ws
         if (lane >= (uint32_t)o) inc += t;
     }
     if (lane == 31) wsum[warp] = inc;
-    __syncthreads();
+    grp.sync();
     if (warp == 0) {
-        const uint32_t w = lane < (uint32_t)kLsWarps ? wsum[lane] : 0u;
+        const uint32_t w = lane < kWarps ? wsum[lane] : 0u;
         uint32_t wi = w;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
             const uint32_t t = __shfl_up_sync(kFull, wi, o);
             if (lane >= (uint32_t)o) wi += t;
         }
-        if (lane < (uint32_t)kLsWarps) wsum[lane] = wi - w;
-        if (lane == 31) wsum[kLsWarps] = wi;
+        if (lane < kWarps) wsum[lane] = wi - w;
+        if (lane == 31) wsum[kWarps] = wi;
     }
-    __syncthreads();
+    grp.sync();
     const uint32_t r = wsum[warp] + inc - x;
-    *total = wsum[kLsWarps];
-    __syncthreads();
+    *total = wsum[kWarps];
+    grp.sync();
     return r;
 }
 
@@ -404,9 +423,12 @@ __device__ __forceinline__ void check_constant(const LocalSortArgs& a, uint32_t 
 // kLsBins) by the block; warp w scans the w-th 32nd of the bins with its
 // lanes on consecutive bins (no bank conflicts), then the warps' totals are
 // scanned and added.
-__device__ __forceinline__ void bins_exclusive_scan(uint32_t* hist, uint32_t bins, uint32_t* wsum) {
-    const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const uint32_t seg = bins / kLsWarps, c0 = warp * seg;
+template <int G = kLsThreads>
+__device__ __forceinline__ void bins_exclusive_scan(uint32_t* hist, uint32_t bins, uint32_t* wsum,
+                                                    LsGroup<G> grp = LsGroup<G>{0}) {
+    constexpr uint32_t kWarps = LsGroup<G>::kWarps;
+    const uint32_t lane = threadIdx.x & 31, warp = grp.tid() >> 5;
+    const uint32_t seg = bins / kWarps, c0 = warp * seg;
     uint32_t run = 0;
     for (uint32_t k = 0; k < seg; k += 32) {
         const bool in = k + lane < seg;
@@ -421,21 +443,21 @@ __device__ __forceinline__ void bins_exclusive_scan(uint32_t* hist, uint32_t bin
         run += __shfl_sync(kFull, inc, 31);
     }
     if (lane == 0) wsum[warp] = run;
-    __syncthreads();
+    grp.sync();
     if (warp == 0) {
-        const uint32_t x = wsum[lane];
+        const uint32_t x = lane < kWarps ? wsum[lane] : 0u;
         uint32_t inc = x;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
             const uint32_t t = __shfl_up_sync(kFull, inc, o);
             if (lane >= (uint32_t)o) inc += t;
         }
-        wsum[lane] = inc - x;
+        if (lane < kWarps) wsum[lane] = inc - x;
     }
-    __syncthreads();
+    grp.sync();
     const uint32_t add = wsum[warp];
     for (uint32_t k = lane; k < seg; k += 32) hist[c0 + k] += add;
-    __syncthreads();
+    grp.sync();
 }
 
 // Shared state of the block-level splits.
@@ -447,29 +469,32 @@ struct LsBlockState {
     uint32_t* orw;     // [KC]
     uint32_t* mm;      // [2]: window minimum, maximum
     uint32_t* wsum;    // [kLsWarps + 1]
-    uint32_t* bytes;   // [3][256]: dense codes (digit terms) of the window's top three bytes
+    uint16_t* bytes;   // [3][256]: dense codes (digit terms, < kLsBins) of the window's top three bytes
     uint32_t* pres;    // [3][8]: which values each of those bytes takes (bitmaps)
     uint32_t* nbytes;  // [3]: values in use of each byte
 };
 
-// Step 1 on range A[p0, p0 + r) by the whole block.  ident: the range is the
-// whole bucket in load order (A not yet written; element = position), and
-// st.orw already holds the OR of every key word's difference to element p0.
-// Ends with every bin of the range listed or finished, and a barrier.
-template <int KW>
+// Step 1 on range A[p0, p0 + r) by a group of G threads (the whole block,
+// or a quarter of it for ranges short enough for its quarter of the bins,
+// hist[0, 2^(F+1))).  ident (whole block only): the range is the whole bucket
+// in load order (A not yet written; element = position), and st.orw already
+// holds the OR of every key word's difference to element p0.  Ends with every
+// bin of the range listed or finished, and a barrier of the group.
+template <int KW, int G = kLsThreads>
 __device__ void block_split(const LsView<KW>& v, uint32_t p0, uint32_t r, bool ident, uint32_t* hist,
-                            const LsBlockState& st, uint32_t* bad) {
+                            const LsBlockState& st, uint32_t* bad, LsGroup<G> grp = LsGroup<G>{0}) {
     constexpr uint32_t KC = KW + 1;
-    const uint32_t tid = threadIdx.x, lane = tid & 31;
+    constexpr uint32_t kWarps = LsGroup<G>::kWarps;
+    const uint32_t tid = grp.tid(), lane = tid & 31;
     const uint32_t pe = p0 + r;
     if (!ident) {  // OR of every composite word's difference to the range's first element
         if (tid < KC) st.orw[tid] = 0;
-        __syncthreads();
+        grp.sync();
         const uint32_t e0 = v.A[p0];
         uint32_t o[KC];
 #pragma unroll
         for (uint32_t w = 0; w < KC; ++w) o[w] = 0;
-        for (uint32_t p = p0 + tid; p < pe; p += kLsThreads) {
+        for (uint32_t p = p0 + tid; p < pe; p += G) {
             const uint32_t e = v.A[p];
 #pragma unroll
             for (uint32_t w = 0; w < KC; ++w) o[w] |= v.cw(e, w) ^ v.cw(e0, w);
@@ -479,12 +504,12 @@ __device__ void block_split(const LsView<KW>& v, uint32_t p0, uint32_t r, bool i
             const uint32_t x = __reduce_or_sync(kFull, o[w]);
             if (lane == 0 && x) atomicOr(&st.orw[w], x);
         }
-        __syncthreads();
+        grp.sync();
     }
     const int P = top_bit_of<KC>(st.orw);
     if (P < 0) {  // one key in a bucket of equal keys (ident): already in order
-        for (uint32_t p = p0 + tid; p < pe; p += kLsThreads) v.A[p] = (uint16_t)p;
-        __syncthreads();
+        for (uint32_t p = p0 + tid; p < pe; p += G) v.A[p] = (uint16_t)p;
+        grp.sync();
         return;
     }
     const LsWin W((uint32_t)(P >= 31 ? P - 31 : 0), KC);
@@ -493,19 +518,19 @@ __device__ void block_split(const LsView<KW>& v, uint32_t p0, uint32_t r, bool i
     // bins of the dense digit: twice the power of two above the range's
     // length (the scan and the bin lists cost in proportion to the bins)
     const uint32_t dbins = F + 1 > (uint32_t)kLsBinBits ? (uint32_t)kLsBins : 2u << F;
-    for (uint32_t d = tid; d < dbins; d += kLsThreads) hist[d] = 0;
+    for (uint32_t d = tid; d < dbins; d += G) hist[d] = 0;
     if (tid < 24) st.pres[tid] = 0;
     if (tid == 0) {
         st.mm[0] = 0xFFFFFFFFu;
         st.mm[1] = 0;
     }
-    __syncthreads();  // mm initialised, bins and byte bitmaps zeroed
+    grp.sync();  // mm initialised, bins and byte bitmaps zeroed
     {  // window range, and which values the window's top three bytes take: a
        // value's bit is set once (a plain read first), so keys over a small
        // alphabet, whose bytes take few values, do not queue on a few words
         uint32_t lo = 0xFFFFFFFFu, hi = 0;
         volatile uint32_t* pr = st.pres;
-        for (uint32_t p = p0 + tid; p < pe; p += kLsThreads) {
+        for (uint32_t p = p0 + tid; p < pe; p += G) {
             const uint32_t x = W(v, ident ? p : v.A[p]);
             lo = min(lo, x);
             hi = max(hi, x);
@@ -523,7 +548,7 @@ __device__ void block_split(const LsView<KW>& v, uint32_t p0, uint32_t r, bool i
             atomicMax(&st.mm[1], hi);
         }
     }
-    __syncthreads();
+    grp.sync();
     if (tid < 96) {  // dense codes of the values each byte takes (warp j: byte j; lane l: values 8l .. 8l + 7)
         const uint32_t j = tid >> 5;
         const uint32_t bits = (st.pres[8 * j + (lane >> 2)] >> (8 * (lane & 3u))) & 255u;
@@ -536,10 +561,11 @@ __device__ void block_split(const LsView<KW>& v, uint32_t p0, uint32_t r, bool i
         }
         const uint32_t run = inc - c;
 #pragma unroll
-        for (uint32_t i = 0; i < 8; ++i) st.bytes[256 * j + 8 * lane + i] = run + __popc(bits & ((1u << i) - 1u));
+        for (uint32_t i = 0; i < 8; ++i)
+            st.bytes[256 * j + 8 * lane + i] = (uint16_t)(run + __popc(bits & ((1u << i) - 1u)));
         if (lane == 31) st.nbytes[j] = inc;
     }
-    __syncthreads();
+    grp.sync();
     // The digit: the window's top bits after subtracting its minimum (2^F
     // bins), unless the top byte is sparse (at most 128 of its values occur,
     // as for keys over a small alphabet whose codes use few bit patterns):
@@ -560,43 +586,43 @@ __device__ void block_split(const LsView<KW>& v, uint32_t p0, uint32_t r, bool i
     if (dense) {
         bins = (n1 * k2 * k3 + 31) & ~31u;  // whole segments of the bin scan; the extra bins stay empty
         // codes -> digit terms: c1 k2 k3, scaled c2 times k3, scaled c3
-        for (uint32_t i = tid; i < 768; i += kLsThreads) {
+        for (uint32_t i = tid; i < 768; i += G) {
             const uint32_t j = i >> 8, c = st.bytes[i];
-            st.bytes[i] = j == 0 ? c * k2 * k3
-                                 : (j == 1 ? (k2 == n2 ? c : c * k2 / n2) * k3 : (k3 == n3 ? c : c * k3 / n3));
+            st.bytes[i] = (uint16_t)(j == 0 ? c * k2 * k3
+                                            : (j == 1 ? (k2 == n2 ? c : c * k2 / n2) * k3 : (k3 == n3 ? c : c * k3 / n3)));
         }
-        __syncthreads();
+        grp.sync();
     }
     const uint32_t wmin = st.mm[0];
     const uint32_t bl = 32 - __clz(st.mm[1] - wmin);
     const uint32_t sh = bl > F ? bl - F : 0u;
-    const uint32_t* c1 = st.bytes;
-    const uint32_t* c2 = st.bytes + 256;
-    const uint32_t* c3 = st.bytes + 512;
+    const uint16_t* c1 = st.bytes;
+    const uint16_t* c2 = st.bytes + 256;
+    const uint16_t* c3 = st.bytes + 512;
     auto digit = [&](uint32_t x) -> uint32_t {
         return dense ? c1[x >> 24] + c2[(x >> 16) & 255u] + c3[(x >> 8) & 255u] : (x - wmin) >> sh;
     };
-    for (uint32_t p = p0 + tid; p < pe; p += kLsThreads) atomicAdd(&hist[digit(W(v, ident ? p : v.A[p]))], 1u);
-    __syncthreads();
-    bins_exclusive_scan(hist, bins, st.wsum);
+    for (uint32_t p = p0 + tid; p < pe; p += G) atomicAdd(&hist[digit(W(v, ident ? p : v.A[p]))], 1u);
+    grp.sync();
+    bins_exclusive_scan<G>(hist, bins, st.wsum, grp);
     if (ident) {
-        for (uint32_t p = tid; p < r; p += kLsThreads) v.A[atomicAdd(&hist[digit(W(v, p))], 1u)] = (uint16_t)p;
+        for (uint32_t p = tid; p < r; p += G) v.A[atomicAdd(&hist[digit(W(v, p))], 1u)] = (uint16_t)p;
     } else {
-        for (uint32_t p = p0 + tid; p < pe; p += kLsThreads) {
+        for (uint32_t p = p0 + tid; p < pe; p += G) {
             const uint32_t e = v.A[p];
             v.T[p0 + atomicAdd(&hist[digit(W(v, e))], 1u)] = (uint16_t)e;
         }
-        __syncthreads();
-        for (uint32_t p = p0 + tid; p < pe; p += kLsThreads) v.A[p] = v.T[p];
+        grp.sync();
+        for (uint32_t p = p0 + tid; p < pe; p += G) v.A[p] = v.T[p];
     }
-    __syncthreads();
+    grp.sync();
     // hist[d] is now the end of bin d (relative to p0).  Long bins are listed
     // for the block or the warps; the short ones densely in T[p0 ..] as
     // (start, length) pairs, 2 .. 4 pairs from the front (one thread each),
     // 5 .. 32 from the back (one warp each).  A listed bin has two pairs or
     // more, so both lists fit the range's r entries of T.
     uint32_t nsmall = 0, nrank = 0;
-    for (uint32_t d = tid; d < bins; d += kLsThreads) {
+    for (uint32_t d = tid; d < bins; d += G) {
         const uint32_t b0 = d ? hist[d - 1] : 0u, sz = hist[d] - b0;
         if (sz >= kLsBlockRange) {
             const uint32_t slot = atomicAdd(st.scount, 1u);
@@ -609,9 +635,9 @@ __device__ void block_split(const LsView<KW>& v, uint32_t p0, uint32_t r, bool i
         nrank += (sz > kLsSmall && sz <= kLsRank) ? 1u : 0u;
     }
     uint32_t ns_tot, nr_tot;
-    uint32_t as = block_exclusive_sum(nsmall, st.wsum, &ns_tot);
-    uint32_t ar = block_exclusive_sum(nrank, st.wsum, &nr_tot);
-    for (uint32_t d = tid; d < bins; d += kLsThreads) {
+    uint32_t as = block_exclusive_sum<G>(nsmall, st.wsum, &ns_tot, grp);
+    uint32_t ar = block_exclusive_sum<G>(nrank, st.wsum, &nr_tot, grp);
+    for (uint32_t d = tid; d < bins; d += G) {
         const uint32_t b0 = d ? hist[d - 1] : 0u, sz = hist[d] - b0;
         if (sz >= 2 && sz <= kLsSmall) {
             v.T[p0 + 2 * as] = (uint16_t)(p0 + b0);
@@ -623,11 +649,11 @@ __device__ void block_split(const LsView<KW>& v, uint32_t p0, uint32_t r, bool i
             ++ar;
         }
     }
-    __syncthreads();
-    for (uint32_t k = tid; k < ns_tot; k += kLsThreads) insertion_sort(v, v.T[p0 + 2 * k], v.T[p0 + 2 * k + 1]);
-    for (uint32_t k = tid >> 5; k < nr_tot; k += kLsWarps)
+    grp.sync();
+    for (uint32_t k = tid; k < ns_tot; k += G) insertion_sort(v, v.T[p0 + 2 * k], v.T[p0 + 2 * k + 1]);
+    for (uint32_t k = tid >> 5; k < nr_tot; k += kWarps)
         warp_rank_sort(v, W, v.T[pe - 2 - 2 * k], v.T[pe - 1 - 2 * k]);
-    __syncthreads();
+    grp.sync();
 }
 
 
@@ -976,7 +1002,12 @@ __global__ void __launch_bounds__(kLsThreads, 1) local_sort_kernel(const LocalSo
     __shared__ uint32_t s_or[kMaxLearnedWords + 1];
     __shared__ uint32_t s_mm[2], s_bucket, s_cnt[2], s_grab, s_bcnt, s_bad;
     __shared__ uint32_t s_bstack[kLsBlockStack];
-    __shared__ uint32_t s_bytes[768], s_pres[24], s_nbytes[3];
+    __shared__ uint16_t s_bytes[768];
+    __shared__ uint32_t s_pres[24], s_nbytes[3];
+    // the four quarter-block groups' own split state
+    __shared__ uint32_t s_gor[4][kMaxLearnedWords + 1], s_gmm[4][2], s_gwsum[4][kLsThreads / 4 / 32 + 1];
+    __shared__ uint16_t s_gbytes[4][768];
+    __shared__ uint32_t s_gpres[4][24], s_gnbytes[4][3];
     __shared__ uint32_t s_wpres[kLsWarps][16];  // warp splits: bitmaps of the window's top two bytes
     __shared__ uint32_t s_scan[kLsWarps + 1];
     const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -1003,6 +1034,16 @@ __global__ void __launch_bounds__(kLsThreads, 1) local_sort_kernel(const LocalSo
     bst.bytes = s_bytes;
     bst.pres = s_pres;
     bst.nbytes = s_nbytes;
+    LsBlockState gst = bst;  // this thread's quarter-block group (ranges shorter than kLsGroupRange)
+    {
+        const uint32_t g = tid / (kLsThreads / 4);
+        gst.orw = s_gor[g];
+        gst.mm = s_gmm[g];
+        gst.wsum = s_gwsum[g];
+        gst.bytes = s_gbytes[g];
+        gst.pres = s_gpres[g];
+        gst.nbytes = s_gnbytes[g];
+    }
     uint64_t my_hash = 0;
     uint32_t my_bad = 0;
     for (;;) {
@@ -1100,12 +1141,25 @@ __global__ void __launch_bounds__(kLsThreads, 1) local_sort_kernel(const LocalSo
         // step 1 on the bucket, then on every long range, then the warp rounds
         block_split<KW>(v, 0, m, true, hist, bst, &s_bad);
         for (;;) {
+            // up to four ranges shorter than kLsGroupRange from the top of the
+            // stack, each split by a quarter of the block on a quarter of the
+            // bins (a split is bound by its chain of barriers, so four at a
+            // time take little longer than one); else the top range, by the block
             const uint32_t nbk = s_bcnt;
             if (nbk == 0) break;
-            const uint32_t r = s_bstack[nbk - 1];
-            __syncthreads();  // every thread has read the top of the stack
-            if (tid == 0) s_bcnt = nbk - 1;
-            block_split<KW>(v, r & 0xFFFFu, r >> 16, false, hist, bst, &s_bad);
+            uint32_t k = 0;
+            while (k < 4 && k < nbk && (s_bstack[nbk - 1 - k] >> 16) < kLsGroupRange) ++k;
+            const uint32_t g = tid / (kLsThreads / 4);
+            const uint32_t r = s_bstack[nbk - 1 - (g < k ? g : 0u)];
+            __syncthreads();  // every thread has read the stack
+            if (tid == 0) s_bcnt = nbk - (k ? k : 1u);
+            __syncthreads();  // the pops precede any push of the splits below
+            if (k == 0)
+                block_split<KW>(v, r & 0xFFFFu, r >> 16, false, hist, bst, &s_bad);
+            else if (g < k)
+                block_split<KW, kLsThreads / 4>(v, r & 0xFFFFu, r >> 16, false, hist + g * (kLsBins / 4), gst, &s_bad,
+                                                LsGroup<kLsThreads / 4>{g});
+            __syncthreads();
         }
         {
             uint32_t cur = 0;
