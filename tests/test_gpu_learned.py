@@ -3,8 +3,9 @@
 The CDF model's forward/backward kernel is checked against the fp64 oracle;
 the learned sort must give exactly the bits of the plain radix sort (itself
 pinned to the oracle), with heavy duplicate keys, skewed and uniform columns,
-the forced-fallback path and the no-model baseline; the trained model must
-place keys closer to their bucket than the untrained baseline does."""
+the forced-fallback path, the no-model run, few model buckets and long
+shared-prefix ranges; training lowers the loss deterministically, and on
+smooth CDFs the trained model sets most bucket boundaries itself."""
 import numpy as np
 import pytest
 
@@ -122,6 +123,40 @@ def test_learned_equals_plain(name):
     assert torch.equal(out[:, :n], ref_ck[:, :n])
     assert st == ck.CK_OK and stats["fell_back"] == 0, stats
     assert ck.ck_device_status()[0] == ck.CK_OK
+
+
+def prefix_group_keys(rng, n, groups, lo, hi, plen=24, width=32):
+    """ACGT keys in which groups of lo..hi keys share a plen-character prefix
+    (and a few share whole keys), the rest i.i.d.: buckets then hold shared-
+    prefix ranges of every length class of the local sort."""
+    alpha = np.frombuffer(b"ACGT", np.uint8)
+    keys = alpha[rng.integers(0, 4, (n, width))]
+    at = 0
+    for _ in range(groups):
+        g = int(rng.integers(lo, hi + 1))
+        if at + g > n:
+            break
+        keys[at:at + g, :plen] = alpha[rng.integers(0, 4, plen)]
+        keys[at:at + g // 50, plen:] = keys[at, plen:]            # duplicates inside the group
+        at += g
+    return keys[rng.permutation(n)]
+
+
+@pytest.mark.parametrize("lo,hi", [(256, 1023), (100, 3000)])
+def test_learned_shared_prefix_ranges(lo, hi):
+    """Shared-prefix groups long enough that a bucket's first split leaves
+    ranges of 256..1023 pairs (split four at a time by quarter-block groups)
+    and of 1024 or more (split by the whole block), beside short ones (warps):
+    the learned sort equals the plain sort bit for bit, without fallback."""
+    rng = np.random.default_rng(lo + hi)
+    n = 2_000_000
+    keys = prefix_group_keys(rng, n, n // ((lo + hi) // 2) // 2, lo, hi)
+    kd, D, ck_in, K, nbits = compressed_column(keys)
+    ref_ck, ref_rid = plain_sort(ck_in, n, K, nbits)
+    st, stats, params, out, rid = learned_sort(ck_in, n, K, nbits)
+    assert st == ck.CK_OK and stats["fell_back"] == 0, stats
+    assert torch.equal(rid, ref_rid)
+    assert torch.equal(out[:, :n], ref_ck[:, :n])
 
 
 def test_learned_matches_oracle_small():
