@@ -1186,20 +1186,16 @@ __global__ void __launch_bounds__(kLsThreads, 1) local_sort_kernel(const LocalSo
             }
         }
         __syncthreads();
-        // checks in shared memory: composite keys ascend; the keys lie in the bucket's range
-        for (uint32_t t = tid + 1; t < m; t += kLsThreads)
-            if (!v.less(v.A[t - 1], v.A[t])) ++my_bad;
+        // the keys lie in the bucket's range
         if (tid == 0) {
             if (b > 0 && cmp_key_spl(v, v.A[0], a.spl + (size_t)(b - 1) * K) < 0) ++my_bad;
             if (b + 1 < nb && cmp_key_spl(v, v.A[m - 1], a.spl + (size_t)b * K) >= 0) ++my_bad;
         }
-        // write the bucket back in order: keys from shared memory, row ids
-        // gathered into registers first (the bucket is rewritten in place)
-        for (uint32_t t = tid; t < m; t += kLsThreads) {
-            const uint32_t e = v.A[t];
-#pragma unroll
-            for (uint32_t w = 0; w < K; ++w) a.ck[(uint64_t)w * a.ld + s0 + t] = v.key(e, w);
-        }
+        // row ids gathered into registers (the bucket is rewritten in place,
+        // so every read precedes the barrier below), then one pass of checks:
+        // adjacent keys ascend, equal keys by position and by row id (the row
+        // id of the pair before comes from the neighbouring lane, or, for a
+        // warp's first lane, from the row ids not yet overwritten)
         uint32_t rr[kLsPerThread];
         const uint32_t jmax = (m + kLsThreads - 1) / kLsThreads;
 #pragma unroll
@@ -1211,7 +1207,30 @@ __global__ void __launch_bounds__(kLsThreads, 1) local_sort_kernel(const LocalSo
             const uint32_t other = __shfl_xor_sync(kFull, rr[0], 1);
             if (warp == 0 && lane < 2 && m >= 2) rr[0] = other;
         }
+#pragma unroll
+        for (int j = 0; j < kLsPerThread; ++j) {
+            if ((uint32_t)j >= jmax) break;  // uniform: every lane of the block has the same jmax
+            const uint32_t t = tid + (uint32_t)j * kLsThreads;
+            const uint32_t before = __shfl_up_sync(kFull, rr[j], 1);
+            if (t >= 1 && t < m) {
+                const uint32_t e = v.A[t - 1], f = v.A[t];
+                int c = 0;
+#pragma unroll
+                for (int w = KW - 1; w >= 0 && c == 0; --w) {
+                    const uint32_t x = v.key(e, w), y = v.key(f, w);
+                    c = x < y ? -1 : (x > y ? 1 : 0);
+                }
+                if (c > 0) {
+                    ++my_bad;
+                } else if (c == 0) {
+                    const uint32_t rp = lane ? before : a.rid[s0 + e];
+                    if (e >= f || rp >= rr[j]) ++my_bad;
+                }
+            }
+        }
         __syncthreads();
+        // write the bucket back in order: keys from shared memory, the row
+        // ids from registers, and the hash of every output pair
 #pragma unroll
         for (int j = 0; j < kLsPerThread; ++j) {
             const uint32_t t = tid + (uint32_t)j * kLsThreads;
@@ -1220,14 +1239,14 @@ __global__ void __launch_bounds__(kLsThreads, 1) local_sort_kernel(const LocalSo
                 const uint32_t e = v.A[t];
                 uint64_t h = pair_hash_start(rr[j]);
 #pragma unroll
-                for (uint32_t w = 0; w < K; ++w) h = pair_hash_word(h, v.key(e, w));
+                for (uint32_t w = 0; w < K; ++w) {
+                    const uint32_t x = v.key(e, w);
+                    a.ck[(uint64_t)w * a.ld + s0 + t] = x;
+                    h = pair_hash_word(h, x);
+                }
                 my_hash += pair_hash_end(h);
             }
         }
-        __syncthreads();
-        // equal keys must leave in increasing row-id order
-        for (uint32_t t = tid + 1; t < m; t += kLsThreads)
-            if (v.same_key(v.A[t - 1], v.A[t]) && a.rid[s0 + t - 1] >= a.rid[s0 + t]) ++my_bad;
         if (tid == 0) atomicAdd(&misc->counts[0], 1u);
         __syncthreads();
     }
