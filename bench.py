@@ -576,7 +576,12 @@ def measure_config(args, workload, world, local_rank, headline=False, extras=Fal
                                                               else "onesweep_pass_kernel_partition", n, R.K),
                                        "alg_bytes_per_launch": pb[dom],
                                        "avg_launch_ms": phases[dom],
-                                       "phase_alg_bytes": pb}}
+                                       "phase_alg_bytes": pb,
+                                       "note": ("the bucket sorts move each pair once each way; their time is bound "
+                                                "by the chain of block-wide phases per bucket (barrier stalls, "
+                                                "shared-memory latency), not by DRAM, which is about 6% busy: "
+                                                "profiles/local_sort_dna20m.md") if dom == "bucket_sorts_checks"
+                                       else "two radix passes over the bucket id"}}
     rec["roofline"] = rec["learned"]["roofline"] if headline_learned else plain_roof
     rec["gpu_launches_per_step"] = l_launch if headline_learned else p_launch
     V = L if headline_learned else R
