@@ -207,6 +207,8 @@ WORD_FORM_MASKS = {
     "ascii": [0, 0, 0x0000001F, 0x1F1F1F5F, 0x5F180000, 0x7F7F7F7F, 0x7F7F7F7F, 0x7F7F7F7F],
     # two runs per byte, the DNA column's words
     "dna": [0x16161616] * 4 + [0x16141400, 0, 0x16161616, 0x16161404],
+    # one byte mask in all four bytes
+    "bytes": [0x0E0E0E0E, 0x63636363, 0x81818181, 0x41414141, 0x3C3C3C3C, 0x16161616, 0x07070707, 0x18181818],
     # one- and two-run words: full, top, bottom, middle, split; then scattered bits
     "runs": [0xFFFFFFFF, 0xFFFFFFF8, 0x000000FF, 0x80000000, 0x00000001, 0x00FFFF00, 0xF000000F, 0x0003C000,
              0xCA94A8A1, 0x30BA202C, 0x55555555, 0],

@@ -59,11 +59,17 @@ def test_word_programs_match_pext(ckmod):
     """The per-word form the extraction kernel runs: one- and two-run masks
     (shift-and-mask terms, including a full word and runs touching bit 0 or
     bit 31), masks of three or more runs (the network with its zero rounds
-    skipped), and mask words of the URL, DNA, Zipf and integer workloads."""
+    skipped; among them every byte mask repeated in all four bytes), and mask
+    words of the URL, DNA, Zipf and integer workloads."""
     rng = np.random.default_rng(1)
     masks = [0xFFFFFFFF, 0x80000000, 0x00000001, 0x0000001F, 0xFFFFFFF8, 0x7F000000, 0xF000000F,
              0x00FF0F00, 0x7F7F7F7F, 0x1F1F1F5F, 0x5F180000, 0x16161616, 0x16141400, 0xCA94A8A1,
-             0x30BA202C, 0x55555555, 0xAAAAAAAA]
+             0x30BA202C, 0x55555555, 0xAAAAAAAA,
+             # one byte mask in all four bytes
+             0x16161616, 0x0E0E0E0E, 0x63636363, 0x81818181, 0x7E7E7E7E, 0x3C3C3C3C, 0x41414141, 0x07070707,
+             0xC0C0C0C0, 0x18181818, 0x01010101, 0x80808080]
+    for b in range(1, 255):                    # every byte mask, in all four bytes
+        masks.append(b * 0x01010101)
     for _ in range(200):                       # random one- and two-run masks
         a, b = sorted(int(v) for v in rng.integers(0, 33, 2))
         c, d = sorted(int(v) for v in rng.integers(0, 33, 2))
