@@ -40,8 +40,8 @@
  *   - Row ids are uint32; n <= CK_MAX_ROWS.
  *   - Every call is asynchronous on the given stream (NULL = the legacy default
  *     stream) and allocates no device memory, except where its comment says
- *     otherwise (ck_insert_batch and ck_autotune_sort synchronise the stream;
- *     ck_btree_plan and ck_partial_key_mask touch no device).  The caller owns
+ *     otherwise (ck_autotune_sort synchronises the stream; ck_btree_plan and
+ *     ck_partial_key_mask touch no device).  The caller owns
  *     every buffer.
  *     Device pointers must come from cudaMalloc (or torch) on the current
  *     device; HOST pointers are read before the call returns.
@@ -494,8 +494,10 @@ ck_status ck_build_index_keys(const ck_column* col, const uint32_t* sorted_rid, 
  *              layout of ck_distinction_bits), updated in place.
  *   ws         device workspace of ck_insert_workspace_bytes(m, key_bytes)
  *              bytes, 256-byte aligned (sorts the batch).
- * The call synchronises the stream once (the batch's varying bits size its
- * sort).  Errors: CK_EINVAL (shape or kind mismatch, n = 0, ref_row >= n, an
+ * The batch is sorted by its full keys (a superset of its D-bitmap, known
+ * without reading the device), so the call never waits for the GPU and can
+ * be captured in a CUDA graph.  Errors: CK_EINVAL (shape or kind mismatch,
+ * n = 0, ref_row >= n, an
  * order entry >= n is skipped and recorded in the device status word),
  * CK_ENOMEM (ws too small), CK_ECUDA. */
 size_t ck_insert_workspace_bytes(uint64_t m, uint32_t key_bytes);

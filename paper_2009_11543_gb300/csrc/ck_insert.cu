@@ -33,11 +33,6 @@ __device__ __forceinline__ void merge(const uint32_t* sm, uint32_t nwords32, uin
     }
 }
 
-__global__ void iota_u32(uint32_t* out, uint64_t m) {
-    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (uint64_t)gridDim.x * blockDim.x)
-        out[i] = (uint32_t)i;
-}
-
 // One thread per batch key in sorted position j (grid-stride, warp-uniform
 // trip count for the warp-wide marking).
 template <int VEC, int QW>
@@ -125,15 +120,13 @@ size_t a256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct InsertPlan {
     uint32_t K;  // words of the batch's sort key (upper bound for the workspace)
-    size_t off_mask, off_ck, off_ck_sorted, off_rid, off_sort_ws, total;
+    size_t off_ck, off_ck_sorted, off_rid, off_sort_ws, total;
 };
 
 bool make_insert_plan(uint64_t m, uint32_t key_bytes, InsertPlan* p) {
     const uint32_t nwords = (key_bytes + 3) / 4;
     p->K = nwords;
     size_t off = 0;
-    p->off_mask = off;
-    off = a256(off + 8 * ((8ull * key_bytes + 63) / 64));
     p->off_ck = off;
     off = a256(off + 4ull * nwords * CK_LD(m));
     p->off_ck_sorted = off;
@@ -180,30 +173,19 @@ ck_status ck_insert_batch(const ck_column* keys, const uint32_t* order, const ck
     auto at = [&](size_t off) { return reinterpret_cast<uint32_t*>(ws + off); };
     uint32_t* border = at(P.off_rid);
 
-    // 1. the batch's sorted order, by its own varying bits (any superset of its
-    //    D-bitmap orders it, Theorem 2)
-    uint64_t* bmask = reinterpret_cast<uint64_t*>(ws + P.off_mask);
-    ck_status st = ck_variant_bits(batch, 0, bmask, stream);
+    // 1. the batch's sorted order by its full keys: any superset of the
+    //    batch's D-bitmap orders it (Theorem 2), and the all-ones bitmap is
+    //    known here without reading the device, so the call never waits for
+    //    the GPU (a batch is small: the extra passes cost little)
+    const uint32_t key_bits = 8u * keys->key_bytes, mw = (key_bits + 63) / 64;
+    static thread_local uint64_t full_mask[(8 * CK_MAX_KEY_BYTES + 63) / 64];
+    for (uint32_t w = 0; w < mw; ++w)
+        full_mask[w] = (w + 1 < mw || key_bits % 64 == 0) ? ~0ull : ~0ull << (64 - key_bits % 64);
+    ck_status st = ck_extract(batch, full_mask, P.K, at(P.off_ck), stream);
     if (st != CK_OK) return st;
-    const uint32_t mw = (uint32_t)((8ull * keys->key_bytes + 63) / 64);
-    static thread_local uint64_t host_mask[(8 * CK_MAX_KEY_BYTES + 63) / 64];
-    if (cudaMemcpyAsync(host_mask, bmask, 8ull * mw, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-        cudaStreamSynchronize(s) != cudaSuccess)
-        return CK_ECUDA;
-    uint32_t nbits = 0;
-    for (uint32_t w = 0; w < mw; ++w) nbits += (uint32_t)__builtin_popcountll(host_mask[w]);
-    if (nbits == 0) {  // all batch keys are equal: any order is sorted
-        iota_u32<<<num_sms() * 4, 256, 0, s>>>(border, m);
-        count_launch();
-        if (cudaGetLastError() != cudaSuccess) return CK_ECUDA;
-    } else {
-        const uint32_t K = (nbits + 31) / 32;
-        st = ck_extract(batch, host_mask, K, at(P.off_ck), stream);
-        if (st != CK_OK) return st;
-        st = ck_sort(at(P.off_ck), nullptr, at(P.off_ck_sorted), border, m, K, nbits, nullptr, ws + P.off_sort_ws,
-                     ws_bytes - P.off_sort_ws, stream);
-        if (st != CK_OK) return st;
-    }
+    st = ck_sort(at(P.off_ck), nullptr, at(P.off_ck_sorted), border, m, P.K, key_bits, nullptr, ws + P.off_sort_ws,
+                 ws_bytes - P.off_sort_ws, stream);
+    if (st != CK_OK) return st;
 
     // 2. every batch key's neighbours in the merged order: D-bits and variant bits
     unsigned long long* status = status_ptr();

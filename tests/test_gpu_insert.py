@@ -90,8 +90,8 @@ def test_insert_matches_oracle_integers(dtype):
 
 
 def test_insert_keeps_stale_bits_and_handles_equal_batches():
-    """Bits a delete left behind stay set (Sec. 4.3); a batch of equal keys and
-    a one-key batch go through the unsorted path."""
+    """Bits a delete left behind stay set (Sec. 4.3); a batch of equal keys, a
+    one-key batch and a batch of zero keys are handled."""
     rng = np.random.default_rng(5)
     old = structured(rng, 5000, 6, 12)
     ref = 0
@@ -116,6 +116,33 @@ def test_insert_grown_url_index():
     got_d, got_v = run_insert(old, new, ref, d0, v0)
     assert np.array_equal(got_d, oracle.dmask(keys))
     assert np.array_equal(got_v, oracle.variant_mask(keys, ref))
+
+
+def test_insert_in_a_cuda_graph():
+    """The call never waits for the GPU, so it can be captured: a replayed
+    graph gives the bitmaps of the eager call."""
+    rng = np.random.default_rng(21)
+    allk = structured(rng, 60_000, 16, 40)
+    old, new = allk[:50_000], allk[50_000:]
+    ref = 3
+    d0, v0 = oracle.dmask(old), oracle.variant_mask(old, ref)
+    want_d, want_v = run_insert(old, new, ref, d0, v0)          # eager, also the library's first call here
+    od, nd = dev(old), dev(new)
+    order = dev(oracle.sort_rows(old).view(np.int32))
+    d, v = mask_dev(d0), mask_dev(v0)
+    ws = torch.empty(max(ck._lib().ck_insert_workspace_bytes(len(new), 16), 256), dtype=torch.uint8, device=DEV)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        with torch.cuda.graph(g, stream=s):
+            ck.ck_insert_batch(od, order, nd, ref, d, v, ws=ws, stream=s)
+    d.copy_(mask_dev(d0))
+    v.copy_(mask_dev(v0))
+    g.replay()
+    torch.cuda.synchronize()
+    assert np.array_equal(host_mask(d), want_d) and np.array_equal(host_mask(v), want_v)
+    assert ck.ck_device_status()[0] == ck.CK_OK
 
 
 def test_insert_argument_errors():
