@@ -140,28 +140,23 @@ __device__ __forceinline__ void insertion_sort(const V& v, uint32_t p, uint32_t 
 }
 
 // One warp sorts A[p, p + len) (2 <= len <= 32) whose pairs share every
-// composite bit above window W: lane i ranks pair i by (window value,
-// position) among the others; pairs with equal window values are then put in
-// full composite order by an insertion sort of lane 0 (the range is already
-// in order apart from them).
+// composite bit above window W: lane i ranks pair i among the others by
+// window value and, where two window values are equal, by the full composite
+// key (read from shared memory for those pairs only), so every pair gets its
+// final slot at once.
 template <class V>
 __device__ __forceinline__ void warp_rank_sort(const V& v, const LsWin& W, uint32_t p, uint32_t len) {
     const uint32_t lane = threadIdx.x & 31;
     const bool in = lane < len;
     const uint32_t e = in ? v.A[p + lane] : 0u;
     const uint32_t w = in ? W(v, e) : 0xFFFFFFFFu;
-    const uint64_t k = in ? (((uint64_t)w << 16) | e) : ~0ull;
     uint32_t rank = 0;
-    bool tie = false;
     for (uint32_t j = 0; j < len; ++j) {
-        const uint64_t kj = __shfl_sync(kFull, k, j);
-        rank += kj < k ? 1u : 0u;
-        tie |= j != lane && (uint32_t)(kj >> 16) == w;
+        const uint32_t wj = __shfl_sync(kFull, w, j), ej = __shfl_sync(kFull, e, j);
+        if (in && j != lane) rank += (wj < w || (wj == w && v.less(ej, e))) ? 1u : 0u;
     }
     __syncwarp();
     if (in) v.A[p + rank] = (uint16_t)e;
-    __syncwarp();
-    if (__any_sync(kFull, in && tie) && lane == 0) insertion_sort(v, p, len);
     __syncwarp();
 }
 
