@@ -215,6 +215,38 @@ __device__ __forceinline__ uint32_t block_exclusive_sum(uint32_t x, uint32_t* ws
     return r;
 }
 
+// Group-wide exclusive prefix of one 64-bit value per thread (several
+// counters packed in bit fields); *total = the sum.  Ends without a barrier:
+// the caller synchronises the group before wsum is written again.
+template <int G = kLsThreads>
+__device__ __forceinline__ uint64_t group_exclusive_sum64(uint64_t x, uint64_t* wsum /*[kWarps + 1]*/,
+                                                          uint64_t* total, LsGroup<G> grp = LsGroup<G>{0}) {
+    constexpr uint32_t kWarps = LsGroup<G>::kWarps;
+    const uint32_t lane = threadIdx.x & 31, warp = grp.tid() >> 5;
+    uint64_t inc = x;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint64_t t = __shfl_up_sync(kFull, inc, o);
+        if (lane >= (uint32_t)o) inc += t;
+    }
+    if (lane == 31) wsum[warp] = inc;
+    grp.sync();
+    if (warp == 0) {
+        const uint64_t w = lane < kWarps ? wsum[lane] : 0ull;
+        uint64_t wi = w;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint64_t t = __shfl_up_sync(kFull, wi, o);
+            if (lane >= (uint32_t)o) wi += t;
+        }
+        if (lane < kWarps) wsum[lane] = wi - w;
+        if (lane == 31) wsum[kWarps] = wi;
+    }
+    grp.sync();
+    *total = wsum[kWarps];
+    return wsum[warp] + inc - x;
+}
+
 // Step 2: one warp splits range A[p0, p0 + r) (r > kLsRank) into 256 bins of
 // its own window; short bins are finished at once, longer ones listed.
 template <int KW>
@@ -464,6 +496,7 @@ struct LsBlockState {
     uint32_t* orw;     // [KC]
     uint32_t* mm;      // [2]: window minimum, maximum
     uint32_t* wsum;    // [kLsWarps + 1]
+    uint64_t* wsum64;  // [kLsWarps + 1]
     uint16_t* bytes;   // [3][256]: dense codes (digit terms, < kLsBins) of the window's top three bytes
     uint32_t* pres;    // [3][8]: which values each of those bytes takes (bitmaps)
     uint32_t* nbytes;  // [3]: values in use of each byte
@@ -599,46 +632,72 @@ __device__ void block_split(const LsView<KW>& v, uint32_t p0, uint32_t r, bool i
     };
     for (uint32_t p = p0 + tid; p < pe; p += G) atomicAdd(&hist[digit(W(v, ident ? p : v.A[p]))], 1u);
     grp.sync();
-    bins_exclusive_scan<G>(hist, bins, st.wsum, grp);
+    // One pass over the bins, each thread on a chunk of c consecutive ones
+    // (bins is a multiple of 32, so every chunk is whole): the bins' starts
+    // and how many short bins of each kind come before the chunk, in one
+    // group scan of three packed counters.  hist[d] becomes start | size << 16
+    // (both < 2^15 <= cap), so the scatter's increments leave the size intact.
+    const uint32_t c = bins <= G ? 1u : (bins <= 2 * G ? 2u : (bins <= 4 * G ? 4u : 8u));
+    const uint32_t d0 = tid * c;
+    const bool mine = d0 < bins;
+    uint32_t as, ar, ns_tot, nr_tot;
+    {
+        uint32_t cnt[8];
+        uint32_t tot = 0, ns = 0, nr = 0;
+#pragma unroll
+        for (uint32_t i = 0; i < 8; ++i) {
+            cnt[i] = mine && i < c ? hist[d0 + i] : 0u;
+            tot += cnt[i];
+            ns += (cnt[i] >= 2 && cnt[i] <= kLsSmall) ? 1u : 0u;
+            nr += (cnt[i] > kLsSmall && cnt[i] <= kLsRank) ? 1u : 0u;
+        }
+        uint64_t all;
+        const uint64_t ex = group_exclusive_sum64<G>((uint64_t)tot | (uint64_t)ns << 21 | (uint64_t)nr << 42,
+                                                     st.wsum64, &all, grp);
+        uint32_t start = (uint32_t)ex & 0x1FFFFFu;
+        as = (uint32_t)(ex >> 21) & 0x1FFFFFu;
+        ar = (uint32_t)(ex >> 42);
+        ns_tot = (uint32_t)(all >> 21) & 0x1FFFFFu;
+        nr_tot = (uint32_t)(all >> 42);
+#pragma unroll
+        for (uint32_t i = 0; i < 8; ++i)
+            if (mine && i < c) {
+                hist[d0 + i] = start | cnt[i] << 16;
+                start += cnt[i];
+            }
+    }
+    grp.sync();
     if (ident) {
-        for (uint32_t p = tid; p < r; p += G) v.A[atomicAdd(&hist[digit(W(v, p))], 1u)] = (uint16_t)p;
+        for (uint32_t p = tid; p < r; p += G) v.A[atomicAdd(&hist[digit(W(v, p))], 1u) & 0xFFFFu] = (uint16_t)p;
     } else {
         for (uint32_t p = p0 + tid; p < pe; p += G) {
             const uint32_t e = v.A[p];
-            v.T[p0 + atomicAdd(&hist[digit(W(v, e))], 1u)] = (uint16_t)e;
+            v.T[p0 + (atomicAdd(&hist[digit(W(v, e))], 1u) & 0xFFFFu)] = (uint16_t)e;
         }
         grp.sync();
         for (uint32_t p = p0 + tid; p < pe; p += G) v.A[p] = v.T[p];
     }
     grp.sync();
-    // hist[d] is now the end of bin d (relative to p0).  Long bins are listed
-    // for the block or the warps; the short ones densely in T[p0 ..] as
-    // (start, length) pairs, 2 .. 4 pairs from the front (one thread each),
-    // 5 .. 32 from the back (one warp each).  A listed bin has two pairs or
-    // more, so both lists fit the range's r entries of T.
-    uint32_t nsmall = 0, nrank = 0;
-    for (uint32_t d = tid; d < bins; d += G) {
-        const uint32_t b0 = d ? hist[d - 1] : 0u, sz = hist[d] - b0;
+    // hist[d] is now (end of bin d) | size << 16 (relative to p0).  Long bins
+    // are listed for the block or the warps; the short ones densely in
+    // T[p0 ..] as (start, length) pairs, 2 .. 4 pairs from the front (one
+    // thread each), 5 .. 32 from the back (one warp each).  A listed bin has
+    // two pairs or more, so both lists fit the range's r entries of T.
+#pragma unroll
+    for (uint32_t i = 0; i < 8; ++i) {
+        if (!mine || i >= c) break;
+        const uint32_t h = hist[d0 + i], sz = h >> 16, b0 = (h & 0xFFFFu) - sz;
         if (sz >= kLsBlockRange) {
             const uint32_t slot = atomicAdd(st.scount, 1u);
             if (slot < (uint32_t)kLsBlockStack) st.stack[slot] = (p0 + b0) | (sz << 16);
             else atomicAdd(bad, 1u);  // cannot happen (disjoint ranges of 256 or more pairs)
         } else if (sz > kLsRank) {
             push_range(st.list, st.count, p0 + b0, sz, bad);
-        }
-        nsmall += (sz >= 2 && sz <= kLsSmall) ? 1u : 0u;
-        nrank += (sz > kLsSmall && sz <= kLsRank) ? 1u : 0u;
-    }
-    uint32_t ns_tot, nr_tot;
-    uint32_t as = block_exclusive_sum<G>(nsmall, st.wsum, &ns_tot, grp);
-    uint32_t ar = block_exclusive_sum<G>(nrank, st.wsum, &nr_tot, grp);
-    for (uint32_t d = tid; d < bins; d += G) {
-        const uint32_t b0 = d ? hist[d - 1] : 0u, sz = hist[d] - b0;
-        if (sz >= 2 && sz <= kLsSmall) {
+        } else if (sz >= 2 && sz <= kLsSmall) {
             v.T[p0 + 2 * as] = (uint16_t)(p0 + b0);
             v.T[p0 + 2 * as + 1] = (uint16_t)sz;
             ++as;
-        } else if (sz > kLsSmall && sz <= kLsRank) {
+        } else if (sz > kLsSmall) {
             v.T[pe - 2 - 2 * ar] = (uint16_t)(p0 + b0);
             v.T[pe - 1 - 2 * ar] = (uint16_t)sz;
             ++ar;
@@ -1003,7 +1062,7 @@ __global__ void __launch_bounds__(kLsThreads, 1) local_sort_kernel(const LocalSo
     __shared__ uint32_t s_gor[4][kMaxLearnedWords + 1], s_gmm[4][2], s_gwsum[4][kLsThreads / 4 / 32 + 1];
     __shared__ uint16_t s_gbytes[4][768];
     __shared__ uint32_t s_gpres[4][24], s_gnbytes[4][3];
-    __shared__ uint32_t s_wpres[kLsWarps][16];  // warp splits: bitmaps of the window's top two bytes
+    __shared__ __align__(16) uint32_t s_wpres[kLsWarps][16];  // warp splits: bitmaps of the window's top two bytes
     __shared__ uint32_t s_scan[kLsWarps + 1];
     const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     constexpr uint32_t K = KW, KC = KW + 1;
@@ -1026,6 +1085,11 @@ __global__ void __launch_bounds__(kLsThreads, 1) local_sort_kernel(const LocalSo
     bst.orw = s_or;
     bst.mm = s_mm;
     bst.wsum = s_scan;
+    // the 64-bit scans of the block splits borrow the warp splits' bitmaps (the
+    // two never run at the same time): the block's, then each quarter's
+    static_assert(sizeof(s_wpres) >= 8 * (kLsWarps + 1 + 4 * (kLsThreads / 4 / 32 + 1)), "scan storage");
+    uint64_t* scan64 = reinterpret_cast<uint64_t*>(&s_wpres[0][0]);
+    bst.wsum64 = scan64;
     bst.bytes = s_bytes;
     bst.pres = s_pres;
     bst.nbytes = s_nbytes;
@@ -1035,6 +1099,7 @@ __global__ void __launch_bounds__(kLsThreads, 1) local_sort_kernel(const LocalSo
         gst.orw = s_gor[g];
         gst.mm = s_gmm[g];
         gst.wsum = s_gwsum[g];
+        gst.wsum64 = scan64 + (kLsWarps + 1) + g * (kLsThreads / 4 / 32 + 1);
         gst.bytes = s_gbytes[g];
         gst.pres = s_gpres[g];
         gst.nbytes = s_gnbytes[g];
