@@ -20,10 +20,11 @@
 //     places almost every pair, the keys of a bucket spanning a narrow key
 //     range;
 //  2. the short bins are listed densely: 2 to 4 pairs are finished by one
-//     thread (insertion sort), 5 to 32 by one warp -- each lane holds one
-//     pair's window value and counts the smaller ones by shuffles, so the keys
-//     are read from shared memory once, not at every comparison (equal
-//     windows, rare, are then settled by an insertion sort on the full keys).
+//     thread (a sorting network over their window values in registers), 5 to
+//     32 by one warp -- each lane holds one pair's window value and counts
+//     the smaller ones by shuffles -- so the keys are read from shared memory
+//     once, not at every comparison (equal windows, rare, are ordered by the
+//     full composite keys).
 //     A bin of 256 pairs or more is split again by the whole block in the same
 //     way (its own window, bins sized to it); the bins in between go to warps,
 //     which repeat the split with 256 bins, until every range is short.  The
@@ -46,7 +47,7 @@ constexpr int kLsBinBits = 13;
 constexpr int kLsBins = 1 << kLsBinBits;            // 8192 bins in step 1
 constexpr int kLsWarpBins = kLsBins / kLsWarps;      // 256 bins per warp in step 2
 constexpr int kLsWarpBinBits = 8;
-constexpr uint32_t kLsSmall = 4;                     // bins up to this length: insertion sort by one thread
+constexpr uint32_t kLsSmall = 4;                     // bins up to this length: sorted by one thread (narrow: insertion sort)
 constexpr uint32_t kLsRank = 32;                     // bins up to this length: rank sort by one warp
 constexpr uint32_t kLsBlockRange = 256;              // ranges from this length on are split by a block group:
 constexpr uint32_t kLsGroupRange = 1024;             // a quarter of the block below this length, else the block
@@ -125,18 +126,36 @@ __device__ __forceinline__ int top_bit_of(const uint32_t* orw) {
     return top;
 }
 
-// Stable insertion sort of A[p, p + len) by composite key (one thread).
+// One thread sorts A[p, p + len) (2 <= len <= 4) whose pairs share every
+// composite bit above window W: the positions and window values are held in
+// registers and put in order by a five-comparator network; equal window
+// values (rare) are ordered by the full composite key.
 template <class V>
-__device__ __forceinline__ void insertion_sort(const V& v, uint32_t p, uint32_t len) {
-    for (uint32_t j = p + 1; j < p + len; ++j) {
-        const uint16_t x = v.A[j];
-        uint32_t k = j;
-        while (k > p && v.less(x, v.A[k - 1])) {
-            v.A[k] = v.A[k - 1];
-            --k;
-        }
-        v.A[k] = x;
+__device__ __forceinline__ void small_sort(const V& v, const LsWin& W, uint32_t p, uint32_t len) {
+    uint32_t e[4], x[4];
+#pragma unroll
+    for (uint32_t i = 0; i < 4; ++i) {
+        e[i] = i < len ? v.A[p + i] : 0xFFFFu;  // 0xFFFF: padding, after every pair
+        x[i] = i < len ? W(v, e[i]) : 0xFFFFFFFFu;
     }
+    auto cs = [&](int a, int b) {
+        const bool sw = x[b] < x[a] || (x[b] == x[a] && e[b] != 0xFFFFu && (e[a] == 0xFFFFu || v.less(e[b], e[a])));
+        if (sw) {
+            const uint32_t te = e[a], tx = x[a];
+            e[a] = e[b];
+            x[a] = x[b];
+            e[b] = te;
+            x[b] = tx;
+        }
+    };
+    cs(0, 1);
+    cs(2, 3);
+    cs(0, 2);
+    cs(1, 3);
+    cs(1, 2);
+#pragma unroll
+    for (uint32_t i = 0; i < 4; ++i)
+        if (i < len) v.A[p + i] = (uint16_t)e[i];
 }
 
 // One warp sorts A[p, p + len) (2 <= len <= 32) whose pairs share every
@@ -391,7 +410,7 @@ __device__ void warp_split_range(const LsView<KW>& v, uint32_t p0, uint32_t r, u
         else if (sz[i] > kLsSmall && sz[i] <= kLsRank) wh[kLsWarpBins - 1 - ar++] = (p0 + st[i]) | (sz[i] << 16);
     }
     __syncwarp();
-    for (uint32_t k = lane; k < tot_s; k += 32) insertion_sort(v, wh[k] & 0xFFFFu, wh[k] >> 16);
+    for (uint32_t k = lane; k < tot_s; k += 32) small_sort(v, W, wh[k] & 0xFFFFu, wh[k] >> 16);
     __syncwarp();
     for (uint32_t k = 0; k < tot_r; ++k) {
         const uint32_t r = wh[kLsWarpBins - 1 - k];
@@ -543,9 +562,10 @@ __device__ void block_split(const LsView<KW>& v, uint32_t p0, uint32_t r, bool i
     const LsWin W((uint32_t)(P >= 31 ? P - 31 : 0), KC);
     uint32_t F = 32 - __clz(r - 1);  // 2^F >= r
     F = F < 8 ? 8u : (F > (uint32_t)kLsBinBits ? (uint32_t)kLsBinBits : F);
-    // bins of the dense digit: twice the power of two above the range's
-    // length (the scan and the bin lists cost in proportion to the bins)
-    const uint32_t dbins = F + 1 > (uint32_t)kLsBinBits ? (uint32_t)kLsBins : 2u << F;
+    // bins of the digit: the power of two at or above the range's length
+    // (the scan and the bin lists cost in proportion to the bins, more than
+    // the extra short bins that fewer bins leave cost to sort)
+    const uint32_t dbins = 1u << F;
     for (uint32_t d = tid; d < dbins; d += G) hist[d] = 0;
     if (tid < 24) st.pres[tid] = 0;
     if (tid == 0) {
@@ -630,7 +650,15 @@ __device__ void block_split(const LsView<KW>& v, uint32_t p0, uint32_t r, bool i
     auto digit = [&](uint32_t x) -> uint32_t {
         return dense ? c1[x >> 24] + c2[(x >> 16) & 255u] + c3[(x >> 8) & 255u] : (x - wmin) >> sh;
     };
-    for (uint32_t p = p0 + tid; p < pe; p += G) atomicAdd(&hist[digit(W(v, ident ? p : v.A[p]))], 1u);
+    if (ident) {  // the digits wait in T for the scatter (T is free until then)
+        for (uint32_t p = tid; p < r; p += G) {
+            const uint32_t d = digit(W(v, p));
+            v.T[p] = (uint16_t)d;
+            atomicAdd(&hist[d], 1u);
+        }
+    } else {
+        for (uint32_t p = p0 + tid; p < pe; p += G) atomicAdd(&hist[digit(W(v, v.A[p]))], 1u);
+    }
     grp.sync();
     // One pass over the bins, each thread on a chunk of c consecutive ones
     // (bins is a multiple of 32, so every chunk is whole): the bins' starts
@@ -668,7 +696,7 @@ __device__ void block_split(const LsView<KW>& v, uint32_t p0, uint32_t r, bool i
     }
     grp.sync();
     if (ident) {
-        for (uint32_t p = tid; p < r; p += G) v.A[atomicAdd(&hist[digit(W(v, p))], 1u) & 0xFFFFu] = (uint16_t)p;
+        for (uint32_t p = tid; p < r; p += G) v.A[atomicAdd(&hist[v.T[p]], 1u) & 0xFFFFu] = (uint16_t)p;
     } else {
         for (uint32_t p = p0 + tid; p < pe; p += G) {
             const uint32_t e = v.A[p];
@@ -704,7 +732,7 @@ __device__ void block_split(const LsView<KW>& v, uint32_t p0, uint32_t r, bool i
         }
     }
     grp.sync();
-    for (uint32_t k = tid; k < ns_tot; k += G) insertion_sort(v, v.T[p0 + 2 * k], v.T[p0 + 2 * k + 1]);
+    for (uint32_t k = tid; k < ns_tot; k += G) small_sort(v, W, v.T[p0 + 2 * k], v.T[p0 + 2 * k + 1]);
     for (uint32_t k = tid >> 5; k < nr_tot; k += kWarps)
         warp_rank_sort(v, W, v.T[pe - 2 - 2 * k], v.T[pe - 1 - 2 * k]);
     grp.sync();
