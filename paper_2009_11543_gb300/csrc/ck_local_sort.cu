@@ -48,6 +48,7 @@ constexpr int kLsBins = 1 << kLsBinBits;            // 8192 bins in step 1
 constexpr int kLsWarpBins = kLsBins / kLsWarps;      // 256 bins per warp in step 2
 constexpr int kLsWarpBinBits = 8;
 constexpr uint32_t kLsSmall = 4;                     // bins up to this length: sorted by one thread (narrow: insertion sort)
+constexpr uint32_t kLsSeg = 8;                       // bins up to this length: rank sort by eight lanes
 constexpr uint32_t kLsRank = 32;                     // bins up to this length: rank sort by one warp
 constexpr uint32_t kLsBlockRange = 256;              // ranges from this length on are split by a block group:
 constexpr uint32_t kLsGroupRange = 1024;             // a quarter of the block below this length, else the block
@@ -173,6 +174,26 @@ __device__ __forceinline__ void warp_rank_sort(const V& v, const LsWin& W, uint3
     for (uint32_t j = 0; j < len; ++j) {
         const uint32_t wj = __shfl_sync(kFull, w, j), ej = __shfl_sync(kFull, e, j);
         if (in && j != lane) rank += (wj < w || (wj == w && v.less(ej, e))) ? 1u : 0u;
+    }
+    __syncwarp();
+    if (in) v.A[p + rank] = (uint16_t)e;
+    __syncwarp();
+}
+
+// Eight lanes sort A[p, p + len) (len <= 8; len = 0: nothing) like
+// warp_rank_sort, so a warp sorts four such bins at once.  Every lane of the
+// warp calls this.
+template <class V>
+__device__ __forceinline__ void seg8_rank_sort(const V& v, const LsWin& W, uint32_t p, uint32_t len) {
+    const uint32_t j = threadIdx.x & 7;
+    const bool in = j < len;
+    const uint32_t e = in ? v.A[p + j] : 0u;
+    const uint32_t w = in ? W(v, e) : 0xFFFFFFFFu;
+    uint32_t rank = 0;
+#pragma unroll
+    for (uint32_t i = 0; i < 8; ++i) {
+        const uint32_t wi = __shfl_sync(kFull, w, i, 8), ei = __shfl_sync(kFull, e, i, 8);
+        if (in && i < len && i != j) rank += (wi < w || (wi == w && v.less(ei, e))) ? 1u : 0u;
     }
     __syncwarp();
     if (in) v.A[p + rank] = (uint16_t)e;
@@ -668,25 +689,29 @@ __device__ void block_split(const LsView<KW>& v, uint32_t p0, uint32_t r, bool i
     const uint32_t c = bins <= G ? 1u : (bins <= 2 * G ? 2u : (bins <= 4 * G ? 4u : 8u));
     const uint32_t d0 = tid * c;
     const bool mine = d0 < bins;
-    uint32_t as, ar, ns_tot, nr_tot;
+    uint32_t as, a8, ar, ns_tot, n8_tot, nr_tot;
     {
         uint32_t cnt[8];
-        uint32_t tot = 0, ns = 0, nr = 0;
+        uint32_t tot = 0, ns = 0, n8 = 0, nr = 0;
 #pragma unroll
         for (uint32_t i = 0; i < 8; ++i) {
             cnt[i] = mine && i < c ? hist[d0 + i] : 0u;
             tot += cnt[i];
             ns += (cnt[i] >= 2 && cnt[i] <= kLsSmall) ? 1u : 0u;
-            nr += (cnt[i] > kLsSmall && cnt[i] <= kLsRank) ? 1u : 0u;
+            n8 += (cnt[i] > kLsSmall && cnt[i] <= kLsSeg) ? 1u : 0u;
+            nr += (cnt[i] > kLsSeg && cnt[i] <= kLsRank) ? 1u : 0u;
         }
+        // four 16-bit fields: every count and sum is at most r <= cap < 2^16
         uint64_t all;
-        const uint64_t ex = group_exclusive_sum64<G>((uint64_t)tot | (uint64_t)ns << 21 | (uint64_t)nr << 42,
-                                                     st.wsum64, &all, grp);
-        uint32_t start = (uint32_t)ex & 0x1FFFFFu;
-        as = (uint32_t)(ex >> 21) & 0x1FFFFFu;
-        ar = (uint32_t)(ex >> 42);
-        ns_tot = (uint32_t)(all >> 21) & 0x1FFFFFu;
-        nr_tot = (uint32_t)(all >> 42);
+        const uint64_t ex = group_exclusive_sum64<G>(
+            (uint64_t)tot | (uint64_t)ns << 16 | (uint64_t)n8 << 32 | (uint64_t)nr << 48, st.wsum64, &all, grp);
+        uint32_t start = (uint32_t)ex & 0xFFFFu;
+        as = (uint32_t)(ex >> 16) & 0xFFFFu;
+        a8 = (uint32_t)(ex >> 32) & 0xFFFFu;
+        ar = (uint32_t)(ex >> 48);
+        ns_tot = (uint32_t)(all >> 16) & 0xFFFFu;
+        n8_tot = (uint32_t)(all >> 32) & 0xFFFFu;
+        nr_tot = (uint32_t)(all >> 48);
 #pragma unroll
         for (uint32_t i = 0; i < 8; ++i)
             if (mine && i < c) {
@@ -708,9 +733,10 @@ __device__ void block_split(const LsView<KW>& v, uint32_t p0, uint32_t r, bool i
     grp.sync();
     // hist[d] is now (end of bin d) | size << 16 (relative to p0).  Long bins
     // are listed for the block or the warps; the short ones densely in
-    // T[p0 ..] as (start, length) pairs, 2 .. 4 pairs from the front (one
-    // thread each), 5 .. 32 from the back (one warp each).  A listed bin has
-    // two pairs or more, so both lists fit the range's r entries of T.
+    // T[p0 ..] as (start, length) pairs: 2 .. 4 pairs from the front (one
+    // thread each), then 9 .. 32 (one warp each), and 5 .. 8 from the back
+    // (eight lanes each).  A listed bin has two pairs or more, so the lists
+    // fit the range's r entries of T.
 #pragma unroll
     for (uint32_t i = 0; i < 8; ++i) {
         if (!mine || i >= c) break;
@@ -725,16 +751,27 @@ __device__ void block_split(const LsView<KW>& v, uint32_t p0, uint32_t r, bool i
             v.T[p0 + 2 * as] = (uint16_t)(p0 + b0);
             v.T[p0 + 2 * as + 1] = (uint16_t)sz;
             ++as;
-        } else if (sz > kLsSmall) {
-            v.T[pe - 2 - 2 * ar] = (uint16_t)(p0 + b0);
-            v.T[pe - 1 - 2 * ar] = (uint16_t)sz;
+        } else if (sz > kLsSeg) {
+            v.T[p0 + 2 * (ns_tot + ar)] = (uint16_t)(p0 + b0);
+            v.T[p0 + 2 * (ns_tot + ar) + 1] = (uint16_t)sz;
             ++ar;
+        } else if (sz > kLsSmall) {
+            v.T[pe - 2 - 2 * a8] = (uint16_t)(p0 + b0);
+            v.T[pe - 1 - 2 * a8] = (uint16_t)sz;
+            ++a8;
         }
     }
     grp.sync();
+    // the first threads take the odd small bins, the last warps the odd
+    // longer ones
+    const uint32_t rw = kWarps - 1 - (tid >> 5);
     for (uint32_t k = tid; k < ns_tot; k += G) small_sort(v, W, v.T[p0 + 2 * k], v.T[p0 + 2 * k + 1]);
-    for (uint32_t k = tid >> 5; k < nr_tot; k += kWarps)
-        warp_rank_sort(v, W, v.T[pe - 2 - 2 * k], v.T[pe - 1 - 2 * k]);
+    for (uint32_t k0 = 4 * rw; k0 < n8_tot; k0 += 4 * kWarps) {  // uniform in the warp
+        const uint32_t k = k0 + (lane >> 3);
+        seg8_rank_sort(v, W, k < n8_tot ? v.T[pe - 2 - 2 * k] : 0u, k < n8_tot ? v.T[pe - 1 - 2 * k] : 0u);
+    }
+    for (uint32_t k = rw; k < nr_tot; k += kWarps)
+        warp_rank_sort(v, W, v.T[p0 + 2 * (ns_tot + k)], v.T[p0 + 2 * (ns_tot + k) + 1]);
     grp.sync();
 }
 
