@@ -1317,10 +1317,9 @@ __global__ void __launch_bounds__(kLsThreads, 1) local_sort_kernel(const LocalSo
             if (b + 1 < nb && cmp_key_spl(v, v.A[m - 1], a.spl + (size_t)b * K) >= 0) ++my_bad;
         }
         // row ids gathered into registers (the bucket is rewritten in place,
-        // so every read precedes the barrier below), then one pass of checks:
-        // adjacent keys ascend, equal keys by position and by row id (the row
-        // id of the pair before comes from the neighbouring lane, or, for a
-        // warp's first lane, from the row ids not yet overwritten)
+        // so every read precedes the barrier below); each warp's last lane
+        // leaves its row ids in shared memory for the next warp's first lane
+        // (s_wpres is free after the warp rounds: 32 warps x 16 rows)
         uint32_t rr[kLsPerThread];
         const uint32_t jmax = (m + kLsThreads - 1) / kLsThreads;
 #pragma unroll
@@ -1332,42 +1331,49 @@ __global__ void __launch_bounds__(kLsThreads, 1) local_sort_kernel(const LocalSo
             const uint32_t other = __shfl_xor_sync(kFull, rr[0], 1);
             if (warp == 0 && lane < 2 && m >= 2) rr[0] = other;
         }
+        static_assert(kLsPerThread <= 16, "one row id per warp and round in s_wpres");
+        if (lane == 31)
+#pragma unroll
+            for (int j = 0; j < kLsPerThread; ++j) s_wpres[warp][j] = rr[j];
+        __syncthreads();
+        // one pass: each pair is checked against the pair before it (adjacent
+        // keys ascend; equal keys by position and by row id) -- whose key,
+        // position and row id come from the neighbouring lane, or for a
+        // warp's first lane from shared memory -- and written back in order
+        // with the hash of every output pair
 #pragma unroll
         for (int j = 0; j < kLsPerThread; ++j) {
             if ((uint32_t)j >= jmax) break;  // uniform: every lane of the block has the same jmax
             const uint32_t t = tid + (uint32_t)j * kLsThreads;
-            const uint32_t before = __shfl_up_sync(kFull, rr[j], 1);
-            if (t >= 1 && t < m) {
-                const uint32_t e = v.A[t - 1], f = v.A[t];
+            const bool in = t < m;
+            const uint32_t f = in ? v.A[t] : 0u;
+            uint32_t x[KW];
+#pragma unroll
+            for (int w = 0; w < KW; ++w) x[w] = in ? v.key(f, w) : 0u;
+            uint32_t e = __shfl_up_sync(kFull, f, 1), rp = __shfl_up_sync(kFull, rr[j], 1);
+            uint32_t y[KW];
+#pragma unroll
+            for (int w = 0; w < KW; ++w) y[w] = __shfl_up_sync(kFull, x[w], 1);
+            if (lane == 0 && t >= 1 && in) {
+                e = v.A[t - 1];
+#pragma unroll
+                for (int w = 0; w < KW; ++w) y[w] = v.key(e, w);
+                rp = warp ? s_wpres[warp - 1][j] : s_wpres[kLsWarps - 1][j - 1];
+            }
+            if (t >= 1 && in) {
                 int c = 0;
 #pragma unroll
-                for (int w = KW - 1; w >= 0 && c == 0; --w) {
-                    const uint32_t x = v.key(e, w), y = v.key(f, w);
-                    c = x < y ? -1 : (x > y ? 1 : 0);
-                }
-                if (c > 0) {
-                    ++my_bad;
-                } else if (c == 0) {
-                    const uint32_t rp = lane ? before : a.rid[s0 + e];
-                    if (e >= f || rp >= rr[j]) ++my_bad;
-                }
+                for (int w = KW - 1; w >= 0; --w)
+                    if (c == 0) c = y[w] < x[w] ? -1 : (y[w] > x[w] ? 1 : 0);
+                if (c > 0 || (c == 0 && (e >= f || rp >= rr[j]))) ++my_bad;
             }
-        }
-        __syncthreads();
-        // write the bucket back in order: keys from shared memory, the row
-        // ids from registers, and the hash of every output pair
-#pragma unroll
-        for (int j = 0; j < kLsPerThread; ++j) {
-            const uint32_t t = tid + (uint32_t)j * kLsThreads;
-            if ((uint32_t)j < jmax && t < m) {
+            if (in) {
                 a.rid[s0 + t] = rr[j];
-                const uint32_t e = v.A[t];
                 uint64_t h = pair_hash_start(rr[j]);
 #pragma unroll
-                for (uint32_t w = 0; w < K; ++w) {
-                    const uint32_t x = v.key(e, w);
-                    a.ck[(uint64_t)w * a.ld + s0 + t] = x;
-                    h = pair_hash_word(h, x);
+                for (int w = 0; w < KW; ++w) {
+                    a.ck[(uint64_t)w * a.ld + s0 + t] = x[w];
+                    h = pair_hash_word(h, x[w]);
                 }
                 my_hash += pair_hash_end(h);
             }
