@@ -1114,12 +1114,22 @@ __device__ void sort_narrow_bucket(const LocalSortArgs& a, const LnView& v, uint
         if (lane == 0 && t > 0 && v.RS[t - 1] == v.RS[t] && a.rid[s0 + t - 1] >= a.rid[s0 + t]) ++*bad;
 }
 
+// Starts words [i0, i1) of a 32-bit array on their way into L2 (a hint that
+// is never waited for: only the 16-byte-aligned interior is named).
+__device__ __forceinline__ void prefetch_l2(const uint32_t* base, uint64_t i0, uint64_t i1) {
+    const uint64_t b0 = ((uint64_t)(uintptr_t)(base + i0) + 15) & ~15ull;
+    const uint64_t b1 = (uint64_t)(uintptr_t)(base + i1) & ~15ull;
+    if (b1 > b0)
+        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(b0), "r"((uint32_t)(b1 - b0)) : "memory");
+}
+
 template <int KW>
 __global__ void __launch_bounds__(kLsThreads, 1) local_sort_kernel(const LocalSortArgs a) {
     extern __shared__ __align__(16) unsigned char ls_raw[];
     __shared__ uint32_t s_list[2][kLsList];
     __shared__ uint32_t s_or[kMaxLearnedWords + 1];
-    __shared__ uint32_t s_mm[2], s_bucket, s_cnt[2], s_grab, s_bcnt, s_bad;
+    __shared__ uint32_t s_mm[2], s_bucket, s_next, s_cnt[2], s_grab, s_bcnt, s_bad;
+    __shared__ uint64_t s_rng[2], s_nrng[2];  // start, end of this bucket and of the next one
     __shared__ uint32_t s_bstack[kLsBlockStack];
     __shared__ uint16_t s_bytes[768];
     __shared__ uint32_t s_pres[24], s_nbytes[3];
@@ -1171,13 +1181,46 @@ __global__ void __launch_bounds__(kLsThreads, 1) local_sort_kernel(const LocalSo
     }
     uint64_t my_hash = 0;
     uint32_t my_bad = 0;
+    constexpr uint32_t kNone = 0xFFFFFFFEu;  // no bucket taken ahead
+    if (tid == 0) s_next = kNone;
     for (;;) {
-        if (tid == 0) s_bucket = *(volatile uint32_t*)&misc->fail ? 0xFFFFFFFFu : atomicAdd(&misc->queue, 1u);
+        // Thread 0 takes the bucket taken ahead in the round before (or a new
+        // one), then takes the following bucket now and starts its rows on
+        // their way into L2, so that its load finds them there.
+        if (tid == 0) {
+            uint32_t b = s_next;
+            if (*(volatile uint32_t*)&misc->fail) {
+                b = 0xFFFFFFFFu;
+            } else if (b == kNone) {
+                b = atomicAdd(&misc->queue, 1u);
+                if (b < nb) {
+                    s_nrng[0] = a.start[b];
+                    s_nrng[1] = a.start[b + 1];
+                }
+            }
+            s_bucket = b;
+            s_next = kNone;
+            if (b < nb) {
+                s_rng[0] = s_nrng[0];
+                s_rng[1] = s_nrng[1];
+                const uint32_t nx = atomicAdd(&misc->queue, 1u);
+                s_next = nx;  // >= nb: the next round ends the loop
+                if (nx < nb) {
+                    const uint64_t n0 = a.start[nx], n1 = a.start[nx + 1];
+                    s_nrng[0] = n0;
+                    s_nrng[1] = n1;
+                    if (n1 - n0 <= cap) {
+                        for (uint32_t w = 0; w < K; ++w) prefetch_l2(a.ck + (uint64_t)w * a.ld, n0, n1);
+                        prefetch_l2(a.rid, n0, n1);
+                    }
+                }
+            }
+        }
         __syncthreads();
         const uint32_t b = s_bucket;
         if (b >= nb) break;
-        const uint64_t s0 = a.start[b];
-        const uint32_t m = (uint32_t)(a.start[b + 1] - s0);
+        const uint64_t s0 = s_rng[0];
+        const uint32_t m = (uint32_t)(s_rng[1] - s0);
         if (m == 0) {
             __syncthreads();
             continue;
