@@ -255,6 +255,36 @@ __device__ __forceinline__ uint32_t block_exclusive_sum(uint32_t x, uint32_t* ws
     return r;
 }
 
+// The c words (c = 0, 1, 2, 4 or 8) of h[0, c), h aligned to 4c bytes, by
+// vector accesses; x[c ..] = 0.
+__device__ __forceinline__ void load_chunk(const uint32_t* h, uint32_t c, uint32_t (&x)[8]) {
+#pragma unroll
+    for (int i = 0; i < 8; ++i) x[i] = 0;
+    if (c >= 4) {
+        const uint4 u = reinterpret_cast<const uint4*>(h)[0];
+        x[0] = u.x; x[1] = u.y; x[2] = u.z; x[3] = u.w;
+        if (c == 8) {
+            const uint4 w = reinterpret_cast<const uint4*>(h)[1];
+            x[4] = w.x; x[5] = w.y; x[6] = w.z; x[7] = w.w;
+        }
+    } else if (c == 2) {
+        const uint2 u = *reinterpret_cast<const uint2*>(h);
+        x[0] = u.x; x[1] = u.y;
+    } else if (c == 1) {
+        x[0] = h[0];
+    }
+}
+__device__ __forceinline__ void store_chunk(uint32_t* h, uint32_t c, const uint32_t (&x)[8]) {
+    if (c >= 4) {
+        reinterpret_cast<uint4*>(h)[0] = make_uint4(x[0], x[1], x[2], x[3]);
+        if (c == 8) reinterpret_cast<uint4*>(h)[1] = make_uint4(x[4], x[5], x[6], x[7]);
+    } else if (c == 2) {
+        *reinterpret_cast<uint2*>(h) = make_uint2(x[0], x[1]);
+    } else {
+        h[0] = x[0];
+    }
+}
+
 // Group-wide exclusive prefix of one 64-bit value per thread (several
 // counters packed in bit fields); *total = the sum.  Ends without a barrier:
 // the caller synchronises the group before wsum is written again.
@@ -555,6 +585,12 @@ __device__ void block_split(const LsView<KW>& v, uint32_t p0, uint32_t r, bool i
     constexpr uint32_t kWarps = LsGroup<G>::kWarps;
     const uint32_t tid = grp.tid(), lane = tid & 31;
     const uint32_t pe = p0 + r;
+    // a quarter of the block holds its range's positions, then window values,
+    // then digits in registers (its ranges are shorter than 4 G)
+    constexpr bool kQuarter = G < kLsThreads;
+    constexpr uint32_t kQItems = 4;
+    static_assert(kLsGroupRange <= kQItems * (kLsThreads / 4), "quarter ranges fit the registers");
+    uint32_t qe[kQItems], qx[kQItems];
     if (!ident) {  // OR of every composite word's difference to the range's first element
         if (tid < KC) st.orw[tid] = 0;
         grp.sync();
@@ -599,8 +635,7 @@ __device__ void block_split(const LsView<KW>& v, uint32_t p0, uint32_t r, bool i
        // alphabet, whose bytes take few values, do not queue on a few words
         uint32_t lo = 0xFFFFFFFFu, hi = 0;
         volatile uint32_t* pr = st.pres;
-        for (uint32_t p = p0 + tid; p < pe; p += G) {
-            const uint32_t x = W(v, ident ? p : v.A[p]);
+        auto visit = [&](uint32_t x) {
             lo = min(lo, x);
             hi = max(hi, x);
             const uint32_t w1 = x >> 29, m1 = 1u << ((x >> 24) & 31u);
@@ -609,6 +644,19 @@ __device__ void block_split(const LsView<KW>& v, uint32_t p0, uint32_t r, bool i
             if (!(pr[w1] & m1)) atomicOr(&st.pres[w1], m1);
             if (!(pr[w2] & m2)) atomicOr(&st.pres[w2], m2);
             if (!(pr[w3] & m3)) atomicOr(&st.pres[w3], m3);
+        };
+        if constexpr (kQuarter) {
+#pragma unroll
+            for (uint32_t i = 0; i < kQItems; ++i) {
+                const uint32_t p = p0 + tid + i * G;
+                if (p < pe) {
+                    qe[i] = v.A[p];
+                    qx[i] = W(v, qe[i]);
+                    visit(qx[i]);
+                }
+            }
+        } else {
+            for (uint32_t p = p0 + tid; p < pe; p += G) visit(W(v, ident ? p : v.A[p]));
         }
         lo = __reduce_min_sync(kFull, lo);
         hi = __reduce_max_sync(kFull, hi);
@@ -678,7 +726,16 @@ __device__ void block_split(const LsView<KW>& v, uint32_t p0, uint32_t r, bool i
             atomicAdd(&hist[d], 1u);
         }
     } else {
-        for (uint32_t p = p0 + tid; p < pe; p += G) atomicAdd(&hist[digit(W(v, v.A[p]))], 1u);
+        if constexpr (kQuarter) {
+#pragma unroll
+            for (uint32_t i = 0; i < kQItems; ++i)
+                if (p0 + tid + i * G < pe) {
+                    qx[i] = digit(qx[i]);
+                    atomicAdd(&hist[qx[i]], 1u);
+                }
+        } else {
+            for (uint32_t p = p0 + tid; p < pe; p += G) atomicAdd(&hist[digit(W(v, v.A[p]))], 1u);
+        }
     }
     grp.sync();
     // One pass over the bins, each thread on a chunk of c consecutive ones
@@ -693,9 +750,9 @@ __device__ void block_split(const LsView<KW>& v, uint32_t p0, uint32_t r, bool i
     {
         uint32_t cnt[8];
         uint32_t tot = 0, ns = 0, n8 = 0, nr = 0;
+        load_chunk(hist + d0, mine ? c : 0u, cnt);
 #pragma unroll
         for (uint32_t i = 0; i < 8; ++i) {
-            cnt[i] = mine && i < c ? hist[d0 + i] : 0u;
             tot += cnt[i];
             ns += (cnt[i] >= 2 && cnt[i] <= kLsSmall) ? 1u : 0u;
             n8 += (cnt[i] > kLsSmall && cnt[i] <= kLsSeg) ? 1u : 0u;
@@ -712,20 +769,29 @@ __device__ void block_split(const LsView<KW>& v, uint32_t p0, uint32_t r, bool i
         ns_tot = (uint32_t)(all >> 16) & 0xFFFFu;
         n8_tot = (uint32_t)(all >> 32) & 0xFFFFu;
         nr_tot = (uint32_t)(all >> 48);
+        if (mine) {
+            uint32_t o[8];
 #pragma unroll
-        for (uint32_t i = 0; i < 8; ++i)
-            if (mine && i < c) {
-                hist[d0 + i] = start | cnt[i] << 16;
+            for (uint32_t i = 0; i < 8; ++i) {
+                o[i] = start | cnt[i] << 16;
                 start += cnt[i];
             }
+            store_chunk(hist + d0, c, o);
+        }
     }
     grp.sync();
     if (ident) {
         for (uint32_t p = tid; p < r; p += G) v.A[atomicAdd(&hist[v.T[p]], 1u) & 0xFFFFu] = (uint16_t)p;
     } else {
-        for (uint32_t p = p0 + tid; p < pe; p += G) {
-            const uint32_t e = v.A[p];
-            v.T[p0 + (atomicAdd(&hist[digit(W(v, e))], 1u) & 0xFFFFu)] = (uint16_t)e;
+        if constexpr (kQuarter) {
+#pragma unroll
+            for (uint32_t i = 0; i < kQItems; ++i)
+                if (p0 + tid + i * G < pe) v.T[p0 + (atomicAdd(&hist[qx[i]], 1u) & 0xFFFFu)] = (uint16_t)qe[i];
+        } else {
+            for (uint32_t p = p0 + tid; p < pe; p += G) {
+                const uint32_t e = v.A[p];
+                v.T[p0 + (atomicAdd(&hist[digit(W(v, e))], 1u) & 0xFFFFu)] = (uint16_t)e;
+            }
         }
         grp.sync();
         for (uint32_t p = p0 + tid; p < pe; p += G) v.A[p] = v.T[p];
@@ -737,10 +803,12 @@ __device__ void block_split(const LsView<KW>& v, uint32_t p0, uint32_t r, bool i
     // thread each), then 9 .. 32 (one warp each), and 5 .. 8 from the back
     // (eight lanes each).  A listed bin has two pairs or more, so the lists
     // fit the range's r entries of T.
+    uint32_t hc[8];
+    load_chunk(hist + d0, mine ? c : 0u, hc);
 #pragma unroll
     for (uint32_t i = 0; i < 8; ++i) {
         if (!mine || i >= c) break;
-        const uint32_t h = hist[d0 + i], sz = h >> 16, b0 = (h & 0xFFFFu) - sz;
+        const uint32_t h = hc[i], sz = h >> 16, b0 = (h & 0xFFFFu) - sz;
         if (sz >= kLsBlockRange) {
             const uint32_t slot = atomicAdd(st.scount, 1u);
             if (slot < (uint32_t)kLsBlockStack) st.stack[slot] = (p0 + b0) | (sz << 16);
