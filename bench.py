@@ -579,7 +579,7 @@ def measure_config(args, workload, world, local_rank, headline=False, extras=Fal
                                        "phase_alg_bytes": pb,
                                        "note": ("the bucket sorts move each pair once each way; their time is bound "
                                                 "by the chain of block-wide phases per bucket (barrier stalls, "
-                                                "shared-memory latency), not by DRAM, which is about 6% busy: "
+                                                "shared-memory latency), not by DRAM, which is about 8% busy: "
                                                 "profiles/local_sort_dna20m.md") if dom == "bucket_sorts_checks"
                                        else "two radix passes over the bucket id"}}
     rec["roofline"] = rec["learned"]["roofline"] if headline_learned else plain_roof
