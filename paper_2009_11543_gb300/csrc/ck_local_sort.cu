@@ -21,13 +21,15 @@
 //     range;
 //  2. the short bins are listed densely: 2 to 4 pairs are finished by one
 //     thread (a sorting network over their window values in registers), 5 to
-//     32 by one warp -- each lane holds one pair's window value and counts
-//     the smaller ones by shuffles -- so the keys are read from shared memory
-//     once, not at every comparison (equal windows, rare, are ordered by the
-//     full composite keys).
-//     A bin of 256 pairs or more is split again by the whole block in the same
-//     way (its own window, bins sized to it); the bins in between go to warps,
-//     which repeat the split with 256 bins, until every range is short.  The
+//     32 by eight lanes or a warp -- each lane holds one pair's window value
+//     and counts the smaller ones by shuffles -- so the keys are read from
+//     shared memory once, not at every comparison (equal windows, rare, are
+//     ordered by the full composite keys).
+//     A bin of 128 pairs or more is split again in the same way (its own
+//     window, bins sized to it) by a quarter of the block, four such bins at
+//     a time, or by the whole block from 1024 pairs on; the bins in between go
+//     to warps, which repeat the split with 256 bins, until every range is
+//     short.  The
 //     minimum and the maximum of a range always land in different bins, so
 //     every split shrinks the ranges it makes.
 //
@@ -50,9 +52,9 @@ constexpr int kLsWarpBinBits = 8;
 constexpr uint32_t kLsSmall = 4;                     // bins up to this length: sorted by one thread (narrow: insertion sort)
 constexpr uint32_t kLsSeg = 8;                       // bins up to this length: rank sort by eight lanes
 constexpr uint32_t kLsRank = 32;                     // bins up to this length: rank sort by one warp
-constexpr uint32_t kLsBlockRange = 256;              // ranges from this length on are split by a block group:
+constexpr uint32_t kLsBlockRange = 128;              // ranges from this length on are split by a block group:
 constexpr uint32_t kLsGroupRange = 1024;             // a quarter of the block below this length, else the block
-constexpr int kLsBlockStack = 64;                    // such ranges are disjoint: at most cap / 256
+constexpr int kLsBlockStack = 128;                   // such ranges are disjoint: at most cap / 128
 constexpr int kLsPerThread = 16;                     // register staging of row ids: cap <= 16 * 1024
 constexpr uint32_t kLsMaxCap = kLsPerThread * kLsThreads;
 constexpr int kLsList = 512;                         // pending ranges: disjoint, > 32 pairs each, so < cap / 33
@@ -345,11 +347,20 @@ __device__ void warp_split_range(const LsView<KW>& v, uint32_t p0, uint32_t r, u
     // warp's 2 x 256-bit bitmaps, a value's bit set once)
     if (lane < 16) wpres[lane] = 0;
     __syncwarp();
+    // each lane holds the positions and window values of its (at most four)
+    // pairs of the range in registers for the three passes below
+    static_assert(kLsBlockRange <= 4 * 32, "a warp's ranges fit four pairs per lane");
+    uint32_t we[4], wx[4];
     uint32_t lo = 0xFFFFFFFFu, hi = 0;
     {
         volatile uint32_t* pr = wpres;
-        for (uint32_t p = p0 + lane; p < pe; p += 32) {
-            const uint32_t x = W(v, v.A[p]);
+#pragma unroll
+        for (uint32_t i = 0; i < 4; ++i) {
+            const uint32_t p = p0 + lane + 32 * i;
+            we[i] = p < pe ? v.A[p] : 0u;
+            wx[i] = p < pe ? W(v, we[i]) : 0u;
+            if (p >= pe) continue;
+            const uint32_t x = wx[i];
             lo = min(lo, x);
             hi = max(hi, x);
             const uint32_t w1 = x >> 29, m1 = 1u << ((x >> 24) & 31u);
@@ -394,10 +405,12 @@ __device__ void warp_split_range(const LsView<KW>& v, uint32_t p0, uint32_t r, u
     };
     for (uint32_t i = lane; i < (uint32_t)kLsWarpBins; i += 32) wh[i] = 0;
     __syncwarp();
-    for (uint32_t q0 = p0; q0 < pe; q0 += 32) {  // warp-uniform trip count: digit() shuffles
-        const uint32_t p = q0 + lane;
-        const uint32_t d = digit(p < pe ? W(v, v.A[p]) : lo);
-        if (p < pe) atomicAdd(&wh[d], 1u);
+#pragma unroll
+    for (uint32_t i = 0; i < 4; ++i) {  // warp-uniform: digit() shuffles
+        if (32 * i >= r) break;
+        const uint32_t p = p0 + lane + 32 * i;
+        wx[i] = digit(p < pe ? wx[i] : lo);
+        if (p < pe) atomicAdd(&wh[wx[i]], 1u);
     }
     __syncwarp();
     {  // exclusive scan, 8 bins per lane
@@ -421,11 +434,10 @@ __device__ void warp_split_range(const LsView<KW>& v, uint32_t p0, uint32_t r, u
         }
     }
     __syncwarp();
-    for (uint32_t q0 = p0; q0 < pe; q0 += 32) {
-        const uint32_t p = q0 + lane;
-        const uint32_t e = p < pe ? v.A[p] : 0u;
-        const uint32_t d = digit(p < pe ? W(v, e) : lo);
-        if (p < pe) v.T[p0 + atomicAdd(&wh[d], 1u)] = (uint16_t)e;
+#pragma unroll
+    for (uint32_t i = 0; i < 4; ++i) {
+        const uint32_t p = p0 + lane + 32 * i;
+        if (p < pe) v.T[p0 + atomicAdd(&wh[wx[i]], 1u)] = (uint16_t)we[i];
     }
     __syncwarp();
     for (uint32_t p = p0 + lane; p < pe; p += 32) v.A[p] = v.T[p];
@@ -812,7 +824,7 @@ __device__ void block_split(const LsView<KW>& v, uint32_t p0, uint32_t r, bool i
         if (sz >= kLsBlockRange) {
             const uint32_t slot = atomicAdd(st.scount, 1u);
             if (slot < (uint32_t)kLsBlockStack) st.stack[slot] = (p0 + b0) | (sz << 16);
-            else atomicAdd(bad, 1u);  // cannot happen (disjoint ranges of 256 or more pairs)
+            else atomicAdd(bad, 1u);  // cannot happen (disjoint ranges of kLsBlockRange pairs or more)
         } else if (sz > kLsRank) {
             push_range(st.list, st.count, p0 + b0, sz, bad);
         } else if (sz >= 2 && sz <= kLsSmall) {
