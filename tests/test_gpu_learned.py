@@ -142,10 +142,10 @@ def prefix_group_keys(rng, n, groups, lo, hi, plen=24, width=32):
     return keys[rng.permutation(n)]
 
 
-@pytest.mark.parametrize("lo,hi", [(256, 1023), (100, 3000)])
+@pytest.mark.parametrize("lo,hi", [(128, 255), (256, 1023), (100, 3000)])
 def test_learned_shared_prefix_ranges(lo, hi):
     """Shared-prefix groups long enough that a bucket's first split leaves
-    ranges of 256..1023 pairs (split four at a time by quarter-block groups)
+    ranges of 128..1023 pairs (split four at a time by quarter-block groups)
     and of 1024 or more (split by the whole block), beside short ones (warps):
     the learned sort equals the plain sort bit for bit, without fallback."""
     rng = np.random.default_rng(lo + hi)
